@@ -1,0 +1,317 @@
+"""Benchmark of the coupled LB + Q-tensor step (MLUPS and HBM roofline fraction).
+
+Default workload: 256^3 periodic lattice, BPII unit cells of pitch 32
+(q0 = 2 pi / 32), A0 = 0.01, gamma = 3.1, K = 0.01, Gamma = 0.3, xi = 0.7,
+tau_f = 2, flow on, Jacobi coupling, FP32 state (FP64 only in diagnostics).
+A step is one coupled update of every site.  The state (4.5 GB) is far larger
+than L2 (129 MB), so no L2 flush is needed between timed steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle
+(a deliberately slow, plain implementation) on the host cores instead.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_SIDE = 256
+Q0 = 2 * np.pi / 32
+PARAMS = dict(A0=0.01, gamma=3.1, K=0.01, q0=Q0, Gamma=0.3, xi=0.7, tau_f=2.0)
+SEED = 20090119
+# algorithmic FP32 bytes per site of each kernel of the Jacobi flow-on step:
+# each value the kernel must read or write once (inputs + outputs)
+KERNEL_BYTES = {
+    "field": (5 + 5 + 5 + 3) * 4,                       # Q -> H, sigma, tau
+    "force_predict": (5 + 5 + 3 + 4 + 3 + 5) * 4,       # Q, H, tau, rho u -> b, Q*
+    "lb_correct": (15 + 4 + 5 + 3 + 5 + 5 + 15 + 4 + 5) * 4,  # f, rho u, sigma, b, Q*, Q -> f, rho u, Q
+}
+KERNELS = ["field", "force_predict", "lb_correct"]
+STATE_BYTES = (15 + 5) * 2 * 4  # read + write of f and Q once per site-step (FP32)
+ORACLE_SAMPLE = 32  # side of the periodic cube the oracle steps (two BPII unit cells)
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.gpu = gpu_index
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def oracle_sample_mlups(steps: int):
+    """FP64 oracle on a periodic 32^3 cube of the same BPII state (two unit
+    cells per side), timed on one host core.  Returns (MLUPS, seconds)."""
+    from oracle import initial, lbq
+    p = lbq.Params(**PARAMS)
+    shape = (ORACLE_SAMPLE,) * 3
+    Q = initial.init_q9(shape, initial.BPII, p.q0, 0.3, 1e-4, SEED)
+    f = lbq.init_f_equilibrium(Q, p)
+    f, Q = lbq.step(f, Q, p)  # warm-up
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        f, Q = lbq.step(f, Q, p)
+    dt = time.perf_counter() - t0
+    return ORACLE_SAMPLE ** 3 * steps / dt / 1e6, dt
+
+
+def oracle_in_subprocess(steps: int):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = ("import sys, json; sys.path.insert(0, %r); import bench; "
+            "m, dt = bench.oracle_sample_mlups(%d); print(json.dumps([m, dt]))" % (ROOT, steps))
+    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, check=True)
+    m, dt = json.loads(out.stdout.strip().splitlines()[-1])
+    return m, dt
+
+
+def cpu_baseline_entry(steps: int):
+    m, dt = oracle_in_subprocess(steps)
+    return {"value": m, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+            "sample": f"{steps} FP64 oracle steps of a periodic {ORACLE_SAMPLE}^3 cube of the same BPII "
+                      f"(pitch 32) state, {dt:.1f} s on one host core (numpy, threads pinned to 1)"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    per_step = []
+    from oracle import initial, lbq
+    p = lbq.Params(**PARAMS)
+    shape = (ORACLE_SAMPLE,) * 3
+    Q = initial.init_q9(shape, initial.BPII, p.q0, 0.3, 1e-4, SEED)
+    f = lbq.init_f_equilibrium(Q, p)
+    for _ in range(args.warmup):
+        f, Q = lbq.step(f, Q, p)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        f, Q = lbq.step(f, Q, p)
+    dt = time.perf_counter() - t0
+    mlups = ORACLE_SAMPLE ** 3 * args.steps / dt / 1e6
+    line = {
+        "impl": "reference", "metric": "coupled LB+Q MLUPS", "value": mlups, "unit": "MLUPS",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"FP64 oracle on a {ORACLE_SAMPLE}^3 periodic sample of the 256^3 BPII (pitch 32) "
+                               "lattice", "sites_per_step": ORACLE_SAMPLE ** 3},
+        "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                         "sample": f"each step is one oracle step of a periodic {ORACLE_SAMPLE}^3 cube"},
+        "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    from paper_0901_3293_gb300 import build, lcbp
+    if not os.path.exists(lcbp.LIB_PATH):
+        build.build()
+    dev = torch.cuda.current_device()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def allmax(x: float) -> float:
+        if world == 1:
+            return x
+        import torch.distributed as dist
+        t = torch.tensor([x], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    # every rank holds its own independent 256^3 lattice (replicas: no data exchange)
+    n = N_SIDE
+    lat = lcbp.Lattice(n, n, n, dtype="f32")
+    lat.set_ldg(PARAMS["A0"], PARAMS["gamma"], PARAMS["K"], PARAMS["q0"])
+    lat.set_flow(PARAMS["tau_f"], PARAMS["xi"], PARAMS["Gamma"], True, lcbp.JACOBI)
+    lat.init_q(lcbp.BPII, 0.3, noise=1e-4, seed=SEED + rank)
+    lat.init_f_equilibrium(1.0)
+    stream = lat._stream
+    lat.step(args.warmup)
+    lat.synchronize()
+
+    # ---- timed region: K steps (CUDA-graph replay) on the lattice's stream
+    clocks = ClockSampler(dev)
+    time.sleep(0.3)
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    lat.step(args.steps)
+    e1.record(stream)
+    e1.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = allmax(e0.elapsed_time(e1))
+    sites = n ** 3
+    mlups = sites * args.steps * world / (ms * 1e-3) / 1e6
+    F = lat.free_energy()  # FP64 diagnostics also check the state is finite
+
+    # ---- per-kernel device times, kernel by kernel with events (same kernels)
+    kms = lat.profile_steps(max(3, min(args.steps, 10)))
+    peak, peak_kind = measured_peaks()
+    per_kernel = {}
+    for name, t in zip(KERNELS, kms):
+        gbs = KERNEL_BYTES[name] * sites / (t * 1e-3) / 1e9
+        per_kernel[name] = {"ms": t, "algorithmic_bytes_per_site": KERNEL_BYTES[name], "GBps": gbs,
+                            "frac_of_" + peak_kind: gbs / peak}
+    dom = max(per_kernel, key=lambda k: per_kernel[k]["ms"])
+    roof = {"bound": "hbm", "achieved": per_kernel[dom]["GBps"], "peak": peak, "unit": "GB/s",
+            "frac": per_kernel[dom]["GBps"] / peak, "traffic": None, "kernel": dom,
+            "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs, burst copy)",
+            "step_algorithmic_frac": STATE_BYTES * sites * args.steps / (ms * 1e-3) / 1e9 / peak,
+            "note": "step_algorithmic_frac counts only the 160 B/site of reading and writing f and Q once"}
+
+    # ---- end to end through the C ABI with pinned host buffers: upload f and Q,
+    # one step, read back Q and u, every step
+    k_e2e = max(2, min(args.steps, 8))
+    f_h = torch.empty((15, n, n, n), dtype=torch.float32, pin_memory=True)
+    q_h = torch.empty((5, n, n, n), dtype=torch.float32, pin_memory=True)
+    u_h = torch.empty((3, n, n, n), dtype=torch.float32, pin_memory=True)
+    lat.read_f(out=f_h)
+    lat.read_q(out=q_h)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(k_e2e):
+        lat.set_f(f_h)
+        lat.set_q(q_h)
+        lat.step(1)
+        lat.read_q(out=q_h)
+        lat.read_u(out=u_h)
+    barrier()
+    e2e_s = allmax(time.perf_counter() - t0)
+    e2e = {"value": sites * k_e2e * world / e2e_s / 1e6, "unit": "MLUPS",
+           "h2d_bytes_per_step": (15 + 5) * 4 * sites, "d2h_bytes_per_step": (5 + 3) * 4 * sites,
+           "steps": k_e2e, "note": "lcbp_set_f + lcbp_set_q from pinned host memory, lcbp_step(1), "
+                                   "lcbp_read_q + lcbp_read_u to pinned host memory"}
+    launches = 3 * args.steps
+    lat.close()
+
+    # ---- the 64x64x256 thin slab (BPII seed for z < 32 inside an x-helix)
+    slab = lcbp.Lattice(64, 64, 256, dtype="f32")
+    slab.set_ldg_kappa_tau(0.01, 2 * np.pi / 16, 1.0, -0.5)
+    slab.set_flow(2.0, 0.7, 0.3, True, lcbp.JACOBI)
+    slab.init_q(lcbp.SLAB_BPII_IN_CHOL, 0.3, noise=1e-4, seed=SEED, z0=32)
+    slab.init_f_equilibrium(1.0)
+    slab.step(max(3, args.warmup))
+    slab.synchronize()
+    s0 = torch.cuda.Event(enable_timing=True)
+    s1 = torch.cuda.Event(enable_timing=True)
+    s0.record(slab._stream)
+    slab.step(args.steps)
+    s1.record(slab._stream)
+    s1.synchronize()
+    slab_ms = s0.elapsed_time(s1)
+    slab_line = {"sites": 64 * 64 * 256, "ms_per_step": slab_ms / args.steps,
+                 "MLUPS": 64 * 64 * 256 * args.steps / (slab_ms * 1e-3) / 1e6,
+                 "note": "state (168 MB) partly L2-resident; not the headline"}
+    slab.close()
+
+    if rank != 0:
+        return
+    cpu = cpu_baseline_entry(int(os.environ.get("LCBP_ORACLE_STEPS", "40")))
+    line = {
+        "metric": "coupled LB+Q MLUPS", "value": mlups, "unit": "MLUPS", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": "256^3 periodic BPII (pitch 32), coupled D3Q15 LB + Beris-Edwards, FP32 state",
+                   "sites_per_gpu": sites, "A0": PARAMS["A0"], "gamma": PARAMS["gamma"], "K": PARAMS["K"],
+                   "q0": PARAMS["q0"], "tau_f": PARAMS["tau_f"], "l2": "state 4.5 GB >> 129 MB L2, no flush",
+                   "parallelism": f"{world} independent replicas" if world > 1 else "single lattice"},
+        "roofline": roof, "per_kernel": per_kernel, "cpu_baseline": cpu, "e2e": e2e,
+        "gpu_launches": launches, "clocks": clk, "free_energy_after": F,
+        "slab_64x64x256": slab_line,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

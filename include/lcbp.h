@@ -1,0 +1,245 @@
+/*
+ * lcbp.h -- C ABI of liblcbp.so, the GB300 (sm_103a) implementation of the
+ * coupled hybrid lattice-Boltzmann / Beris-Edwards step of
+ * Henrich, Marenduzzo, Stratford, Cates, "Domain growth in cholesteric blue
+ * phases: hybrid lattice Boltzmann simulations" (arXiv:0901.3293).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Every call returns an int status: LCBP_OK (0) or a negative LCBP_E* code.
+ *   lcbp_strerror() names a code; lcbp_last_error() returns a thread-local
+ *   message describing the last failure of the calling thread.  No call
+ *   aborts the process, traps the GPU or leaves a kernel waiting forever.
+ * - Lattice sites are indexed s = (z * ny + y) * nx + x (x fastest), periodic
+ *   in all three directions.  Fields cross the boundary in structure-of-arrays
+ *   layout [component][z][y][x]:
+ *     Q : 5 components [xx, xy, xz, yy, yz]; Q_zz = -Q_xx - Q_yy (Q is
+ *         symmetric and traceless, Sec. 2.1 and the 5-value storage of Sec. 2.2).
+ *     u : 3 components [ux, uy, uz];  rho : 1 component.
+ *     f : 15 D3Q15 populations (Sec. 2.2 Eq. latvects) in the order
+ *         0 rest; 1..6 = +x, -x, +y, -y, +z, -z;
+ *         7..14 = (+1,+1,+1), (+1,+1,-1), (+1,-1,+1), (+1,-1,-1),
+ *                 (-1,+1,+1), (-1,+1,-1), (-1,-1,+1), (-1,-1,-1).
+ * - Buffer arguments (const void *src / void *dst) may be host memory
+ *   (pageable or pinned) or device memory of the current device (unified
+ *   addressing decides); `dtype` (LCBP_F32 / LCBP_F64) is their element type,
+ *   converted to and from the lattice's state type.  Reads are synchronous:
+ *   the data is in `dst` when the call returns.  The caller owns every buffer
+ *   it passes; the library keeps no pointer to it after returning.
+ * - Ownership of device memory: lcbp_create allocates the lattice's state and
+ *   scratch with cudaMalloc and frees it in lcbp_destroy.
+ *   lcbp_create_on_buffers instead works inside a caller-owned device
+ *   workspace (e.g. a PyTorch tensor) on a caller-owned stream; the library
+ *   never frees either, and the caller must keep both alive until
+ *   lcbp_destroy.  Diagnostics use a few kilobytes of library-allocated
+ *   device memory in both cases.
+ * - Work is enqueued on the lattice's stream.  lcbp_step returns once the
+ *   steps are enqueued; reads and diagnostics synchronise the stream.
+ * - Lattice units throughout: dx = dt = 1.
+ */
+#ifndef LCBP_H
+#define LCBP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define LCBP_API __attribute__((visibility("default")))
+#else
+#define LCBP_API
+#endif
+
+#define LCBP_VERSION 1
+
+/* status codes */
+#define LCBP_OK 0
+#define LCBP_EINVAL (-1)      /* bad argument (null handle, size, dtype, kind ...) */
+#define LCBP_ENOMEM (-2)      /* device or host allocation failed / workspace too small */
+#define LCBP_ECUDA (-3)       /* a CUDA runtime call or kernel launch failed */
+#define LCBP_ENONFINITE (-4)  /* a diagnostic found NaN or Inf in the state */
+#define LCBP_ETIMEOUT (-5)    /* a bounded device-side wait gave up */
+#define LCBP_ESTATE (-6)      /* call out of order (e.g. stepping before init) */
+#define LCBP_EIO (-7)         /* checkpoint file could not be read or written */
+
+/* element types of state and of caller buffers */
+#define LCBP_F32 0
+#define LCBP_F64 1
+
+/* initial order-parameter kinds (lcbp_init_q) */
+#define LCBP_BPII 0              /* simple-cubic blue phase II seed (O2 structure) */
+#define LCBP_CHOL_X 1            /* cholesteric helix, axis x: n = (0, cos q0x, sin q0x) */
+#define LCBP_CHOL_Y 2            /* axis y: n = (sin q0y, 0, cos q0y) */
+#define LCBP_CHOL_Z 3            /* axis z: n = (cos q0z, sin q0z, 0) */
+#define LCBP_ISO_NOISE 4         /* isotropic Q = 0 plus noise */
+#define LCBP_SLAB_BPII_IN_CHOL 5 /* BPII for z < region[0], x-helix elsewhere */
+
+/* order of the two sub-updates within one step (Sec. 2.2: "sequentially updated") */
+#define LCBP_JACOBI 0       /* LB and Q both read the step-n fields (default) */
+#define LCBP_GAUSS_SEIDEL 1 /* LB first, then Q advanced with u^{n+1} */
+
+typedef struct lcbp_lattice lcbp_lattice;
+
+/* Name of a status code (static string). */
+LCBP_API const char *lcbp_strerror(int code);
+/* Message of the calling thread's last failure ("" if none). */
+LCBP_API const char *lcbp_last_error(void);
+/* LCBP_VERSION of the loaded library. */
+LCBP_API int lcbp_version(void);
+
+/*
+ * Create a periodic nx * ny * nz lattice (each >= 1) with state type
+ * LCBP_F32 or LCBP_F64 on the current CUDA device, allocating its memory and
+ * a non-blocking stream.  Parameters start at the defaults A0 = 0.01,
+ * gamma = 3.1, K = 0.01, q0 = 2 pi / 16, tau_f = 2, xi = 0.7, Gamma = 0.3,
+ * flow on, Jacobi coupling; Q = 0 and f = 0 until initialised.
+ * Errors: LCBP_EINVAL (sizes < 1, more than 2^31 sites, bad dtype, out == NULL),
+ * LCBP_ENOMEM, LCBP_ECUDA.
+ */
+LCBP_API int lcbp_create(int nx, int ny, int nz, int state_dtype, lcbp_lattice **out);
+
+/* Bytes of device workspace lcbp_create_on_buffers needs for this lattice. */
+LCBP_API size_t lcbp_workspace_bytes(int nx, int ny, int nz, int state_dtype);
+
+/*
+ * As lcbp_create, but the state and scratch live in the caller's device
+ * buffer `workspace` (at least lcbp_workspace_bytes, 256-byte aligned) and
+ * work goes to the caller's stream (a cudaStream_t passed as void*, NULL for
+ * the legacy default stream).  Errors: as lcbp_create; LCBP_ENOMEM if
+ * workspace_bytes is too small, LCBP_EINVAL if workspace is misaligned.
+ */
+LCBP_API int lcbp_create_on_buffers(int nx, int ny, int nz, int state_dtype, void *workspace,
+                           size_t workspace_bytes, void *stream, lcbp_lattice **out);
+
+/* Release everything the library allocated for h (NULL is accepted). */
+LCBP_API int lcbp_destroy(lcbp_lattice *h);
+
+/* nx, ny, nz, state dtype and number of completed steps. */
+LCBP_API int lcbp_get_info(const lcbp_lattice *h, int dims[3], int *state_dtype, long long *step);
+
+/*
+ * Landau-de Gennes parameters of Sec. 2.1 Eq. (free_energy): A0, gamma, the
+ * one-constant elastic constant K (= L1 of the kappa definition) and q0 = 2 pi / pitch.
+ * The gradient energy is the one-constant form
+ *   (K/2)|grad Q|^2 + 2 K q0 Q:(eps grad Q) + 2 K q0^2 |Q|^2,
+ * i.e. the printed chiral square plus (K/2)(d_b Q_ab)^2 up to a divergence.
+ * Errors: LCBP_EINVAL (A0 <= 0, gamma <= 0, K < 0, non-finite values).
+ */
+LCBP_API int lcbp_set_ldg(lcbp_lattice *h, double A0, double gamma, double K, double q0);
+
+/*
+ * Same, from the reduced chirality kappa and temperature tau of Sec. 2.1:
+ * gamma = 27 / (9 + tau), K = kappa^2 A0 gamma / (108 q0^2).
+ * Errors: LCBP_EINVAL (tau <= -9, q0 == 0, kappa < 0).
+ */
+LCBP_API int lcbp_set_ldg_kappa_tau(lcbp_lattice *h, double A0, double q0, double kappa, double tau);
+
+/*
+ * Kinetic parameters: LB relaxation time tau_f (viscosity eta = rho tau_f / 3,
+ * Sec. 2.2 Eq. eq4), flow-aligning parameter xi (Sec. 2.1 Eq. mat_der),
+ * rotational diffusion constant Gamma (Eq. Qevolution), flow_on (0 imposes
+ * u = 0 and skips the LB update, Sec. 2.1), coupling LCBP_JACOBI or
+ * LCBP_GAUSS_SEIDEL.  Errors: LCBP_EINVAL (tau_f <= 0, Gamma < 0, bad coupling).
+ */
+LCBP_API int lcbp_set_flow(lcbp_lattice *h, double tau_f, double xi, double Gamma, int flow_on, int coupling);
+
+/*
+ * Fill Q with an analytic initial state on the device (kinds above):
+ * BPII:  Q_xx = A[cos 2q0z - cos 2q0y], Q_yy = A[cos 2q0x - cos 2q0z],
+ *        Q_xy = A sin 2q0z, Q_xz = A sin 2q0y, Q_yz = A sin 2q0x (A = amplitude);
+ * CHOL_*: Q = S (n n - I/3), S = amplitude;  ISO_NOISE: Q = 0;
+ * SLAB_BPII_IN_CHOL: BPII (A = amplitude) for z < region[0], elsewhere the
+ *   x-helix with S = 1/4 + 3/4 sqrt(1 - 8 / (3 gamma)) (bulk equilibrium order).
+ * Then add U[-noise, noise) to each of the five components, the k-th output
+ * (k = 5 * site + component) of SplitMix64 seeded with `seed`, mapped to
+ * (z >> 11) * 2^-53.  region may be NULL except for SLAB_BPII_IN_CHOL.
+ * Errors: LCBP_EINVAL (unknown kind, missing region, noise < 0).
+ */
+LCBP_API int lcbp_init_q(lcbp_lattice *h, int kind, double amplitude, double noise, uint64_t seed,
+                const int *region);
+
+/* Upload Q: q5 holds 5 * N values in the layout above.  Errors: LCBP_EINVAL. */
+LCBP_API int lcbp_set_q(lcbp_lattice *h, const void *q5, int dtype);
+
+/*
+ * Set f = f^eq(rho0, u, sigma_LC(Q)) at every site (Sec. 2.2 Eq. feq, coeff,
+ * without the forcing term), with u from u3 (3 * N values) or u = 0 if u3 is
+ * NULL, and sigma_LC from the current Q.  Errors: LCBP_EINVAL (rho0 <= 0).
+ */
+LCBP_API int lcbp_init_f_equilibrium(lcbp_lattice *h, double rho0, const void *u3, int dtype);
+
+/* Upload the 15 * N populations.  Errors: LCBP_EINVAL. */
+LCBP_API int lcbp_set_f(lcbp_lattice *h, const void *f15, int dtype);
+
+/*
+ * Optional external body force (3 * N values) added to the LC body force b of
+ * Sec. 2.2 Eq. (eq7a) in the LB forcing; NULL removes it.
+ */
+LCBP_API int lcbp_set_body_force(lcbp_lattice *h, const void *b3, int dtype);
+
+/*
+ * Advance nsteps >= 0 coupled steps (Sec. 2.2): molecular field H, LC stress
+ * sigma_LC and tau, body force b = D0_b tau_ab - H_gn D0_a Q_gn (Eq. spurious),
+ * predictor-corrector D3Q15 LB with BGK + forcing (Eq. eq2, eq4), and the Heun
+ * predictor-corrector for Q with central differences (Eq. Qevolution,
+ * mat_der).  Returns once the work is enqueued (CUDA-graph replay).
+ * Errors: LCBP_ESTATE (f never initialised while flow is on), LCBP_ECUDA.
+ */
+LCBP_API int lcbp_step(lcbp_lattice *h, int nsteps);
+
+/*
+ * Advance nsteps >= 1 steps exactly as lcbp_step does, but launched one kernel
+ * at a time with a CUDA event between kernels, and return in kernel_ms the
+ * mean device time of each kernel of one step (milliseconds).  *nkernels is
+ * set to the number of kernels per step: 3 with flow on and Jacobi coupling
+ * (field: H/sigma/tau; force_predict: b and the Heun predictor; lb_correct:
+ * LB predictor-corrector and the Heun corrector), 5 with Gauss-Seidel
+ * coupling (field, force, lb, predict, correct), 3 with flow off (field,
+ * predict, correct).  Errors: LCBP_EINVAL if capacity < *nkernels.
+ */
+LCBP_API int lcbp_profile_steps(lcbp_lattice *h, int nsteps, double *kernel_ms, int capacity, int *nkernels);
+
+/* Synchronise the lattice's stream.  Errors: LCBP_ECUDA. */
+LCBP_API int lcbp_synchronize(lcbp_lattice *h);
+
+/* Copy out Q (5 * N), u (3 * N), rho (N) or f (15 * N) values.  Errors: LCBP_EINVAL. */
+LCBP_API int lcbp_read_q(lcbp_lattice *h, void *dst, int dtype);
+LCBP_API int lcbp_read_u(lcbp_lattice *h, void *dst, int dtype);
+LCBP_API int lcbp_read_rho(lcbp_lattice *h, void *dst, int dtype);
+LCBP_API int lcbp_read_f(lcbp_lattice *h, void *dst, int dtype);
+
+/*
+ * Total lattice free energy F_h = sum_x f_h(x), accumulated in FP64 on the
+ * device, with the lattice density
+ *   f_h = bulk(Q) + (K/2) sum_g |D+_g Q|^2 + 2 K q0 Q:(eps D0 Q) + 2 K q0^2 |Q|^2
+ * whose exact gradient is -H (Sec. 2.1 Eq. free_energy).
+ * Errors: LCBP_ENONFINITE if Q holds NaN/Inf.
+ */
+LCBP_API int lcbp_free_energy(lcbp_lattice *h, double *F);
+
+/* Sum of rho and of rho u over the lattice (FP64 on the device).  LCBP_ENONFINITE on NaN/Inf. */
+LCBP_API int lcbp_totals(lcbp_lattice *h, double *mass, double momentum[3]);
+
+/*
+ * Fraction of sites whose scalar order q (largest eigenvalue of Q, Sec. 2.1)
+ * is below `threshold` (the paper uses 0.19 to mark disclinations).
+ */
+LCBP_API int lcbp_defect_fraction(lcbp_lattice *h, double threshold, double *fraction);
+
+/*
+ * Checkpoint: a versioned binary file with a header (magic, version, dims,
+ * state dtype, parameters, step count) followed by f and Q in the state type.
+ * lcbp_load requires a lattice of the same dims and dtype.  Errors: LCBP_EIO,
+ * LCBP_EINVAL (mismatch).
+ */
+LCBP_API int lcbp_save(lcbp_lattice *h, const char *path);
+LCBP_API int lcbp_load(lcbp_lattice *h, const char *path);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LCBP_H */

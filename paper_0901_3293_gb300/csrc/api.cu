@@ -1,0 +1,801 @@
+// C ABI of liblcbp: lattice handle, memory, parameters, stepping (CUDA graph
+// replay), transfers, diagnostics and checkpoints.  See include/lcbp.h.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/lcbp.h"
+#include "common.cuh"
+#include "kernels.h"
+#include "runtime.h"
+
+using namespace lcbp;
+
+namespace lcbp {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  return fail(LCBP_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+TileShape default_tile(int nx, int ny, int nz) {
+  TileShape t;
+  t.tx = std::min(nx, 32);
+  t.ty = std::min(ny, std::max(1, 128 / t.tx));
+  t.tz = std::min(nz, std::max(1, 128 / (t.tx * t.ty)));
+  return t;
+}
+
+long long tile_count(int nx, int ny, int nz, TileShape t) {
+  return (long long)((nx + t.tx - 1) / t.tx) * ((ny + t.ty - 1) / t.ty) * ((nz + t.tz - 1) / t.tz);
+}
+
+void append_tiles(std::vector<Tile>& out, int rep, int nx, int ny, int nz, TileShape t) {
+  for (int z = 0; z < nz; z += t.tz)
+    for (int y = 0; y < ny; y += t.ty)
+      for (int x = 0; x < nx; x += t.tx) out.push_back(Tile{rep, x, y, z});
+}
+
+bool valid_dtype(int d) { return d == LCBP_F32 || d == LCBP_F64; }
+size_t dtype_size(int d) { return d == LCBP_F64 ? 8 : 4; }
+
+// Model coefficients in the state type, from double parameters
+template <typename real>
+Model<real> make_model(const HostParams& p) {
+  Model<real> m;
+  m.a_bulk = (real)(p.A0 * (1.0 - p.gamma / 3.0));
+  m.b_bulk = (real)(p.A0 * p.gamma);
+  m.K = (real)p.K;
+  m.kq0x2 = (real)(2.0 * p.K * p.q0);
+  m.kq0sq4 = (real)(4.0 * p.K * p.q0 * p.q0);
+  m.Gamma = (real)p.Gamma;
+  m.xi = (real)p.xi;
+  m.inv_tau = (real)(1.0 / p.tau_f);
+  return m;
+}
+
+template <typename real>
+void fill_replica(void* dst, int nx, int ny, int nz, long long base, const HostParams& p) {
+  Replica<real> r{};
+  r.nx = nx;
+  r.ny = ny;
+  r.nz = nz;
+  r.n = (long long)nx * ny * nz;
+  r.base = base;
+  r.m = make_model<real>(p);
+  std::memcpy(dst, &r, sizeof(r));
+}
+template void fill_replica<float>(void*, int, int, int, long long, const HostParams&);
+template void fill_replica<double>(void*, int, int, int, long long, const HostParams&);
+
+size_t replica_bytes(int dtype) { return dtype == LCBP_F64 ? sizeof(Replica<double>) : sizeof(Replica<float>); }
+
+double s_eq(double gamma) {
+  const double d = 1.0 - 8.0 / (3.0 * gamma);
+  return d > 0 ? 0.25 + 0.75 * std::sqrt(d) : 0.0;
+}
+
+int check_params(const HostParams& p) {
+  const double v[] = {p.A0, p.gamma, p.K, p.q0, p.tau_f, p.xi, p.Gamma};
+  for (double x : v)
+    if (!std::isfinite(x)) return fail(LCBP_EINVAL, "non-finite parameter");
+  if (p.A0 <= 0 || p.gamma <= 0 || p.K < 0) return fail(LCBP_EINVAL, "need A0 > 0, gamma > 0, K >= 0");
+  if (p.tau_f <= 0 || p.Gamma < 0) return fail(LCBP_EINVAL, "need tau_f > 0, Gamma >= 0");
+  if (p.coupling != LCBP_JACOBI && p.coupling != LCBP_GAUSS_SEIDEL) return fail(LCBP_EINVAL, "bad coupling");
+  return LCBP_OK;
+}
+
+// Copy `count` values between a caller buffer (host or device, dtype `ud`)
+// and a device state array (dtype `sd`), converting through `staging`.
+int transfer(void* state, int sd, void* user, int ud, long long count, bool upload, void* staging,
+             long long staging_elems, cudaStream_t st) {
+  cudaError_t e;
+  if (ud == sd) {
+    const size_t bytes = (size_t)count * dtype_size(sd);
+    e = upload ? cudaMemcpyAsync(state, user, bytes, cudaMemcpyDefault, st)
+               : cudaMemcpyAsync(user, state, bytes, cudaMemcpyDefault, st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync");
+    e = cudaStreamSynchronize(st);
+    return e == cudaSuccess ? LCBP_OK : cuda_fail(e, "cudaStreamSynchronize");
+  }
+  const size_t ues = dtype_size(ud), ses = dtype_size(sd);
+  for (long long off = 0; off < count; off += staging_elems) {
+    const long long m = std::min(staging_elems, count - off);
+    if (upload) {
+      e = cudaMemcpyAsync(staging, static_cast<char*>(user) + off * ues, m * ues, cudaMemcpyDefault, st);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync");
+      e = launch_convert(staging, ud, static_cast<char*>(state) + off * ses, sd, m, st);
+    } else {
+      e = launch_convert(static_cast<char*>(state) + off * ses, sd, staging, ud, m, st);
+      if (e != cudaSuccess) return cuda_fail(e, "convert");
+      e = cudaMemcpyAsync(static_cast<char*>(user) + off * ues, staging, m * ues, cudaMemcpyDefault, st);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "transfer");
+    e = cudaStreamSynchronize(st);  // staging is reused by the next chunk
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+  }
+  return LCBP_OK;
+}
+
+}  // namespace lcbp
+
+// ---------------------------------------------------------------------------
+// lattice handle
+// ---------------------------------------------------------------------------
+struct lcbp_lattice {
+  int nx, ny, nz;
+  long long n;
+  int dtype;
+  size_t es;
+  int device;
+  HostParams p;
+  cudaStream_t stream;
+  bool own_stream;
+  char* ws;
+  size_t ws_bytes;
+  bool own_ws;
+  // state and scratch (device)
+  void *f[2], *rhou[2], *q, *qs, *h, *sig, *tau, *b, *bext, *staging;
+  long long staging_elems;
+  void* d_rep;
+  Tile* d_tiles;
+  int ntiles;
+  TileShape ts;
+  double *d_q0, *d_shelix;
+  uint64_t* d_seed;
+  double *d_partials, *d_out;
+  double* h_out;  // pinned
+  int cur;
+  bool f_ready, has_bext;
+  cudaGraphExec_t graph;
+  bool graph_ok;
+  long long step;
+};
+
+namespace {
+
+struct Layout {
+  size_t off[16];
+  size_t total;
+};
+
+constexpr long long kStagingMax = 1ll << 22;  // elements of the conversion buffer
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// offsets of: f0 f1 rhou0 rhou1 q qs h sig tau b bext staging rep tiles q0/shelix/seed partials
+Layout layout(int nx, int ny, int nz, int dtype) {
+  const long long n = (long long)nx * ny * nz;
+  const size_t es = dtype_size(dtype);
+  const TileShape ts = default_tile(nx, ny, nz);
+  const long long nt = tile_count(nx, ny, nz, ts);
+  const long long comps[11] = {15, 15, 4, 4, 5, 5, 5, 5, 3, 3, 3};
+  Layout L{};
+  size_t o = 0;
+  for (int i = 0; i < 11; ++i) {
+    L.off[i] = o;
+    o = align256(o + (size_t)(comps[i] * n) * es);
+  }
+  L.off[11] = o;  // staging (doubles)
+  o = align256(o + (size_t)std::min(kStagingMax, 15 * n) * 8);
+  L.off[12] = o;  // replica table
+  o = align256(o + replica_bytes(dtype));
+  L.off[13] = o;  // tiles
+  o = align256(o + (size_t)nt * sizeof(Tile));
+  L.off[14] = o;  // q0, s_helix, seed
+  o = align256(o + 3 * 8);
+  L.off[15] = o;  // partials + out
+  o = align256(o + (kDiagPartials + 8) * 8);
+  L.total = o;
+  return L;
+}
+
+int check_dims(int nx, int ny, int nz) {
+  if (nx < 1 || ny < 1 || nz < 1) return fail(LCBP_EINVAL, "lattice sizes must be >= 1");
+  if ((long long)nx * ny * nz > (1ll << 31)) return fail(LCBP_EINVAL, "more than 2^31 sites");
+  return LCBP_OK;
+}
+
+int upload_replica(lcbp_lattice* h) {
+  std::vector<char> buf(replica_bytes(h->dtype));
+  if (h->dtype == LCBP_F64) fill_replica<double>(buf.data(), h->nx, h->ny, h->nz, 0, h->p);
+  else fill_replica<float>(buf.data(), h->nx, h->ny, h->nz, 0, h->p);
+  const double aux[2] = {h->p.q0, s_eq(h->p.gamma)};
+  cudaError_t e = cudaMemcpyAsync(h->d_rep, buf.data(), buf.size(), cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h->d_q0, aux, sizeof(aux), cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  return e == cudaSuccess ? LCBP_OK : cuda_fail(e, "upload parameters");
+}
+
+int finish_create(lcbp_lattice* h) {
+  const Layout L = layout(h->nx, h->ny, h->nz, h->dtype);
+  char* w = h->ws;
+  h->f[0] = w + L.off[0];
+  h->f[1] = w + L.off[1];
+  h->rhou[0] = w + L.off[2];
+  h->rhou[1] = w + L.off[3];
+  h->q = w + L.off[4];
+  h->qs = w + L.off[5];
+  h->h = w + L.off[6];
+  h->sig = w + L.off[7];
+  h->tau = w + L.off[8];
+  h->b = w + L.off[9];
+  h->bext = w + L.off[10];
+  h->staging = w + L.off[11];
+  h->staging_elems = std::min(kStagingMax, 15 * h->n);
+  h->d_rep = w + L.off[12];
+  h->d_tiles = reinterpret_cast<Tile*>(w + L.off[13]);
+  h->d_q0 = reinterpret_cast<double*>(w + L.off[14]);
+  h->d_shelix = h->d_q0 + 1;
+  h->d_seed = reinterpret_cast<uint64_t*>(h->d_q0 + 2);
+  h->d_partials = reinterpret_cast<double*>(w + L.off[15]);
+  h->d_out = h->d_partials + kDiagPartials;
+  h->ts = default_tile(h->nx, h->ny, h->nz);
+  std::vector<Tile> tiles;
+  append_tiles(tiles, 0, h->nx, h->ny, h->nz, h->ts);
+  h->ntiles = (int)tiles.size();
+  cudaError_t e = cudaMemsetAsync(h->ws, 0, L.off[11], h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->d_tiles, tiles.data(), tiles.size() * sizeof(Tile), cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaMallocHost(&h->h_out, 8 * sizeof(double));
+  if (e != cudaSuccess) return cuda_fail(e, "lattice set-up");
+  return upload_replica(h);
+}
+
+HostParams default_params() {
+  HostParams p;
+  p.A0 = 0.01;
+  p.gamma = 3.1;
+  p.K = 0.01;
+  p.q0 = 2.0 * M_PI / 16.0;
+  p.tau_f = 2.0;
+  p.xi = 0.7;
+  p.Gamma = 0.3;
+  p.flow_on = 1;
+  p.coupling = LCBP_JACOBI;
+  return p;
+}
+
+lcbp_lattice* new_handle(int nx, int ny, int nz, int dtype) {
+  auto* h = new lcbp_lattice();
+  h->nx = nx;
+  h->ny = ny;
+  h->nz = nz;
+  h->n = (long long)nx * ny * nz;
+  h->dtype = dtype;
+  h->es = dtype_size(dtype);
+  h->p = default_params();
+  cudaGetDevice(&h->device);
+  return h;
+}
+
+StepArgs step_args(lcbp_lattice* h) {
+  StepArgs a{};
+  a.reps = h->d_rep;
+  a.tiles = h->d_tiles;
+  a.ntiles = h->ntiles;
+  a.ts = h->ts;
+  a.flow_on = h->p.flow_on;
+  a.coupling = h->p.coupling;
+  a.q = h->q;
+  a.qs = h->qs;
+  a.h = h->h;
+  a.sigma = h->sig;
+  a.tau = h->tau;
+  a.b = h->b;
+  a.bext = h->has_bext ? h->bext : nullptr;
+  a.f = h->f[h->cur];
+  a.fnew = h->f[h->cur ^ 1];
+  a.rhou = h->rhou[h->cur];
+  a.rhou_new = h->rhou[h->cur ^ 1];
+  a.events = nullptr;
+  return a;
+}
+
+cudaError_t eager_step(lcbp_lattice* h) {
+  const StepArgs a = step_args(h);
+  const cudaError_t e = h->dtype == LCBP_F64 ? launch_step<double>(a, h->stream) : launch_step<float>(a, h->stream);
+  if (h->p.flow_on) h->cur ^= 1;
+  return e;
+}
+
+void drop_graph(lcbp_lattice* h) {
+  if (h->graph_ok) cudaGraphExecDestroy(h->graph);
+  h->graph_ok = false;
+}
+
+// capture two steps starting from cur == 0 (the ping-pong buffers return to
+// their roles after two steps)
+int build_graph(lcbp_lattice* h) {
+  if (h->stream == nullptr) return LCBP_OK;  // legacy stream: no capture, eager launches
+  cudaGraph_t g;
+  cudaError_t e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
+  const int saved = h->cur;
+  h->cur = 0;
+  cudaError_t e1 = eager_step(h);
+  cudaError_t e2 = eager_step(h);
+  h->cur = saved;
+  e = cudaStreamEndCapture(h->stream, &g);
+  if (e1 != cudaSuccess) e = e1;
+  if (e2 != cudaSuccess) e = e2;
+  if (e != cudaSuccess) return cuda_fail(e, "graph capture");
+  e = cudaGraphInstantiate(&h->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+  h->graph_ok = true;
+  return LCBP_OK;
+}
+
+int diag(lcbp_lattice* h, double threshold, int with_f) {
+  DiagGeom g{h->nx, h->ny, h->nz, h->n, 0, h->p.A0, h->p.gamma, h->p.K, h->p.q0};
+  cudaError_t e = h->dtype == LCBP_F64
+                      ? launch_diag_one<double>(g, h->q, h->f[h->cur], with_f, threshold, h->d_partials, h->d_out,
+                                                h->stream)
+                      : launch_diag_one<float>(g, h->q, h->f[h->cur], with_f, threshold, h->d_partials, h->d_out,
+                                               h->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h->h_out, h->d_out, 8 * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "diagnostics");
+  if (h->h_out[6] != 0.0) return fail(LCBP_ENONFINITE, "%.0f sites hold NaN or Inf", h->h_out[6]);
+  return LCBP_OK;
+}
+
+#define CHECK_H(h)                                                     \
+  do {                                                                 \
+    if (!(h)) return fail(LCBP_EINVAL, "null lattice handle");         \
+    cudaSetDevice((h)->device);                                        \
+  } while (0)
+
+int refresh_moments(lcbp_lattice* h) {
+  cudaError_t e = h->dtype == LCBP_F64
+                      ? launch_moments<double>(h->d_rep, h->d_tiles, h->ntiles, h->ts, h->f[h->cur], h->rhou[h->cur],
+                                               h->stream)
+                      : launch_moments<float>(h->d_rep, h->d_tiles, h->ntiles, h->ts, h->f[h->cur], h->rhou[h->cur],
+                                              h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  return e == cudaSuccess ? LCBP_OK : cuda_fail(e, "moments");
+}
+
+struct CkptHeader {
+  char magic[8];
+  int32_t version, nx, ny, nz, dtype, flow_on, coupling, pad;
+  double A0, gamma, K, q0, tau_f, xi, Gamma;
+  int64_t step;
+};
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+extern "C" {
+
+const char* lcbp_strerror(int code) {
+  switch (code) {
+    case LCBP_OK: return "LCBP_OK";
+    case LCBP_EINVAL: return "LCBP_EINVAL: invalid argument";
+    case LCBP_ENOMEM: return "LCBP_ENOMEM: out of memory";
+    case LCBP_ECUDA: return "LCBP_ECUDA: CUDA error";
+    case LCBP_ENONFINITE: return "LCBP_ENONFINITE: non-finite state";
+    case LCBP_ETIMEOUT: return "LCBP_ETIMEOUT: device wait timed out";
+    case LCBP_ESTATE: return "LCBP_ESTATE: call out of order";
+    case LCBP_EIO: return "LCBP_EIO: checkpoint I/O failed";
+    default: return "unknown lcbp status";
+  }
+}
+
+const char* lcbp_last_error(void) { return g_last_error.c_str(); }
+
+int lcbp_version(void) { return LCBP_VERSION; }
+
+size_t lcbp_workspace_bytes(int nx, int ny, int nz, int dtype) {
+  if (check_dims(nx, ny, nz) != LCBP_OK || !valid_dtype(dtype)) return 0;
+  return layout(nx, ny, nz, dtype).total;
+}
+
+int lcbp_create(int nx, int ny, int nz, int dtype, lcbp_lattice** out) {
+  if (!out) return fail(LCBP_EINVAL, "out is NULL");
+  *out = nullptr;
+  int rc = check_dims(nx, ny, nz);
+  if (rc) return rc;
+  if (!valid_dtype(dtype)) return fail(LCBP_EINVAL, "bad state dtype %d", dtype);
+  lcbp_lattice* h = new_handle(nx, ny, nz, dtype);
+  const Layout L = layout(nx, ny, nz, dtype);
+  cudaError_t e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    delete h;
+    return cuda_fail(e, "cudaStreamCreate");
+  }
+  h->own_stream = true;
+  e = cudaMalloc(&h->ws, L.total);
+  if (e != cudaSuccess) {
+    cudaStreamDestroy(h->stream);
+    delete h;
+    cudaGetLastError();
+    return fail(LCBP_ENOMEM, "cudaMalloc of %zu bytes failed", L.total);
+  }
+  h->own_ws = true;
+  h->ws_bytes = L.total;
+  rc = finish_create(h);
+  if (rc) {
+    lcbp_destroy(h);
+    return rc;
+  }
+  *out = h;
+  return LCBP_OK;
+}
+
+int lcbp_create_on_buffers(int nx, int ny, int nz, int dtype, void* workspace, size_t workspace_bytes, void* stream,
+                           lcbp_lattice** out) {
+  if (!out) return fail(LCBP_EINVAL, "out is NULL");
+  *out = nullptr;
+  int rc = check_dims(nx, ny, nz);
+  if (rc) return rc;
+  if (!valid_dtype(dtype)) return fail(LCBP_EINVAL, "bad state dtype %d", dtype);
+  if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255))
+    return fail(LCBP_EINVAL, "workspace must be a 256-byte aligned device pointer");
+  const Layout L = layout(nx, ny, nz, dtype);
+  if (workspace_bytes < L.total)
+    return fail(LCBP_ENOMEM, "workspace of %zu bytes, need %zu", workspace_bytes, L.total);
+  lcbp_lattice* h = new_handle(nx, ny, nz, dtype);
+  h->stream = static_cast<cudaStream_t>(stream);
+  h->own_stream = false;
+  h->ws = static_cast<char*>(workspace);
+  h->ws_bytes = workspace_bytes;
+  h->own_ws = false;
+  rc = finish_create(h);
+  if (rc) {
+    lcbp_destroy(h);
+    return rc;
+  }
+  *out = h;
+  return LCBP_OK;
+}
+
+int lcbp_destroy(lcbp_lattice* h) {
+  if (!h) return LCBP_OK;
+  cudaSetDevice(h->device);
+  if (h->stream || h->own_stream) cudaStreamSynchronize(h->stream);
+  drop_graph(h);
+  if (h->h_out) cudaFreeHost(h->h_out);
+  if (h->own_ws && h->ws) cudaFree(h->ws);
+  if (h->own_stream) cudaStreamDestroy(h->stream);
+  delete h;
+  return LCBP_OK;
+}
+
+int lcbp_get_info(const lcbp_lattice* h, int dims[3], int* dtype, long long* step) {
+  if (!h) return fail(LCBP_EINVAL, "null lattice handle");
+  if (dims) {
+    dims[0] = h->nx;
+    dims[1] = h->ny;
+    dims[2] = h->nz;
+  }
+  if (dtype) *dtype = h->dtype;
+  if (step) *step = h->step;
+  return LCBP_OK;
+}
+
+int lcbp_set_ldg(lcbp_lattice* h, double A0, double gamma, double K, double q0) {
+  CHECK_H(h);
+  HostParams p = h->p;
+  p.A0 = A0;
+  p.gamma = gamma;
+  p.K = K;
+  p.q0 = q0;
+  int rc = check_params(p);
+  if (rc) return rc;
+  h->p = p;
+  return upload_replica(h);
+}
+
+int lcbp_set_ldg_kappa_tau(lcbp_lattice* h, double A0, double q0, double kappa, double tau) {
+  CHECK_H(h);
+  if (!(tau > -9.0) || q0 == 0.0 || !(kappa >= 0.0)) return fail(LCBP_EINVAL, "need tau > -9, q0 != 0, kappa >= 0");
+  const double gamma = 27.0 / (9.0 + tau);
+  const double K = kappa * kappa * A0 * gamma / (108.0 * q0 * q0);
+  return lcbp_set_ldg(h, A0, gamma, K, q0);
+}
+
+int lcbp_set_flow(lcbp_lattice* h, double tau_f, double xi, double Gamma, int flow_on, int coupling) {
+  CHECK_H(h);
+  HostParams p = h->p;
+  p.tau_f = tau_f;
+  p.xi = xi;
+  p.Gamma = Gamma;
+  p.flow_on = flow_on ? 1 : 0;
+  p.coupling = coupling;
+  int rc = check_params(p);
+  if (rc) return rc;
+  if (p.flow_on != h->p.flow_on || p.coupling != h->p.coupling) drop_graph(h);
+  h->p = p;
+  return upload_replica(h);
+}
+
+int lcbp_init_q(lcbp_lattice* h, int kind, double amplitude, double noise, uint64_t seed, const int* region) {
+  CHECK_H(h);
+  if (kind < LCBP_BPII || kind > LCBP_SLAB_BPII_IN_CHOL) return fail(LCBP_EINVAL, "unknown initial kind %d", kind);
+  if (!(noise >= 0.0) || !std::isfinite(amplitude)) return fail(LCBP_EINVAL, "need noise >= 0, finite amplitude");
+  if (kind == LCBP_SLAB_BPII_IN_CHOL && !region) return fail(LCBP_EINVAL, "SLAB_BPII_IN_CHOL needs region[0] = z0");
+  InitQArgs a{kind, amplitude, noise, seed, region ? region[0] : 0};
+  cudaError_t e = cudaMemcpyAsync(h->d_seed, &seed, sizeof(seed), cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess)
+    e = h->dtype == LCBP_F64 ? launch_init_q<double>(h->d_rep, h->d_tiles, h->ntiles, h->ts, h->d_q0, h->d_shelix,
+                                                     h->d_seed, a, h->q, h->stream)
+                             : launch_init_q<float>(h->d_rep, h->d_tiles, h->ntiles, h->ts, h->d_q0, h->d_shelix,
+                                                    h->d_seed, a, h->q, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  return e == cudaSuccess ? LCBP_OK : cuda_fail(e, "init_q");
+}
+
+int lcbp_set_q(lcbp_lattice* h, const void* q5, int dtype) {
+  CHECK_H(h);
+  if (!q5 || !valid_dtype(dtype)) return fail(LCBP_EINVAL, "bad buffer or dtype");
+  return transfer(h->q, h->dtype, const_cast<void*>(q5), dtype, 5 * h->n, true, h->staging, h->staging_elems,
+                  h->stream);
+}
+
+int lcbp_init_f_equilibrium(lcbp_lattice* h, double rho0, const void* u3, int dtype) {
+  CHECK_H(h);
+  if (!(rho0 > 0.0) || !valid_dtype(dtype)) return fail(LCBP_EINVAL, "need rho0 > 0 and a valid dtype");
+  int rc;
+  if (u3) {
+    // the body-force scratch holds the uploaded velocity
+    rc = transfer(h->b, h->dtype, const_cast<void*>(u3), dtype, 3 * h->n, true, h->staging, h->staging_elems,
+                  h->stream);
+    if (rc) return rc;
+  }
+  StepArgs a = step_args(h);
+  cudaError_t e = h->dtype == LCBP_F64 ? launch_field<double>(a, h->stream) : launch_field<float>(a, h->stream);
+  if (e == cudaSuccess)
+    e = h->dtype == LCBP_F64 ? launch_init_feq<double>(h->d_rep, h->d_tiles, h->ntiles, h->ts, rho0,
+                                                       u3 ? h->b : nullptr, h->sig, h->f[h->cur], h->stream)
+                             : launch_init_feq<float>(h->d_rep, h->d_tiles, h->ntiles, h->ts, rho0,
+                                                      u3 ? h->b : nullptr, h->sig, h->f[h->cur], h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "init_f_equilibrium");
+  rc = refresh_moments(h);
+  if (rc) return rc;
+  h->f_ready = true;
+  return LCBP_OK;
+}
+
+int lcbp_set_f(lcbp_lattice* h, const void* f15, int dtype) {
+  CHECK_H(h);
+  if (!f15 || !valid_dtype(dtype)) return fail(LCBP_EINVAL, "bad buffer or dtype");
+  int rc = transfer(h->f[h->cur], h->dtype, const_cast<void*>(f15), dtype, 15 * h->n, true, h->staging,
+                    h->staging_elems, h->stream);
+  if (rc) return rc;
+  rc = refresh_moments(h);
+  if (rc) return rc;
+  h->f_ready = true;
+  return LCBP_OK;
+}
+
+int lcbp_set_body_force(lcbp_lattice* h, const void* b3, int dtype) {
+  CHECK_H(h);
+  if (!b3) {
+    if (h->has_bext) drop_graph(h);
+    h->has_bext = false;
+    return LCBP_OK;
+  }
+  if (!valid_dtype(dtype)) return fail(LCBP_EINVAL, "bad dtype");
+  int rc = transfer(h->bext, h->dtype, const_cast<void*>(b3), dtype, 3 * h->n, true, h->staging, h->staging_elems,
+                    h->stream);
+  if (rc) return rc;
+  if (!h->has_bext) drop_graph(h);
+  h->has_bext = true;
+  return LCBP_OK;
+}
+
+int lcbp_step(lcbp_lattice* h, int nsteps) {
+  CHECK_H(h);
+  if (nsteps < 0) return fail(LCBP_EINVAL, "nsteps < 0");
+  if (h->p.flow_on && !h->f_ready) return fail(LCBP_ESTATE, "initialise f before stepping with flow on");
+  if (nsteps == 0) return LCBP_OK;
+  cudaError_t e = cudaSuccess;
+  int left = nsteps;
+  if (h->cur == 1) {
+    e = eager_step(h);
+    --left;
+  }
+  if (left >= 2 && !h->graph_ok && e == cudaSuccess) {
+    int rc = build_graph(h);
+    if (rc) return rc;
+  }
+  while (left >= 2 && e == cudaSuccess) {
+    if (h->graph_ok) {
+      e = cudaGraphLaunch(h->graph, h->stream);
+    } else {
+      e = eager_step(h);
+      if (e == cudaSuccess) e = eager_step(h);
+    }
+    left -= 2;
+  }
+  if (left == 1 && e == cudaSuccess) e = eager_step(h);
+  if (e != cudaSuccess) return cuda_fail(e, "step launch");
+  h->step += nsteps;
+  return LCBP_OK;
+}
+
+int lcbp_profile_steps(lcbp_lattice* h, int nsteps, double* kernel_ms, int capacity, int* nkernels) {
+  CHECK_H(h);
+  if (nsteps < 1 || !kernel_ms || !nkernels) return fail(LCBP_EINVAL, "need nsteps >= 1 and output arrays");
+  if (h->p.flow_on && !h->f_ready) return fail(LCBP_ESTATE, "initialise f before stepping with flow on");
+  const int nk = kernels_per_step(h->p.flow_on, h->p.coupling);
+  *nkernels = nk;
+  if (capacity < nk) return fail(LCBP_EINVAL, "kernel_ms holds %d values, need %d", capacity, nk);
+  std::vector<cudaEvent_t> ev((size_t)nsteps * (nk + 1));
+  cudaError_t e = cudaSuccess;
+  for (auto& x : ev)
+    if (e == cudaSuccess) e = cudaEventCreate(&x);
+  for (int s = 0; s < nsteps && e == cudaSuccess; ++s) {
+    StepArgs a = step_args(h);
+    a.events = ev.data() + (size_t)s * (nk + 1);
+    e = h->dtype == LCBP_F64 ? launch_step<double>(a, h->stream) : launch_step<float>(a, h->stream);
+    if (h->p.flow_on) h->cur ^= 1;
+    h->step += 1;
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  for (int k = 0; k < nk; ++k) kernel_ms[k] = 0.0;
+  for (int s = 0; s < nsteps && e == cudaSuccess; ++s)
+    for (int k = 0; k < nk && e == cudaSuccess; ++k) {
+      float ms = 0.f;
+      e = cudaEventElapsedTime(&ms, ev[(size_t)s * (nk + 1) + k], ev[(size_t)s * (nk + 1) + k + 1]);
+      kernel_ms[k] += ms / nsteps;
+    }
+  for (auto& x : ev)
+    if (x) cudaEventDestroy(x);
+  return e == cudaSuccess ? LCBP_OK : cuda_fail(e, "profile_steps");
+}
+
+int lcbp_synchronize(lcbp_lattice* h) {
+  CHECK_H(h);
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  return e == cudaSuccess ? LCBP_OK : cuda_fail(e, "cudaStreamSynchronize");
+}
+
+int lcbp_read_q(lcbp_lattice* h, void* dst, int dtype) {
+  CHECK_H(h);
+  if (!dst || !valid_dtype(dtype)) return fail(LCBP_EINVAL, "bad buffer or dtype");
+  return transfer(h->q, h->dtype, dst, dtype, 5 * h->n, false, h->staging, h->staging_elems, h->stream);
+}
+
+int lcbp_read_u(lcbp_lattice* h, void* dst, int dtype) {
+  CHECK_H(h);
+  if (!dst || !valid_dtype(dtype)) return fail(LCBP_EINVAL, "bad buffer or dtype");
+  return transfer(static_cast<char*>(h->rhou[h->cur]) + h->n * h->es, h->dtype, dst, dtype, 3 * h->n, false,
+                  h->staging, h->staging_elems, h->stream);
+}
+
+int lcbp_read_rho(lcbp_lattice* h, void* dst, int dtype) {
+  CHECK_H(h);
+  if (!dst || !valid_dtype(dtype)) return fail(LCBP_EINVAL, "bad buffer or dtype");
+  return transfer(h->rhou[h->cur], h->dtype, dst, dtype, h->n, false, h->staging, h->staging_elems, h->stream);
+}
+
+int lcbp_read_f(lcbp_lattice* h, void* dst, int dtype) {
+  CHECK_H(h);
+  if (!dst || !valid_dtype(dtype)) return fail(LCBP_EINVAL, "bad buffer or dtype");
+  return transfer(h->f[h->cur], h->dtype, dst, dtype, 15 * h->n, false, h->staging, h->staging_elems, h->stream);
+}
+
+int lcbp_free_energy(lcbp_lattice* h, double* F) {
+  CHECK_H(h);
+  if (!F) return fail(LCBP_EINVAL, "F is NULL");
+  int rc = diag(h, 0.0, 0);
+  if (rc) return rc;
+  *F = h->h_out[0];
+  return LCBP_OK;
+}
+
+int lcbp_totals(lcbp_lattice* h, double* mass, double momentum[3]) {
+  CHECK_H(h);
+  int rc = diag(h, 0.0, 1);
+  if (rc) return rc;
+  if (mass) *mass = h->h_out[1];
+  if (momentum) {
+    momentum[0] = h->h_out[2];
+    momentum[1] = h->h_out[3];
+    momentum[2] = h->h_out[4];
+  }
+  return LCBP_OK;
+}
+
+int lcbp_defect_fraction(lcbp_lattice* h, double threshold, double* fraction) {
+  CHECK_H(h);
+  if (!fraction) return fail(LCBP_EINVAL, "fraction is NULL");
+  int rc = diag(h, threshold, 0);
+  if (rc) return rc;
+  *fraction = h->h_out[5] / (double)h->n;
+  return LCBP_OK;
+}
+
+int lcbp_save(lcbp_lattice* h, const char* path) {
+  CHECK_H(h);
+  if (!path) return fail(LCBP_EINVAL, "path is NULL");
+  CkptHeader hd{};
+  std::memcpy(hd.magic, "LCBPCKP1", 8);
+  hd.version = 1;
+  hd.nx = h->nx;
+  hd.ny = h->ny;
+  hd.nz = h->nz;
+  hd.dtype = h->dtype;
+  hd.flow_on = h->p.flow_on;
+  hd.coupling = h->p.coupling;
+  hd.A0 = h->p.A0;
+  hd.gamma = h->p.gamma;
+  hd.K = h->p.K;
+  hd.q0 = h->p.q0;
+  hd.tau_f = h->p.tau_f;
+  hd.xi = h->p.xi;
+  hd.Gamma = h->p.Gamma;
+  hd.step = h->step;
+  std::vector<char> buf((size_t)20 * h->n * h->es);
+  int rc = lcbp_read_f(h, buf.data(), h->dtype);
+  if (rc) return rc;
+  rc = lcbp_read_q(h, buf.data() + (size_t)15 * h->n * h->es, h->dtype);
+  if (rc) return rc;
+  FILE* fp = std::fopen(path, "wb");
+  if (!fp) return fail(LCBP_EIO, "cannot open %s for writing", path);
+  const bool ok = std::fwrite(&hd, sizeof(hd), 1, fp) == 1 && std::fwrite(buf.data(), 1, buf.size(), fp) == buf.size();
+  const bool closed = std::fclose(fp) == 0;
+  return ok && closed ? LCBP_OK : fail(LCBP_EIO, "short write to %s", path);
+}
+
+int lcbp_load(lcbp_lattice* h, const char* path) {
+  CHECK_H(h);
+  if (!path) return fail(LCBP_EINVAL, "path is NULL");
+  FILE* fp = std::fopen(path, "rb");
+  if (!fp) return fail(LCBP_EIO, "cannot open %s", path);
+  CkptHeader hd{};
+  if (std::fread(&hd, sizeof(hd), 1, fp) != 1 || std::memcmp(hd.magic, "LCBPCKP1", 8) != 0 || hd.version != 1) {
+    std::fclose(fp);
+    return fail(LCBP_EIO, "%s is not an lcbp checkpoint", path);
+  }
+  if (hd.nx != h->nx || hd.ny != h->ny || hd.nz != h->nz || hd.dtype != h->dtype) {
+    std::fclose(fp);
+    return fail(LCBP_EINVAL, "checkpoint dims/dtype do not match the lattice");
+  }
+  std::vector<char> buf((size_t)20 * h->n * h->es);
+  const bool ok = std::fread(buf.data(), 1, buf.size(), fp) == buf.size();
+  std::fclose(fp);
+  if (!ok) return fail(LCBP_EIO, "truncated checkpoint %s", path);
+  HostParams p = h->p;
+  p.A0 = hd.A0;
+  p.gamma = hd.gamma;
+  p.K = hd.K;
+  p.q0 = hd.q0;
+  p.tau_f = hd.tau_f;
+  p.xi = hd.xi;
+  p.Gamma = hd.Gamma;
+  p.flow_on = hd.flow_on;
+  p.coupling = hd.coupling;
+  int rc = check_params(p);
+  if (rc) return rc;
+  if (p.flow_on != h->p.flow_on || p.coupling != h->p.coupling) drop_graph(h);
+  h->p = p;
+  rc = upload_replica(h);
+  if (rc) return rc;
+  rc = lcbp_set_f(h, buf.data(), h->dtype);
+  if (rc) return rc;
+  rc = lcbp_set_q(h, buf.data() + (size_t)15 * h->n * h->es, h->dtype);
+  if (rc) return rc;
+  h->step = hd.step;
+  return LCBP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,342 @@
+// Internal definitions shared by the CUDA translation units of liblcbp.
+//
+// Layout in HBM: every field is structure-of-arrays.  A batch holds R >= 1
+// replicas (a single lattice is R = 1); replica r owns sites
+// [base_r, base_r + n_r) of the concatenated site range, and a field with C
+// components stores replica r at  field + C * base_r  as  [c][z][y][x].
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace lcbp {
+
+// ---------------------------------------------------------------------------
+// Model parameters of one replica (Sec. 2.1 Eq. free_energy, Qevolution,
+// mat_der; Sec. 2.2 Eq. eq4).  Derived coefficients are precomputed on the
+// host in double and rounded once to the state type.
+// ---------------------------------------------------------------------------
+template <typename real>
+struct Model {
+  real a_bulk;   // A0 (1 - gamma/3)
+  real b_bulk;   // A0 gamma
+  real K;        // one-constant elastic constant
+  real kq0x2;    // 2 K q0
+  real kq0sq4;   // 4 K q0^2
+  real Gamma;    // rotational diffusion constant
+  real xi;       // flow-aligning parameter
+  real inv_tau;  // 1 / tau_f
+};
+
+// geometry + parameters of one replica, read by every CTA of its tiles
+template <typename real>
+struct Replica {
+  int nx, ny, nz, pad;
+  long long n;     // nx * ny * nz
+  long long base;  // first site of this replica in the concatenated range
+  Model<real> m;
+};
+
+// One unit of kernel work: a tile of TX x TY x TZ sites of replica `rep`
+// whose first site is (x0, y0, z0).  Tiles may hang over the lattice edge.
+struct Tile {
+  int rep;
+  int x0, y0, z0;
+};
+
+// tile shape chosen per lattice (autotuned); blockDim.x == tx * ty * tz
+struct TileShape {
+  int tx, ty, tz;
+};
+
+// ---------------------------------------------------------------------------
+// D3Q15 velocity set (Sec. 2.2 Eq. latvects), boundary ordering: rest,
+// +x -x +y -y +z -z, then (+-1,+-1,+-1) lexicographic with + before -.
+// ---------------------------------------------------------------------------
+constexpr int NV = 15;
+__host__ __device__ constexpr int ex(int i) {
+  return i == 1 ? 1 : i == 2 ? -1 : (i >= 7 ? (i < 11 ? 1 : -1) : 0);
+}
+__host__ __device__ constexpr int ey(int i) {
+  return i == 3 ? 1 : i == 4 ? -1 : (i >= 7 ? (((i - 7) & 2) ? -1 : 1) : 0);
+}
+__host__ __device__ constexpr int ez(int i) {
+  return i == 5 ? 1 : i == 6 ? -1 : (i >= 7 ? (((i - 7) & 1) ? -1 : 1) : 0);
+}
+
+// ---------------------------------------------------------------------------
+// Symmetric traceless tensors in 5 components [xx, xy, xz, yy, yz].
+// ---------------------------------------------------------------------------
+template <typename real>
+struct Sym5 {
+  real xx, xy, xz, yy, yz;
+  __device__ __forceinline__ real zz() const { return -xx - yy; }
+};
+
+template <typename real>
+struct Mat3 {
+  real a[3][3];
+};
+
+template <typename real>
+__device__ __forceinline__ Mat3<real> full(const Sym5<real>& s) {
+  Mat3<real> m;
+  m.a[0][0] = s.xx; m.a[0][1] = s.xy; m.a[0][2] = s.xz;
+  m.a[1][0] = s.xy; m.a[1][1] = s.yy; m.a[1][2] = s.yz;
+  m.a[2][0] = s.xz; m.a[2][1] = s.yz; m.a[2][2] = -s.xx - s.yy;
+  return m;
+}
+
+// A_ab B_ab of two symmetric traceless tensors
+template <typename real>
+__device__ __forceinline__ real ddot(const Sym5<real>& a, const Sym5<real>& b) {
+  return a.xx * b.xx + a.yy * b.yy + a.zz() * b.zz() +
+         real(2) * (a.xy * b.xy + a.xz * b.xz + a.yz * b.yz);
+}
+
+template <typename real>
+__device__ __forceinline__ Sym5<real> load5(const real* __restrict__ p, long long n, long long s) {
+  Sym5<real> q;
+  q.xx = __ldg(p + s);
+  q.xy = __ldg(p + n + s);
+  q.xz = __ldg(p + 2 * n + s);
+  q.yy = __ldg(p + 3 * n + s);
+  q.yz = __ldg(p + 4 * n + s);
+  return q;
+}
+
+template <typename real>
+__device__ __forceinline__ void store5(real* __restrict__ p, long long n, long long s, const Sym5<real>& q) {
+  p[s] = q.xx;
+  p[n + s] = q.xy;
+  p[2 * n + s] = q.xz;
+  p[3 * n + s] = q.yy;
+  p[4 * n + s] = q.yz;
+}
+
+// Periodic neighbourhood of one site: linear indices of the 6 face
+// neighbours and the wrapped coordinates.
+struct Nbr {
+  int x, y, z, xm, xp, ym, yp, zm, zp;
+  long long s;
+  __device__ __forceinline__ long long at(int xx, int yy, int zz, int nx, int ny) const {
+    return ((long long)zz * ny + yy) * nx + xx;
+  }
+};
+
+__device__ __forceinline__ Nbr make_nbr(int x, int y, int z, int nx, int ny, int nz) {
+  Nbr b;
+  b.x = x; b.y = y; b.z = z;
+  b.xm = x == 0 ? nx - 1 : x - 1;
+  b.xp = x == nx - 1 ? 0 : x + 1;
+  b.ym = y == 0 ? ny - 1 : y - 1;
+  b.yp = y == ny - 1 ? 0 : y + 1;
+  b.zm = z == 0 ? nz - 1 : z - 1;
+  b.zp = z == nz - 1 ? 0 : z + 1;
+  b.s = ((long long)z * ny + y) * nx + x;
+  return b;
+}
+
+// Q and its 6 face neighbours, as needed by every stencil of the step.
+template <typename real>
+struct Stencil7 {
+  Sym5<real> c, xm, xp, ym, yp, zm, zp;
+};
+
+template <typename real>
+__device__ __forceinline__ Stencil7<real> load_stencil(const real* __restrict__ q, long long n,
+                                                       const Nbr& b, int nx, int ny) {
+  Stencil7<real> st;
+  st.c = load5(q, n, b.s);
+  st.xm = load5(q, n, b.at(b.xm, b.y, b.z, nx, ny));
+  st.xp = load5(q, n, b.at(b.xp, b.y, b.z, nx, ny));
+  st.ym = load5(q, n, b.at(b.x, b.ym, b.z, nx, ny));
+  st.yp = load5(q, n, b.at(b.x, b.yp, b.z, nx, ny));
+  st.zm = load5(q, n, b.at(b.x, b.y, b.zm, nx, ny));
+  st.zp = load5(q, n, b.at(b.x, b.y, b.zp, nx, ny));
+  return st;
+}
+
+template <typename real>
+__device__ __forceinline__ Sym5<real> half_diff(const Sym5<real>& p, const Sym5<real>& m) {
+  const real h = real(0.5);
+  return {h * (p.xx - m.xx), h * (p.xy - m.xy), h * (p.xz - m.xz), h * (p.yy - m.yy), h * (p.yz - m.yz)};
+}
+
+// ---------------------------------------------------------------------------
+// Molecular field, Sec. 2.1 Eq. (Qevolution) with the one-constant energy:
+// H = -A0(1-g/3) Q + A0 g (QQ - Tr(Q^2)/3 I) - A0 g Tr(Q^2) Q
+//     + K Lap7 Q - 2 K q0 (C + C^T) - 4 K q0^2 Q,   C_ab = eps_agd D0_g Q_db.
+// Also returns the three central derivatives D0_g Q for reuse.
+// ---------------------------------------------------------------------------
+template <typename real>
+__device__ __forceinline__ Sym5<real> molecular_field(const Stencil7<real>& st, const Model<real>& m,
+                                                      Sym5<real> dq[3]) {
+  const Sym5<real>& q = st.c;
+  dq[0] = half_diff(st.xp, st.xm);
+  dq[1] = half_diff(st.yp, st.ym);
+  dq[2] = half_diff(st.zp, st.zm);
+  const real qzz = q.zz();
+  // Q.Q (symmetric)
+  const real qq_xx = q.xx * q.xx + q.xy * q.xy + q.xz * q.xz;
+  const real qq_xy = q.xx * q.xy + q.xy * q.yy + q.xz * q.yz;
+  const real qq_xz = q.xx * q.xz + q.xy * q.yz + q.xz * qzz;
+  const real qq_yy = q.xy * q.xy + q.yy * q.yy + q.yz * q.yz;
+  const real qq_yz = q.xy * q.xz + q.yy * q.yz + q.yz * qzz;
+  const real qq_zz = q.xz * q.xz + q.yz * q.yz + qzz * qzz;
+  const real trq2 = qq_xx + qq_yy + qq_zz;
+  const real third = real(1) / real(3);
+  // 7-point Laplacian
+  auto lap = [&](real c, real a, real b, real cc, real d, real e, real f) {
+    return (a + b) + (cc + d) + (e + f) - real(6) * c;
+  };
+  const real l_xx = lap(q.xx, st.xm.xx, st.xp.xx, st.ym.xx, st.yp.xx, st.zm.xx, st.zp.xx);
+  const real l_xy = lap(q.xy, st.xm.xy, st.xp.xy, st.ym.xy, st.yp.xy, st.zm.xy, st.zp.xy);
+  const real l_xz = lap(q.xz, st.xm.xz, st.xp.xz, st.ym.xz, st.yp.xz, st.zm.xz, st.zp.xz);
+  const real l_yy = lap(q.yy, st.xm.yy, st.xp.yy, st.ym.yy, st.yp.yy, st.zm.yy, st.zp.yy);
+  const real l_yz = lap(q.yz, st.xm.yz, st.xp.yz, st.ym.yz, st.yp.yz, st.zm.yz, st.zp.yz);
+  // C_ab = eps_agd D0_g Q_db :  C_xb = D0y Q_zb - D0z Q_yb,  C_yb = D0z Q_xb - D0x Q_zb,
+  //                             C_zb = D0x Q_yb - D0y Q_xb
+  const Sym5<real>& dx = dq[0];
+  const Sym5<real>& dy = dq[1];
+  const Sym5<real>& dz = dq[2];
+  const real c_xx = dy.xz - dz.xy;
+  const real c_xy = dy.yz - dz.yy;
+  const real c_xz = dy.zz() - dz.yz;
+  const real c_yx = dz.xx - dx.xz;
+  const real c_yy = dz.xy - dx.yz;
+  const real c_yz = dz.xz - dx.zz();
+  const real c_zx = dx.xy - dy.xx;
+  const real c_zy = dx.yy - dy.xy;
+  const real c_zz = dx.yz - dy.xz;
+  (void)c_zz;
+  const real bulk_iso = m.a_bulk + m.b_bulk * trq2 + m.kq0sq4;  // coefficient of -Q
+  Sym5<real> H;
+  H.xx = -bulk_iso * q.xx + m.b_bulk * (qq_xx - third * trq2) + m.K * l_xx - m.kq0x2 * (c_xx + c_xx);
+  H.xy = -bulk_iso * q.xy + m.b_bulk * qq_xy + m.K * l_xy - m.kq0x2 * (c_xy + c_yx);
+  H.xz = -bulk_iso * q.xz + m.b_bulk * qq_xz + m.K * l_xz - m.kq0x2 * (c_xz + c_zx);
+  H.yy = -bulk_iso * q.yy + m.b_bulk * (qq_yy - third * trq2) + m.K * l_yy - m.kq0x2 * (c_yy + c_yy);
+  H.yz = -bulk_iso * q.yz + m.b_bulk * qq_yz + m.K * l_yz - m.kq0x2 * (c_yz + c_zy);
+  return H;
+}
+
+// ---------------------------------------------------------------------------
+// Stress, Sec. 2.1 Eq. (BEstress):
+// sigma_LC = 2 xi (Q + I/3) Tr(QH) - xi (H (Q+I/3) + (Q+I/3) H)   (symmetric, traceless)
+// tau = Q H - H Q  (antisymmetric; returned as [xy, xz, yz])
+// ---------------------------------------------------------------------------
+template <typename real>
+__device__ __forceinline__ void lc_stress(const Sym5<real>& q, const Sym5<real>& h, real xi,
+                                          Sym5<real>& sigma, real tau[3]) {
+  const Mat3<real> Q = full(q);
+  const Mat3<real> H = full(h);
+  real QH[3][3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) QH[a][b] = Q.a[a][0] * H.a[0][b] + Q.a[a][1] * H.a[1][b] + Q.a[a][2] * H.a[2][b];
+  // (HQ)_ab = (QH)_ba since both are symmetric
+  const real trqh = QH[0][0] + QH[1][1] + QH[2][2];
+  const real two_xi_tr = real(2) * xi * trqh;
+  const real two_third_xi = real(2) * xi / real(3);
+  // With P = Q + I/3:  H P + P H = H Q + Q H + 2H/3, and 2 xi P Tr(QH) carries
+  // the isotropic part (2 xi / 3) Tr(QH) I on the diagonal.  The total is
+  // traceless, so sigma_zz = -sigma_xx - sigma_yy holds and 5 components suffice.
+  const real iso = two_xi_tr / real(3);
+  sigma.xx = two_xi_tr * q.xx + iso - xi * (QH[0][0] + QH[0][0]) - two_third_xi * h.xx;
+  sigma.xy = two_xi_tr * q.xy - xi * (QH[0][1] + QH[1][0]) - two_third_xi * h.xy;
+  sigma.xz = two_xi_tr * q.xz - xi * (QH[0][2] + QH[2][0]) - two_third_xi * h.xz;
+  sigma.yy = two_xi_tr * q.yy + iso - xi * (QH[1][1] + QH[1][1]) - two_third_xi * h.yy;
+  sigma.yz = two_xi_tr * q.yz - xi * (QH[1][2] + QH[2][1]) - two_third_xi * h.yz;
+  tau[0] = QH[0][1] - QH[1][0];
+  tau[1] = QH[0][2] - QH[2][0];
+  tau[2] = QH[1][2] - QH[2][1];
+}
+
+// ---------------------------------------------------------------------------
+// dQ/dt of Eq. (Qevolution) + (mat_der):  Gamma H + S_traceless(W, Q) - u . D0 Q
+// with W_ab = D0_b u_a given as w[a][b].
+// ---------------------------------------------------------------------------
+template <typename real>
+__device__ __forceinline__ Sym5<real> be_rate(const Sym5<real>& q, const Sym5<real>& h, const Sym5<real> dq[3],
+                                              const real u[3], const real w[3][3], const Model<real>& m,
+                                              bool flow) {
+  Sym5<real> r;
+  r.xx = m.Gamma * h.xx;
+  r.xy = m.Gamma * h.xy;
+  r.xz = m.Gamma * h.xz;
+  r.yy = m.Gamma * h.yy;
+  r.yz = m.Gamma * h.yz;
+  if (!flow) return r;
+  const real xi = m.xi;
+  const Mat3<real> Q = full(q);
+  real D[3][3], O[3][3], P[3][3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      D[a][b] = real(0.5) * (w[a][b] + w[b][a]);
+      O[a][b] = real(0.5) * (w[a][b] - w[b][a]);
+      P[a][b] = Q.a[a][b] + (a == b ? real(1) / real(3) : real(0));
+    }
+  real trQW = real(0);
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) trQW += Q.a[a][b] * w[b][a];
+  // S = xi (D P + P D) + (O P - P O) - 2 xi P Tr(QW)
+  real S[3][3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = a; b < 3; ++b) {
+      real dp = real(0), pd = real(0), op = real(0), po = real(0);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        dp += D[a][c] * P[c][b];
+        pd += P[a][c] * D[c][b];
+        op += O[a][c] * P[c][b];
+        po += P[a][c] * O[c][b];
+      }
+      S[a][b] = xi * (dp + pd) + (op - po) - real(2) * xi * P[a][b] * trQW;
+    }
+  const real trS3 = (S[0][0] + S[1][1] + S[2][2]) / real(3);
+  const real ux = u[0], uy = u[1], uz = u[2];
+  auto adv = [&](real gx, real gy, real gz) { return ux * gx + uy * gy + uz * gz; };
+  r.xx += (S[0][0] - trS3) - adv(dq[0].xx, dq[1].xx, dq[2].xx);
+  r.xy += S[0][1] - adv(dq[0].xy, dq[1].xy, dq[2].xy);
+  r.xz += S[0][2] - adv(dq[0].xz, dq[1].xz, dq[2].xz);
+  r.yy += (S[1][1] - trS3) - adv(dq[0].yy, dq[1].yy, dq[2].yy);
+  r.yz += S[1][2] - adv(dq[0].yz, dq[1].yz, dq[2].yz);
+  return r;
+}
+
+// ---------------------------------------------------------------------------
+// LB equilibrium and forcing for one direction, Sec. 2.2 Eq. (feq), (coeff),
+// T = 1/3:  f_i^eq = A_s + B_s u.e + C_s u^2 + D_s (u.e)^2 + e.E_s.e ,  p_i = P_s b.e
+// ---------------------------------------------------------------------------
+template <typename real>
+__device__ __forceinline__ real feq_dir(int i, real rho, real ux, real uy, real uz, real usq,
+                                        const Sym5<real>& s) {
+  if (i == 0) return rho * (real(8) / real(15)) - rho * (real(2) / real(3)) * usq;
+  const real eu = real(ex(i)) * ux + real(ey(i)) * uy + real(ez(i)) * uz;
+  if (i <= 6) {
+    // faces: A1 = rho/30, B1 = rho/3, C1 = -rho/12, D1 = rho/2, E1 = -sigma/2
+    const real see = (i <= 2) ? s.xx : (i <= 4) ? s.yy : s.zz();
+    return rho * (real(1) / real(30) + eu * (real(1) / real(3)) - usq * (real(1) / real(12)) +
+                  eu * eu * real(0.5)) - real(0.5) * see;
+  }
+  // corners: A2 = rho/30, B2 = rho/24, C2 = -rho/24, D2 = rho/16, E2 = -sigma/16
+  const real see = real(2) * (real(ex(i) * ey(i)) * s.xy + real(ex(i) * ez(i)) * s.xz + real(ey(i) * ez(i)) * s.yz);
+  return rho * (real(1) / real(30) + eu * (real(1) / real(24)) - usq * (real(1) / real(24)) +
+                eu * eu * (real(1) / real(16))) - (real(1) / real(16)) * see;
+}
+
+template <typename real>
+__device__ __forceinline__ real force_dir(int i, real bx, real by, real bz) {
+  if (i == 0) return real(0);
+  const real eb = real(ex(i)) * bx + real(ey(i)) * by + real(ez(i)) * bz;
+  return (i <= 6 ? real(1) / real(3) : real(1) / real(24)) * eb;
+}
+
+}  // namespace lcbp

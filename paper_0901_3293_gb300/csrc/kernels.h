@@ -1,0 +1,80 @@
+// Host-side entry points of the kernels (internal to liblcbp).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace lcbp {
+
+// Device pointers of one step.  `reps` points to a device array of
+// Replica<real>; the field pointers are the bases of the concatenated arrays.
+struct StepArgs {
+  const void* reps;
+  const Tile* tiles;
+  int ntiles;
+  TileShape ts;
+  int flow_on;
+  int coupling;  // 0 Jacobi, 1 Gauss-Seidel
+  void* q;       // 5 comps, updated in place
+  void* qs;      // 5 comps scratch (Heun predictor)
+  void* h;       // 5 comps scratch
+  void* sigma;   // 5 comps scratch
+  void* tau;     // 3 comps scratch
+  void* b;       // 3 comps scratch
+  const void* bext;  // 3 comps or nullptr
+  void* f;       // 15 comps, step n
+  void* fnew;    // 15 comps, step n+1
+  void* rhou;    // 4 comps [rho, ux, uy, uz], step n
+  void* rhou_new;
+  // optional: events[0] is recorded before the first kernel of the step and
+  // events[k + 1] after kernel k (per-kernel timing); nullptr otherwise
+  cudaEvent_t* events;
+};
+
+// number of kernels launch_step issues for a mode
+inline int kernels_per_step(int flow_on, int coupling) { return flow_on ? (coupling ? 5 : 3) : 3; }
+
+template <typename real>
+cudaError_t launch_step(const StepArgs& a, cudaStream_t s);
+template <typename real>
+cudaError_t launch_field(const StepArgs& a, cudaStream_t s);
+
+// initial Q (kinds as in lcbp.h); per-replica q0 is in q0s[rep] (device array)
+struct InitQArgs {
+  int kind;
+  double amplitude;
+  double noise;
+  uint64_t seed;
+  int z0;
+};
+template <typename real>
+cudaError_t launch_init_q(const void* reps, const Tile* tiles, int ntiles, TileShape ts, const double* q0s,
+                          const double* s_helix, const uint64_t* seeds, InitQArgs a, void* q, cudaStream_t s);
+
+// f = f^eq(rho0, u, sigma) with u from u3 (state type, may be null); then moments
+template <typename real>
+cudaError_t launch_init_feq(const void* reps, const Tile* tiles, int ntiles, TileShape ts, double rho0,
+                            const void* u3, const void* sigma, void* f, cudaStream_t s);
+template <typename real>
+cudaError_t launch_moments(const void* reps, const Tile* tiles, int ntiles, TileShape ts, const void* f,
+                           void* rhou, cudaStream_t s);
+
+// element-wise dtype conversion of n values
+cudaError_t launch_convert(const void* src, int src_dtype, void* dst, int dst_dtype, long long n, cudaStream_t s);
+
+// Diagnostics of one lattice (replica), accumulated in FP64 with a fixed
+// reduction order: out[0..6] = [F_h, mass, Px, Py, Pz, #sites with
+// lambda_max(Q) < threshold, #non-finite sites].  partials holds 512 * 8 doubles.
+struct DiagGeom {
+  int nx, ny, nz;
+  long long n, base;
+  double A0, gamma, K, q0;
+};
+template <typename real>
+cudaError_t launch_diag_one(const DiagGeom& g, const void* q, const void* f, int with_f, double threshold,
+                            double* partials, double* out, cudaStream_t s);
+constexpr int kDiagPartials = 512 * 8;
+
+}  // namespace lcbp

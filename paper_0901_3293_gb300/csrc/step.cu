@@ -1,0 +1,337 @@
+// The three kernels of one coupled step (Sec. 2.2, hybrid scheme).
+//
+//   k_field          Q^n            -> H(Q^n), sigma_LC, tau          (Eq. Qevolution, BEstress)
+//   k_force_predict  Q^n, H, tau, u -> b (Eq. eq7a + spurious), Q* = Q^n + R(Q^n)   (Heun predictor)
+//   k_lb_correct     f^n, rho u, sigma, b, Q*, Q^n
+//                    -> f^{n+1}, rho u^{n+1} (Eq. eq2, eq4, feq, coeff),
+//                       Q^{n+1} = (Q^n + Q* + R(Q*)) / 2                       (Heun corrector)
+//
+// One thread per site; each CTA walks a list of tiles (replica, origin) so
+// that a single launch covers every replica of a batch.  Neighbour values
+// come through the read-only data path (L1/L2); the halo of a tile is
+// re-read from L2, not from HBM.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace lcbp {
+
+template <typename real>
+__device__ __forceinline__ bool tile_site(const Replica<real>* reps, const Tile* tiles, int t, TileShape ts,
+                                          Replica<real>& R, int& x, int& y, int& z) {
+  const Tile tl = tiles[t];
+  R = reps[tl.rep];
+  const int tid = threadIdx.x;
+  const int lx = tid % ts.tx;
+  const int ly = (tid / ts.tx) % ts.ty;
+  const int lz = tid / (ts.tx * ts.ty);
+  x = tl.x0 + lx;
+  y = tl.y0 + ly;
+  z = tl.z0 + lz;
+  return lz < ts.tz && x < R.nx && y < R.ny && z < R.nz;
+}
+
+// velocity at a site from the stored moments [rho, ux, uy, uz]
+template <typename real>
+__device__ __forceinline__ void load_u(const real* __restrict__ ru, long long n, long long s, real u[3]) {
+  u[0] = __ldg(ru + n + s);
+  u[1] = __ldg(ru + 2 * n + s);
+  u[2] = __ldg(ru + 3 * n + s);
+}
+
+// W_ab = D0_b u_a from the 6 face neighbours
+template <typename real>
+__device__ __forceinline__ void velocity_gradient(const real* __restrict__ ru, long long n, const Nbr& b,
+                                                  int nx, int ny, real w[3][3]) {
+  real up[3], um[3];
+  load_u(ru, n, b.at(b.xp, b.y, b.z, nx, ny), up);
+  load_u(ru, n, b.at(b.xm, b.y, b.z, nx, ny), um);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) w[a][0] = real(0.5) * (up[a] - um[a]);
+  load_u(ru, n, b.at(b.x, b.yp, b.z, nx, ny), up);
+  load_u(ru, n, b.at(b.x, b.ym, b.z, nx, ny), um);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) w[a][1] = real(0.5) * (up[a] - um[a]);
+  load_u(ru, n, b.at(b.x, b.y, b.zp, nx, ny), up);
+  load_u(ru, n, b.at(b.x, b.y, b.zm, nx, ny), um);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) w[a][2] = real(0.5) * (up[a] - um[a]);
+}
+
+// ---------------------------------------------------------------------------
+template <typename real, bool FLOW>
+__global__ void __launch_bounds__(256) k_field(const Replica<real>* __restrict__ reps,
+                                               const Tile* __restrict__ tiles, int ntiles, TileShape ts,
+                                               const real* __restrict__ Q, real* __restrict__ H,
+                                               real* __restrict__ sigma, real* __restrict__ tau) {
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    Replica<real> R;
+    int x, y, z;
+    if (!tile_site(reps, tiles, t, ts, R, x, y, z)) continue;
+    const long long n = R.n;
+    const Nbr nb = make_nbr(x, y, z, R.nx, R.ny, R.nz);
+    const Stencil7<real> st = load_stencil(Q + 5 * R.base, n, nb, R.nx, R.ny);
+    Sym5<real> dq[3];
+    const Sym5<real> h = molecular_field(st, R.m, dq);
+    store5(H + 5 * R.base, n, nb.s, h);
+    if (FLOW) {
+      Sym5<real> sg;
+      real tu[3];
+      lc_stress(st.c, h, R.m.xi, sg, tu);
+      store5(sigma + 5 * R.base, n, nb.s, sg);
+      real* tp = tau + 3 * R.base;
+      tp[nb.s] = tu[0];
+      tp[n + nb.s] = tu[1];
+      tp[2 * n + nb.s] = tu[2];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// DO_B: body force b = D0_b tau_ab - H_gn D0_a Q_gn (+ external force)
+// DO_QS: Heun predictor Q* = Q + R(Q, u); FLOW: u from the stored moments,
+//        else u = 0.
+template <typename real, bool FLOW, bool DO_B, bool DO_QS, bool BEXT>
+__global__ void __launch_bounds__(256) k_force_predict(const Replica<real>* __restrict__ reps,
+                                                       const Tile* __restrict__ tiles, int ntiles, TileShape ts,
+                                                       const real* __restrict__ Q, const real* __restrict__ H,
+                                                       const real* __restrict__ tau, const real* __restrict__ rhou,
+                                                       const real* __restrict__ bext, real* __restrict__ bout,
+                                                       real* __restrict__ Qs) {
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    Replica<real> R;
+    int x, y, z;
+    if (!tile_site(reps, tiles, t, ts, R, x, y, z)) continue;
+    const long long n = R.n;
+    const Nbr nb = make_nbr(x, y, z, R.nx, R.ny, R.nz);
+    const Stencil7<real> st = load_stencil(Q + 5 * R.base, n, nb, R.nx, R.ny);
+    Sym5<real> dq[3];
+    dq[0] = half_diff(st.xp, st.xm);
+    dq[1] = half_diff(st.yp, st.ym);
+    dq[2] = half_diff(st.zp, st.zm);
+    const Sym5<real> h = load5(H + 5 * R.base, n, nb.s);
+    if (DO_B) {
+      const real* tp = tau + 3 * R.base;
+      auto tv = [&](int c, long long s) { return __ldg(tp + c * n + s); };
+      const long long sxp = nb.at(nb.xp, y, z, R.nx, R.ny), sxm = nb.at(nb.xm, y, z, R.nx, R.ny);
+      const long long syp = nb.at(x, nb.yp, z, R.nx, R.ny), sym = nb.at(x, nb.ym, z, R.nx, R.ny);
+      const long long szp = nb.at(x, y, nb.zp, R.nx, R.ny), szm = nb.at(x, y, nb.zm, R.nx, R.ny);
+      // tau = [xy, xz, yz], tau_yx = -tau_xy etc.
+      const real half = real(0.5);
+      real bx = half * (tv(0, syp) - tv(0, sym)) + half * (tv(1, szp) - tv(1, szm));
+      real by = -half * (tv(0, sxp) - tv(0, sxm)) + half * (tv(2, szp) - tv(2, szm));
+      real bz = -half * (tv(1, sxp) - tv(1, sxm)) - half * (tv(2, syp) - tv(2, sym));
+      bx -= ddot(h, dq[0]);
+      by -= ddot(h, dq[1]);
+      bz -= ddot(h, dq[2]);
+      if (BEXT) {
+        const real* be = bext + 3 * R.base;
+        bx += __ldg(be + nb.s);
+        by += __ldg(be + n + nb.s);
+        bz += __ldg(be + 2 * n + nb.s);
+      }
+      real* bo = bout + 3 * R.base;
+      bo[nb.s] = bx;
+      bo[n + nb.s] = by;
+      bo[2 * n + nb.s] = bz;
+    }
+    if (DO_QS) {
+      real u[3] = {real(0), real(0), real(0)};
+      real w[3][3] = {};
+      if (FLOW) {
+        const real* ru = rhou + 4 * R.base;
+        load_u(ru, n, nb.s, u);
+        velocity_gradient(ru, n, nb, R.nx, R.ny, w);
+      }
+      const Sym5<real> r = be_rate(st.c, h, dq, u, w, R.m, FLOW);
+      const Sym5<real> qs = {st.c.xx + r.xx, st.c.xy + r.xy, st.c.xz + r.xz, st.c.yy + r.yy, st.c.yz + r.yz};
+      store5(Qs + 5 * R.base, n, nb.s, qs);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// DO_LB: predictor-corrector LB (pull form) writing f^{n+1} and its moments.
+// DO_Q2: Heun corrector for Q with u from `rhou_q` (u^n for Jacobi coupling,
+//        u^{n+1} for Gauss-Seidel), in place on Q.
+template <typename real, bool FLOW, bool DO_LB, bool DO_Q2>
+__global__ void __launch_bounds__(256) k_lb_correct(const Replica<real>* __restrict__ reps,
+                                                    const Tile* __restrict__ tiles, int ntiles, TileShape ts,
+                                                    const real* __restrict__ f, const real* __restrict__ rhou,
+                                                    const real* __restrict__ sigma, const real* __restrict__ bf,
+                                                    real* __restrict__ fnew, real* __restrict__ rhou_new,
+                                                    const real* __restrict__ Qs, const real* __restrict__ rhou_q,
+                                                    real* __restrict__ Q) {
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    Replica<real> R;
+    int x, y, z;
+    if (!tile_site(reps, tiles, t, ts, R, x, y, z)) continue;
+    const long long n = R.n;
+    const int nx = R.nx, ny = R.ny;
+    const Nbr nb = make_nbr(x, y, z, nx, ny, R.nz);
+    if (DO_LB) {
+      const real* fr = f + 15 * R.base;
+      const real* ru = rhou + 4 * R.base;
+      const real* sg = sigma + 5 * R.base;
+      const real* bb = bf + 3 * R.base;
+      const real inv_tau = R.m.inv_tau;
+      real fs[NV], fh[NV];
+      Sym5<real> sig_y;
+      real b_y[3];
+#pragma unroll
+      for (int i = 0; i < NV; ++i) {
+        // source site y - e_i
+        const int sx = ex(i) > 0 ? nb.xm : ex(i) < 0 ? nb.xp : x;
+        const int sy = ey(i) > 0 ? nb.ym : ey(i) < 0 ? nb.yp : y;
+        const int sz = ez(i) > 0 ? nb.zm : ez(i) < 0 ? nb.zp : z;
+        const long long src = ((long long)sz * ny + sy) * nx + sx;
+        const real fi = __ldg(fr + i * n + src);
+        const real rho = __ldg(ru + src);
+        const real ux = __ldg(ru + n + src), uy = __ldg(ru + 2 * n + src), uz = __ldg(ru + 3 * n + src);
+        const Sym5<real> s = load5(sg, n, src);
+        const real bx = __ldg(bb + src), by = __ldg(bb + n + src), bz = __ldg(bb + 2 * n + src);
+        if (i == 0) {
+          sig_y = s;
+          b_y[0] = bx; b_y[1] = by; b_y[2] = bz;
+        }
+        const real usq = ux * ux + uy * uy + uz * uz;
+        const real C = -(fi - feq_dir(i, rho, ux, uy, uz, usq, s)) * inv_tau + force_dir(i, bx, by, bz);
+        fs[i] = fi + C;
+        fh[i] = fi + real(0.5) * C;
+      }
+      real rs = real(0), jx = real(0), jy = real(0), jz = real(0);
+#pragma unroll
+      for (int i = 0; i < NV; ++i) {
+        rs += fs[i];
+        jx += real(ex(i)) * fs[i];
+        jy += real(ey(i)) * fs[i];
+        jz += real(ez(i)) * fs[i];
+      }
+      const real inv_rs = real(1) / rs;
+      const real usx = jx * inv_rs, usy = jy * inv_rs, usz = jz * inv_rs;
+      const real ussq = usx * usx + usy * usy + usz * usz;
+      real* fo = fnew + 15 * R.base;
+      real r1 = real(0), j1x = real(0), j1y = real(0), j1z = real(0);
+#pragma unroll
+      for (int i = 0; i < NV; ++i) {
+        const real Cs = -(fs[i] - feq_dir(i, rs, usx, usy, usz, ussq, sig_y)) * inv_tau +
+                        force_dir(i, b_y[0], b_y[1], b_y[2]);
+        const real fo_i = fh[i] + real(0.5) * Cs;
+        fo[i * n + nb.s] = fo_i;
+        r1 += fo_i;
+        j1x += real(ex(i)) * fo_i;
+        j1y += real(ey(i)) * fo_i;
+        j1z += real(ez(i)) * fo_i;
+      }
+      real* rn = rhou_new + 4 * R.base;
+      const real inv_r1 = real(1) / r1;
+      rn[nb.s] = r1;
+      rn[n + nb.s] = j1x * inv_r1;
+      rn[2 * n + nb.s] = j1y * inv_r1;
+      rn[3 * n + nb.s] = j1z * inv_r1;
+    }
+    if (DO_Q2) {
+      const Stencil7<real> st = load_stencil(Qs + 5 * R.base, n, nb, nx, ny);
+      Sym5<real> dq[3];
+      const Sym5<real> h = molecular_field(st, R.m, dq);
+      real u[3] = {real(0), real(0), real(0)};
+      real w[3][3] = {};
+      if (FLOW) {
+        const real* ru = rhou_q + 4 * R.base;
+        load_u(ru, n, nb.s, u);
+        velocity_gradient(ru, n, nb, nx, ny, w);
+      }
+      const Sym5<real> r = be_rate(st.c, h, dq, u, w, R.m, FLOW);
+      real* qp = Q + 5 * R.base;
+      const Sym5<real> q0 = load5(qp, n, nb.s);
+      const real half = real(0.5);
+      const Sym5<real> q1 = {half * (q0.xx + st.c.xx + r.xx), half * (q0.xy + st.c.xy + r.xy),
+                             half * (q0.xz + st.c.xz + r.xz), half * (q0.yy + st.c.yy + r.yy),
+                             half * (q0.yz + st.c.yz + r.yz)};
+      store5(qp, n, nb.s, q1);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host launchers
+// ---------------------------------------------------------------------------
+template <typename real>
+cudaError_t launch_step(const StepArgs& a, cudaStream_t s) {
+  const auto* reps = static_cast<const Replica<real>*>(a.reps);
+  const int threads = a.ts.tx * a.ts.ty * a.ts.tz;
+  const int grid = a.ntiles;
+  auto Rp = [](void* p) { return static_cast<real*>(p); };
+  auto Cp = [](const void* p) { return static_cast<const real*>(p); };
+  int k = 0;
+  auto mark = [&]() {
+    if (a.events) cudaEventRecord(a.events[k], s);
+    ++k;
+  };
+  mark();
+  if (a.flow_on) {
+    k_field<real, true><<<grid, threads, 0, s>>>(reps, a.tiles, a.ntiles, a.ts, Cp(a.q), Rp(a.h), Rp(a.sigma), Rp(a.tau));
+    mark();
+    if (a.coupling == 0) {
+      if (a.bext)
+        k_force_predict<real, true, true, true, true><<<grid, threads, 0, s>>>(
+            reps, a.tiles, a.ntiles, a.ts, Cp(a.q), Cp(a.h), Cp(a.tau), Cp(a.rhou), Cp(a.bext), Rp(a.b), Rp(a.qs));
+      else
+        k_force_predict<real, true, true, true, false><<<grid, threads, 0, s>>>(
+            reps, a.tiles, a.ntiles, a.ts, Cp(a.q), Cp(a.h), Cp(a.tau), Cp(a.rhou), nullptr, Rp(a.b), Rp(a.qs));
+      mark();
+      k_lb_correct<real, true, true, true><<<grid, threads, 0, s>>>(
+          reps, a.tiles, a.ntiles, a.ts, Cp(a.f), Cp(a.rhou), Cp(a.sigma), Cp(a.b), Rp(a.fnew), Rp(a.rhou_new),
+          Cp(a.qs), Cp(a.rhou), Rp(a.q));
+      mark();
+    } else {
+      // Gauss-Seidel: b, LB, then the Heun stages with u^{n+1}
+      if (a.bext)
+        k_force_predict<real, true, true, false, true><<<grid, threads, 0, s>>>(
+            reps, a.tiles, a.ntiles, a.ts, Cp(a.q), Cp(a.h), Cp(a.tau), Cp(a.rhou), Cp(a.bext), Rp(a.b), nullptr);
+      else
+        k_force_predict<real, true, true, false, false><<<grid, threads, 0, s>>>(
+            reps, a.tiles, a.ntiles, a.ts, Cp(a.q), Cp(a.h), Cp(a.tau), Cp(a.rhou), nullptr, Rp(a.b), nullptr);
+      mark();
+      k_lb_correct<real, true, true, false><<<grid, threads, 0, s>>>(
+          reps, a.tiles, a.ntiles, a.ts, Cp(a.f), Cp(a.rhou), Cp(a.sigma), Cp(a.b), Rp(a.fnew), Rp(a.rhou_new),
+          nullptr, nullptr, nullptr);
+      mark();
+      k_force_predict<real, true, false, true, false><<<grid, threads, 0, s>>>(
+          reps, a.tiles, a.ntiles, a.ts, Cp(a.q), Cp(a.h), nullptr, Cp(a.rhou_new), nullptr, nullptr, Rp(a.qs));
+      mark();
+      k_lb_correct<real, true, false, true><<<grid, threads, 0, s>>>(
+          reps, a.tiles, a.ntiles, a.ts, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, Cp(a.qs),
+          Cp(a.rhou_new), Rp(a.q));
+      mark();
+    }
+  } else {
+    k_field<real, false><<<grid, threads, 0, s>>>(reps, a.tiles, a.ntiles, a.ts, Cp(a.q), Rp(a.h), nullptr, nullptr);
+    mark();
+    k_force_predict<real, false, false, true, false><<<grid, threads, 0, s>>>(
+        reps, a.tiles, a.ntiles, a.ts, Cp(a.q), Cp(a.h), nullptr, nullptr, nullptr, nullptr, Rp(a.qs));
+    mark();
+    k_lb_correct<real, false, false, true><<<grid, threads, 0, s>>>(
+        reps, a.tiles, a.ntiles, a.ts, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, Cp(a.qs), nullptr,
+        Rp(a.q));
+    mark();
+  }
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_step<float>(const StepArgs&, cudaStream_t);
+template cudaError_t launch_step<double>(const StepArgs&, cudaStream_t);
+
+// sigma_LC(Q) only (used to build the initial equilibrium distributions)
+template <typename real>
+cudaError_t launch_field(const StepArgs& a, cudaStream_t s) {
+  const auto* reps = static_cast<const Replica<real>*>(a.reps);
+  const int threads = a.ts.tx * a.ts.ty * a.ts.tz;
+  k_field<real, true><<<a.ntiles, threads, 0, s>>>(reps, a.tiles, a.ntiles, a.ts, static_cast<const real*>(a.q),
+                                                   static_cast<real*>(a.h), static_cast<real*>(a.sigma),
+                                                   static_cast<real*>(a.tau));
+  return cudaGetLastError();
+}
+template cudaError_t launch_field<float>(const StepArgs&, cudaStream_t);
+template cudaError_t launch_field<double>(const StepArgs&, cudaStream_t);
+
+}  // namespace lcbp

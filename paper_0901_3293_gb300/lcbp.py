@@ -1,0 +1,293 @@
+"""Thin Python binding of liblcbp.so (ctypes).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+kernels behind the C ABI declared in ``include/lcbp.h``.  There is no CPU
+fallback: if the library is not built, or no GPU is present, calls raise.
+
+PyTorch supplies device memory and streams: by default a lattice lives in a
+``torch.uint8`` CUDA tensor (``lcbp_create_on_buffers``) and runs on a stream
+owned by that lattice.  Field buffers may be numpy arrays (host) or torch
+tensors (host or device); shapes follow the boundary layout
+``[component, z, y, x]``.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "liblcbp.so")
+
+OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, ETIMEOUT, ESTATE, EIO = 0, -1, -2, -3, -4, -5, -6, -7
+F32, F64 = 0, 1
+BPII, CHOL_X, CHOL_Y, CHOL_Z, ISO_NOISE, SLAB_BPII_IN_CHOL = range(6)
+JACOBI, GAUSS_SEIDEL = 0, 1
+
+_lib = None
+
+_c_int, _c_double, _c_void_p, _c_size_t = ctypes.c_int, ctypes.c_double, ctypes.c_void_p, ctypes.c_size_t
+_P = ctypes.c_void_p  # opaque handle
+
+_SIGNATURES = {
+    "lcbp_strerror": (ctypes.c_char_p, [_c_int]),
+    "lcbp_last_error": (ctypes.c_char_p, []),
+    "lcbp_version": (_c_int, []),
+    "lcbp_create": (_c_int, [_c_int, _c_int, _c_int, _c_int, ctypes.POINTER(_P)]),
+    "lcbp_workspace_bytes": (_c_size_t, [_c_int, _c_int, _c_int, _c_int]),
+    "lcbp_create_on_buffers": (_c_int, [_c_int, _c_int, _c_int, _c_int, _c_void_p, _c_size_t, _c_void_p,
+                                        ctypes.POINTER(_P)]),
+    "lcbp_destroy": (_c_int, [_P]),
+    "lcbp_get_info": (_c_int, [_P, ctypes.POINTER(_c_int), ctypes.POINTER(_c_int),
+                               ctypes.POINTER(ctypes.c_longlong)]),
+    "lcbp_set_ldg": (_c_int, [_P, _c_double, _c_double, _c_double, _c_double]),
+    "lcbp_set_ldg_kappa_tau": (_c_int, [_P, _c_double, _c_double, _c_double, _c_double]),
+    "lcbp_set_flow": (_c_int, [_P, _c_double, _c_double, _c_double, _c_int, _c_int]),
+    "lcbp_init_q": (_c_int, [_P, _c_int, _c_double, _c_double, ctypes.c_uint64, ctypes.POINTER(_c_int)]),
+    "lcbp_set_q": (_c_int, [_P, _c_void_p, _c_int]),
+    "lcbp_init_f_equilibrium": (_c_int, [_P, _c_double, _c_void_p, _c_int]),
+    "lcbp_set_f": (_c_int, [_P, _c_void_p, _c_int]),
+    "lcbp_set_body_force": (_c_int, [_P, _c_void_p, _c_int]),
+    "lcbp_step": (_c_int, [_P, _c_int]),
+    "lcbp_synchronize": (_c_int, [_P]),
+    "lcbp_profile_steps": (_c_int, [_P, _c_int, ctypes.POINTER(_c_double), _c_int, ctypes.POINTER(_c_int)]),
+    "lcbp_read_q": (_c_int, [_P, _c_void_p, _c_int]),
+    "lcbp_read_u": (_c_int, [_P, _c_void_p, _c_int]),
+    "lcbp_read_rho": (_c_int, [_P, _c_void_p, _c_int]),
+    "lcbp_read_f": (_c_int, [_P, _c_void_p, _c_int]),
+    "lcbp_free_energy": (_c_int, [_P, ctypes.POINTER(_c_double)]),
+    "lcbp_totals": (_c_int, [_P, ctypes.POINTER(_c_double), ctypes.POINTER(_c_double)]),
+    "lcbp_defect_fraction": (_c_int, [_P, _c_double, ctypes.POINTER(_c_double)]),
+    "lcbp_save": (_c_int, [_P, ctypes.c_char_p]),
+    "lcbp_load": (_c_int, [_P, ctypes.c_char_p]),
+}
+
+
+class LcbpError(RuntimeError):
+    def __init__(self, code: int, message: str):
+        super().__init__(f"{message} (status {code})")
+        self.code = code
+
+
+def lib() -> ctypes.CDLL:
+    """Load liblcbp.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is not built: run paper_0901_3293_gb300.build.build() "
+                               "(or __graft_entry__.build()); there is no CPU fallback")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def check(rc: int) -> None:
+    if rc != OK:
+        msg = lib().lcbp_last_error().decode() or lib().lcbp_strerror(rc).decode()
+        raise LcbpError(rc, msg)
+
+
+def _dtype_code(a) -> int:
+    name = str(a.dtype)
+    if name.endswith("float32"):
+        return F32
+    if name.endswith("float64"):
+        return F64
+    raise TypeError(f"buffers must be float32 or float64, got {name}")
+
+
+def _ptr(a):
+    """(pointer, dtype code, keep-alive) of a numpy array or torch tensor."""
+    if isinstance(a, np.ndarray):
+        a = np.ascontiguousarray(a)
+        return a.ctypes.data, _dtype_code(a), a
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            a = a.contiguous()
+        if a.is_cuda:
+            import torch
+            # the library works on its own stream: finish pending torch work on the tensor
+            torch.cuda.synchronize(a.device)
+        return a.data_ptr(), _dtype_code(a), a
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+    return a.ctypes.data, F64, a
+
+
+class Lattice:
+    """A periodic nx * ny * nz lattice on the current CUDA device.
+
+    memory="torch" (default): state lives in a torch CUDA tensor and work runs
+    on a torch stream owned by the lattice; memory="library": lcbp_create
+    allocates with cudaMalloc and owns its stream.
+    """
+
+    def __init__(self, nx: int, ny: int, nz: int, dtype: str = "f32", memory: str = "torch", device=None):
+        self.dims = (int(nx), int(ny), int(nz))
+        self.n = self.dims[0] * self.dims[1] * self.dims[2]
+        self.state_dtype = {"f32": F32, "f64": F64}[dtype]
+        self.np_dtype = np.float32 if self.state_dtype == F32 else np.float64
+        self._h = _P()
+        self._ws = None
+        self._stream = None
+        L = lib()
+        if memory == "torch":
+            import torch
+            dev = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+            nbytes = L.lcbp_workspace_bytes(*self.dims, self.state_dtype)
+            if nbytes == 0:
+                raise LcbpError(EINVAL, "invalid lattice size")
+            with torch.cuda.device(dev):
+                self._ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=dev)
+                self._stream = torch.cuda.Stream(device=dev)
+                base = self._ws.data_ptr()
+                off = (-base) % 256
+                check(L.lcbp_create_on_buffers(*self.dims, self.state_dtype, base + off, nbytes,
+                                               self._stream.cuda_stream, ctypes.byref(self._h)))
+        elif memory == "library":
+            check(L.lcbp_create(*self.dims, self.state_dtype, ctypes.byref(self._h)))
+        else:
+            raise ValueError(memory)
+
+    # -- lifetime -----------------------------------------------------------
+    def close(self) -> None:
+        if self._h:
+            check(lib().lcbp_destroy(self._h))
+            self._h = _P()
+        self._ws = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- parameters ---------------------------------------------------------
+    def set_ldg(self, A0: float, gamma: float, K: float, q0: float) -> "Lattice":
+        check(lib().lcbp_set_ldg(self._h, A0, gamma, K, q0))
+        return self
+
+    def set_ldg_kappa_tau(self, A0: float, q0: float, kappa: float, tau: float) -> "Lattice":
+        check(lib().lcbp_set_ldg_kappa_tau(self._h, A0, q0, kappa, tau))
+        return self
+
+    def set_flow(self, tau_f: float = 2.0, xi: float = 0.7, Gamma: float = 0.3, flow_on: bool = True,
+                 coupling: int = JACOBI) -> "Lattice":
+        check(lib().lcbp_set_flow(self._h, tau_f, xi, Gamma, int(bool(flow_on)), coupling))
+        return self
+
+    # -- state ----------------------------------------------------------------
+    def init_q(self, kind: int, amplitude: float, noise: float = 0.0, seed: int = 0, z0: int | None = None):
+        region = (ctypes.c_int * 1)(z0) if z0 is not None else None
+        check(lib().lcbp_init_q(self._h, kind, amplitude, noise, seed, region))
+        return self
+
+    def set_q(self, q5) -> "Lattice":
+        p, d, keep = _ptr(q5)
+        self._check_size(keep, 5)
+        check(lib().lcbp_set_q(self._h, p, d))
+        return self
+
+    def init_f_equilibrium(self, rho0: float = 1.0, u3=None) -> "Lattice":
+        if u3 is None:
+            check(lib().lcbp_init_f_equilibrium(self._h, rho0, None, F64))
+        else:
+            p, d, keep = _ptr(u3)
+            self._check_size(keep, 3)
+            check(lib().lcbp_init_f_equilibrium(self._h, rho0, p, d))
+        return self
+
+    def set_f(self, f15) -> "Lattice":
+        p, d, keep = _ptr(f15)
+        self._check_size(keep, 15)
+        check(lib().lcbp_set_f(self._h, p, d))
+        return self
+
+    def set_body_force(self, b3) -> "Lattice":
+        if b3 is None:
+            check(lib().lcbp_set_body_force(self._h, None, F64))
+        else:
+            p, d, keep = _ptr(b3)
+            self._check_size(keep, 3)
+            check(lib().lcbp_set_body_force(self._h, p, d))
+        return self
+
+    def step(self, nsteps: int = 1) -> "Lattice":
+        check(lib().lcbp_step(self._h, int(nsteps)))
+        return self
+
+    def profile_steps(self, nsteps: int):
+        """Advance nsteps steps kernel by kernel; mean device ms per kernel."""
+        ms = (_c_double * 8)()
+        nk = _c_int()
+        check(lib().lcbp_profile_steps(self._h, int(nsteps), ms, 8, ctypes.byref(nk)))
+        return list(ms[:nk.value])
+
+    def synchronize(self) -> None:
+        check(lib().lcbp_synchronize(self._h))
+
+    def _check_size(self, a, comps: int) -> None:
+        if int(np.prod(a.shape)) != comps * self.n:
+            raise LcbpError(EINVAL, f"expected {comps} x {self.n} values, got shape {tuple(a.shape)}")
+
+    def _read(self, fn, comps: int, dtype, out=None):
+        shape = (comps, self.dims[2], self.dims[1], self.dims[0])
+        if out is None:
+            out = np.empty(shape, dtype=dtype)
+        p, d, keep = _ptr(out)
+        check(fn(self._h, p, d))
+        return out
+
+    def read_q(self, dtype=np.float64, out=None):
+        return self._read(lib().lcbp_read_q, 5, dtype, out)
+
+    def read_u(self, dtype=np.float64, out=None):
+        return self._read(lib().lcbp_read_u, 3, dtype, out)
+
+    def read_rho(self, dtype=np.float64, out=None):
+        return self._read(lib().lcbp_read_rho, 1, dtype, out)[0] if out is None else \
+            self._read(lib().lcbp_read_rho, 1, dtype, out)
+
+    def read_f(self, dtype=np.float64, out=None):
+        return self._read(lib().lcbp_read_f, 15, dtype, out)
+
+    # -- diagnostics ------------------------------------------------------------
+    def free_energy(self) -> float:
+        F = _c_double()
+        check(lib().lcbp_free_energy(self._h, ctypes.byref(F)))
+        return F.value
+
+    def totals(self):
+        m = _c_double()
+        P = (_c_double * 3)()
+        check(lib().lcbp_totals(self._h, ctypes.byref(m), P))
+        return m.value, np.array(P[:])
+
+    def defect_fraction(self, threshold: float = 0.19) -> float:
+        fr = _c_double()
+        check(lib().lcbp_defect_fraction(self._h, threshold, ctypes.byref(fr)))
+        return fr.value
+
+    def info(self):
+        dims = (_c_int * 3)()
+        dt = _c_int()
+        st = ctypes.c_longlong()
+        check(lib().lcbp_get_info(self._h, dims, ctypes.byref(dt), ctypes.byref(st)))
+        return tuple(dims), dt.value, st.value
+
+    def save(self, path: str) -> None:
+        check(lib().lcbp_save(self._h, os.fsencode(path)))
+
+    def load(self, path: str) -> None:
+        check(lib().lcbp_load(self._h, os.fsencode(path)))

@@ -1,0 +1,260 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+FP64 state: agreement to rounding (<= 1e-12 after 100 steps).
+FP32 state: max |dQ|, max |du| <= 1e-4 after 100 steps of the 32^3 BPII run
+(the tolerance the hot path is specified to); per-component errors are
+printed.  Shapes include odd and ragged sizes, one-site-wide columns and
+several tiles with a ragged tail.
+"""
+
+import os
+
+import numpy as np
+import pytest
+
+from oracle import initial, lbq
+from paper_0901_3293_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+SEED = synth.BASE_SEED
+
+
+@pytest.fixture(scope="module")
+def lcbp():
+    import torch
+    from paper_0901_3293_gb300 import build
+    build.build()
+    from paper_0901_3293_gb300 import lcbp as L
+    torch.cuda.set_device(0)
+    return L
+
+
+def make(L, shape, dtype, p: lbq.Params, memory="torch"):
+    nz, ny, nx = shape
+    lat = L.Lattice(nx, ny, nz, dtype=dtype, memory=memory)
+    lat.set_ldg(p.A0, p.gamma, p.K, p.q0)
+    lat.set_flow(p.tau_f, p.xi, p.Gamma, p.flow_on, L.GAUSS_SEIDEL if p.coupling == "gauss_seidel" else L.JACOBI)
+    return lat
+
+
+def oracle_u(f):
+    return np.moveaxis(lbq.moments(f)[1], -1, 0)
+
+
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("dtype,tol", [("f64", 1e-15), ("f32", 2e-7)])
+@pytest.mark.parametrize("kind", [initial.BPII, initial.CHOL_X, initial.CHOL_Y, initial.CHOL_Z,
+                                  initial.ISO_NOISE, initial.SLAB_BPII_IN_CHOL])
+def test_init_q_matches_oracle(lcbp, kind, dtype, tol):
+    p = lbq.Params()
+    shape = (9, 6, 7)
+    lat = make(lcbp, shape, dtype, p)
+    amp = 0.3 if kind in (initial.BPII, initial.SLAB_BPII_IN_CHOL) else 0.45
+    lat.init_q(kind, amp, noise=1e-3, seed=SEED + kind, z0=4 if kind == initial.SLAB_BPII_IN_CHOL else None)
+    want = initial.init_q5(shape, kind, p.q0, amp, 1e-3, SEED + kind, z0=4, s_helix=initial.s_eq(p.gamma))
+    assert np.abs(lat.read_q() - want).max() <= tol
+
+
+# ---------------------------------------------------------------------------
+SHAPES = [(5, 6, 7), (4, 4, 4), (64, 1, 1), (3, 5, 33), (1, 9, 2)]
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_one_coupled_step_f64(lcbp, shape):
+    p = lbq.Params()
+    q5 = synth.smooth_q5(shape, 0.3, 1) + synth.random_q5(shape, 1e-2, 2)
+    f15 = synth.random_distributions(shape, 3, amp=2e-3)
+    lat = make(lcbp, shape, "f64", p)
+    lat.set_q(q5).set_f(f15).step(1)
+    f, Q = lbq.step(lbq.f_from_soa(f15), lbq.q5_to_q9(q5), p)
+    assert np.abs(lat.read_q() - lbq.q9_to_q5(Q)).max() < 1e-14
+    assert np.abs(lat.read_f() - lbq.f_to_soa(f)).max() < 1e-14
+    assert np.abs(lat.read_u() - oracle_u(f)).max() < 1e-14
+
+
+@pytest.mark.parametrize("coupling", ["jacobi", "gauss_seidel"])
+@pytest.mark.parametrize("flow_on", [True, False])
+def test_ten_steps_f64_modes(lcbp, coupling, flow_on):
+    p = lbq.Params(coupling=coupling, flow_on=flow_on)
+    shape = (6, 7, 8)
+    q5 = initial.init_q5(shape, initial.BPII, p.q0, 0.3, 1e-2, 5)
+    f15 = synth.random_distributions(shape, 6, amp=2e-3)
+    lat = make(lcbp, shape, "f64", p)
+    lat.set_q(q5).set_f(f15).step(10)
+    f, Q = lbq.run(lbq.f_from_soa(f15), lbq.q5_to_q9(q5), p, 10)
+    assert np.abs(lat.read_q() - lbq.q9_to_q5(Q)).max() < 1e-13
+    assert np.abs(lat.read_f() - lbq.f_to_soa(f)).max() < 1e-14
+
+
+def _config1(lcbp, dtype, nsteps=100):
+    p = lbq.Params()  # A0 0.01, gamma 3.1, K 0.01, q0 2 pi/16, Gamma 0.3, xi 0.7, tau_f 2
+    shape = (32, 32, 32)
+    lat = make(lcbp, shape, dtype, p)
+    lat.init_q(lcbp.BPII, 0.3, noise=1e-4, seed=SEED)
+    lat.init_f_equilibrium(1.0)
+    lat.step(nsteps)
+    Q = initial.init_q9(shape, initial.BPII, p.q0, 0.3, 1e-4, SEED)
+    f = lbq.init_f_equilibrium(Q, p)
+    f, Q = lbq.run(f, Q, p, nsteps)
+    return lat, f, Q, p
+
+
+@pytest.fixture(scope="module")
+def config1_f32(lcbp):
+    return _config1(lcbp, "f32")
+
+
+def test_config1_f32_within_1e_4_after_100_steps(config1_f32):
+    lat, f, Q, p = config1_f32
+    dq = np.abs(lat.read_q() - lbq.q9_to_q5(Q)).reshape(5, -1).max(axis=1)
+    du = np.abs(lat.read_u() - oracle_u(f)).reshape(3, -1).max(axis=1)
+    print("config-1 FP32 max|dQ| per component [xx xy xz yy yz]:", dq)
+    print("config-1 FP32 max|du| per component [x y z]:", du, " max|u| =", np.abs(oracle_u(f)).max())
+    assert dq.max() <= 1e-4 and du.max() <= 1e-4
+
+
+def test_config1_f64_matches_to_rounding(lcbp):
+    lat, f, Q, p = _config1(lcbp, "f64")
+    assert np.abs(lat.read_q() - lbq.q9_to_q5(Q)).max() < 1e-12
+    assert np.abs(lat.read_u() - oracle_u(f)).max() < 1e-13
+    F = lat.free_energy()
+    assert abs(F - lbq.free_energy(Q, p)) < 1e-11 * abs(F)
+    mass, mom = lat.totals()
+    m_o, P_o = lbq.totals(f)
+    assert abs(mass - m_o) < 1e-10 and np.abs(mom - P_o).max() < 1e-12
+    assert lat.defect_fraction(0.19) == lbq.defect_fraction(Q, 0.19)
+
+
+def test_diagnostics_f32(config1_f32):
+    lat, f, Q, p = config1_f32
+    F = lat.free_energy()
+    assert abs(F - lbq.free_energy(Q, p)) < 1e-4 * abs(F)
+    mass, mom = lat.totals()
+    m_o, P_o = lbq.totals(f)
+    assert abs(mass - m_o) < 1e-7 * m_o and np.abs(mom - P_o).max() < 1e-4
+    # sites near the threshold may flip in FP32: compare within a few sites
+    assert abs(lat.defect_fraction(0.19) - lbq.defect_fraction(Q, 0.19)) * 32 ** 3 <= 3
+
+
+@pytest.mark.parametrize("dtype,tol", [("f64", 1e-14), ("f32", 5e-7)])
+def test_external_force_kolmogorov(lcbp, dtype, tol):
+    """Q = 0 and xi = 0 leave pure forced LB: a Kolmogorov force along x."""
+    p = lbq.Params(xi=0.0)
+    L_ = 32
+    shape = (L_, 2, 3)
+    z = np.arange(L_)[:, None, None] * np.ones(shape)
+    b = np.zeros((3,) + shape)
+    b[0] = 1e-5 * np.sin(2 * np.pi * z / L_)
+    lat = make(lcbp, shape, dtype, p)
+    lat.set_q(np.zeros((5,) + shape)).init_f_equilibrium(1.0).set_body_force(b).step(200)
+    f = lbq.equilibrium(np.ones(shape), np.zeros(shape + (3,)), np.zeros(shape + (3, 3)))
+    f, _ = lbq.run(f, np.zeros(shape + (3, 3)), p, 200, b_ext=np.moveaxis(b, 0, -1))
+    assert np.abs(lat.read_u() - oracle_u(f)).max() < tol
+    assert np.abs(lat.read_u()).max() > 1e-5
+
+
+def test_graph_replay_equals_eager_steps(lcbp):
+    p = lbq.Params()
+    shape = (8, 8, 8)
+    a = make(lcbp, shape, "f32", p)
+    b = make(lcbp, shape, "f32", p, memory="library")
+    for lat in (a, b):
+        lat.init_q(lcbp.BPII, 0.3, noise=1e-4, seed=1).init_f_equilibrium(1.0)
+    a.step(11)
+    for _ in range(11):
+        b.step(1)
+    assert np.array_equal(a.read_f(), b.read_f()) and np.array_equal(a.read_q(), b.read_q())
+    assert a.info()[2] == 11 and b.info()[2] == 11
+
+
+def test_checkpoint_resume_is_bitwise(lcbp, tmp_path):
+    p = lbq.Params()
+    shape = (6, 8, 10)
+    a = make(lcbp, shape, "f32", p)
+    a.init_q(lcbp.BPII, 0.3, noise=1e-4, seed=2).init_f_equilibrium(1.0).step(20)
+    b = make(lcbp, shape, "f32", p)
+    b.init_q(lcbp.BPII, 0.3, noise=1e-4, seed=2).init_f_equilibrium(1.0).step(9)
+    path = str(tmp_path / "ck.bin")
+    b.save(path)
+    c = make(lcbp, shape, "f32", lbq.Params(A0=0.5))
+    c.load(path)
+    assert c.info()[2] == 9
+    c.step(11)
+    assert np.array_equal(a.read_f(), c.read_f()) and np.array_equal(a.read_q(), c.read_q())
+
+
+def test_errors_are_status_codes(lcbp):
+    L = lcbp
+    with pytest.raises(L.LcbpError) as e:
+        L.Lattice(0, 4, 4)
+    assert e.value.code == L.EINVAL
+    lat = L.Lattice(4, 4, 4)
+    with pytest.raises(L.LcbpError) as e:
+        lat.step(1)  # f not initialised, flow on
+    assert e.value.code == L.ESTATE
+    with pytest.raises(L.LcbpError) as e:
+        lat.set_flow(tau_f=-1.0)
+    assert e.value.code == L.EINVAL
+    with pytest.raises(L.LcbpError) as e:
+        lat.init_q(99, 0.3)
+    assert e.value.code == L.EINVAL
+    # a NaN planted in the host buffer is reported by the FP64 diagnostics
+    q = np.zeros((5, 4, 4, 4))
+    q[2, 1, 2, 3] = np.nan
+    lat.set_q(q)
+    with pytest.raises(L.LcbpError) as e:
+        lat.free_energy()
+    assert e.value.code == L.ENONFINITE
+    # the lattice stays usable afterwards
+    lat.set_q(np.zeros((5, 4, 4, 4))).init_f_equilibrium(1.0).step(3)
+    assert lat.free_energy() == 0.0
+
+
+def test_torch_device_buffers(lcbp):
+    import torch
+    p = lbq.Params()
+    shape = (4, 5, 6)
+    q5 = torch.tensor(synth.random_q5(shape, 0.1, 9), device="cuda", dtype=torch.float32)
+    lat = make(lcbp, shape, "f32", p)
+    lat.set_q(q5).init_f_equilibrium(1.0)
+    out = torch.empty_like(q5)
+    lat.read_q(out=out)
+    assert torch.equal(out, q5)
+    out64 = lat.read_q()
+    assert np.abs(out64 - q5.double().cpu().numpy()).max() == 0
+
+
+# ---------------------------------------------------------------------------
+# Full-size sampled parity: 256^3 BPII (pitch 32), one step, in the launch
+# configuration the benchmark times.  One coupled step at a site depends on Q
+# within 3 sites and f within 2 sites, so the oracle run on a periodic 9^3
+# cube cut around a sampled site reproduces that site exactly.
+# ---------------------------------------------------------------------------
+def test_full_size_sampled_parity_256(lcbp):
+    p = lbq.Params(q0=2 * np.pi / 32)
+    n = 256
+    lat = make(lcbp, (n, n, n), "f32", p)
+    lat.init_q(lcbp.BPII, 0.3, noise=1e-4, seed=SEED)
+    lat.init_f_equilibrium(1.0)
+    lat.step(2)  # develop some flow first
+    q0 = lat.read_q(dtype=np.float32)
+    f0 = lat.read_f(dtype=np.float32)
+    m0, _ = lat.totals()
+    lat.step(1)
+    q1 = lat.read_q(dtype=np.float32)
+    u1 = lat.read_u(dtype=np.float32)
+    m1, _ = lat.totals()
+    rng = np.random.default_rng(7)
+    sites = [tuple(int(v) for v in rng.integers(0, n, 3)) for _ in range(12)] + [(0, 0, 0), (255, 255, 255)]
+    r = 4
+    for (z, y, x) in sites:
+        idx = [np.arange(c - r, c + r + 1) % n for c in (z, y, x)]
+        cube = np.ix_(idx[0], idx[1], idx[2])
+        Qc = lbq.q5_to_q9(q0[(slice(None),) + cube].astype(np.float64))
+        fc = lbq.f_from_soa(f0[(slice(None),) + cube].astype(np.float64))
+        fo, Qo = lbq.step(fc, Qc, p)
+        dq = np.abs(q1[:, z, y, x] - lbq.q9_to_q5(Qo)[:, r, r, r]).max()
+        du = np.abs(u1[:, z, y, x] - np.moveaxis(lbq.moments(fo)[1], -1, 0)[:, r, r, r]).max()
+        assert dq < 1e-6 and du < 1e-6, ((z, y, x), dq, du)
+    assert abs(m1 - m0) < 1e-6 * m0
