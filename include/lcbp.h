@@ -36,6 +36,10 @@
  * - Work is enqueued on the lattice's stream.  lcbp_step returns once the
  *   steps are enqueued; reads and diagnostics synchronise the stream.
  * - Lattice units throughout: dx = dt = 1.
+ * - Internally the populations are stored as deviations f_i - w_i from the
+ *   rest-state weights w = (8/15, 1/30, ..., 1/30) and the density as rho - 1,
+ *   which keeps FP32 state accurate (mass is conserved to the rounding of
+ *   O(1e-3) numbers).  The boundary always exchanges full f and rho.
  */
 #ifndef LCBP_H
 #define LCBP_H

@@ -579,6 +579,10 @@ int lcbp_set_f(lcbp_lattice* h, const void* f15, int dtype) {
   int rc = transfer(h->f[h->cur], h->dtype, const_cast<void*>(f15), dtype, 15 * h->n, true, h->staging,
                     h->staging_elems, h->stream);
   if (rc) return rc;
+  // to deviation storage, in place
+  cudaError_t e = h->dtype == LCBP_F64 ? launch_shift<double>(h->f[h->cur], h->f[h->cur], h->n, 15, 0, -1, h->stream)
+                                       : launch_shift<float>(h->f[h->cur], h->f[h->cur], h->n, 15, 0, -1, h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "set_f");
   rc = refresh_moments(h);
   if (rc) return rc;
   h->f_ready = true;
@@ -684,13 +688,22 @@ int lcbp_read_u(lcbp_lattice* h, void* dst, int dtype) {
 int lcbp_read_rho(lcbp_lattice* h, void* dst, int dtype) {
   CHECK_H(h);
   if (!dst || !valid_dtype(dtype)) return fail(LCBP_EINVAL, "bad buffer or dtype");
-  return transfer(h->rhou[h->cur], h->dtype, dst, dtype, h->n, false, h->staging, h->staging_elems, h->stream);
+  // rho = 1 + drho, assembled in the (free between steps) predictor scratch
+  cudaError_t e = h->dtype == LCBP_F64 ? launch_shift<double>(h->rhou[h->cur], h->qs, h->n, 1, 1, 1, h->stream)
+                                       : launch_shift<float>(h->rhou[h->cur], h->qs, h->n, 1, 1, 1, h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "read_rho");
+  return transfer(h->qs, h->dtype, dst, dtype, h->n, false, h->staging, h->staging_elems, h->stream);
 }
 
 int lcbp_read_f(lcbp_lattice* h, void* dst, int dtype) {
   CHECK_H(h);
   if (!dst || !valid_dtype(dtype)) return fail(LCBP_EINVAL, "bad buffer or dtype");
-  return transfer(h->f[h->cur], h->dtype, dst, dtype, 15 * h->n, false, h->staging, h->staging_elems, h->stream);
+  // f = w + df, assembled in the other ping-pong buffer (free between steps)
+  void* tmp = h->f[h->cur ^ 1];
+  cudaError_t e = h->dtype == LCBP_F64 ? launch_shift<double>(h->f[h->cur], tmp, h->n, 15, 0, 1, h->stream)
+                                       : launch_shift<float>(h->f[h->cur], tmp, h->n, 15, 0, 1, h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "read_f");
+  return transfer(tmp, h->dtype, dst, dtype, 15 * h->n, false, h->staging, h->staging_elems, h->stream);
 }
 
 int lcbp_free_energy(lcbp_lattice* h, double* F) {

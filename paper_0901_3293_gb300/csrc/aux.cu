@@ -118,8 +118,9 @@ __global__ void k_init_feq(const Replica<real>* __restrict__ reps, const Tile* _
     const Sym5<real> sg = load5(sigma + 5 * R.base, n, s);
     const real usq = ux * ux + uy * uy + uz * uz;
     real* fp = f + 15 * R.base;
+    // stored as deviations from the rest weights
 #pragma unroll
-    for (int i = 0; i < NV; ++i) fp[i * n + s] = feq_dir(i, rho0, ux, uy, uz, usq, sg);
+    for (int i = 0; i < NV; ++i) fp[i * n + s] = feq_delta(i, rho0 - real(1), rho0, ux, uy, uz, usq, sg);
   }
 }
 
@@ -146,17 +147,19 @@ __global__ void k_moments(const Replica<real>* __restrict__ reps, const Tile* __
     const long long n = R.n;
     const long long s = ((long long)z * R.ny + y) * R.nx + x;
     const real* fp = f + 15 * R.base;
-    real r = 0, jx = 0, jy = 0, jz = 0;
+    // deviation storage: drho = sum df_i, rho u = sum df_i e_i (sum w_i e_i = 0)
+    real dr = 0, jx = 0, jy = 0, jz = 0;
 #pragma unroll
     for (int i = 0; i < NV; ++i) {
       const real fi = fp[i * n + s];
-      r += fi;
+      dr += fi;
       jx += real(ex(i)) * fi;
       jy += real(ey(i)) * fi;
       jz += real(ez(i)) * fi;
     }
     real* rp = rhou + 4 * R.base;
-    rp[s] = r;
+    const real r = real(1) + dr;
+    rp[s] = dr;
     rp[n + s] = jx / r;
     rp[2 * n + s] = jy / r;
     rp[3 * n + s] = jz / r;
@@ -196,6 +199,35 @@ cudaError_t launch_convert(const void* src, int sd, void* dst, int dd, long long
     k_convert<double, double><<<grid, threads, 0, s>>>(static_cast<const double*>(src), static_cast<double*>(dst), n);
   return cudaGetLastError();
 }
+
+// ---------------------------------------------------------------------------
+// Deviation storage <-> boundary layout.  For a field of `comps` components
+// of n sites: dst[c n + s] = src[c n + s] + sign * shift(c), with shift(c) the
+// rest weight w_c (populations) or 1 (density).  In place is allowed.
+// ---------------------------------------------------------------------------
+template <typename real>
+__global__ void k_shift(const real* src, real* dst, long long n, int comps, int kind, real sign) {
+  const long long total = n * comps;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < total;
+       k += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(k / n);
+    const real w = kind == 0 ? (real)rest_weight(c) : real(1);
+    dst[k] = src[k] + sign * w;
+  }
+}
+
+template <typename real>
+cudaError_t launch_shift(const void* src, void* dst, long long n, int comps, int kind, int sign, cudaStream_t s) {
+  const long long total = n * comps;
+  if (total <= 0) return cudaSuccess;
+  const long long want = (total + 255) / 256;
+  const int grid = (int)(want < 65536 ? want : 65536);
+  k_shift<real><<<grid, 256, 0, s>>>(static_cast<const real*>(src), static_cast<real*>(dst), n, comps, kind,
+                                      (real)sign);
+  return cudaGetLastError();
+}
+template cudaError_t launch_shift<float>(const void*, void*, long long, int, int, int, cudaStream_t);
+template cudaError_t launch_shift<double>(const void*, void*, long long, int, int, int, cudaStream_t);
 
 // ---------------------------------------------------------------------------
 // Diagnostics in FP64.  Largest eigenvalue of a symmetric 3x3 matrix by the
@@ -273,7 +305,7 @@ __global__ void __launch_bounds__(256) k_diag(DiagGeom g, const real* __restrict
     acc[0] += bulk + 0.5 * g.K * grad2 + 2.0 * g.K * g.q0 * chiral + 2.0 * g.K * g.q0 * g.q0 * tr2;
     acc[5] += finite && lambda_max(Qc) < threshold ? 1.0 : 0.0;
     if (with_f) {
-      double r = 0, jx = 0, jy = 0, jz = 0;
+      double r = 1.0, jx = 0, jy = 0, jz = 0;  // deviation storage: rho = 1 + sum df_i
 #pragma unroll
       for (int i = 0; i < NV; ++i) {
         const double fi = fp[i * n + s];

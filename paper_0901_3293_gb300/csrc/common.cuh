@@ -314,22 +314,32 @@ __device__ __forceinline__ Sym5<real> be_rate(const Sym5<real>& q, const Sym5<re
 // ---------------------------------------------------------------------------
 // LB equilibrium and forcing for one direction, Sec. 2.2 Eq. (feq), (coeff),
 // T = 1/3:  f_i^eq = A_s + B_s u.e + C_s u^2 + D_s (u.e)^2 + e.E_s.e ,  p_i = P_s b.e
+//
+// Storage precision: populations are kept as deviations from the rest-state
+// weights, df_i = f_i - w_i with w = (8/15, 1/30 x 14) = f^eq(rho=1, u=0,
+// sigma=0), and the density as drho = rho - 1.  The deviations are O(1e-3),
+// so FP32 state keeps ~3 more decimal digits than storing f itself, and mass
+// is conserved to that finer rounding.  feq_delta returns f_i^eq - w_i.
 // ---------------------------------------------------------------------------
+__host__ __device__ constexpr double rest_weight(int i) { return i == 0 ? 8.0 / 15.0 : 1.0 / 30.0; }
+
 template <typename real>
-__device__ __forceinline__ real feq_dir(int i, real rho, real ux, real uy, real uz, real usq,
-                                        const Sym5<real>& s) {
-  if (i == 0) return rho * (real(8) / real(15)) - rho * (real(2) / real(3)) * usq;
+__device__ __forceinline__ real feq_delta(int i, real drho, real rho, real ux, real uy, real uz, real usq,
+                                          const Sym5<real>& s) {
+  // A_0 = rho - 14 rho/30 = w_0 rho; A_1 = A_2 = w_s rho  ->  A_s - w_s = w_s drho
+  if (i == 0) return drho * (real(8) / real(15)) - rho * (real(2) / real(3)) * usq;
   const real eu = real(ex(i)) * ux + real(ey(i)) * uy + real(ez(i)) * uz;
   if (i <= 6) {
     // faces: A1 = rho/30, B1 = rho/3, C1 = -rho/12, D1 = rho/2, E1 = -sigma/2
     const real see = (i <= 2) ? s.xx : (i <= 4) ? s.yy : s.zz();
-    return rho * (real(1) / real(30) + eu * (real(1) / real(3)) - usq * (real(1) / real(12)) +
-                  eu * eu * real(0.5)) - real(0.5) * see;
+    return drho * (real(1) / real(30)) +
+           rho * (eu * (real(1) / real(3)) - usq * (real(1) / real(12)) + eu * eu * real(0.5)) - real(0.5) * see;
   }
   // corners: A2 = rho/30, B2 = rho/24, C2 = -rho/24, D2 = rho/16, E2 = -sigma/16
   const real see = real(2) * (real(ex(i) * ey(i)) * s.xy + real(ex(i) * ez(i)) * s.xz + real(ey(i) * ez(i)) * s.yz);
-  return rho * (real(1) / real(30) + eu * (real(1) / real(24)) - usq * (real(1) / real(24)) +
-                eu * eu * (real(1) / real(16))) - (real(1) / real(16)) * see;
+  return drho * (real(1) / real(30)) +
+         rho * (eu * (real(1) / real(24)) - usq * (real(1) / real(24)) + eu * eu * (real(1) / real(16))) -
+         (real(1) / real(16)) * see;
 }
 
 template <typename real>

@@ -61,6 +61,11 @@ template <typename real>
 cudaError_t launch_moments(const void* reps, const Tile* tiles, int ntiles, TileShape ts, const void* f,
                            void* rhou, cudaStream_t s);
 
+// deviation storage <-> full values: dst = src + sign * (kind 0: w_c per
+// component c of an [comps][n] field; kind 1: 1)
+template <typename real>
+cudaError_t launch_shift(const void* src, void* dst, long long n, int comps, int kind, int sign, cudaStream_t s);
+
 // element-wise dtype conversion of n values
 cudaError_t launch_convert(const void* src, int src_dtype, void* dst, int dst_dtype, long long n, cudaStream_t s);
 

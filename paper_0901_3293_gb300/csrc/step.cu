@@ -169,12 +169,13 @@ __global__ void __launch_bounds__(256) k_lb_correct(const Replica<real>* __restr
     const int nx = R.nx, ny = R.ny;
     const Nbr nb = make_nbr(x, y, z, nx, ny, R.nz);
     if (DO_LB) {
+      // populations and density are stored as deviations df = f - w, drho = rho - 1
       const real* fr = f + 15 * R.base;
       const real* ru = rhou + 4 * R.base;
       const real* sg = sigma + 5 * R.base;
       const real* bb = bf + 3 * R.base;
       const real inv_tau = R.m.inv_tau;
-      real fs[NV], fh[NV];
+      real ds[NV], dh[NV];  // predictor f* and f + C/2, pulled from y - e_i (deviation form)
       Sym5<real> sig_y;
       real b_y[3];
 #pragma unroll
@@ -184,8 +185,8 @@ __global__ void __launch_bounds__(256) k_lb_correct(const Replica<real>* __restr
         const int sy = ey(i) > 0 ? nb.ym : ey(i) < 0 ? nb.yp : y;
         const int sz = ez(i) > 0 ? nb.zm : ez(i) < 0 ? nb.zp : z;
         const long long src = ((long long)sz * ny + sy) * nx + sx;
-        const real fi = __ldg(fr + i * n + src);
-        const real rho = __ldg(ru + src);
+        const real di = __ldg(fr + i * n + src);
+        const real drho = __ldg(ru + src);
         const real ux = __ldg(ru + n + src), uy = __ldg(ru + 2 * n + src), uz = __ldg(ru + 3 * n + src);
         const Sym5<real> s = load5(sg, n, src);
         const real bx = __ldg(bb + src), by = __ldg(bb + n + src), bz = __ldg(bb + 2 * n + src);
@@ -194,37 +195,39 @@ __global__ void __launch_bounds__(256) k_lb_correct(const Replica<real>* __restr
           b_y[0] = bx; b_y[1] = by; b_y[2] = bz;
         }
         const real usq = ux * ux + uy * uy + uz * uz;
-        const real C = -(fi - feq_dir(i, rho, ux, uy, uz, usq, s)) * inv_tau + force_dir(i, bx, by, bz);
-        fs[i] = fi + C;
-        fh[i] = fi + real(0.5) * C;
+        const real C = -(di - feq_delta(i, drho, real(1) + drho, ux, uy, uz, usq, s)) * inv_tau +
+                       force_dir(i, bx, by, bz);
+        ds[i] = di + C;
+        dh[i] = di + real(0.5) * C;
       }
-      real rs = real(0), jx = real(0), jy = real(0), jz = real(0);
+      real drs = real(0), jx = real(0), jy = real(0), jz = real(0);
 #pragma unroll
       for (int i = 0; i < NV; ++i) {
-        rs += fs[i];
-        jx += real(ex(i)) * fs[i];
-        jy += real(ey(i)) * fs[i];
-        jz += real(ez(i)) * fs[i];
+        drs += ds[i];
+        jx += real(ex(i)) * ds[i];
+        jy += real(ey(i)) * ds[i];
+        jz += real(ez(i)) * ds[i];
       }
+      const real rs = real(1) + drs;
       const real inv_rs = real(1) / rs;
       const real usx = jx * inv_rs, usy = jy * inv_rs, usz = jz * inv_rs;
       const real ussq = usx * usx + usy * usy + usz * usz;
       real* fo = fnew + 15 * R.base;
-      real r1 = real(0), j1x = real(0), j1y = real(0), j1z = real(0);
+      real dr1 = real(0), j1x = real(0), j1y = real(0), j1z = real(0);
 #pragma unroll
       for (int i = 0; i < NV; ++i) {
-        const real Cs = -(fs[i] - feq_dir(i, rs, usx, usy, usz, ussq, sig_y)) * inv_tau +
+        const real Cs = -(ds[i] - feq_delta(i, drs, rs, usx, usy, usz, ussq, sig_y)) * inv_tau +
                         force_dir(i, b_y[0], b_y[1], b_y[2]);
-        const real fo_i = fh[i] + real(0.5) * Cs;
+        const real fo_i = dh[i] + real(0.5) * Cs;
         fo[i * n + nb.s] = fo_i;
-        r1 += fo_i;
+        dr1 += fo_i;
         j1x += real(ex(i)) * fo_i;
         j1y += real(ey(i)) * fo_i;
         j1z += real(ez(i)) * fo_i;
       }
       real* rn = rhou_new + 4 * R.base;
-      const real inv_r1 = real(1) / r1;
-      rn[nb.s] = r1;
+      const real inv_r1 = real(1) / (real(1) + dr1);
+      rn[nb.s] = dr1;
       rn[n + nb.s] = j1x * inv_r1;
       rn[2 * n + nb.s] = j1y * inv_r1;
       rn[3 * n + nb.s] = j1z * inv_r1;
