@@ -235,7 +235,9 @@ LCBP_API int lcbp_defect_fraction(lcbp_lattice *h, double threshold, double *fra
 
 /*
  * Checkpoint: a versioned binary file with a header (magic, version, dims,
- * state dtype, parameters, step count) followed by f and Q in the state type.
+ * state dtype, parameters, step count) followed by the raw state in the state
+ * type (deviation populations, moments, Q), so a resumed run is bitwise
+ * identical to an uninterrupted one.
  * lcbp_load requires a lattice of the same dims and dtype.  Errors: LCBP_EIO,
  * LCBP_EINVAL (mismatch).
  */

@@ -737,12 +737,14 @@ int lcbp_defect_fraction(lcbp_lattice* h, double threshold, double* fraction) {
   return LCBP_OK;
 }
 
+// Checkpoints hold the raw state (deviation populations, moments, Q) in the
+// state type, so that a resumed run is bitwise identical to an uninterrupted one.
 int lcbp_save(lcbp_lattice* h, const char* path) {
   CHECK_H(h);
   if (!path) return fail(LCBP_EINVAL, "path is NULL");
   CkptHeader hd{};
-  std::memcpy(hd.magic, "LCBPCKP1", 8);
-  hd.version = 1;
+  std::memcpy(hd.magic, "LCBPCKP2", 8);
+  hd.version = 2;
   hd.nx = h->nx;
   hd.ny = h->ny;
   hd.nz = h->nz;
@@ -757,11 +759,13 @@ int lcbp_save(lcbp_lattice* h, const char* path) {
   hd.xi = h->p.xi;
   hd.Gamma = h->p.Gamma;
   hd.step = h->step;
-  std::vector<char> buf((size_t)20 * h->n * h->es);
-  int rc = lcbp_read_f(h, buf.data(), h->dtype);
-  if (rc) return rc;
-  rc = lcbp_read_q(h, buf.data() + (size_t)15 * h->n * h->es, h->dtype);
-  if (rc) return rc;
+  const size_t nf = (size_t)15 * h->n * h->es, nr = (size_t)4 * h->n * h->es, nq = (size_t)5 * h->n * h->es;
+  std::vector<char> buf(nf + nr + nq);
+  cudaError_t e = cudaMemcpyAsync(buf.data(), h->f[h->cur], nf, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(buf.data() + nf, h->rhou[h->cur], nr, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(buf.data() + nf + nr, h->q, nq, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "save");
   FILE* fp = std::fopen(path, "wb");
   if (!fp) return fail(LCBP_EIO, "cannot open %s for writing", path);
   const bool ok = std::fwrite(&hd, sizeof(hd), 1, fp) == 1 && std::fwrite(buf.data(), 1, buf.size(), fp) == buf.size();
@@ -775,7 +779,7 @@ int lcbp_load(lcbp_lattice* h, const char* path) {
   FILE* fp = std::fopen(path, "rb");
   if (!fp) return fail(LCBP_EIO, "cannot open %s", path);
   CkptHeader hd{};
-  if (std::fread(&hd, sizeof(hd), 1, fp) != 1 || std::memcmp(hd.magic, "LCBPCKP1", 8) != 0 || hd.version != 1) {
+  if (std::fread(&hd, sizeof(hd), 1, fp) != 1 || std::memcmp(hd.magic, "LCBPCKP2", 8) != 0 || hd.version != 2) {
     std::fclose(fp);
     return fail(LCBP_EIO, "%s is not an lcbp checkpoint", path);
   }
@@ -783,7 +787,8 @@ int lcbp_load(lcbp_lattice* h, const char* path) {
     std::fclose(fp);
     return fail(LCBP_EINVAL, "checkpoint dims/dtype do not match the lattice");
   }
-  std::vector<char> buf((size_t)20 * h->n * h->es);
+  const size_t nf = (size_t)15 * h->n * h->es, nr = (size_t)4 * h->n * h->es, nq = (size_t)5 * h->n * h->es;
+  std::vector<char> buf(nf + nr + nq);
   const bool ok = std::fread(buf.data(), 1, buf.size(), fp) == buf.size();
   std::fclose(fp);
   if (!ok) return fail(LCBP_EIO, "truncated checkpoint %s", path);
@@ -803,10 +808,12 @@ int lcbp_load(lcbp_lattice* h, const char* path) {
   h->p = p;
   rc = upload_replica(h);
   if (rc) return rc;
-  rc = lcbp_set_f(h, buf.data(), h->dtype);
-  if (rc) return rc;
-  rc = lcbp_set_q(h, buf.data() + (size_t)15 * h->n * h->es, h->dtype);
-  if (rc) return rc;
+  cudaError_t e = cudaMemcpyAsync(h->f[h->cur], buf.data(), nf, cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h->rhou[h->cur], buf.data() + nf, nr, cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h->q, buf.data() + nf + nr, nq, cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "load");
+  h->f_ready = true;
   h->step = hd.step;
   return LCBP_OK;
 }
