@@ -85,6 +85,10 @@ extern "C" {
 #define LCBP_JACOBI 0       /* LB and Q both read the step-n fields (default) */
 #define LCBP_GAUSS_SEIDEL 1 /* LB first, then Q advanced with u^{n+1} */
 
+/* kernel selection (lcbp_set_path) */
+#define LCBP_PATH_AUTO 0    /* fast z-marching TMA kernels where they apply, else generic */
+#define LCBP_PATH_GENERIC 1 /* always the generic one-thread-per-site kernels */
+
 typedef struct lcbp_lattice lcbp_lattice;
 
 /* Name of a status code (static string). */
@@ -198,7 +202,9 @@ LCBP_API int lcbp_step(lcbp_lattice *h, int nsteps);
  * Advance nsteps >= 1 steps exactly as lcbp_step does, but launched one kernel
  * at a time with a CUDA event between kernels, and return in kernel_ms the
  * mean device time of each kernel of one step (milliseconds).  *nkernels is
- * set to the number of kernels per step: 3 with flow on and Jacobi coupling
+ * set to the number of kernels per step: 2 on the fast path (qside: H, sigma,
+ * tau, b and the Heun predictor; lbq: LB predictor-corrector and the Heun
+ * corrector); on the generic path 3 with flow on and Jacobi coupling
  * (field: H/sigma/tau; force_predict: b and the Heun predictor; lb_correct:
  * LB predictor-corrector and the Heun corrector), 5 with Gauss-Seidel
  * coupling (field, force, lb, predict, correct), 3 with flow off (field,
@@ -206,7 +212,26 @@ LCBP_API int lcbp_step(lcbp_lattice *h, int nsteps);
  */
 LCBP_API int lcbp_profile_steps(lcbp_lattice *h, int nsteps, double *kernel_ms, int capacity, int *nkernels);
 
-/* Synchronise the lattice's stream.  Errors: LCBP_ECUDA. */
+/*
+ * Kernel selection.  LCBP_PATH_AUTO (default) runs the fast path -- two
+ * z-marching kernels that stage planes in shared memory with TMA tile loads
+ * -- whenever flow is on, coupling is Jacobi and nx is a multiple of 4;
+ * otherwise, or with LCBP_PATH_GENERIC, three one-thread-per-site kernels.
+ * Both compute the same step.  Errors: LCBP_EINVAL (unknown path).
+ */
+LCBP_API int lcbp_set_path(lcbp_lattice *h, int path);
+
+/*
+ * *fast = 1 if the next step runs the fast path; *planes_per_cta = the
+ * autotuned number of z-planes each CTA marches through (0 before the first
+ * step, or on the generic path).  The tuning times each candidate once per
+ * lattice shape and dtype, writing scratch buffers only; results persist in
+ * the file named by the environment variable LCBP_AUTOTUNE_CACHE, if set.
+ */
+LCBP_API int lcbp_get_path(lcbp_lattice *h, int *fast, int *planes_per_cta);
+
+/* Synchronise the lattice's stream.  Errors: LCBP_ECUDA; LCBP_ETIMEOUT if a
+ * bounded device-side wait of the fast path gave up (results invalid). */
 LCBP_API int lcbp_synchronize(lcbp_lattice *h);
 
 /* Copy out Q (5 * N), u (3 * N), rho (N) or f (15 * N) values.  Errors: LCBP_EINVAL. */

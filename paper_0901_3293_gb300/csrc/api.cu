@@ -2,6 +2,9 @@
 // replay), transfers, diagnostics and checkpoints.  See include/lcbp.h.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
+#include <map>
+#include <mutex>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -165,6 +168,12 @@ struct lcbp_lattice {
   cudaGraphExec_t graph;
   bool graph_ok;
   long long step;
+  // fast path (z-marching TMA kernels)
+  int path_req;   // LCBP_PATH_*
+  bool tmaps_ok;  // tensor maps built
+  int zc;         // planes per CTA, 0 until tuned
+  CUtensorMap tm[6];  // Q, rho u [0], rho u [1], sigma, b, Q*
+  int* d_err;
 };
 
 namespace {
@@ -197,8 +206,8 @@ Layout layout(int nx, int ny, int nz, int dtype) {
   o = align256(o + replica_bytes(dtype));
   L.off[13] = o;  // tiles
   o = align256(o + (size_t)nt * sizeof(Tile));
-  L.off[14] = o;  // q0, s_helix, seed
-  o = align256(o + 3 * 8);
+  L.off[14] = o;  // q0, s_helix, seed, error flag
+  o = align256(o + 64);
   L.off[15] = o;  // partials + out
   o = align256(o + (kDiagPartials + 8) * 8);
   L.total = o;
@@ -211,7 +220,10 @@ int check_dims(int nx, int ny, int nz) {
   return LCBP_OK;
 }
 
+void drop_graph(lcbp_lattice* h);
+
 int upload_replica(lcbp_lattice* h) {
+  drop_graph(h);  // the fast path takes the model coefficients as kernel arguments
   std::vector<char> buf(replica_bytes(h->dtype));
   if (h->dtype == LCBP_F64) fill_replica<double>(buf.data(), h->nx, h->ny, h->nz, 0, h->p);
   else fill_replica<float>(buf.data(), h->nx, h->ny, h->nz, 0, h->p);
@@ -243,6 +255,7 @@ int finish_create(lcbp_lattice* h) {
   h->d_q0 = reinterpret_cast<double*>(w + L.off[14]);
   h->d_shelix = h->d_q0 + 1;
   h->d_seed = reinterpret_cast<uint64_t*>(h->d_q0 + 2);
+  h->d_err = reinterpret_cast<int*>(h->d_q0 + 3);
   h->d_partials = reinterpret_cast<double*>(w + L.off[15]);
   h->d_out = h->d_partials + kDiagPartials;
   h->ts = default_tile(h->nx, h->ny, h->nz);
@@ -250,6 +263,7 @@ int finish_create(lcbp_lattice* h) {
   append_tiles(tiles, 0, h->nx, h->ny, h->nz, h->ts);
   h->ntiles = (int)tiles.size();
   cudaError_t e = cudaMemsetAsync(h->ws, 0, L.off[11], h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(w + L.off[14], 0, 64, h->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(h->d_tiles, tiles.data(), tiles.size() * sizeof(Tile), cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess) e = cudaMallocHost(&h->h_out, 8 * sizeof(double));
@@ -284,6 +298,202 @@ lcbp_lattice* new_handle(int nx, int ny, int nz, int dtype) {
   return h;
 }
 
+// ---- fast path: tensor maps, eligibility, autotuned z-chunk -------------------
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  });
+  return fn;
+}
+
+// field [comps][nz][ny][nx] as a 4-D tensor, box = 40 x rows x 1 x comps
+bool make_field_tmap(CUtensorMap* tm, void* base, int comps, int nx, int ny, int nz, int rows, int dtype) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return false;
+  const cuuint64_t es = dtype_size(dtype);
+  const cuuint64_t dims[4] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz, (cuuint64_t)comps};
+  const cuuint64_t strides[3] = {nx * es, (cuuint64_t)nx * ny * es, (cuuint64_t)nx * ny * nz * es};
+  const cuuint32_t box[4] = {(cuuint32_t)kZmBoxX, (cuuint32_t)rows, 1, (cuuint32_t)comps};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  return fn(tm, dtype == LCBP_F64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base,
+            dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+bool fast_shape_ok(const lcbp_lattice* h) { return h->nx % 4 == 0; }
+
+bool use_fast(lcbp_lattice* h) {
+  if (h->path_req == LCBP_PATH_GENERIC || !h->p.flow_on || h->p.coupling != LCBP_JACOBI || !fast_shape_ok(h))
+    return false;
+  if (!h->tmaps_ok) {
+    static std::once_flag prep32, prep64;
+    if (h->dtype == LCBP_F64) std::call_once(prep64, [] { zm_prepare<double>(); });
+    else std::call_once(prep32, [] { zm_prepare<float>(); });
+    const int ty = h->dtype == LCBP_F64 ? zm_tile_rows<double>() : zm_tile_rows<float>();
+    bool ok = make_field_tmap(&h->tm[0], h->q, 5, h->nx, h->ny, h->nz, ty + 4, h->dtype);
+    ok = ok && make_field_tmap(&h->tm[1], h->rhou[0], 4, h->nx, h->ny, h->nz, ty + 2, h->dtype);
+    ok = ok && make_field_tmap(&h->tm[2], h->rhou[1], 4, h->nx, h->ny, h->nz, ty + 2, h->dtype);
+    ok = ok && make_field_tmap(&h->tm[3], h->sig, 5, h->nx, h->ny, h->nz, ty + 2, h->dtype);
+    ok = ok && make_field_tmap(&h->tm[4], h->b, 3, h->nx, h->ny, h->nz, ty + 2, h->dtype);
+    ok = ok && make_field_tmap(&h->tm[5], h->qs, 5, h->nx, h->ny, h->nz, ty + 2, h->dtype);
+    if (!ok) {
+      h->path_req = LCBP_PATH_GENERIC;  // tensor maps unavailable: stay on the generic kernels
+      return false;
+    }
+    h->tmaps_ok = true;
+  }
+  return true;
+}
+
+ZmArgs zm_args(lcbp_lattice* h, const void* model) {
+  ZmArgs a{};
+  a.nx = h->nx;
+  a.ny = h->ny;
+  a.nz = h->nz;
+  a.zc = h->zc > 0 ? h->zc : std::min(h->nz, 32);
+  a.model = model;
+  a.tm_q = &h->tm[0];
+  a.tm_u = &h->tm[1 + h->cur];
+  a.tm_sigma = &h->tm[3];
+  a.tm_b = &h->tm[4];
+  a.tm_qs = &h->tm[5];
+  a.q = h->q;
+  a.qout = nullptr;
+  a.qs = h->qs;
+  a.sigma = h->sig;
+  a.b = h->b;
+  a.bext = h->has_bext ? h->bext : nullptr;
+  a.f = h->f[h->cur];
+  a.fnew = h->f[h->cur ^ 1];
+  a.rhou = h->rhou[h->cur];
+  a.rhou_new = h->rhou[h->cur ^ 1];
+  a.err = h->d_err;
+  a.events = nullptr;
+  return a;
+}
+
+struct ModelBuf {
+  alignas(16) char bytes[sizeof(Model<double>)];
+};
+
+ModelBuf host_model(const lcbp_lattice* h) {
+  ModelBuf mb{};
+  if (h->dtype == LCBP_F64) {
+    const Model<double> m = make_model<double>(h->p);
+    std::memcpy(mb.bytes, &m, sizeof(m));
+  } else {
+    const Model<float> m = make_model<float>(h->p);
+    std::memcpy(mb.bytes, &m, sizeof(m));
+  }
+  return mb;
+}
+
+cudaError_t launch_zm(lcbp_lattice* h, const ZmArgs& a) {
+  return h->dtype == LCBP_F64 ? launch_step_zm<double>(a, h->stream) : launch_step_zm<float>(a, h->stream);
+}
+
+// planes per CTA, chosen by timing each candidate once per lattice shape and
+// dtype; the runs write only scratch buffers (Q* to the H scratch), so the
+// state is untouched.  Results are kept per process and, if the environment
+// variable LCBP_AUTOTUNE_CACHE names a file, in that file ("nx ny nz dtype zc").
+std::mutex g_tune_mu;
+std::map<std::string, int> g_tune;
+bool g_tune_loaded = false;
+
+std::string tune_key(const lcbp_lattice* h) {
+  char k[64];
+  snprintf(k, sizeof(k), "%d %d %d %d", h->nx, h->ny, h->nz, h->dtype);
+  return k;
+}
+
+int tune_zc(lcbp_lattice* h) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  const char* path = std::getenv("LCBP_AUTOTUNE_CACHE");
+  if (path && !g_tune_loaded) {
+    g_tune_loaded = true;
+    if (FILE* fp = std::fopen(path, "r")) {
+      int a, b, c, d, z;
+      while (std::fscanf(fp, "%d %d %d %d %d", &a, &b, &c, &d, &z) == 5) {
+        char k[64];
+        snprintf(k, sizeof(k), "%d %d %d %d", a, b, c, d);
+        g_tune[k] = z;
+      }
+      std::fclose(fp);
+    }
+  }
+  const std::string key = tune_key(h);
+  auto it = g_tune.find(key);
+  if (it != g_tune.end()) {
+    h->zc = it->second;
+    return LCBP_OK;
+  }
+  const ModelBuf mb = host_model(h);
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    return fail(LCBP_ECUDA, "event create");
+  float best = 1e30f;
+  int best_zc = std::min(h->nz, 32);
+  for (int zc : {4, 8, 16, 32, 64}) {
+    if (zc > h->nz && zc != 4) break;
+    ZmArgs a = zm_args(h, mb.bytes);
+    a.zc = std::min(zc, h->nz);
+    a.qout = h->h;  // scratch
+    float t = 1e30f;
+    for (int rep = 0; rep < 3; ++rep) {
+      cudaEventRecord(e0, h->stream);
+      cudaError_t e = launch_zm(h, a);
+      cudaEventRecord(e1, h->stream);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      if (e != cudaSuccess) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return cuda_fail(e, "autotune");
+      }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      t = std::min(t, ms);
+    }
+    if (t < best) {
+      best = t;
+      best_zc = a.zc;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  h->zc = best_zc;
+  g_tune[key] = best_zc;
+  if (path) {
+    if (FILE* fp = std::fopen(path, "a")) {
+      std::fprintf(fp, "%s %d\n", key.c_str(), best_zc);
+      std::fclose(fp);
+    }
+  }
+  return LCBP_OK;
+}
+
+int check_device_error(lcbp_lattice* h) {
+  int flag = 0;
+  cudaError_t e = cudaMemcpyAsync(&flag, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "error flag");
+  if (flag) {
+    cudaMemsetAsync(h->d_err, 0, sizeof(int), h->stream);
+    return fail(LCBP_ETIMEOUT, "a bounded device-side wait timed out; the step's results are not valid");
+  }
+  return LCBP_OK;
+}
+
 StepArgs step_args(lcbp_lattice* h) {
   StepArgs a{};
   a.reps = h->d_rep;
@@ -308,8 +518,14 @@ StepArgs step_args(lcbp_lattice* h) {
 }
 
 cudaError_t eager_step(lcbp_lattice* h) {
-  const StepArgs a = step_args(h);
-  const cudaError_t e = h->dtype == LCBP_F64 ? launch_step<double>(a, h->stream) : launch_step<float>(a, h->stream);
+  cudaError_t e;
+  if (use_fast(h)) {
+    const ModelBuf mb = host_model(h);
+    e = launch_zm(h, zm_args(h, mb.bytes));
+  } else {
+    const StepArgs a = step_args(h);
+    e = h->dtype == LCBP_F64 ? launch_step<double>(a, h->stream) : launch_step<float>(a, h->stream);
+  }
   if (h->p.flow_on) h->cur ^= 1;
   return e;
 }
@@ -352,6 +568,8 @@ int diag(lcbp_lattice* h, double threshold, int with_f) {
   if (e == cudaSuccess) e = cudaMemcpyAsync(h->h_out, h->d_out, 8 * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return cuda_fail(e, "diagnostics");
+  int rc = check_device_error(h);
+  if (rc) return rc;
   if (h->h_out[6] != 0.0) return fail(LCBP_ENONFINITE, "%.0f sites hold NaN or Inf", h->h_out[6]);
   return LCBP_OK;
 }
@@ -610,6 +828,10 @@ int lcbp_step(lcbp_lattice* h, int nsteps) {
   if (nsteps < 0) return fail(LCBP_EINVAL, "nsteps < 0");
   if (h->p.flow_on && !h->f_ready) return fail(LCBP_ESTATE, "initialise f before stepping with flow on");
   if (nsteps == 0) return LCBP_OK;
+  if (use_fast(h) && h->zc == 0) {
+    int rc = tune_zc(h);
+    if (rc) return rc;
+  }
   cudaError_t e = cudaSuccess;
   int left = nsteps;
   if (h->cur == 1) {
@@ -639,7 +861,12 @@ int lcbp_profile_steps(lcbp_lattice* h, int nsteps, double* kernel_ms, int capac
   CHECK_H(h);
   if (nsteps < 1 || !kernel_ms || !nkernels) return fail(LCBP_EINVAL, "need nsteps >= 1 and output arrays");
   if (h->p.flow_on && !h->f_ready) return fail(LCBP_ESTATE, "initialise f before stepping with flow on");
-  const int nk = kernels_per_step(h->p.flow_on, h->p.coupling);
+  const bool fast = use_fast(h);
+  if (fast && h->zc == 0) {
+    int rc = tune_zc(h);
+    if (rc) return rc;
+  }
+  const int nk = fast ? 2 : kernels_per_step(h->p.flow_on, h->p.coupling);
   *nkernels = nk;
   if (capacity < nk) return fail(LCBP_EINVAL, "kernel_ms holds %d values, need %d", capacity, nk);
   std::vector<cudaEvent_t> ev((size_t)nsteps * (nk + 1));
@@ -647,9 +874,16 @@ int lcbp_profile_steps(lcbp_lattice* h, int nsteps, double* kernel_ms, int capac
   for (auto& x : ev)
     if (e == cudaSuccess) e = cudaEventCreate(&x);
   for (int s = 0; s < nsteps && e == cudaSuccess; ++s) {
-    StepArgs a = step_args(h);
-    a.events = ev.data() + (size_t)s * (nk + 1);
-    e = h->dtype == LCBP_F64 ? launch_step<double>(a, h->stream) : launch_step<float>(a, h->stream);
+    if (fast) {
+      const ModelBuf mb = host_model(h);
+      ZmArgs a = zm_args(h, mb.bytes);
+      a.events = ev.data() + (size_t)s * (nk + 1);
+      e = launch_zm(h, a);
+    } else {
+      StepArgs a = step_args(h);
+      a.events = ev.data() + (size_t)s * (nk + 1);
+      e = h->dtype == LCBP_F64 ? launch_step<double>(a, h->stream) : launch_step<float>(a, h->stream);
+    }
     if (h->p.flow_on) h->cur ^= 1;
     h->step += 1;
   }
@@ -663,13 +897,31 @@ int lcbp_profile_steps(lcbp_lattice* h, int nsteps, double* kernel_ms, int capac
     }
   for (auto& x : ev)
     if (x) cudaEventDestroy(x);
-  return e == cudaSuccess ? LCBP_OK : cuda_fail(e, "profile_steps");
+  if (e != cudaSuccess) return cuda_fail(e, "profile_steps");
+  return check_device_error(h);
+}
+
+int lcbp_set_path(lcbp_lattice* h, int path) {
+  CHECK_H(h);
+  if (path != LCBP_PATH_AUTO && path != LCBP_PATH_GENERIC) return fail(LCBP_EINVAL, "unknown path %d", path);
+  drop_graph(h);
+  h->path_req = path;
+  return LCBP_OK;
+}
+
+int lcbp_get_path(lcbp_lattice* h, int* fast, int* planes_per_cta) {
+  CHECK_H(h);
+  const bool f = use_fast(h);
+  if (fast) *fast = f ? 1 : 0;
+  if (planes_per_cta) *planes_per_cta = f ? h->zc : 0;
+  return LCBP_OK;
 }
 
 int lcbp_synchronize(lcbp_lattice* h) {
   CHECK_H(h);
   cudaError_t e = cudaStreamSynchronize(h->stream);
-  return e == cudaSuccess ? LCBP_OK : cuda_fail(e, "cudaStreamSynchronize");
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+  return check_device_error(h);
 }
 
 int lcbp_read_q(lcbp_lattice* h, void* dst, int dtype) {

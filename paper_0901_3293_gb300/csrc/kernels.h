@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "common.cuh"
@@ -81,5 +82,35 @@ template <typename real>
 cudaError_t launch_diag_one(const DiagGeom& g, const void* q, const void* f, int with_f, double threshold,
                             double* partials, double* out, cudaStream_t s);
 constexpr int kDiagPartials = 512 * 8;
+
+// ---------------------------------------------------------------------------
+// Fast path (flow on, Jacobi coupling, nx % 4 == 0): two z-marching kernels
+// with TMA-staged planes.  Tensor maps describe one field as a 4-D tensor
+// (x, y, z, component) and are built by the host (make_field_tmap).
+// ---------------------------------------------------------------------------
+struct ZmGeom {
+  int nx, ny, nz, zc;
+  long long n;
+  int tiles_x, tiles_y, tiles_z;
+};
+
+struct ZmArgs {
+  int nx, ny, nz, zc;
+  const void* model;  // host copy of Model<real>
+  const CUtensorMap *tm_q, *tm_u, *tm_sigma, *tm_b, *tm_qs;
+  void *q, *qout, *qs, *sigma, *b;  // qout: nullptr = update Q in place
+  const void* bext;
+  void *f, *fnew, *rhou, *rhou_new;
+  int* err;              // set to 1 if a bounded barrier wait timed out
+  cudaEvent_t* events;   // optional: 3 events around the two kernels
+};
+
+constexpr int kZmBoxX = 40;  // elements per TMA box row
+template <typename real>
+int zm_tile_rows();
+template <typename real>
+cudaError_t zm_prepare();
+template <typename real>
+cudaError_t launch_step_zm(const ZmArgs& a, cudaStream_t s);
 
 }  // namespace lcbp

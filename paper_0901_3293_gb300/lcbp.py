@@ -25,6 +25,7 @@ OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, ETIMEOUT, ESTATE, EIO = 0, -1, -2, -3, -4
 F32, F64 = 0, 1
 BPII, CHOL_X, CHOL_Y, CHOL_Z, ISO_NOISE, SLAB_BPII_IN_CHOL = range(6)
 JACOBI, GAUSS_SEIDEL = 0, 1
+PATH_AUTO, PATH_GENERIC = 0, 1
 
 _lib = None
 
@@ -52,6 +53,8 @@ _SIGNATURES = {
     "lcbp_set_body_force": (_c_int, [_P, _c_void_p, _c_int]),
     "lcbp_step": (_c_int, [_P, _c_int]),
     "lcbp_synchronize": (_c_int, [_P]),
+    "lcbp_set_path": (_c_int, [_P, _c_int]),
+    "lcbp_get_path": (_c_int, [_P, ctypes.POINTER(_c_int), ctypes.POINTER(_c_int)]),
     "lcbp_profile_steps": (_c_int, [_P, _c_int, ctypes.POINTER(_c_double), _c_int, ctypes.POINTER(_c_int)]),
     "lcbp_read_q": (_c_int, [_P, _c_void_p, _c_int]),
     "lcbp_read_u": (_c_int, [_P, _c_void_p, _c_int]),
@@ -233,6 +236,17 @@ class Lattice:
         nk = _c_int()
         check(lib().lcbp_profile_steps(self._h, int(nsteps), ms, 8, ctypes.byref(nk)))
         return list(ms[:nk.value])
+
+    def set_path(self, path: int) -> "Lattice":
+        check(lib().lcbp_set_path(self._h, path))
+        return self
+
+    def path(self):
+        """(fast path in use, autotuned planes per CTA)."""
+        fast = _c_int()
+        zc = _c_int()
+        check(lib().lcbp_get_path(self._h, ctypes.byref(fast), ctypes.byref(zc)))
+        return bool(fast.value), zc.value
 
     def synchronize(self) -> None:
         check(lib().lcbp_synchronize(self._h))

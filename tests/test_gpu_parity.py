@@ -57,16 +57,23 @@ def test_init_q_matches_oracle(lcbp, kind, dtype, tol):
 
 
 # ---------------------------------------------------------------------------
-SHAPES = [(5, 6, 7), (4, 4, 4), (64, 1, 1), (3, 5, 33), (1, 9, 2)]
+# (nz, ny, nx): odd and ragged sizes; nx % 4 == 0 selects the fast z-marching
+# TMA kernels (tiles of 32 x TY columns; 36 = one full tile + a ragged tail)
+SHAPES = [(5, 6, 7), (4, 4, 4), (64, 1, 1), (3, 5, 33), (1, 9, 2), (5, 6, 8), (3, 9, 36), (7, 3, 12),
+          (2, 1, 4), (9, 17, 64)]
 
 
+@pytest.mark.parametrize("path", ["auto", "generic"])
 @pytest.mark.parametrize("shape", SHAPES)
-def test_one_coupled_step_f64(lcbp, shape):
+def test_one_coupled_step_f64(lcbp, shape, path):
     p = lbq.Params()
     q5 = synth.smooth_q5(shape, 0.3, 1) + synth.random_q5(shape, 1e-2, 2)
     f15 = synth.random_distributions(shape, 3, amp=2e-3)
     lat = make(lcbp, shape, "f64", p)
+    if path == "generic":
+        lat.set_path(lcbp.PATH_GENERIC)
     lat.set_q(q5).set_f(f15).step(1)
+    assert lat.path()[0] == (path == "auto" and shape[2] % 4 == 0)
     f, Q = lbq.step(lbq.f_from_soa(f15), lbq.q5_to_q9(q5), p)
     assert np.abs(lat.read_q() - lbq.q9_to_q5(Q)).max() < 1e-14
     assert np.abs(lat.read_f() - lbq.f_to_soa(f)).max() < 1e-14
@@ -153,6 +160,35 @@ def test_external_force_kolmogorov(lcbp, dtype, tol):
     f, _ = lbq.run(f, np.zeros(shape + (3, 3)), p, 200, b_ext=np.moveaxis(b, 0, -1))
     assert np.abs(lat.read_u() - oracle_u(f)).max() < tol
     assert np.abs(lat.read_u()).max() > 1e-5
+
+
+@pytest.mark.parametrize("shape", [(32, 32, 32), (6, 10, 36), (64, 64, 64)])
+def test_fast_path_matches_generic_f32(lcbp, shape):
+    """Both kernel sets compute the same FP32 step (op order differs slightly)."""
+    p = lbq.Params()
+    a = make(lcbp, shape, "f32", p)
+    b = make(lcbp, shape, "f32", p)
+    b.set_path(lcbp.PATH_GENERIC)
+    for lat in (a, b):
+        lat.init_q(lcbp.BPII, 0.3, noise=1e-3, seed=4).init_f_equilibrium(1.0).step(20)
+    assert a.path()[0] and not b.path()[0] and a.path()[1] >= 1
+    assert np.abs(a.read_q() - b.read_q()).max() < 1e-6
+    assert np.abs(a.read_u() - b.read_u()).max() < 1e-8
+    assert np.abs(a.read_f() - b.read_f()).max() < 1e-8
+
+
+def test_fast_path_external_force_f64(lcbp):
+    p = lbq.Params(xi=0.0)
+    shape = (32, 2, 4)
+    z = np.arange(32)[:, None, None] * np.ones(shape)
+    b = np.zeros((3,) + shape)
+    b[0] = 1e-5 * np.sin(2 * np.pi * z / 32)
+    lat = make(lcbp, shape, "f64", p)
+    lat.set_q(np.zeros((5,) + shape)).init_f_equilibrium(1.0).set_body_force(b).step(100)
+    assert lat.path()[0]
+    f = lbq.equilibrium(np.ones(shape), np.zeros(shape + (3,)), np.zeros(shape + (3, 3)))
+    f, _ = lbq.run(f, np.zeros(shape + (3, 3)), p, 100, b_ext=np.moveaxis(b, 0, -1))
+    assert np.abs(lat.read_u() - oracle_u(f)).max() < 1e-14
 
 
 def test_graph_replay_equals_eager_steps(lcbp):
