@@ -31,14 +31,19 @@ N_SIDE = 256
 Q0 = 2 * np.pi / 32
 PARAMS = dict(A0=0.01, gamma=3.1, K=0.01, q0=Q0, Gamma=0.3, xi=0.7, tau_f=2.0)
 SEED = 20090119
-# algorithmic FP32 bytes per site of each kernel of the Jacobi flow-on step:
-# each value the kernel must read or write once (inputs + outputs)
+# algorithmic FP32 bytes per site of each kernel: each value the kernel must
+# read or write once (inputs + outputs)
 KERNEL_BYTES = {
-    "field": (5 + 5 + 5 + 3) * 4,                       # Q -> H, sigma, tau
-    "force_predict": (5 + 5 + 3 + 4 + 3 + 5) * 4,       # Q, H, tau, rho u -> b, Q*
-    "lb_correct": (15 + 4 + 5 + 3 + 5 + 5 + 15 + 4 + 5) * 4,  # f, rho u, sigma, b, Q*, Q -> f, rho u, Q
+    # fast path (z-marching, TMA-staged planes)
+    "qside": (5 + 4 + 5 + 3 + 5) * 4,                          # Q, rho u -> sigma, b, Q*
+    "lbq": (15 + 4 + 5 + 3 + 5 + 5 + 15 + 4 + 5) * 4,          # f, rho u, sigma, b, Q*, Q -> f, rho u, Q
+    # generic path
+    "field": (5 + 5 + 5 + 3) * 4,                              # Q -> H, sigma, tau
+    "force_predict": (5 + 5 + 3 + 4 + 3 + 5) * 4,              # Q, H, tau, rho u -> b, Q*
+    "lb_correct": (15 + 4 + 5 + 3 + 5 + 5 + 15 + 4 + 5) * 4,   # f, rho u, sigma, b, Q*, Q -> f, rho u, Q
 }
-KERNELS = ["field", "force_predict", "lb_correct"]
+KERNELS_FAST = ["qside", "lbq"]
+KERNELS_GENERIC = ["field", "force_predict", "lb_correct"]
 STATE_BYTES = (15 + 5) * 2 * 4  # read + write of f and Q once per site-step (FP32)
 ORACLE_SAMPLE = 32  # side of the periodic cube the oracle steps (two BPII unit cells)
 
@@ -221,9 +226,10 @@ def run_ours(args):
 
     # ---- per-kernel device times, kernel by kernel with events (same kernels)
     kms = lat.profile_steps(max(3, min(args.steps, 10)))
+    fast, zc = lat.path()
     peak, peak_kind = measured_peaks()
     per_kernel = {}
-    for name, t in zip(KERNELS, kms):
+    for name, t in zip(KERNELS_FAST if fast else KERNELS_GENERIC, kms):
         gbs = KERNEL_BYTES[name] * sites / (t * 1e-3) / 1e9
         per_kernel[name] = {"ms": t, "algorithmic_bytes_per_site": KERNEL_BYTES[name], "GBps": gbs,
                             "frac_of_" + peak_kind: gbs / peak}
@@ -256,7 +262,7 @@ def run_ours(args):
            "h2d_bytes_per_step": (15 + 5) * 4 * sites, "d2h_bytes_per_step": (5 + 3) * 4 * sites,
            "steps": k_e2e, "note": "lcbp_set_f + lcbp_set_q from pinned host memory, lcbp_step(1), "
                                    "lcbp_read_q + lcbp_read_u to pinned host memory"}
-    launches = 3 * args.steps
+    launches = (2 if fast else 3) * args.steps
     lat.close()
 
     # ---- the 64x64x256 thin slab (BPII seed for z < 32 inside an x-helix)
@@ -290,7 +296,9 @@ def run_ours(args):
         "config": {"workload": "256^3 periodic BPII (pitch 32), coupled D3Q15 LB + Beris-Edwards, FP32 state",
                    "sites_per_gpu": sites, "A0": PARAMS["A0"], "gamma": PARAMS["gamma"], "K": PARAMS["K"],
                    "q0": PARAMS["q0"], "tau_f": PARAMS["tau_f"], "l2": "state 4.5 GB >> 129 MB L2, no flush",
-                   "parallelism": f"{world} independent replicas" if world > 1 else "single lattice"},
+                   "parallelism": f"{world} independent replicas" if world > 1 else "single lattice",
+                   "kernels": "fast (z-marching, TMA-staged planes)" if fast else "generic",
+                   "planes_per_cta": zc},
         "roofline": roof, "per_kernel": per_kernel, "cpu_baseline": cpu, "e2e": e2e,
         "gpu_launches": launches, "clocks": clk, "free_energy_after": F,
         "slab_64x64x256": slab_line,
