@@ -269,6 +269,53 @@ LCBP_API int lcbp_defect_fraction(lcbp_lattice *h, double threshold, double *fra
 LCBP_API int lcbp_save(lcbp_lattice *h, const char *path);
 LCBP_API int lcbp_load(lcbp_lattice *h, const char *path);
 
+/* ------------------------------------------------------------------------
+ * Batched replicas (parameter sweeps): R independent periodic lattices of
+ * uneven sizes, each with its own Landau-de Gennes and kinetic parameters,
+ * advanced together.  Their fields are concatenated structure-of-arrays
+ * blocks on one device; every kernel of a step is one launch of persistent
+ * CTAs walking a single tile work-list that spans all replicas, and nsteps
+ * are replayed from a captured CUDA graph.  The tile shape is picked by
+ * timing candidate shapes on the batch (first lcbp_batch_step), writing
+ * scratch buffers only.  Each replica computes exactly what a lattice of its
+ * own (generic path) computes.
+ * ------------------------------------------------------------------------ */
+typedef struct lcbp_batch lcbp_batch;
+
+/* Per-replica parameters (meanings as in lcbp_set_ldg / lcbp_set_flow). */
+typedef struct lcbp_params {
+  double A0, gamma, K, q0; /* Sec. 2.1 Eq. (free_energy) */
+  double tau_f, xi, Gamma; /* Sec. 2.1, 2.2 kinetics */
+} lcbp_params;
+
+/*
+ * dims: 3 * R ints (nx, ny, nz of replica r, each >= 1); params: R entries.
+ * Flow on, Jacobi coupling; Q = 0, f unset.  Errors: LCBP_EINVAL, LCBP_ENOMEM.
+ */
+LCBP_API int lcbp_batch_create(int R, const int *dims, const lcbp_params *params, int state_dtype, lcbp_batch **out);
+LCBP_API int lcbp_batch_destroy(lcbp_batch *b);
+/* flow_on / coupling for all replicas (as lcbp_set_flow). */
+LCBP_API int lcbp_batch_set_flow(lcbp_batch *b, int flow_on, int coupling);
+/* Initial Q of replica r (as lcbp_init_q; the slab helix uses replica r's gamma). */
+LCBP_API int lcbp_batch_init_q(lcbp_batch *b, int r, int kind, double amplitude, double noise, uint64_t seed,
+                               const int *region);
+/* Upload Q of replica r (5 * n_r values, boundary layout). */
+LCBP_API int lcbp_batch_set_q(lcbp_batch *b, int r, const void *q5, int dtype);
+/* f = f^eq(rho0, u = 0, sigma_LC(Q)) in every replica. */
+LCBP_API int lcbp_batch_init_f_equilibrium(lcbp_batch *b, double rho0);
+/* Advance every replica by nsteps (enqueued; graph replay). */
+LCBP_API int lcbp_batch_step(lcbp_batch *b, int nsteps);
+LCBP_API int lcbp_batch_synchronize(lcbp_batch *b);
+/* Per-replica reads and FP64 diagnostics (as the lattice versions). */
+LCBP_API int lcbp_batch_read_q(lcbp_batch *b, int r, void *dst, int dtype);
+LCBP_API int lcbp_batch_read_u(lcbp_batch *b, int r, void *dst, int dtype);
+LCBP_API int lcbp_batch_free_energy(lcbp_batch *b, int r, double *F);
+LCBP_API int lcbp_batch_totals(lcbp_batch *b, int r, double *mass, double momentum[3]);
+LCBP_API int lcbp_batch_defect_fraction(lcbp_batch *b, int r, double threshold, double *fraction);
+/* R, total sites, tuned tile shape (tx, ty, tz), persistent CTAs per launch, steps done. */
+LCBP_API int lcbp_batch_get_info(lcbp_batch *b, int *R, long long *total_sites, int tile[3], int *persistent_ctas,
+                                 long long *step);
+
 #ifdef __cplusplus
 }
 #endif

@@ -513,6 +513,8 @@ StepArgs step_args(lcbp_lattice* h) {
   a.fnew = h->f[h->cur ^ 1];
   a.rhou = h->rhou[h->cur];
   a.rhou_new = h->rhou[h->cur ^ 1];
+  a.qout = nullptr;
+  a.max_grid = 0;
   a.events = nullptr;
   return a;
 }

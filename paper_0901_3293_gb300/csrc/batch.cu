@@ -1,0 +1,537 @@
+// Batched replicas: R lattices of uneven sizes and per-replica parameters
+// stepped together.  Fields are concatenated structure-of-arrays blocks
+// (replica r of a C-component field at field + C * base_r, laid out
+// [c][z][y][x]); one tile work-list spans every replica, so each kernel of a
+// step is a single launch of persistent CTAs over all replicas, and nsteps
+// are replayed from a captured CUDA graph.  The tile shape is chosen by
+// timing candidate shapes on the batch itself (scratch outputs only).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "../../include/lcbp.h"
+#include "common.cuh"
+#include "kernels.h"
+#include "runtime.h"
+
+using namespace lcbp;
+
+struct lcbp_batch {
+  int R;
+  int dtype;
+  size_t es;
+  int device;
+  std::vector<int> nx, ny, nz;
+  std::vector<long long> n, base;
+  long long ntot;
+  std::vector<HostParams> p;
+  int flow_on, coupling;
+  cudaStream_t stream;
+  char* ws;
+  void *f[2], *rhou[2], *q, *qs, *h, *sig, *tau, *b, *staging;
+  long long staging_elems;
+  void* d_rep;
+  Tile* d_tiles;
+  long long tile_cap;
+  int ntiles;
+  std::vector<int> tile_begin;  // per replica, + end
+  TileShape ts;
+  bool tuned;
+  int max_grid;
+  double *d_q0, *d_shelix, *d_partials, *d_out, *h_out;
+  uint64_t* d_seed;
+  int cur;
+  bool f_ready;
+  cudaGraphExec_t graph;
+  bool graph_ok;
+  long long step;
+};
+
+namespace {
+
+size_t a256(size_t x) { return (x + 255) & ~size_t(255); }
+constexpr long long kStaging = 1ll << 22;
+
+const TileShape kCandidates[] = {{32, 4, 1}, {32, 2, 2}, {16, 8, 1}, {16, 4, 2}, {32, 8, 1}, {8, 8, 2}, {32, 1, 4}};
+
+int check_b(lcbp_batch* b) {
+  if (!b) return fail(LCBP_EINVAL, "null batch handle");
+  cudaSetDevice(b->device);
+  return LCBP_OK;
+}
+
+int check_r(lcbp_batch* b, int r) {
+  if (r < 0 || r >= b->R) return fail(LCBP_EINVAL, "replica %d out of range [0, %d)", r, b->R);
+  return LCBP_OK;
+}
+
+void drop_graph(lcbp_batch* b) {
+  if (b->graph_ok) cudaGraphExecDestroy(b->graph);
+  b->graph_ok = false;
+}
+
+int build_tiles(lcbp_batch* b, TileShape ts) {
+  std::vector<Tile> tiles;
+  b->tile_begin.assign(b->R + 1, 0);
+  for (int r = 0; r < b->R; ++r) {
+    b->tile_begin[r] = (int)tiles.size();
+    // every replica uses the same shape: the kernels map threads by it
+    append_tiles(tiles, r, b->nx[r], b->ny[r], b->nz[r], ts);
+  }
+  b->tile_begin[b->R] = (int)tiles.size();
+  if ((long long)tiles.size() > b->tile_cap) return fail(LCBP_ENOMEM, "tile list overflow");
+  b->ntiles = (int)tiles.size();
+  b->ts = ts;
+  cudaError_t e = cudaMemcpyAsync(b->d_tiles, tiles.data(), tiles.size() * sizeof(Tile), cudaMemcpyHostToDevice,
+                                  b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  return e == cudaSuccess ? LCBP_OK : cuda_fail(e, "tile upload");
+}
+
+int upload_table(lcbp_batch* b) {
+  drop_graph(b);
+  const size_t rb = replica_bytes(b->dtype);
+  std::vector<char> buf(rb * b->R);
+  std::vector<double> aux(2 * b->R);
+  for (int r = 0; r < b->R; ++r) {
+    if (b->dtype == LCBP_F64)
+      fill_replica<double>(buf.data() + rb * r, b->nx[r], b->ny[r], b->nz[r], b->base[r], b->p[r]);
+    else
+      fill_replica<float>(buf.data() + rb * r, b->nx[r], b->ny[r], b->nz[r], b->base[r], b->p[r]);
+    aux[r] = b->p[r].q0;
+    aux[b->R + r] = s_eq(b->p[r].gamma);
+  }
+  cudaError_t e = cudaMemcpyAsync(b->d_rep, buf.data(), buf.size(), cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_q0, aux.data(), b->R * 8, cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->d_shelix, aux.data() + b->R, b->R * 8, cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  return e == cudaSuccess ? LCBP_OK : cuda_fail(e, "replica table upload");
+}
+
+StepArgs args(lcbp_batch* b) {
+  StepArgs a{};
+  a.reps = b->d_rep;
+  a.tiles = b->d_tiles;
+  a.ntiles = b->ntiles;
+  a.ts = b->ts;
+  a.flow_on = b->flow_on;
+  a.coupling = b->coupling;
+  a.q = b->q;
+  a.qs = b->qs;
+  a.h = b->h;
+  a.sigma = b->sig;
+  a.tau = b->tau;
+  a.b = b->b;
+  a.bext = nullptr;
+  a.f = b->f[b->cur];
+  a.fnew = b->f[b->cur ^ 1];
+  a.rhou = b->rhou[b->cur];
+  a.rhou_new = b->rhou[b->cur ^ 1];
+  a.qout = nullptr;
+  a.max_grid = b->max_grid;
+  a.events = nullptr;
+  return a;
+}
+
+cudaError_t launch(lcbp_batch* b, const StepArgs& a) {
+  return b->dtype == LCBP_F64 ? launch_step<double>(a, b->stream) : launch_step<float>(a, b->stream);
+}
+
+cudaError_t eager(lcbp_batch* b) {
+  const cudaError_t e = launch(b, args(b));
+  if (b->flow_on) b->cur ^= 1;
+  return e;
+}
+
+// persistent grid: as many CTAs as can be resident at once
+int resident_ctas(lcbp_batch* b) {
+  int sms = 0, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int threads = b->ts.tx * b->ts.ty * b->ts.tz;
+  // 128-register kernels: at most 65536 / (threads * 128) CTAs per SM
+  const int per_sm = std::max(1, 65536 / (threads * 128));
+  return std::max(1, sms * per_sm);
+}
+
+int tune(lcbp_batch* b) {
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return fail(LCBP_ECUDA, "events");
+  float best = 1e30f;
+  TileShape best_ts = kCandidates[0];
+  for (const TileShape& c : kCandidates) {
+    int rc = build_tiles(b, c);
+    if (rc) return rc;
+    b->max_grid = resident_ctas(b);
+    StepArgs a = args(b);
+    a.qout = b->h;  // scratch: the state is left untouched
+    float t = 1e30f;
+    for (int rep = 0; rep < 3; ++rep) {
+      cudaEventRecord(e0, b->stream);
+      cudaError_t e = launch(b, a);
+      cudaEventRecord(e1, b->stream);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      if (e != cudaSuccess) return cuda_fail(e, "tile tuning");
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      t = std::min(t, ms);
+    }
+    if (t < best) {
+      best = t;
+      best_ts = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  int rc = build_tiles(b, best_ts);
+  if (rc) return rc;
+  b->max_grid = resident_ctas(b);
+  b->tuned = true;
+  return LCBP_OK;
+}
+
+int build_graph(lcbp_batch* b) {
+  cudaGraph_t g;
+  cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return cuda_fail(e, "capture");
+  const int saved = b->cur;
+  b->cur = 0;
+  cudaError_t e1 = eager(b);
+  cudaError_t e2 = eager(b);
+  b->cur = saved;
+  e = cudaStreamEndCapture(b->stream, &g);
+  if (e1 != cudaSuccess) e = e1;
+  if (e2 != cudaSuccess) e = e2;
+  if (e != cudaSuccess) return cuda_fail(e, "capture");
+  e = cudaGraphInstantiate(&b->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return cuda_fail(e, "instantiate");
+  b->graph_ok = true;
+  return LCBP_OK;
+}
+
+void* field(lcbp_batch* b, void* arr, int comps, int r) {
+  return static_cast<char*>(arr) + (size_t)comps * b->base[r] * b->es;
+}
+
+int moments_all(lcbp_batch* b) {
+  cudaError_t e = b->dtype == LCBP_F64 ? launch_moments<double>(b->d_rep, b->d_tiles, b->ntiles, b->ts,
+                                                                b->f[b->cur], b->rhou[b->cur], b->stream)
+                                       : launch_moments<float>(b->d_rep, b->d_tiles, b->ntiles, b->ts, b->f[b->cur],
+                                                               b->rhou[b->cur], b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  return e == cudaSuccess ? LCBP_OK : cuda_fail(e, "moments");
+}
+
+int diag(lcbp_batch* b, int r, double threshold, int with_f) {
+  DiagGeom g{b->nx[r], b->ny[r], b->nz[r], b->n[r], b->base[r], b->p[r].A0, b->p[r].gamma, b->p[r].K, b->p[r].q0};
+  cudaError_t e = b->dtype == LCBP_F64 ? launch_diag_one<double>(g, b->q, b->f[b->cur], with_f, threshold,
+                                                                 b->d_partials, b->d_out, b->stream)
+                                       : launch_diag_one<float>(g, b->q, b->f[b->cur], with_f, threshold,
+                                                                b->d_partials, b->d_out, b->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(b->h_out, b->d_out, 64, cudaMemcpyDeviceToHost, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "diagnostics");
+  if (b->h_out[6] != 0.0) return fail(LCBP_ENONFINITE, "replica %d: %.0f sites hold NaN or Inf", r, b->h_out[6]);
+  return LCBP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lcbp_batch_create(int R, const int* dims, const lcbp_params* params, int dtype, lcbp_batch** out) {
+  if (!out) return fail(LCBP_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (R < 1 || !dims || !params) return fail(LCBP_EINVAL, "need R >= 1, dims and params");
+  if (!valid_dtype(dtype)) return fail(LCBP_EINVAL, "bad dtype");
+  auto* b = new lcbp_batch();
+  b->R = R;
+  b->dtype = dtype;
+  b->es = dtype_size(dtype);
+  cudaGetDevice(&b->device);
+  long long tot = 0, cap = 0;
+  for (int r = 0; r < R; ++r) {
+    const int x = dims[3 * r], y = dims[3 * r + 1], z = dims[3 * r + 2];
+    if (x < 1 || y < 1 || z < 1) {
+      delete b;
+      return fail(LCBP_EINVAL, "replica %d has a size < 1", r);
+    }
+    b->nx.push_back(x);
+    b->ny.push_back(y);
+    b->nz.push_back(z);
+    const long long n = (long long)x * y * z;
+    b->n.push_back(n);
+    b->base.push_back(tot);
+    tot += (n + 63) / 64 * 64;  // 256-byte aligned replica blocks in FP32
+    long long mx = 0;
+    for (const TileShape& c : kCandidates) mx = std::max(mx, tile_count(x, y, z, c));
+    cap += mx;
+    HostParams hp;
+    hp.A0 = params[r].A0;
+    hp.gamma = params[r].gamma;
+    hp.K = params[r].K;
+    hp.q0 = params[r].q0;
+    hp.tau_f = params[r].tau_f;
+    hp.xi = params[r].xi;
+    hp.Gamma = params[r].Gamma;
+    hp.flow_on = 1;
+    hp.coupling = LCBP_JACOBI;
+    int rc = check_params(hp);
+    if (rc) {
+      delete b;
+      return rc;
+    }
+    b->p.push_back(hp);
+  }
+  if (tot > (1ll << 31)) {
+    delete b;
+    return fail(LCBP_EINVAL, "more than 2^31 sites");
+  }
+  b->ntot = tot;
+  b->tile_cap = cap;
+  b->flow_on = 1;
+  b->coupling = LCBP_JACOBI;
+  const long long comps[10] = {15, 15, 4, 4, 5, 5, 5, 5, 3, 3};
+  size_t off[10], o = 0;
+  for (int i = 0; i < 10; ++i) {
+    off[i] = o;
+    o = a256(o + (size_t)comps[i] * tot * b->es);
+  }
+  const size_t off_stage = o;
+  b->staging_elems = std::min(kStaging, 15 * tot);
+  o = a256(o + (size_t)b->staging_elems * 8);
+  const size_t off_rep = o;
+  o = a256(o + replica_bytes(dtype) * R);
+  const size_t off_tiles = o;
+  o = a256(o + (size_t)cap * sizeof(Tile));
+  const size_t off_aux = o;
+  o = a256(o + (size_t)R * 3 * 8);
+  const size_t off_part = o;
+  o = a256(o + (kDiagPartials + 8) * 8);
+  cudaError_t e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaMalloc(&b->ws, o);
+  if (e != cudaSuccess) {
+    if (b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+    cudaGetLastError();
+    return fail(LCBP_ENOMEM, "batch allocation of %zu bytes failed", o);
+  }
+  char* w = b->ws;
+  b->f[0] = w + off[0];
+  b->f[1] = w + off[1];
+  b->rhou[0] = w + off[2];
+  b->rhou[1] = w + off[3];
+  b->q = w + off[4];
+  b->qs = w + off[5];
+  b->h = w + off[6];
+  b->sig = w + off[7];
+  b->tau = w + off[8];
+  b->b = w + off[9];
+  b->staging = w + off_stage;
+  b->d_rep = w + off_rep;
+  b->d_tiles = reinterpret_cast<Tile*>(w + off_tiles);
+  b->d_q0 = reinterpret_cast<double*>(w + off_aux);
+  b->d_shelix = b->d_q0 + R;
+  b->d_seed = reinterpret_cast<uint64_t*>(b->d_q0 + 2 * R);
+  b->d_partials = reinterpret_cast<double*>(w + off_part);
+  b->d_out = b->d_partials + kDiagPartials;
+  e = cudaMemsetAsync(b->ws, 0, off_stage, b->stream);
+  if (e == cudaSuccess) e = cudaMallocHost(&b->h_out, 64);
+  int rc = e == cudaSuccess ? LCBP_OK : cuda_fail(e, "batch set-up");
+  if (!rc) rc = upload_table(b);
+  if (!rc) rc = build_tiles(b, kCandidates[0]);
+  if (!rc) b->max_grid = resident_ctas(b);
+  if (rc) {
+    lcbp_batch_destroy(b);
+    return rc;
+  }
+  *out = b;
+  return LCBP_OK;
+}
+
+int lcbp_batch_destroy(lcbp_batch* b) {
+  if (!b) return LCBP_OK;
+  cudaSetDevice(b->device);
+  cudaStreamSynchronize(b->stream);
+  drop_graph(b);
+  if (b->h_out) cudaFreeHost(b->h_out);
+  if (b->ws) cudaFree(b->ws);
+  if (b->stream) cudaStreamDestroy(b->stream);
+  delete b;
+  return LCBP_OK;
+}
+
+int lcbp_batch_set_flow(lcbp_batch* b, int flow_on, int coupling) {
+  int rc = check_b(b);
+  if (rc) return rc;
+  if (coupling != LCBP_JACOBI && coupling != LCBP_GAUSS_SEIDEL) return fail(LCBP_EINVAL, "bad coupling");
+  drop_graph(b);
+  b->flow_on = flow_on ? 1 : 0;
+  b->coupling = coupling;
+  return LCBP_OK;
+}
+
+int lcbp_batch_init_q(lcbp_batch* b, int r, int kind, double amplitude, double noise, uint64_t seed,
+                      const int* region) {
+  int rc = check_b(b);
+  if (!rc) rc = check_r(b, r);
+  if (rc) return rc;
+  if (kind < LCBP_BPII || kind > LCBP_SLAB_BPII_IN_CHOL) return fail(LCBP_EINVAL, "unknown initial kind %d", kind);
+  if (!(noise >= 0.0)) return fail(LCBP_EINVAL, "noise < 0");
+  if (kind == LCBP_SLAB_BPII_IN_CHOL && !region) return fail(LCBP_EINVAL, "SLAB_BPII_IN_CHOL needs region");
+  InitQArgs a{kind, amplitude, noise, seed, region ? region[0] : 0};
+  cudaError_t e = cudaMemcpyAsync(b->d_seed + r, &seed, 8, cudaMemcpyHostToDevice, b->stream);
+  const Tile* t0 = b->d_tiles + b->tile_begin[r];
+  const int nt = b->tile_begin[r + 1] - b->tile_begin[r];
+  if (e == cudaSuccess)
+    e = b->dtype == LCBP_F64
+            ? launch_init_q<double>(b->d_rep, t0, nt, b->ts, b->d_q0, b->d_shelix, b->d_seed, a, b->q, b->stream)
+            : launch_init_q<float>(b->d_rep, t0, nt, b->ts, b->d_q0, b->d_shelix, b->d_seed, a, b->q, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  return e == cudaSuccess ? LCBP_OK : cuda_fail(e, "batch init_q");
+}
+
+int lcbp_batch_set_q(lcbp_batch* b, int r, const void* q5, int dtype) {
+  int rc = check_b(b);
+  if (!rc) rc = check_r(b, r);
+  if (rc) return rc;
+  if (!q5 || !valid_dtype(dtype)) return fail(LCBP_EINVAL, "bad buffer or dtype");
+  return transfer(field(b, b->q, 5, r), b->dtype, const_cast<void*>(q5), dtype, 5 * b->n[r], true, b->staging,
+                  b->staging_elems, b->stream);
+}
+
+int lcbp_batch_init_f_equilibrium(lcbp_batch* b, double rho0) {
+  int rc = check_b(b);
+  if (rc) return rc;
+  if (!(rho0 > 0)) return fail(LCBP_EINVAL, "rho0 <= 0");
+  StepArgs a = args(b);
+  cudaError_t e = b->dtype == LCBP_F64 ? launch_field<double>(a, b->stream) : launch_field<float>(a, b->stream);
+  if (e == cudaSuccess)
+    e = b->dtype == LCBP_F64 ? launch_init_feq<double>(b->d_rep, b->d_tiles, b->ntiles, b->ts, rho0, nullptr,
+                                                       b->sig, b->f[b->cur], b->stream)
+                             : launch_init_feq<float>(b->d_rep, b->d_tiles, b->ntiles, b->ts, rho0, nullptr, b->sig,
+                                                      b->f[b->cur], b->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "batch init_f");
+  rc = moments_all(b);
+  if (rc) return rc;
+  b->f_ready = true;
+  return LCBP_OK;
+}
+
+int lcbp_batch_step(lcbp_batch* b, int nsteps) {
+  int rc = check_b(b);
+  if (rc) return rc;
+  if (nsteps < 0) return fail(LCBP_EINVAL, "nsteps < 0");
+  if (b->flow_on && !b->f_ready) return fail(LCBP_ESTATE, "initialise f before stepping with flow on");
+  if (nsteps == 0) return LCBP_OK;
+  if (!b->tuned) {
+    rc = tune(b);
+    if (rc) return rc;
+    drop_graph(b);
+  }
+  cudaError_t e = cudaSuccess;
+  int left = nsteps;
+  if (b->cur == 1) {
+    e = eager(b);
+    --left;
+  }
+  if (left >= 2 && !b->graph_ok && e == cudaSuccess) {
+    rc = build_graph(b);
+    if (rc) return rc;
+  }
+  while (left >= 2 && e == cudaSuccess) {
+    e = cudaGraphLaunch(b->graph, b->stream);
+    left -= 2;
+  }
+  if (left == 1 && e == cudaSuccess) e = eager(b);
+  if (e != cudaSuccess) return cuda_fail(e, "batch step");
+  b->step += nsteps;
+  return LCBP_OK;
+}
+
+int lcbp_batch_synchronize(lcbp_batch* b) {
+  int rc = check_b(b);
+  if (rc) return rc;
+  cudaError_t e = cudaStreamSynchronize(b->stream);
+  return e == cudaSuccess ? LCBP_OK : cuda_fail(e, "synchronize");
+}
+
+int lcbp_batch_read_q(lcbp_batch* b, int r, void* dst, int dtype) {
+  int rc = check_b(b);
+  if (!rc) rc = check_r(b, r);
+  if (rc) return rc;
+  if (!dst || !valid_dtype(dtype)) return fail(LCBP_EINVAL, "bad buffer or dtype");
+  return transfer(field(b, b->q, 5, r), b->dtype, dst, dtype, 5 * b->n[r], false, b->staging, b->staging_elems,
+                  b->stream);
+}
+
+int lcbp_batch_read_u(lcbp_batch* b, int r, void* dst, int dtype) {
+  int rc = check_b(b);
+  if (!rc) rc = check_r(b, r);
+  if (rc) return rc;
+  if (!dst || !valid_dtype(dtype)) return fail(LCBP_EINVAL, "bad buffer or dtype");
+  void* u = static_cast<char*>(field(b, b->rhou[b->cur], 4, r)) + b->n[r] * b->es;
+  return transfer(u, b->dtype, dst, dtype, 3 * b->n[r], false, b->staging, b->staging_elems, b->stream);
+}
+
+int lcbp_batch_free_energy(lcbp_batch* b, int r, double* F) {
+  int rc = check_b(b);
+  if (!rc) rc = check_r(b, r);
+  if (rc) return rc;
+  if (!F) return fail(LCBP_EINVAL, "F is NULL");
+  rc = diag(b, r, 0.0, 0);
+  if (rc) return rc;
+  *F = b->h_out[0];
+  return LCBP_OK;
+}
+
+int lcbp_batch_totals(lcbp_batch* b, int r, double* mass, double momentum[3]) {
+  int rc = check_b(b);
+  if (!rc) rc = check_r(b, r);
+  if (rc) return rc;
+  rc = diag(b, r, 0.0, 1);
+  if (rc) return rc;
+  if (mass) *mass = b->h_out[1];
+  if (momentum) {
+    momentum[0] = b->h_out[2];
+    momentum[1] = b->h_out[3];
+    momentum[2] = b->h_out[4];
+  }
+  return LCBP_OK;
+}
+
+int lcbp_batch_defect_fraction(lcbp_batch* b, int r, double threshold, double* fraction) {
+  int rc = check_b(b);
+  if (!rc) rc = check_r(b, r);
+  if (rc) return rc;
+  if (!fraction) return fail(LCBP_EINVAL, "fraction is NULL");
+  rc = diag(b, r, threshold, 0);
+  if (rc) return rc;
+  *fraction = b->h_out[5] / (double)b->n[r];
+  return LCBP_OK;
+}
+
+int lcbp_batch_get_info(lcbp_batch* b, int* R, long long* total_sites, int tile[3], int* persistent_ctas,
+                        long long* step) {
+  int rc = check_b(b);
+  if (rc) return rc;
+  if (R) *R = b->R;
+  if (total_sites) {
+    long long s = 0;
+    for (long long v : b->n) s += v;
+    *total_sites = s;
+  }
+  if (tile) {
+    tile[0] = b->ts.tx;
+    tile[1] = b->ts.ty;
+    tile[2] = b->ts.tz;
+  }
+  if (persistent_ctas) *persistent_ctas = b->max_grid;
+  if (step) *step = b->step;
+  return LCBP_OK;
+}
+
+}  // extern "C"

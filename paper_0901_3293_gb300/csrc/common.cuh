@@ -284,10 +284,12 @@ __device__ __forceinline__ Sym5<real> be_rate(const Sym5<real>& q, const Sym5<re
   for (int a = 0; a < 3; ++a)
 #pragma unroll
     for (int b = 0; b < 3; ++b) trQW += Q.a[a][b] * w[b][a];
-  // S = xi (D P + P D) + (O P - P O) - 2 xi P Tr(QW)
+  // S = xi (D P + P D) + (O P - P O) - 2 xi P Tr(QW); only the five
+  // independent entries are formed.  Its trace is (2 xi / 3) Tr D exactly
+  // (Tr P = 1, Tr(DP) = Q:D + Tr D / 3), which the traceless projection removes.
   real S[3][3];
 #pragma unroll
-  for (int a = 0; a < 3; ++a)
+  for (int a = 0; a < 2; ++a)
 #pragma unroll
     for (int b = a; b < 3; ++b) {
       real dp = real(0), pd = real(0), op = real(0), po = real(0);
@@ -300,7 +302,7 @@ __device__ __forceinline__ Sym5<real> be_rate(const Sym5<real>& q, const Sym5<re
       }
       S[a][b] = xi * (dp + pd) + (op - po) - real(2) * xi * P[a][b] * trQW;
     }
-  const real trS3 = (S[0][0] + S[1][1] + S[2][2]) / real(3);
+  const real trS3 = real(2) * xi * (D[0][0] + D[1][1] + D[2][2]) / real(9);
   const real ux = u[0], uy = u[1], uz = u[2];
   auto adv = [&](real gx, real gy, real gz) { return ux * gx + uy * gy + uz * gz; };
   r.xx += (S[0][0] - trS3) - adv(dq[0].xx, dq[1].xx, dq[2].xx);

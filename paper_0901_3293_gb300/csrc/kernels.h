@@ -27,8 +27,10 @@ struct StepArgs {
   const void* bext;  // 3 comps or nullptr
   void* f;       // 15 comps, step n
   void* fnew;    // 15 comps, step n+1
-  void* rhou;    // 4 comps [rho, ux, uy, uz], step n
+  void* rhou;    // 4 comps [rho - 1, ux, uy, uz], step n
   void* rhou_new;
+  void* qout;    // Q^{n+1}; nullptr = in place on q
+  int max_grid;  // > 0: at most this many (persistent) CTAs walk the tile list
   // optional: events[0] is recorded before the first kernel of the step and
   // events[k + 1] after kernel k (per-kernel timing); nullptr otherwise
   cudaEvent_t* events;

@@ -160,7 +160,7 @@ __global__ void __launch_bounds__(256) k_lb_correct(const Replica<real>* __restr
                                                     const real* __restrict__ sigma, const real* __restrict__ bf,
                                                     real* __restrict__ fnew, real* __restrict__ rhou_new,
                                                     const real* __restrict__ Qs, const real* __restrict__ rhou_q,
-                                                    real* __restrict__ Q) {
+                                                    const real* Qin, real* Qout) {
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
     Replica<real> R;
     int x, y, z;
@@ -244,13 +244,12 @@ __global__ void __launch_bounds__(256) k_lb_correct(const Replica<real>* __restr
         velocity_gradient(ru, n, nb, nx, ny, w);
       }
       const Sym5<real> r = be_rate(st.c, h, dq, u, w, R.m, FLOW);
-      real* qp = Q + 5 * R.base;
-      const Sym5<real> q0 = load5(qp, n, nb.s);
+      const Sym5<real> q0 = load5(Qin + 5 * R.base, n, nb.s);
       const real half = real(0.5);
       const Sym5<real> q1 = {half * (q0.xx + st.c.xx + r.xx), half * (q0.xy + st.c.xy + r.xy),
                              half * (q0.xz + st.c.xz + r.xz), half * (q0.yy + st.c.yy + r.yy),
                              half * (q0.yz + st.c.yz + r.yz)};
-      store5(qp, n, nb.s, q1);
+      store5(Qout + 5 * R.base, n, nb.s, q1);
     }
   }
 }
@@ -262,7 +261,9 @@ template <typename real>
 cudaError_t launch_step(const StepArgs& a, cudaStream_t s) {
   const auto* reps = static_cast<const Replica<real>*>(a.reps);
   const int threads = a.ts.tx * a.ts.ty * a.ts.tz;
-  const int grid = a.ntiles;
+  // persistent CTAs walk the tile list when a cap is given
+  const int grid = a.max_grid > 0 && a.max_grid < a.ntiles ? a.max_grid : a.ntiles;
+  void* qout = a.qout ? a.qout : a.q;
   auto Rp = [](void* p) { return static_cast<real*>(p); };
   auto Cp = [](const void* p) { return static_cast<const real*>(p); };
   int k = 0;
@@ -284,7 +285,7 @@ cudaError_t launch_step(const StepArgs& a, cudaStream_t s) {
       mark();
       k_lb_correct<real, true, true, true><<<grid, threads, 0, s>>>(
           reps, a.tiles, a.ntiles, a.ts, Cp(a.f), Cp(a.rhou), Cp(a.sigma), Cp(a.b), Rp(a.fnew), Rp(a.rhou_new),
-          Cp(a.qs), Cp(a.rhou), Rp(a.q));
+          Cp(a.qs), Cp(a.rhou), Cp(a.q), Rp(qout));
       mark();
     } else {
       // Gauss-Seidel: b, LB, then the Heun stages with u^{n+1}
@@ -297,14 +298,14 @@ cudaError_t launch_step(const StepArgs& a, cudaStream_t s) {
       mark();
       k_lb_correct<real, true, true, false><<<grid, threads, 0, s>>>(
           reps, a.tiles, a.ntiles, a.ts, Cp(a.f), Cp(a.rhou), Cp(a.sigma), Cp(a.b), Rp(a.fnew), Rp(a.rhou_new),
-          nullptr, nullptr, nullptr);
+          nullptr, nullptr, nullptr, nullptr);
       mark();
       k_force_predict<real, true, false, true, false><<<grid, threads, 0, s>>>(
           reps, a.tiles, a.ntiles, a.ts, Cp(a.q), Cp(a.h), nullptr, Cp(a.rhou_new), nullptr, nullptr, Rp(a.qs));
       mark();
       k_lb_correct<real, true, false, true><<<grid, threads, 0, s>>>(
           reps, a.tiles, a.ntiles, a.ts, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, Cp(a.qs),
-          Cp(a.rhou_new), Rp(a.q));
+          Cp(a.rhou_new), Cp(a.q), Rp(qout));
       mark();
     }
   } else {
@@ -315,7 +316,7 @@ cudaError_t launch_step(const StepArgs& a, cudaStream_t s) {
     mark();
     k_lb_correct<real, false, false, true><<<grid, threads, 0, s>>>(
         reps, a.tiles, a.ntiles, a.ts, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, Cp(a.qs), nullptr,
-        Rp(a.q));
+        Cp(a.q), Rp(qout));
     mark();
   }
   return cudaGetLastError();

@@ -155,6 +155,7 @@ __global__ void __launch_bounds__(ZM_TX* TY) k_qside(const __grid_constant__ CUt
 
   // H and tau of plane p on the tile plus a one-site ring (Q planes p-1..p+1)
   auto field_plane = [&](int p) {
+    const bool own = p >= z0 && p < z1;
     const real* qm = qslot(p - 1);
     const real* qc = qslot(p);
     const real* qp = qslot(p + 1);
@@ -176,6 +177,10 @@ __global__ void __launch_bounds__(ZM_TX* TY) k_qside(const __grid_constant__ CUt
       Sym5<real> sg;
       real tu[3];
       lc_stress(st.c, h, m.xi, sg, tu);
+      // sigma of an interior site of a plane this CTA owns goes straight out
+      const int sx = x0 + c - 1, sy = y0 + r - 1;
+      if (own && r >= 1 && r <= TY && c >= 1 && c <= ZM_TX && sx < nx && sy < ny)
+        store5(sigma, n, ((long long)p * ny + sy) * nx + sx, sg);
       const int ti = r * L::TCOLS + c;
       tp[ti] = tu[0];
       tp[L::TROWS * L::TCOLS + ti] = tu[1];
@@ -234,9 +239,6 @@ __global__ void __launch_bounds__(ZM_TX* TY) k_qside(const __grid_constant__ CUt
       dq[1] = half_diff(ld5(qc, L::QCS, qi + ZM_BX), ld5(qc, L::QCS, qi - ZM_BX));
       dq[2] = half_diff(ld5(qp, L::QCS, qi), ld5(qm, L::QCS, qi));
       const Sym5<real> h = ld5(hslot(z), TY * ZM_TX, ty * ZM_TX + tx);
-      Sym5<real> sg;
-      real tu[3];
-      lc_stress(q, h, m.xi, sg, tu);
       // body force; tau = [xy, xz, yz] with tau_yx = -tau_xy etc.
       const real* tm = tslot(z - 1);
       const real* tc = tslot(z);
@@ -271,7 +273,6 @@ __global__ void __launch_bounds__(ZM_TX* TY) k_qside(const __grid_constant__ CUt
         w[a][2] = half * (up[o] - um[o]);
       }
       const Sym5<real> r = be_rate(q, h, dq, u, w, m, true);
-      store5(sigma, n, s, sg);
       bout[s] = bx;
       bout[n + s] = by;
       bout[2 * n + s] = bz;
@@ -393,13 +394,16 @@ __global__ void __launch_bounds__(ZM_TX* TY, TY == 8 ? 2 : 1)
     // populations f_i(y - e_i), issued before the barrier wait so that they overlap it
     real fin[NV];
     if (valid) {
-      const int zm = wrap(z - 1, nz), zp = wrap(z + 1, nz);
+      const int zm = z == 0 ? nz - 1 : z - 1, zp = z + 1 == nz ? 0 : z + 1;
+      // three row bases per plane: rows y-1, y, y+1 of planes z-1, z, z+1
+      const long long rb[3][3] = {
+          {((long long)zm * ny + ym) * nx, ((long long)zm * ny + gy) * nx, ((long long)zm * ny + yp) * nx},
+          {((long long)z * ny + ym) * nx, ((long long)z * ny + gy) * nx, ((long long)z * ny + yp) * nx},
+          {((long long)zp * ny + ym) * nx, ((long long)zp * ny + gy) * nx, ((long long)zp * ny + yp) * nx}};
 #pragma unroll
       for (int i = 0; i < NV; ++i) {
         const int sx = ex(i) > 0 ? xm : ex(i) < 0 ? xp : gx;
-        const int sy = ey(i) > 0 ? ym : ey(i) < 0 ? yp : gy;
-        const int sz = ez(i) > 0 ? zm : ez(i) < 0 ? zp : z;
-        fin[i] = __ldg(f + i * n + ((long long)sz * ny + sy) * nx + sx);
+        fin[i] = __ldg(f + i * n + rb[1 - ez(i)][1 - ey(i)] + sx);
       }
     }
     wait(z + 1);

@@ -65,7 +65,33 @@ _SIGNATURES = {
     "lcbp_defect_fraction": (_c_int, [_P, _c_double, ctypes.POINTER(_c_double)]),
     "lcbp_save": (_c_int, [_P, ctypes.c_char_p]),
     "lcbp_load": (_c_int, [_P, ctypes.c_char_p]),
+    "lcbp_batch_create": (_c_int, [_c_int, ctypes.POINTER(_c_int), _c_void_p, _c_int, ctypes.POINTER(_P)]),
+    "lcbp_batch_destroy": (_c_int, [_P]),
+    "lcbp_batch_set_flow": (_c_int, [_P, _c_int, _c_int]),
+    "lcbp_batch_init_q": (_c_int, [_P, _c_int, _c_int, _c_double, _c_double, ctypes.c_uint64,
+                                   ctypes.POINTER(_c_int)]),
+    "lcbp_batch_set_q": (_c_int, [_P, _c_int, _c_void_p, _c_int]),
+    "lcbp_batch_init_f_equilibrium": (_c_int, [_P, _c_double]),
+    "lcbp_batch_step": (_c_int, [_P, _c_int]),
+    "lcbp_batch_synchronize": (_c_int, [_P]),
+    "lcbp_batch_read_q": (_c_int, [_P, _c_int, _c_void_p, _c_int]),
+    "lcbp_batch_read_u": (_c_int, [_P, _c_int, _c_void_p, _c_int]),
+    "lcbp_batch_free_energy": (_c_int, [_P, _c_int, ctypes.POINTER(_c_double)]),
+    "lcbp_batch_totals": (_c_int, [_P, _c_int, ctypes.POINTER(_c_double), ctypes.POINTER(_c_double)]),
+    "lcbp_batch_defect_fraction": (_c_int, [_P, _c_int, _c_double, ctypes.POINTER(_c_double)]),
+    "lcbp_batch_get_info": (_c_int, [_P, ctypes.POINTER(_c_int), ctypes.POINTER(ctypes.c_longlong),
+                                     ctypes.POINTER(_c_int), ctypes.POINTER(_c_int),
+                                     ctypes.POINTER(ctypes.c_longlong)]),
 }
+
+
+class Params(ctypes.Structure):
+    """lcbp_params: per-replica parameters of a batch."""
+    _fields_ = [(k, _c_double) for k in ("A0", "gamma", "K", "q0", "tau_f", "xi", "Gamma")]
+
+    @classmethod
+    def _fields_names(cls):
+        return [f[0] for f in cls._fields_]
 
 
 class LcbpError(RuntimeError):
@@ -305,3 +331,97 @@ class Lattice:
 
     def load(self, path: str) -> None:
         check(lib().lcbp_load(self._h, os.fsencode(path)))
+
+
+class Batch:
+    """R replicas of uneven sizes and per-replica parameters, stepped together.
+
+    dims: list of (nx, ny, nz); params: list of dicts with keys A0, gamma, K,
+    q0, tau_f, xi, Gamma.
+    """
+
+    def __init__(self, dims, params, dtype: str = "f32"):
+        self.R = len(dims)
+        self.dims = [tuple(int(v) for v in d) for d in dims]
+        arr = (_c_int * (3 * self.R))(*[v for d in self.dims for v in d])
+        ps = (Params * self.R)(*[Params(**{k: float(p[k]) for k in Params._fields_names()}) for p in params])
+        self._h = _P()
+        self.state_dtype = {"f32": F32, "f64": F64}[dtype]
+        check(lib().lcbp_batch_create(self.R, arr, ctypes.cast(ps, _c_void_p), self.state_dtype,
+                                      ctypes.byref(self._h)))
+
+    def close(self) -> None:
+        if self._h:
+            check(lib().lcbp_batch_destroy(self._h))
+            self._h = _P()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_flow(self, flow_on: bool = True, coupling: int = JACOBI) -> "Batch":
+        check(lib().lcbp_batch_set_flow(self._h, int(bool(flow_on)), coupling))
+        return self
+
+    def init_q(self, r: int, kind: int, amplitude: float, noise: float = 0.0, seed: int = 0, z0=None) -> "Batch":
+        region = (_c_int * 1)(z0) if z0 is not None else None
+        check(lib().lcbp_batch_init_q(self._h, r, kind, amplitude, noise, seed, region))
+        return self
+
+    def set_q(self, r: int, q5) -> "Batch":
+        p, d, keep = _ptr(q5)
+        check(lib().lcbp_batch_set_q(self._h, r, p, d))
+        return self
+
+    def init_f_equilibrium(self, rho0: float = 1.0) -> "Batch":
+        check(lib().lcbp_batch_init_f_equilibrium(self._h, rho0))
+        return self
+
+    def step(self, nsteps: int = 1) -> "Batch":
+        check(lib().lcbp_batch_step(self._h, int(nsteps)))
+        return self
+
+    def synchronize(self) -> None:
+        check(lib().lcbp_batch_synchronize(self._h))
+
+    def _read(self, fn, r, comps, dtype):
+        nx, ny, nz = self.dims[r]
+        out = np.empty((comps, nz, ny, nx), dtype=dtype)
+        p, d, keep = _ptr(out)
+        check(fn(self._h, r, p, d))
+        return out
+
+    def read_q(self, r: int, dtype=np.float64):
+        return self._read(lib().lcbp_batch_read_q, r, 5, dtype)
+
+    def read_u(self, r: int, dtype=np.float64):
+        return self._read(lib().lcbp_batch_read_u, r, 3, dtype)
+
+    def free_energy(self, r: int) -> float:
+        F = _c_double()
+        check(lib().lcbp_batch_free_energy(self._h, r, ctypes.byref(F)))
+        return F.value
+
+    def totals(self, r: int):
+        m = _c_double()
+        P = (_c_double * 3)()
+        check(lib().lcbp_batch_totals(self._h, r, ctypes.byref(m), P))
+        return m.value, np.array(P[:])
+
+    def defect_fraction(self, r: int, threshold: float = 0.19) -> float:
+        fr = _c_double()
+        check(lib().lcbp_batch_defect_fraction(self._h, r, threshold, ctypes.byref(fr)))
+        return fr.value
+
+    def info(self):
+        R = _c_int()
+        tot = ctypes.c_longlong()
+        tile = (_c_int * 3)()
+        ctas = _c_int()
+        st = ctypes.c_longlong()
+        check(lib().lcbp_batch_get_info(self._h, ctypes.byref(R), ctypes.byref(tot), tile, ctypes.byref(ctas),
+                                        ctypes.byref(st)))
+        return {"R": R.value, "sites": tot.value, "tile": tuple(tile), "persistent_ctas": ctas.value,
+                "step": st.value}
