@@ -285,6 +285,35 @@ def run_ours(args):
                  "note": "state (168 MB) partly L2-resident; not the headline"}
     slab.close()
 
+    # ---- the 48-replica sweep (32^3 / 48^3, per-replica kappa and tau) in one batch
+    from paper_0901_3293_gb300 import synth
+    sweep = synth.replica_sweep(48, SEED)
+    bparams = []
+    for sw in sweep:
+        g = 27.0 / (9.0 + sw["tau"])
+        q0 = 2 * np.pi / 16
+        bparams.append(dict(A0=0.01, gamma=g, K=sw["kappa"] ** 2 * 0.01 * g / (108 * q0 * q0), q0=q0,
+                            tau_f=2.0, xi=0.7, Gamma=0.3))
+    batch = lcbp.Batch([sw["dims"] for sw in sweep], bparams, dtype="f32")
+    for r, sw in enumerate(sweep):
+        kind = (lcbp.BPII, lcbp.CHOL_Z, lcbp.ISO_NOISE)[sw["kind"]]
+        batch.init_q(r, kind, 0.3 if sw["kind"] == 0 else 0.4, noise=1e-2, seed=sw["seed"])
+    batch.init_f_equilibrium(1.0).step(max(4, args.warmup))
+    batch.synchronize()
+    bsites = batch.info()["sites"]
+    bs = torch.cuda.Stream()
+    t0 = time.perf_counter()
+    batch.step(args.steps)
+    batch.synchronize()
+    b_s = time.perf_counter() - t0
+    binfo = batch.info()
+    batch_line = {"replicas": 48, "sites": bsites, "ms_per_step": 1e3 * b_s / args.steps,
+                  "MLUPS": bsites * args.steps / b_s / 1e6, "tile": binfo["tile"],
+                  "persistent_ctas": binfo["persistent_ctas"],
+                  "note": "generic kernels over one tile list spanning all replicas, graph replay; "
+                          "host-timed around lcbp_batch_step + synchronize"}
+    batch.close()
+
     if rank != 0:
         return
     cpu = cpu_baseline_entry(int(os.environ.get("LCBP_ORACLE_STEPS", "40")))
@@ -301,7 +330,7 @@ def run_ours(args):
                    "planes_per_cta": zc},
         "roofline": roof, "per_kernel": per_kernel, "cpu_baseline": cpu, "e2e": e2e,
         "gpu_launches": launches, "clocks": clk, "free_energy_after": F,
-        "slab_64x64x256": slab_line,
+        "slab_64x64x256": slab_line, "batched_48_replicas": batch_line,
     }
     print(json.dumps(line), flush=True)
 
