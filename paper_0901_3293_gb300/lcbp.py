@@ -387,6 +387,8 @@ class Batch:
         check(lib().lcbp_batch_synchronize(self._h))
 
     def _read(self, fn, r, comps, dtype):
+        if not 0 <= r < self.R:
+            raise LcbpError(EINVAL, f"replica {r} out of range [0, {self.R})")
         nx, ny, nz = self.dims[r]
         out = np.empty((comps, nz, ny, nx), dtype=dtype)
         p, d, keep = _ptr(out)
