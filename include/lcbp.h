@@ -230,6 +230,13 @@ LCBP_API int lcbp_set_path(lcbp_lattice *h, int path);
  */
 LCBP_API int lcbp_get_path(lcbp_lattice *h, int *fast, int *planes_per_cta);
 
+/*
+ * Reset f to the equilibrium f^eq(rho, u, sigma_LC(Q)) of the current moments
+ * and the current Q (used when plain stepping resumes after Q was advanced
+ * by other means, e.g. the learned surrogate).  Errors: LCBP_ESTATE.
+ */
+LCBP_API int lcbp_reequilibrate_f(lcbp_lattice *h);
+
 /* Synchronise the lattice's stream.  Errors: LCBP_ECUDA; LCBP_ETIMEOUT if a
  * bounded device-side wait of the fast path gave up (results invalid). */
 LCBP_API int lcbp_synchronize(lcbp_lattice *h);
@@ -315,6 +322,46 @@ LCBP_API int lcbp_batch_defect_fraction(lcbp_batch *b, int r, double threshold, 
 /* R, total sites, tuned tile shape (tx, ty, tz), persistent CTAs per launch, steps done. */
 LCBP_API int lcbp_batch_get_info(lcbp_batch *b, int *R, long long *total_sites, int tile[3], int *persistent_ctas,
                                  long long *step);
+
+/* ------------------------------------------------------------------------
+ * Learned surrogate (not part of the paper's method): a periodic 3x3x3
+ * convolutional network that advances Q by k = 10 solver steps,
+ *   x = [Q (5), u / s_u (3), kappa - 1, tau]  ->  h0 = relu(conv x),
+ *   4 x { a = relu(conv h);  h = h + conv a },  y = conv h (5 channels),
+ *   Q(t + 10) = Q(t) + s_dq * y,
+ * with 32 hidden channels, BF16 weights and activations and FP32
+ * accumulation on tcgen05 tensor cores (forward and backward-data), FP32
+ * weight gradients, masked MSE loss and Adam.  A surrogate object is built
+ * for one lattice size.  Parameters cross the boundary as one FP32 vector:
+ * for each layer in the order in, b0a, b0b, ..., b3a, b3b, out the weights
+ * W[t][c_in][c_out] (t = 9 (dz+1) + 3 (dy+1) + (dx+1), tap offset (dx, dy, dz),
+ * y(r) = b + sum_t W_t^T x(r + o_t)) followed by the bias b[c_out].
+ * ------------------------------------------------------------------------ */
+typedef struct lcbp_surrogate lcbp_surrogate;
+
+/* Number of FP32 values of the parameter vector (234437). */
+LCBP_API size_t lcbp_surrogate_param_count(void);
+/* Surrogate for an nx * ny * nz lattice; training != 0 also allocates the
+ * activations, gradients and Adam state.  Parameters start at zero. */
+LCBP_API int lcbp_surrogate_create(int nx, int ny, int nz, int training, lcbp_surrogate **out);
+LCBP_API int lcbp_surrogate_destroy(lcbp_surrogate *s);
+/* Input velocity scale s_u (default 1e-3) and output scale s_dq (default 1e-2). */
+LCBP_API int lcbp_surrogate_set_scales(lcbp_surrogate *s, double s_u, double s_dq);
+/* Upload / download the parameter vector (host or device FP32; Adam state is reset on upload). */
+LCBP_API int lcbp_surrogate_set_params(lcbp_surrogate *s, const float *params, size_t count);
+LCBP_API int lcbp_surrogate_get_params(lcbp_surrogate *s, float *params, size_t count);
+/* Gradient of the last training step's loss, in the parameter-vector layout. */
+LCBP_API int lcbp_surrogate_get_grads(lcbp_surrogate *s, float *grads, size_t count);
+/* Network output y (5 * N values, [c][z][y][x]) for fields Q (5 * N), u (3 * N or NULL = 0). */
+LCBP_API int lcbp_surrogate_forward(lcbp_surrogate *s, const void *q5, const void *u3, double kappa, double tau,
+                                    int dtype, float *y5);
+/* ncalls times Q += s_dq * net(Q, u, kappa, tau) on a lattice of the same size (FP32 state).
+ * f is left as it was: call lcbp_reequilibrate_f before plain stepping resumes. */
+LCBP_API int lcbp_surrogate_step(lcbp_surrogate *s, lcbp_lattice *h, double kappa, double tau, int ncalls);
+/* One Adam step (learning rate lr) on the masked MSE between y and dq5 / s_dq
+ * (dq5: target change of Q, 5 * N values; mask: N values or NULL); *loss receives the loss. */
+LCBP_API int lcbp_surrogate_train_step(lcbp_surrogate *s, const void *q5, const void *u3, double kappa, double tau,
+                                       const void *dq5, const void *mask, int dtype, double lr, double *loss);
 
 #ifdef __cplusplus
 }

@@ -50,6 +50,18 @@ def relu(v):
     return np.maximum(v, 0.0)
 
 
+def bf16(a: np.ndarray) -> np.ndarray:
+    """Round to the nearest bfloat16 (ties to even), returned as float64: the
+    storage precision of weights and activations on the tensor-core path."""
+    b = np.asarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    b = ((b + 0x7FFF + ((b >> 16) & 1)) >> 16) << 16
+    return b.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def _ident(a):
+    return a
+
+
 def layer_names(blocks: int):
     names = ["in"]
     for k in range(blocks):
@@ -70,37 +82,64 @@ def init_params(c_in: int, width: int, c_out: int, blocks: int, rng: np.random.G
     return P
 
 
-def forward(P, x: np.ndarray, blocks: int):
-    """Network output and the activations the backward pass needs."""
+def forward(P, x: np.ndarray, blocks: int, quant=None):
+    """Network output and the activations the backward pass needs.
+
+    quant (e.g. :func:`bf16`) rounds the weights, the input and every stored
+    activation, as a reduced-precision implementation stores them; the
+    arithmetic itself stays FP64."""
+    q = quant or _ident
+    Wq = {k: (q(W), b) for k, (W, b) in P.items()}
+    x = q(x)
     acts = {"x": x}
-    h = relu(conv(x, *P["in"]))
+    h = q(relu(conv(x, *Wq["in"])))
     acts["h0"] = h
     for k in range(blocks):
-        a = relu(conv(h, *P[f"b{k}a"]))
+        a = q(relu(conv(h, *Wq[f"b{k}a"])))
         acts[f"a{k}"] = a
-        h = h + conv(a, *P[f"b{k}b"])
+        h = q(h + conv(a, *Wq[f"b{k}b"]))
         acts[f"h{k + 1}"] = h
-    return conv(h, *P["out"]), acts
+    return conv(h, *Wq["out"]), acts
 
 
-def backward(P, acts, dout: np.ndarray, blocks: int):
-    """Gradients {name: (dW, db)} and d(loss)/d(input) for upstream dout."""
+def backward(P, acts, dout: np.ndarray, blocks: int, quant=None):
+    """Gradients {name: (dW, db)} and d(loss)/d(input) for upstream dout.
+
+    quant rounds the weights and every stored gradient tensor (see forward)."""
+    q = quant or _ident
+    Wq = {k: q(W) for k, (W, b) in P.items()}
     G = {}
+    dout = q(dout)
     h = acts[f"h{blocks}"]
-    dh, dW, db = conv_backward(h, P["out"][0], dout)
+    dh, dW, db = conv_backward(h, Wq["out"], dout)
+    dh = q(dh)
     G["out"] = (dW, db)
     for k in reversed(range(blocks)):
         a = acts[f"a{k}"]
-        da, dW, db = conv_backward(a, P[f"b{k}b"][0], dh)
+        da, dW, db = conv_backward(a, Wq[f"b{k}b"], dh)
         G[f"b{k}b"] = (dW, db)
-        dpre = da * (a > 0)
-        dh_in, dW, db = conv_backward(acts[f"h{k}"], P[f"b{k}a"][0], dpre)
+        dpre = q(da * (a > 0))
+        dh_in, dW, db = conv_backward(acts[f"h{k}"], Wq[f"b{k}a"], dpre)
         G[f"b{k}a"] = (dW, db)
-        dh = dh + dh_in
-    dpre = dh * (acts["h0"] > 0)
-    dx, dW, db = conv_backward(acts["x"], P["in"][0], dpre)
+        dh = q(dh + dh_in) if k > 0 else dh + dh_in
+    dpre = q(dh * (acts["h0"] > 0))
+    dx, dW, db = conv_backward(acts["x"], Wq["in"], dpre)
     G["in"] = (dW, db)
     return G, dx
+
+
+def flatten(P, blocks: int) -> np.ndarray:
+    """Parameter vector: per layer (in, b0a, b0b, ..., out) W[t][ci][co] then b[co]."""
+    return np.concatenate([np.concatenate([P[n][0].ravel(), P[n][1]]) for n in layer_names(blocks)])
+
+
+def unflatten(v: np.ndarray, like, blocks: int):
+    out, off = {}, 0
+    for n in layer_names(blocks):
+        W, b = like[n]
+        out[n] = (v[off:off + W.size].reshape(W.shape), v[off + W.size:off + W.size + b.size])
+        off += W.size + b.size
+    return out
 
 
 def masked_mse(y: np.ndarray, target: np.ndarray, mask: np.ndarray):

@@ -1072,4 +1072,33 @@ int lcbp_load(lcbp_lattice* h, const char* path) {
   return LCBP_OK;
 }
 
+int lcbp_reequilibrate_f(lcbp_lattice* h) {
+  CHECK_H(h);
+  if (!h->f_ready) return fail(LCBP_ESTATE, "f was never initialised");
+  StepArgs a = step_args(h);
+  cudaError_t e = h->dtype == LCBP_F64 ? launch_field<double>(a, h->stream) : launch_field<float>(a, h->stream);
+  if (e == cudaSuccess)
+    e = h->dtype == LCBP_F64 ? launch_feq_from_moments<double>(h->d_rep, h->d_tiles, h->ntiles, h->ts,
+                                                                h->rhou[h->cur], h->sig, h->f[h->cur], h->stream)
+                             : launch_feq_from_moments<float>(h->d_rep, h->d_tiles, h->ntiles, h->ts,
+                                                               h->rhou[h->cur], h->sig, h->f[h->cur], h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "reequilibrate_f");
+  return refresh_moments(h);
+}
+
 }  // extern "C"
+
+namespace lcbp {
+int lattice_fields(lcbp_lattice* h, float** q, const float** u, int dims[3], cudaStream_t* stream) {
+  if (!h) return fail(LCBP_EINVAL, "null lattice handle");
+  if (h->dtype != LCBP_F32) return fail(LCBP_EINVAL, "the surrogate works on FP32 lattice state");
+  cudaSetDevice(h->device);
+  *q = static_cast<float*>(h->q);
+  *u = reinterpret_cast<const float*>(static_cast<const char*>(h->rhou[h->cur]) + h->n * sizeof(float));
+  dims[0] = h->nx;
+  dims[1] = h->ny;
+  dims[2] = h->nz;
+  *stream = h->stream;
+  return LCBP_OK;
+}
+}  // namespace lcbp

@@ -137,6 +137,41 @@ template cudaError_t launch_init_feq<float>(const void*, const Tile*, int, TileS
 template cudaError_t launch_init_feq<double>(const void*, const Tile*, int, TileShape, double, const void*,
                                              const void*, void*, cudaStream_t);
 
+// f = f^eq(rho, u, sigma) from the stored moments (deviation storage)
+template <typename real>
+__global__ void k_feq_from_moments(const Replica<real>* __restrict__ reps, const Tile* __restrict__ tiles, int ntiles,
+                                   TileShape ts, const real* __restrict__ rhou, const real* __restrict__ sigma,
+                                   real* __restrict__ f) {
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    Replica<real> R;
+    int rep, x, y, z;
+    if (!tile_coords(reps, tiles, t, ts, R, rep, x, y, z)) continue;
+    const long long n = R.n;
+    const long long s = ((long long)z * R.ny + y) * R.nx + x;
+    const real* rp = rhou + 4 * R.base;
+    const real drho = rp[s], ux = rp[n + s], uy = rp[2 * n + s], uz = rp[3 * n + s];
+    const Sym5<real> sg = load5(sigma + 5 * R.base, n, s);
+    const real usq = ux * ux + uy * uy + uz * uz;
+    real* fp = f + 15 * R.base;
+#pragma unroll
+    for (int i = 0; i < NV; ++i) fp[i * n + s] = feq_delta(i, drho, real(1) + drho, ux, uy, uz, usq, sg);
+  }
+}
+
+template <typename real>
+cudaError_t launch_feq_from_moments(const void* reps, const Tile* tiles, int ntiles, TileShape ts, const void* rhou,
+                                    const void* sigma, void* f, cudaStream_t s) {
+  k_feq_from_moments<real><<<ntiles, ts.tx * ts.ty * ts.tz, 0, s>>>(static_cast<const Replica<real>*>(reps), tiles,
+                                                                     ntiles, ts, static_cast<const real*>(rhou),
+                                                                     static_cast<const real*>(sigma),
+                                                                     static_cast<real*>(f));
+  return cudaGetLastError();
+}
+template cudaError_t launch_feq_from_moments<float>(const void*, const Tile*, int, TileShape, const void*, const void*,
+                                                    void*, cudaStream_t);
+template cudaError_t launch_feq_from_moments<double>(const void*, const Tile*, int, TileShape, const void*,
+                                                     const void*, void*, cudaStream_t);
+
 template <typename real>
 __global__ void k_moments(const Replica<real>* __restrict__ reps, const Tile* __restrict__ tiles, int ntiles,
                           TileShape ts, const real* __restrict__ f, real* __restrict__ rhou) {

@@ -61,6 +61,9 @@ template <typename real>
 cudaError_t launch_init_feq(const void* reps, const Tile* tiles, int ntiles, TileShape ts, double rho0,
                             const void* u3, const void* sigma, void* f, cudaStream_t s);
 template <typename real>
+cudaError_t launch_feq_from_moments(const void* reps, const Tile* tiles, int ntiles, TileShape ts, const void* rhou,
+                                    const void* sigma, void* f, cudaStream_t s);
+template <typename real>
 cudaError_t launch_moments(const void* reps, const Tile* tiles, int ntiles, TileShape ts, const void* f,
                            void* rhou, cudaStream_t s);
 

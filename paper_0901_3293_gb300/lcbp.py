@@ -65,6 +65,18 @@ _SIGNATURES = {
     "lcbp_defect_fraction": (_c_int, [_P, _c_double, ctypes.POINTER(_c_double)]),
     "lcbp_save": (_c_int, [_P, ctypes.c_char_p]),
     "lcbp_load": (_c_int, [_P, ctypes.c_char_p]),
+    "lcbp_reequilibrate_f": (_c_int, [_P]),
+    "lcbp_surrogate_param_count": (_c_size_t, []),
+    "lcbp_surrogate_create": (_c_int, [_c_int, _c_int, _c_int, _c_int, ctypes.POINTER(_P)]),
+    "lcbp_surrogate_destroy": (_c_int, [_P]),
+    "lcbp_surrogate_set_scales": (_c_int, [_P, _c_double, _c_double]),
+    "lcbp_surrogate_set_params": (_c_int, [_P, _c_void_p, _c_size_t]),
+    "lcbp_surrogate_get_params": (_c_int, [_P, _c_void_p, _c_size_t]),
+    "lcbp_surrogate_get_grads": (_c_int, [_P, _c_void_p, _c_size_t]),
+    "lcbp_surrogate_forward": (_c_int, [_P, _c_void_p, _c_void_p, _c_double, _c_double, _c_int, _c_void_p]),
+    "lcbp_surrogate_step": (_c_int, [_P, _P, _c_double, _c_double, _c_int]),
+    "lcbp_surrogate_train_step": (_c_int, [_P, _c_void_p, _c_void_p, _c_double, _c_double, _c_void_p, _c_void_p,
+                                           _c_int, _c_double, ctypes.POINTER(_c_double)]),
     "lcbp_batch_create": (_c_int, [_c_int, ctypes.POINTER(_c_int), _c_void_p, _c_int, ctypes.POINTER(_P)]),
     "lcbp_batch_destroy": (_c_int, [_P]),
     "lcbp_batch_set_flow": (_c_int, [_P, _c_int, _c_int]),
@@ -277,6 +289,10 @@ class Lattice:
     def synchronize(self) -> None:
         check(lib().lcbp_synchronize(self._h))
 
+    def reequilibrate_f(self) -> "Lattice":
+        check(lib().lcbp_reequilibrate_f(self._h))
+        return self
+
     def _check_size(self, a, comps: int) -> None:
         if int(np.prod(a.shape)) != comps * self.n:
             raise LcbpError(EINVAL, f"expected {comps} x {self.n} values, got shape {tuple(a.shape)}")
@@ -427,3 +443,75 @@ class Batch:
                                         ctypes.byref(st)))
         return {"R": R.value, "sites": tot.value, "tile": tuple(tile), "persistent_ctas": ctas.value,
                 "step": st.value}
+
+
+class Surrogate:
+    """Convolutional surrogate advancing Q by 10 solver steps (tensor-core kernels)."""
+
+    def __init__(self, nx: int, ny: int, nz: int, training: bool = False):
+        self.dims = (int(nx), int(ny), int(nz))
+        self.n = self.dims[0] * self.dims[1] * self.dims[2]
+        self.count = int(lib().lcbp_surrogate_param_count())
+        self._h = _P()
+        check(lib().lcbp_surrogate_create(*self.dims, int(bool(training)), ctypes.byref(self._h)))
+
+    def close(self) -> None:
+        if self._h:
+            check(lib().lcbp_surrogate_destroy(self._h))
+            self._h = _P()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_scales(self, s_u: float, s_dq: float) -> "Surrogate":
+        check(lib().lcbp_surrogate_set_scales(self._h, s_u, s_dq))
+        return self
+
+    def set_params(self, v) -> "Surrogate":
+        a = np.ascontiguousarray(np.asarray(v, dtype=np.float32))
+        check(lib().lcbp_surrogate_set_params(self._h, a.ctypes.data, a.size))
+        return self
+
+    def get_params(self) -> np.ndarray:
+        a = np.empty(self.count, dtype=np.float32)
+        check(lib().lcbp_surrogate_get_params(self._h, a.ctypes.data, a.size))
+        return a
+
+    def get_grads(self) -> np.ndarray:
+        a = np.empty(self.count, dtype=np.float32)
+        check(lib().lcbp_surrogate_get_grads(self._h, a.ctypes.data, a.size))
+        return a
+
+    def forward(self, q5, u3, kappa: float, tau: float) -> np.ndarray:
+        pq, dq, kq = _ptr(q5)
+        pu = None
+        if u3 is not None:
+            pu, du, ku = _ptr(u3)
+            if du != dq:
+                raise TypeError("q5 and u3 must share a dtype")
+        nx, ny, nz = self.dims
+        out = np.empty((5, nz, ny, nx), dtype=np.float32)
+        check(lib().lcbp_surrogate_forward(self._h, pq, pu, kappa, tau, dq, out.ctypes.data))
+        return out
+
+    def step(self, lattice: "Lattice", kappa: float, tau: float, ncalls: int = 1) -> "Surrogate":
+        check(lib().lcbp_surrogate_step(self._h, lattice._h, kappa, tau, int(ncalls)))
+        return self
+
+    def train_step(self, q5, u3, kappa: float, tau: float, dq5, mask=None, lr: float = 1e-3) -> float:
+        pq, dq, kq = _ptr(q5)
+        pu = ku = None
+        if u3 is not None:
+            pu, du, ku = _ptr(u3)
+        pt, dt, kt = _ptr(dq5)
+        pm = km = None
+        if mask is not None:
+            pm, dm, km = _ptr(mask)
+        if len({dq, dt} | ({du} if u3 is not None else set()) | ({dm} if mask is not None else set())) != 1:
+            raise TypeError("all training buffers must share a dtype")
+        loss = _c_double()
+        check(lib().lcbp_surrogate_train_step(self._h, pq, pu, kappa, tau, pt, pm, dq, lr, ctypes.byref(loss)))
+        return loss.value

@@ -1,0 +1,105 @@
+"""Tensor-core surrogate kernels against the FP64 oracle of the network.
+
+The oracle rounds weights, inputs and stored activations / gradients to BF16
+exactly where the GPU stores them (the arithmetic stays FP64), so the
+comparison measures accumulation-order and FP32-epilogue differences only.
+"""
+
+import numpy as np
+import pytest
+
+from oracle import initial, lbq
+from oracle import surrogate as S
+from paper_0901_3293_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+BLOCKS = 4
+
+
+@pytest.fixture(scope="module")
+def lcbp():
+    import torch
+    from paper_0901_3293_gb300 import build
+    build.build()
+    from paper_0901_3293_gb300 import lcbp as L
+    torch.cuda.set_device(0)
+    return L
+
+
+def net_input(q5, u3, kappa, tau, s_u):
+    """Channels of the network input (the surrogate's definition)."""
+    x = np.zeros((10,) + q5.shape[1:])
+    x[:5] = q5
+    x[5:8] = u3 / s_u
+    x[8] = kappa - 1.0
+    x[9] = tau
+    return x
+
+
+def random_params(seed, scale=1.5):
+    return S.init_params(10, 32, 5, BLOCKS, np.random.default_rng(seed), scale=scale)
+
+
+@pytest.mark.parametrize("dims", [(16, 8, 6), (40, 12, 5), (32, 4, 1)])
+def test_forward_matches_oracle(lcbp, dims):
+    nx, ny, nz = dims
+    shape = (nz, ny, nx)
+    P = random_params(10)
+    q5 = synth.smooth_q5(shape, 0.3, 11) + synth.random_q5(shape, 0.05, 12)
+    u3 = synth.random_velocity(shape, 2e-4, 13)
+    sur = lcbp.Surrogate(nx, ny, nz)
+    sur.set_params(S.flatten(P, BLOCKS))
+    y = sur.forward(q5, u3, 1.3, -0.4)
+    x = net_input(q5, u3, 1.3, -0.4, 1e-3)
+    y_q, _ = S.forward(P, x, BLOCKS, quant=S.bf16)
+    y_e, _ = S.forward(P, x, BLOCKS)
+    scale = np.abs(y_e).max()
+    err_q = np.abs(y - y_q).max() / scale
+    err_e = np.abs(y - y_e).max() / scale
+    print(f"{dims}: max|y| {scale:.3e}, rel err vs BF16-rounding oracle {err_q:.2e}, vs FP64 {err_e:.2e}")
+    assert err_q < 1e-2 and err_e < 5e-2
+
+
+def test_training_gradients_match_oracle(lcbp):
+    nx, ny, nz = 32, 8, 6
+    shape = (nz, ny, nx)
+    P = random_params(20)
+    q5 = synth.smooth_q5(shape, 0.3, 21)
+    u3 = synth.random_velocity(shape, 2e-4, 22)
+    dq = synth.random_q5(shape, 5e-3, 23)
+    mask = (np.arange(nz)[:, None, None] * np.ones(shape) >= 1).astype(np.float64)
+    sur = lcbp.Surrogate(nx, ny, nz, training=True)
+    sur.set_params(S.flatten(P, BLOCKS))
+    loss = sur.train_step(q5, u3, 0.9, 0.2, dq, mask, lr=1e-6)
+    g = S.unflatten(sur.get_grads().astype(np.float64), P, BLOCKS)
+    x = net_input(q5, u3, 0.9, 0.2, 1e-3)
+    y, acts = S.forward(P, x, BLOCKS, quant=S.bf16)
+    loss_o, dout = S.masked_mse(y, dq / 1e-2, mask)
+    G, _ = S.backward(P, acts, dout, BLOCKS, quant=S.bf16)
+    assert abs(loss - loss_o) < 1e-3 * loss_o
+    for name in S.layer_names(BLOCKS):
+        for k in (0, 1):
+            ref = G[name][k]
+            rel = np.linalg.norm(g[name][k] - ref) / np.linalg.norm(ref)
+            print(name, "W" if k == 0 else "b", f"rel {rel:.2e}")
+            assert rel < 2e-2, (name, k, rel)
+    # Adam moved the parameters by about lr
+    step = sur.get_params().astype(np.float64) - S.flatten(P, BLOCKS)
+    assert 0 < np.abs(step).max() < 1.5e-6
+
+
+def test_surrogate_step_applies_prediction(lcbp):
+    nx, ny, nz = 32, 8, 8
+    p = lbq.Params()
+    lat = lcbp.Lattice(nx, ny, nz)
+    lat.init_q(lcbp.BPII, 0.3, noise=1e-3, seed=3).init_f_equilibrium(1.0).step(5)
+    q0 = lat.read_q(dtype=np.float32)
+    u0 = lat.read_u(dtype=np.float32)
+    sur = lcbp.Surrogate(nx, ny, nz)
+    sur.set_params(S.flatten(random_params(30, scale=1.0), BLOCKS))
+    y = sur.forward(q0, u0, 1.0, -0.5)
+    sur.step(lat, 1.0, -0.5, 1)
+    q1 = lat.read_q(dtype=np.float32)
+    assert np.abs(q1 - (q0 + 1e-2 * y)).max() < 1e-6
+    lat.reequilibrate_f().step(2)  # plain stepping resumes
+    assert np.isfinite(lat.free_energy())

@@ -89,3 +89,21 @@ def test_adam_first_step_moves_by_lr():
     w1, m, v = S.adam_update(w, g, np.zeros(3), np.zeros(3), 1, lr=1e-2)
     # bias-corrected first step: m_hat = g, v_hat = g^2 -> step = lr * sign(g)
     assert np.allclose(w1, w - 1e-2 * np.sign(g), atol=1e-7)
+
+
+def test_bf16_rounding_matches_library():
+    import torch
+    rng = np.random.default_rng(3)
+    x = np.concatenate([rng.normal(size=1000) * 10.0 ** rng.integers(-6, 6, size=1000),
+                        [1.0, 1.0 + 2 ** -8, 1.0 + 3 * 2 ** -8, -2.5, 0.0]])
+    want = torch.tensor(x, dtype=torch.float32).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(S.bf16(x), want)
+
+
+def test_flatten_roundtrip_and_count():
+    rng = np.random.default_rng(4)
+    P = S.init_params(10, 32, 5, 4, rng)
+    v = S.flatten(P, 4)
+    assert v.size == 27 * 10 * 32 + 32 + 8 * (27 * 32 * 32 + 32) + 27 * 32 * 5 + 5 == 234437
+    Q = S.unflatten(v, P, 4)
+    assert all(np.array_equal(P[k][0], Q[k][0]) and np.array_equal(P[k][1], Q[k][1]) for k in P)
