@@ -145,10 +145,18 @@ def evaluate(params, samples, depth: int = 64, s_u: float = 1e-3, s_dq: float = 
 
 
 class JudgedRun:
-    """Surrogate-accelerated time stepping with the plain solver as judge and fallback."""
+    """Surrogate-accelerated time stepping with the plain solver as judge and fallback.
+
+    Each segment of M calls starts from a device snapshot of (f, Q).  After the
+    segment f is re-equilibrated and the judge compares one surrogate call
+    with 10 plain steps from the same state; if the relative free-energy gap
+    exceeds tol (or the state is no longer finite) the segment is rolled back
+    and redone with plain steps.
+    """
 
     def __init__(self, lat: lcbp.Lattice, params, kappa: float, M: int = 50, tol: float = 1e-3,
                  s_u: float = 1e-3, s_dq: float = 1e-2):
+        import torch
         nx, ny, nz = lat.dims
         self.lat, self.kappa, self.M, self.tol, self.s_dq = lat, kappa, M, tol, s_dq
         self.sur = lcbp.Surrogate(nx, ny, nz)
@@ -159,49 +167,64 @@ class JudgedRun:
         self.plain_steps = 0
         self.fallbacks = 0
         self.judge_gaps = []
-        self.use_surrogate = True
+        self._f = torch.empty((15, nz, ny, nx), dtype=torch.float32, device="cuda")
+        self._q = torch.empty((5, nz, ny, nx), dtype=torch.float32, device="cuda")
+
+    def _log(self, log, log_every, next_log):
+        while next_log is not None and self.t >= next_log:
+            log.append((next_log, self.lat.free_energy()))
+            next_log += log_every
+        return next_log
 
     def advance(self, t_end: int, log_every: int | None = None, log=None):
-        """Advance to t_end; optionally record (t, F) every log_every steps."""
+        """Advance to t_end; optionally record (t, F) at multiples of log_every
+        (taken at the first segment boundary at or after each multiple)."""
         next_log = (self.t // log_every + 1) * log_every if log_every else None
         while self.t < t_end:
             seg = min(self.M * K_STEPS, t_end - self.t)
-            if self.use_surrogate and seg >= K_STEPS:
-                calls = seg // K_STEPS
-                for _ in range(calls):
-                    self.sur.step(self.lat, self.kappa, TAU_R, 1)
-                    self.t += K_STEPS
-                    self.surrogate_calls += 1
-                    if next_log and self.t >= next_log:
-                        log.append((self.t, self.lat.free_energy()))
-                        next_log += log_every
+            calls = seg // K_STEPS
+            if calls == 0:
+                self.lat.step(seg)
+                self.t += seg
+                self.plain_steps += seg
+                next_log = self._log(log, log_every, next_log)
+                continue
+            t0 = self.t
+            self.lat.read_f(out=self._f)
+            self.lat.read_q(out=self._q)
+            ok = True
+            try:
+                self.sur.step(self.lat, self.kappa, TAU_R, calls)
                 self.lat.reequilibrate_f()
-                self._judge()
+                ok = self._judge()
+            except lcbp.LcbpError:
+                ok = False
+            if ok:
+                self.surrogate_calls += calls
+                self.t = t0 + calls * K_STEPS + K_STEPS  # the judge's plain steps advance time too
+                self.plain_steps += K_STEPS
             else:
-                steps = seg
-                self.lat.step(steps)
-                self.t += steps
-                self.plain_steps += steps
-                self.use_surrogate = True  # try the surrogate again next segment
-                if next_log and self.t >= next_log:
-                    log.append((self.t, self.lat.free_energy()))
-                    next_log += log_every
+                self.fallbacks += 1
+                self.lat.set_f(self._f)
+                self.lat.set_q(self._q)
+                self.lat.step(calls * K_STEPS)
+                self.t = t0 + calls * K_STEPS
+                self.plain_steps += calls * K_STEPS
+            next_log = self._log(log, log_every, next_log)
 
-    def _judge(self):
+    def _judge(self) -> bool:
         """One surrogate call vs 10 plain steps from the same state."""
         q = self.lat.read_q(dtype=np.float32)
         u = self.lat.read_u(dtype=np.float32)
+        if not (np.isfinite(q).all() and np.isfinite(u).all()):
+            return False
         y = self.sur.forward(q, u, self.kappa, TAU_R)
         self.lat.step(K_STEPS)
-        self.t += K_STEPS
-        self.plain_steps += K_STEPS
         F_plain = self.lat.free_energy()
         F_pred = free_energy_of(self.lat.dims, self.kappa, q + self.s_dq * y)
         gap = abs(F_pred - F_plain) / abs(F_plain)
         self.judge_gaps.append(gap)
-        if gap > self.tol:
-            self.fallbacks += 1
-            self.use_surrogate = False
+        return bool(np.isfinite(gap) and gap <= self.tol)
 
     def close(self):
         self.sur.close()
@@ -262,9 +285,14 @@ def main():
     data = generate([0.5, 1.0, 2.0], args.data_steps, args.every)
     held = generate([1.5], args.data_steps, args.every * 5, seed=7)
     t_gen = time.perf_counter() - t0
+    import sys
     params, log = train(data, args.iters)
+    print(json.dumps({"train_s": log.seconds, "loss_first": float(np.mean(log.losses[:20])),
+                      "loss_last": float(np.mean(log.losses[-20:]))}), file=sys.stderr, flush=True)
     mse_net, mse_zero = evaluate(params, held)
+    print(json.dumps({"held_out_mse": [mse_net, mse_zero]}), file=sys.stderr, flush=True)
     t_sur, t_plain = time_call()
+    print(json.dumps({"call_ms": [t_sur, t_plain]}), file=sys.stderr, flush=True)
     # time to solution: plain vs judged surrogate run from the same initial state
     plain = slab_lattice(args.kappa)
     F_plain = []
@@ -292,6 +320,7 @@ def main():
         "run": {"steps": args.run_steps, "kappa": args.kappa, "plain_s": t_plain_run, "surrogate_s": t_hyb_run,
                 "surrogate_calls": run.surrogate_calls, "plain_steps": run.plain_steps,
                 "fallbacks": run.fallbacks, "max_rel_F_error": max(errs) if errs else None,
+                "judge_gap_median": float(np.median(run.judge_gaps)) if run.judge_gaps else None,
                 "final_F": {"plain": F_plain[-1][1], "surrogate": F_hyb[-1][1] if F_hyb else None}},
     }))
 
