@@ -324,6 +324,32 @@ LCBP_API int lcbp_batch_get_info(lcbp_batch *b, int *R, long long *total_sites, 
                                  long long *step);
 
 /* ------------------------------------------------------------------------
+ * Allocation-free free energy.  For callers that cannot allocate device
+ * memory when they need the free energy -- code running while its stream is
+ * being captured into a CUDA graph, code whose framework allocator owns the
+ * device heap, real-time loops that must not touch an allocator -- this
+ * computes F_h (as lcbp_free_energy) of a caller-owned device Q field without
+ * any cudaMalloc, cudaFree or other allocating call.  Its scratch, the
+ * per-block partial sums of the FP64 reduction (32.8 KB), is a fixed device
+ * array that every GPU loading the library holds until exit.
+ *   q5: device pointer, 5 * N values in the layout above (dtype LCBP_F32 or
+ *       LCBP_F64); A0, gamma, K, q0: as lcbp_set_ldg; stream: a cudaStream_t
+ *       (NULL = legacy default stream); *F receives the result (the call
+ *       synchronises the stream).
+ * The first call on a device looks up the array's device address on that
+ * device; make that first call before any stream capture begins.  All calls
+ * share the one array (its contents are those of the last call; every slot
+ * is rewritten by each call, so nothing needs clearing), hence calls that
+ * overlap on the GPU -- from several threads or streams at once -- race.
+ * Errors: LCBP_EINVAL (NULL pointers, bad dtype, sizes < 1, more than
+ * LCBP_NOALLOC_MAX_SITES sites), LCBP_ENONFINITE, LCBP_ECUDA.
+ * There is no counterpart of this call in the paper.
+ * ------------------------------------------------------------------------ */
+#define LCBP_NOALLOC_MAX_SITES (1LL << 31)
+LCBP_API int lcbp_free_energy_noalloc(const void *q5, int dtype, int nx, int ny, int nz, double A0, double gamma,
+                                      double K, double q0, void *stream, double *F);
+
+/* ------------------------------------------------------------------------
  * Learned surrogate (not part of the paper's method): a periodic 3x3x3
  * convolutional network that advances Q by k = 10 solver steps,
  *   x = [Q (5), u / s_u (3), kappa - 1, tau]  ->  h0 = relu(conv x),

@@ -66,6 +66,8 @@ _SIGNATURES = {
     "lcbp_save": (_c_int, [_P, ctypes.c_char_p]),
     "lcbp_load": (_c_int, [_P, ctypes.c_char_p]),
     "lcbp_reequilibrate_f": (_c_int, [_P]),
+    "lcbp_free_energy_noalloc": (_c_int, [_c_void_p, _c_int, _c_int, _c_int, _c_int, _c_double, _c_double,
+                                          _c_double, _c_double, _c_void_p, ctypes.POINTER(_c_double)]),
     "lcbp_surrogate_param_count": (_c_size_t, []),
     "lcbp_surrogate_create": (_c_int, [_c_int, _c_int, _c_int, _c_int, ctypes.POINTER(_P)]),
     "lcbp_surrogate_destroy": (_c_int, [_P]),
@@ -443,6 +445,20 @@ class Batch:
                                         ctypes.byref(st)))
         return {"R": R.value, "sites": tot.value, "tile": tuple(tile), "persistent_ctas": ctas.value,
                 "step": st.value}
+
+
+def free_energy_noalloc(q5_device, nx: int, ny: int, nz: int, A0: float, gamma: float, K: float, q0: float,
+                        stream=None) -> float:
+    """F_h of a device Q field without any device allocation (lcbp_free_energy_noalloc).
+
+    q5_device: a CUDA tensor of 5 * nx * ny * nz float32 or float64 values;
+    stream: a torch.cuda.Stream or None (legacy default stream)."""
+    F = _c_double()
+    dt = _dtype_code(q5_device)
+    sp = stream.cuda_stream if stream is not None else None
+    check(lib().lcbp_free_energy_noalloc(q5_device.data_ptr(), dt, nx, ny, nz, A0, gamma, K, q0, sp,
+                                         ctypes.byref(F)))
+    return F.value
 
 
 class Surrogate:
