@@ -231,6 +231,14 @@ LCBP_API int lcbp_set_path(lcbp_lattice *h, int path);
 LCBP_API int lcbp_get_path(lcbp_lattice *h, int *fast, int *planes_per_cta);
 
 /*
+ * Copy out the Beris-Edwards rate dQ/dt = R(Q, u) = Gamma H + S(W, Q) - u.grad Q
+ * of the current state (Sec. 2.1 Eq. Qevolution, mat_der; central differences,
+ * trace of S removed, u from f, or u = 0 with flow off): 5 * N values.
+ * Errors: LCBP_EINVAL, LCBP_ESTATE (flow on and f never initialised).
+ */
+LCBP_API int lcbp_read_rate(lcbp_lattice *h, void *dst, int dtype);
+
+/*
  * Reset f to the equilibrium f^eq(rho, u, sigma_LC(Q)) of the current moments
  * and the current Q (used when plain stepping resumes after Q was advanced
  * by other means, e.g. the learned surrogate).  Errors: LCBP_ESTATE.
@@ -351,10 +359,11 @@ LCBP_API int lcbp_free_energy_noalloc(const void *q5, int dtype, int nx, int ny,
 
 /* ------------------------------------------------------------------------
  * Learned surrogate (not part of the paper's method): a periodic 3x3x3
- * convolutional network that advances Q by k = 10 solver steps,
- *   x = [Q (5), u / s_u (3), kappa - 1, tau]  ->  h0 = relu(conv x),
+ * convolutional network that advances Q by k = 10 solver steps as a learned
+ * correction to ten explicit Euler steps of the Beris-Edwards rate R:
+ *   x = [Q (5), u / s_u (3), kappa - 1, tau, R / s_r (5)]  ->  h0 = relu(conv x),
  *   4 x { a = relu(conv h);  h = h + conv a },  y = conv h (5 channels),
- *   Q(t + 10) = Q(t) + s_dq * y,
+ *   Q(t + 10) = Q(t) + 10 R(t) + s_dq * y,
  * with 32 hidden channels, BF16 weights and activations and FP32
  * accumulation on tcgen05 tensor cores (forward and backward-data), FP32
  * weight gradients, masked MSE loss and Adam.  A surrogate object is built
@@ -365,29 +374,34 @@ LCBP_API int lcbp_free_energy_noalloc(const void *q5, int dtype, int nx, int ny,
  * ------------------------------------------------------------------------ */
 typedef struct lcbp_surrogate lcbp_surrogate;
 
-/* Number of FP32 values of the parameter vector (234437). */
+/* Number of FP32 values of the parameter vector (238757). */
 LCBP_API size_t lcbp_surrogate_param_count(void);
 /* Surrogate for an nx * ny * nz lattice; training != 0 also allocates the
  * activations, gradients and Adam state.  Parameters start at zero. */
 LCBP_API int lcbp_surrogate_create(int nx, int ny, int nz, int training, lcbp_surrogate **out);
 LCBP_API int lcbp_surrogate_destroy(lcbp_surrogate *s);
-/* Input velocity scale s_u (default 1e-3) and output scale s_dq (default 1e-2). */
-LCBP_API int lcbp_surrogate_set_scales(lcbp_surrogate *s, double s_u, double s_dq);
+/* Input scales s_u (velocity, default 1e-3) and s_r (rate, default 1e-3) and
+ * the output scale s_dq (default 1e-3). */
+LCBP_API int lcbp_surrogate_set_scales(lcbp_surrogate *s, double s_u, double s_r, double s_dq);
 /* Upload / download the parameter vector (host or device FP32; Adam state is reset on upload). */
 LCBP_API int lcbp_surrogate_set_params(lcbp_surrogate *s, const float *params, size_t count);
 LCBP_API int lcbp_surrogate_get_params(lcbp_surrogate *s, float *params, size_t count);
 /* Gradient of the last training step's loss, in the parameter-vector layout. */
 LCBP_API int lcbp_surrogate_get_grads(lcbp_surrogate *s, float *grads, size_t count);
-/* Network output y (5 * N values, [c][z][y][x]) for fields Q (5 * N), u (3 * N or NULL = 0). */
-LCBP_API int lcbp_surrogate_forward(lcbp_surrogate *s, const void *q5, const void *u3, double kappa, double tau,
-                                    int dtype, float *y5);
-/* ncalls times Q += s_dq * net(Q, u, kappa, tau) on a lattice of the same size (FP32 state).
- * f is left as it was: call lcbp_reequilibrate_f before plain stepping resumes. */
+/* Network output y (5 * N values, [c][z][y][x]) for fields Q (5 * N), u (3 * N,
+ * NULL = 0) and rate R (5 * N, NULL = 0) in the same dtype. */
+LCBP_API int lcbp_surrogate_forward(lcbp_surrogate *s, const void *q5, const void *u3, const void *r5, double kappa,
+                                    double tau, int dtype, float *y5);
+/* ncalls times: R = R(Q, u) of the lattice (FP32 state, same size), then
+ * Q += 10 R + s_dq * net(Q, u, kappa, tau, R).  u is not advanced and f is left
+ * as it was: call lcbp_reequilibrate_f before plain stepping resumes. */
 LCBP_API int lcbp_surrogate_step(lcbp_surrogate *s, lcbp_lattice *h, double kappa, double tau, int ncalls);
-/* One Adam step (learning rate lr) on the masked MSE between y and dq5 / s_dq
- * (dq5: target change of Q, 5 * N values; mask: N values or NULL); *loss receives the loss. */
-LCBP_API int lcbp_surrogate_train_step(lcbp_surrogate *s, const void *q5, const void *u3, double kappa, double tau,
-                                       const void *dq5, const void *mask, int dtype, double lr, double *loss);
+/* One Adam step (learning rate lr) on the masked MSE between y and
+ * (dq5 - 10 R) / s_dq (dq5: the true 10-step change of Q, 5 * N values; mask:
+ * N values or NULL); *loss receives the loss. */
+LCBP_API int lcbp_surrogate_train_step(lcbp_surrogate *s, const void *q5, const void *u3, const void *r5,
+                                       double kappa, double tau, const void *dq5, const void *mask, int dtype,
+                                       double lr, double *loss);
 
 #ifdef __cplusplus
 }

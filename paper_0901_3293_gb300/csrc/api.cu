@@ -1072,6 +1072,16 @@ int lcbp_load(lcbp_lattice* h, const char* path) {
   return LCBP_OK;
 }
 
+int lcbp_read_rate(lcbp_lattice* h, void* dst, int dtype) {
+  CHECK_H(h);
+  if (!dst || !valid_dtype(dtype)) return fail(LCBP_EINVAL, "bad buffer or dtype");
+  if (h->p.flow_on && !h->f_ready) return fail(LCBP_ESTATE, "initialise f first (u comes from f)");
+  StepArgs a = step_args(h);
+  cudaError_t e = h->dtype == LCBP_F64 ? launch_rate<double>(a, h->stream) : launch_rate<float>(a, h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "read_rate");
+  return transfer(h->qs, h->dtype, dst, dtype, 5 * h->n, false, h->staging, h->staging_elems, h->stream);
+}
+
 int lcbp_reequilibrate_f(lcbp_lattice* h) {
   CHECK_H(h);
   if (!h->f_ready) return fail(LCBP_ESTATE, "f was never initialised");
@@ -1089,6 +1099,20 @@ int lcbp_reequilibrate_f(lcbp_lattice* h) {
 }  // extern "C"
 
 namespace lcbp {
+// Beris-Edwards rate of a lattice into its predictor scratch; returns that
+// scratch (5 * N floats, valid until the lattice's next step)
+int lattice_rate(lcbp_lattice* h, const float** rate) {
+  if (!h) return fail(LCBP_EINVAL, "null lattice handle");
+  if (h->dtype != LCBP_F32) return fail(LCBP_EINVAL, "the surrogate works on FP32 lattice state");
+  cudaSetDevice(h->device);
+  StepArgs a = step_args(h);
+  cudaError_t e = launch_rate<float>(a, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "rate");
+  *rate = static_cast<const float*>(h->qs);
+  return LCBP_OK;
+}
+
 int lattice_fields(lcbp_lattice* h, float** q, const float** u, int dims[3], cudaStream_t* stream) {
   if (!h) return fail(LCBP_EINVAL, "null lattice handle");
   if (h->dtype != LCBP_F32) return fail(LCBP_EINVAL, "the surrogate works on FP32 lattice state");

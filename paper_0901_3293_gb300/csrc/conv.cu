@@ -212,7 +212,8 @@ __global__ void __launch_bounds__(kConvThreads) k_conv_tc(const __grid_constant_
         for (int q = 0; q < COUT / 4; ++q) op[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
       } else if (EPI & kEpiUpdateQ) {
 #pragma unroll
-        for (int c = 0; c < 5; ++c) a.qstate[c * a.n + site] += a.qscale * v[c];
+        for (int c = 0; c < 5; ++c)
+          a.qstate[c * a.n + site] += a.qscale * v[c] + (a.rate ? a.rate_scale * a.rate[c * a.n + site] : 0.f);
       } else {
         // BF16 channels-last with the periodic ghost images of boundary sites
         uint4 pk[COUT / 8];

@@ -14,7 +14,7 @@ enum : int {
   kEpiResid = 4,     // + resid (BF16, same padded layout as the output)
   kEpiMask = 8,      // * (mask > 0) with mask BF16 in the padded layout (ReLU backward)
   kEpiOutF32 = 16,   // write FP32 [site][C_out] (unpadded) instead of BF16
-  kEpiUpdateQ = 32,  // Q[c][site] += qscale * value for c < 5 (FP32 SoA lattice field)
+  kEpiUpdateQ = 32,  // Q[c][site] += qscale * value + rate_scale * rate[c][site], c < 5 (FP32 SoA)
 };
 
 struct ConvArgs {
@@ -27,6 +27,8 @@ struct ConvArgs {
   float* out_f32;           // [n][C_out]
   float* qstate;            // [5][n]
   float qscale;
+  const float* rate;        // [5][n]: kEpiUpdateQ adds rate_scale * rate too
+  float rate_scale;
   int* err;
 };
 

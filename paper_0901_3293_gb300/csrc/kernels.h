@@ -43,6 +43,9 @@ template <typename real>
 cudaError_t launch_step(const StepArgs& a, cudaStream_t s);
 template <typename real>
 cudaError_t launch_field(const StepArgs& a, cudaStream_t s);
+// Beris-Edwards rate R(Q, u) (u = 0 with flow off) written to a.qs
+template <typename real>
+cudaError_t launch_rate(const StepArgs& a, cudaStream_t s);
 
 // initial Q (kinds as in lcbp.h); per-replica q0 is in q0s[rep] (device array)
 struct InitQArgs {

@@ -338,4 +338,45 @@ cudaError_t launch_field(const StepArgs& a, cudaStream_t s) {
 template cudaError_t launch_field<float>(const StepArgs&, cudaStream_t);
 template cudaError_t launch_field<double>(const StepArgs&, cudaStream_t);
 
+// rate[c] = Q*[c] - Q[c] for the five components of every site of every replica
+template <typename real>
+__global__ void k_rate_from_predictor(const Replica<real>* __restrict__ reps, const Tile* __restrict__ tiles,
+                                      int ntiles, TileShape ts, const real* __restrict__ Q, real* __restrict__ Qs) {
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    Replica<real> R;
+    int x, y, z;
+    if (!tile_site(reps, tiles, t, ts, R, x, y, z)) continue;
+    const long long s = ((long long)z * R.ny + y) * R.nx + x;
+    const real* q = Q + 5 * R.base;
+    real* qs = Qs + 5 * R.base;
+#pragma unroll
+    for (int c = 0; c < 5; ++c) qs[c * R.n + s] -= q[c * R.n + s];
+  }
+}
+
+// Beris-Edwards rate R(Q^n, u^n) = Gamma H + S - u.grad Q into a.qs (Sec. 2.1
+// Eq. Qevolution, mat_der): the Heun predictor minus Q
+template <typename real>
+cudaError_t launch_rate(const StepArgs& a, cudaStream_t s) {
+  const auto* reps = static_cast<const Replica<real>*>(a.reps);
+  const int threads = a.ts.tx * a.ts.ty * a.ts.tz;
+  auto Rp = [](void* p) { return static_cast<real*>(p); };
+  auto Cp = [](const void* p) { return static_cast<const real*>(p); };
+  if (a.flow_on) {
+    k_field<real, true><<<a.ntiles, threads, 0, s>>>(reps, a.tiles, a.ntiles, a.ts, Cp(a.q), Rp(a.h), Rp(a.sigma),
+                                                      Rp(a.tau));
+    k_force_predict<real, true, false, true, false><<<a.ntiles, threads, 0, s>>>(
+        reps, a.tiles, a.ntiles, a.ts, Cp(a.q), Cp(a.h), nullptr, Cp(a.rhou), nullptr, nullptr, Rp(a.qs));
+  } else {
+    k_field<real, false><<<a.ntiles, threads, 0, s>>>(reps, a.tiles, a.ntiles, a.ts, Cp(a.q), Rp(a.h), nullptr,
+                                                       nullptr);
+    k_force_predict<real, false, false, true, false><<<a.ntiles, threads, 0, s>>>(
+        reps, a.tiles, a.ntiles, a.ts, Cp(a.q), Cp(a.h), nullptr, nullptr, nullptr, nullptr, Rp(a.qs));
+  }
+  k_rate_from_predictor<real><<<a.ntiles, threads, 0, s>>>(reps, a.tiles, a.ntiles, a.ts, Cp(a.q), Rp(a.qs));
+  return cudaGetLastError();
+}
+template cudaError_t launch_rate<float>(const StepArgs&, cudaStream_t);
+template cudaError_t launch_rate<double>(const StepArgs&, cudaStream_t);
+
 }  // namespace lcbp

@@ -25,6 +25,7 @@ using namespace lcbp;
 namespace lcbp {
 // lattice internals needed by the surrogate step (api.cu)
 int lattice_fields(lcbp_lattice* h, float** q, const float** u, int dims[3], cudaStream_t* stream);
+int lattice_rate(lcbp_lattice* h, const float** rate);
 }
 
 namespace {
@@ -32,7 +33,8 @@ namespace {
 constexpr int kBlocks = 4;
 constexpr int kLayers = 2 + 2 * kBlocks;
 constexpr int kWidth = 32;
-constexpr int kInC = 10, kOutC = 5, kPadC = 16;
+constexpr int kInC = 15, kOutC = 5, kPadC = 16;
+constexpr float kSteps = 10.f;  // solver steps per call
 
 struct LayerDim {
   int cin, cout;          // true channels
@@ -57,9 +59,10 @@ size_t true_param_count() {
 // ---------------------------------------------------------------------------
 // kernels
 // ---------------------------------------------------------------------------
-// network input from physical fields: Q [5][n], u [3][n] (FP32) -> padded BF16 [.][16]
-__global__ void k_sur_input(const float* __restrict__ q, const float* __restrict__ u, float su, float kap, float tau,
-                            int nx, int ny, int nz, __nv_bfloat16* __restrict__ out) {
+// network input from physical fields: Q [5][n], u [3][n], R [5][n] (FP32) -> padded BF16 [.][16]
+__global__ void k_sur_input(const float* __restrict__ q, const float* __restrict__ u, const float* __restrict__ r,
+                            float su, float sr, float kap, float tau, int nx, int ny, int nz,
+                            __nv_bfloat16* __restrict__ out) {
   const long long n = (long long)nx * ny * nz;
   const int px = nx + 2, py = ny + 2, pz = nz + 2;
   const long long np = (long long)px * py * pz;
@@ -75,7 +78,8 @@ __global__ void k_sur_input(const float* __restrict__ q, const float* __restrict
     v[8] = kap - 1.f;
     v[9] = tau;
 #pragma unroll
-    for (int c = 10; c < 16; ++c) v[c] = 0.f;
+    for (int c = 0; c < 5; ++c) v[10 + c] = r ? r[c * n + s] / sr : 0.f;
+    v[15] = 0.f;
     uint4 pk[2];
 #pragma unroll
     for (int q2 = 0; q2 < 2; ++q2) {
@@ -91,11 +95,12 @@ __global__ void k_sur_input(const float* __restrict__ q, const float* __restrict
 
 // u of a lattice: rho u stored as [drho, ux, uy, uz] -> pointer to ux..uz given by caller
 
-// masked MSE on y (FP32 [n][16], first 5 channels) against target/s_dq (FP32 [5][n]);
-// writes the BF16 padded gradient d loss / d y and per-block partial sums
+// masked MSE on y (FP32 [n][16], first 5 channels) against (dq - 10 R) / s_dq
+// (FP32 [5][n]); writes the BF16 padded gradient d loss / d y and per-block partial sums
 __global__ void k_sur_loss(const float* __restrict__ y, const float* __restrict__ target,
-                           const float* __restrict__ mask, float inv_sdq, double inv_den, int nx, int ny, int nz,
-                           __nv_bfloat16* __restrict__ grad, double* __restrict__ partial) {
+                           const float* __restrict__ rate, const float* __restrict__ mask, float inv_sdq,
+                           double inv_den, int nx, int ny, int nz, __nv_bfloat16* __restrict__ grad,
+                           double* __restrict__ partial) {
   const long long n = (long long)nx * ny * nz;
   const int px = nx + 2, py = ny + 2, pz = nz + 2;
   const long long np = (long long)px * py * pz;
@@ -111,7 +116,8 @@ __global__ void k_sur_loss(const float* __restrict__ y, const float* __restrict_
     for (int c = 0; c < 16; ++c) g[c] = 0.f;
 #pragma unroll
     for (int c = 0; c < 5; ++c) {
-      const float d = y[s * 16 + c] - target[c * n + s] * inv_sdq;
+      const float tc = target[c * n + s] - (rate ? kSteps * rate[c * n + s] : 0.f);
+      const float d = y[s * 16 + c] - tc * inv_sdq;
       g[c] = (float)(2.0 * w * d * inv_den);
       if (interior) acc += (double)w * d * d;
     }
@@ -325,7 +331,7 @@ struct lcbp_surrogate {
   int training;
   int device;
   cudaStream_t stream;
-  float su, sdq;
+  float su, sr, sdq;
   int max_ctas;
   // parameters: FP32 master (padded) per layer, BF16 forward / backward copies
   float* master;  // all layers, padded
@@ -342,6 +348,7 @@ struct lcbp_surrogate {
   float* msk;     // [n]
   float* qin;     // [5][n] staging of input Q
   float* uin;     // [3][n] staging of input u
+  float* rin;     // [5][n] staging of input R
   float *grad, *adam_m, *adam_v;
   double *partial, *dloss, *h_loss;
   int* d_err;
@@ -380,8 +387,9 @@ ConvArgs cargs(lcbp_surrogate* s) {
   return a;
 }
 
-// forward pass from s->X; the final layer either writes y16 or updates q
-cudaError_t forward(lcbp_surrogate* s, float* qupdate) {
+// forward pass from s->X; the final layer either writes y16 or updates q (with
+// the 10 R baseline from `rate`)
+cudaError_t forward(lcbp_surrogate* s, float* qupdate, const float* rate = nullptr) {
   cudaError_t e;
   ConvArgs a = cargs(s);
   // h0 = relu(conv_in x)
@@ -413,6 +421,8 @@ cudaError_t forward(lcbp_surrogate* s, float* qupdate) {
   if (qupdate) {
     a.qstate = qupdate;
     a.qscale = s->sdq;
+    a.rate = rate;
+    a.rate_scale = kSteps;
     return conv_launch(32, 16, kEpiBias | kEpiUpdateQ, s->tmH[hlast], s->tmWf[kLayers - 1], a, s->max_ctas,
                        s->stream);
   }
@@ -449,11 +459,12 @@ int sync_err(lcbp_surrogate* s, const char* what) {
 
 // stage caller fields (host or device, f32/f64) into s->qin / s->uin
 // (the staging buffer holds 5 n floats = 5 n / 2 doubles)
-int stage_inputs(lcbp_surrogate* s, const void* q5, const void* u3, int dtype) {
+int stage_inputs(lcbp_surrogate* s, const void* q5, const void* u3, const void* r5, int dtype) {
   const long long st = 5 * s->n / 2;
   int rc = transfer(s->qin, LCBP_F32, const_cast<void*>(q5), dtype, 5 * s->n, true, s->tgt, st, s->stream);
   if (rc) return rc;
   if (u3) rc = transfer(s->uin, LCBP_F32, const_cast<void*>(u3), dtype, 3 * s->n, true, s->tgt, st, s->stream);
+  if (!rc && r5) rc = transfer(s->rin, LCBP_F32, const_cast<void*>(r5), dtype, 5 * s->n, true, s->tgt, st, s->stream);
   return rc;
 }
 
@@ -476,7 +487,8 @@ int lcbp_surrogate_create(int nx, int ny, int nz, int training, lcbp_surrogate**
   s->np = (long long)(nx + 2) * (ny + 2) * (nz + 2);
   s->training = training ? 1 : 0;
   s->su = 1e-3f;
-  s->sdq = 1e-2f;
+  s->sr = 1e-3f;
+  s->sdq = 1e-3f;
   cudaGetDevice(&s->device);
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
@@ -514,6 +526,7 @@ int lcbp_surrogate_create(int nx, int ny, int nz, int training, lcbp_surrogate**
   A((void**)&s->tgt, (size_t)s->n * 5 * 4);
   A((void**)&s->qin, (size_t)s->n * 5 * 4);
   A((void**)&s->uin, (size_t)s->n * 3 * 4);
+  A((void**)&s->rin, (size_t)s->n * 5 * 4);
   A((void**)&s->partial, 4096 * 8 + 64);
   A((void**)&s->d_err, 64);
   if (s->training) {
@@ -576,11 +589,12 @@ int lcbp_surrogate_destroy(lcbp_surrogate* s) {
   return LCBP_OK;
 }
 
-int lcbp_surrogate_set_scales(lcbp_surrogate* s, double s_u, double s_dq) {
+int lcbp_surrogate_set_scales(lcbp_surrogate* s, double s_u, double s_r, double s_dq) {
   int rc = check_s(s);
   if (rc) return rc;
-  if (!(s_u > 0) || !(s_dq > 0)) return fail(LCBP_EINVAL, "scales must be > 0");
+  if (!(s_u > 0) || !(s_r > 0) || !(s_dq > 0)) return fail(LCBP_EINVAL, "scales must be > 0");
   s->su = (float)s_u;
+  s->sr = (float)s_r;
   s->sdq = (float)s_dq;
   return LCBP_OK;
 }
@@ -661,15 +675,15 @@ int lcbp_surrogate_get_grads(lcbp_surrogate* s, float* g, size_t count) {
   return e == cudaSuccess ? LCBP_OK : cuda_fail(e, "get_grads");
 }
 
-int lcbp_surrogate_forward(lcbp_surrogate* s, const void* q5, const void* u3, double kappa, double tau, int dtype,
-                           float* y5) {
+int lcbp_surrogate_forward(lcbp_surrogate* s, const void* q5, const void* u3, const void* r5, double kappa,
+                           double tau, int dtype, float* y5) {
   int rc = check_s(s);
   if (rc) return rc;
   if (!q5 || !y5 || !valid_dtype(dtype)) return fail(LCBP_EINVAL, "bad buffers or dtype");
-  rc = stage_inputs(s, q5, u3, dtype);
+  rc = stage_inputs(s, q5, u3, r5, dtype);
   if (rc) return rc;
-  k_sur_input<<<grid_for(s->np), 256, 0, s->stream>>>(s->qin, u3 ? s->uin : nullptr, s->su, (float)kappa, (float)tau,
-                                                      s->nx, s->ny, s->nz, s->X);
+  k_sur_input<<<grid_for(s->np), 256, 0, s->stream>>>(s->qin, u3 ? s->uin : nullptr, r5 ? s->rin : nullptr, s->su,
+                                                      s->sr, (float)kappa, (float)tau, s->nx, s->ny, s->nz, s->X);
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) e = forward(s, nullptr);
   if (e == cudaSuccess) {
@@ -697,22 +711,26 @@ int lcbp_surrogate_step(lcbp_surrogate* s, lcbp_lattice* h, double kappa, double
                 dims[2]);
   cudaError_t e = cudaStreamSynchronize(hs);  // lattice work done before the surrogate touches Q
   for (int c = 0; c < ncalls && e == cudaSuccess; ++c) {
-    k_sur_input<<<grid_for(s->np), 256, 0, s->stream>>>(q, u, s->su, (float)kappa, (float)tau, s->nx, s->ny, s->nz,
-                                                        s->X);
+    const float* r = nullptr;
+    rc = lattice_rate(h, &r);  // FP32 rate of the current Q (synchronises the lattice stream)
+    if (rc) return rc;
+    k_sur_input<<<grid_for(s->np), 256, 0, s->stream>>>(q, u, r, s->su, s->sr, (float)kappa, (float)tau, s->nx,
+                                                        s->ny, s->nz, s->X);
     e = cudaGetLastError();
-    if (e == cudaSuccess) e = forward(s, q);
+    if (e == cudaSuccess) e = forward(s, q, r);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);  // Q updated before the next rate
   }
   if (e != cudaSuccess) return cuda_fail(e, "surrogate step");
   return sync_err(s, "surrogate step");
 }
 
-int lcbp_surrogate_train_step(lcbp_surrogate* s, const void* q5, const void* u3, double kappa, double tau,
-                              const void* dq5, const void* mask, int dtype, double lr, double* loss) {
+int lcbp_surrogate_train_step(lcbp_surrogate* s, const void* q5, const void* u3, const void* r5, double kappa,
+                              double tau, const void* dq5, const void* mask, int dtype, double lr, double* loss) {
   int rc = check_s(s);
   if (rc) return rc;
   if (!s->training) return fail(LCBP_ESTATE, "surrogate was created without training buffers");
   if (!q5 || !dq5 || !valid_dtype(dtype) || !(lr > 0)) return fail(LCBP_EINVAL, "bad arguments");
-  rc = stage_inputs(s, q5, u3, dtype);
+  rc = stage_inputs(s, q5, u3, r5, dtype);
   if (!rc) rc = transfer(s->tgt, LCBP_F32, const_cast<void*>(dq5), dtype, 5 * s->n, true, s->y16, 8 * s->n, s->stream);
   if (!rc && mask) rc = transfer(s->msk, LCBP_F32, const_cast<void*>(mask), dtype, s->n, true, s->y16, 8 * s->n, s->stream);
   if (rc) return rc;
@@ -729,14 +747,14 @@ int lcbp_surrogate_train_step(lcbp_surrogate* s, const void* q5, const void* u3,
     if (!(den > 0)) return fail(LCBP_EINVAL, "mask is empty");
   }
   cudaError_t e = cudaSuccess;
-  k_sur_input<<<grid_for(s->np), 256, 0, s->stream>>>(s->qin, u3 ? s->uin : nullptr, s->su, (float)kappa, (float)tau,
-                                                      s->nx, s->ny, s->nz, s->X);
+  k_sur_input<<<grid_for(s->np), 256, 0, s->stream>>>(s->qin, u3 ? s->uin : nullptr, r5 ? s->rin : nullptr, s->su,
+                                                      s->sr, (float)kappa, (float)tau, s->nx, s->ny, s->nz, s->X);
   e = cudaGetLastError();
   if (e == cudaSuccess) e = forward(s, nullptr);
   const int lb = 1024;
   if (e == cudaSuccess) {
-    k_sur_loss<<<lb, 256, 0, s->stream>>>(s->y16, s->tgt, mask ? s->msk : nullptr, 1.f / s->sdq, 1.0 / den, s->nx,
-                                           s->ny, s->nz, s->G16, s->partial);
+    k_sur_loss<<<lb, 256, 0, s->stream>>>(s->y16, s->tgt, r5 ? s->rin : nullptr, mask ? s->msk : nullptr,
+                                           1.f / s->sdq, 1.0 / den, s->nx, s->ny, s->nz, s->G16, s->partial);
     k_sum<<<1, 32, 0, s->stream>>>(s->partial, lb, 1.0 / den, s->dloss);
     k_zero<<<256, 256, 0, s->stream>>>(s->grad, (long long)s->master_count);
     e = cudaGetLastError();

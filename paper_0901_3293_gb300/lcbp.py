@@ -71,14 +71,16 @@ _SIGNATURES = {
     "lcbp_surrogate_param_count": (_c_size_t, []),
     "lcbp_surrogate_create": (_c_int, [_c_int, _c_int, _c_int, _c_int, ctypes.POINTER(_P)]),
     "lcbp_surrogate_destroy": (_c_int, [_P]),
-    "lcbp_surrogate_set_scales": (_c_int, [_P, _c_double, _c_double]),
+    "lcbp_surrogate_set_scales": (_c_int, [_P, _c_double, _c_double, _c_double]),
     "lcbp_surrogate_set_params": (_c_int, [_P, _c_void_p, _c_size_t]),
     "lcbp_surrogate_get_params": (_c_int, [_P, _c_void_p, _c_size_t]),
     "lcbp_surrogate_get_grads": (_c_int, [_P, _c_void_p, _c_size_t]),
-    "lcbp_surrogate_forward": (_c_int, [_P, _c_void_p, _c_void_p, _c_double, _c_double, _c_int, _c_void_p]),
+    "lcbp_surrogate_forward": (_c_int, [_P, _c_void_p, _c_void_p, _c_void_p, _c_double, _c_double, _c_int,
+                                        _c_void_p]),
     "lcbp_surrogate_step": (_c_int, [_P, _P, _c_double, _c_double, _c_int]),
-    "lcbp_surrogate_train_step": (_c_int, [_P, _c_void_p, _c_void_p, _c_double, _c_double, _c_void_p, _c_void_p,
-                                           _c_int, _c_double, ctypes.POINTER(_c_double)]),
+    "lcbp_surrogate_train_step": (_c_int, [_P, _c_void_p, _c_void_p, _c_void_p, _c_double, _c_double, _c_void_p,
+                                           _c_void_p, _c_int, _c_double, ctypes.POINTER(_c_double)]),
+    "lcbp_read_rate": (_c_int, [_P, _c_void_p, _c_int]),
     "lcbp_batch_create": (_c_int, [_c_int, ctypes.POINTER(_c_int), _c_void_p, _c_int, ctypes.POINTER(_P)]),
     "lcbp_batch_destroy": (_c_int, [_P]),
     "lcbp_batch_set_flow": (_c_int, [_P, _c_int, _c_int]),
@@ -320,6 +322,10 @@ class Lattice:
     def read_f(self, dtype=np.float64, out=None):
         return self._read(lib().lcbp_read_f, 15, dtype, out)
 
+    def read_rate(self, dtype=np.float64, out=None):
+        """Beris-Edwards rate dQ/dt = Gamma H + S - u.grad Q of the current state."""
+        return self._read(lib().lcbp_read_rate, 5, dtype, out)
+
     # -- diagnostics ------------------------------------------------------------
     def free_energy(self) -> float:
         F = _c_double()
@@ -482,8 +488,8 @@ class Surrogate:
         except Exception:
             pass
 
-    def set_scales(self, s_u: float, s_dq: float) -> "Surrogate":
-        check(lib().lcbp_surrogate_set_scales(self._h, s_u, s_dq))
+    def set_scales(self, s_u: float = 1e-3, s_r: float = 1e-3, s_dq: float = 1e-3) -> "Surrogate":
+        check(lib().lcbp_surrogate_set_scales(self._h, s_u, s_r, s_dq))
         return self
 
     def set_params(self, v) -> "Surrogate":
@@ -501,33 +507,36 @@ class Surrogate:
         check(lib().lcbp_surrogate_get_grads(self._h, a.ctypes.data, a.size))
         return a
 
-    def forward(self, q5, u3, kappa: float, tau: float) -> np.ndarray:
+    @staticmethod
+    def _opt(a, dt):
+        if a is None:
+            return None, None
+        p, d, keep = _ptr(a)
+        if d != dt:
+            raise TypeError("all field buffers must share a dtype")
+        return p, keep
+
+    def forward(self, q5, u3, r5, kappa: float, tau: float) -> np.ndarray:
+        """Network output y for fields Q, u (or None), rate R (or None)."""
         pq, dq, kq = _ptr(q5)
-        pu = None
-        if u3 is not None:
-            pu, du, ku = _ptr(u3)
-            if du != dq:
-                raise TypeError("q5 and u3 must share a dtype")
+        pu, ku = self._opt(u3, dq)
+        pr, kr = self._opt(r5, dq)
         nx, ny, nz = self.dims
         out = np.empty((5, nz, ny, nx), dtype=np.float32)
-        check(lib().lcbp_surrogate_forward(self._h, pq, pu, kappa, tau, dq, out.ctypes.data))
+        check(lib().lcbp_surrogate_forward(self._h, pq, pu, pr, kappa, tau, dq, out.ctypes.data))
         return out
 
     def step(self, lattice: "Lattice", kappa: float, tau: float, ncalls: int = 1) -> "Surrogate":
         check(lib().lcbp_surrogate_step(self._h, lattice._h, kappa, tau, int(ncalls)))
         return self
 
-    def train_step(self, q5, u3, kappa: float, tau: float, dq5, mask=None, lr: float = 1e-3) -> float:
+    def train_step(self, q5, u3, r5, kappa: float, tau: float, dq5, mask=None, lr: float = 1e-3) -> float:
+        """One Adam step; dq5 is the true 10-step change of Q."""
         pq, dq, kq = _ptr(q5)
-        pu = ku = None
-        if u3 is not None:
-            pu, du, ku = _ptr(u3)
-        pt, dt, kt = _ptr(dq5)
-        pm = km = None
-        if mask is not None:
-            pm, dm, km = _ptr(mask)
-        if len({dq, dt} | ({du} if u3 is not None else set()) | ({dm} if mask is not None else set())) != 1:
-            raise TypeError("all training buffers must share a dtype")
+        pu, ku = self._opt(u3, dq)
+        pr, kr = self._opt(r5, dq)
+        pt, kt = self._opt(dq5, dq)
+        pm, km = self._opt(mask, dq)
         loss = _c_double()
-        check(lib().lcbp_surrogate_train_step(self._h, pq, pu, kappa, tau, pt, pm, dq, lr, ctypes.byref(loss)))
+        check(lib().lcbp_surrogate_train_step(self._h, pq, pu, pr, kappa, tau, pt, pm, dq, lr, ctypes.byref(loss)))
         return loss.value

@@ -13,8 +13,11 @@ kernels, loss and Adam); this module only orchestrates:
 * ``JudgedRun``: advances a lattice with the surrogate in segments of M calls
   (10 steps each).  After each segment the judge re-equilibrates f, runs 10
   plain steps from the surrogate state and compares the free energy with one
-  surrogate call from the same state; a relative gap above ``tol`` switches
-  the next segment to plain stepping.
+  surrogate call from the same state; a relative gap above ``tol`` rolls the
+  segment back and redoes it with plain steps.
+
+The surrogate predicts a correction to ten explicit Euler steps of the exact
+FP32 Beris-Edwards rate R(Q, u): Q(t + 10) = Q + 10 R + s_dq * net(Q, u, kappa, tau, R).
 """
 
 from __future__ import annotations
@@ -47,26 +50,28 @@ def slab_lattice(kappa: float, seed: int = 20090119, shape=(64, 64, 256)) -> lcb
 class Sample:
     q: np.ndarray  # [5, z, y, x] float32 at t
     u: np.ndarray  # [3, z, y, x]
+    r: np.ndarray  # Beris-Edwards rate at t
     dq: np.ndarray  # Q(t + 10) - Q(t)
     kappa: float
     t: int
 
 
-def generate(kappas, steps: int, every: int, seed: int = 20090119, shape=(64, 64, 256)):
-    """Plain runs; returns the list of (state, 10-step change) samples."""
+def generate(kappas, steps: int, every: int, t_min: int = 0, seed: int = 20090119, shape=(64, 64, 256)):
+    """Plain runs; a sample (state, rate, 10-step change) every `every` steps from t_min."""
     out = []
     for i, kappa in enumerate(kappas):
         lat = slab_lattice(kappa, seed + i, shape)
-        t = 0
+        lat.step(t_min)
+        t = t_min
         while t + K_STEPS <= steps:
-            lat.step(every - K_STEPS if t else 0)
-            t += every - K_STEPS if t else 0
             q0 = lat.read_q(dtype=np.float32)
             u0 = lat.read_u(dtype=np.float32)
+            r0 = lat.read_rate(dtype=np.float32)
             lat.step(K_STEPS)
             q1 = lat.read_q(dtype=np.float32)
-            out.append(Sample(q0, u0, q1 - q0, float(kappa), t))
-            t += K_STEPS
+            out.append(Sample(q0, u0, r0, q1 - q0, float(kappa), t))
+            lat.step(every - K_STEPS)
+            t += every
         lat.close()
     return out
 
@@ -75,10 +80,11 @@ def crop(s: Sample, z0: int, depth: int):
     nz = s.q.shape[1]
     idx = np.arange(z0, z0 + depth) % nz
     mask = np.ones((depth,) + s.q.shape[2:], dtype=np.float32)
-    mask[:RECEPTIVE] = 0.0
-    mask[depth - RECEPTIVE:] = 0.0
+    if depth < nz:
+        mask[:RECEPTIVE] = 0.0
+        mask[depth - RECEPTIVE:] = 0.0
     return (np.ascontiguousarray(s.q[:, idx]), np.ascontiguousarray(s.u[:, idx]),
-            np.ascontiguousarray(s.dq[:, idx]), mask)
+            np.ascontiguousarray(s.r[:, idx]), np.ascontiguousarray(s.dq[:, idx]), mask)
 
 
 @dataclass
@@ -88,13 +94,15 @@ class TrainLog:
     iters: int = 0
 
 
-def train(samples, iters: int, lr: float = 1e-3, depth: int = 64, seed: int = 0, params=None,
-          s_u: float = 1e-3, s_dq: float = 1e-2):
+S_U, S_R, S_DQ = 1e-3, 1e-3, 1e-3
+
+
+def train(samples, iters: int, lr: float = 1e-3, depth: int = 64, seed: int = 0, params=None):
     """Adam on random crops; returns (parameter vector, TrainLog)."""
     rng = np.random.default_rng(seed)
     nx, ny = samples[0].q.shape[3], samples[0].q.shape[2]
     sur = lcbp.Surrogate(nx, ny, depth, training=True)
-    sur.set_scales(s_u, s_dq)
+    sur.set_scales(S_U, S_R, S_DQ)
     if params is None:
         params = init_params(rng)
     sur.set_params(params)
@@ -103,9 +111,9 @@ def train(samples, iters: int, lr: float = 1e-3, depth: int = 64, seed: int = 0,
     for it in range(iters):
         s = samples[rng.integers(len(samples))]
         z0 = int(rng.integers(s.q.shape[1]))
-        q, u, dq, mask = crop(s, z0, depth)
-        lr_it = lr if it < iters // 2 else lr * 0.3
-        log.losses.append(sur.train_step(q, u, s.kappa, TAU_R, dq, mask, lr=lr_it))
+        q, u, r, dq, mask = crop(s, z0, depth)
+        lr_it = lr if it < iters // 2 else (lr * 0.3 if it < 3 * iters // 4 else lr * 0.1)
+        log.losses.append(sur.train_step(q, u, r, s.kappa, TAU_R, dq, mask, lr=lr_it))
     log.seconds = time.perf_counter() - t0
     log.iters = iters
     p = sur.get_params()
@@ -117,7 +125,7 @@ def init_params(rng, blocks: int = 4, width: int = 32):
     """He-normal weights; the last layer and the second conv of each block start
     small so the untrained network is close to persistence (dQ = 0)."""
     parts = []
-    dims = [(10, width)] + [(width, width)] * (2 * blocks) + [(width, 5)]
+    dims = [(15, width)] + [(width, width)] * (2 * blocks) + [(width, 5)]
     for i, (ci, co) in enumerate(dims):
         std = np.sqrt(2.0 / (27 * ci))
         if i == len(dims) - 1 or (i > 0 and i % 2 == 0):
@@ -126,22 +134,25 @@ def init_params(rng, blocks: int = 4, width: int = 32):
     return np.concatenate(parts).astype(np.float32)
 
 
-def evaluate(params, samples, depth: int = 64, s_u: float = 1e-3, s_dq: float = 1e-2):
-    """Mean masked MSE of the 10-step change on the given samples, for the
-    network and for persistence (dQ = 0, the method without the network)."""
+def evaluate(params, samples, depth: int = 64):
+    """Mean masked MSE of the predicted 10-step change on the given samples for
+    the network, for ten Euler steps of the rate (the integrator the network
+    corrects) and for persistence (dQ = 0)."""
     nx, ny = samples[0].q.shape[3], samples[0].q.shape[2]
     sur = lcbp.Surrogate(nx, ny, depth)
-    sur.set_scales(s_u, s_dq)
+    sur.set_scales(S_U, S_R, S_DQ)
     sur.set_params(params)
-    err_net, err_zero = [], []
+    err = {"network": [], "euler10": [], "persistence": []}
     for s in samples:
-        q, u, dq, mask = crop(s, 0, depth)
-        y = sur.forward(q, u, s.kappa, TAU_R) * s_dq
+        q, u, r, dq, mask = crop(s, 0, depth)
+        pred = 10.0 * r + S_DQ * sur.forward(q, u, r, s.kappa, TAU_R)
         w = mask[None]
-        err_net.append(float((w * (y - dq) ** 2).sum() / (5 * w.sum())))
-        err_zero.append(float((w * dq ** 2).sum() / (5 * w.sum())))
+        den = 5 * w.sum()
+        err["network"].append(float((w * (pred - dq) ** 2).sum() / den))
+        err["euler10"].append(float((w * (10.0 * r - dq) ** 2).sum() / den))
+        err["persistence"].append(float((w * dq ** 2).sum() / den))
     sur.close()
-    return float(np.mean(err_net)), float(np.mean(err_zero))
+    return {k: float(np.mean(v)) for k, v in err.items()}
 
 
 class JudgedRun:
@@ -154,13 +165,12 @@ class JudgedRun:
     and redone with plain steps.
     """
 
-    def __init__(self, lat: lcbp.Lattice, params, kappa: float, M: int = 50, tol: float = 1e-3,
-                 s_u: float = 1e-3, s_dq: float = 1e-2):
+    def __init__(self, lat: lcbp.Lattice, params, kappa: float, M: int = 49, tol: float = 1e-3):
         import torch
         nx, ny, nz = lat.dims
-        self.lat, self.kappa, self.M, self.tol, self.s_dq = lat, kappa, M, tol, s_dq
+        self.lat, self.kappa, self.M, self.tol = lat, kappa, M, tol
         self.sur = lcbp.Surrogate(nx, ny, nz)
-        self.sur.set_scales(s_u, s_dq)
+        self.sur.set_scales(S_U, S_R, S_DQ)
         self.sur.set_params(params)
         self.t = 0
         self.surrogate_calls = 0
@@ -216,12 +226,13 @@ class JudgedRun:
         """One surrogate call vs 10 plain steps from the same state."""
         q = self.lat.read_q(dtype=np.float32)
         u = self.lat.read_u(dtype=np.float32)
+        r = self.lat.read_rate(dtype=np.float32)
         if not (np.isfinite(q).all() and np.isfinite(u).all()):
             return False
-        y = self.sur.forward(q, u, self.kappa, TAU_R)
+        y = self.sur.forward(q, u, r, self.kappa, TAU_R)
         self.lat.step(K_STEPS)
         F_plain = self.lat.free_energy()
-        F_pred = free_energy_of(self.lat.dims, self.kappa, q + self.s_dq * y)
+        F_pred = free_energy_of(self.lat.dims, self.kappa, q + 10.0 * r + S_DQ * y)
         gap = abs(F_pred - F_plain) / abs(F_plain)
         self.judge_gaps.append(gap)
         return bool(np.isfinite(gap) and gap <= self.tol)
@@ -251,6 +262,7 @@ def time_call(shape=(64, 64, 256), reps: int = 20):
     lat.step(20)
     lat.synchronize()
     sur = lcbp.Surrogate(*shape)
+    sur.set_scales(S_U, S_R, S_DQ)
     sur.set_params(init_params(np.random.default_rng(0)))
     sur.step(lat, 1.0, TAU_R, 2)  # warm-up
     t0 = time.perf_counter()
@@ -272,56 +284,62 @@ def time_call(shape=(64, 64, 256), reps: int = 20):
 def main():
     import argparse
     import json
+    import sys
     import torch
     ap = argparse.ArgumentParser(description="train the surrogate on slab runs and judge it against the solver")
-    ap.add_argument("--data-steps", type=int, default=6000)
-    ap.add_argument("--every", type=int, default=100)
-    ap.add_argument("--iters", type=int, default=1500)
+    ap.add_argument("--data-steps", type=int, default=12000)
+    ap.add_argument("--every", type=int, default=400)
+    ap.add_argument("--t-min", type=int, default=500)
+    ap.add_argument("--iters", type=int, default=2000)
     ap.add_argument("--run-steps", type=int, default=20000)
     ap.add_argument("--kappa", type=float, default=1.0)
+    ap.add_argument("--tol", type=float, default=1e-3)
     args = ap.parse_args()
     torch.cuda.set_device(0)
+
+    def note(d):
+        print(json.dumps(d), file=sys.stderr, flush=True)
+
     t0 = time.perf_counter()
-    data = generate([0.5, 1.0, 2.0], args.data_steps, args.every)
-    held = generate([1.5], args.data_steps, args.every * 5, seed=7)
+    data = generate([0.5, 1.0, 2.0], args.data_steps, args.every, t_min=args.t_min)
+    held = generate([1.5], args.data_steps, args.every * 4, t_min=args.t_min, seed=7)
     t_gen = time.perf_counter() - t0
-    import sys
+    note({"samples": len(data), "held_out": len(held), "gen_s": t_gen})
     params, log = train(data, args.iters)
-    print(json.dumps({"train_s": log.seconds, "loss_first": float(np.mean(log.losses[:20])),
-                      "loss_last": float(np.mean(log.losses[-20:]))}), file=sys.stderr, flush=True)
-    mse_net, mse_zero = evaluate(params, held)
-    print(json.dumps({"held_out_mse": [mse_net, mse_zero]}), file=sys.stderr, flush=True)
+    note({"train_s": log.seconds, "loss_first": float(np.mean(log.losses[:20])),
+          "loss_last": float(np.mean(log.losses[-20:]))})
+    mse = evaluate(params, held, depth=held[0].q.shape[1])
+    note({"held_out_mse": mse})
     t_sur, t_plain = time_call()
-    print(json.dumps({"call_ms": [t_sur, t_plain]}), file=sys.stderr, flush=True)
-    # time to solution: plain vs judged surrogate run from the same initial state
+    note({"call_ms": [t_sur, t_plain]})
+    seg = (49 + 1) * K_STEPS  # judged segments are 500 steps: 49 calls + 10 judge steps
     plain = slab_lattice(args.kappa)
-    F_plain = []
+    F_plain = {}
     tp0 = time.perf_counter()
-    for t in range(100, args.run_steps + 1, 100):
-        plain.step(100)
-        F_plain.append((t, plain.free_energy()))
+    for t in range(seg, args.run_steps + 1, seg):
+        plain.step(seg)
+        F_plain[t] = plain.free_energy()
     plain.synchronize()
     t_plain_run = time.perf_counter() - tp0
     hyb = slab_lattice(args.kappa)
-    run = JudgedRun(hyb, params, args.kappa)
+    run = JudgedRun(hyb, params, args.kappa, M=49, tol=args.tol)
     F_hyb = []
     th0 = time.perf_counter()
-    run.advance(args.run_steps, log_every=100, log=F_hyb)
+    run.advance(args.run_steps, log_every=seg, log=F_hyb)
     hyb.synchronize()
     t_hyb_run = time.perf_counter() - th0
-    fp = dict(F_plain)
-    errs = [abs(F - fp[t]) / abs(fp[t]) for t, F in F_hyb if t in fp]
+    errs = [abs(F - F_plain[t]) / abs(F_plain[t]) for t, F in F_hyb if t in F_plain]
     print(json.dumps({
         "data": {"samples": len(data), "held_out": len(held), "seconds": t_gen},
         "train": {"iters": log.iters, "seconds": log.seconds, "ms_per_iter": 1e3 * log.seconds / log.iters,
                   "loss_first": float(np.mean(log.losses[:20])), "loss_last": float(np.mean(log.losses[-20:]))},
-        "held_out_mse": {"network": mse_net, "persistence": mse_zero},
+        "held_out_mse": mse,
         "call_ms": {"surrogate_10_steps": t_sur, "plain_10_steps": t_plain},
         "run": {"steps": args.run_steps, "kappa": args.kappa, "plain_s": t_plain_run, "surrogate_s": t_hyb_run,
                 "surrogate_calls": run.surrogate_calls, "plain_steps": run.plain_steps,
                 "fallbacks": run.fallbacks, "max_rel_F_error": max(errs) if errs else None,
                 "judge_gap_median": float(np.median(run.judge_gaps)) if run.judge_gaps else None,
-                "final_F": {"plain": F_plain[-1][1], "surrogate": F_hyb[-1][1] if F_hyb else None}},
+                "final_F": {"plain": F_plain[max(F_plain)], "surrogate": F_hyb[-1][1] if F_hyb else None}},
     }))
 
 

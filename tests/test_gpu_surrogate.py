@@ -26,18 +26,22 @@ def lcbp():
     return L
 
 
-def net_input(q5, u3, kappa, tau, s_u):
+S_U, S_R, S_DQ = 1e-3, 1e-3, 1e-3
+
+
+def net_input(q5, u3, r5, kappa, tau):
     """Channels of the network input (the surrogate's definition)."""
-    x = np.zeros((10,) + q5.shape[1:])
+    x = np.zeros((15,) + q5.shape[1:])
     x[:5] = q5
-    x[5:8] = u3 / s_u
+    x[5:8] = u3 / S_U
     x[8] = kappa - 1.0
     x[9] = tau
+    x[10:15] = r5 / S_R
     return x
 
 
 def random_params(seed, scale=1.5):
-    return S.init_params(10, 32, 5, BLOCKS, np.random.default_rng(seed), scale=scale)
+    return S.init_params(15, 32, 5, BLOCKS, np.random.default_rng(seed), scale=scale)
 
 
 @pytest.mark.parametrize("dims", [(16, 8, 6), (40, 12, 5), (32, 4, 1)])
@@ -47,10 +51,11 @@ def test_forward_matches_oracle(lcbp, dims):
     P = random_params(10)
     q5 = synth.smooth_q5(shape, 0.3, 11) + synth.random_q5(shape, 0.05, 12)
     u3 = synth.random_velocity(shape, 2e-4, 13)
+    r5 = synth.random_q5(shape, 1e-3, 14)
     sur = lcbp.Surrogate(nx, ny, nz)
     sur.set_params(S.flatten(P, BLOCKS))
-    y = sur.forward(q5, u3, 1.3, -0.4)
-    x = net_input(q5, u3, 1.3, -0.4, 1e-3)
+    y = sur.forward(q5, u3, r5, 1.3, -0.4)
+    x = net_input(q5, u3, r5, 1.3, -0.4)
     y_q, _ = S.forward(P, x, BLOCKS, quant=S.bf16)
     y_e, _ = S.forward(P, x, BLOCKS)
     scale = np.abs(y_e).max()
@@ -66,15 +71,17 @@ def test_training_gradients_match_oracle(lcbp):
     P = random_params(20)
     q5 = synth.smooth_q5(shape, 0.3, 21)
     u3 = synth.random_velocity(shape, 2e-4, 22)
+    r5 = synth.random_q5(shape, 1e-3, 24)
     dq = synth.random_q5(shape, 5e-3, 23)
     mask = (np.arange(nz)[:, None, None] * np.ones(shape) >= 1).astype(np.float64)
     sur = lcbp.Surrogate(nx, ny, nz, training=True)
     sur.set_params(S.flatten(P, BLOCKS))
-    loss = sur.train_step(q5, u3, 0.9, 0.2, dq, mask, lr=1e-6)
+    loss = sur.train_step(q5, u3, r5, 0.9, 0.2, dq, mask, lr=1e-6)
     g = S.unflatten(sur.get_grads().astype(np.float64), P, BLOCKS)
-    x = net_input(q5, u3, 0.9, 0.2, 1e-3)
+    x = net_input(q5, u3, r5, 0.9, 0.2)
     y, acts = S.forward(P, x, BLOCKS, quant=S.bf16)
-    loss_o, dout = S.masked_mse(y, dq / 1e-2, mask)
+    # the network learns the correction to ten Euler steps of the rate
+    loss_o, dout = S.masked_mse(y, (dq - 10.0 * r5) / S_DQ, mask)
     G, _ = S.backward(P, acts, dout, BLOCKS, quant=S.bf16)
     assert abs(loss - loss_o) < 1e-3 * loss_o
     for name in S.layer_names(BLOCKS):
@@ -95,11 +102,16 @@ def test_surrogate_step_applies_prediction(lcbp):
     lat.init_q(lcbp.BPII, 0.3, noise=1e-3, seed=3).init_f_equilibrium(1.0).step(5)
     q0 = lat.read_q(dtype=np.float32)
     u0 = lat.read_u(dtype=np.float32)
+    r0 = lat.read_rate(dtype=np.float32)
+    # the rate is the Beris-Edwards right-hand side of the oracle
+    Q9 = lbq.q5_to_q9(q0.astype(np.float64))
+    R9 = lbq.be_rhs(Q9, np.moveaxis(u0.astype(np.float64), 0, -1), p)
+    assert np.abs(r0 - lbq.q9_to_q5(R9)).max() < 1e-6
     sur = lcbp.Surrogate(nx, ny, nz)
     sur.set_params(S.flatten(random_params(30, scale=1.0), BLOCKS))
-    y = sur.forward(q0, u0, 1.0, -0.5)
+    y = sur.forward(q0, u0, r0, 1.0, -0.5)
     sur.step(lat, 1.0, -0.5, 1)
     q1 = lat.read_q(dtype=np.float32)
-    assert np.abs(q1 - (q0 + 1e-2 * y)).max() < 1e-6
+    assert np.abs(q1 - (q0 + 10.0 * r0 + S_DQ * y)).max() < 1e-6
     lat.reequilibrate_f().step(2)  # plain stepping resumes
     assert np.isfinite(lat.free_energy())
