@@ -1,9 +1,11 @@
 """Run a few coupled steps on an L^3 BPII lattice, for profilers.
 
     python -m paper_0901_3293_gb300.profile --size 128 --steps 4 [--dtype f32]
+    python -m paper_0901_3293_gb300.profile --conv --dims 64 64 256 --steps 3
 
-Each step launches the three step kernels once (no CUDA graph), so a
-profiler can select them by name and launch index.
+Each step launches the step kernels once (no CUDA graph), so a profiler can
+select them by name and launch index.  --conv instead runs surrogate calls
+(ten tensor-core convolutions each) on a lattice of the given dims.
 """
 
 from __future__ import annotations
@@ -21,9 +23,25 @@ def main():
     ap.add_argument("--size", type=int, default=128)
     ap.add_argument("--steps", type=int, default=4)
     ap.add_argument("--dtype", default="f32")
+    ap.add_argument("--conv", action="store_true")
+    ap.add_argument("--dims", type=int, nargs=3, default=[64, 64, 256])
     args = ap.parse_args()
     build.build()
     torch.cuda.set_device(0)
+    if args.conv:
+        import time
+
+        import numpy as np
+        nx, ny, nz = args.dims
+        lat = lcbp.Lattice(nx, ny, nz)
+        lat.init_q(lcbp.BPII, 0.3, noise=1e-4, seed=1).init_f_equilibrium(1.0)
+        sur = lcbp.Surrogate(nx, ny, nz)
+        rng = np.random.default_rng(0)
+        sur.set_params((rng.normal(size=sur.count) * 0.02).astype(np.float32))
+        t0 = time.perf_counter()
+        sur.step(lat, 1.0, -0.5, args.steps)
+        print({"dims": args.dims, "calls": args.steps, "ms_per_call": 1e3 * (time.perf_counter() - t0) / args.steps})
+        return
     n = args.size
     lat = lcbp.Lattice(n, n, n, dtype=args.dtype)
     lat.set_ldg(0.01, 3.1, 0.01, 2 * math.pi / 32)
