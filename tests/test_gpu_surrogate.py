@@ -72,7 +72,8 @@ def test_training_gradients_match_oracle(lcbp):
     q5 = synth.smooth_q5(shape, 0.3, 21)
     u3 = synth.random_velocity(shape, 2e-4, 22)
     r5 = synth.random_q5(shape, 1e-3, 24)
-    dq = synth.random_q5(shape, 5e-3, 23)
+    # a realistic target: ten Euler steps of the rate plus a small correction
+    dq = 10.0 * r5 + synth.random_q5(shape, 5e-4, 23)
     mask = (np.arange(nz)[:, None, None] * np.ones(shape) >= 1).astype(np.float64)
     sur = lcbp.Surrogate(nx, ny, nz, training=True)
     sur.set_params(S.flatten(P, BLOCKS))
