@@ -1099,15 +1099,16 @@ int lcbp_reequilibrate_f(lcbp_lattice* h) {
 }  // extern "C"
 
 namespace lcbp {
-// Beris-Edwards rate of a lattice into its predictor scratch; returns that
-// scratch (5 * N floats, valid until the lattice's next step)
-int lattice_rate(lcbp_lattice* h, const float** rate) {
+// Enqueue the Beris-Edwards rate of a lattice into its predictor scratch on
+// the lattice's stream and record `done` after it; returns that scratch
+// (5 * N floats, valid until the lattice's next step)
+int lattice_rate(lcbp_lattice* h, const float** rate, cudaEvent_t done) {
   if (!h) return fail(LCBP_EINVAL, "null lattice handle");
   if (h->dtype != LCBP_F32) return fail(LCBP_EINVAL, "the surrogate works on FP32 lattice state");
   cudaSetDevice(h->device);
   StepArgs a = step_args(h);
   cudaError_t e = launch_rate<float>(a, h->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e == cudaSuccess) e = cudaEventRecord(done, h->stream);
   if (e != cudaSuccess) return cuda_fail(e, "rate");
   *rate = static_cast<const float*>(h->qs);
   return LCBP_OK;

@@ -25,7 +25,7 @@ using namespace lcbp;
 namespace lcbp {
 // lattice internals needed by the surrogate step (api.cu)
 int lattice_fields(lcbp_lattice* h, float** q, const float** u, int dims[3], cudaStream_t* stream);
-int lattice_rate(lcbp_lattice* h, const float** rate);
+int lattice_rate(lcbp_lattice* h, const float** rate, cudaEvent_t done);
 }
 
 namespace {
@@ -353,6 +353,7 @@ struct lcbp_surrogate {
   double *partial, *dloss, *h_loss;
   int* d_err;
   long long adam_step;
+  cudaEvent_t ev_rate, ev_update;  // cross-stream ordering with a lattice
   std::vector<void*> allocs;
 };
 
@@ -539,6 +540,11 @@ int lcbp_surrogate_create(int nx, int ny, int nz, int training, lcbp_surrogate**
     A((void**)&s->adam_v, mc * 4);
   }
   if (!rc) {
+    e = cudaEventCreateWithFlags(&s->ev_rate, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_update, cudaEventDisableTiming);
+    if (e != cudaSuccess) rc = cuda_fail(e, "events");
+  }
+  if (!rc) {
     s->dloss = s->partial + 4096;
     e = cudaMallocHost(&s->h_loss, 8);
     if (e != cudaSuccess) rc = cuda_fail(e, "host alloc");
@@ -584,6 +590,8 @@ int lcbp_surrogate_destroy(lcbp_surrogate* s) {
   cudaStreamSynchronize(s->stream);
   for (void* p : s->allocs) cudaFree(p);
   if (s->h_loss) cudaFreeHost(s->h_loss);
+  if (s->ev_rate) cudaEventDestroy(s->ev_rate);
+  if (s->ev_update) cudaEventDestroy(s->ev_update);
   cudaStreamDestroy(s->stream);
   delete s;
   return LCBP_OK;
@@ -709,16 +717,21 @@ int lcbp_surrogate_step(lcbp_surrogate* s, lcbp_lattice* h, double kappa, double
   if (dims[0] != s->nx || dims[1] != s->ny || dims[2] != s->nz)
     return fail(LCBP_EINVAL, "surrogate built for %dx%dx%d, lattice is %dx%dx%d", s->nx, s->ny, s->nz, dims[0], dims[1],
                 dims[2]);
-  cudaError_t e = cudaStreamSynchronize(hs);  // lattice work done before the surrogate touches Q
+  // The rate runs on the lattice's stream, the network on the surrogate's;
+  // events order them without host round trips.
+  cudaError_t e = cudaSuccess;
   for (int c = 0; c < ncalls && e == cudaSuccess; ++c) {
     const float* r = nullptr;
-    rc = lattice_rate(h, &r);  // FP32 rate of the current Q (synchronises the lattice stream)
+    rc = lattice_rate(h, &r, s->ev_rate);
     if (rc) return rc;
+    e = cudaStreamWaitEvent(s->stream, s->ev_rate, 0);
+    if (e != cudaSuccess) break;
     k_sur_input<<<grid_for(s->np), 256, 0, s->stream>>>(q, u, r, s->su, s->sr, (float)kappa, (float)tau, s->nx,
                                                         s->ny, s->nz, s->X);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = forward(s, q, r);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);  // Q updated before the next rate
+    if (e == cudaSuccess) e = cudaEventRecord(s->ev_update, s->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(hs, s->ev_update, 0);  // next rate sees the updated Q
   }
   if (e != cudaSuccess) return cuda_fail(e, "surrogate step");
   return sync_err(s, "surrogate step");

@@ -179,6 +179,9 @@ class JudgedRun:
         self.judge_gaps = []
         self._f = torch.empty((15, nz, ny, nx), dtype=torch.float32, device="cuda")
         self._q = torch.empty((5, nz, ny, nx), dtype=torch.float32, device="cuda")
+        self._f2 = torch.empty_like(self._f)
+        self._q2 = torch.empty_like(self._q)
+        self._scratch = None
 
     def _log(self, log, log_every, next_log):
         while next_log is not None and self.t >= next_log:
@@ -223,36 +226,31 @@ class JudgedRun:
             next_log = self._log(log, log_every, next_log)
 
     def _judge(self) -> bool:
-        """One surrogate call vs 10 plain steps from the same state."""
-        q = self.lat.read_q(dtype=np.float32)
-        u = self.lat.read_u(dtype=np.float32)
-        r = self.lat.read_rate(dtype=np.float32)
-        if not (np.isfinite(q).all() and np.isfinite(u).all()):
+        """One surrogate call vs 10 plain steps from the same state (all on device:
+        the call runs on a scratch lattice holding a copy of the state)."""
+        nx, ny, nz = self.lat.dims
+        if self._scratch is None:
+            self._scratch = lcbp.Lattice(nx, ny, nz, dtype="f32")
+            self._scratch.set_ldg_kappa_tau(A0, Q0, self.kappa, TAU_R)
+            self._scratch.set_flow(2.0, 0.7, 0.3, True, lcbp.JACOBI)
+        self.lat.read_f(out=self._f2)
+        self.lat.read_q(out=self._q2)
+        self._scratch.set_f(self._f2).set_q(self._q2)
+        try:
+            self.sur.step(self._scratch, self.kappa, TAU_R, 1)
+            F_pred = self._scratch.free_energy()
+            self.lat.step(K_STEPS)
+            F_plain = self.lat.free_energy()
+        except lcbp.LcbpError:
             return False
-        y = self.sur.forward(q, u, r, self.kappa, TAU_R)
-        self.lat.step(K_STEPS)
-        F_plain = self.lat.free_energy()
-        F_pred = free_energy_of(self.lat.dims, self.kappa, q + 10.0 * r + S_DQ * y)
         gap = abs(F_pred - F_plain) / abs(F_plain)
         self.judge_gaps.append(gap)
         return bool(np.isfinite(gap) and gap <= self.tol)
 
     def close(self):
         self.sur.close()
-
-
-def free_energy_of(dims, kappa: float, q5) -> float:
-    """F_h of an arbitrary Q on a scratch lattice of the same size (slab parameters)."""
-    scratch = _SCRATCH.get(dims)
-    if scratch is None:
-        _SCRATCH.clear()
-        scratch = _SCRATCH[dims] = lcbp.Lattice(*dims, dtype="f32")
-    scratch.set_ldg_kappa_tau(A0, Q0, kappa, TAU_R)
-    scratch.set_q(q5)
-    return scratch.free_energy()
-
-
-_SCRATCH: dict = {}
+        if self._scratch is not None:
+            self._scratch.close()
 
 
 def time_call(shape=(64, 64, 256), reps: int = 20):
