@@ -259,192 +259,6 @@ __global__ void __launch_bounds__(kConvThreads) k_conv_tc(const __grid_constant_
 
 
 // ---------------------------------------------------------------------------
-// z-marching variant: a CTA owns a 32 x 4 column of output sites over zc
-// planes.  For every input plane it loads, once, three x-shifted boxes of
-// 32 x 6 sites (dx = -1, 0, +1; rows y0-1 .. y0+4); the A operand of tap
-// (dx, dy, dz) of output plane z is the 128 consecutive rows starting at row
-// 32 (dy + 1) of the dx box of plane z + dz -- a 2 KB-aligned sub-view, so no
-// im2col copy exists anywhere.  Each input plane is read from L2 once per CTA
-// instead of nine times per output plane.
-// ---------------------------------------------------------------------------
-constexpr int kZmSlots = 4;
-
-template <int CIN, int COUT>
-struct ConvZmSmem {
-  static constexpr int WBYTES = ((27 * COUT * CIN * 2 + 1023) / 1024) * 1024;
-  static constexpr int ROW = CIN * 2;      // bytes of one site row
-  static constexpr int BOX = 32 * 6 * ROW;  // one dx box
-  static constexpr int SLOT = 3 * BOX;      // dx = -1, 0, +1 of one plane
-  static constexpr int OFF_SLOTS = WBYTES;
-  static constexpr int OFF_BARS = OFF_SLOTS + kZmSlots * SLOT;
-  static constexpr int NBARS = 2 * kZmSlots + 5;  // full[4], empty[4], accf[2], acce[2], wbar
-  static constexpr size_t bytes = OFF_BARS + NBARS * 8 + 16 + 1024;
-  static constexpr uint32_t SWZ = CIN == 32 ? kSwizzle64B : kSwizzle32B;
-  static constexpr uint32_t SBO = 8 * CIN * 2;
-  static constexpr uint32_t TMEM_COLS = 2 * COUT < 32 ? 32 : 2 * COUT;
-};
-
-template <int CIN, int COUT, int EPI>
-__global__ void __launch_bounds__(kConvThreads) k_conv_zm(const __grid_constant__ CUtensorMap tmA,
-                                                          const __grid_constant__ CUtensorMap tmW, ConvArgs a,
-                                                          int zc) {
-  using L = ConvZmSmem<CIN, COUT>;
-  extern __shared__ unsigned char smem_raw[];
-  unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  unsigned char* wsm = smem;
-  unsigned char* slots = smem + L::OFF_SLOTS;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L::OFF_BARS);
-  uint64_t* full = bars;
-  uint64_t* empty = bars + kZmSlots;
-  uint64_t* accf = bars + 2 * kZmSlots;
-  uint64_t* acce = accf + 2;
-  uint64_t* wbar = acce + 2;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(wbar + 1);
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
-
-  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const int tiles_x = (a.nx + 31) / 32, tiles_y = (a.ny + 3) / 4;
-  const int x0 = (blockIdx.x % tiles_x) * 32, y0 = ((blockIdx.x / tiles_x) % tiles_y) * 4;
-  const int z0 = (blockIdx.x / (tiles_x * tiles_y)) * zc;
-  const int nout = min(z0 + zc, a.nz) - z0;  // output planes of this CTA
-  const int nplanes = nout + 2;                // input planes z0-1 .. z0+nout
-
-  if (threadIdx.x == 0) {
-    for (int i = 0; i < kZmSlots; ++i) {
-      mbar_init(&full[i], 1);
-      mbar_init(&empty[i], 1);
-    }
-    mbar_init(&accf[0], 1);
-    mbar_init(&accf[1], 1);
-    mbar_init(&acce[0], 128);
-    mbar_init(&acce[1], 128);
-    mbar_init(wbar, 1);
-    *abort_flag = 0;
-    mbar_init_fence();
-  }
-  if (warp == 0) {
-    tmem_alloc(tmem_slot, L::TMEM_COLS);
-    tmem_relinquish();
-  }
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  const uint32_t tmem_base = *tmem_slot;
-
-  auto bounded_wait = [&](uint64_t* bar, uint32_t parity) {
-    if (*abort_flag) return false;
-    if (!mbar_wait_bounded(bar, parity, kConvWaitNs)) {
-      *abort_flag = 1;
-      atomicExch(a.err, 1);
-      return false;
-    }
-    return true;
-  };
-
-  if (warp == 4) {
-    // ---------------- TMA producer: plane k (global z = z0 - 1 + k) into slot k % 4
-    if (lane == 0) {
-      tma_prefetch_desc(&tmA);
-      tma_prefetch_desc(&tmW);
-      mbar_arrive_expect_tx(wbar, 27 * COUT * CIN * 2);
-      tma_load_3d(wsm, &tmW, 0, 0, 0, wbar);
-      for (int k = 0; k < nplanes; ++k) {
-        const int s = k % kZmSlots;
-        if (k >= kZmSlots && !bounded_wait(&empty[s], ((k / kZmSlots) - 1) & 1)) break;
-        mbar_arrive_expect_tx(&full[s], L::SLOT);
-        unsigned char* dst = slots + s * L::SLOT;
-        // padded coordinates: x = x0 + dx + 1 (first of 32), y = y0 (= y0 - 1 + 1), z = z0 + k
-        for (int d = 0; d < 3; ++d) tma_load_4d(dst + d * L::BOX, &tmA, 0, x0 + d, y0, z0 + k, &full[s]);
-      }
-    }
-  } else if (warp == 5) {
-    // ---------------- MMA issuer
-    if (lane == 0) {
-      constexpr uint32_t idesc = umma_idesc_bf16(128, COUT);
-      const uint32_t w_addr = smem_addr(wsm), sl_addr = smem_addr(slots);
-      bool ok = bounded_wait(wbar, 0);
-      int kw = 0;  // next input plane to wait for
-      for (int j = 0; ok && j < nout; ++j) {
-        const int acc = j & 1;
-        if (j >= 2 && !bounded_wait(&acce[acc], ((j >> 1) - 1) & 1)) break;
-        for (; ok && kw <= j + 2; ++kw) ok = bounded_wait(&full[kw % kZmSlots], (kw / kZmSlots) & 1);
-        if (!ok) break;
-        tc_fence_after();
-        const uint32_t d_tmem = tmem_base + acc * COUT;
-#pragma unroll 1
-        for (int t = 0; t < 27; ++t) {
-          const int dx = t % 3, dy = (t / 3) % 3, dz = t / 9;  // each 0..2 (offset + 1)
-          const uint32_t a_row = sl_addr + ((j + dz) % kZmSlots) * L::SLOT + dx * L::BOX + dy * 32 * L::ROW;
-#pragma unroll
-          for (int kk = 0; kk < CIN / 16; ++kk) {
-            const uint64_t ad = umma_sdesc(a_row + kk * 32, L::SBO, L::SWZ);
-            const uint64_t bd = umma_sdesc(w_addr + t * (COUT * CIN * 2) + kk * 32, L::SBO, L::SWZ);
-            umma_bf16(d_tmem, ad, bd, idesc, (t > 0 || kk > 0) ? 1u : 0u);
-          }
-        }
-        umma_commit(&accf[acc]);
-        umma_commit(&empty[j % kZmSlots]);  // plane j is not read by later outputs
-      }
-    }
-  } else {
-    // ---------------- epilogue: warps 0..3, one TMEM lane (= one site) per thread
-    for (int j = 0; j < nout; ++j) {
-      const int acc = j & 1;
-      const bool ok = __all_sync(0xffffffffu, bounded_wait(&accf[acc], (j >> 1) & 1));
-      if (!ok) break;
-      tc_fence_after();
-      const uint32_t taddr = tmem_base + ((uint32_t)(warp * 32) << 16) + acc * COUT;
-      float v[COUT];
-      if constexpr (COUT == 32) {
-        uint32_t r[32];
-        tmem_ld32(taddr, r);
-        tmem_ld_wait();
-#pragma unroll
-        for (int c = 0; c < 32; ++c) v[c] = __uint_as_float(r[c]);
-      } else {
-        uint32_t r[16];
-        tmem_ld16(taddr, r);
-        tmem_ld_wait();
-#pragma unroll
-        for (int c = 0; c < 16; ++c) v[c] = __uint_as_float(r[c]);
-      }
-      tc_fence_before();
-      mbar_arrive(&acce[acc]);
-      const int m = warp * 32 + lane;
-      conv_epilogue<COUT, EPI>(v, x0 + (m & 31), y0 + (m >> 5), z0 + j, a);
-    }
-  }
-  tc_fence_before();
-  __syncthreads();
-  if (warp == 0) {
-    tc_fence_after();
-    tmem_dealloc(tmem_base, L::TMEM_COLS);
-  }
-}
-
-template <int CIN, int COUT, int EPI>
-cudaError_t conv_zm_launch_t(const CUtensorMap& tmA, const CUtensorMap& tmW, const ConvArgs& a, int sms,
-                             cudaStream_t s) {
-  using L = ConvZmSmem<CIN, COUT>;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_conv_zm<CIN, COUT, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)L::bytes);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
-  const int tiles_xy = ((a.nx + 31) / 32) * ((a.ny + 3) / 4);
-  const int per_sm = L::bytes * 2 <= 227 * 1024 ? 2 : 1;
-  // about two waves of CTAs, at least 4 planes each
-  int zc = (int)((long long)a.nz * tiles_xy / (2LL * per_sm * sms));
-  zc = zc < 4 ? 4 : zc;
-  zc = zc > a.nz ? a.nz : zc;
-  const int grid = tiles_xy * ((a.nz + zc - 1) / zc);
-  k_conv_zm<CIN, COUT, EPI><<<grid, kConvThreads, L::bytes, s>>>(tmA, tmW, a, zc);
-  return cudaGetLastError();
-}
-
-// ---------------------------------------------------------------------------
 // host launch
 // ---------------------------------------------------------------------------
 template <int CIN, int COUT, int EPI>
@@ -467,7 +281,7 @@ cudaError_t conv_launch_t(const CUtensorMap& tmA, const CUtensorMap& tmW, const 
 cudaError_t conv_launch(int cin, int cout, int epi, const CUtensorMap& tmA, const CUtensorMap& tmW,
                         const ConvArgs& a, int max_ctas, cudaStream_t s) {
 #define LCBP_CONV_CASE(CI, CO, E) \
-  if (cin == CI && cout == CO && epi == (E)) return conv_zm_launch_t<CI, CO, E>(tmA, tmW, a, max_ctas / 2, s);
+  if (cin == CI && cout == CO && epi == (E)) return conv_launch_t<CI, CO, E>(tmA, tmW, a, max_ctas, s);
   // forward: input layer, hidden layers, residual layers, output layer (FP32 out / Q update)
   LCBP_CONV_CASE(16, 32, kEpiBias | kEpiRelu)
   LCBP_CONV_CASE(32, 32, kEpiBias | kEpiRelu)

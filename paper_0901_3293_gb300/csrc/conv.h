@@ -32,9 +32,8 @@ struct ConvArgs {
   int* err;
 };
 
-// y = conv(x) on tcgen05 (z-marching kernel); tmA describes the padded BF16
-// input (box C_in x 32 x 6 x 1, swizzled), tmW the BF16 weights
-// [27][C_out][C_in] (one box of all taps); max_ctas = 2 x SM count
+// y = conv(x) on tcgen05; tmA describes the padded BF16 input (box C_in x 32 x 4 x 1,
+// swizzled), tmW the BF16 weights [27][C_out][C_in] (one box of all taps)
 cudaError_t conv_launch(int cin, int cout, int epi, const CUtensorMap& tmA, const CUtensorMap& tmW,
                         const ConvArgs& a, int max_ctas, cudaStream_t s);
 

@@ -294,15 +294,14 @@ EncodeFn encoder() {
   return fn;
 }
 
-// padded activations [nz+2][ny+2][nx+2][C] as a 4-D tensor, box C x 32 x 6 x 1
-// (32 sites of six rows: the y halo of a 4-row output tile)
+// padded activations [nz+2][ny+2][nx+2][C] as a 4-D tensor, box C x 32 x 4 x 1
 bool act_map(CUtensorMap* m, void* base, int C, int nx, int ny, int nz) {
   EncodeFn fn = encoder();
   if (!fn) return false;
   const cuuint64_t px = nx + 2, py = ny + 2, pz = nz + 2;
   const cuuint64_t dims[4] = {(cuuint64_t)C, px, py, pz};
   const cuuint64_t str[3] = {(cuuint64_t)C * 2, (cuuint64_t)C * 2 * px, (cuuint64_t)C * 2 * px * py};
-  const cuuint32_t box[4] = {(cuuint32_t)C, 32, 6, 1};
+  const cuuint32_t box[4] = {(cuuint32_t)C, 32, 4, 1};
   const cuuint32_t es[4] = {1, 1, 1, 1};
   return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, base, dims, str, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
             C == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
