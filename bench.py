@@ -226,7 +226,7 @@ def run_ours(args):
 
     # ---- per-kernel device times, kernel by kernel with events (same kernels)
     kms = lat.profile_steps(max(3, min(args.steps, 10)))
-    fast, zc = lat.path()
+    fast, zc, spt = lat.path()
     peak, peak_kind = measured_peaks()
     per_kernel = {}
     for name, t in zip(KERNELS_FAST if fast else KERNELS_GENERIC, kms):
@@ -327,7 +327,7 @@ def run_ours(args):
                    "q0": PARAMS["q0"], "tau_f": PARAMS["tau_f"], "l2": "state 4.5 GB >> 129 MB L2, no flush",
                    "parallelism": f"{world} independent replicas" if world > 1 else "single lattice",
                    "kernels": "fast (z-marching, TMA-staged planes)" if fast else "generic",
-                   "planes_per_cta": zc},
+                   "planes_per_cta": zc, "sites_per_thread": spt},
         "roofline": roof, "per_kernel": per_kernel, "cpu_baseline": cpu, "e2e": e2e,
         "gpu_launches": launches, "clocks": clk, "free_energy_after": F,
         "slab_64x64x256": slab_line, "batched_48_replicas": batch_line,

@@ -88,6 +88,8 @@ extern "C" {
 /* kernel selection (lcbp_set_path) */
 #define LCBP_PATH_AUTO 0    /* fast z-marching TMA kernels where they apply, else generic */
 #define LCBP_PATH_GENERIC 1 /* always the generic one-thread-per-site kernels */
+#define LCBP_PATH_FAST1 2   /* as AUTO, fast kernels pinned to one site per thread */
+#define LCBP_PATH_FAST2 3   /* as AUTO, fast kernels pinned to two sites per thread (FP32 only) */
 
 typedef struct lcbp_lattice lcbp_lattice;
 
@@ -217,18 +219,23 @@ LCBP_API int lcbp_profile_steps(lcbp_lattice *h, int nsteps, double *kernel_ms, 
  * z-marching kernels that stage planes in shared memory with TMA tile loads
  * -- whenever flow is on, coupling is Jacobi and nx is a multiple of 4;
  * otherwise, or with LCBP_PATH_GENERIC, three one-thread-per-site kernels.
- * Both compute the same step.  Errors: LCBP_EINVAL (unknown path).
+ * FP32 fast kernels come in two builds, one or two lattice sites per thread
+ * (the latter on packed FP32x2 arithmetic); AUTO times both, LCBP_PATH_FAST1
+ * and LCBP_PATH_FAST2 pin one.  All compute the same step.  Errors:
+ * LCBP_EINVAL (unknown path, or LCBP_PATH_FAST2 on an FP64 lattice).
  */
 LCBP_API int lcbp_set_path(lcbp_lattice *h, int path);
 
 /*
  * *fast = 1 if the next step runs the fast path; *planes_per_cta = the
- * autotuned number of z-planes each CTA marches through (0 before the first
- * step, or on the generic path).  The tuning times each candidate once per
- * lattice shape and dtype, writing scratch buffers only; results persist in
- * the file named by the environment variable LCBP_AUTOTUNE_CACHE, if set.
+ * autotuned number of z-planes each CTA marches through and
+ * *sites_per_thread = the autotuned 1 or 2 (both 0 before the first step, or
+ * on the generic path).  The tuning times each candidate once per lattice
+ * shape and dtype, writing scratch buffers only; AUTO results persist in the
+ * file named by the environment variable LCBP_AUTOTUNE_CACHE, if set
+ * (lines "nx ny nz dtype planes sites").  Any pointer may be NULL.
  */
-LCBP_API int lcbp_get_path(lcbp_lattice *h, int *fast, int *planes_per_cta);
+LCBP_API int lcbp_get_path(lcbp_lattice *h, int *fast, int *planes_per_cta, int *sites_per_thread);
 
 /*
  * Copy out the Beris-Edwards rate dQ/dt = R(Q, u) = Gamma H + S(W, Q) - u.grad Q

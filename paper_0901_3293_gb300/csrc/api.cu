@@ -172,6 +172,7 @@ struct lcbp_lattice {
   int path_req;   // LCBP_PATH_*
   bool tmaps_ok;  // tensor maps built
   int zc;         // planes per CTA, 0 until tuned
+  int spt;        // sites per thread of the fast kernels, set by the tuner
   CUtensorMap tm[6];  // Q, rho u [0], rho u [1], sigma, b, Q*
   int* d_err;
 };
@@ -362,6 +363,7 @@ ZmArgs zm_args(lcbp_lattice* h, const void* model) {
   a.ny = h->ny;
   a.nz = h->nz;
   a.zc = h->zc > 0 ? h->zc : std::min(h->nz, 32);
+  a.spt = h->spt > 0 ? h->spt : 1;
   a.model = model;
   a.tm_q = &h->tm[0];
   a.tm_u = &h->tm[1 + h->cur];
@@ -403,12 +405,13 @@ cudaError_t launch_zm(lcbp_lattice* h, const ZmArgs& a) {
   return h->dtype == LCBP_F64 ? launch_step_zm<double>(a, h->stream) : launch_step_zm<float>(a, h->stream);
 }
 
-// planes per CTA, chosen by timing each candidate once per lattice shape and
-// dtype; the runs write only scratch buffers (Q* to the H scratch), so the
-// state is untouched.  Results are kept per process and, if the environment
-// variable LCBP_AUTOTUNE_CACHE names a file, in that file ("nx ny nz dtype zc").
+// planes per CTA and sites per thread, chosen by timing each candidate once per
+// lattice shape and dtype; the runs write only scratch buffers (Q* to the H
+// scratch), so the state is untouched.  Results are kept per process and, if
+// the environment variable LCBP_AUTOTUNE_CACHE names a file, in that file
+// ("nx ny nz dtype zc spt" per line).
 std::mutex g_tune_mu;
-std::map<std::string, int> g_tune;
+std::map<std::string, std::pair<int, int>> g_tune;
 bool g_tune_loaded = false;
 
 std::string tune_key(const lcbp_lattice* h) {
@@ -420,22 +423,28 @@ std::string tune_key(const lcbp_lattice* h) {
 int tune_zc(lcbp_lattice* h) {
   std::lock_guard<std::mutex> lk(g_tune_mu);
   const char* path = std::getenv("LCBP_AUTOTUNE_CACHE");
+  const int spt_max = h->dtype == LCBP_F64 ? zm_spt_max<double>() : zm_spt_max<float>();
+  // a pinned sites-per-thread choice tunes only the planes per CTA, uncached
+  const bool pinned = h->path_req == LCBP_PATH_FAST1 || h->path_req == LCBP_PATH_FAST2;
+  const int spt_lo = h->path_req == LCBP_PATH_FAST2 ? 2 : 1;
+  const int spt_hi = h->path_req == LCBP_PATH_FAST1 ? 1 : spt_max;
   if (path && !g_tune_loaded) {
     g_tune_loaded = true;
     if (FILE* fp = std::fopen(path, "r")) {
-      int a, b, c, d, z;
-      while (std::fscanf(fp, "%d %d %d %d %d", &a, &b, &c, &d, &z) == 5) {
+      int a, b, c, d, z, sp;
+      while (std::fscanf(fp, "%d %d %d %d %d %d", &a, &b, &c, &d, &z, &sp) == 6) {
         char k[64];
         snprintf(k, sizeof(k), "%d %d %d %d", a, b, c, d);
-        g_tune[k] = z;
+        if (z >= 1 && sp >= 1 && sp <= 2) g_tune[k] = {z, sp};
       }
       std::fclose(fp);
     }
   }
   const std::string key = tune_key(h);
   auto it = g_tune.find(key);
-  if (it != g_tune.end()) {
-    h->zc = it->second;
+  if (!pinned && it != g_tune.end() && it->second.second <= spt_max) {
+    h->zc = it->second.first;
+    h->spt = it->second.second;
     return LCBP_OK;
   }
   const ModelBuf mb = host_model(h);
@@ -443,39 +452,45 @@ int tune_zc(lcbp_lattice* h) {
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
     return fail(LCBP_ECUDA, "event create");
   float best = 1e30f;
-  int best_zc = std::min(h->nz, 32);
-  for (int zc : {4, 8, 16, 32, 64}) {
-    if (zc > h->nz && zc != 4) break;
-    ZmArgs a = zm_args(h, mb.bytes);
-    a.zc = std::min(zc, h->nz);
-    a.qout = h->h;  // scratch
-    float t = 1e30f;
-    for (int rep = 0; rep < 3; ++rep) {
-      cudaEventRecord(e0, h->stream);
-      cudaError_t e = launch_zm(h, a);
-      cudaEventRecord(e1, h->stream);
-      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-      if (e != cudaSuccess) {
-        cudaEventDestroy(e0);
-        cudaEventDestroy(e1);
-        return cuda_fail(e, "autotune");
+  int best_zc = std::min(h->nz, 32), best_spt = spt_lo;
+  for (int spt = spt_lo; spt <= spt_hi; ++spt) {
+    for (int zc : {4, 8, 16, 32, 64}) {
+      if (zc > h->nz && zc != 4) break;
+      ZmArgs a = zm_args(h, mb.bytes);
+      a.zc = std::min(zc, h->nz);
+      a.spt = spt;
+      a.qout = h->h;  // scratch
+      float t = 1e30f;
+      for (int rep = 0; rep < 3; ++rep) {
+        cudaEventRecord(e0, h->stream);
+        cudaError_t e = launch_zm(h, a);
+        cudaEventRecord(e1, h->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        if (e != cudaSuccess) {
+          cudaEventDestroy(e0);
+          cudaEventDestroy(e1);
+          return cuda_fail(e, "autotune");
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        t = std::min(t, ms);
       }
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      t = std::min(t, ms);
-    }
-    if (t < best) {
-      best = t;
-      best_zc = a.zc;
+      if (t < best) {
+        best = t;
+        best_zc = a.zc;
+        best_spt = spt;
+      }
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   h->zc = best_zc;
-  g_tune[key] = best_zc;
+  h->spt = best_spt;
+  if (pinned) return LCBP_OK;
+  g_tune[key] = {best_zc, best_spt};
   if (path) {
     if (FILE* fp = std::fopen(path, "a")) {
-      std::fprintf(fp, "%s %d\n", key.c_str(), best_zc);
+      std::fprintf(fp, "%s %d %d\n", key.c_str(), best_zc, best_spt);
       std::fclose(fp);
     }
   }
@@ -905,17 +920,22 @@ int lcbp_profile_steps(lcbp_lattice* h, int nsteps, double* kernel_ms, int capac
 
 int lcbp_set_path(lcbp_lattice* h, int path) {
   CHECK_H(h);
-  if (path != LCBP_PATH_AUTO && path != LCBP_PATH_GENERIC) return fail(LCBP_EINVAL, "unknown path %d", path);
+  if (path < LCBP_PATH_AUTO || path > LCBP_PATH_FAST2) return fail(LCBP_EINVAL, "unknown path %d", path);
+  if (path == LCBP_PATH_FAST2 && h->dtype == LCBP_F64)
+    return fail(LCBP_EINVAL, "two sites per thread exist for FP32 lattices only");
   drop_graph(h);
   h->path_req = path;
+  h->zc = 0;  // retune for the new choice
+  h->spt = 0;
   return LCBP_OK;
 }
 
-int lcbp_get_path(lcbp_lattice* h, int* fast, int* planes_per_cta) {
+int lcbp_get_path(lcbp_lattice* h, int* fast, int* planes_per_cta, int* sites_per_thread) {
   CHECK_H(h);
   const bool f = use_fast(h);
   if (fast) *fast = f ? 1 : 0;
   if (planes_per_cta) *planes_per_cta = f ? h->zc : 0;
+  if (sites_per_thread) *sites_per_thread = f && h->zc > 0 ? h->spt : 0;
   return LCBP_OK;
 }
 

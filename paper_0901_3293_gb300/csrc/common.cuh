@@ -67,6 +67,92 @@ __host__ __device__ constexpr int ez(int i) {
 // ---------------------------------------------------------------------------
 // Symmetric traceless tensors in 5 components [xx, xy, xz, yy, yz].
 // ---------------------------------------------------------------------------
+// ---------------------------------------------------------------------------
+// Two-site vectors.  The fast kernels compute two lattice sites per thread in
+// the two lanes of a Vec2; for FP32 the lanes are packed into one 64-bit
+// register and added / multiplied with the paired FP32 instructions of the
+// sm_100 family (add / sub / mul .f32x2), which halves the floating-point
+// instruction count.  Vec2<double> is a plain pair.
+// ---------------------------------------------------------------------------
+template <typename T>
+struct Vec2 {
+  T x, y;
+  __device__ __forceinline__ Vec2() : x(T(0)), y(T(0)) {}
+  __device__ __forceinline__ Vec2(double v) : x(T(v)), y(T(v)) {}
+  __device__ __forceinline__ Vec2(float v) : x(T(v)), y(T(v)) {}
+  __device__ __forceinline__ Vec2(int v) : x(T(v)), y(T(v)) {}
+  __device__ __forceinline__ Vec2(T a, T b, int) : x(a), y(b) {}
+  __device__ __forceinline__ T lo() const { return x; }
+  __device__ __forceinline__ T hi() const { return y; }
+};
+template <typename T>
+__device__ __forceinline__ Vec2<T> operator+(Vec2<T> a, Vec2<T> b) { return Vec2<T>(a.x + b.x, a.y + b.y, 0); }
+template <typename T>
+__device__ __forceinline__ Vec2<T> operator-(Vec2<T> a, Vec2<T> b) { return Vec2<T>(a.x - b.x, a.y - b.y, 0); }
+template <typename T>
+__device__ __forceinline__ Vec2<T> operator*(Vec2<T> a, Vec2<T> b) { return Vec2<T>(a.x * b.x, a.y * b.y, 0); }
+template <typename T>
+__device__ __forceinline__ Vec2<T> operator-(Vec2<T> a) { return Vec2<T>(-a.x, -a.y, 0); }
+
+template <>
+struct Vec2<float> {
+  unsigned long long b;  // lane 0 in the low word, lane 1 in the high word
+  __device__ __forceinline__ Vec2() : b(0ull) {}
+  __device__ __forceinline__ Vec2(float v) { asm("mov.b64 %0, {%1, %1};" : "=l"(b) : "f"(v)); }
+  __device__ __forceinline__ Vec2(double v) : Vec2((float)v) {}
+  __device__ __forceinline__ Vec2(int v) : Vec2((float)v) {}
+  __device__ __forceinline__ Vec2(float a, float c, int) { asm("mov.b64 %0, {%1, %2};" : "=l"(b) : "f"(a), "f"(c)); }
+  __device__ __forceinline__ float lo() const {
+    float a, c;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(c) : "l"(b));
+    (void)c;
+    return a;
+  }
+  __device__ __forceinline__ float hi() const {
+    float a, c;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(c) : "l"(b));
+    (void)a;
+    return c;
+  }
+};
+using F2 = Vec2<float>;
+// no rounding modifier: the code generator may fuse a multiply and an add
+__device__ __forceinline__ F2 operator+(F2 a, F2 c) {
+  F2 r;
+  asm("add.f32x2 %0, %1, %2;" : "=l"(r.b) : "l"(a.b), "l"(c.b));
+  return r;
+}
+__device__ __forceinline__ F2 operator-(F2 a, F2 c) {
+  F2 r;
+  asm("sub.f32x2 %0, %1, %2;" : "=l"(r.b) : "l"(a.b), "l"(c.b));
+  return r;
+}
+__device__ __forceinline__ F2 operator*(F2 a, F2 c) {
+  F2 r;
+  asm("mul.f32x2 %0, %1, %2;" : "=l"(r.b) : "l"(a.b), "l"(c.b));
+  return r;
+}
+__device__ __forceinline__ F2 operator-(F2 a) { return F2(0.f) - a; }
+
+template <typename T>
+__device__ __forceinline__ Vec2<T>& operator+=(Vec2<T>& a, Vec2<T> c) { return a = a + c; }
+template <typename T>
+__device__ __forceinline__ Vec2<T>& operator-=(Vec2<T>& a, Vec2<T> c) { return a = a - c; }
+template <typename T>
+__device__ __forceinline__ Vec2<T>& operator*=(Vec2<T>& a, Vec2<T> c) { return a = a * c; }
+// lane-wise reciprocal
+template <typename T>
+__device__ __forceinline__ Vec2<T> recip(Vec2<T> a) { return Vec2<T>(T(1) / a.lo(), T(1) / a.hi(), 0); }
+__device__ __forceinline__ float recip(float a) { return 1.f / a; }
+__device__ __forceinline__ double recip(double a) { return 1.0 / a; }
+
+template <typename T>
+struct ScalarOf { using type = T; };
+template <typename T>
+struct ScalarOf<Vec2<T>> { using type = T; };
+// the rational constant a / b in the scalar type of `real`, folded at compile time
+#define LCBP_Q(a, b) real(typename ScalarOf<real>::type(a) / typename ScalarOf<real>::type(b))
+
 template <typename real>
 struct Sym5 {
   real xx, xy, xz, yy, yz;
@@ -185,7 +271,7 @@ __device__ __forceinline__ Sym5<real> molecular_field(const Stencil7<real>& st, 
   const real qq_yz = q.xy * q.xz + q.yy * q.yz + q.yz * qzz;
   const real qq_zz = q.xz * q.xz + q.yz * q.yz + qzz * qzz;
   const real trq2 = qq_xx + qq_yy + qq_zz;
-  const real third = real(1) / real(3);
+  const real third = LCBP_Q(1, 3);
   // 7-point Laplacian
   auto lap = [&](real c, real a, real b, real cc, real d, real e, real f) {
     return (a + b) + (cc + d) + (e + f) - real(6) * c;
@@ -238,11 +324,11 @@ __device__ __forceinline__ void lc_stress(const Sym5<real>& q, const Sym5<real>&
   // (HQ)_ab = (QH)_ba since both are symmetric
   const real trqh = QH[0][0] + QH[1][1] + QH[2][2];
   const real two_xi_tr = real(2) * xi * trqh;
-  const real two_third_xi = real(2) * xi / real(3);
+  const real two_third_xi = LCBP_Q(2, 3) * xi;
   // With P = Q + I/3:  H P + P H = H Q + Q H + 2H/3, and 2 xi P Tr(QH) carries
   // the isotropic part (2 xi / 3) Tr(QH) I on the diagonal.  The total is
   // traceless, so sigma_zz = -sigma_xx - sigma_yy holds and 5 components suffice.
-  const real iso = two_xi_tr / real(3);
+  const real iso = LCBP_Q(1, 3) * two_xi_tr;
   sigma.xx = two_xi_tr * q.xx + iso - xi * (QH[0][0] + QH[0][0]) - two_third_xi * h.xx;
   sigma.xy = two_xi_tr * q.xy - xi * (QH[0][1] + QH[1][0]) - two_third_xi * h.xy;
   sigma.xz = two_xi_tr * q.xz - xi * (QH[0][2] + QH[2][0]) - two_third_xi * h.xz;
@@ -277,7 +363,7 @@ __device__ __forceinline__ Sym5<real> be_rate(const Sym5<real>& q, const Sym5<re
     for (int b = 0; b < 3; ++b) {
       D[a][b] = real(0.5) * (w[a][b] + w[b][a]);
       O[a][b] = real(0.5) * (w[a][b] - w[b][a]);
-      P[a][b] = Q.a[a][b] + (a == b ? real(1) / real(3) : real(0));
+      P[a][b] = a == b ? Q.a[a][b] + LCBP_Q(1, 3) : Q.a[a][b];
     }
   real trQW = real(0);
 #pragma unroll
@@ -302,7 +388,7 @@ __device__ __forceinline__ Sym5<real> be_rate(const Sym5<real>& q, const Sym5<re
       }
       S[a][b] = xi * (dp + pd) + (op - po) - real(2) * xi * P[a][b] * trQW;
     }
-  const real trS3 = real(2) * xi * (D[0][0] + D[1][1] + D[2][2]) / real(9);
+  const real trS3 = LCBP_Q(2, 9) * xi * (D[0][0] + D[1][1] + D[2][2]);
   const real ux = u[0], uy = u[1], uz = u[2];
   auto adv = [&](real gx, real gy, real gz) { return ux * gx + uy * gy + uz * gz; };
   r.xx += (S[0][0] - trS3) - adv(dq[0].xx, dq[1].xx, dq[2].xx);
@@ -325,30 +411,56 @@ __device__ __forceinline__ Sym5<real> be_rate(const Sym5<real>& q, const Sym5<re
 // ---------------------------------------------------------------------------
 __host__ __device__ constexpr double rest_weight(int i) { return i == 0 ? 8.0 / 15.0 : 1.0 / 30.0; }
 
+// s_a x + s_b y + s_c z for signs s in {-1, 0, 1}.  With the signs known at
+// compile time (unrolled direction loops) only the additions and subtractions
+// of the nonzero terms remain, for the scalar and the packed types alike.
+template <typename real>
+__device__ __forceinline__ real signed_sum(int sa, real x, int sb, real y, int sc, real z) {
+  real pos = real(0), neg = real(0);
+  int np = 0, nn = 0;
+  auto put = [&](int sgn, real v) {
+    if (sgn > 0) {
+      pos = np ? pos + v : v;
+      ++np;
+    } else if (sgn < 0) {
+      neg = nn ? neg + v : v;
+      ++nn;
+    }
+  };
+  put(sa, x);
+  put(sb, y);
+  put(sc, z);
+  if (np && nn) return pos - neg;
+  if (np) return pos;
+  if (nn) return -neg;
+  return real(0);
+}
+
 template <typename real>
 __device__ __forceinline__ real feq_delta(int i, real drho, real rho, real ux, real uy, real uz, real usq,
                                           const Sym5<real>& s) {
   // A_0 = rho - 14 rho/30 = w_0 rho; A_1 = A_2 = w_s rho  ->  A_s - w_s = w_s drho
-  if (i == 0) return drho * (real(8) / real(15)) - rho * (real(2) / real(3)) * usq;
-  const real eu = real(ex(i)) * ux + real(ey(i)) * uy + real(ez(i)) * uz;
+  if (i == 0) return drho * LCBP_Q(8, 15) - rho * (LCBP_Q(2, 3) * usq);
+  const real eu = signed_sum(ex(i), ux, ey(i), uy, ez(i), uz);
   if (i <= 6) {
     // faces: A1 = rho/30, B1 = rho/3, C1 = -rho/12, D1 = rho/2, E1 = -sigma/2
-    const real see = (i <= 2) ? s.xx : (i <= 4) ? s.yy : s.zz();
-    return drho * (real(1) / real(30)) +
-           rho * (eu * (real(1) / real(3)) - usq * (real(1) / real(12)) + eu * eu * real(0.5)) - real(0.5) * see;
+    const real base = drho * LCBP_Q(1, 30) + rho * (eu * LCBP_Q(1, 3) - usq * LCBP_Q(1, 12) + eu * eu * real(0.5));
+    if (i <= 2) return base - real(0.5) * s.xx;
+    if (i <= 4) return base - real(0.5) * s.yy;
+    return base + real(0.5) * (s.xx + s.yy);  // sigma_zz = -sigma_xx - sigma_yy
   }
-  // corners: A2 = rho/30, B2 = rho/24, C2 = -rho/24, D2 = rho/16, E2 = -sigma/16
-  const real see = real(2) * (real(ex(i) * ey(i)) * s.xy + real(ex(i) * ez(i)) * s.xz + real(ey(i) * ez(i)) * s.yz);
-  return drho * (real(1) / real(30)) +
-         rho * (eu * (real(1) / real(24)) - usq * (real(1) / real(24)) + eu * eu * (real(1) / real(16))) -
-         (real(1) / real(16)) * see;
+  // corners: A2 = rho/30, B2 = rho/24, C2 = -rho/24, D2 = rho/16, E2 = -sigma/16 with
+  // e.sigma.e = 2 (ex ey sxy + ex ez sxz + ey ez syz) for a traceless sigma
+  const real off = signed_sum(ex(i) * ey(i), s.xy, ex(i) * ez(i), s.xz, ey(i) * ez(i), s.yz);
+  return drho * LCBP_Q(1, 30) + rho * (eu * LCBP_Q(1, 24) - usq * LCBP_Q(1, 24) + eu * eu * LCBP_Q(1, 16)) -
+         LCBP_Q(1, 8) * off;
 }
 
 template <typename real>
 __device__ __forceinline__ real force_dir(int i, real bx, real by, real bz) {
   if (i == 0) return real(0);
-  const real eb = real(ex(i)) * bx + real(ey(i)) * by + real(ez(i)) * bz;
-  return (i <= 6 ? real(1) / real(3) : real(1) / real(24)) * eb;
+  const real eb = signed_sum(ex(i), bx, ey(i), by, ez(i), bz);
+  return (i <= 6 ? LCBP_Q(1, 3) : LCBP_Q(1, 24)) * eb;
 }
 
 }  // namespace lcbp

@@ -104,6 +104,7 @@ struct ZmGeom {
 
 struct ZmArgs {
   int nx, ny, nz, zc;
+  int spt;            // sites per thread, 1 or 2 (2 only where zm_spt_max allows)
   const void* model;  // host copy of Model<real>
   const CUtensorMap *tm_q, *tm_u, *tm_sigma, *tm_b, *tm_qs;
   void *q, *qout, *qs, *sigma, *b;  // qout: nullptr = update Q in place
@@ -116,6 +117,8 @@ struct ZmArgs {
 constexpr int kZmBoxX = 40;  // elements per TMA box row
 template <typename real>
 int zm_tile_rows();
+template <typename real>
+int zm_spt_max();
 template <typename real>
 cudaError_t zm_prepare();
 template <typename real>

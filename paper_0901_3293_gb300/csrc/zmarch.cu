@@ -68,6 +68,63 @@ __device__ __forceinline__ Sym5<real> ld5(const real* sl, int comp_stride, int i
   return v;
 }
 
+// Sites per thread (SPT): with SPT = 2 a thread computes rows y and y + TY/2 of
+// the tile in the two lanes of a packed Vec2<float>, which halves the FP32
+// instruction count but also the resident warps (shared memory, not threads,
+// bounds the CTAs per SM).  Both builds exist for FP32; the autotuner times
+// them.  FP64 uses SPT = 1.
+template <typename real, int SPT>
+struct LaneT {
+  using V = real;
+};
+template <typename real>
+struct LaneT<real, 2> {
+  using V = Vec2<real>;
+};
+
+// value at element i0 (lane 0) and i1 (lane 1) of a shared or global array
+template <int SPT, typename real>
+__device__ __forceinline__ typename LaneT<real, SPT>::V vld(const real* p, long long i0, long long i1) {
+  if constexpr (SPT == 1) return p[i0];
+  else return Vec2<real>(p[i0], p[i1], 0);
+}
+template <int SPT, typename real, typename V>
+__device__ __forceinline__ real lane(const V& v, int k) {
+  if constexpr (SPT == 1) return v;
+  else return k == 0 ? v.lo() : v.hi();
+}
+template <int SPT, typename real>
+__device__ __forceinline__ Sym5<typename LaneT<real, SPT>::V> ld5v(const real* sl, int cs, int i0, int i1) {
+  Sym5<typename LaneT<real, SPT>::V> v;
+  v.xx = vld<SPT>(sl, i0, i1);
+  v.xy = vld<SPT>(sl, cs + i0, cs + i1);
+  v.xz = vld<SPT>(sl, 2 * cs + i0, 2 * cs + i1);
+  v.yy = vld<SPT>(sl, 3 * cs + i0, 3 * cs + i1);
+  v.yz = vld<SPT>(sl, 4 * cs + i0, 4 * cs + i1);
+  return v;
+}
+template <int SPT, typename real, typename V>
+__device__ __forceinline__ void store5_lane(real* p, long long n, long long s, const Sym5<V>& q, int k) {
+  p[s] = lane<SPT, real>(q.xx, k);
+  p[n + s] = lane<SPT, real>(q.xy, k);
+  p[2 * n + s] = lane<SPT, real>(q.xz, k);
+  p[3 * n + s] = lane<SPT, real>(q.yy, k);
+  p[4 * n + s] = lane<SPT, real>(q.yz, k);
+}
+template <typename V, typename real>
+__device__ __forceinline__ Model<V> widen(const Model<real>& m) {
+  Model<V> w;
+  w.a_bulk = V(m.a_bulk);
+  w.b_bulk = V(m.b_bulk);
+  w.K = V(m.K);
+  w.kq0x2 = V(m.kq0x2);
+  w.kq0sq4 = V(m.kq0sq4);
+  w.Gamma = V(m.Gamma);
+  w.xi = V(m.xi);
+  w.inv_tau = V(m.inv_tau);
+  return w;
+}
+
 // ---------------------------------------------------------------------------
 // Kernel A: H, sigma, tau, b and the Heun predictor
 // ---------------------------------------------------------------------------
@@ -83,14 +140,17 @@ struct QsideSmem {
   static constexpr size_t bytes = sizeof(real) * (size_t)OFF_BAR + 16 * 8 + 16;
 };
 
-template <typename real, int TY>
-__global__ void __launch_bounds__(ZM_TX* TY) k_qside(const __grid_constant__ CUtensorMap tmQ,
+template <typename real, int TY, int SPT>
+__global__ void __launch_bounds__(ZM_TX* TY / SPT) k_qside(const __grid_constant__ CUtensorMap tmQ,
                                                      const __grid_constant__ CUtensorMap tmU, ZmGeom G,
                                                      Model<real> m, const real* __restrict__ Q,
                                                      const real* __restrict__ rhou, const real* __restrict__ bext,
                                                      real* __restrict__ sigma, real* __restrict__ bout,
                                                      real* __restrict__ Qs, int* __restrict__ err) {
   using L = QsideSmem<real, TY>;
+  using V = typename LaneT<real, SPT>::V;
+  constexpr int TYH = TY / SPT;  // rows handled by one pass of the CTA
+  static_assert(TY % SPT == 0 && (TY + 2) % SPT == 0, "tile rows must split evenly between the lanes");
   extern __shared__ __align__(128) unsigned char smem_raw[];
   real* base = reinterpret_cast<real*>(smem_raw);
   real* qring = base;
@@ -107,9 +167,8 @@ __global__ void __launch_bounds__(ZM_TX* TY) k_qside(const __grid_constant__ CUt
   const int y0 = ((bt / G.tiles_x) % G.tiles_y) * TY;
   const int z0 = (bt / (G.tiles_x * G.tiles_y)) * G.zc;
   const int z1 = min(z0 + G.zc, nz);
-  const int tx = threadIdx.x % ZM_TX, ty = threadIdx.x / ZM_TX;
-  const int gx = x0 + tx, gy = y0 + ty;
-  const bool valid = gx < nx && gy < ny;
+  const int tx = threadIdx.x % ZM_TX, ty = threadIdx.x / ZM_TX;  // rows ty + k * TYH, k < SPT
+  const int gx = x0 + tx;
   const bool edge_q = x0 - 2 < 0 || x0 + ZM_TX + 2 > nx || y0 - 2 < 0 || y0 + TY + 2 > ny;
   const bool edge_u = x0 - 1 < 0 || x0 + ZM_TX + 1 > nx || y0 - 1 < 0 || y0 + TY + 1 > ny;
   constexpr uint32_t qbytes = 5 * L::QCS * sizeof(real), ubytes = 4 * L::UCS * sizeof(real);
@@ -153,7 +212,9 @@ __global__ void __launch_bounds__(ZM_TX* TY) k_qside(const __grid_constant__ CUt
   auto tslot = [&](int p) { return tring + wrap(p - z0, 3) * L::TSLOT; };
   auto hslot = [&](int p) { return hbuf + ((p - z0 + 2) & 1) * L::HSLOT; };
 
-  // H and tau of plane p on the tile plus a one-site ring (Q planes p-1..p+1)
+  // H and tau of plane p on the tile plus a one-site ring (Q planes p-1..p+1);
+  // a thread takes cells (r, c) and (r + TROWS / SPT, c) together
+  const Model<V> mv = widen<V>(m);
   auto field_plane = [&](int p) {
     const bool own = p >= z0 && p < z1;
     const real* qm = qslot(p - 1);
@@ -161,37 +222,42 @@ __global__ void __launch_bounds__(ZM_TX* TY) k_qside(const __grid_constant__ CUt
     const real* qp = qslot(p + 1);
     real* tp = tslot(p);
     real* hp = hslot(p);
-    for (int t = threadIdx.x; t < L::TROWS * L::TCOLS; t += blockDim.x) {
-      const int r = t / L::TCOLS, c = t % L::TCOLS;
-      const int idx = (r + 1) * ZM_BX + (c + 3);  // position in the Q box
-      Stencil7<real> st;
-      st.c = ld5(qc, L::QCS, idx);
-      st.xm = ld5(qc, L::QCS, idx - 1);
-      st.xp = ld5(qc, L::QCS, idx + 1);
-      st.ym = ld5(qc, L::QCS, idx - ZM_BX);
-      st.yp = ld5(qc, L::QCS, idx + ZM_BX);
-      st.zm = ld5(qm, L::QCS, idx);
-      st.zp = ld5(qp, L::QCS, idx);
-      Sym5<real> dq[3];
-      const Sym5<real> h = molecular_field(st, m, dq);
-      Sym5<real> sg;
-      real tu[3];
-      lc_stress(st.c, h, m.xi, sg, tu);
-      // sigma of an interior site of a plane this CTA owns goes straight out
-      const int sx = x0 + c - 1, sy = y0 + r - 1;
-      if (own && r >= 1 && r <= TY && c >= 1 && c <= ZM_TX && sx < nx && sy < ny)
-        store5(sigma, n, ((long long)p * ny + sy) * nx + sx, sg);
-      const int ti = r * L::TCOLS + c;
-      tp[ti] = tu[0];
-      tp[L::TROWS * L::TCOLS + ti] = tu[1];
-      tp[2 * L::TROWS * L::TCOLS + ti] = tu[2];
-      if (r >= 1 && r <= TY && c >= 1 && c <= ZM_TX) {
-        const int i = (r - 1) * ZM_TX + (c - 1);
-        hp[0 * TY * ZM_TX + i] = h.xx;
-        hp[1 * TY * ZM_TX + i] = h.xy;
-        hp[2 * TY * ZM_TX + i] = h.xz;
-        hp[3 * TY * ZM_TX + i] = h.yy;
-        hp[4 * TY * ZM_TX + i] = h.yz;
+    constexpr int RH = L::TROWS / SPT;
+    for (int t = threadIdx.x; t < RH * L::TCOLS; t += blockDim.x) {
+      const int r0 = t / L::TCOLS, c = t % L::TCOLS;
+      const int i0 = (r0 + 1) * ZM_BX + (c + 3);  // position in the Q box
+      const int i1 = i0 + RH * ZM_BX;
+      Stencil7<V> st;
+      st.c = ld5v<SPT>(qc, L::QCS, i0, i1);
+      st.xm = ld5v<SPT>(qc, L::QCS, i0 - 1, i1 - 1);
+      st.xp = ld5v<SPT>(qc, L::QCS, i0 + 1, i1 + 1);
+      st.ym = ld5v<SPT>(qc, L::QCS, i0 - ZM_BX, i1 - ZM_BX);
+      st.yp = ld5v<SPT>(qc, L::QCS, i0 + ZM_BX, i1 + ZM_BX);
+      st.zm = ld5v<SPT>(qm, L::QCS, i0, i1);
+      st.zp = ld5v<SPT>(qp, L::QCS, i0, i1);
+      Sym5<V> dq[3];
+      const Sym5<V> h = molecular_field(st, mv, dq);
+      Sym5<V> sg;
+      V tu[3];
+      lc_stress(st.c, h, mv.xi, sg, tu);
+#pragma unroll
+      for (int k = 0; k < SPT; ++k) {
+        const int r = r0 + k * RH;
+        const int ti = r * L::TCOLS + c;
+        tp[ti] = lane<SPT, real>(tu[0], k);
+        tp[L::TROWS * L::TCOLS + ti] = lane<SPT, real>(tu[1], k);
+        tp[2 * L::TROWS * L::TCOLS + ti] = lane<SPT, real>(tu[2], k);
+        if (r >= 1 && r <= TY && c >= 1 && c <= ZM_TX) {
+          const int i = (r - 1) * ZM_TX + (c - 1);
+          hp[0 * TY * ZM_TX + i] = lane<SPT, real>(h.xx, k);
+          hp[1 * TY * ZM_TX + i] = lane<SPT, real>(h.xy, k);
+          hp[2 * TY * ZM_TX + i] = lane<SPT, real>(h.xz, k);
+          hp[3 * TY * ZM_TX + i] = lane<SPT, real>(h.yy, k);
+          hp[4 * TY * ZM_TX + i] = lane<SPT, real>(h.yz, k);
+          // sigma of an interior site of a plane this CTA owns goes straight out
+          const int sx = x0 + c - 1, sy = y0 + r - 1;
+          if (own && sx < nx && sy < ny) store5_lane<SPT, real>(sigma, n, ((long long)p * ny + sy) * nx + sx, sg, k);
+        }
       }
     }
   };
@@ -227,57 +293,66 @@ __global__ void __launch_bounds__(ZM_TX* TY) k_qside(const __grid_constant__ CUt
     }
     field_plane(z + 1);
     __syncthreads();
-    if (valid) {
-      const long long s = ((long long)z * ny + gy) * nx + gx;
+    if (gx < nx && y0 + ty < ny) {
       const real* qm = qslot(z - 1);
       const real* qc = qslot(z);
       const real* qp = qslot(z + 1);
-      const int qi = (ty + 2) * ZM_BX + (tx + ZM_XOFF);
-      const Sym5<real> q = ld5(qc, L::QCS, qi);
-      Sym5<real> dq[3];
-      dq[0] = half_diff(ld5(qc, L::QCS, qi + 1), ld5(qc, L::QCS, qi - 1));
-      dq[1] = half_diff(ld5(qc, L::QCS, qi + ZM_BX), ld5(qc, L::QCS, qi - ZM_BX));
-      dq[2] = half_diff(ld5(qp, L::QCS, qi), ld5(qm, L::QCS, qi));
-      const Sym5<real> h = ld5(hslot(z), TY * ZM_TX, ty * ZM_TX + tx);
+      const int qi0 = (ty + 2) * ZM_BX + (tx + ZM_XOFF), qi1 = qi0 + TYH * ZM_BX;
+      const Sym5<V> q = ld5v<SPT>(qc, L::QCS, qi0, qi1);
+      Sym5<V> dq[3];
+      dq[0] = half_diff(ld5v<SPT>(qc, L::QCS, qi0 + 1, qi1 + 1), ld5v<SPT>(qc, L::QCS, qi0 - 1, qi1 - 1));
+      dq[1] = half_diff(ld5v<SPT>(qc, L::QCS, qi0 + ZM_BX, qi1 + ZM_BX),
+                        ld5v<SPT>(qc, L::QCS, qi0 - ZM_BX, qi1 - ZM_BX));
+      dq[2] = half_diff(ld5v<SPT>(qp, L::QCS, qi0, qi1), ld5v<SPT>(qm, L::QCS, qi0, qi1));
+      const int hi0 = ty * ZM_TX + tx;
+      const Sym5<V> h = ld5v<SPT>(hslot(z), TY * ZM_TX, hi0, hi0 + TYH * ZM_TX);
       // body force; tau = [xy, xz, yz] with tau_yx = -tau_xy etc.
       const real* tm = tslot(z - 1);
       const real* tc = tslot(z);
       const real* tpz = tslot(z + 1);
       constexpr int TCS = L::TROWS * L::TCOLS;
-      const int ti = (ty + 1) * L::TCOLS + (tx + 1);
-      const real half = real(0.5);
-      real bx = half * (tc[ti + L::TCOLS] - tc[ti - L::TCOLS]) + half * (tpz[TCS + ti] - tm[TCS + ti]);
-      real by = -half * (tc[ti + 1] - tc[ti - 1]) + half * (tpz[2 * TCS + ti] - tm[2 * TCS + ti]);
-      real bz = -half * (tc[TCS + ti + 1] - tc[TCS + ti - 1]) -
-                half * (tc[2 * TCS + ti + L::TCOLS] - tc[2 * TCS + ti - L::TCOLS]);
+      const int t0 = (ty + 1) * L::TCOLS + (tx + 1), t1 = t0 + TYH * L::TCOLS;
+      auto T = [&](const real* sl, int off) { return vld<SPT>(sl, t0 + off, t1 + off); };
+      const V half = V(0.5);
+      V bx = half * (T(tc, L::TCOLS) - T(tc, -L::TCOLS)) + half * (T(tpz, TCS) - T(tm, TCS));
+      V by = -(half * (T(tc, 1) - T(tc, -1))) + half * (T(tpz, 2 * TCS) - T(tm, 2 * TCS));
+      V bz = -(half * (T(tc, TCS + 1) - T(tc, TCS - 1))) -
+             half * (T(tc, 2 * TCS + L::TCOLS) - T(tc, 2 * TCS - L::TCOLS));
       bx -= ddot(h, dq[0]);
       by -= ddot(h, dq[1]);
       bz -= ddot(h, dq[2]);
-      if (bext) {
-        bx += bext[s];
-        by += bext[n + s];
-        bz += bext[2 * n + s];
-      }
       // velocity and its gradient from the rho u ring (components 1..3)
       const real* um = uslot(z - 1);
       const real* uc = uslot(z);
       const real* up = uslot(z + 1);
-      const int ui = (ty + 1) * ZM_BX + (tx + ZM_XOFF);
-      real u[3], w[3][3];
+      const int u0 = (ty + 1) * ZM_BX + (tx + ZM_XOFF), u1 = u0 + TYH * ZM_BX;
+      V u[3], w[3][3];
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
-        const int o = (a + 1) * L::UCS + ui;
-        u[a] = uc[o];
-        w[a][0] = half * (uc[o + 1] - uc[o - 1]);
-        w[a][1] = half * (uc[o + ZM_BX] - uc[o - ZM_BX]);
-        w[a][2] = half * (up[o] - um[o]);
+        const int o = (a + 1) * L::UCS;
+        u[a] = vld<SPT>(uc, o + u0, o + u1);
+        w[a][0] = half * (vld<SPT>(uc, o + u0 + 1, o + u1 + 1) - vld<SPT>(uc, o + u0 - 1, o + u1 - 1));
+        w[a][1] = half * (vld<SPT>(uc, o + u0 + ZM_BX, o + u1 + ZM_BX) - vld<SPT>(uc, o + u0 - ZM_BX, o + u1 - ZM_BX));
+        w[a][2] = half * (vld<SPT>(up, o + u0, o + u1) - vld<SPT>(um, o + u0, o + u1));
       }
-      const Sym5<real> r = be_rate(q, h, dq, u, w, m, true);
-      bout[s] = bx;
-      bout[n + s] = by;
-      bout[2 * n + s] = bz;
-      const Sym5<real> qs = {q.xx + r.xx, q.xy + r.xy, q.xz + r.xz, q.yy + r.yy, q.yz + r.yz};
-      store5(Qs, n, s, qs);
+      const Sym5<V> r = be_rate(q, h, dq, u, w, mv, true);
+      const Sym5<V> qs = {q.xx + r.xx, q.xy + r.xy, q.xz + r.xz, q.yy + r.yy, q.yz + r.yz};
+#pragma unroll
+      for (int k = 0; k < SPT; ++k) {
+        const int gy = y0 + ty + k * TYH;
+        if (gy >= ny) continue;
+        const long long s = ((long long)z * ny + gy) * nx + gx;
+        real ex_b[3] = {real(0), real(0), real(0)};
+        if (bext) {
+          ex_b[0] = bext[s];
+          ex_b[1] = bext[n + s];
+          ex_b[2] = bext[2 * n + s];
+        }
+        bout[s] = lane<SPT, real>(bx, k) + ex_b[0];
+        bout[n + s] = lane<SPT, real>(by, k) + ex_b[1];
+        bout[2 * n + s] = lane<SPT, real>(bz, k) + ex_b[2];
+        store5_lane<SPT, real>(Qs, n, s, qs, k);
+      }
     }
     __syncthreads();
   }
@@ -307,14 +382,16 @@ struct LbqSmem {
   static constexpr size_t bytes = sizeof(real) * (size_t)SLOTS * SLOT + 8 * 8 + 16;
 };
 
-template <typename real, int TY>
-__global__ void __launch_bounds__(ZM_TX* TY, TY == 8 ? 2 : 1)
+template <typename real, int TY, int SPT>
+__global__ void __launch_bounds__(ZM_TX* TY / SPT, 2)
     k_lbq(const __grid_constant__ CUtensorMap tmU, const __grid_constant__ CUtensorMap tmS,
           const __grid_constant__ CUtensorMap tmB, const __grid_constant__ CUtensorMap tmQs, ZmGeom G, Model<real> m,
           const real* __restrict__ f, const real* __restrict__ rhou, const real* __restrict__ sigma,
           const real* __restrict__ bf, const real* __restrict__ Qs, const real* __restrict__ Qin,
           real* __restrict__ fnew, real* __restrict__ rhou_new, real* __restrict__ Qout, int* __restrict__ err) {
   using L = LbqSmem<real, TY>;
+  using V = typename LaneT<real, SPT>::V;
+  constexpr int TYH = TY / SPT;  // a thread takes rows ty + k * TYH, k < SPT
   extern __shared__ __align__(128) unsigned char smem_raw[];
   real* ring = reinterpret_cast<real*>(smem_raw);
   uint64_t* bars = reinterpret_cast<uint64_t*>(ring + L::SLOTS * L::SLOT);
@@ -328,8 +405,16 @@ __global__ void __launch_bounds__(ZM_TX* TY, TY == 8 ? 2 : 1)
   const int z0 = (bt / (G.tiles_x * G.tiles_y)) * G.zc;
   const int z1 = min(z0 + G.zc, nz);
   const int tx = threadIdx.x % ZM_TX, ty = threadIdx.x / ZM_TX;
-  const int gx = x0 + tx, gy = y0 + ty;
-  const bool valid = gx < nx && gy < ny;
+  const int gx = x0 + tx;
+  int gy[SPT];
+  bool lane_ok[SPT];
+#pragma unroll
+  for (int k = 0; k < SPT; ++k) {
+    lane_ok[k] = gx < nx && y0 + ty + k * TYH < ny;
+    // a lane past the ragged y edge reads lane 0's site and stores nothing
+    gy[k] = lane_ok[k] ? y0 + ty + k * TYH : y0 + ty;
+  }
+  const bool valid = lane_ok[0];
   const bool edge = x0 - 1 < 0 || x0 + ZM_TX + 1 > nx || y0 - 1 < 0 || y0 + TY + 1 > ny;
   constexpr int CS = L::CS;
   constexpr uint32_t slot_bytes = (uint32_t)(17 * CS * sizeof(real));
@@ -370,10 +455,16 @@ __global__ void __launch_bounds__(ZM_TX* TY, TY == 8 ? 2 : 1)
       patch_plane(sl + L::OFF_Q, 5, L::ROWS, 3, ZM_TX + 5, Qs, n, nx, ny, zz, x0, y0 - 1);
     }
   };
-  // neighbour data: component k of [drho ux uy uz | sigma | b]
+  // neighbour data: component k of [drho ux uy uz | sigma | b] at box index idx
+  // for lane 0 and idx + TYH rows for lane 1
   auto Nv = [&](const real* sl, int k, int idx) {
     const int off = k < 4 ? k * CS : (k < 9 ? L::OFF_S + (k - 4) * CS : L::OFF_B + (k - 9) * CS);
-    return sl[off + idx];
+    return vld<SPT>(sl, off + idx, off + idx + TYH * ZM_BX);
+  };
+  // acc +/- v by the sign of e (compile-time after unrolling)
+  auto acc = [](V& a, int e, V v) {
+    if (e > 0) a += v;
+    else if (e < 0) a -= v;
   };
 
   bool aborted = false;
@@ -384,7 +475,14 @@ __global__ void __launch_bounds__(ZM_TX* TY, TY == 8 ? 2 : 1)
 
   // periodic source coordinates of the pull
   const int xm = wrap(gx - 1, nx), xp = wrap(gx + 1, nx);
-  const int ym = wrap(gy - 1, ny), yp = wrap(gy + 1, ny);
+  int ym[SPT], yp[SPT];
+#pragma unroll
+  for (int k = 0; k < SPT; ++k) {
+    ym[k] = wrap(gy[k] - 1, ny);
+    yp[k] = wrap(gy[k] + 1, ny);
+  }
+  const V inv_tau = V(m.inv_tau);
+  const Model<V> mv = widen<V>(m);
 
   for (int z = z0; z < z1; ++z) {
     if (threadIdx.x == 0) {
@@ -392,18 +490,21 @@ __global__ void __launch_bounds__(ZM_TX* TY, TY == 8 ? 2 : 1)
       if (z + 2 <= z1) issue(z + 2);
     }
     // populations f_i(y - e_i), issued before the barrier wait so that they overlap it
-    real fin[NV];
+    real fin_l[SPT][NV];
     if (valid) {
       const int zm = z == 0 ? nz - 1 : z - 1, zp = z + 1 == nz ? 0 : z + 1;
-      // three row bases per plane: rows y-1, y, y+1 of planes z-1, z, z+1
-      const long long rb[3][3] = {
-          {((long long)zm * ny + ym) * nx, ((long long)zm * ny + gy) * nx, ((long long)zm * ny + yp) * nx},
-          {((long long)z * ny + ym) * nx, ((long long)z * ny + gy) * nx, ((long long)z * ny + yp) * nx},
-          {((long long)zp * ny + ym) * nx, ((long long)zp * ny + gy) * nx, ((long long)zp * ny + yp) * nx}};
 #pragma unroll
-      for (int i = 0; i < NV; ++i) {
-        const int sx = ex(i) > 0 ? xm : ex(i) < 0 ? xp : gx;
-        fin[i] = __ldg(f + i * n + rb[1 - ez(i)][1 - ey(i)] + sx);
+      for (int k = 0; k < SPT; ++k) {
+        // three row bases per plane: rows y-1, y, y+1 of planes z-1, z, z+1
+        const long long rb[3][3] = {
+            {((long long)zm * ny + ym[k]) * nx, ((long long)zm * ny + gy[k]) * nx, ((long long)zm * ny + yp[k]) * nx},
+            {((long long)z * ny + ym[k]) * nx, ((long long)z * ny + gy[k]) * nx, ((long long)z * ny + yp[k]) * nx},
+            {((long long)zp * ny + ym[k]) * nx, ((long long)zp * ny + gy[k]) * nx, ((long long)zp * ny + yp[k]) * nx}};
+#pragma unroll
+        for (int i = 0; i < NV; ++i) {
+          const int sx = ex(i) > 0 ? xm : ex(i) < 0 ? xp : gx;
+          fin_l[k][i] = __ldg(f + i * n + rb[1 - ez(i)][1 - ey(i)] + sx);
+        }
       }
     }
     wait(z + 1);
@@ -413,79 +514,95 @@ __global__ void __launch_bounds__(ZM_TX* TY, TY == 8 ? 2 : 1)
       break;
     }
     if (valid) {
-      const long long s = ((long long)z * ny + gy) * nx + gx;
+      long long s[SPT];
+#pragma unroll
+      for (int k = 0; k < SPT; ++k) s[k] = ((long long)z * ny + gy[k]) * nx + gx;
       const real* nm = slot(z - 1);
       const real* nc = slot(z);
       const real* np = slot(z + 1);
       const int ci = (ty + 1) * ZM_BX + (tx + ZM_XOFF);
-      const real inv_tau = m.inv_tau;
-      real ds[NV], dh[NV];
-      Sym5<real> sig_y;
-      real b_y[3];
+      V fin[NV], ds[NV], dh[NV];
+#pragma unroll
+      for (int i = 0; i < NV; ++i) {
+        if constexpr (SPT == 1) fin[i] = fin_l[0][i];
+        else fin[i] = V(fin_l[0][i], fin_l[SPT - 1][i], 0);
+      }
+      Sym5<V> sig_y;
+      V b_y[3];
 #pragma unroll
       for (int i = 0; i < NV; ++i) {
         const real* sl = ez(i) > 0 ? nm : ez(i) < 0 ? np : nc;
         const int idx = ci - ey(i) * ZM_BX - ex(i);
-        const real drho = Nv(sl, 0, idx);
-        const real ux = Nv(sl, 1, idx), uy = Nv(sl, 2, idx), uz = Nv(sl, 3, idx);
-        const Sym5<real> sv = {Nv(sl, 4, idx), Nv(sl, 5, idx), Nv(sl, 6, idx), Nv(sl, 7, idx), Nv(sl, 8, idx)};
-        const real bx = Nv(sl, 9, idx), by = Nv(sl, 10, idx), bz = Nv(sl, 11, idx);
+        const V drho = Nv(sl, 0, idx);
+        const V ux = Nv(sl, 1, idx), uy = Nv(sl, 2, idx), uz = Nv(sl, 3, idx);
+        const Sym5<V> sv = {Nv(sl, 4, idx), Nv(sl, 5, idx), Nv(sl, 6, idx), Nv(sl, 7, idx), Nv(sl, 8, idx)};
+        const V bx = Nv(sl, 9, idx), by = Nv(sl, 10, idx), bz = Nv(sl, 11, idx);
         if (i == 0) {
           sig_y = sv;
-          b_y[0] = bx; b_y[1] = by; b_y[2] = bz;
+          b_y[0] = bx;
+          b_y[1] = by;
+          b_y[2] = bz;
         }
-        const real usq = ux * ux + uy * uy + uz * uz;
-        const real C = -(fin[i] - feq_delta(i, drho, real(1) + drho, ux, uy, uz, usq, sv)) * inv_tau +
-                       force_dir(i, bx, by, bz);
+        const V usq = ux * ux + uy * uy + uz * uz;
+        V C = (feq_delta(i, drho, V(1) + drho, ux, uy, uz, usq, sv) - fin[i]) * inv_tau;
+        if (i != 0) C += force_dir(i, bx, by, bz);
         ds[i] = fin[i] + C;
-        dh[i] = fin[i] + real(0.5) * C;
+        dh[i] = fin[i] + V(0.5) * C;
       }
-      real drs = real(0), jx = real(0), jy = real(0), jz = real(0);
+      V drs = ds[0], jx = V(0), jy = V(0), jz = V(0);
 #pragma unroll
-      for (int i = 0; i < NV; ++i) {
+      for (int i = 1; i < NV; ++i) {
         drs += ds[i];
-        jx += real(ex(i)) * ds[i];
-        jy += real(ey(i)) * ds[i];
-        jz += real(ez(i)) * ds[i];
+        acc(jx, ex(i), ds[i]);
+        acc(jy, ey(i), ds[i]);
+        acc(jz, ez(i), ds[i]);
       }
-      const real rs = real(1) + drs;
-      const real inv_rs = real(1) / rs;
-      const real usx = jx * inv_rs, usy = jy * inv_rs, usz = jz * inv_rs;
-      const real ussq = usx * usx + usy * usy + usz * usz;
-      real dr1 = real(0), j1x = real(0), j1y = real(0), j1z = real(0);
+      const V rs = V(1) + drs;
+      const V inv_rs = recip(rs);
+      const V usx = jx * inv_rs, usy = jy * inv_rs, usz = jz * inv_rs;
+      const V ussq = usx * usx + usy * usy + usz * usz;
+      V dr1 = V(0), j1x = V(0), j1y = V(0), j1z = V(0);
 #pragma unroll
       for (int i = 0; i < NV; ++i) {
-        const real Cs = -(ds[i] - feq_delta(i, drs, rs, usx, usy, usz, ussq, sig_y)) * inv_tau +
-                        force_dir(i, b_y[0], b_y[1], b_y[2]);
-        const real fo = dh[i] + real(0.5) * Cs;
-        fnew[i * n + s] = fo;
-        dr1 += fo;
-        j1x += real(ex(i)) * fo;
-        j1y += real(ey(i)) * fo;
-        j1z += real(ez(i)) * fo;
+        V Cs = (feq_delta(i, drs, rs, usx, usy, usz, ussq, sig_y) - ds[i]) * inv_tau;
+        if (i != 0) Cs += force_dir(i, b_y[0], b_y[1], b_y[2]);
+        const V fo = dh[i] + V(0.5) * Cs;
+#pragma unroll
+        for (int k = 0; k < SPT; ++k)
+          if (lane_ok[k]) fnew[i * n + s[k]] = lane<SPT, real>(fo, k);
+        dr1 = i == 0 ? fo : dr1 + fo;
+        acc(j1x, ex(i), fo);
+        acc(j1y, ey(i), fo);
+        acc(j1z, ez(i), fo);
       }
-      const real inv_r1 = real(1) / (real(1) + dr1);
-      rhou_new[s] = dr1;
-      rhou_new[n + s] = j1x * inv_r1;
-      rhou_new[2 * n + s] = j1y * inv_r1;
-      rhou_new[3 * n + s] = j1z * inv_r1;
+      const V inv_r1 = recip(V(1) + dr1);
+      const V u1x = j1x * inv_r1, u1y = j1y * inv_r1, u1z = j1z * inv_r1;
+#pragma unroll
+      for (int k = 0; k < SPT; ++k) {
+        if (!lane_ok[k]) continue;
+        rhou_new[s[k]] = lane<SPT, real>(dr1, k);
+        rhou_new[n + s[k]] = lane<SPT, real>(u1x, k);
+        rhou_new[2 * n + s[k]] = lane<SPT, real>(u1y, k);
+        rhou_new[3 * n + s[k]] = lane<SPT, real>(u1z, k);
+      }
 
       // Heun corrector with u^n
       const real* sm = nm + L::OFF_Q;
       const real* sc = nc + L::OFF_Q;
       const real* sp = np + L::OFF_Q;
-      Stencil7<real> st;
-      st.c = ld5(sc, CS, ci);
-      st.xm = ld5(sc, CS, ci - 1);
-      st.xp = ld5(sc, CS, ci + 1);
-      st.ym = ld5(sc, CS, ci - ZM_BX);
-      st.yp = ld5(sc, CS, ci + ZM_BX);
-      st.zm = ld5(sm, CS, ci);
-      st.zp = ld5(sp, CS, ci);
-      Sym5<real> dq[3];
-      const Sym5<real> h = molecular_field(st, m, dq);
-      real u[3], w[3][3];
-      const real half = real(0.5);
+      const int c1 = ci + TYH * ZM_BX;
+      Stencil7<V> st;
+      st.c = ld5v<SPT>(sc, CS, ci, c1);
+      st.xm = ld5v<SPT>(sc, CS, ci - 1, c1 - 1);
+      st.xp = ld5v<SPT>(sc, CS, ci + 1, c1 + 1);
+      st.ym = ld5v<SPT>(sc, CS, ci - ZM_BX, c1 - ZM_BX);
+      st.yp = ld5v<SPT>(sc, CS, ci + ZM_BX, c1 + ZM_BX);
+      st.zm = ld5v<SPT>(sm, CS, ci, c1);
+      st.zp = ld5v<SPT>(sp, CS, ci, c1);
+      Sym5<V> dq[3];
+      const Sym5<V> h = molecular_field(st, mv, dq);
+      V u[3], w[3][3];
+      const V half = V(0.5);
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
         u[a] = Nv(nc, a + 1, ci);
@@ -493,12 +610,19 @@ __global__ void __launch_bounds__(ZM_TX* TY, TY == 8 ? 2 : 1)
         w[a][1] = half * (Nv(nc, a + 1, ci + ZM_BX) - Nv(nc, a + 1, ci - ZM_BX));
         w[a][2] = half * (Nv(np, a + 1, ci) - Nv(nm, a + 1, ci));
       }
-      const Sym5<real> r = be_rate(st.c, h, dq, u, w, m, true);
-      const Sym5<real> q0 = load5(Qin, n, s);
-      const Sym5<real> q1 = {half * (q0.xx + st.c.xx + r.xx), half * (q0.xy + st.c.xy + r.xy),
-                             half * (q0.xz + st.c.xz + r.xz), half * (q0.yy + st.c.yy + r.yy),
-                             half * (q0.yz + st.c.yz + r.yz)};
-      store5(Qout, n, s, q1);
+      const Sym5<V> r = be_rate(st.c, h, dq, u, w, mv, true);
+      Sym5<V> q0;
+      q0.xx = vld<SPT>(Qin, s[0], s[SPT - 1]);
+      q0.xy = vld<SPT>(Qin, n + s[0], n + s[SPT - 1]);
+      q0.xz = vld<SPT>(Qin, 2 * n + s[0], 2 * n + s[SPT - 1]);
+      q0.yy = vld<SPT>(Qin, 3 * n + s[0], 3 * n + s[SPT - 1]);
+      q0.yz = vld<SPT>(Qin, 4 * n + s[0], 4 * n + s[SPT - 1]);
+      const Sym5<V> q1 = {half * (q0.xx + st.c.xx + r.xx), half * (q0.xy + st.c.xy + r.xy),
+                          half * (q0.xz + st.c.xz + r.xz), half * (q0.yy + st.c.yy + r.yy),
+                          half * (q0.yz + st.c.yz + r.yz)};
+#pragma unroll
+      for (int k = 0; k < SPT; ++k)
+        if (lane_ok[k]) store5_lane<SPT, real>(Qout, n, s[k], q1, k);
     }
     __syncthreads();
   }
@@ -524,15 +648,34 @@ int zm_tile_rows() {
   return zm_ty<real>();
 }
 
+// sites per thread the kernels are built for: FP32 one or two, FP64 one
 template <typename real>
-cudaError_t zm_prepare() {
+constexpr int zm_max_spt() {
+  return sizeof(real) == 4 ? 2 : 1;
+}
+
+template <typename real, int SPT>
+cudaError_t zm_prepare_spt() {
   constexpr int TY = zm_ty<real>();
-  cudaError_t e = cudaFuncSetAttribute(k_qside<real, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(k_qside<real, TY, SPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)QsideSmem<real, TY>::bytes);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_lbq<real, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(k_lbq<real, TY, SPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)LbqSmem<real, TY>::bytes);
   return e;
+}
+
+template <typename real>
+cudaError_t zm_prepare() {
+  cudaError_t e = zm_prepare_spt<real, 1>();
+  if constexpr (zm_max_spt<real>() == 2)
+    if (e == cudaSuccess) e = zm_prepare_spt<real, 2>();
+  return e;
+}
+
+template <typename real>
+int zm_spt_max() {
+  return zm_max_spt<real>();
 }
 
 ZmGeom zm_geom(int nx, int ny, int nz, int zc, int ty) {
@@ -548,19 +691,19 @@ ZmGeom zm_geom(int nx, int ny, int nz, int zc, int ty) {
   return G;
 }
 
-template <typename real>
-cudaError_t launch_step_zm(const ZmArgs& a, cudaStream_t s) {
+template <typename real, int SPT>
+cudaError_t launch_step_zm_spt(const ZmArgs& a, cudaStream_t s) {
   constexpr int TY = zm_ty<real>();
   const ZmGeom G = zm_geom(a.nx, a.ny, a.nz, a.zc, TY);
   const int grid = G.tiles_x * G.tiles_y * G.tiles_z;
   const Model<real> m = *static_cast<const Model<real>*>(a.model);
   if (a.events) cudaEventRecord(a.events[0], s);
-  k_qside<real, TY><<<grid, ZM_TX * TY, QsideSmem<real, TY>::bytes, s>>>(
+  k_qside<real, TY, SPT><<<grid, ZM_TX * TY / SPT, QsideSmem<real, TY>::bytes, s>>>(
       *a.tm_q, *a.tm_u, G, m, static_cast<const real*>(a.q), static_cast<const real*>(a.rhou),
       static_cast<const real*>(a.bext), static_cast<real*>(a.sigma), static_cast<real*>(a.b),
       static_cast<real*>(a.qs), a.err);
   if (a.events) cudaEventRecord(a.events[1], s);
-  k_lbq<real, TY><<<grid, ZM_TX * TY, LbqSmem<real, TY>::bytes, s>>>(
+  k_lbq<real, TY, SPT><<<grid, ZM_TX * TY / SPT, LbqSmem<real, TY>::bytes, s>>>(
       *a.tm_u, *a.tm_sigma, *a.tm_b, *a.tm_qs, G, m, static_cast<const real*>(a.f),
       static_cast<const real*>(a.rhou), static_cast<const real*>(a.sigma), static_cast<const real*>(a.b),
       static_cast<const real*>(a.qs), static_cast<const real*>(a.q), static_cast<real*>(a.fnew),
@@ -569,10 +712,19 @@ cudaError_t launch_step_zm(const ZmArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+template <typename real>
+cudaError_t launch_step_zm(const ZmArgs& a, cudaStream_t s) {
+  if constexpr (zm_max_spt<real>() == 2)
+    if (a.spt == 2) return launch_step_zm_spt<real, 2>(a, s);
+  return launch_step_zm_spt<real, 1>(a, s);
+}
+
 template cudaError_t zm_prepare<float>();
 template cudaError_t zm_prepare<double>();
 template int zm_tile_rows<float>();
 template int zm_tile_rows<double>();
+template int zm_spt_max<float>();
+template int zm_spt_max<double>();
 template cudaError_t launch_step_zm<float>(const ZmArgs&, cudaStream_t);
 template cudaError_t launch_step_zm<double>(const ZmArgs&, cudaStream_t);
 

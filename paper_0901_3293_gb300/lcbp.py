@@ -25,7 +25,7 @@ OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, ETIMEOUT, ESTATE, EIO = 0, -1, -2, -3, -4
 F32, F64 = 0, 1
 BPII, CHOL_X, CHOL_Y, CHOL_Z, ISO_NOISE, SLAB_BPII_IN_CHOL = range(6)
 JACOBI, GAUSS_SEIDEL = 0, 1
-PATH_AUTO, PATH_GENERIC = 0, 1
+PATH_AUTO, PATH_GENERIC, PATH_FAST1, PATH_FAST2 = 0, 1, 2, 3
 
 _lib = None
 
@@ -54,7 +54,7 @@ _SIGNATURES = {
     "lcbp_step": (_c_int, [_P, _c_int]),
     "lcbp_synchronize": (_c_int, [_P]),
     "lcbp_set_path": (_c_int, [_P, _c_int]),
-    "lcbp_get_path": (_c_int, [_P, ctypes.POINTER(_c_int), ctypes.POINTER(_c_int)]),
+    "lcbp_get_path": (_c_int, [_P, ctypes.POINTER(_c_int), ctypes.POINTER(_c_int), ctypes.POINTER(_c_int)]),
     "lcbp_profile_steps": (_c_int, [_P, _c_int, ctypes.POINTER(_c_double), _c_int, ctypes.POINTER(_c_int)]),
     "lcbp_read_q": (_c_int, [_P, _c_void_p, _c_int]),
     "lcbp_read_u": (_c_int, [_P, _c_void_p, _c_int]),
@@ -284,11 +284,12 @@ class Lattice:
         return self
 
     def path(self):
-        """(fast path in use, autotuned planes per CTA)."""
+        """(fast path in use, autotuned planes per CTA, sites per thread)."""
         fast = _c_int()
         zc = _c_int()
-        check(lib().lcbp_get_path(self._h, ctypes.byref(fast), ctypes.byref(zc)))
-        return bool(fast.value), zc.value
+        spt = _c_int()
+        check(lib().lcbp_get_path(self._h, ctypes.byref(fast), ctypes.byref(zc), ctypes.byref(spt)))
+        return bool(fast.value), zc.value, spt.value
 
     def synchronize(self) -> None:
         check(lib().lcbp_synchronize(self._h))

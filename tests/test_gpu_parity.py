@@ -80,6 +80,33 @@ def test_one_coupled_step_f64(lcbp, shape, path):
     assert np.abs(lat.read_u() - oracle_u(f)).max() < 1e-14
 
 
+FAST_PATHS = {"fast1": "PATH_FAST1", "fast2": "PATH_FAST2", "generic": "PATH_GENERIC"}
+
+
+@pytest.mark.parametrize("path", list(FAST_PATHS))
+@pytest.mark.parametrize("shape", SHAPES)
+def test_one_coupled_step_f32(lcbp, shape, path):
+    """FP32 state, both fast builds (one and two sites per thread) and the generic
+    kernels against the FP64 oracle.  Bounds: Q and f are O(1/2) in FP32 (ulp
+    2^-24 = 6e-8) after ~10^2 rounded operations of O(1e-3) increments, so a few
+    ulp; u is O(1e-3) and carries the rounding of O(1e-3) deviations."""
+    p = lbq.Params()
+    q5 = synth.smooth_q5(shape, 0.3, 1) + synth.random_q5(shape, 1e-2, 2)
+    f15 = synth.random_distributions(shape, 3, amp=2e-3)
+    lat = make(lcbp, shape, "f32", p)
+    lat.set_path(getattr(lcbp, FAST_PATHS[path]))
+    lat.set_q(q5).set_f(f15).step(1)
+    fast, _, spt = lat.path()
+    assert fast == (path != "generic" and shape[2] % 4 == 0)
+    if fast:
+        assert spt == (1 if path == "fast1" else 2)
+    f, Q = lbq.step(lbq.f_from_soa(f15.astype(np.float32).astype(np.float64)),
+                    lbq.q5_to_q9(q5.astype(np.float32).astype(np.float64)), p)
+    assert np.abs(lat.read_q() - lbq.q9_to_q5(Q)).max() < 2.5e-7
+    assert np.abs(lat.read_f() - lbq.f_to_soa(f)).max() < 2.5e-7
+    assert np.abs(lat.read_u() - oracle_u(f)).max() < 1e-8
+
+
 @pytest.mark.parametrize("coupling", ["jacobi", "gauss_seidel"])
 @pytest.mark.parametrize("flow_on", [True, False])
 def test_ten_steps_f64_modes(lcbp, coupling, flow_on):
@@ -162,19 +189,22 @@ def test_external_force_kolmogorov(lcbp, dtype, tol):
     assert np.abs(lat.read_u()).max() > 1e-5
 
 
+@pytest.mark.parametrize("fast", ["PATH_FAST1", "PATH_FAST2"])
 @pytest.mark.parametrize("shape", [(32, 32, 32), (6, 10, 36), (64, 64, 64)])
-def test_fast_path_matches_generic_f32(lcbp, shape):
+def test_fast_path_matches_generic_f32(lcbp, shape, fast):
     """Both kernel sets compute the same FP32 step (op order differs slightly)."""
     p = lbq.Params()
     a = make(lcbp, shape, "f32", p)
     b = make(lcbp, shape, "f32", p)
+    a.set_path(getattr(lcbp, fast))
     b.set_path(lcbp.PATH_GENERIC)
     for lat in (a, b):
         lat.init_q(lcbp.BPII, 0.3, noise=1e-3, seed=4).init_f_equilibrium(1.0).step(20)
     assert a.path()[0] and not b.path()[0] and a.path()[1] >= 1
     assert np.abs(a.read_q() - b.read_q()).max() < 1e-6
     assert np.abs(a.read_u() - b.read_u()).max() < 1e-8
-    assert np.abs(a.read_f() - b.read_f()).max() < 1e-8
+    # read_f rebuilds f = w + df in FP32: one ulp of a population in [1/2, 1) is 2^-24
+    assert np.abs(a.read_f() - b.read_f()).max() <= 2.0 ** -23
 
 
 def test_fast_path_external_force_f64(lcbp):
@@ -235,6 +265,12 @@ def test_errors_are_status_codes(lcbp):
     assert e.value.code == L.EINVAL
     with pytest.raises(L.LcbpError) as e:
         lat.init_q(99, 0.3)
+    assert e.value.code == L.EINVAL
+    with pytest.raises(L.LcbpError) as e:
+        lat.set_path(7)
+    assert e.value.code == L.EINVAL
+    with pytest.raises(L.LcbpError) as e:
+        L.Lattice(4, 4, 4, dtype="f64").set_path(L.PATH_FAST2)  # packed lanes are FP32 only
     assert e.value.code == L.EINVAL
     # a NaN planted in the host buffer is reported by the FP64 diagnostics
     q = np.zeros((5, 4, 4, 4))
