@@ -105,7 +105,7 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def oracle_sample_mlups(steps: int):
+def oracle_sample_mlups(steps: int, warmup: int = 1):
     """FP64 oracle on a periodic 32^3 cube of the same BPII state (two unit
     cells per side), timed on one host core.  Returns (MLUPS, seconds)."""
     from oracle import initial, lbq
@@ -113,7 +113,8 @@ def oracle_sample_mlups(steps: int):
     shape = (ORACLE_SAMPLE,) * 3
     Q = initial.init_q9(shape, initial.BPII, p.q0, 0.3, 1e-4, SEED)
     f = lbq.init_f_equilibrium(Q, p)
-    f, Q = lbq.step(f, Q, p)  # warm-up
+    for _ in range(warmup):
+        f, Q = lbq.step(f, Q, p)
     t0 = time.perf_counter()
     for _ in range(steps):
         f, Q = lbq.step(f, Q, p)
@@ -121,10 +122,11 @@ def oracle_sample_mlups(steps: int):
     return ORACLE_SAMPLE ** 3 * steps / dt / 1e6, dt
 
 
-def oracle_in_subprocess(steps: int):
+def oracle_in_subprocess(steps: int, warmup: int = 1):
+    """The oracle timed in a child process whose math libraries use one thread."""
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
     code = ("import sys, json; sys.path.insert(0, %r); import bench; "
-            "m, dt = bench.oracle_sample_mlups(%d); print(json.dumps([m, dt]))" % (ROOT, steps))
+            "m, dt = bench.oracle_sample_mlups(%d, %d); print(json.dumps([m, dt]))" % (ROOT, steps, warmup))
     out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, check=True)
     m, dt = json.loads(out.stdout.strip().splitlines()[-1])
     return m, dt
@@ -137,32 +139,28 @@ def cpu_baseline_entry(steps: int):
                       f"(pitch 32) state, {dt:.1f} s on one host core (numpy, threads pinned to 1)"}
 
 
+def workload_config(world: int) -> dict:
+    """The timed workload, shared by both arms' JSON lines."""
+    return {"workload": f"{N_SIDE}^3 periodic BPII (pitch 32), coupled D3Q15 LB + Beris-Edwards, FP32 state",
+            "sites_per_gpu": N_SIDE ** 3, "A0": PARAMS["A0"], "gamma": PARAMS["gamma"], "K": PARAMS["K"],
+            "q0": PARAMS["q0"], "tau_f": PARAMS["tau_f"], "l2": "state 4.5 GB >> 129 MB L2, no flush",
+            "parallelism": f"{world} independent replicas" if world > 1 else "single lattice"}
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    per_step = []
-    from oracle import initial, lbq
-    p = lbq.Params(**PARAMS)
-    shape = (ORACLE_SAMPLE,) * 3
-    Q = initial.init_q9(shape, initial.BPII, p.q0, 0.3, 1e-4, SEED)
-    f = lbq.init_f_equilibrium(Q, p)
-    for _ in range(args.warmup):
-        f, Q = lbq.step(f, Q, p)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        f, Q = lbq.step(f, Q, p)
-    dt = time.perf_counter() - t0
-    mlups = ORACLE_SAMPLE ** 3 * args.steps / dt / 1e6
+    mlups, dt = oracle_in_subprocess(args.steps, args.warmup)
     line = {
         "impl": "reference", "metric": "coupled LB+Q MLUPS", "value": mlups, "unit": "MLUPS",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"FP64 oracle on a {ORACLE_SAMPLE}^3 periodic sample of the 256^3 BPII (pitch 32) "
-                               "lattice", "sites_per_step": ORACLE_SAMPLE ** 3},
+        "config": workload_config(world),
         "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle",
-                         "sample": f"each step is one oracle step of a periodic {ORACLE_SAMPLE}^3 cube"},
+                         "sample": f"each step is one FP64 oracle step of a periodic {ORACLE_SAMPLE}^3 cube of "
+                                   f"the same BPII (pitch 32) state (numpy, one thread); MLUPS scale with sites"},
         "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -322,10 +320,7 @@ def run_ours(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": "256^3 periodic BPII (pitch 32), coupled D3Q15 LB + Beris-Edwards, FP32 state",
-                   "sites_per_gpu": sites, "A0": PARAMS["A0"], "gamma": PARAMS["gamma"], "K": PARAMS["K"],
-                   "q0": PARAMS["q0"], "tau_f": PARAMS["tau_f"], "l2": "state 4.5 GB >> 129 MB L2, no flush",
-                   "parallelism": f"{world} independent replicas" if world > 1 else "single lattice",
+        "config": {**workload_config(world),
                    "kernels": "fast (z-marching, TMA-staged planes)" if fast else "generic",
                    "planes_per_cta": zc, "sites_per_thread": spt},
         "roofline": roof, "per_kernel": per_kernel, "cpu_baseline": cpu, "e2e": e2e,

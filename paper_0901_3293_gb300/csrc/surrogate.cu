@@ -3,9 +3,12 @@
 // (conv.cu), FP32 weight gradients, masked-MSE loss and Adam, all on device.
 //
 // Network (channels-last BF16 activations, FP32 accumulate):
-//   x = [Q_xx Q_xy Q_xz Q_yy Q_yz, u / s_u, kappa - 1, tau]   (10 of 16 channels)
+//   x = [Q_xx Q_xy Q_xz Q_yy Q_yz, u / s_u, kappa - 1, tau, R / s_r]   (15 of 16 channels)
 //   h0 = relu(conv_in x);  4 x { a = relu(conv_a h);  h = h + conv_b a };
-//   y = conv_out h (5 of 16 channels);   Q(t + 10) = Q(t) + s_dq * y
+//   y = conv_out h (5 of 16 channels);   Q(t + 10) = Q(t) + 10 R + s_dq * y
+// with R = R(Q, u) the Beris-Edwards rate of the solver (Sec. 2.1 Eq.
+// Qevolution, mat_der), so the network learns the correction to ten explicit
+// Euler steps.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
