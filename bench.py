@@ -45,7 +45,30 @@ KERNEL_BYTES = {
 KERNELS_FAST = ["qside", "lbq"]
 KERNELS_GENERIC = ["field", "force_predict", "lb_correct"]
 STATE_BYTES = (15 + 5) * 2 * 4  # read + write of f and Q once per site-step (FP32)
+# DRAM bytes per site of one launch of each fast kernel (dram__bytes_read.sum +
+# dram__bytes_write.sum), from an ncu capture of 160^3 FP32 at the 256^3 tuning
+# (16 planes per CTA, one site per thread); summary and command in
+# profiles/step_256cube_fast_path.md.  Traffic per launch scales with the sites.
+# Valid only for the kernel sources it was taken on (hash below); otherwise null.
+MEASURED_TRAFFIC = {
+    "sources": ["paper_0901_3293_gb300/csrc/zmarch.cu", "paper_0901_3293_gb300/csrc/common.cuh",
+                "paper_0901_3293_gb300/csrc/tma.cuh"],
+    "sha256_16": "022ca92b361dd9c0",
+    "bytes_per_site": {"qside": (163475712 + 168136448) / 160 ** 3, "lbq": (837724160 + 360356608) / 160 ** 3},
+}
 ORACLE_SAMPLE = 32  # side of the periodic cube the oracle steps (two BPII unit cells)
+
+
+def measured_traffic_per_site(kernel: str):
+    """ncu DRAM bytes per site of `kernel`, or None if its sources changed since the capture."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in MEASURED_TRAFFIC["sources"]:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    if h.hexdigest()[:16] != MEASURED_TRAFFIC["sha256_16"]:
+        return None
+    return MEASURED_TRAFFIC["bytes_per_site"].get(kernel)
 
 
 def dist_env():
@@ -232,8 +255,11 @@ def run_ours(args):
         per_kernel[name] = {"ms": t, "algorithmic_bytes_per_site": KERNEL_BYTES[name], "GBps": gbs,
                             "frac_of_" + peak_kind: gbs / peak}
     dom = max(per_kernel, key=lambda k: per_kernel[k]["ms"])
+    tps = measured_traffic_per_site(dom) if fast else None
     roof = {"bound": "hbm", "achieved": per_kernel[dom]["GBps"], "peak": peak, "unit": "GB/s",
-            "frac": per_kernel[dom]["GBps"] / peak, "traffic": None, "kernel": dom,
+            "frac": per_kernel[dom]["GBps"] / peak, "traffic": tps * sites if tps else None,
+            "traffic_note": "ncu DRAM bytes per launch, captured on 160^3 and scaled by sites" if tps else
+            "no capture for these kernel sources", "kernel": dom,
             "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs, burst copy)",
             "step_algorithmic_frac": STATE_BYTES * sites * args.steps / (ms * 1e-3) / 1e9 / peak,
             "note": "step_algorithmic_frac counts only the 160 B/site of reading and writing f and Q once"}
