@@ -390,6 +390,16 @@ LCBP_API int lcbp_surrogate_destroy(lcbp_surrogate *s);
 /* Input scales s_u (velocity, default 1e-3) and s_r (rate, default 1e-3) and
  * the output scale s_dq (default 1e-3). */
 LCBP_API int lcbp_surrogate_set_scales(lcbp_surrogate *s, double s_u, double s_r, double s_dq);
+/* Convolution kernel: LCBP_CONV_AUTO (default) stages each input plane once
+ * per 128-site tile and serves all 27 taps from it (the "window" kernel)
+ * where that window fits shared memory (nx <= 101), else loads one shifted
+ * tile per tap (LCBP_CONV_TAPS).  LCBP_CONV_WINDOW
+ * requires the window kernel (LCBP_EINVAL where it does not fit).  Both
+ * compute the same sums (FP32 accumulation in a different order). */
+#define LCBP_CONV_AUTO 0
+#define LCBP_CONV_TAPS 1
+#define LCBP_CONV_WINDOW 2
+LCBP_API int lcbp_surrogate_set_conv_kernel(lcbp_surrogate *s, int kind);
 /* Upload / download the parameter vector (host or device FP32; Adam state is reset on upload). */
 LCBP_API int lcbp_surrogate_set_params(lcbp_surrogate *s, const float *params, size_t count);
 LCBP_API int lcbp_surrogate_get_params(lcbp_surrogate *s, float *params, size_t count);

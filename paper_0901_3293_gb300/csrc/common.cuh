@@ -103,15 +103,13 @@ struct Vec2<float> {
   __device__ __forceinline__ Vec2(int v) : Vec2((float)v) {}
   __device__ __forceinline__ Vec2(float a, float c, int) { asm("mov.b64 %0, {%1, %2};" : "=l"(b) : "f"(a), "f"(c)); }
   __device__ __forceinline__ float lo() const {
-    float a, c;
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(c) : "l"(b));
-    (void)c;
+    float a;
+    asm("{\n\t.reg .f32 t;\n\tmov.b64 {%0, t}, %1;\n\t}" : "=f"(a) : "l"(b));
     return a;
   }
   __device__ __forceinline__ float hi() const {
-    float a, c;
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(c) : "l"(b));
-    (void)a;
+    float c;
+    asm("{\n\t.reg .f32 t;\n\tmov.b64 {t, %0}, %1;\n\t}" : "=f"(c) : "l"(b));
     return c;
   }
 };

@@ -16,6 +16,8 @@
 #include <cuda.h>
 #include <cuda_bf16.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 #include "conv.h"
 #include "tc.cuh"
@@ -43,60 +45,56 @@ struct ConvSmem {
 __device__ __forceinline__ float bf2f(__nv_bfloat16 v) { return __bfloat162float(v); }
 
 
-// Epilogue of one output site: v[] holds the COUT accumulator values of site (x, y, z).
-template <int COUT, int EPI>
-__device__ __forceinline__ void conv_epilogue(float (&v)[COUT], int x, int y, int z, const ConvArgs& a) {
-  if (x >= a.nx || y >= a.ny) return;
+// Epilogue of channels c0 .. c0 + NC of one output site (x, y, z): bias from
+// registers, residual / mask operands already loaded (BF16, 8 per uint4).
+template <int COUT, int NC, int EPI>
+__device__ __forceinline__ void conv_epilogue_part(float (&v)[NC], const float (&bias)[NC], const uint4 (&rsd)[NC / 8],
+                                                   const uint4 (&msk)[NC / 8], int c0, int x, int y, int z,
+                                                   const ConvArgs& a) {
+  static_assert(NC % 8 == 0, "channel slices are whole 16-byte groups");
   const int px = a.nx + 2, py = a.ny + 2;
-  const long long pidx = ((long long)(z + 1) * py + (y + 1)) * px + (x + 1);
-  if (EPI & kEpiBias) {
 #pragma unroll
-    for (int c = 0; c < COUT; ++c) v[c] += a.bias[c];
-  }
+  for (int c = 0; c < NC; ++c) v[c] += bias[c];
   if (EPI & kEpiResid) {
-    const uint4* rp = reinterpret_cast<const uint4*>(a.resid + pidx * COUT);
 #pragma unroll
-    for (int q = 0; q < COUT / 8; ++q) {
-      const uint4 w4 = rp[q];
-      const __nv_bfloat16* h8 = reinterpret_cast<const __nv_bfloat16*>(&w4);
+    for (int q = 0; q < NC / 8; ++q) {
+      const __nv_bfloat16* h8 = reinterpret_cast<const __nv_bfloat16*>(&rsd[q]);
 #pragma unroll
       for (int j = 0; j < 8; ++j) v[q * 8 + j] += bf2f(h8[j]);
     }
   }
   if (EPI & kEpiRelu) {
 #pragma unroll
-    for (int c = 0; c < COUT; ++c) v[c] = fmaxf(v[c], 0.f);
+    for (int c = 0; c < NC; ++c) v[c] = fmaxf(v[c], 0.f);
   }
   if (EPI & kEpiMask) {
-    const uint4* mp = reinterpret_cast<const uint4*>(a.mask + pidx * COUT);
 #pragma unroll
-    for (int q = 0; q < COUT / 8; ++q) {
-      const uint4 w4 = mp[q];
-      const __nv_bfloat16* h8 = reinterpret_cast<const __nv_bfloat16*>(&w4);
+    for (int q = 0; q < NC / 8; ++q) {
+      const __nv_bfloat16* h8 = reinterpret_cast<const __nv_bfloat16*>(&msk[q]);
 #pragma unroll
       for (int j = 0; j < 8; ++j) v[q * 8 + j] = bf2f(h8[j]) > 0.f ? v[q * 8 + j] : 0.f;
     }
   }
   const long long site = ((long long)z * a.ny + y) * a.nx + x;
   if (EPI & kEpiOutF32) {
-    float4* op = reinterpret_cast<float4*>(a.out_f32 + site * COUT);
+    float4* op = reinterpret_cast<float4*>(a.out_f32 + site * COUT + c0);
 #pragma unroll
-    for (int q = 0; q < COUT / 4; ++q) op[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+    for (int q = 0; q < NC / 4; ++q) op[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
   } else if (EPI & kEpiUpdateQ) {
 #pragma unroll
-    for (int c = 0; c < 5; ++c)
-      a.qstate[c * a.n + site] += a.qscale * v[c] + (a.rate ? a.rate_scale * a.rate[c * a.n + site] : 0.f);
+    for (int c = 0; c < NC; ++c)
+      if (c0 + c < 5)
+        a.qstate[(c0 + c) * a.n + site] +=
+            a.qscale * v[c] + (a.rate ? a.rate_scale * a.rate[(c0 + c) * a.n + site] : 0.f);
   } else {
-    // BF16 channels-last at the site and at every ghost image of it
-    uint4 pk[COUT / 8];
+    uint4 pk[NC / 8];
 #pragma unroll
-    for (int q = 0; q < COUT / 8; ++q) {
+    for (int q = 0; q < NC / 8; ++q) {
       __nv_bfloat16* h8 = reinterpret_cast<__nv_bfloat16*>(&pk[q]);
 #pragma unroll
       for (int j = 0; j < 8; ++j) h8[j] = __float2bfloat16_rn(v[q * 8 + j]);
     }
-    // padded coordinates that hold this site: the interior one, and the
-    // opposite ghost layer when the site lies on a face (both for width 1)
+    // the interior position and, for a site on a face, the opposite ghost layer
     const int gx[3] = {x + 1, x == a.nx - 1 ? 0 : -1, x == 0 ? a.nx + 1 : -1};
     const int gy[3] = {y + 1, y == a.ny - 1 ? 0 : -1, y == 0 ? a.ny + 1 : -1};
     const int gz[3] = {z + 1, z == a.nz - 1 ? 0 : -1, z == 0 ? a.nz + 1 : -1};
@@ -106,13 +104,32 @@ __device__ __forceinline__ void conv_epilogue(float (&v)[COUT], int x, int y, in
         if (gy[iy] < 0) continue;
         for (int ix = 0; ix < 3; ++ix) {
           if (gx[ix] < 0) continue;
-          uint4* op = reinterpret_cast<uint4*>(a.out_bf16 + (((long long)gz[iz] * py + gy[iy]) * px + gx[ix]) * COUT);
 #pragma unroll
-          for (int q = 0; q < COUT / 8; ++q) op[q] = pk[q];
+          for (int q = 0; q < NC / 8; ++q)
+            *reinterpret_cast<uint4*>(a.out_bf16 + act_off(gx[ix], gy[iy], gz[iz], c0 / 8 + q, COUT, px, py)) = pk[q];
         }
       }
     }
   }
+}
+
+// Epilogue of one output site: v[] holds the COUT accumulator values of site
+// (x, y, z); residual and mask operands are read here.
+template <int COUT, int EPI>
+__device__ __forceinline__ void conv_epilogue(float (&v)[COUT], int x, int y, int z, const ConvArgs& a) {
+  if (x >= a.nx || y >= a.ny) return;
+  const int px = a.nx + 2, py = a.ny + 2;
+  float bias[COUT];
+  uint4 rsd[COUT / 8], msk[COUT / 8];
+#pragma unroll
+  for (int c = 0; c < COUT; ++c) bias[c] = (EPI & kEpiBias) ? a.bias[c] : 0.f;
+#pragma unroll
+  for (int q = 0; q < COUT / 8; ++q) {
+    const long long o = act_off(x + 1, y + 1, z + 1, q, COUT, px, py);
+    if (EPI & kEpiResid) rsd[q] = *reinterpret_cast<const uint4*>(a.resid + o);
+    if (EPI & kEpiMask) msk[q] = *reinterpret_cast<const uint4*>(a.mask + o);
+  }
+  conv_epilogue_part<COUT, COUT, EPI>(v, bias, rsd, msk, 0, x, y, z, a);
 }
 
 template <int CIN, int COUT, int EPI>
@@ -183,7 +200,10 @@ __global__ void __launch_bounds__(kConvThreads) k_conv_tc(const __grid_constant_
           if (k >= kConvStages && !bounded_wait(&empty[s], ((k / kConvStages) - 1) & 1)) break;
           const int dx = t % 3 - 1, dy = (t / 3) % 3 - 1, dz = t / 9 - 1;
           mbar_arrive_expect_tx(&full[s], L::STAGE);
-          tma_load_4d(stages + s * L::STAGE, &tmA, 0, x0 + 1 + dx, y0 + 1 + dy, z0 + 1 + dz, &full[s]);
+          // one box per channel group: 32 sites x 8 channels (512 B rows) x 4 rows
+          for (int q = 0; q < CIN / 8; ++q)
+            tma_load_4d(stages + s * L::STAGE + q * 2048, &tmA, 8 * (x0 + 1 + dx), y0 + 1 + dy, q, z0 + 1 + dz,
+                        &full[s]);
         }
       }
     }
@@ -208,7 +228,8 @@ __global__ void __launch_bounds__(kConvThreads) k_conv_tc(const __grid_constant_
           tc_fence_after();
 #pragma unroll
           for (int kk = 0; kk < CIN / 16; ++kk) {
-            const uint64_t ad = umma_sdesc(st_addr + s * L::STAGE + kk * 32, L::SBO, L::SWZ);
+            // A: [group][128 sites][8 channels], 16 B per site; one K step = two groups
+            const uint64_t ad = umma_sdesc_noswz(st_addr + s * L::STAGE + kk * 2 * 2048, 2048u, 128u);
             const uint64_t bd = umma_sdesc(w_addr + t * (COUT * CIN * 2) + kk * 32, L::SBO, L::SWZ);
             umma_bf16(d_tmem, ad, bd, idesc, (t > 0 || kk > 0) ? 1u : 0u);
           }
@@ -259,11 +280,307 @@ __global__ void __launch_bounds__(kConvThreads) k_conv_tc(const __grid_constant_
 
 
 // ---------------------------------------------------------------------------
+// Window kernel: one staged input window per plane serves all 27 taps.
+//
+// The padded plane is indexed linearly, l = Y px + X.  An M tile is 128
+// consecutive l; tap (dx, dy) of it is the same 128 rows shifted by
+// dy px + dx.  Each input plane is staged once per tile as the window
+// [l0 - px - 1, l0 + 128 + px + 1) in the no-swizzle K-major layout
+// [channel group of 8][site][8 BF16] (16 B per site, so SBO = 128 B and any
+// row shift is a 16-B shift of the descriptor's start address).  In the
+// chunk-planar activation layout each group's window is one contiguous run,
+// brought in by one bulk copy.  A CTA
+// walks a contiguous range of (tile, z) items with z fastest, so consecutive
+// items reuse two of their three planes; rows of a tile that fall on ghost
+// positions (X or Y on the padding) are computed and discarded.
+// ---------------------------------------------------------------------------
+constexpr int kWinPipes = 2;   // independent pipelines per CTA (they share the weights)
+constexpr int kWinSlots = 4;   // staged planes per pipeline
+constexpr int kWinAcc = 4;     // accumulator stages per pipeline in tensor memory
+// warps: 4 epilogue warps per pipeline (one TMEM lane quadrant each), then one
+// producer and one MMA warp per pipeline
+constexpr int kWinEpiWarps = 4 * kWinPipes;
+constexpr int kWinThreads = 32 * (kWinEpiWarps + 2 * kWinPipes);
+
+template <int CIN, int COUT>
+struct WinSmem {
+  static constexpr int CH = CIN / 8;  // 16-byte channel groups per site
+  // per pipeline: full[S], empty[S], accf[A], acce[A], done; then wbar
+  static constexpr int PBARS = 2 * kWinSlots + 2 * kWinAcc + 1;
+  static constexpr int NBARS = kWinPipes * PBARS + 1;
+  static constexpr uint32_t SWZ = CIN == 32 ? kSwizzle64B : kSwizzle32B;
+  static constexpr uint32_t WSBO = 8 * CIN * 2;
+  static constexpr uint32_t PIPE_COLS = kWinAcc * COUT;
+  static constexpr uint32_t TMEM_COLS = kWinPipes * PIPE_COLS < 32 ? 32 : kWinPipes * PIPE_COLS;
+};
+
+template <int CIN, int COUT, int EPI>
+__global__ void __launch_bounds__(kWinThreads) k_conv_win(const void* __restrict__ base,
+                                                          const __grid_constant__ CUtensorMap tmW, ConvArgs a,
+                                                          ConvWin g) {
+  using L = WinSmem<CIN, COUT>;
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  unsigned char* wsm = smem + g.off_w;  // 1024-aligned
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + g.off_bars);
+  uint64_t* wbar = bars + kWinPipes * L::PBARS;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(wbar + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  // role and pipeline of this warp
+  const int pipe = warp < kWinEpiWarps ? warp / 4 : (warp - kWinEpiWarps) % kWinPipes;
+  unsigned char* slots = smem + (size_t)pipe * kWinSlots * g.slot_bytes;  // this pipeline's planes
+  uint64_t* pb = bars + pipe * L::PBARS;
+  uint64_t* full = pb;
+  uint64_t* empty = pb + kWinSlots;
+  uint64_t* accf = pb + 2 * kWinSlots;
+  uint64_t* acce = accf + kWinAcc;
+  uint64_t* done = acce + kWinAcc;
+
+  // this pipeline's items: (tile T, plane z) with z fastest, a contiguous share
+  // of the CTA's range; every role walks them with incremental 32-bit counters
+  const long long items = (long long)g.ntiles * a.nz;
+  const long long cbeg = items * blockIdx.x / gridDim.x, cend = items * (blockIdx.x + 1) / gridDim.x;
+  const long long jbeg = cbeg + (cend - cbeg) * pipe / kWinPipes;
+  const long long jend = cbeg + (cend - cbeg) * (pipe + 1) / kWinPipes;
+  const int nitems = (int)(jend - jbeg);
+  const int T0 = (int)(jbeg / a.nz), z0 = (int)(jbeg % a.nz);
+  const long long plane = (long long)g.px * g.py;
+
+  if (threadIdx.x == 0) {
+    for (int p = 0; p < kWinPipes; ++p) {
+      uint64_t* q = bars + p * L::PBARS;
+      for (int i = 0; i < kWinSlots; ++i) {
+        mbar_init(&q[i], 1);
+        mbar_init(&q[kWinSlots + i], 1);
+      }
+      for (int i = 0; i < kWinAcc; ++i) {
+        mbar_init(&q[2 * kWinSlots + i], 1);
+        mbar_init(&q[2 * kWinSlots + kWinAcc + i], 128);
+      }
+      mbar_init(&q[2 * kWinSlots + 2 * kWinAcc], 1);
+    }
+    mbar_init(wbar, 1);
+    *abort_flag = 0;
+    mbar_init_fence();
+  }
+  if (warp == 0) {
+    tmem_alloc(tmem_slot, L::TMEM_COLS);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot + (uint32_t)pipe * L::PIPE_COLS;
+
+  auto bounded_wait = [&](uint64_t* bar, uint32_t parity) {
+    if (*abort_flag) return false;
+    if (!mbar_wait_bounded(bar, parity, kConvWaitNs)) {
+      *abort_flag = 1;
+      atomicExch(a.err, 1);
+      return false;
+    }
+    return true;
+  };
+
+  if (warp >= kWinEpiWarps && warp < kWinEpiWarps + kWinPipes) {
+    // ---------------- TMA producer: planes in the order the items need them
+    if (lane == 0) {
+      if (pipe == 0) {
+        tma_prefetch_desc(&tmW);
+        mbar_arrive_expect_tx(wbar, 27 * COUT * CIN * 2);
+        tma_load_3d(wsm, &tmW, 0, 0, 0, wbar);
+      }
+      const uint32_t tx_bytes = (uint32_t)(L::CH * g.wb * 16);
+      const __nv_bfloat16* src = static_cast<const __nv_bfloat16*>(base);
+      int sl = 0;        // slot of the next plane load
+      uint32_t eph = 0;  // parity of that slot's next release
+      int nloads = 0;
+      bool ok = true;
+      int T = T0, z = z0;
+      for (int it = 0; ok && it < nitems; ++it) {
+        const bool first = it == 0 || z == 0;
+        // window start inside a plane: first row of the tile minus px + 1
+        const long long w0 = (long long)g.l_first + (long long)T * 128 - (g.px + 1);
+        // padded planes z .. z+2 hold input planes z-1 .. z+1
+        for (int Z = first ? z : z + 2; Z <= z + 2; ++Z) {
+          if (nloads >= kWinSlots && !bounded_wait(&empty[sl], eph)) {
+            ok = false;
+            break;
+          }
+          unsigned char* dst = slots + (size_t)sl * g.slot_bytes;
+          mbar_arrive_expect_tx(&full[sl], tx_bytes);
+          for (int c = 0; c < L::CH; ++c)
+            bulk_load(dst + (size_t)c * g.lbo, src + ((long long)Z * L::CH + c) * plane * 8 + w0 * 8, g.wb * 16,
+                      &full[sl]);
+          ++nloads;
+          if (++sl == kWinSlots) {
+            sl = 0;
+            if (nloads > kWinSlots) eph ^= 1u;  // load n waits for release n - S: parity (n / S - 1) & 1
+          }
+        }
+        if (++z == a.nz) {
+          z = 0;
+          ++T;
+        }
+      }
+      if (!ok) {
+        // let copies still in flight land before the CTA's shared memory goes away
+        for (int i = 0; i < kWinSlots; ++i) {
+          mbar_wait_bounded(&full[i], 0, kConvWaitNs / 16);
+          mbar_wait_bounded(&full[i], 1, kConvWaitNs / 16);
+        }
+      }
+    }
+  } else if (warp >= kWinEpiWarps + kWinPipes) {
+    // ---------------- MMA issuer
+    if (lane == 0) {
+      constexpr uint32_t idesc = umma_idesc_bf16(128, COUT);
+      // descriptors are advanced by adding (byte offset >> 4) to the start-address field
+      const uint64_t bdesc0 = umma_sdesc(smem_addr(wsm), L::WSBO, L::SWZ);
+      const uint64_t adesc0 = umma_sdesc_noswz(smem_addr(slots), g.lbo, 128u);
+      const uint32_t slot16 = g.slot_bytes >> 4, lbo16 = g.lbo >> 4;
+      const int px = g.px;
+      bool ok = bounded_wait(wbar, 0);
+      // ring state of the loads: the three planes of the current item, oldest first
+      int ps[3] = {0, 0, 0};
+      uint32_t pph[3] = {0, 0, 0};
+      int nsl = 0;       // slot of the next load to consume
+      uint32_t nph = 0;  // its full-barrier parity
+      int acc = 0;
+      uint32_t aph = 0;  // accumulator-free parity
+      int z = z0;
+      for (int it = 0; ok && it < nitems; ++it) {
+        const bool first = it == 0 || z == 0;
+        for (int d = first ? 0 : 2; d < 3; ++d) {
+          if (!first) {
+            ps[0] = ps[1];
+            pph[0] = pph[1];
+            ps[1] = ps[2];
+            pph[1] = pph[2];
+          }
+          ps[d] = nsl;
+          pph[d] = nph;
+          if (++nsl == kWinSlots) {
+            nsl = 0;
+            nph ^= 1u;
+          }
+        }
+        if (it >= kWinAcc && !bounded_wait(&acce[acc], aph ^ 1u)) break;
+        // planes already seen complete by the previous item stay loaded until released
+        for (int d = first ? 0 : 2; d < 3; ++d)
+          if (!bounded_wait(&full[ps[d]], pph[d])) ok = false;
+        if (!ok) break;
+        tc_fence_after();
+        const uint32_t d_tmem = tmem_base + acc * COUT;
+        const uint64_t ab0 = adesc0 + (uint64_t)ps[0] * slot16, ab1 = adesc0 + (uint64_t)ps[1] * slot16,
+                       ab2 = adesc0 + (uint64_t)ps[2] * slot16;
+#pragma unroll
+        for (int t = 0; t < 27; ++t) {
+          const int dx = t % 3 - 1, dy = (t / 3) % 3 - 1, dz = t / 9;
+          // row shift of the tap in 16-byte units: px + 1 + dy px + dx
+          const uint32_t row16 = (uint32_t)(px + 1 + dy * px + dx);
+          const uint64_t ab = dz == 0 ? ab0 : (dz == 1 ? ab1 : ab2);
+#pragma unroll
+          for (int kc = 0; kc < CIN / 16; ++kc)
+            umma_bf16(d_tmem, ab + row16 + 2u * kc * lbo16, bdesc0 + (uint64_t)((t * (COUT * CIN * 2) + kc * 32) >> 4),
+                      idesc, (t > 0 || kc > 0) ? 1u : 0u);
+        }
+        umma_commit(&accf[acc]);
+        if (++acc == kWinAcc) {
+          acc = 0;
+          aph ^= 1u;
+        }
+        if (++z == a.nz) z = 0;
+        // release the planes the next item does not share with this one
+        const bool cont = it + 1 < nitems && z != 0;
+        umma_commit(&empty[ps[0]]);
+        if (!cont) {
+          umma_commit(&empty[ps[1]]);
+          umma_commit(&empty[ps[2]]);
+        }
+      }
+      // every issued MMA has finished before the CTA leaves
+      umma_commit(done);
+      mbar_wait_bounded(done, 0, kConvWaitNs);
+    }
+  } else {
+    // ---------------- epilogue: 4 warps per pipeline; warp w reads TMEM lanes 32 (w % 4) ..
+    // (one row of the tile each), all COUT channels
+    const int quad = warp % 4;
+    const int m = quad * 32 + lane;
+    float bias[COUT];
+#pragma unroll
+    for (int c = 0; c < COUT; ++c) bias[c] = (EPI & kEpiBias) ? a.bias[c] : 0.f;
+    int T = T0, z = z0;
+    // padded (X, Y) of this thread's row of tile T, advanced by 128 positions per tile
+    int l = g.l_first + T * 128 + m;
+    int Y = l / g.px, X = l - Y * g.px;
+    int acc = 0;
+    uint32_t fph = 0;
+    for (int it = 0; it < nitems; ++it) {
+      const bool real = X >= 1 && X <= g.px - 2 && Y >= 1 && Y <= g.py - 2;
+      // residual / mask operands do not depend on the accumulator: load them first
+      uint4 rsd[COUT / 8], msk[COUT / 8];
+      if (real) {
+#pragma unroll
+        for (int q = 0; q < COUT / 8; ++q) {
+          const long long o = act_off(X, Y, z + 1, q, COUT, g.px, g.py);
+          if (EPI & kEpiResid) rsd[q] = *reinterpret_cast<const uint4*>(a.resid + o);
+          if (EPI & kEpiMask) msk[q] = *reinterpret_cast<const uint4*>(a.mask + o);
+        }
+      }
+      const bool ok = __all_sync(0xffffffffu, bounded_wait(&accf[acc], fph));
+      if (!ok) break;
+      tc_fence_after();
+      const uint32_t taddr = tmem_base + ((uint32_t)(quad * 32) << 16) + acc * COUT;
+      float v[COUT];
+      if constexpr (COUT == 32) {
+        uint32_t r[32];
+        tmem_ld32(taddr, r);
+        tmem_ld_wait();
+#pragma unroll
+        for (int c = 0; c < 32; ++c) v[c] = __uint_as_float(r[c]);
+      } else {
+        uint32_t r[16];
+        tmem_ld16(taddr, r);
+        tmem_ld_wait();
+#pragma unroll
+        for (int c = 0; c < 16; ++c) v[c] = __uint_as_float(r[c]);
+      }
+      tc_fence_before();
+      mbar_arrive(&acce[acc]);
+      if (real) conv_epilogue_part<COUT, COUT, EPI>(v, bias, rsd, msk, 0, X - 1, Y - 1, z, a);
+      if (++acc == kWinAcc) {
+        acc = 0;
+        fph ^= 1u;
+      }
+      if (++z == a.nz) {
+        z = 0;
+        X += 128;
+        while (X >= g.px) {
+          X -= g.px;
+          ++Y;
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc(*tmem_slot, L::TMEM_COLS);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // host launch
 // ---------------------------------------------------------------------------
 template <int CIN, int COUT, int EPI>
-cudaError_t conv_launch_t(const CUtensorMap& tmA, const CUtensorMap& tmW, const ConvArgs& a, int max_ctas,
+cudaError_t conv_launch_t(const CUtensorMap& tmA, const CUtensorMap& tmW, const ConvArgs& a, int sms,
                           cudaStream_t s) {
+  const int max_ctas = 2 * sms;  // two CTAs fit an SM
   using L = ConvSmem<CIN, COUT>;
   static bool attr = false;
   if (!attr) {
@@ -278,10 +595,77 @@ cudaError_t conv_launch_t(const CUtensorMap& tmA, const CUtensorMap& tmW, const 
   return cudaGetLastError();
 }
 
-cudaError_t conv_launch(int cin, int cout, int epi, const CUtensorMap& tmA, const CUtensorMap& tmW,
-                        const ConvArgs& a, int max_ctas, cudaStream_t s) {
+bool conv_win_geometry(int cin, int cout, int nx, int ny, ConvWin* g, size_t* smem_bytes) {
+  ConvWin w{};
+  w.px = nx + 2;
+  w.py = ny + 2;
+  w.l_first = w.px + 1;
+  const long long span = (long long)(w.py - 2) * w.px - 2;  // linear positions from the first to the last interior site
+  w.ntiles = (int)((span + 127) / 128);
+  const int W = 128 + 2 * (w.px + 1);  // window length in sites
+  w.wb = (W + 7) / 8 * 8;
+  // the last window of a buffer may run past its last group: stay within the tail
+  const long long over = (long long)w.l_first + (long long)(w.ntiles - 1) * 128 - (w.px + 1) + w.wb -
+                         (long long)w.px * w.py;
+  if (over * 16 > (long long)kActTailBytes) return false;
+  w.lbo = (uint32_t)w.wb * 16;
+  w.slot_bytes = (uint32_t)(cin / 8) * w.lbo;
+  const uint32_t slots = kWinPipes * kWinSlots * w.slot_bytes;
+  w.off_w = (slots + 1023) / 1024 * 1024;
+  const uint32_t wbytes = ((27 * cout * cin * 2 + 1023) / 1024) * 1024;
+  w.off_bars = w.off_w + wbytes;
+  const int nbars = kWinPipes * (2 * kWinSlots + 2 * kWinAcc + 1) + 1;
+  const size_t need = (size_t)w.off_bars + nbars * 8 + 16 + 1024;  // + base alignment
+  if (need > 227 * 1024) return false;
+  *g = w;
+  *smem_bytes = need;
+  return true;
+}
+
+template <int CIN, int COUT, int EPI>
+cudaError_t conv_launch_win_t(const void* base, const CUtensorMap& tmW, const ConvArgs& a, const ConvWin& g,
+                              size_t smem, int sms, cudaStream_t s) {
+  static size_t attr = 0;
+  static int per_sm = 1;
+  if (attr < smem) {
+    cudaError_t e =
+        cudaFuncSetAttribute(k_conv_win<CIN, COUT, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_conv_win<CIN, COUT, EPI>, kWinThreads, smem);
+    if (e != cudaSuccess) return e;
+    per_sm = std::max(per_sm, 1);
+    attr = smem;
+  }
+  // one wave of persistent CTAs, each taking an equal share of the (tile, z) items
+  const long long items = (long long)g.ntiles * a.nz;
+  const int grid = (int)std::min<long long>(items, (long long)per_sm * sms);
+  k_conv_win<CIN, COUT, EPI><<<grid, kWinThreads, smem, s>>>(base, tmW, a, g);
+  return cudaGetLastError();
+}
+
+cudaError_t conv_launch(int cin, int cout, int epi, const ConvMaps& m, bool allow_win, const CUtensorMap& tmW,
+                        const ConvArgs& a, int sms, cudaStream_t s) {
+  ConvWin g;
+  size_t smem = 0;
+  if (allow_win && m.use_win && conv_win_geometry(cin, cout, a.nx, a.ny, &g, &smem)) {
+#define LCBP_CONV_WIN_CASE(CI, CO, E) \
+  if (cin == CI && cout == CO && epi == (E)) return conv_launch_win_t<CI, CO, E>(m.base, tmW, a, g, smem, sms, s);
+    LCBP_CONV_WIN_CASE(16, 32, kEpiBias | kEpiRelu)
+    LCBP_CONV_WIN_CASE(32, 32, kEpiBias | kEpiRelu)
+    LCBP_CONV_WIN_CASE(32, 32, kEpiBias | kEpiResid)
+    LCBP_CONV_WIN_CASE(32, 16, kEpiBias | kEpiOutF32)
+    LCBP_CONV_WIN_CASE(32, 16, kEpiBias | kEpiUpdateQ)
+    LCBP_CONV_WIN_CASE(16, 32, 0)
+    LCBP_CONV_WIN_CASE(32, 32, kEpiMask)
+    LCBP_CONV_WIN_CASE(32, 32, kEpiResid)
+    LCBP_CONV_WIN_CASE(32, 32, kEpiResid | kEpiMask)
+    LCBP_CONV_WIN_CASE(32, 32, 0)
+#undef LCBP_CONV_WIN_CASE
+    return cudaErrorInvalidValue;
+  }
+  const CUtensorMap& tmA = m.tile;
 #define LCBP_CONV_CASE(CI, CO, E) \
-  if (cin == CI && cout == CO && epi == (E)) return conv_launch_t<CI, CO, E>(tmA, tmW, a, max_ctas, s);
+  if (cin == CI && cout == CO && epi == (E)) return conv_launch_t<CI, CO, E>(tmA, tmW, a, sms, s);
   // forward: input layer, hidden layers, residual layers, output layer (FP32 out / Q update)
   LCBP_CONV_CASE(16, 32, kEpiBias | kEpiRelu)
   LCBP_CONV_CASE(32, 32, kEpiBias | kEpiRelu)

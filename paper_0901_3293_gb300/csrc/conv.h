@@ -5,6 +5,8 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <cstdint>
+
 namespace lcbp {
 
 // epilogue flags
@@ -32,9 +34,46 @@ struct ConvArgs {
   int* err;
 };
 
-// y = conv(x) on tcgen05; tmA describes the padded BF16 input (box C_in x 32 x 4 x 1,
-// swizzled), tmW the BF16 weights [27][C_out][C_in] (one box of all taps)
-cudaError_t conv_launch(int cin, int cout, int epi, const CUtensorMap& tmA, const CUtensorMap& tmW,
-                        const ConvArgs& a, int max_ctas, cudaStream_t s);
+// Padded BF16 activations are stored chunk-planar: channels in groups of 8
+// (16 bytes), each group a full padded volume,
+//   element (X, Y, Z, c) at (((Z * C/8 + c/8) * py + Y) * px + X) * 8 + c % 8,
+// with px = nx + 2, py = ny + 2 and one ghost layer per face holding periodic
+// images.  A run of consecutive sites of one group is contiguous memory.
+__host__ __device__ inline long long act_off(int X, int Y, int Z, int group, int C, int px, int py) {
+  return ((((long long)Z * (C / 8) + group) * py + Y) * px + X) * 8;
+}
+// bytes allocated after the last group of a buffer, which the window kernel's
+// last copies may read past (into nothing it uses)
+constexpr size_t kActTailBytes = 64 * 1024;
+
+// geometry of the window kernel (host-computed)
+struct ConvWin {
+  int px, py;          // padded plane extents
+  int l_first;         // linear index of the first interior site in a padded plane
+  int ntiles;          // 128-row tiles covering the interior rows of a plane
+  int wb;              // sites copied per channel group and plane (window, rounded up to 8)
+  uint32_t lbo;        // bytes between channel groups of a staged plane (= wb * 16)
+  uint32_t slot_bytes; // bytes of one staged plane
+  uint32_t off_w, off_bars;
+};
+
+// one padded BF16 activation buffer: the per-tap kernel's tensor map (4-D
+// view (8 px, py, C/8, pz), boxes of 32 sites x 4 rows of one group) and the
+// raw pointer the window kernel copies from
+struct ConvMaps {
+  CUtensorMap tile;
+  const void* base;
+  bool use_win;
+};
+
+// window geometry for C_in, C_out on an nx x ny plane; false if it does not fit
+bool conv_win_geometry(int cin, int cout, int nx, int ny, ConvWin* g, size_t* smem_bytes);
+
+// y = conv(x) on tcgen05; m describes the padded BF16 input, tmW the BF16
+// weights [27][C_out][C_in] (one box of all taps), sms the device's SM count.
+// The window kernel runs where allowed, m.use_win is set and the geometry
+// fits; the per-tap kernel otherwise.
+cudaError_t conv_launch(int cin, int cout, int epi, const ConvMaps& m, bool allow_win, const CUtensorMap& tmW,
+                        const ConvArgs& a, int sms, cudaStream_t s);
 
 }  // namespace lcbp

@@ -62,7 +62,7 @@ size_t true_param_count() {
 // ---------------------------------------------------------------------------
 // kernels
 // ---------------------------------------------------------------------------
-// network input from physical fields: Q [5][n], u [3][n], R [5][n] (FP32) -> padded BF16 [.][16]
+// network input from physical fields: Q [5][n], u [3][n], R [5][n] (FP32) -> padded BF16, 16 channels, chunk-planar
 __global__ void k_sur_input(const float* __restrict__ q, const float* __restrict__ u, const float* __restrict__ r,
                             float su, float sr, float kap, float tau, int nx, int ny, int nz,
                             __nv_bfloat16* __restrict__ out) {
@@ -90,16 +90,15 @@ __global__ void k_sur_input(const float* __restrict__ q, const float* __restrict
 #pragma unroll
       for (int j = 0; j < 8; ++j) h8[j] = __float2bfloat16_rn(v[q2 * 8 + j]);
     }
-    uint4* op = reinterpret_cast<uint4*>(out + p * 16);
-    op[0] = pk[0];
-    op[1] = pk[1];
+    *reinterpret_cast<uint4*>(out + act_off(X, Y, Z, 0, 16, px, py)) = pk[0];
+    *reinterpret_cast<uint4*>(out + act_off(X, Y, Z, 1, 16, px, py)) = pk[1];
   }
 }
 
 // u of a lattice: rho u stored as [drho, ux, uy, uz] -> pointer to ux..uz given by caller
 
 // masked MSE on y (FP32 [n][16], first 5 channels) against (dq - 10 R) / s_dq
-// (FP32 [5][n]); writes the BF16 padded gradient d loss / d y and per-block partial sums
+// (FP32 [5][n]); writes the BF16 padded (chunk-planar) gradient d loss / d y and per-block partial sums
 __global__ void k_sur_loss(const float* __restrict__ y, const float* __restrict__ target,
                            const float* __restrict__ rate, const float* __restrict__ mask, float inv_sdq,
                            double inv_den, int nx, int ny, int nz, __nv_bfloat16* __restrict__ grad,
@@ -131,9 +130,8 @@ __global__ void k_sur_loss(const float* __restrict__ y, const float* __restrict_
 #pragma unroll
       for (int j = 0; j < 8; ++j) h8[j] = __float2bfloat16_rn(g[q2 * 8 + j]);
     }
-    uint4* op = reinterpret_cast<uint4*>(grad + p * 16);
-    op[0] = pk[0];
-    op[1] = pk[1];
+    *reinterpret_cast<uint4*>(grad + act_off(X, Y, Z, 0, 16, px, py)) = pk[0];
+    *reinterpret_cast<uint4*>(grad + act_off(X, Y, Z, 1, 16, px, py)) = pk[1];
   }
   __shared__ double red[256];
   red[threadIdx.x] = acc;
@@ -184,8 +182,8 @@ __global__ void __launch_bounds__(CX* CY / 16) k_sur_dw(const __nv_bfloat16* __r
       if (s < s_end) {
         const int x = (int)(s % nx), y = (int)((s / nx) % ny), z = (int)(s / ((long long)nx * ny));
         const __nv_bfloat16* src;
-        if (inx) src = X + ((((long long)(z + 1 + dz) * py + (y + 1 + dy)) * px + (x + 1 + dx)) * CX + part * 8);
-        else src = dY + ((((long long)(z + 1) * py + (y + 1)) * px + (x + 1)) * CY + (part - CX / 8) * 8);
+        if (inx) src = X + act_off(x + 1 + dx, y + 1 + dy, z + 1 + dz, part, CX, px, py);
+        else src = dY + act_off(x + 1, y + 1, z + 1, part - CX / 8, CY, px, py);
         const uint4 w4 = *reinterpret_cast<const uint4*>(src);
         const __nv_bfloat16* h8 = reinterpret_cast<const __nv_bfloat16*>(&w4);
 #pragma unroll
@@ -297,18 +295,29 @@ EncodeFn encoder() {
   return fn;
 }
 
-// padded activations [nz+2][ny+2][nx+2][C] as a 4-D tensor, box C x 32 x 4 x 1
+// padded chunk-planar activations as the 4-D tensor (8 px, py, C/8, pz): a box
+// of 256 x 4 x 1 x 1 is 32 sites x 8 channels in 4 rows of one channel group
 bool act_map(CUtensorMap* m, void* base, int C, int nx, int ny, int nz) {
   EncodeFn fn = encoder();
   if (!fn) return false;
   const cuuint64_t px = nx + 2, py = ny + 2, pz = nz + 2;
-  const cuuint64_t dims[4] = {(cuuint64_t)C, px, py, pz};
-  const cuuint64_t str[3] = {(cuuint64_t)C * 2, (cuuint64_t)C * 2 * px, (cuuint64_t)C * 2 * px * py};
-  const cuuint32_t box[4] = {(cuuint32_t)C, 32, 4, 1};
+  const cuuint64_t dims[4] = {8 * px, py, (cuuint64_t)C / 8, pz};
+  const cuuint64_t str[3] = {16 * px, 16 * px * py, 16 * px * py * (cuuint64_t)(C / 8)};
+  const cuuint32_t box[4] = {256, 4, 1, 1};
   const cuuint32_t es[4] = {1, 1, 1, 1};
   return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, base, dims, str, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-            C == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// both views of one activation buffer; the window kernel only where its geometry fits
+bool conv_maps(ConvMaps* m, void* base, int C, int nx, int ny, int nz) {
+  if (!act_map(&m->tile, base, C, nx, ny, nz)) return false;
+  ConvWin g;
+  size_t smem = 0;
+  m->base = base;
+  m->use_win = conv_win_geometry(C, 32, nx, ny, &g, &smem) && conv_win_geometry(32, 16, nx, ny, &g, &smem);
+  return true;
 }
 
 // weights [27][rows][K] BF16 as a 3-D tensor, one box of all taps
@@ -335,7 +344,8 @@ struct lcbp_surrogate {
   int device;
   cudaStream_t stream;
   float su, sr, sdq;
-  int max_ctas;
+  int sms;
+  int conv_kernel;  // LCBP_CONV_*
   // parameters: FP32 master (padded) per layer, BF16 forward / backward copies
   float* master;  // all layers, padded
   size_t off_w[kLayers], off_b[kLayers];
@@ -345,7 +355,7 @@ struct lcbp_surrogate {
   CUtensorMap tmWf[kLayers], tmWb[kLayers];
   // activations (padded BF16): X (16), H[0..4], A[0..3] (32); gradients dH, dA (32), G16 (16)
   __nv_bfloat16 *X, *H[kBlocks + 1], *A[kBlocks], *dH, *dA, *G16;
-  CUtensorMap tmX, tmH[kBlocks + 1], tmA[kBlocks], tmdH, tmdA, tmG16;
+  ConvMaps tmX, tmH[kBlocks + 1], tmA[kBlocks], tmdH, tmdA, tmG16;
   float* y16;     // [n][16]
   float* tgt;     // [5][n] staging of the target
   float* msk;     // [n]
@@ -361,6 +371,8 @@ struct lcbp_surrogate {
 };
 
 namespace {
+
+bool use_win(const lcbp_surrogate* s) { return s->conv_kernel != LCBP_CONV_TAPS; }
 
 int sur_alloc(lcbp_surrogate* s, void** p, size_t bytes) {
   cudaError_t e = cudaMalloc(p, bytes);
@@ -399,24 +411,24 @@ cudaError_t forward(lcbp_surrogate* s, float* qupdate, const float* rate = nullp
   // h0 = relu(conv_in x)
   a.bias = s->master + s->off_b[0];
   a.out_bf16 = s->H[0];
-  e = conv_launch(16, 32, kEpiBias | kEpiRelu, s->tmX, s->tmWf[0], a, s->max_ctas, s->stream);
+  e = conv_launch(16, 32, kEpiBias | kEpiRelu, s->tmX, use_win(s), s->tmWf[0], a, s->sms, s->stream);
   if (e != cudaSuccess) return e;
   for (int k = 0; k < kBlocks; ++k) {
     const int la = 1 + 2 * k, lb = 2 + 2 * k;
     // training keeps every activation; inference ping-pongs H[0] / H[1]
     const int hin = s->training ? k : (k & 1), hout = s->training ? k + 1 : ((k + 1) & 1);
     __nv_bfloat16* abuf = s->training ? s->A[k] : s->A[0];
-    const CUtensorMap& tma = s->training ? s->tmA[k] : s->tmA[0];
+    const ConvMaps& tma = s->training ? s->tmA[k] : s->tmA[0];
     a = cargs(s);
     a.bias = s->master + s->off_b[la];
     a.out_bf16 = abuf;
-    e = conv_launch(32, 32, kEpiBias | kEpiRelu, s->tmH[hin], s->tmWf[la], a, s->max_ctas, s->stream);
+    e = conv_launch(32, 32, kEpiBias | kEpiRelu, s->tmH[hin], use_win(s), s->tmWf[la], a, s->sms, s->stream);
     if (e != cudaSuccess) return e;
     a = cargs(s);
     a.bias = s->master + s->off_b[lb];
     a.resid = s->H[hin];
     a.out_bf16 = s->H[hout];
-    e = conv_launch(32, 32, kEpiBias | kEpiResid, tma, s->tmWf[lb], a, s->max_ctas, s->stream);
+    e = conv_launch(32, 32, kEpiBias | kEpiResid, tma, use_win(s), s->tmWf[lb], a, s->sms, s->stream);
     if (e != cudaSuccess) return e;
   }
   const int hlast = s->training ? kBlocks : (kBlocks & 1);
@@ -427,11 +439,11 @@ cudaError_t forward(lcbp_surrogate* s, float* qupdate, const float* rate = nullp
     a.qscale = s->sdq;
     a.rate = rate;
     a.rate_scale = kSteps;
-    return conv_launch(32, 16, kEpiBias | kEpiUpdateQ, s->tmH[hlast], s->tmWf[kLayers - 1], a, s->max_ctas,
+    return conv_launch(32, 16, kEpiBias | kEpiUpdateQ, s->tmH[hlast], use_win(s), s->tmWf[kLayers - 1], a, s->sms,
                        s->stream);
   }
   a.out_f32 = s->y16;
-  return conv_launch(32, 16, kEpiBias | kEpiOutF32, s->tmH[hlast], s->tmWf[kLayers - 1], a, s->max_ctas, s->stream);
+  return conv_launch(32, 16, kEpiBias | kEpiOutF32, s->tmH[hlast], use_win(s), s->tmWf[kLayers - 1], a, s->sms, s->stream);
 }
 
 template <int CX, int CY>
@@ -496,7 +508,7 @@ int lcbp_surrogate_create(int nx, int ny, int nz, int training, lcbp_surrogate**
   cudaGetDevice(&s->device);
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
-  s->max_ctas = 2 * std::max(sms, 1);
+  s->sms = std::max(sms, 1);
   cudaError_t e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
   if (e != cudaSuccess) {
     delete s;
@@ -521,7 +533,8 @@ int lcbp_surrogate_create(int nx, int ny, int nz, int training, lcbp_surrogate**
     A((void**)&s->wf[l], 27 * (size_t)d.cin_p * d.cout_p * 2);
     if (s->training) A((void**)&s->wb[l], 27 * (size_t)d.cin_p * d.cout_p * 2);
   }
-  const size_t b16 = (size_t)s->np * 16 * 2, b32 = (size_t)s->np * 32 * 2;
+  // padded chunk-planar activations plus the tail the window copies may read
+  const size_t b16 = (size_t)s->np * 16 * 2 + kActTailBytes, b32 = (size_t)s->np * 32 * 2 + kActTailBytes;
   A((void**)&s->X, b16);
   const int nh = s->training ? kBlocks + 1 : 2, na = s->training ? kBlocks : 1;
   for (int k = 0; k < nh; ++k) A((void**)&s->H[k], b32);
@@ -560,12 +573,12 @@ int lcbp_surrogate_create(int nx, int ny, int nz, int training, lcbp_surrogate**
       cudaMemsetAsync(s->adam_m, 0, mc * 4, s->stream);
       cudaMemsetAsync(s->adam_v, 0, mc * 4, s->stream);
     }
-    bool ok = act_map(&s->tmX, s->X, 16, nx, ny, nz);
-    for (int k = 0; k < nh; ++k) ok = ok && act_map(&s->tmH[k], s->H[k], 32, nx, ny, nz);
-    for (int k = 0; k < na; ++k) ok = ok && act_map(&s->tmA[k], s->A[k], 32, nx, ny, nz);
+    bool ok = conv_maps(&s->tmX, s->X, 16, nx, ny, nz);
+    for (int k = 0; k < nh; ++k) ok = ok && conv_maps(&s->tmH[k], s->H[k], 32, nx, ny, nz);
+    for (int k = 0; k < na; ++k) ok = ok && conv_maps(&s->tmA[k], s->A[k], 32, nx, ny, nz);
     if (s->training) {
-      ok = ok && act_map(&s->tmdH, s->dH, 32, nx, ny, nz) && act_map(&s->tmdA, s->dA, 32, nx, ny, nz) &&
-           act_map(&s->tmG16, s->G16, 16, nx, ny, nz);
+      ok = ok && conv_maps(&s->tmdH, s->dH, 32, nx, ny, nz) && conv_maps(&s->tmdA, s->dA, 32, nx, ny, nz) &&
+           conv_maps(&s->tmG16, s->G16, 16, nx, ny, nz);
     }
     for (int l = 0; l < kLayers && ok; ++l) {
       const LayerDim d = layer_dim(l);
@@ -607,6 +620,16 @@ int lcbp_surrogate_set_scales(lcbp_surrogate* s, double s_u, double s_r, double 
   s->su = (float)s_u;
   s->sr = (float)s_r;
   s->sdq = (float)s_dq;
+  return LCBP_OK;
+}
+
+int lcbp_surrogate_set_conv_kernel(lcbp_surrogate* s, int kind) {
+  int rc = check_s(s);
+  if (rc) return rc;
+  if (kind < LCBP_CONV_AUTO || kind > LCBP_CONV_WINDOW) return fail(LCBP_EINVAL, "unknown conv kernel %d", kind);
+  if (kind == LCBP_CONV_WINDOW && !s->tmX.use_win)
+    return fail(LCBP_EINVAL, "a %d x %d plane does not fit the window kernel", s->nx, s->ny);
+  s->conv_kernel = kind;
   return LCBP_OK;
 }
 
@@ -781,7 +804,7 @@ int lcbp_surrogate_train_step(lcbp_surrogate* s, const void* q5, const void* u3,
     launch_dw<32, 16>(s, s->H[kBlocks], s->G16, lout);
     ConvArgs a = cargs(s);
     a.out_bf16 = s->dH;
-    e = conv_launch(16, 32, 0, s->tmG16, s->tmWb[lout], a, s->max_ctas, s->stream);
+    e = conv_launch(16, 32, 0, s->tmG16, use_win(s), s->tmWb[lout], a, s->sms, s->stream);
   }
   for (int k = kBlocks - 1; k >= 0 && e == cudaSuccess; --k) {
     const int la = 1 + 2 * k, lbb = 2 + 2 * k;
@@ -789,7 +812,7 @@ int lcbp_surrogate_train_step(lcbp_surrogate* s, const void* q5, const void* u3,
     ConvArgs a = cargs(s);
     a.mask = s->A[k];
     a.out_bf16 = s->dA;
-    e = conv_launch(32, 32, kEpiMask, s->tmdH, s->tmWb[lbb], a, s->max_ctas, s->stream);
+    e = conv_launch(32, 32, kEpiMask, s->tmdH, use_win(s), s->tmWb[lbb], a, s->sms, s->stream);
     if (e != cudaSuccess) break;
     launch_dw<32, 32>(s, s->A[k], s->dH, lbb);
     launch_dw<32, 32>(s, s->H[k], s->dA, la);
@@ -798,7 +821,7 @@ int lcbp_surrogate_train_step(lcbp_surrogate* s, const void* q5, const void* u3,
     a.resid = s->dH;
     a.out_bf16 = s->dH;
     if (k == 0) a.mask = s->H[0];
-    e = conv_launch(32, 32, k == 0 ? (kEpiResid | kEpiMask) : kEpiResid, s->tmdA, s->tmWb[la], a, s->max_ctas,
+    e = conv_launch(32, 32, k == 0 ? (kEpiResid | kEpiMask) : kEpiResid, s->tmdA, use_win(s), s->tmWb[la], a, s->sms,
                     s->stream);
   }
   if (e == cudaSuccess) {

@@ -42,6 +42,20 @@ __device__ __forceinline__ uint64_t umma_sdesc(uint32_t saddr, uint32_t sbo_byte
   return d;
 }
 
+// Descriptor of a K-major operand without swizzling: core matrices of 8 rows
+// x 16 bytes stored contiguously (128 B), `lbo_bytes` apart along K and
+// `sbo_bytes` apart along M / N.  With sbo = 128 the rows of the operand are
+// evenly spaced 16 B apart, so a window shifted by whole rows is the same
+// layout at a start address 16 B x shift further.
+__device__ __forceinline__ uint64_t umma_sdesc_noswz(uint32_t saddr, uint32_t lbo_bytes, uint32_t sbo_bytes) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)((lbo_bytes >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo_bytes >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1u << 46;
+  return d;  // swizzle mode 0 (none)
+}
+
 // Instruction descriptor of kind::f16 with BF16 A and B, FP32 accumulator,
 // both operands K-major, dense, shape M x N.
 __host__ __device__ constexpr uint32_t umma_idesc_bf16(int M, int N) {
@@ -74,7 +88,13 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 }
 
 // ---- tensor memory -> registers ---------------------------------------------
-// 32 lanes x 32-bit, 16 or 32 consecutive columns per thread (warp w reads lanes 32 (w % 4) ...)
+// 32 lanes x 32-bit, 8, 16 or 32 consecutive columns per thread (warp w reads lanes 32 (w % 4) ...)
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr)
+               : "memory");
+}
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"

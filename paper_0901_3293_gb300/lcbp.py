@@ -26,6 +26,7 @@ F32, F64 = 0, 1
 BPII, CHOL_X, CHOL_Y, CHOL_Z, ISO_NOISE, SLAB_BPII_IN_CHOL = range(6)
 JACOBI, GAUSS_SEIDEL = 0, 1
 PATH_AUTO, PATH_GENERIC, PATH_FAST1, PATH_FAST2 = 0, 1, 2, 3
+CONV_AUTO, CONV_TAPS, CONV_WINDOW = 0, 1, 2
 
 _lib = None
 
@@ -72,6 +73,7 @@ _SIGNATURES = {
     "lcbp_surrogate_create": (_c_int, [_c_int, _c_int, _c_int, _c_int, ctypes.POINTER(_P)]),
     "lcbp_surrogate_destroy": (_c_int, [_P]),
     "lcbp_surrogate_set_scales": (_c_int, [_P, _c_double, _c_double, _c_double]),
+    "lcbp_surrogate_set_conv_kernel": (_c_int, [_P, _c_int]),
     "lcbp_surrogate_set_params": (_c_int, [_P, _c_void_p, _c_size_t]),
     "lcbp_surrogate_get_params": (_c_int, [_P, _c_void_p, _c_size_t]),
     "lcbp_surrogate_get_grads": (_c_int, [_P, _c_void_p, _c_size_t]),
@@ -491,6 +493,11 @@ class Surrogate:
 
     def set_scales(self, s_u: float = 1e-3, s_r: float = 1e-3, s_dq: float = 1e-3) -> "Surrogate":
         check(lib().lcbp_surrogate_set_scales(self._h, s_u, s_r, s_dq))
+        return self
+
+    def set_conv_kernel(self, kind: int) -> "Surrogate":
+        """CONV_AUTO, CONV_TAPS (one shifted tile per tap) or CONV_WINDOW (one staged plane for all taps)."""
+        check(lib().lcbp_surrogate_set_conv_kernel(self._h, kind))
         return self
 
     def set_params(self, v) -> "Surrogate":

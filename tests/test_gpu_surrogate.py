@@ -44,8 +44,15 @@ def random_params(seed, scale=1.5):
     return S.init_params(15, 32, 5, BLOCKS, np.random.default_rng(seed), scale=scale)
 
 
-@pytest.mark.parametrize("dims", [(16, 8, 6), (40, 12, 5), (32, 4, 1)])
-def test_forward_matches_oracle(lcbp, dims):
+KERNELS = ["CONV_TAPS", "CONV_WINDOW"]
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+@pytest.mark.parametrize("dims", [(16, 8, 6), (40, 12, 5), (32, 4, 1), (6, 70, 3)])
+def test_forward_matches_oracle(lcbp, dims, kernel):
+    """Both convolution kernels: one shifted tile per tap, and one staged
+    window per plane (tiles of 128 linear positions of the padded plane that
+    straddle rows, with ghost rows discarded)."""
     nx, ny, nz = dims
     shape = (nz, ny, nx)
     P = random_params(10)
@@ -53,6 +60,7 @@ def test_forward_matches_oracle(lcbp, dims):
     u3 = synth.random_velocity(shape, 2e-4, 13)
     r5 = synth.random_q5(shape, 1e-3, 14)
     sur = lcbp.Surrogate(nx, ny, nz)
+    sur.set_conv_kernel(getattr(lcbp, kernel))
     sur.set_params(S.flatten(P, BLOCKS))
     y = sur.forward(q5, u3, r5, 1.3, -0.4)
     x = net_input(q5, u3, r5, 1.3, -0.4)
@@ -65,7 +73,8 @@ def test_forward_matches_oracle(lcbp, dims):
     assert err_q < 1e-2 and err_e < 5e-2
 
 
-def test_training_gradients_match_oracle(lcbp):
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_training_gradients_match_oracle(lcbp, kernel):
     nx, ny, nz = 32, 8, 6
     shape = (nz, ny, nx)
     P = random_params(20)
@@ -76,6 +85,7 @@ def test_training_gradients_match_oracle(lcbp):
     dq = 10.0 * r5 + synth.random_q5(shape, 5e-4, 23)
     mask = (np.arange(nz)[:, None, None] * np.ones(shape) >= 1).astype(np.float64)
     sur = lcbp.Surrogate(nx, ny, nz, training=True)
+    sur.set_conv_kernel(getattr(lcbp, kernel))
     sur.set_params(S.flatten(P, BLOCKS))
     loss = sur.train_step(q5, u3, r5, 0.9, 0.2, dq, mask, lr=1e-6)
     g = S.unflatten(sur.get_grads().astype(np.float64), P, BLOCKS)
@@ -116,3 +126,35 @@ def test_surrogate_step_applies_prediction(lcbp):
     assert np.abs(q1 - (q0 + 10.0 * r0 + S_DQ * y)).max() < 1e-6
     lat.reequilibrate_f().step(2)  # plain stepping resumes
     assert np.isfinite(lat.free_energy())
+
+
+def test_window_and_tap_kernels_agree_on_slab(lcbp):
+    """The two kernels on a 64 x 64 x 16 slab section (the window kernel's
+    production shape): same sums, FP32 accumulation in a different order."""
+    nx, ny, nz = 64, 64, 16
+    shape = (nz, ny, nx)
+    q5 = initial.init_q5(shape, initial.SLAB_BPII_IN_CHOL, 2 * np.pi / 16, 0.3, 1e-4, 5, z0=4)
+    u3 = synth.random_velocity(shape, 2e-4, 6)
+    r5 = synth.random_q5(shape, 1e-3, 7)
+    params = S.flatten(random_params(40, scale=1.0), BLOCKS)
+    out = {}
+    for kernel in KERNELS:
+        sur = lcbp.Surrogate(nx, ny, nz)
+        sur.set_conv_kernel(getattr(lcbp, kernel)).set_params(params)
+        out[kernel] = sur.forward(q5, u3, r5, 1.0, -0.5)
+        sur.close()
+    a, b = out["CONV_TAPS"], out["CONV_WINDOW"]
+    # the MMA sequence per output row is the same (tap-major, 16 channels per
+    # step), so the two usually agree bit for bit
+    print("bitwise equal:", np.array_equal(a, b), "max diff", np.abs(a - b).max())
+    assert np.abs(a - b).max() <= 1e-2 * np.abs(a).max()
+    assert np.mean(np.abs(a - b)) <= 1e-3 * np.mean(np.abs(a))
+
+
+def test_window_kernel_rejected_where_it_does_not_fit(lcbp):
+    sur = lcbp.Surrogate(256, 4, 2)
+    with pytest.raises(lcbp.LcbpError) as e:
+        sur.set_conv_kernel(lcbp.CONV_WINDOW)
+    assert e.value.code == lcbp.EINVAL
+    with pytest.raises(lcbp.LcbpError):
+        sur.set_conv_kernel(7)
