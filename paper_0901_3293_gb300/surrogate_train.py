@@ -87,6 +87,25 @@ def crop(s: Sample, z0: int, depth: int):
             np.ascontiguousarray(s.r[:, idx]), np.ascontiguousarray(s.dq[:, idx]), mask)
 
 
+def rotate_z(q5, u3, k: int):
+    """Fields rotated by k quarter turns about z (square x-y planes): F'(r) =
+    R F(R^-1 r) R^T for the tensors, R u(R^-1 r) for the velocity, with R
+    taking x to y.  The equations of motion are invariant under proper
+    rotations of the cubic lattice, so a rotated trajectory is a trajectory."""
+    for _ in range(k % 4):
+        n = q5.shape[-1]
+        yp, xp = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+        src_y, src_x = (-xp) % n, yp
+
+        def move(a):
+            return a[..., src_y, src_x]
+
+        q5 = np.stack([move(q5[3]), -move(q5[1]), -move(q5[4]), move(q5[0]), move(q5[2])])
+        if u3 is not None:
+            u3 = np.stack([-move(u3[1]), move(u3[0]), move(u3[2])])
+    return q5, u3
+
+
 @dataclass
 class TrainLog:
     losses: list = field(default_factory=list)
@@ -97,8 +116,10 @@ class TrainLog:
 S_U, S_R, S_DQ = 1e-3, 1e-3, 1e-3
 
 
-def train(samples, iters: int, lr: float = 1e-3, depth: int = 64, seed: int = 0, params=None):
-    """Adam on random crops; returns (parameter vector, TrainLog)."""
+def train(samples, iters: int, lr: float = 1e-3, depth: int = 64, seed: int = 0, params=None,
+          augment: bool = True):
+    """Adam on random crops (rotated by a random quarter turn about z when
+    `augment`); returns (parameter vector, TrainLog)."""
     rng = np.random.default_rng(seed)
     nx, ny = samples[0].q.shape[3], samples[0].q.shape[2]
     sur = lcbp.Surrogate(nx, ny, depth, training=True)
@@ -112,6 +133,12 @@ def train(samples, iters: int, lr: float = 1e-3, depth: int = 64, seed: int = 0,
         s = samples[rng.integers(len(samples))]
         z0 = int(rng.integers(s.q.shape[1]))
         q, u, r, dq, mask = crop(s, z0, depth)
+        if augment and q.shape[-1] == q.shape[-2]:
+            k = int(rng.integers(4))
+            q, u = rotate_z(q, u, k)
+            r, _ = rotate_z(r, None, k)
+            dq, _ = rotate_z(dq, None, k)
+            q, u, r, dq = (np.ascontiguousarray(a) for a in (q, u, r, dq))
         lr_it = lr if it < iters // 2 else (lr * 0.3 if it < 3 * iters // 4 else lr * 0.1)
         log.losses.append(sur.train_step(q, u, r, s.kappa, TAU_R, dq, mask, lr=lr_it))
     log.seconds = time.perf_counter() - t0
@@ -292,6 +319,7 @@ def main():
     ap.add_argument("--run-steps", type=int, default=20000)
     ap.add_argument("--kappa", type=float, default=1.0)
     ap.add_argument("--tol", type=float, default=1e-3)
+    ap.add_argument("--train-kappas", type=int, default=6, help="training chiralities, evenly in [0.5, 2]")
     args = ap.parse_args()
     torch.cuda.set_device(0)
 
@@ -299,7 +327,7 @@ def main():
         print(json.dumps(d), file=sys.stderr, flush=True)
 
     t0 = time.perf_counter()
-    data = generate([0.5, 1.0, 2.0], args.data_steps, args.every, t_min=args.t_min)
+    data = generate(list(np.linspace(0.5, 2.0, args.train_kappas)), args.data_steps, args.every, t_min=args.t_min)
     held = generate([1.5], args.data_steps, args.every * 4, t_min=args.t_min, seed=7)
     t_gen = time.perf_counter() - t0
     note({"samples": len(data), "held_out": len(held), "gen_s": t_gen})
@@ -319,25 +347,38 @@ def main():
         F_plain[t] = plain.free_energy()
     plain.synchronize()
     t_plain_run = time.perf_counter() - tp0
-    hyb = slab_lattice(args.kappa)
-    run = JudgedRun(hyb, params, args.kappa, M=49, tol=args.tol)
-    F_hyb = []
-    th0 = time.perf_counter()
-    run.advance(args.run_steps, log_every=seg, log=F_hyb)
-    hyb.synchronize()
-    t_hyb_run = time.perf_counter() - th0
-    errs = [abs(F - F_plain[t]) / abs(F_plain[t]) for t, F in F_hyb if t in F_plain]
+
+    def judged(p):
+        """The judged run with parameter vector p, against the plain trajectory."""
+        hyb = slab_lattice(args.kappa)
+        run = JudgedRun(hyb, p, args.kappa, M=49, tol=args.tol)
+        F_hyb = []
+        th0 = time.perf_counter()
+        run.advance(args.run_steps, log_every=seg, log=F_hyb)
+        hyb.synchronize()
+        secs = time.perf_counter() - th0
+        errs = [abs(F - F_plain[t]) / abs(F_plain[t]) for t, F in F_hyb if t in F_plain]
+        out = {"seconds": secs, "surrogate_calls": run.surrogate_calls, "plain_steps": run.plain_steps,
+               "fallbacks": run.fallbacks, "max_rel_F_error": max(errs) if errs else None,
+               "mean_rel_F_error": float(np.mean(errs)) if errs else None,
+               "judge_gap_median": float(np.median(run.judge_gaps)) if run.judge_gaps else None,
+               "final_F": F_hyb[-1][1] if F_hyb else None}
+        run.close()
+        hyb.close()
+        return out
+
+    res = judged(params)
+    # the same pipeline without the learned correction: ten explicit Euler steps per call
+    res0 = judged(np.zeros_like(params))
+    note({"judged_network": res, "judged_euler10": res0})
     print(json.dumps({
         "data": {"samples": len(data), "held_out": len(held), "seconds": t_gen},
         "train": {"iters": log.iters, "seconds": log.seconds, "ms_per_iter": 1e3 * log.seconds / log.iters,
                   "loss_first": float(np.mean(log.losses[:20])), "loss_last": float(np.mean(log.losses[-20:]))},
         "held_out_mse": mse,
         "call_ms": {"surrogate_10_steps": t_sur, "plain_10_steps": t_plain},
-        "run": {"steps": args.run_steps, "kappa": args.kappa, "plain_s": t_plain_run, "surrogate_s": t_hyb_run,
-                "surrogate_calls": run.surrogate_calls, "plain_steps": run.plain_steps,
-                "fallbacks": run.fallbacks, "max_rel_F_error": max(errs) if errs else None,
-                "judge_gap_median": float(np.median(run.judge_gaps)) if run.judge_gaps else None,
-                "final_F": {"plain": F_plain[max(F_plain)], "surrogate": F_hyb[-1][1] if F_hyb else None}},
+        "run": {"steps": args.run_steps, "kappa": args.kappa, "plain_s": t_plain_run,
+                "final_F_plain": F_plain[max(F_plain)], "network": res, "euler10_without_network": res0},
     }))
 
 
