@@ -53,8 +53,8 @@ STATE_BYTES = (15 + 5) * 2 * 4  # read + write of f and Q once per site-step (FP
 MEASURED_TRAFFIC = {
     "sources": ["paper_0901_3293_gb300/csrc/zmarch.cu", "paper_0901_3293_gb300/csrc/common.cuh",
                 "paper_0901_3293_gb300/csrc/tma.cuh"],
-    "sha256_16": "022ca92b361dd9c0",
-    "bytes_per_site": {"qside": (163475712 + 168136448) / 160 ** 3, "lbq": (837724160 + 360356608) / 160 ** 3},
+    "sha256_16": "553266f1b7003b05",
+    "bytes_per_site": {"qside": (163261952 + 168020992) / 160 ** 3, "lbq": (838447360 + 360688384) / 160 ** 3},
 }
 ORACLE_SAMPLE = 32  # side of the periodic cube the oracle steps (two BPII unit cells)
 
@@ -73,6 +73,20 @@ def measured_traffic_per_site(kernel: str):
 
 def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+# multiply-accumulates per site of one surrogate call: conv 15->32, eight 32->32, 32->5 (3^3 taps)
+SURROGATE_MAC_PER_SITE = 27 * (15 * 32 + 8 * 32 * 32 + 32 * 5)
+
+
+def measured_bf16_peak():
+    """Dense BF16 TFLOP/s: the measured burst figure (a call is short), else the fallback."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["bf16_tflops"]), "measured burst (MEASURED_PEAKS.json bf16_tflops)"
+    return 1900.0, "fallback"
 
 
 def measured_peaks():
@@ -309,6 +323,20 @@ def run_ours(args):
                  "note": "state (168 MB) partly L2-resident; not the headline"}
     slab.close()
 
+    # ---- the learned surrogate on the same slab: one call (ten steps' worth of
+    # Q change: input packing, ten tensor-core convolutions, Q update) against
+    # ten plain steps; untrained random parameters (the arithmetic is the same)
+    from paper_0901_3293_gb300 import surrogate_train as st
+    t_call, t_plain10 = st.time_call(reps=max(10, min(args.steps, 50)))
+    sur_flop = 2.0 * SURROGATE_MAC_PER_SITE * 64 * 64 * 256
+    bf16_peak = measured_bf16_peak()
+    sur_line = {"ms_per_call": t_call, "plain_10_steps_ms": t_plain10, "speedup_per_10_steps": t_plain10 / t_call,
+                "network_tflops": sur_flop / (t_call * 1e-3) / 1e12,
+                "frac_of_bf16_peak": sur_flop / (t_call * 1e-3) / 1e12 / bf16_peak[0],
+                "bf16_peak": {"tflops": bf16_peak[0], "source": bf16_peak[1]},
+                "note": "whole call host-timed over repeated calls; network FLOPs use the true channel counts "
+                        "(238464 MAC/site); conv kernels are the window kernel"}
+
     # ---- the 48-replica sweep (32^3 / 48^3, per-replica kappa and tau) in one batch
     from paper_0901_3293_gb300 import synth
     sweep = synth.replica_sweep(48, SEED)
@@ -351,7 +379,7 @@ def run_ours(args):
                    "planes_per_cta": zc, "sites_per_thread": spt},
         "roofline": roof, "per_kernel": per_kernel, "cpu_baseline": cpu, "e2e": e2e,
         "gpu_launches": launches, "clocks": clk, "free_energy_after": F,
-        "slab_64x64x256": slab_line, "batched_48_replicas": batch_line,
+        "slab_64x64x256": slab_line, "surrogate_slab_64x64x256": sur_line, "batched_48_replicas": batch_line,
     }
     print(json.dumps(line), flush=True)
 
