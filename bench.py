@@ -337,6 +337,21 @@ def run_ours(args):
                 "note": "whole call host-timed over repeated calls; network FLOPs use the true channel counts "
                         "(238464 MAC/site); conv kernels are the window kernel"}
 
+    # ---- the polarised-light texture of the slab (Sec. 2.3): one image of the
+    # current Q (64 x 64 columns of 256 planes, three wavelengths)
+    tex_lat = st.slab_lattice(1.0)
+    tex_lat.step(20)
+    tex_lat.texture()
+    tex_lat.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(20):
+        tex_lat.texture()
+    tex_ms = 1e3 * (time.perf_counter() - t0) / 20
+    tex_line = {"ms_per_image": tex_ms, "sites": 64 * 64 * 256,
+                "GBps_of_Q": 64 * 64 * 256 * 5 * 4 / (tex_ms * 1e-3) / 1e9,
+                "note": "host-timed lcbp_texture including the 16 KB image copy; reads Q (20 B/site) once"}
+    tex_lat.close()
+
     # ---- the 48-replica sweep (32^3 / 48^3, per-replica kappa and tau) in one batch
     from paper_0901_3293_gb300 import synth
     sweep = synth.replica_sweep(48, SEED)
@@ -379,7 +394,8 @@ def run_ours(args):
                    "planes_per_cta": zc, "sites_per_thread": spt},
         "roofline": roof, "per_kernel": per_kernel, "cpu_baseline": cpu, "e2e": e2e,
         "gpu_launches": launches, "clocks": clk, "free_energy_after": F,
-        "slab_64x64x256": slab_line, "surrogate_slab_64x64x256": sur_line, "batched_48_replicas": batch_line,
+        "slab_64x64x256": slab_line, "surrogate_slab_64x64x256": sur_line, "texture_slab_64x64x256": tex_line,
+        "batched_48_replicas": batch_line,
     }
     print(json.dumps(line), flush=True)
 

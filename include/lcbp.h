@@ -281,6 +281,33 @@ LCBP_API int lcbp_totals(lcbp_lattice *h, double *mass, double momentum[3]);
 LCBP_API int lcbp_defect_fraction(lcbp_lattice *h, double threshold, double *fraction);
 
 /*
+ * Polarised-light texture (Sec. 2.3, rendering of the optical pattern): the
+ * transmitted intensity S_0 of unpolarised light of unit intensity that
+ * passes a linear polariser at phi_in, the lattice planes z = 0 .. Nz-1 in
+ * turn (each a uniaxial retarder of thickness h: director = unit eigenvector
+ * of the largest eigenvalue q of Q, beta = atan2(d_x, d_y), retardance
+ * delta = 2 pi q h / lambda (n_o n_e / sqrt(n_o^2 sin^2 alpha +
+ * n_e^2 cos^2 alpha) - n_o), cos alpha = d_z), and an analyser at phi_out;
+ * the image is the weighted sum over the wavelengths.  Polariser angles enter
+ * the Mueller matrices as 2 phi, so phi_in = 0, phi_out = pi/2 is the crossed
+ * pair.  lcbp_optics_default fills the section's values: lambda = 16, 18,
+ * 20 lattice units with weights 0.2, 0.6, 0.2, n_o = 1.5, n_e = 2.0, h = 1,
+ * phi_in = 0, phi_out = pi/2.
+ * img: caller-owned host buffer of Nx * Ny floats, [y][x].  Computed on the
+ * GPU in FP32 from the current Q.  Errors: LCBP_EINVAL (NULL, nlambda outside
+ * 1..4, a wavelength <= 0).
+ */
+typedef struct lcbp_optics {
+  int nlambda;
+  double lambda[4];
+  double weight[4];
+  double n_o, n_e, h;
+  double phi_in, phi_out;
+} lcbp_optics;
+LCBP_API int lcbp_optics_default(lcbp_optics *o);
+LCBP_API int lcbp_texture(lcbp_lattice *h, const lcbp_optics *o, float *img);
+
+/*
  * Checkpoint: a versioned binary file with a header (magic, version, dims,
  * state dtype, parameters, step count) followed by the raw state in the state
  * type (deviation populations, moments, Q), so a resumed run is bitwise

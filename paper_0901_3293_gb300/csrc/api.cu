@@ -1011,6 +1011,23 @@ int lcbp_defect_fraction(lcbp_lattice* h, double threshold, double* fraction) {
   return LCBP_OK;
 }
 
+int lcbp_texture(lcbp_lattice* h, const lcbp_optics* o, float* img) {
+  CHECK_H(h);
+  if (!o || !img) return fail(LCBP_EINVAL, "o and img must not be NULL");
+  if (o->nlambda < 1 || o->nlambda > 4) return fail(LCBP_EINVAL, "nlambda must be 1..4, got %d", o->nlambda);
+  for (int l = 0; l < o->nlambda; ++l)
+    if (!(o->lambda[l] > 0)) return fail(LCBP_EINVAL, "wavelength %d must be > 0", l);
+  // the H scratch (5 N elements) is free between steps and holds the image
+  float* d_img = static_cast<float*>(h->h);
+  cudaError_t e = h->dtype == LCBP_F64 ? launch_texture<double>(h->q, h->nx, h->ny, h->nz, *o, d_img, h->stream)
+                                       : launch_texture<float>(h->q, h->nx, h->ny, h->nz, *o, d_img, h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(img, d_img, sizeof(float) * (size_t)h->nx * h->ny, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "texture");
+  return LCBP_OK;
+}
+
 // Checkpoints hold the raw state (deviation populations, moments, Q) in the
 // state type, so that a resumed run is bitwise identical to an uninterrupted one.
 int lcbp_save(lcbp_lattice* h, const char* path) {

@@ -5,6 +5,7 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include "../../include/lcbp.h"
 #include "common.cuh"
 
 namespace lcbp {
@@ -117,6 +118,11 @@ struct ZmArgs {
 constexpr int kZmBoxX = 40;  // elements per TMA box row
 template <typename real>
 int zm_tile_rows();
+// polarised texture of a Q field into a device image [ny][nx] (optics.cu)
+template <typename real>
+cudaError_t launch_texture(const void* q, int nx, int ny, int nz, const lcbp_optics& o, float* d_img,
+                           cudaStream_t s);
+
 template <typename real>
 int zm_spt_max();
 template <typename real>

@@ -64,6 +64,8 @@ _SIGNATURES = {
     "lcbp_free_energy": (_c_int, [_P, ctypes.POINTER(_c_double)]),
     "lcbp_totals": (_c_int, [_P, ctypes.POINTER(_c_double), ctypes.POINTER(_c_double)]),
     "lcbp_defect_fraction": (_c_int, [_P, _c_double, ctypes.POINTER(_c_double)]),
+    "lcbp_optics_default": (_c_int, [_P]),
+    "lcbp_texture": (_c_int, [_P, _P, _P]),
     "lcbp_save": (_c_int, [_P, ctypes.c_char_p]),
     "lcbp_load": (_c_int, [_P, ctypes.c_char_p]),
     "lcbp_reequilibrate_f": (_c_int, [_P]),
@@ -164,6 +166,31 @@ def _ptr(a):
         return a.data_ptr(), _dtype_code(a), a
     a = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
     return a.ctypes.data, F64, a
+
+
+class Optics(ctypes.Structure):
+    """lcbp_optics: wavelengths and weights, indices, layer thickness, polariser angles."""
+    _fields_ = [("nlambda", _c_int), ("lambda_", _c_double * 4), ("weight", _c_double * 4),
+                ("n_o", _c_double), ("n_e", _c_double), ("h", _c_double),
+                ("phi_in", _c_double), ("phi_out", _c_double)]
+
+    @classmethod
+    def default(cls) -> "Optics":
+        """The values of the paper's rendering: lambda 16, 18, 20 with weights 0.2, 0.6, 0.2,
+        n_o 1.5, n_e 2.0, h 1, crossed polarisers at 0 and pi/2."""
+        o = cls()
+        check(lib().lcbp_optics_default(ctypes.byref(o)))
+        return o
+
+
+def write_pgm(img: np.ndarray, path: str, vmax: float | None = None) -> None:
+    """Write a grayscale image (e.g. a texture) as binary 8-bit PGM, scaled to [0, vmax]."""
+    a = np.asarray(img, dtype=np.float64)
+    top = float(vmax) if vmax else (float(a.max()) if a.max() > 0 else 1.0)
+    g = np.clip(np.rint(255.0 * a / top), 0, 255).astype(np.uint8)
+    with open(path, "wb") as fh:
+        fh.write(b"P5\n%d %d\n255\n" % (g.shape[1], g.shape[0]))
+        fh.write(g.tobytes())
 
 
 class Lattice:
@@ -345,6 +372,14 @@ class Lattice:
         fr = _c_double()
         check(lib().lcbp_defect_fraction(self._h, threshold, ctypes.byref(fr)))
         return fr.value
+
+    def texture(self, optics: "Optics | None" = None) -> np.ndarray:
+        """Polarised-light texture [ny, nx] (FP32) of the current Q between crossed polarisers."""
+        o = optics if optics is not None else Optics.default()
+        nx, ny, _ = self.dims
+        img = np.empty((ny, nx), dtype=np.float32)
+        check(lib().lcbp_texture(self._h, ctypes.byref(o), img.ctypes.data))
+        return img
 
     def info(self):
         dims = (_c_int * 3)()

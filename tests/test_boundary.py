@@ -70,3 +70,15 @@ def test_no_cpu_fallback_in_product_package():
             if fn.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
                 text = open(os.path.join(dirpath, fn)).read()
                 assert "import oracle" not in text and "from oracle" not in text, fn
+
+
+def test_write_pgm_roundtrip(tmp_path):
+    import numpy as np
+    from paper_0901_3293_gb300 import lcbp
+    img = np.linspace(0, 0.5, 12, dtype=np.float32).reshape(3, 4)
+    path = str(tmp_path / "t.pgm")
+    lcbp.write_pgm(img, path)
+    data = open(path, "rb").read()
+    assert data.startswith(b"P5\n4 3\n255\n")
+    px = np.frombuffer(data[len(b"P5\n4 3\n255\n"):], dtype=np.uint8).reshape(3, 4)
+    assert px[0, 0] == 0 and px[-1, -1] == 255
