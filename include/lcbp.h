@@ -80,6 +80,8 @@ extern "C" {
 #define LCBP_CHOL_Z 3            /* axis z: n = (cos q0z, sin q0z, 0) */
 #define LCBP_ISO_NOISE 4         /* isotropic Q = 0 plus noise */
 #define LCBP_SLAB_BPII_IN_CHOL 5 /* BPII for z < region[0], x-helix elsewhere */
+#define LCBP_SLAB_BPII_IN_ISO 6  /* BPII for z < region[0], isotropic (noise only) elsewhere (Sec. 3, Fig. 3) */
+#define LCBP_SLAB_BPII_IN_CHOL_Z 7 /* BPII for z < region[0], z-helix (axis normal to the wall) elsewhere (Sec. 3) */
 
 /* order of the two sub-updates within one step (Sec. 2.2: "sequentially updated") */
 #define LCBP_JACOBI 0       /* LB and Q both read the step-n fields (default) */
@@ -162,10 +164,13 @@ LCBP_API int lcbp_set_flow(lcbp_lattice *h, double tau_f, double xi, double Gamm
  *        Q_xy = A sin 2q0z, Q_xz = A sin 2q0y, Q_yz = A sin 2q0x (A = amplitude);
  * CHOL_*: Q = S (n n - I/3), S = amplitude;  ISO_NOISE: Q = 0;
  * SLAB_BPII_IN_CHOL: BPII (A = amplitude) for z < region[0], elsewhere the
- *   x-helix with S = 1/4 + 3/4 sqrt(1 - 8 / (3 gamma)) (bulk equilibrium order).
+ *   x-helix with S = 1/4 + 3/4 sqrt(1 - 8 / (3 gamma)) (bulk equilibrium order);
+ * SLAB_BPII_IN_CHOL_Z: the same with the z-helix (axis normal to the wall);
+ * SLAB_BPII_IN_ISO: BPII for z < region[0], Q = 0 elsewhere (Sec. 3, the
+ *   seed growing into the isotropic phase).
  * Then add U[-noise, noise) to each of the five components, the k-th output
  * (k = 5 * site + component) of SplitMix64 seeded with `seed`, mapped to
- * (z >> 11) * 2^-53.  region may be NULL except for SLAB_BPII_IN_CHOL.
+ * (z >> 11) * 2^-53.  region may be NULL except for the SLAB_* kinds.
  * Errors: LCBP_EINVAL (unknown kind, missing region, noise < 0).
  */
 LCBP_API int lcbp_init_q(lcbp_lattice *h, int kind, double amplitude, double noise, uint64_t seed,

@@ -102,14 +102,16 @@ def s_eq(gamma: float) -> float:
 
 
 # kinds, numbered as at the library boundary
-BPII, CHOL_X, CHOL_Y, CHOL_Z, ISO_NOISE, SLAB_BPII_IN_CHOL = range(6)
+BPII, CHOL_X, CHOL_Y, CHOL_Z, ISO_NOISE, SLAB_BPII_IN_CHOL, SLAB_BPII_IN_ISO, SLAB_BPII_IN_CHOL_Z = range(8)
 
 
 def init_q5(shape, kind: int, q0: float, amplitude: float, noise: float, seed: int,
             z0: int = 0, s_helix: float = 0.0) -> np.ndarray:
     """Initial Q in q5 layout.  amplitude is A for BPII, S for the helices and
-    unused for ISO_NOISE (zero mean); SLAB_BPII_IN_CHOL puts BPII with
-    A = amplitude for z < z0 and an x-helix with S = s_helix elsewhere."""
+    unused for ISO_NOISE (zero mean); the slab kinds put BPII with
+    A = amplitude for z < z0 and, elsewhere, an x-helix (SLAB_BPII_IN_CHOL) or a
+    z-helix (SLAB_BPII_IN_CHOL_Z) with S = s_helix, or the isotropic phase
+    (SLAB_BPII_IN_ISO, noise only)."""
     shape = tuple(int(v) for v in shape)
     if kind == BPII:
         q = bpii5(shape, q0, amplitude)
@@ -117,9 +119,15 @@ def init_q5(shape, kind: int, q0: float, amplitude: float, noise: float, seed: i
         q = cholesteric5(shape, q0, amplitude, "xyz"[kind - CHOL_X])
     elif kind == ISO_NOISE:
         q = np.zeros((5,) + shape)
-    elif kind == SLAB_BPII_IN_CHOL:
+    elif kind in (SLAB_BPII_IN_CHOL, SLAB_BPII_IN_ISO, SLAB_BPII_IN_CHOL_Z):
+        # Sec. 3: a BPII seed slab next to a cholesteric (helix in the wall
+        # plane, along x, or normal to it, along z) or an isotropic phase
         zz = np.arange(shape[0])[None, :, None, None]
-        q = np.where(zz < z0, bpii5(shape, q0, amplitude), cholesteric5(shape, q0, s_helix, "x"))
+        if kind == SLAB_BPII_IN_ISO:
+            other = np.zeros((5,) + shape)
+        else:
+            other = cholesteric5(shape, q0, s_helix, "x" if kind == SLAB_BPII_IN_CHOL else "z")
+        q = np.where(zz < z0, bpii5(shape, q0, amplitude), other)
     else:
         raise ValueError(kind)
     if noise != 0.0:

@@ -763,9 +763,9 @@ int lcbp_set_flow(lcbp_lattice* h, double tau_f, double xi, double Gamma, int fl
 
 int lcbp_init_q(lcbp_lattice* h, int kind, double amplitude, double noise, uint64_t seed, const int* region) {
   CHECK_H(h);
-  if (kind < LCBP_BPII || kind > LCBP_SLAB_BPII_IN_CHOL) return fail(LCBP_EINVAL, "unknown initial kind %d", kind);
+  if (kind < LCBP_BPII || kind > LCBP_SLAB_BPII_IN_CHOL_Z) return fail(LCBP_EINVAL, "unknown initial kind %d", kind);
   if (!(noise >= 0.0) || !std::isfinite(amplitude)) return fail(LCBP_EINVAL, "need noise >= 0, finite amplitude");
-  if (kind == LCBP_SLAB_BPII_IN_CHOL && !region) return fail(LCBP_EINVAL, "SLAB_BPII_IN_CHOL needs region[0] = z0");
+  if (kind >= LCBP_SLAB_BPII_IN_CHOL && !region) return fail(LCBP_EINVAL, "slab kinds need region[0] = z0");
   InitQArgs a{kind, amplitude, noise, seed, region ? region[0] : 0};
   cudaError_t e = cudaMemcpyAsync(h->d_seed, &seed, sizeof(seed), cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess)

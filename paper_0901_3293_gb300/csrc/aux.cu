@@ -70,6 +70,13 @@ __global__ void k_init_q(const Replica<real>* __restrict__ reps, const Tile* __r
         if (z < a.z0) bpii(a.amplitude, 2.0 * q0, x, y, z, q);
         else uniaxial(s_helix[rep], 0.0, cos(q0 * x), sin(q0 * x), q);
         break;
+      case 6:
+        if (z < a.z0) bpii(a.amplitude, 2.0 * q0, x, y, z, q);
+        break;
+      case 7:
+        if (z < a.z0) bpii(a.amplitude, 2.0 * q0, x, y, z, q);
+        else uniaxial(s_helix[rep], cos(q0 * z), sin(q0 * z), 0.0, q);
+        break;
       default: break;
     }
     const long long s = ((long long)z * R.ny + y) * R.nx + x;

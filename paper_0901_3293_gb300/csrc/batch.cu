@@ -379,9 +379,9 @@ int lcbp_batch_init_q(lcbp_batch* b, int r, int kind, double amplitude, double n
   int rc = check_b(b);
   if (!rc) rc = check_r(b, r);
   if (rc) return rc;
-  if (kind < LCBP_BPII || kind > LCBP_SLAB_BPII_IN_CHOL) return fail(LCBP_EINVAL, "unknown initial kind %d", kind);
+  if (kind < LCBP_BPII || kind > LCBP_SLAB_BPII_IN_CHOL_Z) return fail(LCBP_EINVAL, "unknown initial kind %d", kind);
   if (!(noise >= 0.0)) return fail(LCBP_EINVAL, "noise < 0");
-  if (kind == LCBP_SLAB_BPII_IN_CHOL && !region) return fail(LCBP_EINVAL, "SLAB_BPII_IN_CHOL needs region");
+  if (kind >= LCBP_SLAB_BPII_IN_CHOL && !region) return fail(LCBP_EINVAL, "slab kinds need region");
   InitQArgs a{kind, amplitude, noise, seed, region ? region[0] : 0};
   cudaError_t e = cudaMemcpyAsync(b->d_seed + r, &seed, 8, cudaMemcpyHostToDevice, b->stream);
   const Tile* t0 = b->d_tiles + b->tile_begin[r];

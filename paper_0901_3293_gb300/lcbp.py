@@ -23,7 +23,7 @@ LIB_PATH = os.path.join(HERE, "_lib", "liblcbp.so")
 
 OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, ETIMEOUT, ESTATE, EIO = 0, -1, -2, -3, -4, -5, -6, -7
 F32, F64 = 0, 1
-BPII, CHOL_X, CHOL_Y, CHOL_Z, ISO_NOISE, SLAB_BPII_IN_CHOL = range(6)
+BPII, CHOL_X, CHOL_Y, CHOL_Z, ISO_NOISE, SLAB_BPII_IN_CHOL, SLAB_BPII_IN_ISO, SLAB_BPII_IN_CHOL_Z = range(8)
 JACOBI, GAUSS_SEIDEL = 0, 1
 PATH_AUTO, PATH_GENERIC, PATH_FAST1, PATH_FAST2 = 0, 1, 2, 3
 CONV_AUTO, CONV_TAPS, CONV_WINDOW = 0, 1, 2

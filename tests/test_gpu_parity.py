@@ -45,13 +45,15 @@ def oracle_u(f):
 # ---------------------------------------------------------------------------
 @pytest.mark.parametrize("dtype,tol", [("f64", 1e-15), ("f32", 2e-7)])
 @pytest.mark.parametrize("kind", [initial.BPII, initial.CHOL_X, initial.CHOL_Y, initial.CHOL_Z,
-                                  initial.ISO_NOISE, initial.SLAB_BPII_IN_CHOL])
+                                  initial.ISO_NOISE, initial.SLAB_BPII_IN_CHOL, initial.SLAB_BPII_IN_ISO,
+                                  initial.SLAB_BPII_IN_CHOL_Z])
 def test_init_q_matches_oracle(lcbp, kind, dtype, tol):
     p = lbq.Params()
     shape = (9, 6, 7)
     lat = make(lcbp, shape, dtype, p)
-    amp = 0.3 if kind in (initial.BPII, initial.SLAB_BPII_IN_CHOL) else 0.45
-    lat.init_q(kind, amp, noise=1e-3, seed=SEED + kind, z0=4 if kind == initial.SLAB_BPII_IN_CHOL else None)
+    slab = kind >= initial.SLAB_BPII_IN_CHOL
+    amp = 0.3 if kind == initial.BPII or slab else 0.45
+    lat.init_q(kind, amp, noise=1e-3, seed=SEED + kind, z0=4 if slab else None)
     want = initial.init_q5(shape, kind, p.q0, amp, 1e-3, SEED + kind, z0=4, s_helix=initial.s_eq(p.gamma))
     assert np.abs(lat.read_q() - want).max() <= tol
 
@@ -77,6 +79,20 @@ def test_one_coupled_step_f64(lcbp, shape, path):
     f, Q = lbq.step(lbq.f_from_soa(f15), lbq.q5_to_q9(q5), p)
     assert np.abs(lat.read_q() - lbq.q9_to_q5(Q)).max() < 1e-14
     assert np.abs(lat.read_f() - lbq.f_to_soa(f)).max() < 1e-14
+    assert np.abs(lat.read_u() - oracle_u(f)).max() < 1e-14
+
+
+@pytest.mark.parametrize("kind", [initial.SLAB_BPII_IN_ISO, initial.SLAB_BPII_IN_CHOL_Z])
+def test_slab_growth_states_step_f64(lcbp, kind):
+    """Ten coupled steps from the growth states of Sec. 3: a BPII seed next to
+    the isotropic phase, and next to a helix whose axis is normal to the wall."""
+    p = lbq.Params()
+    shape = (16, 8, 8)
+    lat = make(lcbp, shape, "f64", p)
+    lat.init_q(kind, 0.3, noise=1e-4, seed=SEED, z0=8).init_f_equilibrium(1.0).step(10)
+    Q = initial.init_q9(shape, kind, p.q0, 0.3, 1e-4, SEED, z0=8, s_helix=initial.s_eq(p.gamma))
+    f, Q = lbq.run(lbq.init_f_equilibrium(Q, p), Q, p, 10)
+    assert np.abs(lat.read_q() - lbq.q9_to_q5(Q)).max() < 1e-13
     assert np.abs(lat.read_u() - oracle_u(f)).max() < 1e-14
 
 

@@ -491,6 +491,17 @@ def test_cholesteric_and_slab_initial_states():
     q = initial.init_q5((8, 4, 4), initial.SLAB_BPII_IN_CHOL, q0, 0.3, 0.0, 0, z0=3, s_helix=S)
     assert np.allclose(q[:, :3], initial.bpii5((8, 4, 4), q0, 0.3)[:, :3])
     assert np.allclose(q[:, 3:], initial.cholesteric5((8, 4, 4), q0, S, "x")[:, 3:])
+    # BPII next to the isotropic phase (Sec. 3, Fig. 3): Q vanishes beyond the seed
+    q = initial.init_q5((8, 4, 4), initial.SLAB_BPII_IN_ISO, q0, 0.3, 0.0, 0, z0=3, s_helix=S)
+    assert np.allclose(q[:, :3], initial.bpii5((8, 4, 4), q0, 0.3)[:, :3]) and not q[:, 3:].any()
+    # helix normal to the wall: the director turns in the x-y plane along z,
+    # n = (cos q0 z, sin q0 z, 0), uniaxial with eigenvalues 2S/3, -S/3, -S/3
+    q = initial.init_q5((8, 4, 4), initial.SLAB_BPII_IN_CHOL_Z, q0, 0.3, 0.0, 0, z0=3, s_helix=S)
+    Q = initial.q5_to_q9(q)[3:]
+    z = np.arange(3, 8)[:, None, None]
+    n = np.stack([np.cos(q0 * z) * np.ones((1, 4, 4)), np.sin(q0 * z) * np.ones((1, 4, 4)), np.zeros((5, 4, 4))], -1)
+    assert np.abs(np.einsum("...ab,...b->...a", Q, n) - 2 * S / 3 * n).max() < 1e-14
+    assert np.abs(Q[..., 2, 2] + S / 3).max() < 1e-14
 
 
 def test_s_eq_is_bulk_minimum():
