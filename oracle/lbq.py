@@ -89,6 +89,10 @@ class Params:
     tau_f: float = 2.0
     flow_on: bool = True
     coupling: str = "jacobi"
+    # solid walls half a spacing below z = 0 and above z = Nz-1 (see the
+    # "Solid walls" section below); q_wall = the anchored Q in q5 order
+    walls_z: bool = False
+    q_wall: tuple = (0.0, 0.0, 0.0, 0.0, 0.0)
 
     def with_(self, **kw) -> "Params":
         return replace(self, **kw)
@@ -163,6 +167,37 @@ def transpose(M: np.ndarray) -> np.ndarray:
 
 
 # ---------------------------------------------------------------------------
+# Solid walls (a reading: the paper's slab is periodic; walls are an option).
+# Walls sit half a lattice spacing below z = 0 and above z = Nz-1:
+#  * LB: half-way bounce-back, a population that would arrive from beyond a
+#    wall is the reflected one of the same site (see stream);
+#  * Q: strong anchoring, ghost planes z = -1 and z = Nz hold Q = q_wall;
+#  * u: no slip at the wall, ghost u = -u of the adjacent plane;
+#  * tau and H: zero on the ghost planes (the wall carries no molecular field).
+# Field operators act on arrays padded with these ghost planes; the energy
+# counts every bond with at least one end inside, so H stays its exact gradient.
+# ---------------------------------------------------------------------------
+def _pad_z(A: np.ndarray, lo: np.ndarray, hi: np.ndarray) -> np.ndarray:
+    return np.concatenate([lo[None], A, hi[None]], axis=0)
+
+
+def q_wall9(Q: np.ndarray, p: "Params") -> np.ndarray:
+    """The anchored Q as a ghost plane shaped like one z-plane of Q."""
+    qw = np.asarray(p.q_wall, dtype=np.float64).reshape(5, 1, 1, 1)
+    plane = q5_to_q9(np.broadcast_to(qw, (5, 1) + Q.shape[1:3]))[0]
+    return plane
+
+
+def _pad_q(Q: np.ndarray, p: "Params") -> np.ndarray:
+    w = q_wall9(Q, p)
+    return _pad_z(Q, w, w)
+
+
+def _no_walls(p: "Params") -> "Params":
+    return replace(p, walls_z=False)
+
+
+# ---------------------------------------------------------------------------
 # Free energy and molecular field, Sec. 2.1 Eq. (free_energy), Eq. (Qevolution)
 # ---------------------------------------------------------------------------
 def curl_term(Q: np.ndarray) -> np.ndarray:
@@ -201,8 +236,38 @@ def free_energy_density(Q: np.ndarray, p: Params) -> np.ndarray:
             + 2.0 * p.K * p.q0 * p.q0 * ddot(Q, Q))
 
 
+def bond_energy(A: np.ndarray, B: np.ndarray, g: int, p: Params) -> np.ndarray:
+    """Energy of the bond from A (at r) to B (at r + e_g):
+    (K/2)|B - A|^2 + K q0 (A_ab eps_agd B_db - B_ab eps_agd A_db).  Summed over
+    all bonds it equals the gradient and chiral parts of free_energy_density
+    (the chiral site term 2 K q0 Q:(eps D0 Q) splits into these bond halves)."""
+    e = EPS[:, g, :]
+    dQ = B - A
+    chiral = np.einsum("...ab,ad,...db->...", A, e, B) - np.einsum("...ab,ad,...db->...", B, e, A)
+    return 0.5 * p.K * ddot(dQ, dQ) + p.K * p.q0 * chiral
+
+
+def free_energy_bonds(Q: np.ndarray, p: Params) -> float:
+    """F_h in bond form: site terms (bulk + 2 K q0^2 |Q|^2) plus every bond with
+    at least one end on the lattice; with walls the bonds to the anchored ghost
+    planes are included (periodic in x, y)."""
+    site = bulk_free_energy_density(Q, p) + 2.0 * p.K * p.q0 * p.q0 * ddot(Q, Q)
+    F = float(np.sum(site))
+    for g in (0, 1):  # x, y: periodic bonds
+        F += float(np.sum(bond_energy(Q, shift(Q, unit(g, 1)), g, p)))
+    if p.walls_z:
+        Qp = _pad_q(Q, p)
+        F += float(np.sum(bond_energy(Qp[:-1], Qp[1:], 2, p)))
+    else:
+        F += float(np.sum(bond_energy(Q, shift(Q, unit(2, 1)), 2, p)))
+    return F
+
+
 def free_energy(Q: np.ndarray, p: Params) -> float:
-    """F_h = sum over sites of :func:`free_energy_density` (FP64)."""
+    """F_h = sum over sites of :func:`free_energy_density` (FP64); with walls the
+    bond form :func:`free_energy_bonds`."""
+    if p.walls_z:
+        return free_energy_bonds(Q, p)
     return float(np.sum(free_energy_density(Q, p)))
 
 
@@ -212,6 +277,8 @@ def dF_dQ(Q: np.ndarray, p: Params) -> np.ndarray:
     Bulk: A0(1-gamma/3) Q - A0 gamma Q.Q + A0 gamma Tr(Q^2) Q.
     Gradient: -K Lap7 Q + 2 K q0 (C + C^T) + 4 K q0^2 Q with C = eps D0 Q.
     """
+    if p.walls_z:
+        return dF_dQ(_pad_q(Q, p), _no_walls(p))[1:-1]
     q2 = ddot(Q, Q)[..., None, None]
     QQ = Q @ Q
     C = curl_term(Q)
@@ -247,9 +314,13 @@ def lc_stress(Q: np.ndarray, H: np.ndarray, p: Params) -> tuple[np.ndarray, np.n
     return sigma, tau
 
 
-def body_force(Q: np.ndarray, H: np.ndarray, tau: np.ndarray) -> np.ndarray:
+def body_force(Q: np.ndarray, H: np.ndarray, tau: np.ndarray, p: Params | None = None) -> np.ndarray:
     """b_a = D0_b tau_ab - H_gn D0_a Q_gn, Sec. 2.2 Eq. (eq7a) with the last two
-    terms rewritten through Eq. (spurious); the sum runs over all 9 (g, n)."""
+    terms rewritten through Eq. (spurious); the sum runs over all 9 (g, n).
+    With walls (p.walls_z) the ghost planes hold Q = q_wall, H = tau = 0."""
+    if p is not None and p.walls_z:
+        z = np.zeros_like(H[:1])
+        return body_force(_pad_q(Q, p), _pad_z(H, z[0], z[0]), _pad_z(tau, z[0], z[0]))[1:-1]
     b = np.zeros(Q.shape[:3] + (3,))
     for a in range(3):
         for bb in range(3):
@@ -360,7 +431,11 @@ def be_rhs(Q: np.ndarray, u: np.ndarray, p: Params) -> np.ndarray:
     """dQ/dt = Gamma H + S(W, Q) - u.grad Q  (Eq. Qevolution with Eq. mat_der).
 
     Central differences for grad u and the advection; the trace of S is removed.
+    With walls the ghost planes hold Q = q_wall and u = -u (no slip).
     """
+    if p.walls_z:
+        up = _pad_z(u, -u[0], -u[-1])
+        return be_rhs(_pad_q(Q, p), up, _no_walls(p))[1:-1]
     H = molecular_field(Q, p)
     S = corotational(Q, velocity_gradient(u), p.xi)
     S = S - (trace(S) / 3.0)[..., None, None] * EYE
@@ -396,10 +471,10 @@ def step(f: np.ndarray, Q: np.ndarray, p: Params,
     _, u = moments(f)
     H = molecular_field(Q, p)
     sigma, tau = lc_stress(Q, H, p)
-    b = body_force(Q, H, tau)
+    b = body_force(Q, H, tau, p)
     if b_ext is not None:
         b = b + b_ext
-    f_new = lb_step(f, sigma, b, p.tau_f)
+    f_new = lb_step(f, sigma, b, p.tau_f, walls_z=p.walls_z)
     if p.coupling == "gauss_seidel":
         _, u = moments(f_new)
     elif p.coupling != "jacobi":
