@@ -159,6 +159,24 @@ LCBP_API int lcbp_set_ldg_kappa_tau(lcbp_lattice *h, double A0, double q0, doubl
 LCBP_API int lcbp_set_flow(lcbp_lattice *h, double tau_f, double xi, double Gamma, int flow_on, int coupling);
 
 /*
+ * Solid walls in z (not in the paper, whose slab is periodic; an extension).
+ * With walls_z != 0 the lattice has walls half a spacing below z = 0 and above
+ * z = Nz-1, while x and y stay periodic:
+ *  - LB: half-way bounce-back (no slip): a population that would arrive from
+ *    beyond a wall is the reflected one of the same site;
+ *  - Q: strong anchoring, the ghost planes z = -1 and z = Nz hold Q = q_wall5
+ *    (q5 order [xx, xy, xz, yy, yz]; NULL = 0) in every stencil;
+ *  - u: no slip, ghost u = -u of the adjacent plane (velocity gradient,
+ *    advection);
+ *  - tau and H vanish on the ghost planes (body force).
+ * The free energy then counts every bond with at least one end on the
+ * lattice, so H stays its exact gradient.  Walled lattices run the generic
+ * kernels; the surrogate refuses them.  walls_z = 0 restores periodic z.
+ * Errors: LCBP_EINVAL (non-finite q_wall).
+ */
+LCBP_API int lcbp_set_walls(lcbp_lattice *h, int walls_z, const double *q_wall5);
+
+/*
  * Fill Q with an analytic initial state on the device (kinds above):
  * BPII:  Q_xx = A[cos 2q0z - cos 2q0y], Q_yy = A[cos 2q0x - cos 2q0z],
  *        Q_xy = A sin 2q0z, Q_xz = A sin 2q0y, Q_yz = A sin 2q0x (A = amplitude);

@@ -81,6 +81,8 @@ void fill_replica(void* dst, int nx, int ny, int nz, long long base, const HostP
   r.n = (long long)nx * ny * nz;
   r.base = base;
   r.m = make_model<real>(p);
+  r.walls = p.walls_z;
+  for (int c = 0; c < 5; ++c) r.qw[c] = (real)p.q_wall[c];
   std::memcpy(dst, &r, sizeof(r));
 }
 template void fill_replica<float>(void*, int, int, int, long long, const HostParams&);
@@ -146,7 +148,7 @@ struct lcbp_lattice {
   int dtype;
   size_t es;
   int device;
-  HostParams p;
+  HostParams p{};
   cudaStream_t stream;
   bool own_stream;
   char* ws;
@@ -273,7 +275,7 @@ int finish_create(lcbp_lattice* h) {
 }
 
 HostParams default_params() {
-  HostParams p;
+  HostParams p{};
   p.A0 = 0.01;
   p.gamma = 3.1;
   p.K = 0.01;
@@ -335,7 +337,8 @@ bool make_field_tmap(CUtensorMap* tm, void* base, int comps, int nx, int ny, int
 bool fast_shape_ok(const lcbp_lattice* h) { return h->nx % 4 == 0; }
 
 bool use_fast(lcbp_lattice* h) {
-  if (h->path_req == LCBP_PATH_GENERIC || !h->p.flow_on || h->p.coupling != LCBP_JACOBI || !fast_shape_ok(h))
+  if (h->path_req == LCBP_PATH_GENERIC || !h->p.flow_on || h->p.coupling != LCBP_JACOBI || !fast_shape_ok(h) ||
+      h->p.walls_z)
     return false;
   if (!h->tmaps_ok) {
     static std::once_flag prep32, prep64;
@@ -517,6 +520,7 @@ StepArgs step_args(lcbp_lattice* h) {
   a.ts = h->ts;
   a.flow_on = h->p.flow_on;
   a.coupling = h->p.coupling;
+  a.walls = h->p.walls_z;
   a.q = h->q;
   a.qs = h->qs;
   a.h = h->h;
@@ -576,7 +580,8 @@ int build_graph(lcbp_lattice* h) {
 }
 
 int diag(lcbp_lattice* h, double threshold, int with_f) {
-  DiagGeom g{h->nx, h->ny, h->nz, h->n, 0, h->p.A0, h->p.gamma, h->p.K, h->p.q0};
+  DiagGeom g{h->nx, h->ny, h->nz, h->n, 0, h->p.A0, h->p.gamma, h->p.K, h->p.q0, h->p.walls_z, {}};
+  for (int c = 0; c < 5; ++c) g.qw[c] = h->p.q_wall[c];
   cudaError_t e = h->dtype == LCBP_F64
                       ? launch_diag_one<double>(g, h->q, h->f[h->cur], with_f, threshold, h->d_partials, h->d_out,
                                                 h->stream)
@@ -612,6 +617,11 @@ struct CkptHeader {
   int32_t version, nx, ny, nz, dtype, flow_on, coupling, pad;
   double A0, gamma, K, q0, tau_f, xi, Gamma;
   int64_t step;
+};
+// version 3 appends the walls after the version-2 header
+struct CkptWalls {
+  int32_t walls_z, pad;
+  double q_wall[5];
 };
 
 }  // namespace
@@ -757,6 +767,19 @@ int lcbp_set_flow(lcbp_lattice* h, double tau_f, double xi, double Gamma, int fl
   int rc = check_params(p);
   if (rc) return rc;
   if (p.flow_on != h->p.flow_on || p.coupling != h->p.coupling) drop_graph(h);
+  h->p = p;
+  return upload_replica(h);
+}
+
+int lcbp_set_walls(lcbp_lattice* h, int walls_z, const double* q_wall5) {
+  CHECK_H(h);
+  HostParams p = h->p;
+  p.walls_z = walls_z ? 1 : 0;
+  for (int c = 0; c < 5; ++c) {
+    p.q_wall[c] = q_wall5 ? q_wall5[c] : 0.0;
+    if (!std::isfinite(p.q_wall[c])) return fail(LCBP_EINVAL, "non-finite q_wall");
+  }
+  if (p.walls_z != h->p.walls_z) drop_graph(h);
   h->p = p;
   return upload_replica(h);
 }
@@ -1035,7 +1058,10 @@ int lcbp_save(lcbp_lattice* h, const char* path) {
   if (!path) return fail(LCBP_EINVAL, "path is NULL");
   CkptHeader hd{};
   std::memcpy(hd.magic, "LCBPCKP2", 8);
-  hd.version = 2;
+  hd.version = 3;
+  CkptWalls wl{};
+  wl.walls_z = h->p.walls_z;
+  for (int c = 0; c < 5; ++c) wl.q_wall[c] = h->p.q_wall[c];
   hd.nx = h->nx;
   hd.ny = h->ny;
   hd.nz = h->nz;
@@ -1059,7 +1085,8 @@ int lcbp_save(lcbp_lattice* h, const char* path) {
   if (e != cudaSuccess) return cuda_fail(e, "save");
   FILE* fp = std::fopen(path, "wb");
   if (!fp) return fail(LCBP_EIO, "cannot open %s for writing", path);
-  const bool ok = std::fwrite(&hd, sizeof(hd), 1, fp) == 1 && std::fwrite(buf.data(), 1, buf.size(), fp) == buf.size();
+  const bool ok = std::fwrite(&hd, sizeof(hd), 1, fp) == 1 && std::fwrite(&wl, sizeof(wl), 1, fp) == 1 &&
+                  std::fwrite(buf.data(), 1, buf.size(), fp) == buf.size();
   const bool closed = std::fclose(fp) == 0;
   return ok && closed ? LCBP_OK : fail(LCBP_EIO, "short write to %s", path);
 }
@@ -1070,9 +1097,15 @@ int lcbp_load(lcbp_lattice* h, const char* path) {
   FILE* fp = std::fopen(path, "rb");
   if (!fp) return fail(LCBP_EIO, "cannot open %s", path);
   CkptHeader hd{};
-  if (std::fread(&hd, sizeof(hd), 1, fp) != 1 || std::memcmp(hd.magic, "LCBPCKP2", 8) != 0 || hd.version != 2) {
+  if (std::fread(&hd, sizeof(hd), 1, fp) != 1 || std::memcmp(hd.magic, "LCBPCKP2", 8) != 0 ||
+      (hd.version != 2 && hd.version != 3)) {
     std::fclose(fp);
     return fail(LCBP_EIO, "%s is not an lcbp checkpoint", path);
+  }
+  CkptWalls wl{};  // version 2 files have no walls
+  if (hd.version == 3 && std::fread(&wl, sizeof(wl), 1, fp) != 1) {
+    std::fclose(fp);
+    return fail(LCBP_EIO, "truncated checkpoint %s", path);
   }
   if (hd.nx != h->nx || hd.ny != h->ny || hd.nz != h->nz || hd.dtype != h->dtype) {
     std::fclose(fp);
@@ -1093,9 +1126,11 @@ int lcbp_load(lcbp_lattice* h, const char* path) {
   p.Gamma = hd.Gamma;
   p.flow_on = hd.flow_on;
   p.coupling = hd.coupling;
+  p.walls_z = wl.walls_z;
+  for (int c = 0; c < 5; ++c) p.q_wall[c] = wl.q_wall[c];
   int rc = check_params(p);
   if (rc) return rc;
-  if (p.flow_on != h->p.flow_on || p.coupling != h->p.coupling) drop_graph(h);
+  if (p.flow_on != h->p.flow_on || p.coupling != h->p.coupling || p.walls_z != h->p.walls_z) drop_graph(h);
   h->p = p;
   rc = upload_replica(h);
   if (rc) return rc;
@@ -1154,6 +1189,7 @@ int lattice_rate(lcbp_lattice* h, const float** rate, cudaEvent_t done) {
 int lattice_fields(lcbp_lattice* h, float** q, const float** u, int dims[3], cudaStream_t* stream) {
   if (!h) return fail(LCBP_EINVAL, "null lattice handle");
   if (h->dtype != LCBP_F32) return fail(LCBP_EINVAL, "the surrogate works on FP32 lattice state");
+  if (h->p.walls_z) return fail(LCBP_EINVAL, "the surrogate's convolutions are periodic: no walls");
   cudaSetDevice(h->device);
   *q = static_cast<float*>(h->q);
   *u = reinterpret_cast<const float*>(static_cast<const char*>(h->rhou[h->cur]) + h->n * sizeof(float));

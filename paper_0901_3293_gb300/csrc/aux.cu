@@ -299,6 +299,26 @@ __device__ __forceinline__ void q9(const real* __restrict__ qp, long long n, lon
   m[2][0] = xz; m[2][1] = yz; m[2][2] = -xx - yy;
 }
 
+// A_ab eps_agd B_db for one direction g
+__device__ __forceinline__ double eps_contract(const double A[3][3], const double B[3][3], int g) {
+  double v = 0;
+  for (int b = 0; b < 3; ++b) {
+    if (g == 0) v += A[2][b] * B[1][b] - A[1][b] * B[2][b];
+    else if (g == 1) v += A[0][b] * B[2][b] - A[2][b] * B[0][b];
+    else v += A[1][b] * B[0][b] - A[0][b] * B[1][b];
+  }
+  return v;
+}
+
+// energy of the bond from A (at r) to B (at r + e_g): (K/2)|B - A|^2 + K q0 (A:eps_g B - B:eps_g A)
+__device__ __forceinline__ double bond_energy(const double A[3][3], const double B[3][3], int g, double K,
+                                              double q0) {
+  double d2 = 0;
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) d2 += (B[a][b] - A[a][b]) * (B[a][b] - A[a][b]);
+  return 0.5 * K * d2 + K * q0 * (eps_contract(A, B, g) - eps_contract(B, A, g));
+}
+
 // sums per block: [F_h, mass, Px, Py, Pz, defects, nonfinite, 0]
 template <typename real>
 __global__ void __launch_bounds__(256) k_diag(DiagGeom g, const real* __restrict__ Q, const real* __restrict__ f,
@@ -344,7 +364,21 @@ __global__ void __launch_bounds__(256) k_diag(DiagGeom g, const real* __restrict
     }
     const double bulk = 0.5 * g.A0 * (1.0 - g.gamma / 3.0) * tr2 - g.A0 * g.gamma / 3.0 * tr3 +
                         0.25 * g.A0 * g.gamma * tr2 * tr2;
-    acc[0] += bulk + 0.5 * g.K * grad2 + 2.0 * g.K * g.q0 * chiral + 2.0 * g.K * g.q0 * g.q0 * tr2;
+    if (!g.walls) {
+      acc[0] += bulk + 0.5 * g.K * grad2 + 2.0 * g.K * g.q0 * chiral + 2.0 * g.K * g.q0 * g.q0 * tr2;
+    } else {
+      // bond form: this site's three forward bonds (the z bond of the top plane
+      // ends on the anchored ghost) and, on the bottom plane, the bond from the
+      // ghost below; every bond touching the lattice is counted once
+      double Qw[3][3];
+      Qw[0][0] = g.qw[0]; Qw[0][1] = g.qw[1]; Qw[0][2] = g.qw[2];
+      Qw[1][0] = g.qw[1]; Qw[1][1] = g.qw[3]; Qw[1][2] = g.qw[4];
+      Qw[2][0] = g.qw[2]; Qw[2][1] = g.qw[4]; Qw[2][2] = -g.qw[0] - g.qw[3];
+      double Fb = bond_energy(Qc, Qp[0], 0, g.K, g.q0) + bond_energy(Qc, Qp[1], 1, g.K, g.q0);
+      Fb += bond_energy(Qc, z == g.nz - 1 ? Qw : Qp[2], 2, g.K, g.q0);
+      if (z == 0) Fb += bond_energy(Qw, Qc, 2, g.K, g.q0);
+      acc[0] += bulk + Fb + 2.0 * g.K * g.q0 * g.q0 * tr2;
+    }
     acc[5] += finite && lambda_max(Qc) < threshold ? 1.0 : 0.0;
     if (with_f) {
       double r = 1.0, jx = 0, jy = 0, jz = 0;  // deviation storage: rho = 1 + sum df_i

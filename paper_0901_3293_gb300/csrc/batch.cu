@@ -269,7 +269,7 @@ int lcbp_batch_create(int R, const int* dims, const lcbp_params* params, int dty
     long long mx = 0;
     for (const TileShape& c : kCandidates) mx = std::max(mx, tile_count(x, y, z, c));
     cap += mx;
-    HostParams hp;
+    HostParams hp{};
     hp.A0 = params[r].A0;
     hp.gamma = params[r].gamma;
     hp.K = params[r].K;

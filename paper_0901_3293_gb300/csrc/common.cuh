@@ -31,10 +31,12 @@ struct Model {
 // geometry + parameters of one replica, read by every CTA of its tiles
 template <typename real>
 struct Replica {
-  int nx, ny, nz, pad;
+  int nx, ny, nz;
+  int walls;       // 1: solid walls half a spacing below z = 0 and above z = nz-1
   long long n;     // nx * ny * nz
   long long base;  // first site of this replica in the concatenated range
   Model<real> m;
+  real qw[5];      // anchored Q on the ghost planes beyond the walls (q5 order)
 };
 
 // One unit of kernel work: a tile of TX x TY x TZ sites of replica `rep`
@@ -63,6 +65,10 @@ __host__ __device__ constexpr int ey(int i) {
 __host__ __device__ constexpr int ez(int i) {
   return i == 5 ? 1 : i == 6 ? -1 : (i >= 7 ? (((i - 7) & 1) ? -1 : 1) : 0);
 }
+
+// opposite direction: 1..6 pair up (+x,-x), (+y,-y), (+z,-z); the corners are
+// ordered lexicographically with + first, so i and 21 - i are opposite
+__host__ __device__ constexpr int opp(int i) { return i == 0 ? 0 : (i <= 6 ? ((i & 1) ? i + 1 : i - 1) : 21 - i); }
 
 // ---------------------------------------------------------------------------
 // Symmetric traceless tensors in 5 components [xx, xy, xz, yy, yz].
@@ -202,15 +208,18 @@ __device__ __forceinline__ void store5(real* __restrict__ p, long long n, long l
 // neighbours and the wrapped coordinates.
 struct Nbr {
   int x, y, z, xm, xp, ym, yp, zm, zp;
+  bool wlo, whi;  // the z-1 / z+1 neighbour is a ghost plane beyond a wall
   long long s;
   __device__ __forceinline__ long long at(int xx, int yy, int zz, int nx, int ny) const {
     return ((long long)zz * ny + yy) * nx + xx;
   }
 };
 
-__device__ __forceinline__ Nbr make_nbr(int x, int y, int z, int nx, int ny, int nz) {
+__device__ __forceinline__ Nbr make_nbr(int x, int y, int z, int nx, int ny, int nz, int walls = 0) {
   Nbr b;
   b.x = x; b.y = y; b.z = z;
+  b.wlo = walls && z == 0;
+  b.whi = walls && z == nz - 1;
   b.xm = x == 0 ? nx - 1 : x - 1;
   b.xp = x == nx - 1 ? 0 : x + 1;
   b.ym = y == 0 ? ny - 1 : y - 1;
@@ -238,6 +247,20 @@ __device__ __forceinline__ Stencil7<real> load_stencil(const real* __restrict__ 
   st.yp = load5(q, n, b.at(b.x, b.yp, b.z, nx, ny));
   st.zm = load5(q, n, b.at(b.x, b.y, b.zm, nx, ny));
   st.zp = load5(q, n, b.at(b.x, b.y, b.zp, nx, ny));
+  return st;
+}
+
+// the same with the anchored ghost planes of walled replicas (strong anchoring:
+// Q = qw on the planes z = -1 and z = nz)
+template <typename real>
+__device__ __forceinline__ Stencil7<real> load_stencil(const real* __restrict__ q, long long n, const Nbr& b,
+                                                       const Replica<real>& R) {
+  Stencil7<real> st = load_stencil(q, n, b, R.nx, R.ny);
+  if (b.wlo || b.whi) {
+    const Sym5<real> w = {R.qw[0], R.qw[1], R.qw[2], R.qw[3], R.qw[4]};
+    if (b.wlo) st.zm = w;
+    if (b.whi) st.zp = w;
+  }
   return st;
 }
 

@@ -19,6 +19,7 @@ struct StepArgs {
   TileShape ts;
   int flow_on;
   int coupling;  // 0 Jacobi, 1 Gauss-Seidel
+  int walls;     // some replica has solid walls in z (selects the bounce-back LB build)
   void* q;       // 5 comps, updated in place
   void* qs;      // 5 comps scratch (Heun predictor)
   void* h;       // 5 comps scratch
@@ -86,6 +87,8 @@ struct DiagGeom {
   int nx, ny, nz;
   long long n, base;
   double A0, gamma, K, q0;
+  int walls;       // solid walls in z: F_h in bond form with the anchored ghost planes
+  double qw[5];    // anchored Q (q5 order)
 };
 template <typename real>
 cudaError_t launch_diag_one(const DiagGeom& g, const void* q, const void* f, int with_f, double threshold,

@@ -15,6 +15,8 @@ struct HostParams {
   double A0, gamma, K, q0;  // Landau-de Gennes (Sec. 2.1 Eq. free_energy)
   double tau_f, xi, Gamma;  // kinetics (Sec. 2.1, 2.2)
   int flow_on, coupling;
+  int walls_z;              // solid walls below z = 0 and above z = nz-1
+  double q_wall[5];         // anchored Q beyond the walls (q5 order)
 };
 
 extern thread_local std::string g_last_error;

@@ -38,10 +38,11 @@ __device__ __forceinline__ void load_u(const real* __restrict__ ru, long long n,
   u[2] = __ldg(ru + 3 * n + s);
 }
 
-// W_ab = D0_b u_a from the 6 face neighbours
+// W_ab = D0_b u_a from the 6 face neighbours; beyond a wall the ghost velocity
+// is -u of the site itself (no slip half a spacing away), u_own = u at b.s
 template <typename real>
 __device__ __forceinline__ void velocity_gradient(const real* __restrict__ ru, long long n, const Nbr& b,
-                                                  int nx, int ny, real w[3][3]) {
+                                                  int nx, int ny, real w[3][3], const real* u_own = nullptr) {
   real up[3], um[3];
   load_u(ru, n, b.at(b.xp, b.y, b.z, nx, ny), up);
   load_u(ru, n, b.at(b.xm, b.y, b.z, nx, ny), um);
@@ -53,6 +54,14 @@ __device__ __forceinline__ void velocity_gradient(const real* __restrict__ ru, l
   for (int a = 0; a < 3; ++a) w[a][1] = real(0.5) * (up[a] - um[a]);
   load_u(ru, n, b.at(b.x, b.y, b.zp, nx, ny), up);
   load_u(ru, n, b.at(b.x, b.y, b.zm, nx, ny), um);
+  if (u_own && b.whi) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) up[a] = -u_own[a];
+  }
+  if (u_own && b.wlo) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) um[a] = -u_own[a];
+  }
 #pragma unroll
   for (int a = 0; a < 3; ++a) w[a][2] = real(0.5) * (up[a] - um[a]);
 }
@@ -68,8 +77,8 @@ __global__ void __launch_bounds__(256) k_field(const Replica<real>* __restrict__
     int x, y, z;
     if (!tile_site(reps, tiles, t, ts, R, x, y, z)) continue;
     const long long n = R.n;
-    const Nbr nb = make_nbr(x, y, z, R.nx, R.ny, R.nz);
-    const Stencil7<real> st = load_stencil(Q + 5 * R.base, n, nb, R.nx, R.ny);
+    const Nbr nb = make_nbr(x, y, z, R.nx, R.ny, R.nz, R.walls);
+    const Stencil7<real> st = load_stencil(Q + 5 * R.base, n, nb, R);
     Sym5<real> dq[3];
     const Sym5<real> h = molecular_field(st, R.m, dq);
     store5(H + 5 * R.base, n, nb.s, h);
@@ -102,8 +111,8 @@ __global__ void __launch_bounds__(256) k_force_predict(const Replica<real>* __re
     int x, y, z;
     if (!tile_site(reps, tiles, t, ts, R, x, y, z)) continue;
     const long long n = R.n;
-    const Nbr nb = make_nbr(x, y, z, R.nx, R.ny, R.nz);
-    const Stencil7<real> st = load_stencil(Q + 5 * R.base, n, nb, R.nx, R.ny);
+    const Nbr nb = make_nbr(x, y, z, R.nx, R.ny, R.nz, R.walls);
+    const Stencil7<real> st = load_stencil(Q + 5 * R.base, n, nb, R);
     Sym5<real> dq[3];
     dq[0] = half_diff(st.xp, st.xm);
     dq[1] = half_diff(st.yp, st.ym);
@@ -112,13 +121,16 @@ __global__ void __launch_bounds__(256) k_force_predict(const Replica<real>* __re
     if (DO_B) {
       const real* tp = tau + 3 * R.base;
       auto tv = [&](int c, long long s) { return __ldg(tp + c * n + s); };
+      // tau on a ghost plane beyond a wall is 0 (the wall carries no molecular field)
+      auto tvzp = [&](int c, long long s) { return nb.whi ? real(0) : tv(c, s); };
+      auto tvzm = [&](int c, long long s) { return nb.wlo ? real(0) : tv(c, s); };
       const long long sxp = nb.at(nb.xp, y, z, R.nx, R.ny), sxm = nb.at(nb.xm, y, z, R.nx, R.ny);
       const long long syp = nb.at(x, nb.yp, z, R.nx, R.ny), sym = nb.at(x, nb.ym, z, R.nx, R.ny);
       const long long szp = nb.at(x, y, nb.zp, R.nx, R.ny), szm = nb.at(x, y, nb.zm, R.nx, R.ny);
       // tau = [xy, xz, yz], tau_yx = -tau_xy etc.
       const real half = real(0.5);
-      real bx = half * (tv(0, syp) - tv(0, sym)) + half * (tv(1, szp) - tv(1, szm));
-      real by = -half * (tv(0, sxp) - tv(0, sxm)) + half * (tv(2, szp) - tv(2, szm));
+      real bx = half * (tv(0, syp) - tv(0, sym)) + half * (tvzp(1, szp) - tvzm(1, szm));
+      real by = -half * (tv(0, sxp) - tv(0, sxm)) + half * (tvzp(2, szp) - tvzm(2, szm));
       real bz = -half * (tv(1, sxp) - tv(1, sxm)) - half * (tv(2, syp) - tv(2, sym));
       bx -= ddot(h, dq[0]);
       by -= ddot(h, dq[1]);
@@ -140,7 +152,7 @@ __global__ void __launch_bounds__(256) k_force_predict(const Replica<real>* __re
       if (FLOW) {
         const real* ru = rhou + 4 * R.base;
         load_u(ru, n, nb.s, u);
-        velocity_gradient(ru, n, nb, R.nx, R.ny, w);
+        velocity_gradient(ru, n, nb, R.nx, R.ny, w, u);
       }
       const Sym5<real> r = be_rate(st.c, h, dq, u, w, R.m, FLOW);
       const Sym5<real> qs = {st.c.xx + r.xx, st.c.xy + r.xy, st.c.xz + r.xz, st.c.yy + r.yy, st.c.yz + r.yz};
@@ -153,7 +165,7 @@ __global__ void __launch_bounds__(256) k_force_predict(const Replica<real>* __re
 // DO_LB: predictor-corrector LB (pull form) writing f^{n+1} and its moments.
 // DO_Q2: Heun corrector for Q with u from `rhou_q` (u^n for Jacobi coupling,
 //        u^{n+1} for Gauss-Seidel), in place on Q.
-template <typename real, bool FLOW, bool DO_LB, bool DO_Q2>
+template <typename real, bool FLOW, bool DO_LB, bool DO_Q2, bool WALLS = false>
 __global__ void __launch_bounds__(256) k_lb_correct(const Replica<real>* __restrict__ reps,
                                                     const Tile* __restrict__ tiles, int ntiles, TileShape ts,
                                                     const real* __restrict__ f, const real* __restrict__ rhou,
@@ -167,7 +179,9 @@ __global__ void __launch_bounds__(256) k_lb_correct(const Replica<real>* __restr
     if (!tile_site(reps, tiles, t, ts, R, x, y, z)) continue;
     const long long n = R.n;
     const int nx = R.nx, ny = R.ny;
-    const Nbr nb = make_nbr(x, y, z, nx, ny, R.nz);
+    // walls: Q and u ghosts are handled at run time; the LB bounce-back is
+    // compiled in only for WALLS (a lattice with walls launches that build)
+    const Nbr nb = make_nbr(x, y, z, nx, ny, R.nz, R.walls);
     if (DO_LB) {
       // populations and density are stored as deviations df = f - w, drho = rho - 1
       const real* fr = f + 15 * R.base;
@@ -178,8 +192,21 @@ __global__ void __launch_bounds__(256) k_lb_correct(const Replica<real>* __restr
       real ds[NV], dh[NV];  // predictor f* and f + C/2, pulled from y - e_i (deviation form)
       Sym5<real> sig_y;
       real b_y[3];
+      real drho_y = real(0), u_y[3] = {real(0), real(0), real(0)};
 #pragma unroll
       for (int i = 0; i < NV; ++i) {
+        if (WALLS && ((ez(i) > 0 && nb.wlo) || (ez(i) < 0 && nb.whi))) {
+          // half-way bounce-back: the population arriving from beyond the wall
+          // is the reflected one of this site, [f + C]_opp(i)(y)
+          const int o = opp(i);
+          const real di = __ldg(fr + o * n + nb.s);
+          const real usq = u_y[0] * u_y[0] + u_y[1] * u_y[1] + u_y[2] * u_y[2];
+          const real C = -(di - feq_delta(o, drho_y, real(1) + drho_y, u_y[0], u_y[1], u_y[2], usq, sig_y)) * inv_tau +
+                         force_dir(o, b_y[0], b_y[1], b_y[2]);
+          ds[i] = di + C;
+          dh[i] = di + real(0.5) * C;
+          continue;
+        }
         // source site y - e_i
         const int sx = ex(i) > 0 ? nb.xm : ex(i) < 0 ? nb.xp : x;
         const int sy = ey(i) > 0 ? nb.ym : ey(i) < 0 ? nb.yp : y;
@@ -193,6 +220,8 @@ __global__ void __launch_bounds__(256) k_lb_correct(const Replica<real>* __restr
         if (i == 0) {
           sig_y = s;
           b_y[0] = bx; b_y[1] = by; b_y[2] = bz;
+          drho_y = drho;
+          u_y[0] = ux; u_y[1] = uy; u_y[2] = uz;
         }
         const real usq = ux * ux + uy * uy + uz * uz;
         const real C = -(di - feq_delta(i, drho, real(1) + drho, ux, uy, uz, usq, s)) * inv_tau +
@@ -233,7 +262,7 @@ __global__ void __launch_bounds__(256) k_lb_correct(const Replica<real>* __restr
       rn[3 * n + nb.s] = j1z * inv_r1;
     }
     if (DO_Q2) {
-      const Stencil7<real> st = load_stencil(Qs + 5 * R.base, n, nb, nx, ny);
+      const Stencil7<real> st = load_stencil(Qs + 5 * R.base, n, nb, R);
       Sym5<real> dq[3];
       const Sym5<real> h = molecular_field(st, R.m, dq);
       real u[3] = {real(0), real(0), real(0)};
@@ -241,7 +270,7 @@ __global__ void __launch_bounds__(256) k_lb_correct(const Replica<real>* __restr
       if (FLOW) {
         const real* ru = rhou_q + 4 * R.base;
         load_u(ru, n, nb.s, u);
-        velocity_gradient(ru, n, nb, nx, ny, w);
+        velocity_gradient(ru, n, nb, nx, ny, w, u);
       }
       const Sym5<real> r = be_rate(st.c, h, dq, u, w, R.m, FLOW);
       const Sym5<real> q0 = load5(Qin + 5 * R.base, n, nb.s);
@@ -283,9 +312,14 @@ cudaError_t launch_step(const StepArgs& a, cudaStream_t s) {
         k_force_predict<real, true, true, true, false><<<grid, threads, 0, s>>>(
             reps, a.tiles, a.ntiles, a.ts, Cp(a.q), Cp(a.h), Cp(a.tau), Cp(a.rhou), nullptr, Rp(a.b), Rp(a.qs));
       mark();
-      k_lb_correct<real, true, true, true><<<grid, threads, 0, s>>>(
-          reps, a.tiles, a.ntiles, a.ts, Cp(a.f), Cp(a.rhou), Cp(a.sigma), Cp(a.b), Rp(a.fnew), Rp(a.rhou_new),
-          Cp(a.qs), Cp(a.rhou), Cp(a.q), Rp(qout));
+      if (a.walls)
+        k_lb_correct<real, true, true, true, true><<<grid, threads, 0, s>>>(
+            reps, a.tiles, a.ntiles, a.ts, Cp(a.f), Cp(a.rhou), Cp(a.sigma), Cp(a.b), Rp(a.fnew), Rp(a.rhou_new),
+            Cp(a.qs), Cp(a.rhou), Cp(a.q), Rp(qout));
+      else
+        k_lb_correct<real, true, true, true><<<grid, threads, 0, s>>>(
+            reps, a.tiles, a.ntiles, a.ts, Cp(a.f), Cp(a.rhou), Cp(a.sigma), Cp(a.b), Rp(a.fnew), Rp(a.rhou_new),
+            Cp(a.qs), Cp(a.rhou), Cp(a.q), Rp(qout));
       mark();
     } else {
       // Gauss-Seidel: b, LB, then the Heun stages with u^{n+1}
@@ -296,9 +330,14 @@ cudaError_t launch_step(const StepArgs& a, cudaStream_t s) {
         k_force_predict<real, true, true, false, false><<<grid, threads, 0, s>>>(
             reps, a.tiles, a.ntiles, a.ts, Cp(a.q), Cp(a.h), Cp(a.tau), Cp(a.rhou), nullptr, Rp(a.b), nullptr);
       mark();
-      k_lb_correct<real, true, true, false><<<grid, threads, 0, s>>>(
-          reps, a.tiles, a.ntiles, a.ts, Cp(a.f), Cp(a.rhou), Cp(a.sigma), Cp(a.b), Rp(a.fnew), Rp(a.rhou_new),
-          nullptr, nullptr, nullptr, nullptr);
+      if (a.walls)
+        k_lb_correct<real, true, true, false, true><<<grid, threads, 0, s>>>(
+            reps, a.tiles, a.ntiles, a.ts, Cp(a.f), Cp(a.rhou), Cp(a.sigma), Cp(a.b), Rp(a.fnew), Rp(a.rhou_new),
+            nullptr, nullptr, nullptr, nullptr);
+      else
+        k_lb_correct<real, true, true, false><<<grid, threads, 0, s>>>(
+            reps, a.tiles, a.ntiles, a.ts, Cp(a.f), Cp(a.rhou), Cp(a.sigma), Cp(a.b), Rp(a.fnew), Rp(a.rhou_new),
+            nullptr, nullptr, nullptr, nullptr);
       mark();
       k_force_predict<real, true, false, true, false><<<grid, threads, 0, s>>>(
           reps, a.tiles, a.ntiles, a.ts, Cp(a.q), Cp(a.h), nullptr, Cp(a.rhou_new), nullptr, nullptr, Rp(a.qs));

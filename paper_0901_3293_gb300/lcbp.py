@@ -65,6 +65,7 @@ _SIGNATURES = {
     "lcbp_totals": (_c_int, [_P, ctypes.POINTER(_c_double), ctypes.POINTER(_c_double)]),
     "lcbp_defect_fraction": (_c_int, [_P, _c_double, ctypes.POINTER(_c_double)]),
     "lcbp_optics_default": (_c_int, [_P]),
+    "lcbp_set_walls": (_c_int, [_P, _c_int, _P]),
     "lcbp_texture": (_c_int, [_P, _P, _P]),
     "lcbp_save": (_c_int, [_P, ctypes.c_char_p]),
     "lcbp_load": (_c_int, [_P, ctypes.c_char_p]),
@@ -262,6 +263,12 @@ class Lattice:
         return self
 
     # -- state ----------------------------------------------------------------
+    def set_walls(self, walls: bool = True, q_wall=None) -> "Lattice":
+        """Solid walls below z = 0 and above z = Nz-1 (bounce-back, strong anchoring to q_wall, q5 order)."""
+        qw = None if q_wall is None else np.ascontiguousarray(np.asarray(q_wall, dtype=np.float64).reshape(5))
+        check(lib().lcbp_set_walls(self._h, 1 if walls else 0, qw.ctypes.data if qw is not None else None))
+        return self
+
     def init_q(self, kind: int, amplitude: float, noise: float = 0.0, seed: int = 0, z0: int | None = None):
         region = (ctypes.c_int * 1)(z0) if z0 is not None else None
         check(lib().lcbp_init_q(self._h, kind, amplitude, noise, seed, region))
