@@ -278,18 +278,23 @@ __global__ void __launch_bounds__(ZM_TX* TY / SPT) k_qside(const __grid_constant
     field_plane(z0);
   }
 
+  // Per plane two CTA barriers: after the waits (patched halos, a uniform abort
+  // decision) and after the H / tau pass.  A thread past the first barrier of
+  // plane z knows every thread has finished plane z-1, the last reader of the
+  // Q and u slots the next loads overwrite (planes z-2) and of the tau / H
+  // slots this plane's pass overwrites, so no barrier closes the plane.
   for (int z = z0; z < z1 && !aborted; ++z) {
-    if (threadIdx.x == 0) {
-      fence_proxy_async();
-      if (z + 3 <= z1 + 1) issue_q(z + 3);
-      if (z + 2 <= z1) issue_u(z + 2);
-    }
     wait_q(z + 2);
     wait_u(z + 1);
     __syncthreads();
     if (*abort_flag) {
       aborted = true;
       break;
+    }
+    if (threadIdx.x == 0) {
+      fence_proxy_async();
+      if (z + 3 <= z1 + 1) issue_q(z + 3);
+      if (z + 2 <= z1) issue_u(z + 2);
     }
     field_plane(z + 1);
     __syncthreads();
@@ -354,7 +359,6 @@ __global__ void __launch_bounds__(ZM_TX* TY / SPT) k_qside(const __grid_constant
         store5_lane<SPT, real>(Qs, n, s, qs, k);
       }
     }
-    __syncthreads();
   }
   if (aborted && threadIdx.x == 0) {
     // a barrier wait timed out: record it and give copies in flight a
@@ -484,11 +488,10 @@ __global__ void __launch_bounds__(ZM_TX* TY / SPT, 2)
   const V inv_tau = V(m.inv_tau);
   const Model<V> mv = widen<V>(m);
 
+  // One CTA barrier per plane, after the wait: past it every thread has
+  // finished plane z-1, the last reader of the slot that the load of plane
+  // z+2 overwrites (plane z-2), so that load is issued right after it.
   for (int z = z0; z < z1; ++z) {
-    if (threadIdx.x == 0) {
-      fence_proxy_async();
-      if (z + 2 <= z1) issue(z + 2);
-    }
     // populations f_i(y - e_i), issued before the barrier wait so that they overlap it
     real fin_l[SPT][NV];
     if (valid) {
@@ -512,6 +515,10 @@ __global__ void __launch_bounds__(ZM_TX* TY / SPT, 2)
     if (*abort_flag) {
       aborted = true;
       break;
+    }
+    if (threadIdx.x == 0) {
+      fence_proxy_async();
+      if (z + 2 <= z1) issue(z + 2);
     }
     if (valid) {
       long long s[SPT];
@@ -624,7 +631,6 @@ __global__ void __launch_bounds__(ZM_TX* TY / SPT, 2)
       for (int k = 0; k < SPT; ++k)
         if (lane_ok[k]) store5_lane<SPT, real>(Qout, n, s[k], q1, k);
     }
-    __syncthreads();
   }
   if (aborted && threadIdx.x == 0) {
     atomicExch(err, 1);
