@@ -83,9 +83,6 @@ __device__ __forceinline__ void umma_commit(uint64_t* bar) {
                : "memory");
 }
 
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
-}
 
 // ---- tensor memory -> registers ---------------------------------------------
 // 32 lanes x 32-bit, 8, 16 or 32 consecutive columns per thread (warp w reads lanes 32 (w % 4) ...)
