@@ -140,8 +140,17 @@ struct QsideSmem {
   static constexpr size_t bytes = sizeof(real) * (size_t)OFF_BAR + 16 * 8 + 16;
 };
 
+// Threads of a k_qside CTA: enough to cover the H / tau ring of a plane
+// ((TY + 2) x (TX + 2) cells, a pair per thread with SPT = 2) in one pass, and
+// at least the TY / SPT rows of the output pass.
+template <int TY, int SPT>
+constexpr int qside_threads() {
+  constexpr int ring = (TY + 2) / SPT * (ZM_TX + 2), out = ZM_TX * TY / SPT;
+  return ((ring > out ? ring : out) + 31) / 32 * 32;
+}
+
 template <typename real, int TY, int SPT>
-__global__ void __launch_bounds__(ZM_TX* TY / SPT) k_qside(const __grid_constant__ CUtensorMap tmQ,
+__global__ void __launch_bounds__(qside_threads<TY, SPT>()) k_qside(const __grid_constant__ CUtensorMap tmQ,
                                                      const __grid_constant__ CUtensorMap tmU, ZmGeom G,
                                                      Model<real> m, const real* __restrict__ Q,
                                                      const real* __restrict__ rhou, const real* __restrict__ bext,
@@ -298,7 +307,7 @@ __global__ void __launch_bounds__(ZM_TX* TY / SPT) k_qside(const __grid_constant
     }
     field_plane(z + 1);
     __syncthreads();
-    if (gx < nx && y0 + ty < ny) {
+    if (ty < TYH && gx < nx && y0 + ty < ny) {
       const real* qm = qslot(z - 1);
       const real* qc = qslot(z);
       const real* qp = qslot(z + 1);
@@ -704,7 +713,7 @@ cudaError_t launch_step_zm_spt(const ZmArgs& a, cudaStream_t s) {
   const int grid = G.tiles_x * G.tiles_y * G.tiles_z;
   const Model<real> m = *static_cast<const Model<real>*>(a.model);
   if (a.events) cudaEventRecord(a.events[0], s);
-  k_qside<real, TY, SPT><<<grid, ZM_TX * TY / SPT, QsideSmem<real, TY>::bytes, s>>>(
+  k_qside<real, TY, SPT><<<grid, qside_threads<TY, SPT>(), QsideSmem<real, TY>::bytes, s>>>(
       *a.tm_q, *a.tm_u, G, m, static_cast<const real*>(a.q), static_cast<const real*>(a.rhou),
       static_cast<const real*>(a.bext), static_cast<real*>(a.sigma), static_cast<real*>(a.b),
       static_cast<real*>(a.qs), a.err);
