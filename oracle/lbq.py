@@ -93,6 +93,14 @@ class Params:
     # "Solid walls" section below); q_wall = the anchored Q in q5 order
     walls_z: bool = False
     q_wall: tuple = (0.0, 0.0, 0.0, 0.0, 0.0)
+    # coefficient of (1/2)(d_b Q_ab)^2 beside the printed chiral square: None =
+    # K (the one-constant energy, default); 0 = the energy exactly as printed
+    L2: float | None = None
+
+    @property
+    def c_div(self) -> float:
+        """(K - L2) / 2: weight of -(d_b Q_ab)^2 relative to the one-constant energy."""
+        return 0.0 if self.L2 is None else 0.5 * (self.K - self.L2)
 
     def with_(self, **kw) -> "Params":
         return replace(self, **kw)
@@ -207,6 +215,15 @@ def curl_term(Q: np.ndarray) -> np.ndarray:
     return np.einsum("agd,...gdb->...ab", EPS, dQ)
 
 
+def divergence(Q: np.ndarray) -> np.ndarray:
+    """div_a = sum_b D0_b Q_ab (central differences)."""
+    d = np.zeros(Q.shape[:3] + (3,))
+    for a in range(3):
+        for b in range(3):
+            d[..., a] += d0(Q[..., a, b], b)
+    return d
+
+
 def bulk_free_energy_density(Q: np.ndarray, p: Params) -> np.ndarray:
     """Bulk part of Eq. (free_energy):
     A0/2 (1 - gamma/3) Q_ab^2 - A0 gamma/3 Q_ab Q_bc Q_ca + A0 gamma/4 (Q_ab^2)^2."""
@@ -230,10 +247,16 @@ def free_energy_density(Q: np.ndarray, p: Params) -> np.ndarray:
         dq = dplus(Q, g)
         grad2 += ddot(dq, dq)
     chiral = ddot(Q, curl_term(Q))
-    return (bulk_free_energy_density(Q, p)
-            + 0.5 * p.K * grad2
-            + 2.0 * p.K * p.q0 * chiral
-            + 2.0 * p.K * p.q0 * p.q0 * ddot(Q, Q))
+    out = (bulk_free_energy_density(Q, p)
+           + 0.5 * p.K * grad2
+           + 2.0 * p.K * p.q0 * chiral
+           + 2.0 * p.K * p.q0 * p.q0 * ddot(Q, Q))
+    if p.c_div != 0.0:
+        # (K/2)(eps dQ + 2 q0 Q)^2 = one-constant energy - (K/2)(d_b Q_ab)^2 up to a
+        # divergence; a general L2 keeps -((K - L2)/2)(div Q)^2 of that difference
+        dv = divergence(Q)
+        out = out - p.c_div * np.sum(dv * dv, axis=-1)
+    return out
 
 
 def bond_energy(A: np.ndarray, B: np.ndarray, g: int, p: Params) -> np.ndarray:
@@ -278,16 +301,28 @@ def dF_dQ(Q: np.ndarray, p: Params) -> np.ndarray:
     Gradient: -K Lap7 Q + 2 K q0 (C + C^T) + 4 K q0^2 Q with C = eps D0 Q.
     """
     if p.walls_z:
+        if p.c_div != 0.0:
+            raise ValueError("walls with L2 != K are not supported")
         return dF_dQ(_pad_q(Q, p), _no_walls(p))[1:-1]
     q2 = ddot(Q, Q)[..., None, None]
     QQ = Q @ Q
     C = curl_term(Q)
-    return (p.A0 * (1.0 - p.gamma / 3.0) * Q
-            - p.A0 * p.gamma * QQ
-            + p.A0 * p.gamma * q2 * Q
-            - p.K * laplacian7(Q)
-            + 2.0 * p.K * p.q0 * (C + transpose(C))
-            + 4.0 * p.K * p.q0 * p.q0 * Q)
+    G = (p.A0 * (1.0 - p.gamma / 3.0) * Q
+         - p.A0 * p.gamma * QQ
+         + p.A0 * p.gamma * q2 * Q
+         - p.K * laplacian7(Q)
+         + 2.0 * p.K * p.q0 * (C + transpose(C))
+         + 4.0 * p.K * p.q0 * p.q0 * Q)
+    if p.c_div != 0.0:
+        # d/dQ_ab of -c sum_x |div|^2 (summation by parts: the adjoint of D0 is -D0),
+        # symmetrised: c (D0_b div_a + D0_a div_b)
+        dv = divergence(Q)
+        M = np.zeros_like(Q)
+        for a in range(3):
+            for b in range(3):
+                M[..., a, b] = d0(dv[..., a], b)
+        G = G + p.c_div * (M + transpose(M))
+    return G
 
 
 def molecular_field(Q: np.ndarray, p: Params) -> np.ndarray:
