@@ -159,6 +159,19 @@ LCBP_API int lcbp_set_ldg_kappa_tau(lcbp_lattice *h, double A0, double q0, doubl
 LCBP_API int lcbp_set_flow(lcbp_lattice *h, double tau_f, double xi, double Gamma, int flow_on, int coupling);
 
 /*
+ * Elastic energy variant (Sec. 2.1, Eq. free_energy).  The printed gradient
+ * energy is the chiral square (K/2)(eps dQ + 2 q0 Q)^2; on a periodic domain
+ * it equals the one-constant energy (K/2)|grad Q|^2 + 2 K q0 Q:(eps grad Q) +
+ * 2 K q0^2 |Q|^2 minus (K/2)(d_b Q_ab)^2.  By default (use_l2 = 0) the library
+ * uses the one-constant energy; with use_l2 != 0 the energy gains
+ * -((K - L2)/2) sum_x |div Q|^2, div_a = sum_b D0_b Q_ab (central differences),
+ * and H its exact lattice gradient: L2 = 0 is the energy exactly as printed,
+ * L2 = K the default.  Lattices with L2 != K run the generic kernels.
+ * Errors: LCBP_EINVAL (non-finite L2; walls set).
+ */
+LCBP_API int lcbp_set_l2(lcbp_lattice *h, int use_l2, double L2);
+
+/*
  * Solid walls in z (not in the paper, whose slab is periodic; an extension).
  * With walls_z != 0 the lattice has walls half a spacing below z = 0 and above
  * z = Nz-1, while x and y stay periodic:
@@ -172,7 +185,7 @@ LCBP_API int lcbp_set_flow(lcbp_lattice *h, double tau_f, double xi, double Gamm
  * The free energy then counts every bond with at least one end on the
  * lattice, so H stays its exact gradient.  Walled lattices run the generic
  * kernels; the surrogate refuses them.  walls_z = 0 restores periodic z.
- * Errors: LCBP_EINVAL (non-finite q_wall).
+ * Errors: LCBP_EINVAL (non-finite q_wall; L2 set).
  */
 LCBP_API int lcbp_set_walls(lcbp_lattice *h, int walls_z, const double *q_wall5);
 

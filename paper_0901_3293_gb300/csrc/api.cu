@@ -69,6 +69,7 @@ Model<real> make_model(const HostParams& p) {
   m.Gamma = (real)p.Gamma;
   m.xi = (real)p.xi;
   m.inv_tau = (real)(1.0 / p.tau_f);
+  m.c_div = (real)(p.l2_set ? 0.5 * (p.K - p.L2) : 0.0);
   return m;
 }
 
@@ -338,7 +339,7 @@ bool fast_shape_ok(const lcbp_lattice* h) { return h->nx % 4 == 0; }
 
 bool use_fast(lcbp_lattice* h) {
   if (h->path_req == LCBP_PATH_GENERIC || !h->p.flow_on || h->p.coupling != LCBP_JACOBI || !fast_shape_ok(h) ||
-      h->p.walls_z)
+      h->p.walls_z || (h->p.l2_set && h->p.L2 != h->p.K))
     return false;
   if (!h->tmaps_ok) {
     static std::once_flag prep32, prep64;
@@ -580,8 +581,9 @@ int build_graph(lcbp_lattice* h) {
 }
 
 int diag(lcbp_lattice* h, double threshold, int with_f) {
-  DiagGeom g{h->nx, h->ny, h->nz, h->n, 0, h->p.A0, h->p.gamma, h->p.K, h->p.q0, h->p.walls_z, {}};
+  DiagGeom g{h->nx, h->ny, h->nz, h->n, 0, h->p.A0, h->p.gamma, h->p.K, h->p.q0, h->p.walls_z, {}, 0.0};
   for (int c = 0; c < 5; ++c) g.qw[c] = h->p.q_wall[c];
+  g.c_div = h->p.l2_set ? 0.5 * (h->p.K - h->p.L2) : 0.0;
   cudaError_t e = h->dtype == LCBP_F64
                       ? launch_diag_one<double>(g, h->q, h->f[h->cur], with_f, threshold, h->d_partials, h->d_out,
                                                 h->stream)
@@ -620,8 +622,9 @@ struct CkptHeader {
 };
 // version 3 appends the walls after the version-2 header
 struct CkptWalls {
-  int32_t walls_z, pad;
+  int32_t walls_z, l2_set;
   double q_wall[5];
+  double L2;
 };
 
 }  // namespace
@@ -771,8 +774,21 @@ int lcbp_set_flow(lcbp_lattice* h, double tau_f, double xi, double Gamma, int fl
   return upload_replica(h);
 }
 
+int lcbp_set_l2(lcbp_lattice* h, int use_l2, double L2) {
+  CHECK_H(h);
+  if (use_l2 && !std::isfinite(L2)) return fail(LCBP_EINVAL, "L2 must be finite");
+  if (use_l2 && h->p.walls_z) return fail(LCBP_EINVAL, "L2 with walls is not supported");
+  HostParams p = h->p;
+  p.l2_set = use_l2 ? 1 : 0;
+  p.L2 = use_l2 ? L2 : 0.0;
+  drop_graph(h);  // the fast path may no longer apply
+  h->p = p;
+  return upload_replica(h);
+}
+
 int lcbp_set_walls(lcbp_lattice* h, int walls_z, const double* q_wall5) {
   CHECK_H(h);
+  if (walls_z && h->p.l2_set) return fail(LCBP_EINVAL, "walls with L2 are not supported");
   HostParams p = h->p;
   p.walls_z = walls_z ? 1 : 0;
   for (int c = 0; c < 5; ++c) {
@@ -1062,6 +1078,8 @@ int lcbp_save(lcbp_lattice* h, const char* path) {
   CkptWalls wl{};
   wl.walls_z = h->p.walls_z;
   for (int c = 0; c < 5; ++c) wl.q_wall[c] = h->p.q_wall[c];
+  wl.l2_set = h->p.l2_set;
+  wl.L2 = h->p.L2;
   hd.nx = h->nx;
   hd.ny = h->ny;
   hd.nz = h->nz;
@@ -1128,9 +1146,13 @@ int lcbp_load(lcbp_lattice* h, const char* path) {
   p.coupling = hd.coupling;
   p.walls_z = wl.walls_z;
   for (int c = 0; c < 5; ++c) p.q_wall[c] = wl.q_wall[c];
+  p.l2_set = wl.l2_set;
+  p.L2 = wl.L2;
   int rc = check_params(p);
   if (rc) return rc;
-  if (p.flow_on != h->p.flow_on || p.coupling != h->p.coupling || p.walls_z != h->p.walls_z) drop_graph(h);
+  if (p.flow_on != h->p.flow_on || p.coupling != h->p.coupling || p.walls_z != h->p.walls_z ||
+      p.l2_set != h->p.l2_set || p.L2 != h->p.L2)
+    drop_graph(h);
   h->p = p;
   rc = upload_replica(h);
   if (rc) return rc;

@@ -366,6 +366,16 @@ __global__ void __launch_bounds__(256) k_diag(DiagGeom g, const real* __restrict
                         0.25 * g.A0 * g.gamma * tr2 * tr2;
     if (!g.walls) {
       acc[0] += bulk + 0.5 * g.K * grad2 + 2.0 * g.K * g.q0 * chiral + 2.0 * g.K * g.q0 * g.q0 * tr2;
+      if (g.c_div != 0.0) {
+        // div_a = sum_b D0_b Q_ab from the face neighbours
+        double d2 = 0;
+        for (int a = 0; a < 3; ++a) {
+          double dv = 0;
+          for (int b = 0; b < 3; ++b) dv += 0.5 * (Qp[b][a][b] - Qm[b][a][b]);
+          d2 += dv * dv;
+        }
+        acc[0] -= g.c_div * d2;
+      }
     } else {
       // bond form: this site's three forward bonds (the z bond of the top plane
       // ends on the anchored ghost) and, on the bottom plane, the bond from the

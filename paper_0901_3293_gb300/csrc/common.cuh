@@ -26,6 +26,7 @@ struct Model {
   real Gamma;    // rotational diffusion constant
   real xi;       // flow-aligning parameter
   real inv_tau;  // 1 / tau_f
+  real c_div;    // (K - L2) / 2: weight of -(div Q)^2 (0 = one-constant energy)
 };
 
 // geometry + parameters of one replica, read by every CTA of its tiles
@@ -482,6 +483,54 @@ __device__ __forceinline__ real force_dir(int i, real bx, real by, real bz) {
   if (i == 0) return real(0);
   const real eb = signed_sum(ex(i), bx, ey(i), by, ez(i), bz);
   return (i <= 6 ? LCBP_Q(1, 3) : LCBP_Q(1, 24)) * eb;
+}
+
+// ---------------------------------------------------------------------------
+// The (div Q)^2 part of the energy for L2 != K: F gains -c sum_x |div Q|^2 with
+// div_a = sum_b D0_b Q_ab, so dF/dQ gains c (D0_b div_a + D0_a div_b) and H the
+// negative of that, made traceless.  div is taken at the 6 face neighbours
+// from their own face neighbours (Q at distance 2 on the axes and on the 12
+// in-plane diagonals).  Periodic lattice.
+// ---------------------------------------------------------------------------
+template <typename real>
+__device__ __forceinline__ void add_div_field(Sym5<real>& h, const real* __restrict__ q, long long n, int x, int y,
+                                              int z, int nx, int ny, int nz, real c) {
+  auto wr = [](int v, int m) { return v < 0 ? v + m : (v >= m ? v - m : v); };
+  auto at = [&](int xx, int yy, int zz) {
+    return ((long long)wr(zz, nz) * ny + wr(yy, ny)) * nx + wr(xx, nx);
+  };
+  // column b of Q at site s: (Q_xb, Q_yb, Q_zb)
+  auto col = [&](long long s, int b, real out[3]) {
+    const Sym5<real> v = load5(q, n, s);
+    if (b == 0) { out[0] = v.xx; out[1] = v.xy; out[2] = v.xz; }
+    else if (b == 1) { out[0] = v.xy; out[1] = v.yy; out[2] = v.yz; }
+    else { out[0] = v.xz; out[1] = v.yz; out[2] = -v.xx - v.yy; }
+  };
+  real dv[3][2][3];  // div_a at x + s e_g: [g][s = +, -][a]
+  for (int g = 0; g < 3; ++g)
+    for (int sg = 0; sg < 2; ++sg) {
+      const int o = sg == 0 ? 1 : -1;
+      const int yx = x + (g == 0 ? o : 0), yy = y + (g == 1 ? o : 0), yz = z + (g == 2 ? o : 0);
+      real d[3] = {real(0), real(0), real(0)};
+      for (int b = 0; b < 3; ++b) {
+        real cp[3], cm[3];
+        col(at(yx + (b == 0), yy + (b == 1), yz + (b == 2)), b, cp);
+        col(at(yx - (b == 0), yy - (b == 1), yz - (b == 2)), b, cm);
+        for (int a = 0; a < 3; ++a) d[a] += real(0.5) * (cp[a] - cm[a]);
+      }
+      for (int a = 0; a < 3; ++a) dv[g][sg][a] = d[a];
+    }
+  // M_ab = D0_b div_a;  G = c (M + M^T)
+  real M[3][3];
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) M[a][b] = real(0.5) * (dv[b][0][a] - dv[b][1][a]);
+  const real Gxx = c * (M[0][0] + M[0][0]), Gyy = c * (M[1][1] + M[1][1]), Gzz = c * (M[2][2] + M[2][2]);
+  const real tr3 = (Gxx + Gyy + Gzz) * LCBP_Q(1, 3);
+  h.xx += tr3 - Gxx;
+  h.yy += tr3 - Gyy;
+  h.xy -= c * (M[0][1] + M[1][0]);
+  h.xz -= c * (M[0][2] + M[2][0]);
+  h.yz -= c * (M[1][2] + M[2][1]);
 }
 
 }  // namespace lcbp

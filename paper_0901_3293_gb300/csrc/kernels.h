@@ -89,6 +89,7 @@ struct DiagGeom {
   double A0, gamma, K, q0;
   int walls;       // solid walls in z: F_h in bond form with the anchored ghost planes
   double qw[5];    // anchored Q (q5 order)
+  double c_div;    // (K - L2) / 2: F_h gains -c_div |div Q|^2 per site
 };
 template <typename real>
 cudaError_t launch_diag_one(const DiagGeom& g, const void* q, const void* f, int with_f, double threshold,

@@ -17,6 +17,8 @@ struct HostParams {
   int flow_on, coupling;
   int walls_z;              // solid walls below z = 0 and above z = nz-1
   double q_wall[5];         // anchored Q beyond the walls (q5 order)
+  int l2_set;               // 0: one-constant energy (L2 = K); 1: L2 below
+  double L2;
 };
 
 extern thread_local std::string g_last_error;

@@ -80,7 +80,8 @@ __global__ void __launch_bounds__(256) k_field(const Replica<real>* __restrict__
     const Nbr nb = make_nbr(x, y, z, R.nx, R.ny, R.nz, R.walls);
     const Stencil7<real> st = load_stencil(Q + 5 * R.base, n, nb, R);
     Sym5<real> dq[3];
-    const Sym5<real> h = molecular_field(st, R.m, dq);
+    Sym5<real> h = molecular_field(st, R.m, dq);
+    if (R.m.c_div != real(0)) add_div_field(h, Q + 5 * R.base, n, x, y, z, R.nx, R.ny, R.nz, R.m.c_div);
     store5(H + 5 * R.base, n, nb.s, h);
     if (FLOW) {
       Sym5<real> sg;
@@ -264,7 +265,8 @@ __global__ void __launch_bounds__(256) k_lb_correct(const Replica<real>* __restr
     if (DO_Q2) {
       const Stencil7<real> st = load_stencil(Qs + 5 * R.base, n, nb, R);
       Sym5<real> dq[3];
-      const Sym5<real> h = molecular_field(st, R.m, dq);
+      Sym5<real> h = molecular_field(st, R.m, dq);
+      if (R.m.c_div != real(0)) add_div_field(h, Qs + 5 * R.base, n, x, y, z, nx, ny, R.nz, R.m.c_div);
       real u[3] = {real(0), real(0), real(0)};
       real w[3][3] = {};
       if (FLOW) {

@@ -122,6 +122,7 @@ __device__ __forceinline__ Model<V> widen(const Model<real>& m) {
   w.Gamma = V(m.Gamma);
   w.xi = V(m.xi);
   w.inv_tau = V(m.inv_tau);
+  w.c_div = V(m.c_div);
   return w;
 }
 

@@ -66,6 +66,7 @@ _SIGNATURES = {
     "lcbp_defect_fraction": (_c_int, [_P, _c_double, ctypes.POINTER(_c_double)]),
     "lcbp_optics_default": (_c_int, [_P]),
     "lcbp_set_walls": (_c_int, [_P, _c_int, _P]),
+    "lcbp_set_l2": (_c_int, [_P, _c_int, _c_double]),
     "lcbp_texture": (_c_int, [_P, _P, _P]),
     "lcbp_save": (_c_int, [_P, ctypes.c_char_p]),
     "lcbp_load": (_c_int, [_P, ctypes.c_char_p]),
@@ -263,6 +264,11 @@ class Lattice:
         return self
 
     # -- state ----------------------------------------------------------------
+    def set_l2(self, L2: float | None) -> "Lattice":
+        """Energy with -((K - L2)/2)|div Q|^2 added (L2 = 0: exactly as printed); None: one-constant."""
+        check(lib().lcbp_set_l2(self._h, 0 if L2 is None else 1, 0.0 if L2 is None else float(L2)))
+        return self
+
     def set_walls(self, walls: bool = True, q_wall=None) -> "Lattice":
         """Solid walls below z = 0 and above z = Nz-1 (bounce-back, strong anchoring to q_wall, q5 order)."""
         qw = None if q_wall is None else np.ascontiguousarray(np.asarray(q_wall, dtype=np.float64).reshape(5))
