@@ -113,7 +113,10 @@ class TrainLog:
     iters: int = 0
 
 
-S_U, S_R, S_DQ = 1e-3, 1e-3, 1e-3
+# input scales of u and of the rate R, output scale of the correction: chosen so
+# that the inputs R / s_r and the target (dq - 10 R) / s_dq are O(1) on the slab
+# (the BF16 activations then resolve them)
+S_U, S_R, S_DQ = 1e-3, 1e-4, 3e-6
 
 
 def train(samples, iters: int, lr: float = 1e-3, depth: int = 64, seed: int = 0, params=None,
@@ -320,7 +323,12 @@ def main():
     ap.add_argument("--kappa", type=float, default=1.0)
     ap.add_argument("--tol", type=float, default=1e-3)
     ap.add_argument("--train-kappas", type=int, default=6, help="training chiralities, evenly in [0.5, 2]")
+    ap.add_argument("--s-r", type=float, default=None, help="input scale of the rate R")
+    ap.add_argument("--s-dq", type=float, default=None, help="output scale of the correction")
     args = ap.parse_args()
+    global S_R, S_DQ
+    S_R = args.s_r if args.s_r is not None else S_R
+    S_DQ = args.s_dq if args.s_dq is not None else S_DQ
     torch.cuda.set_device(0)
 
     def note(d):
