@@ -53,8 +53,8 @@ STATE_BYTES = (15 + 5) * 2 * 4  # read + write of f and Q once per site-step (FP
 MEASURED_TRAFFIC = {
     "sources": ["paper_0901_3293_gb300/csrc/zmarch.cu", "paper_0901_3293_gb300/csrc/common.cuh",
                 "paper_0901_3293_gb300/csrc/tma.cuh"],
-    "sha256_16": "d002a9f5e6e69351",
-    "bytes_per_site": {"qside": (168265984 + 168874240) / 160 ** 3, "lbq": (843835648 + 361818368) / 160 ** 3},
+    "sha256_16": "eb19e476c9de655a",
+    "bytes_per_site": {"qside": (164382976 + 168876544) / 160 ** 3, "lbq": (843158016 + 362482432) / 160 ** 3},
 }
 ORACLE_SAMPLE = 32  # side of the periodic cube the oracle steps (two BPII unit cells)
 

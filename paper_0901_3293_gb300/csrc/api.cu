@@ -522,6 +522,7 @@ StepArgs step_args(lcbp_lattice* h) {
   a.flow_on = h->p.flow_on;
   a.coupling = h->p.coupling;
   a.walls = h->p.walls_z;
+  a.div = h->p.l2_set && h->p.L2 != h->p.K;
   a.q = h->q;
   a.qs = h->qs;
   a.h = h->h;

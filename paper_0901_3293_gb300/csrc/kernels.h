@@ -20,6 +20,7 @@ struct StepArgs {
   int flow_on;
   int coupling;  // 0 Jacobi, 1 Gauss-Seidel
   int walls;     // some replica has solid walls in z (selects the bounce-back LB build)
+  int div;       // some replica has L2 != K (selects the build with the div Q term of H)
   void* q;       // 5 comps, updated in place
   void* qs;      // 5 comps scratch (Heun predictor)
   void* h;       // 5 comps scratch

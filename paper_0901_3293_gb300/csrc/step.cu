@@ -67,7 +67,8 @@ __device__ __forceinline__ void velocity_gradient(const real* __restrict__ ru, l
 }
 
 // ---------------------------------------------------------------------------
-template <typename real, bool FLOW>
+// DIV: the lattice has L2 != K (the divergence term of H is compiled in only here)
+template <typename real, bool FLOW, bool DIV = false>
 __global__ void __launch_bounds__(256) k_field(const Replica<real>* __restrict__ reps,
                                                const Tile* __restrict__ tiles, int ntiles, TileShape ts,
                                                const real* __restrict__ Q, real* __restrict__ H,
@@ -81,7 +82,7 @@ __global__ void __launch_bounds__(256) k_field(const Replica<real>* __restrict__
     const Stencil7<real> st = load_stencil(Q + 5 * R.base, n, nb, R);
     Sym5<real> dq[3];
     Sym5<real> h = molecular_field(st, R.m, dq);
-    if (R.m.c_div != real(0)) add_div_field(h, Q + 5 * R.base, n, x, y, z, R.nx, R.ny, R.nz, R.m.c_div);
+    if (DIV) add_div_field(h, Q + 5 * R.base, n, x, y, z, R.nx, R.ny, R.nz, R.m.c_div);
     store5(H + 5 * R.base, n, nb.s, h);
     if (FLOW) {
       Sym5<real> sg;
@@ -166,7 +167,7 @@ __global__ void __launch_bounds__(256) k_force_predict(const Replica<real>* __re
 // DO_LB: predictor-corrector LB (pull form) writing f^{n+1} and its moments.
 // DO_Q2: Heun corrector for Q with u from `rhou_q` (u^n for Jacobi coupling,
 //        u^{n+1} for Gauss-Seidel), in place on Q.
-template <typename real, bool FLOW, bool DO_LB, bool DO_Q2, bool WALLS = false>
+template <typename real, bool FLOW, bool DO_LB, bool DO_Q2, bool WALLS = false, bool DIV = false>
 __global__ void __launch_bounds__(256) k_lb_correct(const Replica<real>* __restrict__ reps,
                                                     const Tile* __restrict__ tiles, int ntiles, TileShape ts,
                                                     const real* __restrict__ f, const real* __restrict__ rhou,
@@ -266,7 +267,7 @@ __global__ void __launch_bounds__(256) k_lb_correct(const Replica<real>* __restr
       const Stencil7<real> st = load_stencil(Qs + 5 * R.base, n, nb, R);
       Sym5<real> dq[3];
       Sym5<real> h = molecular_field(st, R.m, dq);
-      if (R.m.c_div != real(0)) add_div_field(h, Qs + 5 * R.base, n, x, y, z, nx, ny, R.nz, R.m.c_div);
+      if (DIV) add_div_field(h, Qs + 5 * R.base, n, x, y, z, nx, ny, R.nz, R.m.c_div);
       real u[3] = {real(0), real(0), real(0)};
       real w[3][3] = {};
       if (FLOW) {
@@ -288,6 +289,24 @@ __global__ void __launch_bounds__(256) k_lb_correct(const Replica<real>* __restr
 // ---------------------------------------------------------------------------
 // host launchers
 // ---------------------------------------------------------------------------
+// the field and corrector kernels in the build with or without the divergence
+// term of H (L2 != K); walls and L2 never come together
+template <typename real, bool FLOW, typename... Args>
+void launch_fld(bool div, int grid, int threads, cudaStream_t s, Args... args) {
+  if (div) k_field<real, FLOW, true><<<grid, threads, 0, s>>>(args...);
+  else k_field<real, FLOW, false><<<grid, threads, 0, s>>>(args...);
+}
+template <typename real, bool FLOW, bool DO_LB, bool DO_Q2, bool WALLS, typename... Args>
+void launch_lbc(bool div, int grid, int threads, cudaStream_t s, Args... args) {
+  if constexpr (!WALLS && DO_Q2) {
+    if (div) {
+      k_lb_correct<real, FLOW, DO_LB, DO_Q2, false, true><<<grid, threads, 0, s>>>(args...);
+      return;
+    }
+  }
+  k_lb_correct<real, FLOW, DO_LB, DO_Q2, WALLS, false><<<grid, threads, 0, s>>>(args...);
+}
+
 template <typename real>
 cudaError_t launch_step(const StepArgs& a, cudaStream_t s) {
   const auto* reps = static_cast<const Replica<real>*>(a.reps);
@@ -304,7 +323,8 @@ cudaError_t launch_step(const StepArgs& a, cudaStream_t s) {
   };
   mark();
   if (a.flow_on) {
-    k_field<real, true><<<grid, threads, 0, s>>>(reps, a.tiles, a.ntiles, a.ts, Cp(a.q), Rp(a.h), Rp(a.sigma), Rp(a.tau));
+    launch_fld<real, true>(a.div, grid, threads, s, reps, a.tiles, a.ntiles, a.ts, Cp(a.q), Rp(a.h), Rp(a.sigma),
+                           Rp(a.tau));
     mark();
     if (a.coupling == 0) {
       if (a.bext)
@@ -315,13 +335,13 @@ cudaError_t launch_step(const StepArgs& a, cudaStream_t s) {
             reps, a.tiles, a.ntiles, a.ts, Cp(a.q), Cp(a.h), Cp(a.tau), Cp(a.rhou), nullptr, Rp(a.b), Rp(a.qs));
       mark();
       if (a.walls)
-        k_lb_correct<real, true, true, true, true><<<grid, threads, 0, s>>>(
-            reps, a.tiles, a.ntiles, a.ts, Cp(a.f), Cp(a.rhou), Cp(a.sigma), Cp(a.b), Rp(a.fnew), Rp(a.rhou_new),
-            Cp(a.qs), Cp(a.rhou), Cp(a.q), Rp(qout));
+        launch_lbc<real, true, true, true, true>(a.div, grid, threads, s, reps, a.tiles, a.ntiles, a.ts, Cp(a.f),
+                                                 Cp(a.rhou), Cp(a.sigma), Cp(a.b), Rp(a.fnew), Rp(a.rhou_new),
+                                                 Cp(a.qs), Cp(a.rhou), Cp(a.q), Rp(qout));
       else
-        k_lb_correct<real, true, true, true><<<grid, threads, 0, s>>>(
-            reps, a.tiles, a.ntiles, a.ts, Cp(a.f), Cp(a.rhou), Cp(a.sigma), Cp(a.b), Rp(a.fnew), Rp(a.rhou_new),
-            Cp(a.qs), Cp(a.rhou), Cp(a.q), Rp(qout));
+        launch_lbc<real, true, true, true, false>(a.div, grid, threads, s, reps, a.tiles, a.ntiles, a.ts, Cp(a.f),
+                                                  Cp(a.rhou), Cp(a.sigma), Cp(a.b), Rp(a.fnew), Rp(a.rhou_new),
+                                                  Cp(a.qs), Cp(a.rhou), Cp(a.q), Rp(qout));
       mark();
     } else {
       // Gauss-Seidel: b, LB, then the Heun stages with u^{n+1}
@@ -344,20 +364,23 @@ cudaError_t launch_step(const StepArgs& a, cudaStream_t s) {
       k_force_predict<real, true, false, true, false><<<grid, threads, 0, s>>>(
           reps, a.tiles, a.ntiles, a.ts, Cp(a.q), Cp(a.h), nullptr, Cp(a.rhou_new), nullptr, nullptr, Rp(a.qs));
       mark();
-      k_lb_correct<real, true, false, true><<<grid, threads, 0, s>>>(
-          reps, a.tiles, a.ntiles, a.ts, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, Cp(a.qs),
-          Cp(a.rhou_new), Cp(a.q), Rp(qout));
+      launch_lbc<real, true, false, true, false>(a.div, grid, threads, s, reps, a.tiles, a.ntiles, a.ts,
+                                                 (const real*)nullptr, (const real*)nullptr, (const real*)nullptr,
+                                                 (const real*)nullptr, (real*)nullptr, (real*)nullptr, Cp(a.qs),
+                                                 Cp(a.rhou_new), Cp(a.q), Rp(qout));
       mark();
     }
   } else {
-    k_field<real, false><<<grid, threads, 0, s>>>(reps, a.tiles, a.ntiles, a.ts, Cp(a.q), Rp(a.h), nullptr, nullptr);
+    launch_fld<real, false>(a.div, grid, threads, s, reps, a.tiles, a.ntiles, a.ts, Cp(a.q), Rp(a.h), (real*)nullptr,
+                            (real*)nullptr);
     mark();
     k_force_predict<real, false, false, true, false><<<grid, threads, 0, s>>>(
         reps, a.tiles, a.ntiles, a.ts, Cp(a.q), Cp(a.h), nullptr, nullptr, nullptr, nullptr, Rp(a.qs));
     mark();
-    k_lb_correct<real, false, false, true><<<grid, threads, 0, s>>>(
-        reps, a.tiles, a.ntiles, a.ts, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, Cp(a.qs), nullptr,
-        Cp(a.q), Rp(qout));
+    launch_lbc<real, false, false, true, false>(a.div, grid, threads, s, reps, a.tiles, a.ntiles, a.ts,
+                                                (const real*)nullptr, (const real*)nullptr, (const real*)nullptr,
+                                                (const real*)nullptr, (real*)nullptr, (real*)nullptr, Cp(a.qs),
+                                                (const real*)nullptr, Cp(a.q), Rp(qout));
     mark();
   }
   return cudaGetLastError();
@@ -371,9 +394,8 @@ template <typename real>
 cudaError_t launch_field(const StepArgs& a, cudaStream_t s) {
   const auto* reps = static_cast<const Replica<real>*>(a.reps);
   const int threads = a.ts.tx * a.ts.ty * a.ts.tz;
-  k_field<real, true><<<a.ntiles, threads, 0, s>>>(reps, a.tiles, a.ntiles, a.ts, static_cast<const real*>(a.q),
-                                                   static_cast<real*>(a.h), static_cast<real*>(a.sigma),
-                                                   static_cast<real*>(a.tau));
+  launch_fld<real, true>(a.div, a.ntiles, threads, s, reps, a.tiles, a.ntiles, a.ts, static_cast<const real*>(a.q),
+                         static_cast<real*>(a.h), static_cast<real*>(a.sigma), static_cast<real*>(a.tau));
   return cudaGetLastError();
 }
 template cudaError_t launch_field<float>(const StepArgs&, cudaStream_t);
@@ -404,13 +426,13 @@ cudaError_t launch_rate(const StepArgs& a, cudaStream_t s) {
   auto Rp = [](void* p) { return static_cast<real*>(p); };
   auto Cp = [](const void* p) { return static_cast<const real*>(p); };
   if (a.flow_on) {
-    k_field<real, true><<<a.ntiles, threads, 0, s>>>(reps, a.tiles, a.ntiles, a.ts, Cp(a.q), Rp(a.h), Rp(a.sigma),
-                                                      Rp(a.tau));
+    launch_fld<real, true>(a.div, a.ntiles, threads, s, reps, a.tiles, a.ntiles, a.ts, Cp(a.q), Rp(a.h),
+                           Rp(a.sigma), Rp(a.tau));
     k_force_predict<real, true, false, true, false><<<a.ntiles, threads, 0, s>>>(
         reps, a.tiles, a.ntiles, a.ts, Cp(a.q), Cp(a.h), nullptr, Cp(a.rhou), nullptr, nullptr, Rp(a.qs));
   } else {
-    k_field<real, false><<<a.ntiles, threads, 0, s>>>(reps, a.tiles, a.ntiles, a.ts, Cp(a.q), Rp(a.h), nullptr,
-                                                       nullptr);
+    launch_fld<real, false>(a.div, a.ntiles, threads, s, reps, a.tiles, a.ntiles, a.ts, Cp(a.q), Rp(a.h),
+                            (real*)nullptr, (real*)nullptr);
     k_force_predict<real, false, false, true, false><<<a.ntiles, threads, 0, s>>>(
         reps, a.tiles, a.ntiles, a.ts, Cp(a.q), Cp(a.h), nullptr, nullptr, nullptr, nullptr, Rp(a.qs));
   }
