@@ -349,7 +349,8 @@ def run_ours(args):
     tex_ms = 1e3 * (time.perf_counter() - t0) / 20
     tex_line = {"ms_per_image": tex_ms, "sites": 64 * 64 * 256,
                 "GBps_of_Q": 64 * 64 * 256 * 5 * 4 / (tex_ms * 1e-3) / 1e9,
-                "note": "host-timed lcbp_texture including the 16 KB image copy; reads Q (20 B/site) once"}
+                "note": "host-timed lcbp_texture (the column-product kernel, split over z into 3 ranges for "
+                        "this 64 x 64 image, the combine kernel and the 16 KB image copy); reads Q (20 B/site) once"}
     tex_lat.close()
 
     # ---- the 48-replica sweep (32^3 / 48^3, per-replica kappa and tau) in one batch

@@ -1058,9 +1058,12 @@ int lcbp_texture(lcbp_lattice* h, const lcbp_optics* o, float* img) {
   for (int l = 0; l < o->nlambda; ++l)
     if (!(o->lambda[l] > 0)) return fail(LCBP_EINVAL, "wavelength %d must be > 0", l);
   // the H scratch (5 N elements) is free between steps and holds the image
+  // and the per-split column products
   float* d_img = static_cast<float*>(h->h);
-  cudaError_t e = h->dtype == LCBP_F64 ? launch_texture<double>(h->q, h->nx, h->ny, h->nz, *o, d_img, h->stream)
-                                       : launch_texture<float>(h->q, h->nx, h->ny, h->nz, *o, d_img, h->stream);
+  const long long scratch = 5LL * h->n * dtype_size(h->dtype) / (long long)sizeof(float);
+  cudaError_t e = h->dtype == LCBP_F64
+                      ? launch_texture<double>(h->q, h->nx, h->ny, h->nz, *o, d_img, scratch, h->stream)
+                      : launch_texture<float>(h->q, h->nx, h->ny, h->nz, *o, d_img, scratch, h->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(img, d_img, sizeof(float) * (size_t)h->nx * h->ny, cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);

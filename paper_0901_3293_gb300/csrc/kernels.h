@@ -124,9 +124,10 @@ constexpr int kZmBoxX = 40;  // elements per TMA box row
 template <typename real>
 int zm_tile_rows();
 // polarised texture of a Q field into a device image [ny][nx] (optics.cu)
+// d_img: nx * ny image followed by scratch; scratch_floats counts both
 template <typename real>
 cudaError_t launch_texture(const void* q, int nx, int ny, int nz, const lcbp_optics& o, float* d_img,
-                           cudaStream_t s);
+                           long long scratch_floats, cudaStream_t s);
 
 template <typename real>
 int zm_spt_max();

@@ -10,9 +10,12 @@
 // T = B(Nz-1) ... B(0), taken per wavelength.
 //
 // Layout of the work: a CTA covers 32 consecutive x of one row y (lanes, so
-// the Q loads coalesce) and splits z into kTexChunks chunks, one warp each;
-// every thread multiplies the blocks of its chunk, and the chunk products are
-// combined in order through shared memory.  cos 2 beta and sin 2 beta come
+// the Q loads coalesce) and splits its planes into kTexChunks chunks, one warp
+// each; every thread multiplies the blocks of its chunk, and the chunk
+// products are combined in order through shared memory.  Where the image has
+// too few 32-column rows to fill the GPU, the planes of a column are first
+// split into S ranges taken by different CTAs, and a second kernel multiplies
+// the S range products in order.  cos 2 beta and sin 2 beta come
 // from d_x, d_y directly: (d_y^2 - d_x^2, 2 d_x d_y) / (d_x^2 + d_y^2).
 #include "../../include/lcbp.h"
 #include "common.cuh"
@@ -97,22 +100,39 @@ __device__ __forceinline__ void apply_plane(float P[9], float cb, float sb, floa
   for (int k = 0; k < 9; ++k) P[k] = R[k];
 }
 
+// S_out[0] of one column from the product T of its planes' blocks, summed over
+// the wavelengths with their weights: T acts on the polarised input
+// (S_1, S_2, S_3) = (c_in, s_in, 0) / 2 and the analyser reads the result.
+__device__ __forceinline__ float analyse(const OpticsArgs& a, int l, const float T[9]) {
+  const float v0 = 0.5f * a.c_in, v1 = 0.5f * a.s_in;
+  const float r0 = T[0] * v0 + T[1] * v1, r1 = T[3] * v0 + T[4] * v1;
+  return a.weight[l] * 0.5f * (0.5f + a.c_out * r0 + a.s_out * r1);
+}
+
+// One work unit: 32 columns x of row y, planes [z_begin, z_end) of split sp of
+// S; the 8 warps take consecutive sub-chunks and their products are combined
+// in order by a tree in shared memory.  With S = 1 the unit writes the image;
+// otherwise it writes its 3x3 products to part[((sp * nl + l) * 9 + k) * nx * ny + pixel].
 template <typename real>
-__global__ void __launch_bounds__(32 * kTexChunks) k_texture(const real* __restrict__ Q, OpticsArgs a,
-                                                             float* __restrict__ img) {
-  __shared__ float part[kTexChunks][kTexMaxLambda][9][32];
+__global__ void __launch_bounds__(32 * kTexChunks) k_texture(const real* __restrict__ Q, OpticsArgs a, int S,
+                                                             float* __restrict__ img, float* __restrict__ part) {
+  __shared__ float sp_part[kTexChunks][kTexMaxLambda][9][32];
   const int lane = threadIdx.x % 32, w = threadIdx.x / 32;
   const int tiles_x = (a.nx + 31) / 32;
-  const int chunk = (a.nz + kTexChunks - 1) / kTexChunks;
-  for (int t = blockIdx.x; t < tiles_x * a.ny; t += gridDim.x) {
+  const int items = tiles_x * a.ny;
+  const long long pix = (long long)a.nx * a.ny;
+  for (int u = blockIdx.x; u < items * S; u += gridDim.x) {
+    const int t = u % items, sp = u / items;
     const int x = (t % tiles_x) * 32 + lane, y = t / tiles_x;
     const bool valid = x < a.nx;
+    const int zb = (int)((long long)sp * a.nz / S), ze = (int)((long long)(sp + 1) * a.nz / S);
+    const int chunk = (ze - zb + kTexChunks - 1) / kTexChunks;
     float P[kTexMaxLambda][9];
 #pragma unroll
     for (int l = 0; l < kTexMaxLambda; ++l)
 #pragma unroll
       for (int k = 0; k < 9; ++k) P[l][k] = (k % 4 == 0) ? 1.f : 0.f;
-    const int z_lo = w * chunk, z_hi = min(a.nz, z_lo + chunk);
+    const int z_lo = zb + w * chunk, z_hi = min(ze, z_lo + chunk);
     for (int z = z_lo; valid && z < z_hi; ++z) {
       const long long s = ((long long)z * a.ny + y) * a.nx + x;
       const float xx = (float)Q[s], xy = (float)Q[a.n + s], xz = (float)Q[2 * a.n + s];
@@ -142,34 +162,86 @@ __global__ void __launch_bounds__(32 * kTexChunks) k_texture(const real* __restr
 #pragma unroll
     for (int l = 0; l < kTexMaxLambda; ++l)
 #pragma unroll
-      for (int k = 0; k < 9; ++k) part[w][l][k][lane] = P[l][k];
+      for (int k = 0; k < 9; ++k) sp_part[w][l][k][lane] = P[l][k];
     __syncthreads();
-    if (w == 0 && valid) {
-      float out = 0.f;
-      for (int l = 0; l < a.nl; ++l) {
-        // T = P_{C-1} ... P_0 applied to the polarised input (S_1, S_2, S_3) = (c_in, s_in, 0) / 2
-        float v[3] = {0.5f * a.c_in, 0.5f * a.s_in, 0.f};
-        for (int c = 0; c < kTexChunks; ++c) {
-          float r[3];
+    // tree: warp w takes the product of chunks w + st (later) and w (earlier)
+    for (int st = 1; st < kTexChunks; st *= 2) {
+      if (w % (2 * st) == 0) {
+        for (int l = 0; l < a.nl; ++l) {
+          float R[9];
 #pragma unroll
           for (int i = 0; i < 3; ++i)
-            r[i] = part[c][l][3 * i][lane] * v[0] + part[c][l][3 * i + 1][lane] * v[1] +
-                   part[c][l][3 * i + 2][lane] * v[2];
-          v[0] = r[0];
-          v[1] = r[1];
-          v[2] = r[2];
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+              R[3 * i + j] = sp_part[w + st][l][3 * i][lane] * sp_part[w][l][j][lane] +
+                             sp_part[w + st][l][3 * i + 1][lane] * sp_part[w][l][3 + j][lane] +
+                             sp_part[w + st][l][3 * i + 2][lane] * sp_part[w][l][6 + j][lane];
+#pragma unroll
+          for (int k = 0; k < 9; ++k) sp_part[w][l][k][lane] = R[k];
         }
-        out += a.weight[l] * 0.5f * (0.5f + a.c_out * v[0] + a.s_out * v[1]);
       }
-      img[(long long)y * a.nx + x] = out;
+      __syncthreads();
+    }
+    if (w == 0 && valid) {
+      const long long px = (long long)y * a.nx + x;
+      if (S == 1) {
+        float out = 0.f;
+        for (int l = 0; l < a.nl; ++l) {
+          float T[9];
+#pragma unroll
+          for (int k = 0; k < 9; ++k) T[k] = sp_part[0][l][k][lane];
+          out += analyse(a, l, T);
+        }
+        img[px] = out;
+      } else {
+        for (int l = 0; l < a.nl; ++l)
+#pragma unroll
+          for (int k = 0; k < 9; ++k) part[((long long)(sp * a.nl + l) * 9 + k) * pix + px] = sp_part[0][l][k][lane];
+      }
     }
     __syncthreads();
   }
 }
 
+// image from S split products per column: T = T_{S-1} ... T_0 per wavelength
+__global__ void k_texture_combine(OpticsArgs a, int S, const float* __restrict__ part, float* __restrict__ img) {
+  const long long pix = (long long)a.nx * a.ny;
+  for (long long px = blockIdx.x * (long long)blockDim.x + threadIdx.x; px < pix; px += (long long)gridDim.x * blockDim.x) {
+    float out = 0.f;
+    for (int l = 0; l < a.nl; ++l) {
+      float T[9] = {1.f, 0.f, 0.f, 0.f, 1.f, 0.f, 0.f, 0.f, 1.f};
+      for (int sp = 0; sp < S; ++sp) {
+        const float* M = part + (long long)(sp * a.nl + l) * 9 * pix + px;
+        float R[9];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+          for (int j = 0; j < 3; ++j)
+            R[3 * i + j] = M[(3 * i) * pix] * T[j] + M[(3 * i + 1) * pix] * T[3 + j] + M[(3 * i + 2) * pix] * T[6 + j];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) T[k] = R[k];
+      }
+      out += analyse(a, l, T);
+    }
+    img[px] = out;
+  }
+}
+
+// Splits of z per column: enough work units for about two per SM, each warp
+// keeping at least 4 planes, and the split products fitting in `scratch_floats`
+// after the image.
+int texture_splits(int nx, int ny, int nz, int nl, long long scratch_floats, int sms) {
+  const long long items = (long long)((nx + 31) / 32) * ny;
+  const long long pix = (long long)nx * ny, pix_r = (pix + 63) / 64 * 64;
+  long long S = (2LL * sms + items - 1) / items;
+  S = std::min<long long>(S, std::max(1, nz / (4 * kTexChunks)));
+  S = std::min<long long>(S, std::max<long long>(1, (scratch_floats - pix_r) / (9LL * nl * pix)));
+  return (int)std::max<long long>(1, S);
+}
+
 template <typename real>
 cudaError_t launch_texture(const void* q, int nx, int ny, int nz, const lcbp_optics& o, float* d_img,
-                           cudaStream_t s) {
+                           long long scratch_floats, cudaStream_t s) {
   OpticsArgs a{};
   a.nx = nx;
   a.ny = ny;
@@ -186,14 +258,26 @@ cudaError_t launch_texture(const void* q, int nx, int ny, int nz, const lcbp_opt
   a.s_in = (float)std::sin(2.0 * o.phi_in);
   a.c_out = (float)std::cos(2.0 * o.phi_out);
   a.s_out = (float)std::sin(2.0 * o.phi_out);
-  const int tiles = ((nx + 31) / 32) * ny;
-  const int grid = tiles < 65535 ? tiles : 65535;
-  k_texture<real><<<grid, 32 * kTexChunks, 0, s>>>(static_cast<const real*>(q), a, d_img);
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const long long pix = (long long)nx * ny;
+  const int S = texture_splits(nx, ny, nz, a.nl, scratch_floats, sms);
+  float* part = d_img + ((pix + 63) / 64) * 64;  // split products after the image (256-byte aligned)
+  const long long units = (long long)((nx + 31) / 32) * ny * S;
+  const int grid = (int)std::min<long long>(units, 65535);
+  k_texture<real><<<grid, 32 * kTexChunks, 0, s>>>(static_cast<const real*>(q), a, S, d_img, part);
+  if (S > 1) {
+    const int g2 = (int)std::min<long long>((pix + 255) / 256, 65535);
+    k_texture_combine<<<g2, 256, 0, s>>>(a, S, part, d_img);
+  }
   return cudaGetLastError();
 }
 
-template cudaError_t launch_texture<float>(const void*, int, int, int, const lcbp_optics&, float*, cudaStream_t);
-template cudaError_t launch_texture<double>(const void*, int, int, int, const lcbp_optics&, float*, cudaStream_t);
+template cudaError_t launch_texture<float>(const void*, int, int, int, const lcbp_optics&, float*, long long,
+                                           cudaStream_t);
+template cudaError_t launch_texture<double>(const void*, int, int, int, const lcbp_optics&, float*, long long,
+                                            cudaStream_t);
 
 }  // namespace lcbp
 

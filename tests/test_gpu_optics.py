@@ -33,8 +33,10 @@ def nematic_field(shape, seed, S=0.4):
     return lbq.q9_to_q5(Q9)
 
 
-# (nz, ny, nx): ragged x tiles, z not a multiple of the 8 chunks, fewer planes than chunks
-SHAPES = [(12, 5, 40), (3, 4, 7), (33, 2, 32), (1, 3, 70)]
+# (nz, ny, nx): ragged x tiles, z not a multiple of the 8 chunks, fewer planes than
+# chunks; the last two have so few columns that each column's planes are split
+# between several CTAs (4 and 3 ranges) and the range products combined after
+SHAPES = [(12, 5, 40), (3, 4, 7), (33, 2, 32), (1, 3, 70), (128, 4, 8), (100, 3, 40)]
 
 
 @pytest.mark.parametrize("dtype,tol", [("f32", 2e-5), ("f64", 2e-5)])
