@@ -424,6 +424,33 @@ std::string tune_key(const lcbp_lattice* h) {
   return k;
 }
 
+// Planes-per-CTA candidates: the powers of two, and the values that make the
+// grid (column tiles x z-chunks) fill a whole number of waves of resident CTAs
+// or fall just short of one, for 1 to 48 waves.  All lie in [4, 64] (or are nz).
+std::vector<int> zc_candidates(const lcbp_lattice* h, int spt) {
+  std::vector<int> c;
+  for (int zc : {4, 8, 16, 32, 64})
+    if (zc <= h->nz) c.push_back(zc);
+  if (h->nz < 64) c.push_back(h->nz);
+  int dev = 0, sms = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int ty = h->dtype == LCBP_F64 ? zm_tile_rows<double>() : zm_tile_rows<float>();
+  const long long tiles_xy = (long long)((h->nx + 31) / 32) * ((h->ny + ty - 1) / ty);
+  const long long resident = (long long)sms * (h->dtype == LCBP_F64 ? zm_resident<double>(spt) : zm_resident<float>(spt));
+  for (int w = 1; w <= 48; ++w) {
+    const long long want = w * resident;
+    for (long long chunks : {want / tiles_xy, (want + tiles_xy - 1) / tiles_xy}) {
+      if (chunks < 1) continue;
+      const long long zc = (h->nz + chunks - 1) / chunks;
+      if (zc >= 4 && zc <= 64) c.push_back((int)zc);
+    }
+  }
+  std::sort(c.begin(), c.end());
+  c.erase(std::unique(c.begin(), c.end()), c.end());
+  return c;
+}
+
 int tune_zc(lcbp_lattice* h) {
   std::lock_guard<std::mutex> lk(g_tune_mu);
   const char* path = std::getenv("LCBP_AUTOTUNE_CACHE");
@@ -458,10 +485,9 @@ int tune_zc(lcbp_lattice* h) {
   float best = 1e30f;
   int best_zc = std::min(h->nz, 32), best_spt = spt_lo;
   for (int spt = spt_lo; spt <= spt_hi; ++spt) {
-    for (int zc : {4, 8, 16, 32, 64}) {
-      if (zc > h->nz && zc != 4) break;
+    for (int zc : zc_candidates(h, spt)) {
       ZmArgs a = zm_args(h, mb.bytes);
-      a.zc = std::min(zc, h->nz);
+      a.zc = zc;
       a.spt = spt;
       a.qout = h->h;  // scratch
       float t = 1e30f;

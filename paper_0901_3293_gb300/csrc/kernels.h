@@ -132,6 +132,8 @@ cudaError_t launch_texture(const void* q, int nx, int ny, int nz, const lcbp_opt
 template <typename real>
 int zm_spt_max();
 template <typename real>
+int zm_resident(int spt);  // k_lbq CTAs resident per SM
+template <typename real>
 cudaError_t zm_prepare();
 template <typename real>
 cudaError_t launch_step_zm(const ZmArgs& a, cudaStream_t s);

@@ -694,6 +694,24 @@ int zm_spt_max() {
   return zm_max_spt<real>();
 }
 
+// CTAs of k_lbq (the longer kernel) resident per SM at `spt` sites per thread
+template <typename real, int SPT>
+int zm_resident_spt() {
+  constexpr int TY = zm_ty<real>();
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_lbq<real, TY, SPT>, ZM_TX * TY / SPT,
+                                                    LbqSmem<real, TY>::bytes) != cudaSuccess)
+    n = 1;
+  return n > 0 ? n : 1;
+}
+
+template <typename real>
+int zm_resident(int spt) {
+  if constexpr (zm_max_spt<real>() == 2)
+    if (spt == 2) return zm_resident_spt<real, 2>();
+  return zm_resident_spt<real, 1>();
+}
+
 ZmGeom zm_geom(int nx, int ny, int nz, int zc, int ty) {
   ZmGeom G;
   G.nx = nx;
@@ -741,6 +759,8 @@ template int zm_tile_rows<float>();
 template int zm_tile_rows<double>();
 template int zm_spt_max<float>();
 template int zm_spt_max<double>();
+template int zm_resident<float>(int);
+template int zm_resident<double>(int);
 template cudaError_t launch_step_zm<float>(const ZmArgs&, cudaStream_t);
 template cudaError_t launch_step_zm<double>(const ZmArgs&, cudaStream_t);
 
