@@ -375,11 +375,15 @@ def run_ours(args):
     batch.synchronize()
     b_s = time.perf_counter() - t0
     binfo = batch.info()
+    bfast, bzc = batch.path()
     batch_line = {"replicas": 48, "sites": bsites, "ms_per_step": 1e3 * b_s / args.steps,
-                  "MLUPS": bsites * args.steps / b_s / 1e6, "tile": binfo["tile"],
-                  "persistent_ctas": binfo["persistent_ctas"],
-                  "note": "generic kernels over one tile list spanning all replicas, graph replay; "
-                          "host-timed around lcbp_batch_step + synchronize"}
+                  "MLUPS": bsites * args.steps / b_s / 1e6,
+                  "kernels": "fast (z-marching TMA kernels, 5-D maps per class)" if bfast else "generic",
+                  "planes_per_cta": bzc if bfast else None,
+                  "tile": None if bfast else binfo["tile"],
+                  "persistent_ctas": None if bfast else binfo["persistent_ctas"],
+                  "note": "kernel set chosen by timing both on the batch; one launch per kernel over all "
+                          "replicas, graph replay; host-timed around lcbp_batch_step + synchronize"}
     batch.close()
 
     if rank != 0:

@@ -358,12 +358,21 @@ LCBP_API int lcbp_load(lcbp_lattice *h, const char *path);
  * Batched replicas (parameter sweeps): R independent periodic lattices of
  * uneven sizes, each with its own Landau-de Gennes and kinetic parameters,
  * advanced together.  Their fields are concatenated structure-of-arrays
- * blocks on one device; every kernel of a step is one launch of persistent
- * CTAs walking a single tile work-list that spans all replicas, and nsteps
- * are replayed from a captured CUDA graph.  The tile shape is picked by
- * timing candidate shapes on the batch (first lcbp_batch_step), writing
- * scratch buffers only.  Each replica computes exactly what a lattice of its
- * own (generic path) computes.
+ * blocks on one device, replicas of equal dims (a class) back to back.
+ * Every kernel of a step is one launch over all replicas, and nsteps are
+ * replayed from a captured CUDA graph.  Two kernel sets:
+ *   fast (open when flow is on, coupling is Jacobi, every class has
+ *     nx % 4 == 0 and there are at most 4 classes): the two z-marching TMA
+ *     kernels of the single-lattice fast path, each field of a class read as
+ *     one 5-D tensor; the planes per CTA are picked by timing candidates;
+ *   generic: persistent CTAs walking one tile work-list that spans all
+ *     replicas; the tile shape is picked by timing candidate shapes.
+ * LCBP_PATH_AUTO (default) tunes both where the fast set is open and runs
+ * the faster; LCBP_PATH_FAST1 runs the fast set wherever it is open;
+ * LCBP_PATH_GENERIC always the generic set.  Tuning happens at the first
+ * lcbp_batch_step after creation or a path change and writes scratch
+ * buffers only.  Each replica computes exactly what a lattice of its own
+ * computes with the same kernel set (one site per thread on the fast set).
  * ------------------------------------------------------------------------ */
 typedef struct lcbp_batch lcbp_batch;
 
@@ -397,7 +406,17 @@ LCBP_API int lcbp_batch_read_u(lcbp_batch *b, int r, void *dst, int dtype);
 LCBP_API int lcbp_batch_free_energy(lcbp_batch *b, int r, double *F);
 LCBP_API int lcbp_batch_totals(lcbp_batch *b, int r, double *mass, double momentum[3]);
 LCBP_API int lcbp_batch_defect_fraction(lcbp_batch *b, int r, double threshold, double *fraction);
-/* R, total sites, tuned tile shape (tx, ty, tz), persistent CTAs per launch, steps done. */
+/*
+ * Kernel selection for the batch: LCBP_PATH_AUTO (default), LCBP_PATH_FAST1
+ * or LCBP_PATH_GENERIC (see above).  Waits for the batch's stream, drops its
+ * graph; the next lcbp_batch_step retunes.  Errors: LCBP_EINVAL (other paths).
+ */
+LCBP_API int lcbp_batch_set_path(lcbp_batch *b, int path);
+/* *fast = 1 if steps run the fast kernels; *planes_per_cta = their tuned
+ * z-chunk (0 before the first step or on the generic path).  Either may be NULL. */
+LCBP_API int lcbp_batch_get_path(lcbp_batch *b, int *fast, int *planes_per_cta);
+/* R, total sites, tuned tile shape (tx, ty, tz) and persistent CTAs per launch
+ * of the generic path, steps done. */
 LCBP_API int lcbp_batch_get_info(lcbp_batch *b, int *R, long long *total_sites, int tile[3], int *persistent_ctas,
                                  long long *step);
 

@@ -138,6 +138,33 @@ int transfer(void* state, int sd, void* user, int ud, long long count, bool uplo
   return LCBP_OK;
 }
 
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no libcuda
+// link): a tiled map with unit element strides, no swizzle or interleave,
+// 128-byte L2 promotion and zero fill.  strides: rank - 1 byte strides.
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+bool encode_tiled(CUtensorMap* tm, void* base, int rank, const cuuint64_t* dims, const cuuint64_t* strides,
+                  const cuuint32_t* box, int dtype) {
+  static EncodeTiledFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  });
+  if (!fn || rank < 1 || rank > 5) return false;
+  const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+  return fn(tm, dtype == LCBP_F64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, rank, base,
+            dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 }  // namespace lcbp
 
 // ---------------------------------------------------------------------------
@@ -303,36 +330,13 @@ lcbp_lattice* new_handle(int nx, int ny, int nz, int dtype) {
 }
 
 // ---- fast path: tensor maps, eligibility, autotuned z-chunk -------------------
-typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-EncodeTiledFn encode_fn() {
-  static EncodeTiledFn fn = nullptr;
-  static std::once_flag once;
-  std::call_once(once, [] {
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-            cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<EncodeTiledFn>(p);
-  });
-  return fn;
-}
-
 // field [comps][nz][ny][nx] as a 4-D tensor, box = 40 x rows x 1 x comps
 bool make_field_tmap(CUtensorMap* tm, void* base, int comps, int nx, int ny, int nz, int rows, int dtype) {
-  EncodeTiledFn fn = encode_fn();
-  if (!fn) return false;
   const cuuint64_t es = dtype_size(dtype);
   const cuuint64_t dims[4] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz, (cuuint64_t)comps};
   const cuuint64_t strides[3] = {nx * es, (cuuint64_t)nx * ny * es, (cuuint64_t)nx * ny * nz * es};
   const cuuint32_t box[4] = {(cuuint32_t)kZmBoxX, (cuuint32_t)rows, 1, (cuuint32_t)comps};
-  const cuuint32_t estr[4] = {1, 1, 1, 1};
-  return fn(tm, dtype == LCBP_F64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base,
-            dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+  return encode_tiled(tm, base, 4, dims, strides, box, dtype);
 }
 
 bool fast_shape_ok(const lcbp_lattice* h) { return h->nx % 4 == 0; }

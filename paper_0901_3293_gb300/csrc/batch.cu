@@ -1,13 +1,21 @@
 // Batched replicas: R lattices of uneven sizes and per-replica parameters
 // stepped together.  Fields are concatenated structure-of-arrays blocks
 // (replica r of a C-component field at field + C * base_r, laid out
-// [c][z][y][x]); one tile work-list spans every replica, so each kernel of a
-// step is a single launch of persistent CTAs over all replicas, and nsteps
-// are replayed from a captured CUDA graph.  The tile shape is chosen by
-// timing candidate shapes on the batch itself (scratch outputs only).
+// [c][z][y][x]); replicas of equal dims (a class) are stored back to back.
+//
+// Two step paths, both one launch per kernel over every replica and replayed
+// from a captured CUDA graph:
+// * fast (flow on, Jacobi coupling, every class with nx % 4 = 0, at most
+//   kZmMaxClasses classes): the z-marching TMA kernels, each field of a class
+//   read as one 5-D tensor (x, y, z, component, replica); the planes per CTA
+//   are chosen by timing candidates on the batch (scratch outputs only);
+// * generic: one tile work-list spans every replica and the one-site-per-
+//   thread kernels run as persistent CTAs; the tile shape is chosen by timing
+//   candidate shapes on the batch.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "../../include/lcbp.h"
@@ -46,6 +54,16 @@ struct lcbp_batch {
   cudaGraphExec_t graph;
   bool graph_ok;
   long long step;
+  // fast path
+  std::vector<int> order;  // replica indices class by class, in storage order
+  ZmBatch zb;              // classes (zc and CTA ranges filled when tuned)
+  ZmBatchMaps maps[2];     // tensor maps with rho u buffer 0 / 1
+  bool fast_ok;            // every class fits the fast kernels
+  bool fast_pick;          // AUTO: the fast kernels timed faster than the generic ones
+  int path_req;            // LCBP_PATH_AUTO, LCBP_PATH_GENERIC or LCBP_PATH_FAST1
+  int zc;                  // planes per CTA (0 = not tuned)
+  int* d_order;
+  int* d_err;
 };
 
 namespace {
@@ -69,6 +87,97 @@ int check_r(lcbp_batch* b, int r) {
 void drop_graph(lcbp_batch* b) {
   if (b->graph_ok) cudaGraphExecDestroy(b->graph);
   b->graph_ok = false;
+}
+
+bool fast_eligible(const lcbp_batch* b) {
+  return b->fast_ok && b->path_req != LCBP_PATH_GENERIC && b->flow_on && b->coupling == LCBP_JACOBI;
+}
+
+bool use_fast(const lcbp_batch* b) {
+  return fast_eligible(b) && (b->path_req == LCBP_PATH_FAST1 || b->fast_pick);
+}
+
+// 5-D tensor maps of every class: field [c][z][y][x] per replica, replicas of
+// a class back to back (stride comps * padded sites)
+bool build_maps(lcbp_batch* b) {
+  const int ty = b->dtype == LCBP_F64 ? zm_tile_rows<double>() : zm_tile_rows<float>();
+  for (int k = 0; k < b->zb.nclass; ++k) {
+    const ZmClass& c = b->zb.c[k];
+    const int r0 = b->order[c.rep0];
+    const cuuint64_t es = b->es;
+    const cuuint64_t nx = c.G.nx, ny = c.G.ny, nz = c.G.nz, n = c.G.n;
+    const cuuint64_t npad = c.count > 1 ? (cuuint64_t)(b->base[b->order[c.rep0 + 1]] - b->base[r0]) : (cuuint64_t)n;
+    auto map = [&](CUtensorMap* tm, void* field, int comps, int rows) {
+      const cuuint64_t dims[5] = {nx, ny, nz, (cuuint64_t)comps, (cuuint64_t)c.count};
+      const cuuint64_t strides[4] = {nx * es, nx * ny * es, n * es, (cuuint64_t)comps * npad * es};
+      const cuuint32_t box[5] = {(cuuint32_t)kZmBoxX, (cuuint32_t)rows, 1, (cuuint32_t)comps, 1};
+      void* base = static_cast<char*>(field) + (size_t)comps * b->base[r0] * b->es;
+      return encode_tiled(tm, base, 5, dims, strides, box, b->dtype);
+    };
+    bool ok = map(&b->maps[0].q[k], b->q, 5, ty + 4) && map(&b->maps[0].u[k], b->rhou[0], 4, ty + 2) &&
+              map(&b->maps[1].u[k], b->rhou[1], 4, ty + 2) && map(&b->maps[0].s[k], b->sig, 5, ty + 2) &&
+              map(&b->maps[0].b[k], b->b, 3, ty + 2) && map(&b->maps[0].qs[k], b->qs, 5, ty + 2);
+    if (!ok) return false;
+    b->maps[1].q[k] = b->maps[0].q[k];
+    b->maps[1].s[k] = b->maps[0].s[k];
+    b->maps[1].b[k] = b->maps[0].b[k];
+    b->maps[1].qs[k] = b->maps[0].qs[k];
+  }
+  return true;
+}
+
+// geometry and CTA ranges of the classes for `zc` planes per CTA
+void set_zc(lcbp_batch* b, int zc) {
+  const int ty = b->dtype == LCBP_F64 ? zm_tile_rows<double>() : zm_tile_rows<float>();
+  int cta = 0;
+  for (int k = 0; k < b->zb.nclass; ++k) {
+    ZmClass& c = b->zb.c[k];
+    c.G.zc = std::min(zc, c.G.nz);
+    c.G.tiles_x = (c.G.nx + 31) / 32;
+    c.G.tiles_y = (c.G.ny + ty - 1) / ty;
+    c.G.tiles_z = (c.G.nz + c.G.zc - 1) / c.G.zc;
+    c.ctas_per_rep = c.G.tiles_x * c.G.tiles_y * c.G.tiles_z;
+    c.cta0 = cta;
+    cta += c.ctas_per_rep * c.count;
+  }
+  b->zb.total_ctas = cta;
+  b->zc = zc;
+}
+
+ZmBatchArgs zm_args(lcbp_batch* b) {
+  ZmBatchArgs a{};
+  a.B = b->zb;
+  a.maps = &b->maps[b->cur];
+  a.reps = b->d_rep;
+  a.order = b->d_order;
+  a.q = b->q;
+  a.qout = nullptr;
+  a.qs = b->qs;
+  a.sigma = b->sig;
+  a.b = b->b;
+  a.f = b->f[b->cur];
+  a.fnew = b->f[b->cur ^ 1];
+  a.rhou = b->rhou[b->cur];
+  a.rhou_new = b->rhou[b->cur ^ 1];
+  a.err = b->d_err;
+  return a;
+}
+
+cudaError_t launch_zm(lcbp_batch* b, const ZmBatchArgs& a) {
+  return b->dtype == LCBP_F64 ? launch_step_zm_batch<double>(a, b->stream)
+                              : launch_step_zm_batch<float>(a, b->stream);
+}
+
+int check_error_flag(lcbp_batch* b) {
+  int flag = 0;
+  cudaError_t e = cudaMemcpyAsync(&flag, b->d_err, sizeof(int), cudaMemcpyDeviceToHost, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "error flag");
+  if (flag) {
+    cudaMemsetAsync(b->d_err, 0, sizeof(int), b->stream);
+    return fail(LCBP_ETIMEOUT, "a bounded device-side wait timed out; the step's results are not valid");
+  }
+  return LCBP_OK;
 }
 
 int build_tiles(lcbp_batch* b, TileShape ts) {
@@ -140,7 +249,7 @@ cudaError_t launch(lcbp_batch* b, const StepArgs& a) {
 }
 
 cudaError_t eager(lcbp_batch* b) {
-  const cudaError_t e = launch(b, args(b));
+  const cudaError_t e = use_fast(b) ? launch_zm(b, zm_args(b)) : launch(b, args(b));
   if (b->flow_on) b->cur ^= 1;
   return e;
 }
@@ -156,7 +265,48 @@ int resident_ctas(lcbp_batch* b) {
   return std::max(1, sms * per_sm);
 }
 
-int tune(lcbp_batch* b) {
+// planes per CTA of the fast path: timed candidates, one step each (best of 3)
+int tune_fast(lcbp_batch* b, float* best_ms) {
+  int max_nz = 1;
+  for (int k = 0; k < b->zb.nclass; ++k) max_nz = std::max(max_nz, b->zb.c[k].G.nz);
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return fail(LCBP_ECUDA, "events");
+  float best = 1e30f;
+  int best_zc = 8;
+  for (int zc : {4, 6, 8, 10, 12, 16, 24, 32, 48, 64}) {
+    if (zc > max_nz && zc != 4) break;
+    set_zc(b, zc);
+    ZmBatchArgs a = zm_args(b);
+    a.qout = b->h;  // scratch: the state is left untouched
+    float t = 1e30f;
+    for (int rep = 0; rep < 3; ++rep) {
+      cudaEventRecord(e0, b->stream);
+      cudaError_t e = launch_zm(b, a);
+      cudaEventRecord(e1, b->stream);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      if (e != cudaSuccess) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return cuda_fail(e, "batch planes-per-CTA tuning");
+      }
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      t = std::min(t, ms);
+    }
+    if (t < best) {
+      best = t;
+      best_zc = zc;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  set_zc(b, best_zc);
+  *best_ms = best;
+  return check_error_flag(b);
+}
+
+// tile shape of the generic path: timed candidates, one step each (best of 3)
+int tune_generic(lcbp_batch* b, float* best_ms) {
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return fail(LCBP_ECUDA, "events");
   float best = 1e30f;
@@ -188,6 +338,19 @@ int tune(lcbp_batch* b) {
   int rc = build_tiles(b, best_ts);
   if (rc) return rc;
   b->max_grid = resident_ctas(b);
+  *best_ms = best;
+  return LCBP_OK;
+}
+
+// Tune the path the batch will run; with LCBP_PATH_AUTO and both paths open,
+// tune both and keep the faster.
+int tune(lcbp_batch* b) {
+  float t_fast = 1e30f, t_gen = 1e30f;
+  int rc = LCBP_OK;
+  if (fast_eligible(b)) rc = tune_fast(b, &t_fast);
+  if (!rc && (!fast_eligible(b) || b->path_req == LCBP_PATH_AUTO)) rc = tune_generic(b, &t_gen);
+  if (rc) return rc;
+  b->fast_pick = t_fast < t_gen;
   b->tuned = true;
   return LCBP_OK;
 }
@@ -234,6 +397,8 @@ int diag(lcbp_batch* b, int r, double threshold, int with_f) {
   if (e == cudaSuccess) e = cudaMemcpyAsync(b->h_out, b->d_out, 64, cudaMemcpyDeviceToHost, b->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
   if (e != cudaSuccess) return cuda_fail(e, "diagnostics");
+  int rc = check_error_flag(b);
+  if (rc) return rc;
   if (b->h_out[6] != 0.0) return fail(LCBP_ENONFINITE, "replica %d: %.0f sites hold NaN or Inf", r, b->h_out[6]);
   return LCBP_OK;
 }
@@ -264,8 +429,6 @@ int lcbp_batch_create(int R, const int* dims, const lcbp_params* params, int dty
     b->nz.push_back(z);
     const long long n = (long long)x * y * z;
     b->n.push_back(n);
-    b->base.push_back(tot);
-    tot += (n + 63) / 64 * 64;  // 256-byte aligned replica blocks in FP32
     long long mx = 0;
     for (const TileShape& c : kCandidates) mx = std::max(mx, tile_count(x, y, z, c));
     cap += mx;
@@ -286,6 +449,46 @@ int lcbp_batch_create(int R, const int* dims, const lcbp_params* params, int dty
     }
     b->p.push_back(hp);
   }
+  // classes of equal dims, in order of first appearance; storage class by class
+  b->zb = ZmBatch{};
+  b->fast_ok = true;
+  std::vector<int> cls(R, -1);
+  std::vector<std::vector<int>> members;
+  for (int r = 0; r < R; ++r) {
+    for (int k = 0; k < (int)members.size() && cls[r] < 0; ++k) {
+      const int q = members[k][0];
+      if (b->nx[q] == b->nx[r] && b->ny[q] == b->ny[r] && b->nz[q] == b->nz[r]) cls[r] = k;
+    }
+    if (cls[r] < 0) {
+      cls[r] = (int)members.size();
+      members.emplace_back();
+    }
+    members[cls[r]].push_back(r);
+  }
+  b->base.assign(R, 0);
+  for (int k = 0; k < (int)members.size(); ++k) {
+    const int q = members[k][0];
+    if (k < kZmMaxClasses) {
+      ZmClass& c = b->zb.c[k];
+      c.G.nx = b->nx[q];
+      c.G.ny = b->ny[q];
+      c.G.nz = b->nz[q];
+      c.G.n = b->n[q];
+      c.rep0 = (int)b->order.size();
+      c.count = (int)members[k].size();
+    }
+    if (b->nx[q] % 4 != 0) b->fast_ok = false;
+    for (int r : members[k]) {
+      b->order.push_back(r);
+      b->base[r] = tot;
+      tot += (b->n[r] + 63) / 64 * 64;  // 256-byte aligned replica blocks in FP32
+    }
+  }
+  if ((int)members.size() > kZmMaxClasses) b->fast_ok = false;
+  b->zb.nclass = std::min((int)members.size(), kZmMaxClasses);
+  b->path_req = LCBP_PATH_AUTO;
+  b->fast_pick = true;
+  b->zc = 0;
   if (tot > (1ll << 31)) {
     delete b;
     return fail(LCBP_EINVAL, "more than 2^31 sites");
@@ -311,6 +514,8 @@ int lcbp_batch_create(int R, const int* dims, const lcbp_params* params, int dty
   o = a256(o + (size_t)R * 3 * 8);
   const size_t off_part = o;
   o = a256(o + (kDiagPartials + 8) * 8);
+  const size_t off_order = o;
+  o = a256(o + (size_t)R * sizeof(int) + sizeof(int));
   cudaError_t e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaMalloc(&b->ws, o);
   if (e != cudaSuccess) {
@@ -338,12 +543,23 @@ int lcbp_batch_create(int R, const int* dims, const lcbp_params* params, int dty
   b->d_seed = reinterpret_cast<uint64_t*>(b->d_q0 + 2 * R);
   b->d_partials = reinterpret_cast<double*>(w + off_part);
   b->d_out = b->d_partials + kDiagPartials;
+  b->d_order = reinterpret_cast<int*>(w + off_order);
+  b->d_err = b->d_order + R;
   e = cudaMemsetAsync(b->ws, 0, off_stage, b->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->d_err, 0, sizeof(int), b->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->d_order, b->order.data(), (size_t)R * sizeof(int), cudaMemcpyHostToDevice, b->stream);
   if (e == cudaSuccess) e = cudaMallocHost(&b->h_out, 64);
   int rc = e == cudaSuccess ? LCBP_OK : cuda_fail(e, "batch set-up");
   if (!rc) rc = upload_table(b);
   if (!rc) rc = build_tiles(b, kCandidates[0]);
   if (!rc) b->max_grid = resident_ctas(b);
+  if (!rc && b->fast_ok) {
+    static std::once_flag prep32, prep64;
+    if (dtype == LCBP_F64) std::call_once(prep64, [] { zm_batch_prepare<double>(); });
+    else std::call_once(prep32, [] { zm_batch_prepare<float>(); });
+    b->fast_ok = build_maps(b);  // no tensor maps: the generic kernels serve the batch
+  }
   if (rc) {
     lcbp_batch_destroy(b);
     return rc;
@@ -369,8 +585,31 @@ int lcbp_batch_set_flow(lcbp_batch* b, int flow_on, int coupling) {
   if (rc) return rc;
   if (coupling != LCBP_JACOBI && coupling != LCBP_GAUSS_SEIDEL) return fail(LCBP_EINVAL, "bad coupling");
   drop_graph(b);
+  const bool was_open = fast_eligible(b);
   b->flow_on = flow_on ? 1 : 0;
   b->coupling = coupling;
+  if (fast_eligible(b) != was_open) b->tuned = false;
+  return LCBP_OK;
+}
+
+int lcbp_batch_set_path(lcbp_batch* b, int path) {
+  int rc = check_b(b);
+  if (rc) return rc;
+  if (path != LCBP_PATH_AUTO && path != LCBP_PATH_GENERIC && path != LCBP_PATH_FAST1)
+    return fail(LCBP_EINVAL, "a batch takes LCBP_PATH_AUTO, LCBP_PATH_GENERIC or LCBP_PATH_FAST1, got %d", path);
+  cudaStreamSynchronize(b->stream);
+  drop_graph(b);
+  b->path_req = path;
+  b->tuned = false;
+  return LCBP_OK;
+}
+
+int lcbp_batch_get_path(lcbp_batch* b, int* fast, int* planes_per_cta) {
+  int rc = check_b(b);
+  if (rc) return rc;
+  const bool f = use_fast(b);
+  if (fast) *fast = f ? 1 : 0;
+  if (planes_per_cta) *planes_per_cta = f && b->tuned ? b->zc : 0;
   return LCBP_OK;
 }
 
@@ -456,7 +695,8 @@ int lcbp_batch_synchronize(lcbp_batch* b) {
   int rc = check_b(b);
   if (rc) return rc;
   cudaError_t e = cudaStreamSynchronize(b->stream);
-  return e == cudaSuccess ? LCBP_OK : cuda_fail(e, "synchronize");
+  if (e != cudaSuccess) return cuda_fail(e, "synchronize");
+  return check_error_flag(b);
 }
 
 int lcbp_batch_read_q(lcbp_batch* b, int r, void* dst, int dtype) {

@@ -121,6 +121,41 @@ struct ZmArgs {
 };
 
 constexpr int kZmBoxX = 40;  // elements per TMA box row
+
+// Fast path over a batch: replicas of equal dims form a class whose fields are
+// stored back to back, so that each field of a class is one 5-D tensor
+// (x, y, z, component, replica).  Classes own consecutive CTA ranges of one
+// launch per kernel.
+constexpr int kZmMaxClasses = 4;
+struct ZmClass {
+  ZmGeom G;
+  int cta0;          // first CTA of the class
+  int ctas_per_rep;  // tiles_x * tiles_y * tiles_z
+  int rep0;          // first entry of the class in the replica order table
+  int count;         // replicas in the class
+};
+struct ZmBatch {
+  int nclass;
+  int total_ctas;
+  ZmClass c[kZmMaxClasses];
+};
+// per class: Q (box rows TY + 4), rho u, sigma, b, Q* (box rows TY + 2); 5-D
+struct ZmBatchMaps {
+  CUtensorMap q[kZmMaxClasses], u[kZmMaxClasses], s[kZmMaxClasses], b[kZmMaxClasses], qs[kZmMaxClasses];
+};
+struct ZmBatchArgs {
+  ZmBatch B;
+  const ZmBatchMaps* maps;  // host copy (rho u maps of the current buffer)
+  const void* reps;         // device Replica<real>[R]: base offsets and models
+  const int* order;         // device: replica indices, class by class in storage order
+  void *q, *qout, *qs, *sigma, *b;  // qout: nullptr = update Q in place
+  void *f, *fnew, *rhou, *rhou_new;
+  int* err;
+};
+template <typename real>
+cudaError_t zm_batch_prepare();
+template <typename real>
+cudaError_t launch_step_zm_batch(const ZmBatchArgs& a, cudaStream_t s);
 template <typename real>
 int zm_tile_rows();
 // polarised texture of a Q field into a device image [ny][nx] (optics.cu)

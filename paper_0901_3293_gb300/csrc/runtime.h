@@ -4,6 +4,7 @@
 #include <string>
 #include <vector>
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "common.cuh"
@@ -37,5 +38,7 @@ double s_eq(double gamma);
 int check_params(const HostParams& p);
 int transfer(void* state, int sd, void* user, int ud, long long count, bool upload, void* staging,
              long long staging_elems, cudaStream_t st);
+bool encode_tiled(CUtensorMap* tm, void* base, int rank, const cuuint64_t* dims, const cuuint64_t* strides,
+                  const cuuint32_t* box, int dtype);
 
 }  // namespace lcbp

@@ -42,19 +42,50 @@ __device__ __forceinline__ int wrap(int v, int n) {
 
 // Overwrite out-of-range cells of a TMA-loaded plane with periodic images.
 // Layout [comp][row][ZM_BX]; row r <-> global y = gy0 + r, column c <->
-// global x = x0 - ZM_XOFF + c; only columns [c0, c1) are needed.
+// global x = x0 - ZM_XOFF + c; only columns [c0, c1) are needed.  The cells
+// inside the lattice form one rectangle (rows [ra, rb), columns [ca, cb)), so
+// the threads walk only the frame around it: the rows above and below it, then
+// the columns left and right of it.
 template <typename real>
 __device__ void patch_plane(real* slot, int ncomp, int rows, int c0, int c1, const real* __restrict__ g, long long n,
                             int nx, int ny, int gz, int x0, int gy0) {
   const int w = c1 - c0;
-  const int cells = rows * w;
+  const int ra = max(0, -gy0), rb = min(rows, ny - gy0);
+  const int ca = max(c0, ZM_XOFF - x0), cb = min(c1, nx - x0 + ZM_XOFF);
+  const int lw = ca - c0, rw = c1 - cb, mid = rb - ra;
+  const int n_top = ra * w, n_bot = (rows - rb) * w, n_left = mid * lw, n_right = mid * rw;
+  const int cells = n_top + n_bot + n_left + n_right;
   for (int t = threadIdx.x; t < cells; t += blockDim.x) {
-    const int r = t / w, c = c0 + t % w;
+    int r, c;
+    if (t < n_top) {
+      r = t / w;
+      c = c0 + t % w;
+    } else if (t < n_top + n_bot) {
+      const int u = t - n_top;
+      r = rb + u / w;
+      c = c0 + u % w;
+    } else if (t < n_top + n_bot + n_left) {
+      const int u = t - n_top - n_bot;
+      r = ra + u / lw;
+      c = c0 + u % lw;
+    } else {
+      const int u = t - n_top - n_bot - n_left;
+      r = ra + u / rw;
+      c = cb + u % rw;
+    }
     const int gx = x0 - ZM_XOFF + c, gy = gy0 + r;
-    if (gx >= 0 && gx < nx && gy >= 0 && gy < ny) continue;
     const long long s = ((long long)gz * ny + wrap(gy, ny)) * nx + wrap(gx, nx);
     for (int k = 0; k < ncomp; ++k) slot[(k * rows + r) * ZM_BX + c] = g[k * n + s];
   }
+}
+
+// TMA tile load of plane z of a field: 4-D (x, y, z, component) for one
+// lattice, 5-D with the replica rc outermost for a batch class
+template <bool BATCH>
+__device__ __forceinline__ void zm_load(void* dst, const CUtensorMap* map, int x, int y, int z, int rc,
+                                        uint64_t* bar) {
+  if constexpr (BATCH) tma_load_5d(dst, map, x, y, z, 0, rc, bar);
+  else tma_load_4d(dst, map, x, y, z, 0, bar);
 }
 
 template <typename real>
@@ -150,13 +181,14 @@ constexpr int qside_threads() {
   return ((ring > out ? ring : out) + 31) / 32 * 32;
 }
 
-template <typename real, int TY, int SPT>
-__global__ void __launch_bounds__(qside_threads<TY, SPT>()) k_qside(const __grid_constant__ CUtensorMap tmQ,
-                                                     const __grid_constant__ CUtensorMap tmU, ZmGeom G,
-                                                     Model<real> m, const real* __restrict__ Q,
-                                                     const real* __restrict__ rhou, const real* __restrict__ bext,
-                                                     real* __restrict__ sigma, real* __restrict__ bout,
-                                                     real* __restrict__ Qs, int* __restrict__ err) {
+// Tile bt of one lattice (or of replica rc of a batch class, whose fields are
+// 5-D tensors with the replica outermost: BATCH) of the k_qside step.
+template <typename real, int TY, int SPT, bool BATCH>
+__device__ __forceinline__ void qside_body(const CUtensorMap* tmQ, const CUtensorMap* tmU, const ZmGeom G,
+                                           const Model<real> m, int bt, int rc, const real* __restrict__ Q,
+                                           const real* __restrict__ rhou, const real* __restrict__ bext,
+                                           real* __restrict__ sigma, real* __restrict__ bout,
+                                           real* __restrict__ Qs, int* __restrict__ err) {
   using L = QsideSmem<real, TY>;
   using V = typename LaneT<real, SPT>::V;
   constexpr int TYH = TY / SPT;  // rows handled by one pass of the CTA
@@ -172,7 +204,6 @@ __global__ void __launch_bounds__(qside_threads<TY, SPT>()) k_qside(const __grid
 
   const int nx = G.nx, ny = G.ny, nz = G.nz;
   const long long n = G.n;
-  const int bt = blockIdx.x;
   const int x0 = (bt % G.tiles_x) * ZM_TX;
   const int y0 = ((bt / G.tiles_x) % G.tiles_y) * TY;
   const int z0 = (bt / (G.tiles_x * G.tiles_y)) * G.zc;
@@ -187,8 +218,8 @@ __global__ void __launch_bounds__(qside_threads<TY, SPT>()) k_qside(const __grid
     for (int i = 0; i < L::QSLOTS + L::USLOTS; ++i) mbar_init(&bars[i], 1);
     *abort_flag = 0;
     mbar_init_fence();
-    tma_prefetch_desc(&tmQ);
-    tma_prefetch_desc(&tmU);
+    tma_prefetch_desc(tmQ);
+    tma_prefetch_desc(tmU);
   }
   __syncthreads();
 
@@ -199,13 +230,13 @@ __global__ void __launch_bounds__(qside_threads<TY, SPT>()) k_qside(const __grid
     const int k = p - (z0 - 2);
     uint64_t* bar = &bars[k % L::QSLOTS];
     mbar_arrive_expect_tx(bar, qbytes);
-    tma_load_4d(qslot(p), &tmQ, x0 - ZM_XOFF, y0 - 2, wrap(p, nz), 0, bar);
+    zm_load<BATCH>(qslot(p), tmQ, x0 - ZM_XOFF, y0 - 2, wrap(p, nz), rc, bar);
   };
   auto issue_u = [&](int p) {
     const int k = p - (z0 - 1);
     uint64_t* bar = &bars[L::QSLOTS + k % L::USLOTS];
     mbar_arrive_expect_tx(bar, ubytes);
-    tma_load_4d(uslot(p), &tmU, x0 - ZM_XOFF, y0 - 1, wrap(p, nz), 0, bar);
+    zm_load<BATCH>(uslot(p), tmU, x0 - ZM_XOFF, y0 - 1, wrap(p, nz), rc, bar);
   };
   // Wait for a plane, then patch its periodic halo.  Every thread reaches the
   // __syncthreads that follows a wait, so a timeout cannot strand part of the CTA.
@@ -381,6 +412,76 @@ __global__ void __launch_bounds__(qside_threads<TY, SPT>()) k_qside(const __grid
   }
 }
 
+template <typename real, int TY, int SPT>
+__global__ void __launch_bounds__(qside_threads<TY, SPT>()) k_qside(const __grid_constant__ CUtensorMap tmQ,
+                                                     const __grid_constant__ CUtensorMap tmU, ZmGeom G,
+                                                     Model<real> m, const real* __restrict__ Q,
+                                                     const real* __restrict__ rhou, const real* __restrict__ bext,
+                                                     real* __restrict__ sigma, real* __restrict__ bout,
+                                                     real* __restrict__ Qs, int* __restrict__ err) {
+  qside_body<real, TY, SPT, false>(&tmQ, &tmU, G, m, blockIdx.x, 0, Q, rhou, bext, sigma, bout, Qs, err);
+}
+
+// The CTA's batch class, its replica and tile: classes own consecutive CTA ranges.
+struct ZmItem {
+  int k;   // class
+  int j;   // replica position within the class (the 5-D tensor coordinate)
+  int bt;  // tile within the replica
+};
+__device__ __forceinline__ ZmItem zm_item(const ZmBatch& B) {
+  ZmItem it{0, 0, 0};
+  int cta0 = B.c[0].cta0, per = B.c[0].ctas_per_rep;
+#pragma unroll
+  for (int i = 1; i < kZmMaxClasses; ++i)
+    if (i < B.nclass && (int)blockIdx.x >= B.c[i].cta0) {
+      it.k = i;
+      cta0 = B.c[i].cta0;
+      per = B.c[i].ctas_per_rep;
+    }
+  const int local = (int)blockIdx.x - cta0;
+  it.j = local / per;
+  it.bt = local % per;
+  return it;
+}
+
+template <typename real>
+__device__ __forceinline__ ZmGeom zm_class_geom(const ZmBatch& B, int k) {
+  ZmGeom G = B.c[0].G;
+#pragma unroll
+  for (int i = 1; i < kZmMaxClasses; ++i)
+    if (i == k) G = B.c[i].G;
+  return G;
+}
+
+template <typename real, int TY>
+__global__ void __launch_bounds__(qside_threads<TY, 1>(), 2) k_qside_batch(const __grid_constant__ ZmBatchMaps maps,
+                                                         ZmBatch B, const Replica<real>* __restrict__ reps,
+                                                         const int* __restrict__ order, const real* __restrict__ Q,
+                                                         const real* __restrict__ rhou, real* __restrict__ sigma,
+                                                         real* __restrict__ bout, real* __restrict__ Qs,
+                                                         int* __restrict__ err) {
+  const ZmItem it = zm_item(B);
+  const ZmGeom G = zm_class_geom<real>(B, it.k);
+  int rep0 = B.c[0].rep0;
+#pragma unroll
+  for (int i = 1; i < kZmMaxClasses; ++i)
+    if (i == it.k) rep0 = B.c[i].rep0;
+  const int r = order[rep0 + it.j];
+  const long long o = reps[r].base;
+  const Model<real> m = reps[r].m;
+  // the class's maps, selected at compile-time offsets (a runtime index into
+  // the parameter arrays would copy them to local memory)
+  const CUtensorMap *mq = &maps.q[0], *mu = &maps.u[0];
+#pragma unroll
+  for (int i = 1; i < kZmMaxClasses; ++i)
+    if (i == it.k) {
+      mq = &maps.q[i];
+      mu = &maps.u[i];
+    }
+  qside_body<real, TY, 1, true>(mq, mu, G, m, it.bt, it.j, Q + 5 * o, rhou + 4 * o, nullptr, sigma + 5 * o,
+                                bout + 3 * o, Qs + 5 * o, err);
+}
+
 // ---------------------------------------------------------------------------
 // Kernel B: LB predictor-corrector and the Heun corrector
 // ---------------------------------------------------------------------------
@@ -396,13 +497,14 @@ struct LbqSmem {
   static constexpr size_t bytes = sizeof(real) * (size_t)SLOTS * SLOT + 8 * 8 + 16;
 };
 
-template <typename real, int TY, int SPT>
-__global__ void __launch_bounds__(ZM_TX* TY / SPT, 2)
-    k_lbq(const __grid_constant__ CUtensorMap tmU, const __grid_constant__ CUtensorMap tmS,
-          const __grid_constant__ CUtensorMap tmB, const __grid_constant__ CUtensorMap tmQs, ZmGeom G, Model<real> m,
-          const real* __restrict__ f, const real* __restrict__ rhou, const real* __restrict__ sigma,
-          const real* __restrict__ bf, const real* __restrict__ Qs, const real* __restrict__ Qin,
-          real* __restrict__ fnew, real* __restrict__ rhou_new, real* __restrict__ Qout, int* __restrict__ err) {
+template <typename real, int TY, int SPT, bool BATCH>
+__device__ __forceinline__ void lbq_body(const CUtensorMap* tmU, const CUtensorMap* tmS, const CUtensorMap* tmB,
+                                         const CUtensorMap* tmQs, const ZmGeom& G, const Model<real>& m, int bt,
+                                         int rc, const real* __restrict__ f, const real* __restrict__ rhou,
+                                         const real* __restrict__ sigma, const real* __restrict__ bf,
+                                         const real* __restrict__ Qs, const real* __restrict__ Qin,
+                                         real* __restrict__ fnew, real* __restrict__ rhou_new,
+                                         real* __restrict__ Qout, int* __restrict__ err) {
   using L = LbqSmem<real, TY>;
   using V = typename LaneT<real, SPT>::V;
   constexpr int TYH = TY / SPT;  // a thread takes rows ty + k * TYH, k < SPT
@@ -413,7 +515,6 @@ __global__ void __launch_bounds__(ZM_TX* TY / SPT, 2)
 
   const int nx = G.nx, ny = G.ny, nz = G.nz;
   const long long n = G.n;
-  const int bt = blockIdx.x;
   const int x0 = (bt % G.tiles_x) * ZM_TX;
   const int y0 = ((bt / G.tiles_x) % G.tiles_y) * TY;
   const int z0 = (bt / (G.tiles_x * G.tiles_y)) * G.zc;
@@ -437,10 +538,10 @@ __global__ void __launch_bounds__(ZM_TX* TY / SPT, 2)
     for (int i = 0; i < L::SLOTS; ++i) mbar_init(&bars[i], 1);
     *abort_flag = 0;
     mbar_init_fence();
-    tma_prefetch_desc(&tmU);
-    tma_prefetch_desc(&tmS);
-    tma_prefetch_desc(&tmB);
-    tma_prefetch_desc(&tmQs);
+    tma_prefetch_desc(tmU);
+    tma_prefetch_desc(tmS);
+    tma_prefetch_desc(tmB);
+    tma_prefetch_desc(tmQs);
   }
   __syncthreads();
 
@@ -451,10 +552,10 @@ __global__ void __launch_bounds__(ZM_TX* TY / SPT, 2)
     real* sl = slot(p);
     const int zz = wrap(p, nz);
     mbar_arrive_expect_tx(bar, slot_bytes);
-    tma_load_4d(sl, &tmU, x0 - ZM_XOFF, y0 - 1, zz, 0, bar);
-    tma_load_4d(sl + L::OFF_S, &tmS, x0 - ZM_XOFF, y0 - 1, zz, 0, bar);
-    tma_load_4d(sl + L::OFF_B, &tmB, x0 - ZM_XOFF, y0 - 1, zz, 0, bar);
-    tma_load_4d(sl + L::OFF_Q, &tmQs, x0 - ZM_XOFF, y0 - 1, zz, 0, bar);
+    zm_load<BATCH>(sl, tmU, x0 - ZM_XOFF, y0 - 1, zz, rc, bar);
+    zm_load<BATCH>(sl + L::OFF_S, tmS, x0 - ZM_XOFF, y0 - 1, zz, rc, bar);
+    zm_load<BATCH>(sl + L::OFF_B, tmB, x0 - ZM_XOFF, y0 - 1, zz, rc, bar);
+    zm_load<BATCH>(sl + L::OFF_Q, tmQs, x0 - ZM_XOFF, y0 - 1, zz, rc, bar);
   };
   auto wait = [&](int p) {
     const int k = p - (z0 - 1);
@@ -651,6 +752,46 @@ __global__ void __launch_bounds__(ZM_TX* TY / SPT, 2)
   }
 }
 
+template <typename real, int TY, int SPT>
+__global__ void __launch_bounds__(ZM_TX* TY / SPT, 2)
+    k_lbq(const __grid_constant__ CUtensorMap tmU, const __grid_constant__ CUtensorMap tmS,
+          const __grid_constant__ CUtensorMap tmB, const __grid_constant__ CUtensorMap tmQs, ZmGeom G, Model<real> m,
+          const real* __restrict__ f, const real* __restrict__ rhou, const real* __restrict__ sigma,
+          const real* __restrict__ bf, const real* __restrict__ Qs, const real* __restrict__ Qin,
+          real* __restrict__ fnew, real* __restrict__ rhou_new, real* __restrict__ Qout, int* __restrict__ err) {
+  lbq_body<real, TY, SPT, false>(&tmU, &tmS, &tmB, &tmQs, G, m, blockIdx.x, 0, f, rhou, sigma, bf, Qs, Qin, fnew,
+                                 rhou_new, Qout, err);
+}
+
+template <typename real, int TY>
+__global__ void __launch_bounds__(ZM_TX* TY, 2)
+    k_lbq_batch(const __grid_constant__ ZmBatchMaps maps, ZmBatch B, const Replica<real>* __restrict__ reps,
+                const int* __restrict__ order, const real* __restrict__ f, const real* __restrict__ rhou,
+                const real* __restrict__ sigma, const real* __restrict__ bf, const real* __restrict__ Qs,
+                const real* __restrict__ Qin, real* __restrict__ fnew, real* __restrict__ rhou_new,
+                real* __restrict__ Qout, int* __restrict__ err) {
+  const ZmItem it = zm_item(B);
+  const ZmGeom G = zm_class_geom<real>(B, it.k);
+  int rep0 = B.c[0].rep0;
+#pragma unroll
+  for (int i = 1; i < kZmMaxClasses; ++i)
+    if (i == it.k) rep0 = B.c[i].rep0;
+  const int r = order[rep0 + it.j];
+  const long long o = reps[r].base;
+  const Model<real> m = reps[r].m;
+  const CUtensorMap *mu = &maps.u[0], *ms = &maps.s[0], *mb = &maps.b[0], *mqs = &maps.qs[0];
+#pragma unroll
+  for (int i = 1; i < kZmMaxClasses; ++i)
+    if (i == it.k) {
+      mu = &maps.u[i];
+      ms = &maps.s[i];
+      mb = &maps.b[i];
+      mqs = &maps.qs[i];
+    }
+  lbq_body<real, TY, 1, true>(mu, ms, mb, mqs, G, m, it.bt, it.j, f + NV * o, rhou + 4 * o, sigma + 5 * o, bf + 3 * o, Qs + 5 * o, Qin + 5 * o,
+                              fnew + NV * o, rhou_new + 4 * o, Qout + 5 * o, err);
+}
+
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
@@ -753,8 +894,39 @@ cudaError_t launch_step_zm(const ZmArgs& a, cudaStream_t s) {
   return launch_step_zm_spt<real, 1>(a, s);
 }
 
+template <typename real>
+cudaError_t zm_batch_prepare() {
+  constexpr int TY = zm_ty<real>();
+  cudaError_t e = cudaFuncSetAttribute(k_qside_batch<real, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)QsideSmem<real, TY>::bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_lbq_batch<real, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)LbqSmem<real, TY>::bytes);
+  return e;
+}
+
+template <typename real>
+cudaError_t launch_step_zm_batch(const ZmBatchArgs& a, cudaStream_t s) {
+  constexpr int TY = zm_ty<real>();
+  const int grid = a.B.total_ctas;
+  const auto* reps = static_cast<const Replica<real>*>(a.reps);
+  k_qside_batch<real, TY><<<grid, qside_threads<TY, 1>(), QsideSmem<real, TY>::bytes, s>>>(
+      *a.maps, a.B, reps, a.order, static_cast<const real*>(a.q), static_cast<const real*>(a.rhou),
+      static_cast<real*>(a.sigma), static_cast<real*>(a.b), static_cast<real*>(a.qs), a.err);
+  k_lbq_batch<real, TY><<<grid, ZM_TX * TY, LbqSmem<real, TY>::bytes, s>>>(
+      *a.maps, a.B, reps, a.order, static_cast<const real*>(a.f), static_cast<const real*>(a.rhou),
+      static_cast<const real*>(a.sigma), static_cast<const real*>(a.b), static_cast<const real*>(a.qs),
+      static_cast<const real*>(a.q), static_cast<real*>(a.fnew), static_cast<real*>(a.rhou_new),
+      static_cast<real*>(a.qout ? a.qout : a.q), a.err);
+  return cudaGetLastError();
+}
+
 template cudaError_t zm_prepare<float>();
 template cudaError_t zm_prepare<double>();
+template cudaError_t zm_batch_prepare<float>();
+template cudaError_t zm_batch_prepare<double>();
+template cudaError_t launch_step_zm_batch<float>(const ZmBatchArgs&, cudaStream_t);
+template cudaError_t launch_step_zm_batch<double>(const ZmBatchArgs&, cudaStream_t);
 template int zm_tile_rows<float>();
 template int zm_tile_rows<double>();
 template int zm_spt_max<float>();

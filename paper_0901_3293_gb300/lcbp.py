@@ -101,6 +101,8 @@ _SIGNATURES = {
     "lcbp_batch_free_energy": (_c_int, [_P, _c_int, ctypes.POINTER(_c_double)]),
     "lcbp_batch_totals": (_c_int, [_P, _c_int, ctypes.POINTER(_c_double), ctypes.POINTER(_c_double)]),
     "lcbp_batch_defect_fraction": (_c_int, [_P, _c_int, _c_double, ctypes.POINTER(_c_double)]),
+    "lcbp_batch_set_path": (_c_int, [_P, _c_int]),
+    "lcbp_batch_get_path": (_c_int, [_P, ctypes.POINTER(_c_int), ctypes.POINTER(_c_int)]),
     "lcbp_batch_get_info": (_c_int, [_P, ctypes.POINTER(_c_int), ctypes.POINTER(ctypes.c_longlong),
                                      ctypes.POINTER(_c_int), ctypes.POINTER(_c_int),
                                      ctypes.POINTER(ctypes.c_longlong)]),
@@ -439,6 +441,17 @@ class Batch:
     def set_flow(self, flow_on: bool = True, coupling: int = JACOBI) -> "Batch":
         check(lib().lcbp_batch_set_flow(self._h, int(bool(flow_on)), coupling))
         return self
+
+    def set_path(self, path: int) -> "Batch":
+        check(lib().lcbp_batch_set_path(self._h, path))
+        return self
+
+    def path(self):
+        """(fast kernels in use, tuned planes per CTA or 0)."""
+        fast = _c_int()
+        zc = _c_int()
+        check(lib().lcbp_batch_get_path(self._h, ctypes.byref(fast), ctypes.byref(zc)))
+        return bool(fast.value), zc.value
 
     def init_q(self, r: int, kind: int, amplitude: float, noise: float = 0.0, seed: int = 0, z0=None) -> "Batch":
         region = (_c_int * 1)(z0) if z0 is not None else None

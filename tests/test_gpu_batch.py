@@ -57,21 +57,26 @@ def test_batch_replicas_match_oracle_f64(lcbp):
         assert abs(m - m_o) < 1e-10 and np.abs(P - P_o).max() < 1e-12
 
 
-def test_batch_equals_single_lattices_bitwise_f32(lcbp):
+@pytest.mark.parametrize("path", ["generic", "fast"])
+def test_batch_equals_single_lattices_bitwise_f32(lcbp, path):
+    """Three classes (32^3, 48^3 and one 20 x 12 x 8 replica): on either path
+    every replica equals the lattice stepped alone on the same path."""
     sweep = synth.replica_sweep(6)
     sweep[1]["dims"] = (20, 12, 8)  # a ragged replica among the cubes
     dims = [s["dims"] for s in sweep]
     params = [replica_params(s["kappa"], s["tau"]) for s in sweep]
     kinds = [initial.BPII, initial.CHOL_Z, initial.ISO_NOISE]
     b = lcbp.Batch(dims, params, dtype="f32")
+    b.set_path(lcbp.PATH_GENERIC if path == "generic" else lcbp.PATH_FAST1)
     for r, s in enumerate(sweep):
         b.init_q(r, kinds[s["kind"]], 0.3 if s["kind"] == 0 else 0.4, noise=1e-3, seed=s["seed"])
     b.init_f_equilibrium(1.0).step(25)
+    assert b.path()[0] == (path == "fast")
     for r, s in enumerate(sweep):
         nx, ny, nz = s["dims"]
         p = params[r]
         lat = lcbp.Lattice(nx, ny, nz, dtype="f32")
-        lat.set_path(lcbp.PATH_GENERIC)
+        lat.set_path(lcbp.PATH_GENERIC if path == "generic" else lcbp.PATH_FAST1)
         lat.set_ldg(p["A0"], p["gamma"], p["K"], p["q0"]).set_flow(p["tau_f"], p["xi"], p["Gamma"])
         lat.init_q(kinds[s["kind"]], 0.3 if s["kind"] == 0 else 0.4, noise=1e-3, seed=s["seed"])
         lat.init_f_equilibrium(1.0).step(25)
@@ -101,3 +106,79 @@ def test_sweep_of_48_replicas(lcbp):
         assert np.isfinite(b.free_energy(r))
     with pytest.raises(lcbp.LcbpError):
         b.read_q(48)
+
+
+# classes of equal dims with nx % 4 == 0: the fast path; one class has a single replica
+FAST_MIXED = [((8, 8, 8), 0.5, -0.5, initial.BPII), ((12, 10, 6), 1.0, 0.0, initial.CHOL_Z),
+              ((8, 8, 8), 2.0, -1.0, initial.ISO_NOISE), ((16, 6, 9), 1.5, 0.3, initial.CHOL_X),
+              ((12, 10, 6), 0.3, 0.5, initial.BPII)]
+
+
+def test_fast_batch_matches_oracle_f64(lcbp):
+    dims = [d for d, *_ in FAST_MIXED]
+    params = [replica_params(k, t) for _, k, t, _ in FAST_MIXED]
+    b = lcbp.Batch(dims, params, dtype="f64").set_path(lcbp.PATH_FAST1)
+    for r, (d, k, t, kind) in enumerate(FAST_MIXED):
+        b.init_q(r, kind, 0.3 if kind == initial.BPII else 0.4, noise=1e-2, seed=200 + r)
+    b.init_f_equilibrium(1.0).step(10)
+    fast, zc = b.path()
+    assert fast and zc >= 1
+    for r, (d, k, t, kind) in enumerate(FAST_MIXED):
+        nx, ny, nz = d
+        p = lbq.Params(**params[r])
+        Q = initial.init_q9((nz, ny, nx), kind, p.q0, 0.3 if kind == initial.BPII else 0.4, 1e-2, 200 + r)
+        f = lbq.init_f_equilibrium(Q, p)
+        f, Q = lbq.run(f, Q, p, 10)
+        assert np.abs(b.read_q(r) - lbq.q9_to_q5(Q)).max() < 1e-13, r
+        assert np.abs(b.read_u(r) - np.moveaxis(lbq.moments(f)[1], -1, 0)).max() < 1e-14, r
+
+
+def test_fast_batch_matches_generic_batch_f32(lcbp):
+    """The 48-replica sweep's two classes, a few replicas each: fast and generic
+    batches agree to FP32 rounding after 20 steps."""
+    sweep = synth.replica_sweep(8)
+    dims = [s["dims"] for s in sweep]
+    params = [replica_params(s["kappa"], s["tau"]) for s in sweep]
+    kinds = [initial.BPII, initial.CHOL_Z, initial.ISO_NOISE]
+    out = {}
+    for path in (lcbp.PATH_FAST1, lcbp.PATH_GENERIC):
+        b = lcbp.Batch(dims, params, dtype="f32").set_path(path)
+        for r, s in enumerate(sweep):
+            b.init_q(r, kinds[s["kind"]], 0.3 if s["kind"] == 0 else 0.4, noise=1e-3, seed=s["seed"])
+        b.init_f_equilibrium(1.0).step(20)
+        assert b.path()[0] == (path == lcbp.PATH_FAST1)
+        out[path] = [(b.read_q(r, np.float32), b.read_u(r, np.float32)) for r in range(len(sweep))]
+        b.close()
+    for r in range(len(sweep)):
+        (qa, ua), (qg, ug) = out[lcbp.PATH_FAST1][r], out[lcbp.PATH_GENERIC][r]
+        # the same bounds as a single lattice's fast-against-generic check
+        assert np.abs(qa - qg).max() < 1e-6, r
+        assert np.abs(ua - ug).max() < 1e-8, r
+
+
+def test_batch_path_rules(lcbp):
+    """More than four classes, an nx not divisible by 4, flow off or
+    Gauss-Seidel coupling: the generic kernels even when the fast ones are
+    asked for; AUTO keeps the faster of the two after timing both."""
+    p = replica_params(1.0, 0.0)
+    five = lcbp.Batch([(8, 4, 4), (8, 4, 5), (8, 4, 6), (8, 4, 7), (8, 4, 8)], [p] * 5).set_path(lcbp.PATH_FAST1)
+    ragged = lcbp.Batch([(8, 8, 8), (6, 8, 8)], [p] * 2).set_path(lcbp.PATH_FAST1)
+    ok = lcbp.Batch([(8, 8, 8), (12, 4, 4)], [p] * 2).set_path(lcbp.PATH_FAST1)
+    for b in (five, ragged, ok):
+        for r in range(b.R):
+            b.init_q(r, initial.BPII, 0.3, noise=1e-3, seed=r)
+        b.init_f_equilibrium(1.0).step(2)
+    assert not five.path()[0] and not ragged.path()[0] and ok.path()[0]
+    ok.set_flow(True, lcbp.GAUSS_SEIDEL).step(1)
+    assert not ok.path()[0]
+    ok.set_flow(True, lcbp.JACOBI).step(1)
+    assert ok.path()[0]
+    ok.set_flow(False).step(1)
+    assert not ok.path()[0]
+    with pytest.raises(lcbp.LcbpError):
+        ok.set_path(lcbp.PATH_FAST2)
+    ok.set_flow(True, lcbp.JACOBI).set_path(lcbp.PATH_AUTO).step(1)
+    fast, zc = ok.path()
+    assert (zc >= 1) if fast else (zc == 0)
+    for b in (five, ragged, ok):
+        b.close()
