@@ -40,43 +40,49 @@ __device__ __forceinline__ int wrap(int v, int n) {
   return v < 0 ? v + n : v;
 }
 
-// Overwrite out-of-range cells of a TMA-loaded plane with periodic images.
-// Layout [comp][row][ZM_BX]; row r <-> global y = gy0 + r, column c <->
-// global x = x0 - ZM_XOFF + c; only columns [c0, c1) are needed.  The cells
-// inside the lattice form one rectangle (rows [ra, rb), columns [ca, cb)), so
-// the threads walk only the frame around it: the rows above and below it, then
-// the columns left and right of it.
-template <typename real>
-__device__ void patch_plane(real* slot, int ncomp, int rows, int c0, int c1, const real* __restrict__ g, long long n,
-                            int nx, int ny, int gz, int x0, int gy0) {
-  const int w = c1 - c0;
-  const int ra = max(0, -gy0), rb = min(rows, ny - gy0);
-  const int ca = max(c0, ZM_XOFF - x0), cb = min(c1, nx - x0 + ZM_XOFF);
-  const int lw = ca - c0, rw = c1 - cb, mid = rb - ra;
-  const int n_top = ra * w, n_bot = (rows - rb) * w, n_left = mid * lw, n_right = mid * rw;
-  const int cells = n_top + n_bot + n_left + n_right;
-  for (int t = threadIdx.x; t < cells; t += blockDim.x) {
-    int r, c;
-    if (t < n_top) {
-      r = t / w;
-      c = c0 + t % w;
-    } else if (t < n_top + n_bot) {
-      const int u = t - n_top;
-      r = rb + u / w;
-      c = c0 + u % w;
-    } else if (t < n_top + n_bot + n_left) {
-      const int u = t - n_top - n_bot;
-      r = ra + u / lw;
-      c = c0 + u % lw;
-    } else {
-      const int u = t - n_top - n_bot - n_left;
-      r = ra + u / rw;
-      c = cb + u % rw;
-    }
-    const int gx = x0 - ZM_XOFF + c, gy = gy0 + r;
-    const long long s = ((long long)gz * ny + wrap(gy, ny)) * nx + wrap(gx, nx);
-    for (int k = 0; k < ncomp; ++k) slot[(k * rows + r) * ZM_BX + c] = g[k * n + s];
+// The out-of-range cells of a staged plane (edge tiles).  Layout
+// [comp][row][ZM_BX]; row r <-> global y = gy0 + r, column c <-> global
+// x = x0 - ZM_XOFF + c; only rows [0, ROWS) and columns [C0, C1) are needed.
+// The cells inside the lattice form one rectangle, so the frame around it is
+// enumerated as the rows above and below it, then the columns left and right
+// of it.  TMA zero-fills these cells; the kernels overwrite them with their
+// periodic images.
+template <int ROWS, int C0, int C1>
+struct Frame {
+  static constexpr int W = C1 - C0;
+  int ra, rb, lw, rw;  // in-lattice rows [ra, rb); out-of-range columns left / right
+  __device__ __forceinline__ Frame(int nx, int ny, int x0, int gy0) {
+    ra = max(0, -gy0);
+    rb = min(ROWS, ny - gy0);
+    lw = max(C0, ZM_XOFF - x0) - C0;
+    rw = C1 - min(C1, nx - x0 + ZM_XOFF);
   }
+  __device__ __forceinline__ int cells() const { return (ROWS - (rb - ra)) * W + (rb - ra) * (lw + rw); }
+  // row and column of cell t < cells()
+  __device__ __forceinline__ void cell(int t, int& r, int& c) const {
+    const int n_top = ra * W, n_tb = n_top + (ROWS - rb) * W, n_tbl = n_tb + (rb - ra) * lw;
+    if (t < n_top) {
+      r = t / W;
+      c = C0 + t % W;
+    } else if (t < n_tb) {
+      const int u = t - n_top;
+      r = rb + u / W;
+      c = C0 + u % W;
+    } else if (t < n_tbl) {
+      const int u = t - n_tb;
+      r = ra + u / lw;
+      c = C0 + u % lw;
+    } else {
+      const int u = t - n_tbl;
+      r = ra + u / rw;
+      c = C1 - rw + u % rw;
+    }
+  }
+};
+
+// site of the periodic image of frame cell (r, c) on plane gz
+__device__ __forceinline__ long long image_site(int r, int c, int nx, int ny, int gz, int x0, int gy0) {
+  return ((long long)gz * ny + wrap(gy0 + r, ny)) * nx + wrap(x0 - ZM_XOFF + c, nx);
 }
 
 // TMA tile load of plane z of a field: 4-D (x, y, z, component) for one
@@ -238,17 +244,52 @@ __device__ __forceinline__ void qside_body(const CUtensorMap* tmQ, const CUtenso
     mbar_arrive_expect_tx(bar, ubytes);
     zm_load<BATCH>(uslot(p), tmU, x0 - ZM_XOFF, y0 - 1, wrap(p, nz), rc, bar);
   };
-  // Wait for a plane, then patch its periodic halo.  Every thread reaches the
-  // __syncthreads that follows a wait, so a timeout cannot strand part of the CTA.
+  // Wait for a plane.  Every thread reaches the __syncthreads that follows a
+  // wait, so a timeout cannot strand part of the CTA.
   auto wait_q = [&](int p) {
     const int k = p - (z0 - 2);
-    if (!mbar_wait_bounded(&bars[k % L::QSLOTS], (k / L::QSLOTS) & 1, kWaitLimitNs)) *abort_flag = 1;
-    else if (edge_q) patch_plane(qslot(p), 5, L::QROWS, 2, ZM_TX + 6, Q, n, nx, ny, wrap(p, nz), x0, y0 - 2);
+    const bool ok = mbar_wait_bounded(&bars[k % L::QSLOTS], (k / L::QSLOTS) & 1, kWaitLimitNs);
+    if (!ok) *abort_flag = 1;
+    return ok;
   };
   auto wait_u = [&](int p) {
     const int k = p - (z0 - 1);
-    if (!mbar_wait_bounded(&bars[L::QSLOTS + k % L::USLOTS], (k / L::USLOTS) & 1, kWaitLimitNs)) *abort_flag = 1;
-    else if (edge_u) patch_plane(uslot(p), 4, L::UROWS, 3, ZM_TX + 5, rhou, n, nx, ny, wrap(p, nz), x0, y0 - 1);
+    const bool ok = mbar_wait_bounded(&bars[L::QSLOTS + k % L::USLOTS], (k / L::USLOTS) & 1, kWaitLimitNs);
+    if (!ok) *abort_flag = 1;
+    return ok;
+  };
+  // Periodic halo of edge tiles: item t is one component of a frame cell of
+  // the Q plane pq (t < items_q, 5 components) or of the rho u plane pu (4).
+  // patch_item returns its value and its index in shared memory.
+  const Frame<L::QROWS, 2, ZM_TX + 6> FQ(nx, ny, x0, y0 - 2);
+  const Frame<L::UROWS, 3, ZM_TX + 5> FU(nx, ny, x0, y0 - 1);
+  const int items_q = edge_q ? FQ.cells() * 5 : 0, items = items_q + (edge_u ? FU.cells() * 4 : 0);
+  auto patch_item = [&](int t, int pq, int pu, int& dst) -> real {
+    int r, c;
+    if (t < items_q) {
+      const int cell = t / 5, k = t - 5 * cell;
+      FQ.cell(cell, r, c);
+      dst = (int)(qslot(pq) - base) + (k * L::QROWS + r) * ZM_BX + c;
+      return Q[k * n + image_site(r, c, nx, ny, wrap(pq, nz), x0, y0 - 2)];
+    }
+    const int u = t - items_q, cell = u / 4, k = u - 4 * cell;
+    FU.cell(cell, r, c);
+    dst = (int)(uslot(pu) - base) + (k * L::UROWS + r) * ZM_BX + c;
+    return rhou[k * n + image_site(r, c, nx, ny, wrap(pu, nz), x0, y0 - 1)];
+  };
+  auto patch_q = [&](int p) {
+    for (int t = threadIdx.x; t < items_q; t += blockDim.x) {
+      int d;
+      const real v = patch_item(t, p, p, d);
+      base[d] = v;
+    }
+  };
+  auto patch_u = [&](int p) {
+    for (int t = items_q + threadIdx.x; t < items; t += blockDim.x) {
+      int d;
+      const real v = patch_item(t, p, p, d);
+      base[d] = v;
+    }
   };
   auto tslot = [&](int p) { return tring + wrap(p - z0, 3) * L::TSLOT; };
   auto hslot = [&](int p) { return hbuf + ((p - z0 + 2) & 1) * L::HSLOT; };
@@ -309,9 +350,10 @@ __device__ __forceinline__ void qside_body(const CUtensorMap* tmQ, const CUtenso
     for (int p = z0 - 2; p <= z0 + 2; ++p) issue_q(p);
     for (int p = z0 - 1; p <= z0 + 1; ++p) issue_u(p);
   }
-  for (int p = z0 - 2; p <= z0 + 1; ++p) wait_q(p);
-  wait_u(z0 - 1);
-  wait_u(z0);
+  for (int p = z0 - 2; p <= z0 + 1; ++p)
+    if (wait_q(p)) patch_q(p);
+  if (wait_u(z0 - 1)) patch_u(z0 - 1);
+  if (wait_u(z0)) patch_u(z0);
   __syncthreads();
   aborted = *abort_flag != 0;
   if (!aborted) {
@@ -325,8 +367,28 @@ __device__ __forceinline__ void qside_body(const CUtensorMap* tmQ, const CUtenso
   // Q and u slots the next loads overwrite (planes z-2) and of the tau / H
   // slots this plane's pass overwrites, so no barrier closes the plane.
   for (int z = z0; z < z1 && !aborted; ++z) {
-    wait_q(z + 2);
-    wait_u(z + 1);
+    // the periodic images for the planes waited for are loaded before the
+    // waits (they do not depend on the copies), and stored after them
+    constexpr int KP = 2;
+    real pv[KP];
+    int pd[KP];
+#pragma unroll
+    for (int q = 0; q < KP; ++q) {
+      const int t = threadIdx.x + q * blockDim.x;
+      pd[q] = -1;
+      if (t < items) pv[q] = patch_item(t, z + 2, z + 1, pd[q]);
+    }
+    const bool okq = wait_q(z + 2), oku = wait_u(z + 1);
+    if (okq && oku) {
+#pragma unroll
+      for (int q = 0; q < KP; ++q)
+        if (pd[q] >= 0) base[pd[q]] = pv[q];
+      for (int t = threadIdx.x + KP * blockDim.x; t < items; t += blockDim.x) {
+        int d;
+        const real v = patch_item(t, z + 2, z + 1, d);
+        base[d] = v;
+      }
+    }
     __syncthreads();
     if (*abort_flag) {
       aborted = true;
@@ -412,8 +474,10 @@ __device__ __forceinline__ void qside_body(const CUtensorMap* tmQ, const CUtenso
   }
 }
 
+// FP32: two CTAs per SM (shared memory allows two; the bound keeps the registers within it)
 template <typename real, int TY, int SPT>
-__global__ void __launch_bounds__(qside_threads<TY, SPT>()) k_qside(const __grid_constant__ CUtensorMap tmQ,
+__global__ void __launch_bounds__(qside_threads<TY, SPT>(), sizeof(real) == 4 ? 2 : 1)
+    k_qside(const __grid_constant__ CUtensorMap tmQ,
                                                      const __grid_constant__ CUtensorMap tmU, ZmGeom G,
                                                      Model<real> m, const real* __restrict__ Q,
                                                      const real* __restrict__ rhou, const real* __restrict__ bext,
@@ -454,7 +518,7 @@ __device__ __forceinline__ ZmGeom zm_class_geom(const ZmBatch& B, int k) {
 }
 
 template <typename real, int TY>
-__global__ void __launch_bounds__(qside_threads<TY, 1>(), 2) k_qside_batch(const __grid_constant__ ZmBatchMaps maps,
+__global__ void __launch_bounds__(qside_threads<TY, 1>(), sizeof(real) == 4 ? 2 : 1) k_qside_batch(const __grid_constant__ ZmBatchMaps maps,
                                                          ZmBatch B, const Replica<real>* __restrict__ reps,
                                                          const int* __restrict__ order, const real* __restrict__ Q,
                                                          const real* __restrict__ rhou, real* __restrict__ sigma,
@@ -559,15 +623,46 @@ __device__ __forceinline__ void lbq_body(const CUtensorMap* tmU, const CUtensorM
   };
   auto wait = [&](int p) {
     const int k = p - (z0 - 1);
-    if (!mbar_wait_bounded(&bars[k % L::SLOTS], (k / L::SLOTS) & 1, kWaitLimitNs)) {
-      *abort_flag = 1;
-    } else if (edge) {
-      real* sl = slot(p);
-      const int zz = wrap(p, nz);
-      patch_plane(sl, 4, L::ROWS, 3, ZM_TX + 5, rhou, n, nx, ny, zz, x0, y0 - 1);
-      patch_plane(sl + L::OFF_S, 5, L::ROWS, 3, ZM_TX + 5, sigma, n, nx, ny, zz, x0, y0 - 1);
-      patch_plane(sl + L::OFF_B, 3, L::ROWS, 3, ZM_TX + 5, bf, n, nx, ny, zz, x0, y0 - 1);
-      patch_plane(sl + L::OFF_Q, 5, L::ROWS, 3, ZM_TX + 5, Qs, n, nx, ny, zz, x0, y0 - 1);
+    const bool ok = mbar_wait_bounded(&bars[k % L::SLOTS], (k / L::SLOTS) & 1, kWaitLimitNs);
+    if (!ok) *abort_flag = 1;
+    return ok;
+  };
+  // Periodic halo of edge tiles: item t is component t % 17 of frame cell
+  // t / 17 of plane p, over the slot's groups [drho ux uy uz | sigma | b | Q*].
+  // patch_item returns its value and its index in the ring.
+  const Frame<L::ROWS, 3, ZM_TX + 5> F(nx, ny, x0, y0 - 1);
+  const int items = edge ? F.cells() * 17 : 0;
+  auto patch_item = [&](int t, int p, int& dst) -> real {
+    const int cell = t / 17, comp = t - 17 * cell;
+    int r, c;
+    F.cell(cell, r, c);
+    const real* g;
+    int k, off;
+    if (comp < 4) {
+      g = rhou;
+      k = comp;
+      off = 0;
+    } else if (comp < 9) {
+      g = sigma;
+      k = comp - 4;
+      off = L::OFF_S;
+    } else if (comp < 12) {
+      g = bf;
+      k = comp - 9;
+      off = L::OFF_B;
+    } else {
+      g = Qs;
+      k = comp - 12;
+      off = L::OFF_Q;
+    }
+    dst = (int)(slot(p) - ring) + off + (k * L::ROWS + r) * ZM_BX + c;
+    return g[k * n + image_site(r, c, nx, ny, wrap(p, nz), x0, y0 - 1)];
+  };
+  auto patch = [&](int p) {
+    for (int t = threadIdx.x; t < items; t += blockDim.x) {
+      int d;
+      const real v = patch_item(t, p, d);
+      ring[d] = v;
     }
   };
   // neighbour data: component k of [drho ux uy uz | sigma | b] at box index idx
@@ -585,8 +680,8 @@ __device__ __forceinline__ void lbq_body(const CUtensorMap* tmU, const CUtensorM
   bool aborted = false;
   if (threadIdx.x == 0)
     for (int p = z0 - 1; p <= z0 + 1; ++p) issue(p);
-  wait(z0 - 1);
-  wait(z0);
+  if (wait(z0 - 1)) patch(z0 - 1);
+  if (wait(z0)) patch(z0);
 
   // periodic source coordinates of the pull
   const int xm = wrap(gx - 1, nx), xp = wrap(gx + 1, nx);
@@ -621,7 +716,27 @@ __device__ __forceinline__ void lbq_body(const CUtensorMap* tmU, const CUtensorM
         }
       }
     }
-    wait(z + 1);
+    // the periodic images for plane z+1 are loaded before its wait (they do
+    // not depend on the copy) and stored after it
+    constexpr int KP = 3;
+    real pv[KP];
+    int pd[KP];
+#pragma unroll
+    for (int q = 0; q < KP; ++q) {
+      const int t = threadIdx.x + q * blockDim.x;
+      pd[q] = -1;
+      if (t < items) pv[q] = patch_item(t, z + 1, pd[q]);
+    }
+    if (wait(z + 1)) {
+#pragma unroll
+      for (int q = 0; q < KP; ++q)
+        if (pd[q] >= 0) ring[pd[q]] = pv[q];
+      for (int t = threadIdx.x + KP * blockDim.x; t < items; t += blockDim.x) {
+        int d;
+        const real v = patch_item(t, z + 1, d);
+        ring[d] = v;
+      }
+    }
     __syncthreads();
     if (*abort_flag) {
       aborted = true;
