@@ -40,34 +40,49 @@ __device__ __forceinline__ int wrap(int v, int n) {
   return v < 0 ? v + n : v;
 }
 
-// The out-of-range cells of a staged plane (edge tiles).  Layout
-// [comp][row][ZM_BX]; row r <-> global y = gy0 + r, column c <-> global
-// x = x0 - ZM_XOFF + c; only rows [0, ROWS) and columns [C0, C1) are needed.
-// The cells inside the lattice form one rectangle, so the frame around it is
-// enumerated as the rows above and below it, then the columns left and right
-// of it.  TMA zero-fills these cells; the kernels overwrite them with their
-// periodic images.
-template <int ROWS, int C0, int C1>
+// The out-of-range cells of a staged plane (edge tiles) that the tile reads.
+// Layout [comp][row][ZM_BX]; row r <-> global y = gy0 + r, column c <->
+// global x = x0 - ZM_XOFF + c.  The kernel reads rows [0, ROWS) and columns
+// [C0, C1), but with a halo of H only up to y = ny - 1 + H and x = nx - 1 + H
+// (a ragged tile's lanes past the lattice edge store nothing), so the window
+// is cut there.  The window's cells inside the lattice form one rectangle,
+// and the frame around it is enumerated as the rows above and below it, then
+// the columns left and right of it.  TMA zero-fills these cells; the kernels
+// overwrite them with their periodic images.
+template <int ROWS, int C0, int C1, int H, bool FAST_DIV>
 struct Frame {
-  static constexpr int W = C1 - C0;
-  int ra, rb, lw, rw;  // in-lattice rows [ra, rb); out-of-range columns left / right
+  int rmax, w, ra, rb, lw, rw;  // window rows [0, rmax), columns [C0, C0 + w); in-lattice rows [ra, rb)
   __device__ __forceinline__ Frame(int nx, int ny, int x0, int gy0) {
+    rmax = min(ROWS, ny + H - gy0);
+    w = min(C1, nx + H - x0 + ZM_XOFF) - C0;
     ra = max(0, -gy0);
-    rb = min(ROWS, ny - gy0);
+    rb = min(rmax, ny - gy0);
     lw = max(C0, ZM_XOFF - x0) - C0;
-    rw = C1 - min(C1, nx - x0 + ZM_XOFF);
+    rw = C0 + w - min(C0 + w, nx - x0 + ZM_XOFF);
   }
-  __device__ __forceinline__ int cells() const { return (ROWS - (rb - ra)) * W + (rb - ra) * (lw + rw); }
+  __device__ __forceinline__ int cells() const { return (rmax - (rb - ra)) * w + (rb - ra) * (lw + rw); }
+  // t / w and t % w (FAST_DIV: with a constant divisor when the window is not cut)
+  __device__ __forceinline__ void divw(int t, int& q, int& m) const {
+    if (FAST_DIV && w == C1 - C0) {
+      q = t / (C1 - C0);
+      m = t % (C1 - C0);
+    } else {
+      q = t / w;
+      m = t - q * w;
+    }
+  }
   // row and column of cell t < cells()
   __device__ __forceinline__ void cell(int t, int& r, int& c) const {
-    const int n_top = ra * W, n_tb = n_top + (ROWS - rb) * W, n_tbl = n_tb + (rb - ra) * lw;
+    const int n_top = ra * w, n_tb = n_top + (rmax - rb) * w, n_tbl = n_tb + (rb - ra) * lw;
+    int q, m;
     if (t < n_top) {
-      r = t / W;
-      c = C0 + t % W;
+      divw(t, q, m);
+      r = q;
+      c = C0 + m;
     } else if (t < n_tb) {
-      const int u = t - n_top;
-      r = rb + u / W;
-      c = C0 + u % W;
+      divw(t - n_top, q, m);
+      r = rb + q;
+      c = C0 + m;
     } else if (t < n_tbl) {
       const int u = t - n_tb;
       r = ra + u / lw;
@@ -75,7 +90,7 @@ struct Frame {
     } else {
       const int u = t - n_tbl;
       r = ra + u / rw;
-      c = C1 - rw + u % rw;
+      c = C0 + w - rw + u % rw;
     }
   }
 };
@@ -261,8 +276,8 @@ __device__ __forceinline__ void qside_body(const CUtensorMap* tmQ, const CUtenso
   // Periodic halo of edge tiles: item t is one component of a frame cell of
   // the Q plane pq (t < items_q, 5 components) or of the rho u plane pu (4).
   // patch_item returns its value and its index in shared memory.
-  const Frame<L::QROWS, 2, ZM_TX + 6> FQ(nx, ny, x0, y0 - 2);
-  const Frame<L::UROWS, 3, ZM_TX + 5> FU(nx, ny, x0, y0 - 1);
+  const Frame<L::QROWS, 2, ZM_TX + 6, 2, true> FQ(nx, ny, x0, y0 - 2);
+  const Frame<L::UROWS, 3, ZM_TX + 5, 1, true> FU(nx, ny, x0, y0 - 1);
   const int items_q = edge_q ? FQ.cells() * 5 : 0, items = items_q + (edge_u ? FU.cells() * 4 : 0);
   auto patch_item = [&](int t, int pq, int pu, int& dst) -> real {
     int r, c;
@@ -630,8 +645,9 @@ __device__ __forceinline__ void lbq_body(const CUtensorMap* tmU, const CUtensorM
   // Periodic halo of edge tiles: item t is component t % 17 of frame cell
   // t / 17 of plane p, over the slot's groups [drho ux uy uz | sigma | b | Q*].
   // patch_item returns its value and its index in the ring.
-  const Frame<L::ROWS, 3, ZM_TX + 5> F(nx, ny, x0, y0 - 1);
+  const Frame<L::ROWS, 3, ZM_TX + 5, 1, false> F(nx, ny, x0, y0 - 1);
   const int items = edge ? F.cells() * 17 : 0;
+  const bool small_frame = items <= (int)blockDim.x;  // one value per thread in the loop
   auto patch_item = [&](int t, int p, int& dst) -> real {
     const int cell = t / 17, comp = t - 17 * cell;
     int r, c;
@@ -682,6 +698,9 @@ __device__ __forceinline__ void lbq_body(const CUtensorMap* tmU, const CUtensorM
     for (int p = z0 - 1; p <= z0 + 1; ++p) issue(p);
   if (wait(z0 - 1)) patch(z0 - 1);
   if (wait(z0)) patch(z0);
+  if (small_frame && wait(z0 + 1)) patch(z0 + 1);
+  real v_ahead = real(0);  // small frames: the image value read one plane ahead
+  int d_ahead = -1;
 
   // periodic source coordinates of the pull
   const int xm = wrap(gx - 1, nx), xp = wrap(gx + 1, nx);
@@ -716,8 +735,11 @@ __device__ __forceinline__ void lbq_body(const CUtensorMap* tmU, const CUtensorM
         }
       }
     }
-    // the periodic images for plane z+1 are loaded before its wait (they do
-    // not depend on the copy) and stored after it
+    // Periodic images of edge tiles.  Small frames (one value per thread):
+    // the value for plane z+2 is read here and stored after the wait of the
+    // next iteration, so that its latency hides behind this plane's work.
+    // Larger frames: the values for plane z+1 are read here, beside the
+    // pulled populations, and stored after its wait.
     constexpr int KP = 3;
     real pv[KP];
     int pd[KP];
@@ -725,9 +747,14 @@ __device__ __forceinline__ void lbq_body(const CUtensorMap* tmU, const CUtensorM
     for (int q = 0; q < KP; ++q) {
       const int t = threadIdx.x + q * blockDim.x;
       pd[q] = -1;
-      if (t < items) pv[q] = patch_item(t, z + 1, pd[q]);
+      if (small_frame ? q == 0 && z + 2 <= z1 && t < items : t < items)
+        pv[q] = patch_item(t, small_frame ? z + 2 : z + 1, pd[q]);
     }
-    if (wait(z + 1)) {
+    const bool landed = wait(z + 1);
+    if (landed && small_frame && d_ahead >= 0) ring[d_ahead] = v_ahead;
+    v_ahead = pv[0];
+    d_ahead = small_frame ? pd[0] : -1;
+    if (landed && !small_frame) {
 #pragma unroll
       for (int q = 0; q < KP; ++q)
         if (pd[q] >= 0) ring[pd[q]] = pv[q];
