@@ -645,7 +645,7 @@ __device__ __forceinline__ void lbq_body(const CUtensorMap* tmU, const CUtensorM
   // Periodic halo of edge tiles: item t is component t % 17 of frame cell
   // t / 17 of plane p, over the slot's groups [drho ux uy uz | sigma | b | Q*].
   // patch_item returns its value and its index in the ring.
-  const Frame<L::ROWS, 3, ZM_TX + 5, 1, false> F(nx, ny, x0, y0 - 1);
+  const Frame<L::ROWS, 3, ZM_TX + 5, 1, true> F(nx, ny, x0, y0 - 1);
   const int items = edge ? F.cells() * 17 : 0;
   const bool small_frame = items <= (int)blockDim.x;  // one value per thread in the loop
   auto patch_item = [&](int t, int p, int& dst) -> real {
