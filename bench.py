@@ -46,15 +46,15 @@ KERNELS_FAST = ["qside", "lbq"]
 KERNELS_GENERIC = ["field", "force_predict", "lb_correct"]
 STATE_BYTES = (15 + 5) * 2 * 4  # read + write of f and Q once per site-step (FP32)
 # DRAM bytes per site of one launch of each fast kernel (dram__bytes_read.sum +
-# dram__bytes_write.sum), from an ncu capture of 160^3 FP32 at the 256^3 tuning
-# (16 planes per CTA, one site per thread); summary and command in
+# dram__bytes_write.sum), from an ncu capture of 160^3 FP32 near the 256^3
+# tuning (20 planes per CTA, one site per thread); summary and command in
 # profiles/step_256cube_fast_path.md.  Traffic per launch scales with the sites.
 # Valid only for the kernel sources it was taken on (hash below); otherwise null.
 MEASURED_TRAFFIC = {
     "sources": ["paper_0901_3293_gb300/csrc/zmarch.cu", "paper_0901_3293_gb300/csrc/common.cuh",
                 "paper_0901_3293_gb300/csrc/tma.cuh"],
-    "sha256_16": "eb19e476c9de655a",
-    "bytes_per_site": {"qside": (164382976 + 168876544) / 160 ** 3, "lbq": (843158016 + 362482432) / 160 ** 3},
+    "sha256_16": "9db3e0d1052ce40a",
+    "bytes_per_site": {"qside": (160696832 + 166658816) / 160 ** 3, "lbq": (651194368 + 358619392) / 160 ** 3},
 }
 ORACLE_SAMPLE = 32  # side of the periodic cube the oracle steps (two BPII unit cells)
 
