@@ -312,6 +312,12 @@ __device__ __forceinline__ void qside_body(const CUtensorMap* tmQ, const CUtenso
   // H and tau of plane p on the tile plus a one-site ring (Q planes p-1..p+1);
   // a thread takes cells (r, c) and (r + TROWS / SPT, c) together
   const Model<V> mv = widen<V>(m);
+  // With one site per thread, threads 0 .. TY*32-1 take the tile's own cells
+  // in the order of the output pass and keep the gradients of their cell in
+  // registers for it (dq_next); H goes through hslot; the ring cells go to
+  // the threads after them.  With two sites per thread the output pass
+  // recomputes the gradients from the staged Q.
+  Sym5<V> dq_next[3];
   auto field_plane = [&](int p) {
     const bool own = p >= z0 && p < z1;
     const real* qm = qslot(p - 1);
@@ -319,6 +325,63 @@ __device__ __forceinline__ void qside_body(const CUtensorMap* tmQ, const CUtenso
     const real* qp = qslot(p + 1);
     real* tp = tslot(p);
     real* hp = hslot(p);
+    if constexpr (SPT == 1) {
+      constexpr int NIN = TY * ZM_TX, TC = L::TCOLS;
+      const int t = threadIdx.x;
+      int r = -1, c = 0;
+      if (t < NIN) {
+        r = t / ZM_TX + 1;
+        c = t % ZM_TX + 1;
+      } else {
+        const int u = t - NIN;
+        if (u < TC) {
+          r = 0;
+          c = u;
+        } else if (u < 2 * TC) {
+          r = L::TROWS - 1;
+          c = u - TC;
+        } else if (u < 2 * TC + TY) {
+          r = u - 2 * TC + 1;
+          c = 0;
+        } else if (u < 2 * TC + 2 * TY) {
+          r = u - 2 * TC - TY + 1;
+          c = TC - 1;
+        }
+      }
+      if (r >= 0) {
+        const int i0 = (r + 1) * ZM_BX + (c + 3);  // position in the Q box
+        Stencil7<V> st;
+        st.c = ld5v<1>(qc, L::QCS, i0, i0);
+        st.xm = ld5v<1>(qc, L::QCS, i0 - 1, i0 - 1);
+        st.xp = ld5v<1>(qc, L::QCS, i0 + 1, i0 + 1);
+        st.ym = ld5v<1>(qc, L::QCS, i0 - ZM_BX, i0 - ZM_BX);
+        st.yp = ld5v<1>(qc, L::QCS, i0 + ZM_BX, i0 + ZM_BX);
+        st.zm = ld5v<1>(qm, L::QCS, i0, i0);
+        st.zp = ld5v<1>(qp, L::QCS, i0, i0);
+        Sym5<V> dq[3];
+        const Sym5<V> h = molecular_field(st, mv, dq);
+        Sym5<V> sg;
+        V tu[3];
+        lc_stress(st.c, h, mv.xi, sg, tu);
+        const int ti = r * TC + c;
+        tp[ti] = tu[0];
+        tp[L::TROWS * TC + ti] = tu[1];
+        tp[2 * L::TROWS * TC + ti] = tu[2];
+        if (t < NIN) {
+          hp[0 * NIN + t] = h.xx;
+          hp[1 * NIN + t] = h.xy;
+          hp[2 * NIN + t] = h.xz;
+          hp[3 * NIN + t] = h.yy;
+          hp[4 * NIN + t] = h.yz;
+          dq_next[0] = dq[0];
+          dq_next[1] = dq[1];
+          dq_next[2] = dq[2];
+          const int sx = x0 + c - 1, sy = y0 + r - 1;
+          if (own && sx < nx && sy < ny) store5_lane<1, real>(sigma, n, ((long long)p * ny + sy) * nx + sx, sg, 0);
+        }
+      }
+      return;
+    }
     constexpr int RH = L::TROWS / SPT;
     for (int t = threadIdx.x; t < RH * L::TCOLS; t += blockDim.x) {
       const int r0 = t / L::TCOLS, c = t % L::TCOLS;
@@ -414,6 +477,8 @@ __device__ __forceinline__ void qside_body(const CUtensorMap* tmQ, const CUtenso
       if (z + 3 <= z1 + 1) issue_q(z + 3);
       if (z + 2 <= z1) issue_u(z + 2);
     }
+    // H and the gradients of plane z, kept from the previous pass (one site per thread)
+    const Sym5<V> dq_cur[3] = {dq_next[0], dq_next[1], dq_next[2]};
     field_plane(z + 1);
     __syncthreads();
     if (ty < TYH && gx < nx && y0 + ty < ny) {
@@ -422,13 +487,21 @@ __device__ __forceinline__ void qside_body(const CUtensorMap* tmQ, const CUtenso
       const real* qp = qslot(z + 1);
       const int qi0 = (ty + 2) * ZM_BX + (tx + ZM_XOFF), qi1 = qi0 + TYH * ZM_BX;
       const Sym5<V> q = ld5v<SPT>(qc, L::QCS, qi0, qi1);
-      Sym5<V> dq[3];
-      dq[0] = half_diff(ld5v<SPT>(qc, L::QCS, qi0 + 1, qi1 + 1), ld5v<SPT>(qc, L::QCS, qi0 - 1, qi1 - 1));
-      dq[1] = half_diff(ld5v<SPT>(qc, L::QCS, qi0 + ZM_BX, qi1 + ZM_BX),
-                        ld5v<SPT>(qc, L::QCS, qi0 - ZM_BX, qi1 - ZM_BX));
-      dq[2] = half_diff(ld5v<SPT>(qp, L::QCS, qi0, qi1), ld5v<SPT>(qm, L::QCS, qi0, qi1));
-      const int hi0 = ty * ZM_TX + tx;
-      const Sym5<V> h = ld5v<SPT>(hslot(z), TY * ZM_TX, hi0, hi0 + TYH * ZM_TX);
+      Sym5<V> dq[3], h;
+      if constexpr (SPT == 1) {
+        dq[0] = dq_cur[0];
+        dq[1] = dq_cur[1];
+        dq[2] = dq_cur[2];
+        const int hi0 = ty * ZM_TX + tx;
+        h = ld5v<SPT>(hslot(z), TY * ZM_TX, hi0, hi0);
+      } else {
+        dq[0] = half_diff(ld5v<SPT>(qc, L::QCS, qi0 + 1, qi1 + 1), ld5v<SPT>(qc, L::QCS, qi0 - 1, qi1 - 1));
+        dq[1] = half_diff(ld5v<SPT>(qc, L::QCS, qi0 + ZM_BX, qi1 + ZM_BX),
+                          ld5v<SPT>(qc, L::QCS, qi0 - ZM_BX, qi1 - ZM_BX));
+        dq[2] = half_diff(ld5v<SPT>(qp, L::QCS, qi0, qi1), ld5v<SPT>(qm, L::QCS, qi0, qi1));
+        const int hi0 = ty * ZM_TX + tx;
+        h = ld5v<SPT>(hslot(z), TY * ZM_TX, hi0, hi0 + TYH * ZM_TX);
+      }
       // body force; tau = [xy, xz, yz] with tau_yx = -tau_xy etc.
       const real* tm = tslot(z - 1);
       const real* tc = tslot(z);

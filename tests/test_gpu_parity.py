@@ -205,8 +205,11 @@ def test_external_force_kolmogorov(lcbp, dtype, tol):
     assert np.abs(lat.read_u()).max() > 1e-5
 
 
+# (nz, ny, nx): cubes, and ragged tiles in x (36 and 68: 4 lanes of the last
+# column tile in the lattice) and in y (13, 9) over several z-chunks, so that
+# edge tiles of every kind patch their periodic frames through many planes
 @pytest.mark.parametrize("fast", ["PATH_FAST1", "PATH_FAST2"])
-@pytest.mark.parametrize("shape", [(32, 32, 32), (6, 10, 36), (64, 64, 64)])
+@pytest.mark.parametrize("shape", [(32, 32, 32), (6, 10, 36), (64, 64, 64), (45, 13, 36), (20, 9, 68)])
 def test_fast_path_matches_generic_f32(lcbp, shape, fast):
     """Both kernel sets compute the same FP32 step (op order differs slightly)."""
     p = lbq.Params()
