@@ -44,6 +44,10 @@ struct ConvSmem {
 
 __device__ __forceinline__ float bf2f(__nv_bfloat16 v) { return __bfloat162float(v); }
 
+// shared-memory position of weight tap t = 9 (dz + 1) + 3 (dy + 1) + (dx + 1):
+// the weights are staged shift-major, [in-plane shift][dz][C_out][C_in]
+__host__ __device__ constexpr int w_slot(int t) { return (t % 9) * 3 + t / 9; }
+
 
 // Epilogue of channels c0 .. c0 + NC of one output site (x, y, z): bias from
 // registers, residual / mask operands already loaded (BF16, 8 per uint4).
@@ -191,7 +195,7 @@ __global__ void __launch_bounds__(kConvThreads) k_conv_tc(const __grid_constant_
       tma_prefetch_desc(&tmA);
       tma_prefetch_desc(&tmW);
       mbar_arrive_expect_tx(wbar, 27 * COUT * CIN * 2);
-      tma_load_3d(wsm, &tmW, 0, 0, 0, wbar);
+      tma_load_4d(wsm, &tmW, 0, 0, 0, 0, wbar);
       int k = 0;
       for (int tile = blockIdx.x; tile < ntiles && !*abort_flag; tile += gridDim.x) {
         const int x0 = (tile % tiles_x) * 32, y0 = ((tile / tiles_x) % tiles_y) * 4, z0 = tile / (tiles_x * tiles_y);
@@ -230,7 +234,7 @@ __global__ void __launch_bounds__(kConvThreads) k_conv_tc(const __grid_constant_
           for (int kk = 0; kk < CIN / 16; ++kk) {
             // A: [group][128 sites][8 channels], 16 B per site; one K step = two groups
             const uint64_t ad = umma_sdesc_noswz(st_addr + s * L::STAGE + kk * 2 * 2048, 2048u, 128u);
-            const uint64_t bd = umma_sdesc(w_addr + t * (COUT * CIN * 2) + kk * 32, L::SBO, L::SWZ);
+            const uint64_t bd = umma_sdesc(w_addr + w_slot(t) * (COUT * CIN * 2) + kk * 32, L::SBO, L::SWZ);
             umma_bf16(d_tmem, ad, bd, idesc, (t > 0 || kk > 0) ? 1u : 0u);
           }
           umma_commit(&empty[s]);
@@ -310,7 +314,7 @@ struct WinSmem {
   static constexpr int NBARS = kWinPipes * PBARS + 1;
   static constexpr uint32_t SWZ = CIN == 32 ? kSwizzle64B : kSwizzle32B;
   static constexpr uint32_t WSBO = 8 * CIN * 2;
-  static constexpr uint32_t PIPE_COLS = kWinAcc * COUT;
+  static constexpr uint32_t PIPE_COLS = kWinAcc * 2 * COUT;  // an accumulator stage holds two output planes
   static constexpr uint32_t TMEM_COLS = kWinPipes * PIPE_COLS < 32 ? 32 : kWinPipes * PIPE_COLS;
 };
 
@@ -338,14 +342,17 @@ __global__ void __launch_bounds__(kWinThreads) k_conv_win(const void* __restrict
   uint64_t* acce = accf + kWinAcc;
   uint64_t* done = acce + kWinAcc;
 
-  // this pipeline's items: (tile T, plane z) with z fastest, a contiguous share
-  // of the CTA's range; every role walks them with incremental 32-bit counters
-  const long long items = (long long)g.ntiles * a.nz;
+  // this pipeline's items: (tile T, plane pair k) with k fastest, a contiguous
+  // share of the CTA's range; pair k is output planes 2k and 2k + 1 (2k alone
+  // when nz is odd and k is the last); every role walks them with incremental
+  // 32-bit counters
+  const int npairs = (a.nz + 1) / 2;
+  const long long items = (long long)g.ntiles * npairs;
   const long long cbeg = items * blockIdx.x / gridDim.x, cend = items * (blockIdx.x + 1) / gridDim.x;
   const long long jbeg = cbeg + (cend - cbeg) * pipe / kWinPipes;
   const long long jend = cbeg + (cend - cbeg) * (pipe + 1) / kWinPipes;
   const int nitems = (int)(jend - jbeg);
-  const int T0 = (int)(jbeg / a.nz), z0 = (int)(jbeg % a.nz);
+  const int T0 = (int)(jbeg / npairs), k0 = (int)(jbeg % npairs);
   const long long plane = (long long)g.px * g.py;
 
   if (threadIdx.x == 0) {
@@ -390,7 +397,7 @@ __global__ void __launch_bounds__(kWinThreads) k_conv_win(const void* __restrict
       if (pipe == 0) {
         tma_prefetch_desc(&tmW);
         mbar_arrive_expect_tx(wbar, 27 * COUT * CIN * 2);
-        tma_load_3d(wsm, &tmW, 0, 0, 0, wbar);
+        tma_load_4d(wsm, &tmW, 0, 0, 0, 0, wbar);
       }
       const uint32_t tx_bytes = (uint32_t)(L::CH * g.wb * 16);
       const __nv_bfloat16* src = static_cast<const __nv_bfloat16*>(base);
@@ -398,13 +405,16 @@ __global__ void __launch_bounds__(kWinThreads) k_conv_win(const void* __restrict
       uint32_t eph = 0;  // parity of that slot's next release
       int nloads = 0;
       bool ok = true;
-      int T = T0, z = z0;
+      int T = T0, k = k0;
       for (int it = 0; ok && it < nitems; ++it) {
-        const bool first = it == 0 || z == 0;
+        const int zA = 2 * k;
+        const bool first = it == 0 || k == 0;
         // window start inside a plane: first row of the tile minus px + 1
         const long long w0 = (long long)g.l_first + (long long)T * 128 - (g.px + 1);
-        // padded planes z .. z+2 hold input planes z-1 .. z+1
-        for (int Z = first ? z : z + 2; Z <= z + 2; ++Z) {
+        // padded planes zA .. zA+3 hold input planes zA-1 .. zA+2 (zA .. zA+2 for a lone plane);
+        // a pair continuing the previous one shares its first two
+        const int zlast = zA + (zA + 1 < a.nz ? 3 : 2);
+        for (int Z = first ? zA : zA + 2; Z <= zlast; ++Z) {
           if (nloads >= kWinSlots && !bounded_wait(&empty[sl], eph)) {
             ok = false;
             break;
@@ -420,8 +430,8 @@ __global__ void __launch_bounds__(kWinThreads) k_conv_win(const void* __restrict
             if (nloads > kWinSlots) eph ^= 1u;  // load n waits for release n - S: parity (n / S - 1) & 1
           }
         }
-        if (++z == a.nz) {
-          z = 0;
+        if (++k == npairs) {
+          k = 0;
           ++T;
         }
       }
@@ -436,30 +446,38 @@ __global__ void __launch_bounds__(kWinThreads) k_conv_win(const void* __restrict
   } else if (warp >= kWinEpiWarps + kWinPipes) {
     // ---------------- MMA issuer
     if (lane == 0) {
-      constexpr uint32_t idesc = umma_idesc_bf16(128, COUT);
+      constexpr uint32_t idesc1 = umma_idesc_bf16(128, COUT), idesc2 = umma_idesc_bf16(128, 2 * COUT);
       // descriptors are advanced by adding (byte offset >> 4) to the start-address field
       const uint64_t bdesc0 = umma_sdesc(smem_addr(wsm), L::WSBO, L::SWZ);
       const uint64_t adesc0 = umma_sdesc_noswz(smem_addr(slots), g.lbo, 128u);
       const uint32_t slot16 = g.slot_bytes >> 4, lbo16 = g.lbo >> 4;
       const int px = g.px;
+      // weights of in-plane shift sh and z-offset dz, K chunk kc (staged [shift][dz][C_out][C_in])
+      auto wdesc = [&](int sh, int dz, int kc) {
+        return bdesc0 + (uint64_t)((((sh * 3 + dz + 1) * (COUT * CIN * 2)) + kc * 32) >> 4);
+      };
+      // row shift of in-plane shift sh in 16-byte units: px + 1 + dy px + dx
+      auto row16 = [&](int sh) { return (uint32_t)(px + 1 + (sh / 3 - 1) * px + (sh % 3 - 1)); };
       bool ok = bounded_wait(wbar, 0);
-      // ring state of the loads: the three planes of the current item, oldest first
-      int ps[3] = {0, 0, 0};
-      uint32_t pph[3] = {0, 0, 0};
+      // ring state of the loads: the planes of the current item, oldest first
+      int ps[4] = {0, 0, 0, 0};
+      uint32_t pph[4] = {0, 0, 0, 0};
       int nsl = 0;       // slot of the next load to consume
       uint32_t nph = 0;  // its full-barrier parity
       int acc = 0;
       uint32_t aph = 0;  // accumulator-free parity
-      int z = z0;
+      int k = k0;
       for (int it = 0; ok && it < nitems; ++it) {
-        const bool first = it == 0 || z == 0;
-        for (int d = first ? 0 : 2; d < 3; ++d) {
-          if (!first) {
-            ps[0] = ps[1];
-            pph[0] = pph[1];
-            ps[1] = ps[2];
-            pph[1] = pph[2];
-          }
+        const int zA = 2 * k;
+        const bool pair = zA + 1 < a.nz, first = it == 0 || k == 0;
+        const int np = pair ? 4 : 3;
+        if (!first) {
+          ps[0] = ps[2];
+          pph[0] = pph[2];
+          ps[1] = ps[3];
+          pph[1] = pph[3];
+        }
+        for (int d = first ? 0 : 2; d < np; ++d) {
           ps[d] = nsl;
           pph[d] = nph;
           if (++nsl == kWinSlots) {
@@ -469,36 +487,68 @@ __global__ void __launch_bounds__(kWinThreads) k_conv_win(const void* __restrict
         }
         if (it >= kWinAcc && !bounded_wait(&acce[acc], aph ^ 1u)) break;
         // planes already seen complete by the previous item stay loaded until released
-        for (int d = first ? 0 : 2; d < 3; ++d)
+        for (int d = first ? 0 : 2; d < np; ++d)
           if (!bounded_wait(&full[ps[d]], pph[d])) ok = false;
         if (!ok) break;
         tc_fence_after();
-        const uint32_t d_tmem = tmem_base + acc * COUT;
-        const uint64_t ab0 = adesc0 + (uint64_t)ps[0] * slot16, ab1 = adesc0 + (uint64_t)ps[1] * slot16,
-                       ab2 = adesc0 + (uint64_t)ps[2] * slot16;
+        // accumulator stage: block 0 (columns [0, COUT)) = output plane zA+1, block 1 = zA
+        const uint32_t d0 = tmem_base + acc * 2 * COUT, d1 = d0 + COUT;
+        uint64_t ab[4];
 #pragma unroll
-        for (int t = 0; t < 27; ++t) {
-          const int dx = t % 3 - 1, dy = (t / 3) % 3 - 1, dz = t / 9;
-          // row shift of the tap in 16-byte units: px + 1 + dy px + dx
-          const uint32_t row16 = (uint32_t)(px + 1 + dy * px + dx);
-          const uint64_t ab = dz == 0 ? ab0 : (dz == 1 ? ab1 : ab2);
+        for (int d = 0; d < 4; ++d) ab[d] = adesc0 + (uint64_t)ps[d] * slot16;
+        if (pair) {
+          // input plane zA-1 feeds plane zA only (dz = -1), into block 1
 #pragma unroll
-          for (int kc = 0; kc < CIN / 16; ++kc)
-            umma_bf16(d_tmem, ab + row16 + 2u * kc * lbo16, bdesc0 + (uint64_t)((t * (COUT * CIN * 2) + kc * 32) >> 4),
-                      idesc, (t > 0 || kc > 0) ? 1u : 0u);
+          for (int sh = 0; sh < 9; ++sh)
+#pragma unroll
+            for (int kc = 0; kc < CIN / 16; ++kc)
+              umma_bf16(d1, ab[0] + row16(sh) + 2u * kc * lbo16, wdesc(sh, -1, kc), idesc1,
+                        (sh > 0 || kc > 0) ? 1u : 0u);
+          umma_commit(&empty[ps[0]]);
+          // input plane zA+2 feeds plane zA+1 only (dz = +1), into block 0
+#pragma unroll
+          for (int sh = 0; sh < 9; ++sh)
+#pragma unroll
+            for (int kc = 0; kc < CIN / 16; ++kc)
+              umma_bf16(d0, ab[3] + row16(sh) + 2u * kc * lbo16, wdesc(sh, 1, kc), idesc1,
+                        (sh > 0 || kc > 0) ? 1u : 0u);
+          // input plane zA feeds both: B rows [W(dz = -1); W(dz = 0)] -> blocks 0 (zA+1) and 1 (zA)
+#pragma unroll
+          for (int sh = 0; sh < 9; ++sh)
+#pragma unroll
+            for (int kc = 0; kc < CIN / 16; ++kc)
+              umma_bf16(d0, ab[1] + row16(sh) + 2u * kc * lbo16, wdesc(sh, -1, kc), idesc2, 1u);
+          umma_commit(&empty[ps[1]]);
+          // input plane zA+1 feeds both: B rows [W(dz = 0); W(dz = +1)] -> blocks 0 (zA+1) and 1 (zA)
+#pragma unroll
+          for (int sh = 0; sh < 9; ++sh)
+#pragma unroll
+            for (int kc = 0; kc < CIN / 16; ++kc)
+              umma_bf16(d0, ab[2] + row16(sh) + 2u * kc * lbo16, wdesc(sh, 0, kc), idesc2, 1u);
+        } else {
+          // a lone plane zA: all 27 taps from input planes zA-1 .. zA+1, into block 1
+#pragma unroll
+          for (int t = 0; t < 27; ++t) {
+            const int sh = t % 9, dz = t / 9 - 1;
+#pragma unroll
+            for (int kc = 0; kc < CIN / 16; ++kc)
+              umma_bf16(d1, ab[dz + 1] + row16(sh) + 2u * kc * lbo16, wdesc(sh, dz, kc), idesc1,
+                        (t > 0 || kc > 0) ? 1u : 0u);
+          }
+          umma_commit(&empty[ps[0]]);
+          umma_commit(&empty[ps[1]]);
         }
         umma_commit(&accf[acc]);
         if (++acc == kWinAcc) {
           acc = 0;
           aph ^= 1u;
         }
-        if (++z == a.nz) z = 0;
+        if (++k == npairs) k = 0;
         // release the planes the next item does not share with this one
-        const bool cont = it + 1 < nitems && z != 0;
-        umma_commit(&empty[ps[0]]);
+        const bool cont = it + 1 < nitems && k != 0;
         if (!cont) {
-          umma_commit(&empty[ps[1]]);
           umma_commit(&empty[ps[2]]);
+          if (pair) umma_commit(&empty[ps[3]]);
         }
       }
       // every issued MMA has finished before the CTA leaves
@@ -513,29 +563,15 @@ __global__ void __launch_bounds__(kWinThreads) k_conv_win(const void* __restrict
     float bias[COUT];
 #pragma unroll
     for (int c = 0; c < COUT; ++c) bias[c] = (EPI & kEpiBias) ? a.bias[c] : 0.f;
-    int T = T0, z = z0;
+    int T = T0, k = k0;
     // padded (X, Y) of this thread's row of tile T, advanced by 128 positions per tile
     int l = g.l_first + T * 128 + m;
     int Y = l / g.px, X = l - Y * g.px;
     int acc = 0;
     uint32_t fph = 0;
-    for (int it = 0; it < nitems; ++it) {
-      const bool real = X >= 1 && X <= g.px - 2 && Y >= 1 && Y <= g.py - 2;
-      // residual / mask operands do not depend on the accumulator: load them first
-      uint4 rsd[COUT / 8], msk[COUT / 8];
-      if (real) {
-#pragma unroll
-        for (int q = 0; q < COUT / 8; ++q) {
-          const long long o = act_off(X, Y, z + 1, q, COUT, g.px, g.py);
-          if (EPI & kEpiResid) rsd[q] = *reinterpret_cast<const uint4*>(a.resid + o);
-          if (EPI & kEpiMask) msk[q] = *reinterpret_cast<const uint4*>(a.mask + o);
-        }
-      }
-      const bool ok = __all_sync(0xffffffffu, bounded_wait(&accf[acc], fph));
-      if (!ok) break;
-      tc_fence_after();
-      const uint32_t taddr = tmem_base + ((uint32_t)(quad * 32) << 16) + acc * COUT;
-      float v[COUT];
+    // this thread's accumulator row of block b (COUT columns) of the current stage
+    auto read_block = [&](int b, float (&v)[COUT]) {
+      const uint32_t taddr = tmem_base + ((uint32_t)(quad * 32) << 16) + acc * 2 * COUT + b * COUT;
       if constexpr (COUT == 32) {
         uint32_t r[32];
         tmem_ld32(taddr, r);
@@ -549,15 +585,42 @@ __global__ void __launch_bounds__(kWinThreads) k_conv_win(const void* __restrict
 #pragma unroll
         for (int c = 0; c < 16; ++c) v[c] = __uint_as_float(r[c]);
       }
+    };
+    // residual / mask operands of plane z (they do not depend on the accumulator)
+    auto operands = [&](int z, uint4 (&rsd)[COUT / 8], uint4 (&msk)[COUT / 8]) {
+#pragma unroll
+      for (int q = 0; q < COUT / 8; ++q) {
+        const long long o = act_off(X, Y, z + 1, q, COUT, g.px, g.py);
+        if (EPI & kEpiResid) rsd[q] = *reinterpret_cast<const uint4*>(a.resid + o);
+        if (EPI & kEpiMask) msk[q] = *reinterpret_cast<const uint4*>(a.mask + o);
+      }
+    };
+    for (int it = 0; it < nitems; ++it) {
+      const int zA = 2 * k;
+      const bool pair = zA + 1 < a.nz;
+      const bool real = X >= 1 && X <= g.px - 2 && Y >= 1 && Y <= g.py - 2;
+      uint4 rsd[COUT / 8], msk[COUT / 8];
+      if (real) operands(zA, rsd, msk);
+      const bool ok = __all_sync(0xffffffffu, bounded_wait(&accf[acc], fph));
+      if (!ok) break;
+      tc_fence_after();
+      // block 1 holds plane zA, block 0 plane zA+1 (of a pair)
+      float v[COUT], v2[COUT];
+      read_block(1, v);
+      if (pair) read_block(0, v2);
       tc_fence_before();
       mbar_arrive(&acce[acc]);
-      if (real) conv_epilogue_part<COUT, COUT, EPI>(v, bias, rsd, msk, 0, X - 1, Y - 1, z, a);
+      if (real) conv_epilogue_part<COUT, COUT, EPI>(v, bias, rsd, msk, 0, X - 1, Y - 1, zA, a);
+      if (real && pair) {
+        operands(zA + 1, rsd, msk);
+        conv_epilogue_part<COUT, COUT, EPI>(v2, bias, rsd, msk, 0, X - 1, Y - 1, zA + 1, a);
+      }
       if (++acc == kWinAcc) {
         acc = 0;
         fph ^= 1u;
       }
-      if (++z == a.nz) {
-        z = 0;
+      if (++k == npairs) {
+        k = 0;
         X += 128;
         while (X >= g.px) {
           X -= g.px;
@@ -636,9 +699,11 @@ cudaError_t conv_launch_win_t(const void* base, const CUtensorMap& tmW, const Co
     per_sm = std::max(per_sm, 1);
     attr = smem;
   }
-  // one wave of persistent CTAs, each taking an equal share of the (tile, z) items
-  const long long items = (long long)g.ntiles * a.nz;
-  const int grid = (int)std::min<long long>(items, (long long)per_sm * sms);
+  // one wave of persistent CTAs, each taking an equal share of the (tile, plane pair)
+  // items; a CTA's accumulators may fill the SM's 512 tensor-memory columns
+  const long long items = (long long)g.ntiles * ((a.nz + 1) / 2);
+  const int tmem_per_sm = std::max(1, 512 / (int)WinSmem<CIN, COUT>::TMEM_COLS);
+  const int grid = (int)std::min<long long>(items, (long long)std::min(per_sm, tmem_per_sm) * sms);
   k_conv_win<CIN, COUT, EPI><<<grid, kWinThreads, smem, s>>>(base, tmW, a, g);
   return cudaGetLastError();
 }

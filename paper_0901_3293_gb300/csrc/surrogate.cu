@@ -321,14 +321,20 @@ bool conv_maps(ConvMaps* m, void* base, int C, int nx, int ny, int nz) {
 }
 
 // weights [27][rows][K] BF16 as a 3-D tensor, one box of all taps
+// Weights [27][rows][K] with tap t = 9 (dz + 1) + 3 (dy + 1) + (dx + 1), viewed
+// as a 4-D tensor (K, rows, dz, in-plane shift) so that the one box of all taps
+// lands in shared memory shift-major: [shift][dz][rows][K].  The three z-taps of
+// one in-plane shift are then adjacent, which lets one MMA with N = 2 rows
+// apply two of them.
 bool weight_map(CUtensorMap* m, void* base, int K, int rows) {
   EncodeFn fn = encoder();
   if (!fn) return false;
-  const cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)rows, 27};
-  const cuuint64_t str[2] = {(cuuint64_t)K * 2, (cuuint64_t)K * 2 * rows};
-  const cuuint32_t box[3] = {(cuuint32_t)K, (cuuint32_t)rows, 27};
-  const cuuint32_t es[3] = {1, 1, 1};
-  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, str, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+  const cuuint64_t tap = (cuuint64_t)K * 2 * rows;
+  const cuuint64_t dims[4] = {(cuuint64_t)K, (cuuint64_t)rows, 3, 9};
+  const cuuint64_t str[3] = {(cuuint64_t)K * 2, 9 * tap, tap};
+  const cuuint32_t box[4] = {(cuuint32_t)K, (cuuint32_t)rows, 3, 9};
+  const cuuint32_t es[4] = {1, 1, 1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, base, dims, str, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
             K == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
