@@ -376,8 +376,13 @@ def run_ours(args):
     b_s = time.perf_counter() - t0
     binfo = batch.info()
     bfast, bzc = batch.path()
+    # algorithmic bytes of one step per site: the two fast kernels, or the three generic ones
+    b_bytes = (KERNEL_BYTES["qside"] + KERNEL_BYTES["lbq"]) if bfast else sum(
+        KERNEL_BYTES[k] for k in KERNELS_GENERIC)
+    b_gbps = b_bytes * bsites * args.steps / b_s / 1e9
     batch_line = {"replicas": 48, "sites": bsites, "ms_per_step": 1e3 * b_s / args.steps,
                   "MLUPS": bsites * args.steps / b_s / 1e6,
+                  "algorithmic_bytes_per_site": b_bytes, "GBps": b_gbps, "frac_of_" + peak_kind: b_gbps / peak,
                   "kernels": "fast (z-marching TMA kernels, 5-D maps per class)" if bfast else "generic",
                   "planes_per_cta": bzc if bfast else None,
                   "tile": None if bfast else binfo["tile"],
