@@ -85,11 +85,19 @@ __device__ __forceinline__ void conv_epilogue_part(float (&v)[NC], const float (
 #pragma unroll
     for (int q = 0; q < NC / 4; ++q) op[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
   } else if (EPI & kEpiUpdateQ) {
+    // all loads first: Q and the rate may alias as far as the compiler knows, and
+    // interleaved with the stores they would be five serial round trips
+    constexpr int NQ = NC < 5 ? NC : 5;
+    float qv[NQ], rv[NQ];
 #pragma unroll
-    for (int c = 0; c < NC; ++c)
-      if (c0 + c < 5)
-        a.qstate[(c0 + c) * a.n + site] +=
-            a.qscale * v[c] + (a.rate ? a.rate_scale * a.rate[(c0 + c) * a.n + site] : 0.f);
+    for (int c = 0; c < NQ; ++c) {
+      const bool in = c0 + c < 5;
+      qv[c] = in ? a.qstate[(c0 + c) * a.n + site] : 0.f;
+      rv[c] = in && a.rate ? a.rate[(c0 + c) * a.n + site] : 0.f;
+    }
+#pragma unroll
+    for (int c = 0; c < NQ; ++c)
+      if (c0 + c < 5) a.qstate[(c0 + c) * a.n + site] = qv[c] + (a.qscale * v[c] + a.rate_scale * rv[c]);
   } else {
     uint4 pk[NC / 8];
 #pragma unroll
