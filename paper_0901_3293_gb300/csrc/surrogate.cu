@@ -70,8 +70,21 @@ __global__ void k_sur_input(const float* __restrict__ q, const float* __restrict
   const int px = nx + 2, py = ny + 2, pz = nz + 2;
   const long long np = (long long)px * py * pz;
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < np; p += (long long)gridDim.x * blockDim.x) {
-    const int X = (int)(p % px), Y = (int)((p / px) % py), Z = (int)(p / ((long long)px * py));
-    const int x = (X + nx - 1) % nx, y = (Y + ny - 1) % ny, z = (Z + nz - 1) % nz;  // periodic source
+    // padded position (X, Y, Z); 32-bit division where the padded volume allows it
+    int X, Y, Z;
+    if (np < (1ll << 31)) {
+      const int pi = (int)p, row = pi / px;
+      X = pi - row * px;
+      Y = row % py;
+      Z = row / py;
+    } else {
+      X = (int)(p % px);
+      Y = (int)((p / px) % py);
+      Z = (int)(p / ((long long)px * py));
+    }
+    const int x = X == 0 ? nx - 1 : (X > nx ? 0 : X - 1);  // periodic source
+    const int y = Y == 0 ? ny - 1 : (Y > ny ? 0 : Y - 1);
+    const int z = Z == 0 ? nz - 1 : (Z > nz ? 0 : Z - 1);
     const long long s = ((long long)z * ny + y) * nx + x;
     float v[16];
 #pragma unroll
