@@ -488,7 +488,7 @@ __device__ __forceinline__ void qside_body(const CUtensorMap* tmQ, const CUtenso
       const int qi0 = (ty + 2) * ZM_BX + (tx + ZM_XOFF), qi1 = qi0 + TYH * ZM_BX;
       const Sym5<V> q = ld5v<SPT>(qc, L::QCS, qi0, qi1);
       Sym5<V> dq[3], h;
-      if constexpr (SPT == 1) {
+      if constexpr (SPT == 1 && !BATCH) {  // (a batch CTA has no registers to spare for the carry)
         dq[0] = dq_cur[0];
         dq[1] = dq_cur[1];
         dq[2] = dq_cur[2];
@@ -596,7 +596,7 @@ __device__ __forceinline__ ZmItem zm_item(const ZmBatch& B) {
   return it;
 }
 
-template <typename real>
+// geometry of class k, selected at compile-time indices of the parameter array
 __device__ __forceinline__ ZmGeom zm_class_geom(const ZmBatch& B, int k) {
   ZmGeom G = B.c[0].G;
 #pragma unroll
@@ -606,14 +606,12 @@ __device__ __forceinline__ ZmGeom zm_class_geom(const ZmBatch& B, int k) {
 }
 
 template <typename real, int TY>
-__global__ void __launch_bounds__(qside_threads<TY, 1>(), sizeof(real) == 4 ? 2 : 1) k_qside_batch(const __grid_constant__ ZmBatchMaps maps,
-                                                         ZmBatch B, const Replica<real>* __restrict__ reps,
-                                                         const int* __restrict__ order, const real* __restrict__ Q,
-                                                         const real* __restrict__ rhou, real* __restrict__ sigma,
-                                                         real* __restrict__ bout, real* __restrict__ Qs,
-                                                         int* __restrict__ err) {
+__global__ void __launch_bounds__(qside_threads<TY, 1>(), sizeof(real) == 4 ? 2 : 1)
+    k_qside_batch(const __grid_constant__ ZmBatchMaps maps, ZmBatch B, const Replica<real>* __restrict__ reps,
+                  const int* __restrict__ order, const real* __restrict__ Q, const real* __restrict__ rhou,
+                  real* __restrict__ sigma, real* __restrict__ bout, real* __restrict__ Qs, int* __restrict__ err) {
   const ZmItem it = zm_item(B);
-  const ZmGeom G = zm_class_geom<real>(B, it.k);
+  const ZmGeom G = zm_class_geom(B, it.k);
   int rep0 = B.c[0].rep0;
 #pragma unroll
   for (int i = 1; i < kZmMaxClasses; ++i)
@@ -986,7 +984,7 @@ __global__ void __launch_bounds__(ZM_TX* TY, 2)
                 const real* __restrict__ Qin, real* __restrict__ fnew, real* __restrict__ rhou_new,
                 real* __restrict__ Qout, int* __restrict__ err) {
   const ZmItem it = zm_item(B);
-  const ZmGeom G = zm_class_geom<real>(B, it.k);
+  const ZmGeom G = zm_class_geom(B, it.k);
   int rep0 = B.c[0].rep0;
 #pragma unroll
   for (int i = 1; i < kZmMaxClasses; ++i)
