@@ -53,8 +53,8 @@ STATE_BYTES = (15 + 5) * 2 * 4  # read + write of f and Q once per site-step (FP
 MEASURED_TRAFFIC = {
     "sources": ["paper_0901_3293_gb300/csrc/zmarch.cu", "paper_0901_3293_gb300/csrc/common.cuh",
                 "paper_0901_3293_gb300/csrc/tma.cuh"],
-    "sha256_16": "9db3e0d1052ce40a",
-    "bytes_per_site": {"qside": (160696832 + 166658816) / 160 ** 3, "lbq": (651194368 + 358619392) / 160 ** 3},
+    "sha256_16": "f2ec35af8d537c02",
+    "bytes_per_site": {"qside": (162886400 + 169034496) / 160 ** 3, "lbq": (649575936 + 358576384) / 160 ** 3},
 }
 ORACLE_SAMPLE = 32  # side of the periodic cube the oracle steps (two BPII unit cells)
 
