@@ -75,6 +75,37 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
+class Ranks:
+    """The ranks of one run: a barrier and the max over ranks of a timing.
+    device "cuda" (NCCL, the bench) or "cpu" (gloo); world 1 needs no process group."""
+
+    def __init__(self, world: int, device: str = "cuda"):
+        self.world, self.device = world, device
+
+    def barrier(self) -> None:
+        import torch
+        if self.world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        if self.device == "cuda":
+            torch.cuda.synchronize()
+
+    def allmax(self, x: float) -> float:
+        if self.world == 1:
+            return x
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([x], device=self.device, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+
+def whole_job_mlups(sites_per_rank: int, steps: int, world: int, ms_max: float) -> float:
+    """Replicas: every rank steps its own lattice, so the job advances world x
+    sites_per_rank sites per step in the slowest rank's time."""
+    return sites_per_rank * steps * world / (ms_max * 1e-3) / 1e6
+
+
 # multiply-accumulates per site of one surrogate call: conv 15->32, eight 32->32, 32->5 (3^3 taps)
 SURROGATE_MAC_PER_SITE = 27 * (15 * 32 + 8 * 32 * 32 + 32 * 5)
 
@@ -216,20 +247,8 @@ def run_ours(args):
     if not os.path.exists(lcbp.LIB_PATH):
         build.build()
     dev = torch.cuda.current_device()
-
-    def barrier():
-        if world > 1:
-            import torch.distributed as dist
-            dist.barrier()
-        torch.cuda.synchronize()
-
-    def allmax(x: float) -> float:
-        if world == 1:
-            return x
-        import torch.distributed as dist
-        t = torch.tensor([x], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    ranks = Ranks(world, "cuda")
+    barrier, allmax = ranks.barrier, ranks.allmax
 
     # every rank holds its own independent 256^3 lattice (replicas: no data exchange)
     n = N_SIDE
@@ -256,7 +275,7 @@ def run_ours(args):
     clk = clocks.stop()
     ms = allmax(e0.elapsed_time(e1))
     sites = n ** 3
-    mlups = sites * args.steps * world / (ms * 1e-3) / 1e6
+    mlups = whole_job_mlups(sites, args.steps, world, ms)
     F = lat.free_energy()  # FP64 diagnostics also check the state is finite
 
     # ---- per-kernel device times, kernel by kernel with events (same kernels)

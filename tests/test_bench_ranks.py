@@ -1,0 +1,61 @@
+"""The multi-rank host logic of bench.py on CPU: two gloo ranks, each with its
+own replica timing, agree on the slowest rank's time; the whole-job value
+counts every rank's sites; the reference arm prints from rank 0 only."""
+
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+
+def _rank(rank: int, world: int, port: int, out: str) -> None:
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    ranks = bench.Ranks(world, "cpu")
+    ranks.barrier()
+    # rank r "took" 10 (r + 1) ms for its replica's steps
+    ms = ranks.allmax(10.0 * (rank + 1))
+    value = bench.whole_job_mlups(1000, 50, world, ms)
+    ranks.barrier()
+    with open(f"{out}.{rank}", "w") as fh:
+        json.dump({"ms": ms, "value": value}, fh)
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_take_the_slowest_time(tmp_path):
+    import socket
+
+    import torch.multiprocessing as mp
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    out = str(tmp_path / "rank")
+    mp.start_processes(_rank, args=(2, port, out), nprocs=2, join=True, start_method="spawn")
+    res = [json.load(open(f"{out}.{r}")) for r in range(2)]
+    assert res[0] == res[1]
+    assert res[0]["ms"] == 20.0
+    # 2 ranks x 1000 sites x 50 steps in 20 ms
+    assert res[0]["value"] == pytest.approx(2 * 1000 * 50 / 20e-3 / 1e6)
+
+
+def test_single_rank_needs_no_process_group():
+    ranks = bench.Ranks(1, "cpu")
+    ranks.barrier()
+    assert ranks.allmax(3.5) == 3.5
+    assert bench.whole_job_mlups(16777216, 200, 1, 1.6 * 200) == pytest.approx(16777216 / 1.6e-3 / 1e6)
+
+
+def test_reference_arm_prints_from_rank_zero_only():
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1")
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--gpus", "2",
+                        "--steps", "3", "--warmup", "3"], env=env, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr
+    assert r.stdout.strip() == ""
