@@ -401,42 +401,52 @@ cudaError_t launch_field(const StepArgs& a, cudaStream_t s) {
 template cudaError_t launch_field<float>(const StepArgs&, cudaStream_t);
 template cudaError_t launch_field<double>(const StepArgs&, cudaStream_t);
 
-// rate[c] = Q*[c] - Q[c] for the five components of every site of every replica
-template <typename real>
-__global__ void k_rate_from_predictor(const Replica<real>* __restrict__ reps, const Tile* __restrict__ tiles,
-                                      int ntiles, TileShape ts, const real* __restrict__ Q, real* __restrict__ Qs) {
+// Beris-Edwards rate R(Q, u) = Gamma H + S(W, Q) - u.grad Q at every site of
+// every replica (Sec. 2.1 Eq. Qevolution, mat_der) in one pass: the stencil of
+// Q gives H and the gradients, the stencil of u gives W (u = 0 without flow).
+// The same per-site functions as the Heun predictor, so R is what the step
+// adds to Q there.
+template <typename real, bool FLOW, bool DIV = false>
+__global__ void __launch_bounds__(256) k_rate(const Replica<real>* __restrict__ reps, const Tile* __restrict__ tiles,
+                                              int ntiles, TileShape ts, const real* __restrict__ Q,
+                                              const real* __restrict__ rhou, real* __restrict__ Rout) {
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
     Replica<real> R;
     int x, y, z;
     if (!tile_site(reps, tiles, t, ts, R, x, y, z)) continue;
-    const long long s = ((long long)z * R.ny + y) * R.nx + x;
-    const real* q = Q + 5 * R.base;
-    real* qs = Qs + 5 * R.base;
-#pragma unroll
-    for (int c = 0; c < 5; ++c) qs[c * R.n + s] -= q[c * R.n + s];
+    const long long n = R.n;
+    const Nbr nb = make_nbr(x, y, z, R.nx, R.ny, R.nz, R.walls);
+    const Stencil7<real> st = load_stencil(Q + 5 * R.base, n, nb, R);
+    Sym5<real> dq[3];
+    Sym5<real> h = molecular_field(st, R.m, dq);
+    if (DIV) add_div_field(h, Q + 5 * R.base, n, x, y, z, R.nx, R.ny, R.nz, R.m.c_div);
+    real u[3] = {real(0), real(0), real(0)};
+    real w[3][3] = {};
+    if (FLOW) {
+      const real* ru = rhou + 4 * R.base;
+      load_u(ru, n, nb.s, u);
+      velocity_gradient(ru, n, nb, R.nx, R.ny, w, u);
+    }
+    const Sym5<real> r = be_rate(st.c, h, dq, u, w, R.m, FLOW);
+    store5(Rout + 5 * R.base, n, nb.s, r);
   }
 }
 
-// Beris-Edwards rate R(Q^n, u^n) = Gamma H + S - u.grad Q into a.qs (Sec. 2.1
-// Eq. Qevolution, mat_der): the Heun predictor minus Q
+// R(Q^n, u^n) into a.qs
 template <typename real>
 cudaError_t launch_rate(const StepArgs& a, cudaStream_t s) {
   const auto* reps = static_cast<const Replica<real>*>(a.reps);
   const int threads = a.ts.tx * a.ts.ty * a.ts.tz;
-  auto Rp = [](void* p) { return static_cast<real*>(p); };
-  auto Cp = [](const void* p) { return static_cast<const real*>(p); };
+  const real* q = static_cast<const real*>(a.q);
+  const real* ru = static_cast<const real*>(a.rhou);
+  real* out = static_cast<real*>(a.qs);
   if (a.flow_on) {
-    launch_fld<real, true>(a.div, a.ntiles, threads, s, reps, a.tiles, a.ntiles, a.ts, Cp(a.q), Rp(a.h),
-                           Rp(a.sigma), Rp(a.tau));
-    k_force_predict<real, true, false, true, false><<<a.ntiles, threads, 0, s>>>(
-        reps, a.tiles, a.ntiles, a.ts, Cp(a.q), Cp(a.h), nullptr, Cp(a.rhou), nullptr, nullptr, Rp(a.qs));
+    if (a.div) k_rate<real, true, true><<<a.ntiles, threads, 0, s>>>(reps, a.tiles, a.ntiles, a.ts, q, ru, out);
+    else k_rate<real, true, false><<<a.ntiles, threads, 0, s>>>(reps, a.tiles, a.ntiles, a.ts, q, ru, out);
   } else {
-    launch_fld<real, false>(a.div, a.ntiles, threads, s, reps, a.tiles, a.ntiles, a.ts, Cp(a.q), Rp(a.h),
-                            (real*)nullptr, (real*)nullptr);
-    k_force_predict<real, false, false, true, false><<<a.ntiles, threads, 0, s>>>(
-        reps, a.tiles, a.ntiles, a.ts, Cp(a.q), Cp(a.h), nullptr, nullptr, nullptr, nullptr, Rp(a.qs));
+    if (a.div) k_rate<real, false, true><<<a.ntiles, threads, 0, s>>>(reps, a.tiles, a.ntiles, a.ts, q, ru, out);
+    else k_rate<real, false, false><<<a.ntiles, threads, 0, s>>>(reps, a.tiles, a.ntiles, a.ts, q, ru, out);
   }
-  k_rate_from_predictor<real><<<a.ntiles, threads, 0, s>>>(reps, a.tiles, a.ntiles, a.ts, Cp(a.q), Rp(a.qs));
   return cudaGetLastError();
 }
 template cudaError_t launch_rate<float>(const StepArgs&, cudaStream_t);

@@ -96,6 +96,41 @@ def test_slab_growth_states_step_f64(lcbp, kind):
     assert np.abs(lat.read_u() - oracle_u(f)).max() < 1e-14
 
 
+@pytest.mark.parametrize("mode", ["flow", "no_flow", "l2", "walls"])
+@pytest.mark.parametrize("dtype,tol", [("f64", 1e-15), ("f32", 3e-8)])
+def test_rate_matches_oracle(lcbp, mode, dtype, tol):
+    """lcbp_read_rate: the Beris-Edwards rate R(Q, u) with u from the stored
+    moments (Sec. 2.1 Eq. Qevolution, mat_der) against the oracle's be_rhs, with
+    flow, without flow (u = 0), with L2 != K, and between walls."""
+    shape = (7, 6, 8)
+    kw = {}
+    if mode == "no_flow":
+        kw["flow_on"] = False
+    if mode == "l2":
+        kw["L2"] = 0.004
+    if mode == "walls":
+        kw["walls_z"] = True
+    p = lbq.Params(**kw)
+    q5 = synth.smooth_q5(shape, 0.3, 1) + synth.random_q5(shape, 1e-2, 2)
+    f15 = synth.random_distributions(shape, 3, amp=2e-3)
+    lat = make(lcbp, shape, dtype, p)
+    if mode == "l2":
+        lat.set_l2(p.L2)
+    if mode == "walls":
+        lat.set_walls(True)
+    lat.set_q(q5).set_f(f15)
+    f = lbq.f_from_soa(f15)
+    u = lbq.moments(f)[1] if p.flow_on else np.zeros(shape + (3,))
+    # the lattice holds Q in its state type: the oracle takes that Q
+    Q9 = lbq.q5_to_q9(lat.read_q())
+    want = lbq.q9_to_q5(lbq.be_rhs(Q9, np.asarray(u, dtype=np.float64), p))
+    got = lat.read_rate()
+    # FP32: the rate carries the rounding of u (from FP32 populations) and of its own
+    # arithmetic; the bound is half an ulp of the Q values (O(0.3)) it is added to
+    assert np.abs(want).max() > 1e-6
+    assert np.abs(got - want).max() < tol, np.abs(got - want).max()
+
+
 FAST_PATHS = {"fast1": "PATH_FAST1", "fast2": "PATH_FAST2", "generic": "PATH_GENERIC"}
 
 
