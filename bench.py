@@ -55,6 +55,8 @@ MEASURED_TRAFFIC = {
                 "paper_0901_3293_gb300/csrc/tma.cuh"],
     "sha256_16": "f2ec35af8d537c02",
     "bytes_per_site": {"qside": (162886400 + 169034496) / 160 ** 3, "lbq": (649575936 + 358576384) / 160 ** 3},
+    # smsp__inst_executed.sum (warp instructions) x 32 of one launch of the same capture
+    "thread_instr_per_site": {"qside": 151784052 * 32 / 160 ** 3, "lbq": 191949456 * 32 / 160 ** 3},
 }
 ORACLE_SAMPLE = 32  # side of the periodic cube the oracle steps (two BPII unit cells)
 
@@ -69,6 +71,13 @@ def measured_traffic_per_site(kernel: str):
     if h.hexdigest()[:16] != MEASURED_TRAFFIC["sha256_16"]:
         return None
     return MEASURED_TRAFFIC["bytes_per_site"].get(kernel)
+
+
+def measured_instr_per_site(kernel: str):
+    """ncu thread instructions per site of `kernel`, or None if its sources changed since the capture."""
+    if measured_traffic_per_site(kernel) is None:
+        return None
+    return MEASURED_TRAFFIC["thread_instr_per_site"].get(kernel)
 
 
 def dist_env():
@@ -283,10 +292,19 @@ def run_ours(args):
     fast, zc, spt = lat.path()
     peak, peak_kind = measured_peaks()
     per_kernel = {}
+    # instruction-issue peak: one warp instruction per scheduler per cycle, 4 schedulers per
+    # SM, at the SM clock median measured under load (else the maximum)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_hz = 1e6 * (clk.get("sm_mhz") or clk.get("sm_max_mhz") or 2070.0)
+    issue_peak = sms * 4 * sm_hz * 32  # thread instructions per second
     for name, t in zip(KERNELS_FAST if fast else KERNELS_GENERIC, kms):
         gbs = KERNEL_BYTES[name] * sites / (t * 1e-3) / 1e9
         per_kernel[name] = {"ms": t, "algorithmic_bytes_per_site": KERNEL_BYTES[name], "GBps": gbs,
                             "frac_of_" + peak_kind: gbs / peak}
+        ips = measured_instr_per_site(name) if fast else None
+        if ips:
+            per_kernel[name]["thread_instr_per_site"] = ips
+            per_kernel[name]["frac_of_issue_peak"] = ips * sites / (t * 1e-3) / issue_peak
     dom = max(per_kernel, key=lambda k: per_kernel[k]["ms"])
     tps = measured_traffic_per_site(dom) if fast else None
     roof = {"bound": "hbm", "achieved": per_kernel[dom]["GBps"], "peak": peak, "unit": "GB/s",
