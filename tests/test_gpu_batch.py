@@ -182,3 +182,28 @@ def test_batch_path_rules(lcbp):
     assert (zc >= 1) if fast else (zc == 0)
     for b in (five, ragged, ok):
         b.close()
+
+
+@pytest.mark.parametrize("dims_list", [[(8, 8, 8)], [(8, 4, 3), (12, 4, 5), (4, 8, 9), (16, 12, 2)]])
+def test_fast_batch_edge_counts_bitwise_f32(lcbp, dims_list):
+    """One replica, and exactly four classes (one replica each, with nz of 2,
+    3, 5 and 9): the fast batch equals the lattices stepped alone on the fast
+    kernels, bit for bit."""
+    params = [replica_params(0.5 + 0.4 * r, -0.3 + 0.2 * r) for r in range(len(dims_list))]
+    b = lcbp.Batch(dims_list, params, dtype="f32").set_path(lcbp.PATH_FAST1)
+    for r in range(len(dims_list)):
+        b.init_q(r, initial.BPII, 0.3, noise=1e-3, seed=50 + r)
+    b.init_f_equilibrium(1.0).step(7)
+    assert b.path()[0]
+    for r, (nx, ny, nz) in enumerate(dims_list):
+        p = params[r]
+        lat = lcbp.Lattice(nx, ny, nz, dtype="f32")
+        lat.set_path(lcbp.PATH_FAST1)
+        lat.set_ldg(p["A0"], p["gamma"], p["K"], p["q0"]).set_flow(p["tau_f"], p["xi"], p["Gamma"])
+        lat.init_q(initial.BPII, 0.3, noise=1e-3, seed=50 + r)
+        lat.init_f_equilibrium(1.0).step(7)
+        assert lat.path()[0]
+        assert np.array_equal(b.read_q(r, np.float32), lat.read_q(dtype=np.float32)), r
+        assert np.array_equal(b.read_u(r, np.float32), lat.read_u(dtype=np.float32)), r
+        lat.close()
+    b.close()
