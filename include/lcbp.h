@@ -413,7 +413,8 @@ LCBP_API int lcbp_batch_defect_fraction(lcbp_batch *b, int r, double threshold, 
  */
 LCBP_API int lcbp_batch_set_path(lcbp_batch *b, int path);
 /* *fast = 1 if steps run the fast kernels; *planes_per_cta = their tuned
- * z-chunk (0 before the first step or on the generic path).  Either may be NULL. */
+ * z-chunk (tuned per class; the first class's value), 0 before the first step
+ * or on the generic path.  Either may be NULL. */
 LCBP_API int lcbp_batch_get_path(lcbp_batch *b, int *fast, int *planes_per_cta);
 /* R, total sites, tuned tile shape (tx, ty, tz) and persistent CTAs per launch
  * of the generic path, steps done. */

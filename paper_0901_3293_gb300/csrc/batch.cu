@@ -126,13 +126,13 @@ bool build_maps(lcbp_batch* b) {
   return true;
 }
 
-// geometry and CTA ranges of the classes for `zc` planes per CTA
-void set_zc(lcbp_batch* b, int zc) {
+// geometry and CTA ranges of the classes for zc[k] planes per CTA in class k
+void set_zc(lcbp_batch* b, const int* zc) {
   const int ty = b->dtype == LCBP_F64 ? zm_tile_rows<double>() : zm_tile_rows<float>();
   int cta = 0;
   for (int k = 0; k < b->zb.nclass; ++k) {
     ZmClass& c = b->zb.c[k];
-    c.G.zc = std::min(zc, c.G.nz);
+    c.G.zc = std::min(zc[k], c.G.nz);
     c.G.tiles_x = (c.G.nx + 31) / 32;
     c.G.tiles_y = (c.G.ny + ty - 1) / ty;
     c.G.tiles_z = (c.G.nz + c.G.zc - 1) / c.G.zc;
@@ -141,7 +141,7 @@ void set_zc(lcbp_batch* b, int zc) {
     cta += c.ctas_per_rep * c.count;
   }
   b->zb.total_ctas = cta;
-  b->zc = zc;
+  b->zc = zc[0];
 }
 
 ZmBatchArgs zm_args(lcbp_batch* b) {
@@ -265,41 +265,60 @@ int resident_ctas(lcbp_batch* b) {
   return std::max(1, sms * per_sm);
 }
 
-// planes per CTA of the fast path: timed candidates, one step each (best of 3)
+// planes per CTA of the fast path, per class: one value for every class first,
+// then each class's own value with the others held (one pass); every
+// candidate is timed as one step of the whole batch (best of 3)
 int tune_fast(lcbp_batch* b, float* best_ms) {
-  int max_nz = 1;
-  for (int k = 0; k < b->zb.nclass; ++k) max_nz = std::max(max_nz, b->zb.c[k].G.nz);
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return fail(LCBP_ECUDA, "events");
-  float best = 1e30f;
-  int best_zc = 8;
-  for (int zc : {4, 6, 8, 10, 12, 16, 24, 32, 48, 64}) {
-    if (zc > max_nz && zc != 4) break;
+  const int nc = b->zb.nclass;
+  const int cand[] = {4, 6, 8, 10, 12, 16, 24, 32, 48, 64};
+  cudaError_t err = cudaSuccess;
+  auto time_zc = [&](const int* zc) {
     set_zc(b, zc);
     ZmBatchArgs a = zm_args(b);
     a.qout = b->h;  // scratch: the state is left untouched
     float t = 1e30f;
-    for (int rep = 0; rep < 3; ++rep) {
+    for (int rep = 0; rep < 3 && err == cudaSuccess; ++rep) {
       cudaEventRecord(e0, b->stream);
-      cudaError_t e = launch_zm(b, a);
+      err = launch_zm(b, a);
       cudaEventRecord(e1, b->stream);
-      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-      if (e != cudaSuccess) {
-        cudaEventDestroy(e0);
-        cudaEventDestroy(e1);
-        return cuda_fail(e, "batch planes-per-CTA tuning");
-      }
+      if (err == cudaSuccess) err = cudaEventSynchronize(e1);
       float ms = 0;
-      cudaEventElapsedTime(&ms, e0, e1);
+      if (err == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
       t = std::min(t, ms);
     }
+    return t;
+  };
+  int zc[kZmMaxClasses], best_zc[kZmMaxClasses];
+  float best = 1e30f;
+  int max_nz = 1;
+  for (int k = 0; k < nc; ++k) max_nz = std::max(max_nz, b->zb.c[k].G.nz);
+  for (int v : cand) {
+    if (v > max_nz && v != 4) break;
+    for (int k = 0; k < nc; ++k) zc[k] = v;
+    const float t = time_zc(zc);
     if (t < best) {
       best = t;
-      best_zc = zc;
+      std::copy(zc, zc + nc, best_zc);
+    }
+  }
+  for (int k = 0; k < nc && nc > 1 && err == cudaSuccess; ++k) {
+    std::copy(best_zc, best_zc + nc, zc);
+    for (int v : cand) {
+      if (v > b->zb.c[k].G.nz && v != 4) break;
+      if (v == best_zc[k]) continue;
+      zc[k] = v;
+      const float t = time_zc(zc);
+      if (t < best) {
+        best = t;
+        best_zc[k] = v;
+      }
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  if (err != cudaSuccess) return cuda_fail(err, "batch planes-per-CTA tuning");
   set_zc(b, best_zc);
   *best_ms = best;
   return check_error_flag(b);
