@@ -182,9 +182,11 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def oracle_sample_mlups(steps: int, warmup: int = 1):
+def oracle_sample_mlups(steps: int, warmup: int = 1, start_at: float = 0.0):
     """FP64 oracle on a periodic 32^3 cube of the same BPII state (two unit
-    cells per side), timed on one host core.  Returns (MLUPS, seconds)."""
+    cells per side), timed on one host core.  The timed loop starts no earlier
+    than the wall-clock time start_at, so that concurrent copies overlap.
+    Returns (MLUPS, seconds)."""
     from oracle import initial, lbq
     p = lbq.Params(**PARAMS)
     shape = (ORACLE_SAMPLE,) * 3
@@ -192,6 +194,8 @@ def oracle_sample_mlups(steps: int, warmup: int = 1):
     f = lbq.init_f_equilibrium(Q, p)
     for _ in range(warmup):
         f, Q = lbq.step(f, Q, p)
+    while time.time() < start_at:
+        time.sleep(0.01)
     t0 = time.perf_counter()
     for _ in range(steps):
         f, Q = lbq.step(f, Q, p)
@@ -199,21 +203,52 @@ def oracle_sample_mlups(steps: int, warmup: int = 1):
     return ORACLE_SAMPLE ** 3 * steps / dt / 1e6, dt
 
 
-def oracle_in_subprocess(steps: int, warmup: int = 1):
-    """The oracle timed in a child process whose math libraries use one thread."""
+def oracle_in_subprocess(steps: int, warmup: int = 1, copies: int = 1):
+    """The oracle timed in child processes whose math libraries use one thread
+    each: `copies` independent samples stepped at the same time, one per core.
+    Returns (MLUPS of all copies together, seconds of the slowest copy)."""
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    start_at = time.time() + (0.0 if copies == 1 else 5.0 + 0.05 * copies)
     code = ("import sys, json; sys.path.insert(0, %r); import bench; "
-            "m, dt = bench.oracle_sample_mlups(%d, %d); print(json.dumps([m, dt]))" % (ROOT, steps, warmup))
-    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, check=True)
-    m, dt = json.loads(out.stdout.strip().splitlines()[-1])
-    return m, dt
+            "m, dt = bench.oracle_sample_mlups(%d, %d, %r); print(json.dumps([m, dt]))"
+            % (ROOT, steps, warmup, start_at))
+    procs = [subprocess.Popen([sys.executable, "-c", code], env=env, stdout=subprocess.PIPE, stderr=subprocess.PIPE,
+                              text=True) for _ in range(copies)]
+    dts = []
+    for pr in procs:
+        out, err = pr.communicate()
+        if pr.returncode != 0:
+            raise RuntimeError(f"oracle sample failed: {err.strip()[-400:]}")
+        dts.append(json.loads(out.strip().splitlines()[-1])[1])
+    dt = max(dts)
+    return copies * ORACLE_SAMPLE ** 3 * steps / dt / 1e6, dt
+
+
+def host_cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
+    return platform.processor() or platform.machine()
 
 
 def cpu_baseline_entry(steps: int):
     m, dt = oracle_in_subprocess(steps)
-    return {"value": m, "unit": "MLUPS", "cores": 1, "kind": "oracle",
-            "sample": f"{steps} FP64 oracle steps of a periodic {ORACLE_SAMPLE}^3 cube of the same BPII "
-                      f"(pitch 32) state, {dt:.1f} s on one host core (numpy, threads pinned to 1)"}
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    entry = {"value": m, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+             "sample": f"{steps} FP64 oracle steps of a periodic {ORACLE_SAMPLE}^3 cube of the same BPII "
+                       f"(pitch 32) state, {dt:.1f} s on one host core (numpy, threads pinned to 1)",
+             "host": f"{host_cpu_model()}, {cores} cores"}
+    if cores > 1:
+        ma, dta = oracle_in_subprocess(steps, copies=cores)
+        entry["all_cores"] = {"value": ma, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+                              "sample": f"{cores} independent copies of the same sample stepped at once, one per "
+                                        f"core; the slowest took {dta:.1f} s"}
+    return entry
 
 
 def workload_config(world: int) -> dict:
