@@ -59,6 +59,7 @@ MEASURED_TRAFFIC = {
     "thread_instr_per_site": {"qside": 151784052 * 32 / 160 ** 3, "lbq": 191949456 * 32 / 160 ** 3},
 }
 ORACLE_SAMPLE = 32  # side of the periodic cube the oracle steps (two BPII unit cells)
+WALL_Q = (0.2, 0.0, 0.0, -0.1, 0.0)  # planar anchoring S (x x - I/3), S = 0.3, on the ghost planes
 
 
 def measured_traffic_per_site(kernel: str):
@@ -373,6 +374,27 @@ def run_ours(args):
            "steps": k_e2e, "note": "lcbp_set_f + lcbp_set_q from pinned host memory, lcbp_step(1), "
                                    "lcbp_read_q + lcbp_read_u to pinned host memory"}
     launches = (2 if fast else 3) * args.steps
+
+    # ---- the same lattice between walls in z (half-way bounce-back, Q anchored
+    # to a planar q_wall on the ghost planes): the walled build of the kernels
+    lat.set_walls(True, WALL_Q)
+    lat.step(max(3, args.warmup))  # tunes the walled build
+    lat.synchronize()
+    w0 = torch.cuda.Event(enable_timing=True)
+    w1 = torch.cuda.Event(enable_timing=True)
+    w0.record(stream)
+    lat.step(args.steps)
+    w1.record(stream)
+    w1.synchronize()
+    walls_ms = w0.elapsed_time(w1)
+    wfast, wzc, wspt = lat.path()
+    wkms = lat.profile_steps(max(3, min(args.steps, 10)))
+    walls_line = {"ms_per_step": walls_ms / args.steps, "MLUPS": sites * args.steps / (walls_ms * 1e-3) / 1e6,
+                  "fast_path": wfast, "planes_per_cta": wzc, "sites_per_thread": wspt,
+                  "per_kernel": {name: {"ms": t, "GBps": KERNEL_BYTES[name] * sites / (t * 1e-3) / 1e9,
+                                        "frac_of_" + peak_kind: KERNEL_BYTES[name] * sites / (t * 1e-3) / 1e9 / peak}
+                                 for name, t in zip(KERNELS_FAST if wfast else KERNELS_GENERIC, wkms)},
+                  "q_wall": list(WALL_Q)}
     lat.close()
 
     # ---- the 64x64x256 thin slab (BPII seed for z < 32 inside an x-helix)
@@ -476,7 +498,7 @@ def run_ours(args):
                    "planes_per_cta": zc, "sites_per_thread": spt},
         "roofline": roof, "per_kernel": per_kernel, "cpu_baseline": cpu, "e2e": e2e,
         "gpu_launches": launches, "clocks": clk, "free_energy_after": F,
-        "slab_64x64x256": slab_line, "surrogate_slab_64x64x256": sur_line, "texture_slab_64x64x256": tex_line,
+        "walls_256cube": walls_line, "slab_64x64x256": slab_line, "surrogate_slab_64x64x256": sur_line, "texture_slab_64x64x256": tex_line,
         "batched_48_replicas": batch_line,
     }
     print(json.dumps(line), flush=True)

@@ -183,8 +183,10 @@ LCBP_API int lcbp_set_l2(lcbp_lattice *h, int use_l2, double L2);
  *    advection);
  *  - tau and H vanish on the ghost planes (body force).
  * The free energy then counts every bond with at least one end on the
- * lattice, so H stays its exact gradient.  Walled lattices run the generic
- * kernels; the surrogate refuses them.  walls_z = 0 restores periodic z.
+ * lattice, so H stays its exact gradient.  Walled lattices run the fast
+ * kernels (one site per thread) where the fast path applies, else the generic
+ * ones; the surrogate refuses them.  walls_z = 0 restores periodic z.  Every
+ * call re-records the captured step (q_wall is a launch argument).
  * Errors: LCBP_EINVAL (non-finite q_wall; L2 set).
  */
 LCBP_API int lcbp_set_walls(lcbp_lattice *h, int walls_z, const double *q_wall5);
@@ -257,7 +259,8 @@ LCBP_API int lcbp_profile_steps(lcbp_lattice *h, int nsteps, double *kernel_ms, 
  * otherwise, or with LCBP_PATH_GENERIC, three one-thread-per-site kernels.
  * FP32 fast kernels come in two builds, one or two lattice sites per thread
  * (the latter on packed FP32x2 arithmetic); AUTO times both, LCBP_PATH_FAST1
- * and LCBP_PATH_FAST2 pin one.  All compute the same step.  Errors:
+ * and LCBP_PATH_FAST2 pin one (a lattice with walls runs one site per thread
+ * under either).  All compute the same step.  Errors:
  * LCBP_EINVAL (unknown path, or LCBP_PATH_FAST2 on an FP64 lattice).
  */
 LCBP_API int lcbp_set_path(lcbp_lattice *h, int path);
@@ -269,7 +272,8 @@ LCBP_API int lcbp_set_path(lcbp_lattice *h, int path);
  * on the generic path).  The tuning times each candidate once per lattice
  * shape and dtype, writing scratch buffers only; AUTO results persist in the
  * file named by the environment variable LCBP_AUTOTUNE_CACHE, if set
- * (lines "nx ny nz dtype planes sites").  Any pointer may be NULL.
+ * (lines "nx ny nz dtype planes sites", dtype + 100 for a lattice with
+ * walls).  Any pointer may be NULL.
  */
 LCBP_API int lcbp_get_path(lcbp_lattice *h, int *fast, int *planes_per_cta, int *sites_per_thread);
 

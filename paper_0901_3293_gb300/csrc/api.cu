@@ -343,7 +343,7 @@ bool fast_shape_ok(const lcbp_lattice* h) { return h->nx % 4 == 0; }
 
 bool use_fast(lcbp_lattice* h) {
   if (h->path_req == LCBP_PATH_GENERIC || !h->p.flow_on || h->p.coupling != LCBP_JACOBI || !fast_shape_ok(h) ||
-      h->p.walls_z || (h->p.l2_set && h->p.L2 != h->p.K))
+      (h->p.l2_set && h->p.L2 != h->p.K))
     return false;
   if (!h->tmaps_ok) {
     static std::once_flag prep32, prep64;
@@ -390,6 +390,7 @@ ZmArgs zm_args(lcbp_lattice* h, const void* model) {
   a.rhou_new = h->rhou[h->cur ^ 1];
   a.err = h->d_err;
   a.events = nullptr;
+  a.q_wall = h->p.walls_z ? h->p.q_wall : nullptr;
   return a;
 }
 
@@ -417,14 +418,15 @@ cudaError_t launch_zm(lcbp_lattice* h, const ZmArgs& a) {
 // lattice shape and dtype; the runs write only scratch buffers (Q* to the H
 // scratch), so the state is untouched.  Results are kept per process and, if
 // the environment variable LCBP_AUTOTUNE_CACHE names a file, in that file
-// ("nx ny nz dtype zc spt" per line).
+// ("nx ny nz dtype zc spt" per line, dtype + 100 with walls).
 std::mutex g_tune_mu;
 std::map<std::string, std::pair<int, int>> g_tune;
 bool g_tune_loaded = false;
 
+// "nx ny nz dtype", with 100 added to dtype for a lattice with walls
 std::string tune_key(const lcbp_lattice* h) {
   char k[64];
-  snprintf(k, sizeof(k), "%d %d %d %d", h->nx, h->ny, h->nz, h->dtype);
+  snprintf(k, sizeof(k), "%d %d %d %d", h->nx, h->ny, h->nz, h->dtype + (h->p.walls_z ? 100 : 0));
   return k;
 }
 
@@ -461,8 +463,9 @@ int tune_zc(lcbp_lattice* h) {
   const int spt_max = h->dtype == LCBP_F64 ? zm_spt_max<double>() : zm_spt_max<float>();
   // a pinned sites-per-thread choice tunes only the planes per CTA, uncached
   const bool pinned = h->path_req == LCBP_PATH_FAST1 || h->path_req == LCBP_PATH_FAST2;
-  const int spt_lo = h->path_req == LCBP_PATH_FAST2 ? 2 : 1;
-  const int spt_hi = h->path_req == LCBP_PATH_FAST1 ? 1 : spt_max;
+  // (walls: one site per thread only)
+  const int spt_lo = h->path_req == LCBP_PATH_FAST2 && !h->p.walls_z ? 2 : 1;
+  const int spt_hi = h->path_req == LCBP_PATH_FAST1 || h->p.walls_z ? 1 : spt_max;
   if (path && !g_tune_loaded) {
     g_tune_loaded = true;
     if (FILE* fp = std::fopen(path, "r")) {
@@ -826,7 +829,12 @@ int lcbp_set_walls(lcbp_lattice* h, int walls_z, const double* q_wall5) {
     p.q_wall[c] = q_wall5 ? q_wall5[c] : 0.0;
     if (!std::isfinite(p.q_wall[c])) return fail(LCBP_EINVAL, "non-finite q_wall");
   }
-  if (p.walls_z != h->p.walls_z) drop_graph(h);
+  // the fast kernels take q_wall as a launch argument: recapture the step
+  drop_graph(h);
+  if (p.walls_z != h->p.walls_z) {
+    h->zc = 0;  // tuned separately with walls
+    h->spt = 0;
+  }
   h->p = p;
   return upload_replica(h);
 }

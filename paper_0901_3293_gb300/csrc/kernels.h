@@ -118,6 +118,7 @@ struct ZmArgs {
   void *f, *fnew, *rhou, *rhou_new;
   int* err;              // set to 1 if a bounded barrier wait timed out
   cudaEvent_t* events;   // optional: 3 events around the two kernels
+  const double* q_wall;  // walls in z with this anchored Q (5 values), or nullptr: periodic
 };
 
 constexpr int kZmBoxX = 40;  // elements per TMA box row

@@ -204,12 +204,15 @@ constexpr int qside_threads() {
 
 // Tile bt of one lattice (or of replica rc of a batch class, whose fields are
 // 5-D tensors with the replica outermost: BATCH) of the k_qside step.
-template <typename real, int TY, int SPT, bool BATCH>
+// WALLS: walls half a spacing below z = 0 and above z = nz-1.  The ghost
+// planes z = -1 and z = nz hold the anchored qw in every Q stencil, carry no
+// molecular field (tau = 0 there) and the velocity -u of the adjacent plane.
+template <typename real, int TY, int SPT, bool BATCH, bool WALLS>
 __device__ __forceinline__ void qside_body(const CUtensorMap* tmQ, const CUtensorMap* tmU, const ZmGeom G,
                                            const Model<real> m, int bt, int rc, const real* __restrict__ Q,
                                            const real* __restrict__ rhou, const real* __restrict__ bext,
                                            real* __restrict__ sigma, real* __restrict__ bout,
-                                           real* __restrict__ Qs, int* __restrict__ err) {
+                                           real* __restrict__ Qs, int* __restrict__ err, const Sym5<real> qw) {
   using L = QsideSmem<real, TY>;
   using V = typename LaneT<real, SPT>::V;
   constexpr int TYH = TY / SPT;  // rows handled by one pass of the CTA
@@ -292,7 +295,20 @@ __device__ __forceinline__ void qside_body(const CUtensorMap* tmQ, const CUtenso
     dst = (int)(uslot(pu) - base) + (k * L::UROWS + r) * ZM_BX + c;
     return rhou[k * n + image_site(r, c, nx, ny, wrap(pu, nz), x0, y0 - 1)];
   };
+  // a staged Q plane beyond a wall: qw in every cell (no periodic images)
+  auto ghost = [&](int p) { return WALLS && (p < 0 || p >= nz); };
+  auto fill_q = [&](int p) {
+    real* sl = qslot(p);
+    for (int t = threadIdx.x; t < 5 * L::QCS; t += blockDim.x) {
+      const int k = t / L::QCS;
+      sl[t] = k == 0 ? qw.xx : k == 1 ? qw.xy : k == 2 ? qw.xz : k == 3 ? qw.yy : qw.yz;
+    }
+  };
   auto patch_q = [&](int p) {
+    if (ghost(p)) {
+      fill_q(p);
+      return;
+    }
     for (int t = threadIdx.x; t < items_q; t += blockDim.x) {
       int d;
       const real v = patch_item(t, p, p, d);
@@ -319,6 +335,10 @@ __device__ __forceinline__ void qside_body(const CUtensorMap* tmQ, const CUtenso
   // recomputes the gradients from the staged Q.
   Sym5<V> dq_next[3];
   auto field_plane = [&](int p) {
+    if (ghost(p)) {  // tau = 0 beyond a wall; H there is never read
+      for (int t = threadIdx.x; t < L::TSLOT; t += blockDim.x) tslot(p)[t] = real(0);
+      return;
+    }
     const bool own = p >= z0 && p < z1;
     const real* qm = qslot(p - 1);
     const real* qc = qslot(p);
@@ -454,7 +474,7 @@ __device__ __forceinline__ void qside_body(const CUtensorMap* tmQ, const CUtenso
     for (int q = 0; q < KP; ++q) {
       const int t = threadIdx.x + q * blockDim.x;
       pd[q] = -1;
-      if (t < items) pv[q] = patch_item(t, z + 2, z + 1, pd[q]);
+      if (t < items && !(t < items_q && ghost(z + 2))) pv[q] = patch_item(t, z + 2, z + 1, pd[q]);
     }
     const bool okq = wait_q(z + 2), oku = wait_u(z + 1);
     if (okq && oku) {
@@ -462,10 +482,12 @@ __device__ __forceinline__ void qside_body(const CUtensorMap* tmQ, const CUtenso
       for (int q = 0; q < KP; ++q)
         if (pd[q] >= 0) base[pd[q]] = pv[q];
       for (int t = threadIdx.x + KP * blockDim.x; t < items; t += blockDim.x) {
+        if (t < items_q && ghost(z + 2)) continue;
         int d;
         const real v = patch_item(t, z + 2, z + 1, d);
         base[d] = v;
       }
+      if (ghost(z + 2)) fill_q(z + 2);
     }
     __syncthreads();
     if (*abort_flag) {
@@ -529,7 +551,10 @@ __device__ __forceinline__ void qside_body(const CUtensorMap* tmQ, const CUtenso
         u[a] = vld<SPT>(uc, o + u0, o + u1);
         w[a][0] = half * (vld<SPT>(uc, o + u0 + 1, o + u1 + 1) - vld<SPT>(uc, o + u0 - 1, o + u1 - 1));
         w[a][1] = half * (vld<SPT>(uc, o + u0 + ZM_BX, o + u1 + ZM_BX) - vld<SPT>(uc, o + u0 - ZM_BX, o + u1 - ZM_BX));
-        w[a][2] = half * (vld<SPT>(up, o + u0, o + u1) - vld<SPT>(um, o + u0, o + u1));
+        V upz = vld<SPT>(up, o + u0, o + u1), umz = vld<SPT>(um, o + u0, o + u1);
+        if (WALLS && z == 0) umz = -u[a];  // no slip half a spacing beyond the wall
+        if (WALLS && z == nz - 1) upz = -u[a];
+        w[a][2] = half * (upz - umz);
       }
       const Sym5<V> r = be_rate(q, h, dq, u, w, mv, true);
       const Sym5<V> qs = {q.xx + r.xx, q.xy + r.xy, q.xz + r.xz, q.yy + r.yy, q.yz + r.yz};
@@ -563,15 +588,13 @@ __device__ __forceinline__ void qside_body(const CUtensorMap* tmQ, const CUtenso
 }
 
 // FP32: two CTAs per SM (shared memory allows two; the bound keeps the registers within it)
-template <typename real, int TY, int SPT>
+template <typename real, int TY, int SPT, bool WALLS>
 __global__ void __launch_bounds__(qside_threads<TY, SPT>(), sizeof(real) == 4 ? 2 : 1)
-    k_qside(const __grid_constant__ CUtensorMap tmQ,
-                                                     const __grid_constant__ CUtensorMap tmU, ZmGeom G,
-                                                     Model<real> m, const real* __restrict__ Q,
-                                                     const real* __restrict__ rhou, const real* __restrict__ bext,
-                                                     real* __restrict__ sigma, real* __restrict__ bout,
-                                                     real* __restrict__ Qs, int* __restrict__ err) {
-  qside_body<real, TY, SPT, false>(&tmQ, &tmU, G, m, blockIdx.x, 0, Q, rhou, bext, sigma, bout, Qs, err);
+    k_qside(const __grid_constant__ CUtensorMap tmQ, const __grid_constant__ CUtensorMap tmU, ZmGeom G,
+            Model<real> m, const real* __restrict__ Q, const real* __restrict__ rhou,
+            const real* __restrict__ bext, real* __restrict__ sigma, real* __restrict__ bout,
+            real* __restrict__ Qs, int* __restrict__ err, Sym5<real> qw) {
+  qside_body<real, TY, SPT, false, WALLS>(&tmQ, &tmU, G, m, blockIdx.x, 0, Q, rhou, bext, sigma, bout, Qs, err, qw);
 }
 
 // The CTA's batch class, its replica and tile: classes own consecutive CTA ranges.
@@ -628,8 +651,8 @@ __global__ void __launch_bounds__(qside_threads<TY, 1>(), sizeof(real) == 4 ? 2 
       mq = &maps.q[i];
       mu = &maps.u[i];
     }
-  qside_body<real, TY, 1, true>(mq, mu, G, m, it.bt, it.j, Q + 5 * o, rhou + 4 * o, nullptr, sigma + 5 * o,
-                                bout + 3 * o, Qs + 5 * o, err);
+  qside_body<real, TY, 1, true, false>(mq, mu, G, m, it.bt, it.j, Q + 5 * o, rhou + 4 * o, nullptr, sigma + 5 * o,
+                                       bout + 3 * o, Qs + 5 * o, err, Sym5<real>{});
 }
 
 // ---------------------------------------------------------------------------
@@ -647,14 +670,18 @@ struct LbqSmem {
   static constexpr size_t bytes = sizeof(real) * (size_t)SLOTS * SLOT + 8 * 8 + 16;
 };
 
-template <typename real, int TY, int SPT, bool BATCH>
+// WALLS: walls half a spacing below z = 0 and above z = nz-1.  A population
+// that would arrive from beyond a wall is the reflected one of the same site
+// (half-way bounce-back); the staged Q* of a ghost plane is the anchored qw and
+// its velocity is -u of the adjacent plane.
+template <typename real, int TY, int SPT, bool BATCH, bool WALLS>
 __device__ __forceinline__ void lbq_body(const CUtensorMap* tmU, const CUtensorMap* tmS, const CUtensorMap* tmB,
                                          const CUtensorMap* tmQs, const ZmGeom& G, const Model<real>& m, int bt,
                                          int rc, const real* __restrict__ f, const real* __restrict__ rhou,
                                          const real* __restrict__ sigma, const real* __restrict__ bf,
                                          const real* __restrict__ Qs, const real* __restrict__ Qin,
                                          real* __restrict__ fnew, real* __restrict__ rhou_new,
-                                         real* __restrict__ Qout, int* __restrict__ err) {
+                                         real* __restrict__ Qout, int* __restrict__ err, const Sym5<real> qw) {
   using L = LbqSmem<real, TY>;
   using V = typename LaneT<real, SPT>::V;
   constexpr int TYH = TY / SPT;  // a thread takes rows ty + k * TYH, k < SPT
@@ -745,7 +772,20 @@ __device__ __forceinline__ void lbq_body(const CUtensorMap* tmU, const CUtensorM
     dst = (int)(slot(p) - ring) + off + (k * L::ROWS + r) * ZM_BX + c;
     return g[k * n + image_site(r, c, nx, ny, wrap(p, nz), x0, y0 - 1)];
   };
+  // a staged plane beyond a wall: only its Q* is read (the anchored qw)
+  auto ghost = [&](int p) { return WALLS && (p < 0 || p >= nz); };
+  auto fill = [&](int p) {
+    real* sl = slot(p) + L::OFF_Q;
+    for (int t = threadIdx.x; t < 5 * CS; t += blockDim.x) {
+      const int k = t / CS;
+      sl[t] = k == 0 ? qw.xx : k == 1 ? qw.xy : k == 2 ? qw.xz : k == 3 ? qw.yy : qw.yz;
+    }
+  };
   auto patch = [&](int p) {
+    if (ghost(p)) {
+      fill(p);
+      return;
+    }
     for (int t = threadIdx.x; t < items; t += blockDim.x) {
       int d;
       const real v = patch_item(t, p, d);
@@ -790,6 +830,7 @@ __device__ __forceinline__ void lbq_body(const CUtensorMap* tmU, const CUtensorM
   for (int z = z0; z < z1; ++z) {
     // populations f_i(y - e_i), issued before the barrier wait so that they overlap it
     real fin_l[SPT][NV];
+    const bool wlo = WALLS && z == 0, whi = WALLS && z == nz - 1;
     if (valid) {
       const int zm = z == 0 ? nz - 1 : z - 1, zp = z + 1 == nz ? 0 : z + 1;
 #pragma unroll
@@ -802,7 +843,8 @@ __device__ __forceinline__ void lbq_body(const CUtensorMap* tmU, const CUtensorM
 #pragma unroll
         for (int i = 0; i < NV; ++i) {
           const int sx = ex(i) > 0 ? xm : ex(i) < 0 ? xp : gx;
-          fin_l[k][i] = __ldg(f + i * n + rb[1 - ez(i)][1 - ey(i)] + sx);
+          if ((ez(i) > 0 && wlo) || (ez(i) < 0 && whi)) fin_l[k][i] = __ldg(f + opp(i) * n + rb[1][1] + gx);
+          else fin_l[k][i] = __ldg(f + i * n + rb[1 - ez(i)][1 - ey(i)] + sx);
         }
       }
     }
@@ -818,14 +860,14 @@ __device__ __forceinline__ void lbq_body(const CUtensorMap* tmU, const CUtensorM
     for (int q = 0; q < KP; ++q) {
       const int t = threadIdx.x + q * blockDim.x;
       pd[q] = -1;
-      if (small_frame ? q == 0 && z + 2 <= z1 && t < items : t < items)
+      if (small_frame ? q == 0 && z + 2 <= z1 && t < items && !ghost(z + 2) : t < items && !ghost(z + 1))
         pv[q] = patch_item(t, small_frame ? z + 2 : z + 1, pd[q]);
     }
     const bool landed = wait(z + 1);
     if (landed && small_frame && d_ahead >= 0) ring[d_ahead] = v_ahead;
     v_ahead = pv[0];
     d_ahead = small_frame ? pd[0] : -1;
-    if (landed && !small_frame) {
+    if (landed && !small_frame && !ghost(z + 1)) {
 #pragma unroll
       for (int q = 0; q < KP; ++q)
         if (pd[q] >= 0) ring[pd[q]] = pv[q];
@@ -835,6 +877,7 @@ __device__ __forceinline__ void lbq_body(const CUtensorMap* tmU, const CUtensorM
         ring[d] = v;
       }
     }
+    if (landed && ghost(z + 1)) fill(z + 1);
     __syncthreads();
     if (*abort_flag) {
       aborted = true;
@@ -859,9 +902,19 @@ __device__ __forceinline__ void lbq_body(const CUtensorMap* tmU, const CUtensorM
         else fin[i] = V(fin_l[0][i], fin_l[SPT - 1][i], 0);
       }
       Sym5<V> sig_y;
-      V b_y[3];
+      V b_y[3], drho_y, u_y[3];
 #pragma unroll
       for (int i = 0; i < NV; ++i) {
+        if ((ez(i) > 0 && wlo) || (ez(i) < 0 && whi)) {
+          // half-way bounce-back: [f + C]_opp(i) of this site (i = 0 came first)
+          const int o = opp(i);
+          const V usq = u_y[0] * u_y[0] + u_y[1] * u_y[1] + u_y[2] * u_y[2];
+          V C = (feq_delta(o, drho_y, V(1) + drho_y, u_y[0], u_y[1], u_y[2], usq, sig_y) - fin[i]) * inv_tau;
+          C += force_dir(o, b_y[0], b_y[1], b_y[2]);
+          ds[i] = fin[i] + C;
+          dh[i] = fin[i] + V(0.5) * C;
+          continue;
+        }
         const real* sl = ez(i) > 0 ? nm : ez(i) < 0 ? np : nc;
         const int idx = ci - ey(i) * ZM_BX - ex(i);
         const V drho = Nv(sl, 0, idx);
@@ -873,6 +926,10 @@ __device__ __forceinline__ void lbq_body(const CUtensorMap* tmU, const CUtensorM
           b_y[0] = bx;
           b_y[1] = by;
           b_y[2] = bz;
+          drho_y = drho;
+          u_y[0] = ux;
+          u_y[1] = uy;
+          u_y[2] = uz;
         }
         const V usq = ux * ux + uy * uy + uz * uz;
         V C = (feq_delta(i, drho, V(1) + drho, ux, uy, uz, usq, sv) - fin[i]) * inv_tau;
@@ -939,7 +996,10 @@ __device__ __forceinline__ void lbq_body(const CUtensorMap* tmU, const CUtensorM
         u[a] = Nv(nc, a + 1, ci);
         w[a][0] = half * (Nv(nc, a + 1, ci + 1) - Nv(nc, a + 1, ci - 1));
         w[a][1] = half * (Nv(nc, a + 1, ci + ZM_BX) - Nv(nc, a + 1, ci - ZM_BX));
-        w[a][2] = half * (Nv(np, a + 1, ci) - Nv(nm, a + 1, ci));
+        V upz = Nv(np, a + 1, ci), umz = Nv(nm, a + 1, ci);
+        if (wlo) umz = -u[a];  // no slip half a spacing beyond the wall
+        if (whi) upz = -u[a];
+        w[a][2] = half * (upz - umz);
       }
       const Sym5<V> r = be_rate(st.c, h, dq, u, w, mv, true);
       Sym5<V> q0;
@@ -965,15 +1025,16 @@ __device__ __forceinline__ void lbq_body(const CUtensorMap* tmU, const CUtensorM
   }
 }
 
-template <typename real, int TY, int SPT>
+template <typename real, int TY, int SPT, bool WALLS>
 __global__ void __launch_bounds__(ZM_TX* TY / SPT, 2)
     k_lbq(const __grid_constant__ CUtensorMap tmU, const __grid_constant__ CUtensorMap tmS,
           const __grid_constant__ CUtensorMap tmB, const __grid_constant__ CUtensorMap tmQs, ZmGeom G, Model<real> m,
           const real* __restrict__ f, const real* __restrict__ rhou, const real* __restrict__ sigma,
           const real* __restrict__ bf, const real* __restrict__ Qs, const real* __restrict__ Qin,
-          real* __restrict__ fnew, real* __restrict__ rhou_new, real* __restrict__ Qout, int* __restrict__ err) {
-  lbq_body<real, TY, SPT, false>(&tmU, &tmS, &tmB, &tmQs, G, m, blockIdx.x, 0, f, rhou, sigma, bf, Qs, Qin, fnew,
-                                 rhou_new, Qout, err);
+          real* __restrict__ fnew, real* __restrict__ rhou_new, real* __restrict__ Qout, int* __restrict__ err,
+          Sym5<real> qw) {
+  lbq_body<real, TY, SPT, false, WALLS>(&tmU, &tmS, &tmB, &tmQs, G, m, blockIdx.x, 0, f, rhou, sigma, bf, Qs, Qin,
+                                        fnew, rhou_new, Qout, err, qw);
 }
 
 template <typename real, int TY>
@@ -1001,8 +1062,9 @@ __global__ void __launch_bounds__(ZM_TX* TY, 2)
       mb = &maps.b[i];
       mqs = &maps.qs[i];
     }
-  lbq_body<real, TY, 1, true>(mu, ms, mb, mqs, G, m, it.bt, it.j, f + NV * o, rhou + 4 * o, sigma + 5 * o, bf + 3 * o, Qs + 5 * o, Qin + 5 * o,
-                              fnew + NV * o, rhou_new + 4 * o, Qout + 5 * o, err);
+  lbq_body<real, TY, 1, true, false>(mu, ms, mb, mqs, G, m, it.bt, it.j, f + NV * o, rhou + 4 * o, sigma + 5 * o,
+                                     bf + 3 * o, Qs + 5 * o, Qin + 5 * o, fnew + NV * o, rhou_new + 4 * o,
+                                     Qout + 5 * o, err, Sym5<real>{});
 }
 
 // ---------------------------------------------------------------------------
@@ -1024,22 +1086,24 @@ constexpr int zm_max_spt() {
   return sizeof(real) == 4 ? 2 : 1;
 }
 
-template <typename real, int SPT>
+template <typename real, int SPT, bool WALLS>
 cudaError_t zm_prepare_spt() {
   constexpr int TY = zm_ty<real>();
-  cudaError_t e = cudaFuncSetAttribute(k_qside<real, TY, SPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(k_qside<real, TY, SPT, WALLS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)QsideSmem<real, TY>::bytes);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_lbq<real, TY, SPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(k_lbq<real, TY, SPT, WALLS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)LbqSmem<real, TY>::bytes);
   return e;
 }
 
+// lattices with walls run one site per thread
 template <typename real>
 cudaError_t zm_prepare() {
-  cudaError_t e = zm_prepare_spt<real, 1>();
+  cudaError_t e = zm_prepare_spt<real, 1, false>();
+  if (e == cudaSuccess) e = zm_prepare_spt<real, 1, true>();
   if constexpr (zm_max_spt<real>() == 2)
-    if (e == cudaSuccess) e = zm_prepare_spt<real, 2>();
+    if (e == cudaSuccess) e = zm_prepare_spt<real, 2, false>();
   return e;
 }
 
@@ -1053,7 +1117,7 @@ template <typename real, int SPT>
 int zm_resident_spt() {
   constexpr int TY = zm_ty<real>();
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_lbq<real, TY, SPT>, ZM_TX * TY / SPT,
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_lbq<real, TY, SPT, false>, ZM_TX * TY / SPT,
                                                     LbqSmem<real, TY>::bytes) != cudaSuccess)
     n = 1;
   return n > 0 ? n : 1;
@@ -1079,32 +1143,35 @@ ZmGeom zm_geom(int nx, int ny, int nz, int zc, int ty) {
   return G;
 }
 
-template <typename real, int SPT>
+template <typename real, int SPT, bool WALLS>
 cudaError_t launch_step_zm_spt(const ZmArgs& a, cudaStream_t s) {
   constexpr int TY = zm_ty<real>();
   const ZmGeom G = zm_geom(a.nx, a.ny, a.nz, a.zc, TY);
   const int grid = G.tiles_x * G.tiles_y * G.tiles_z;
   const Model<real> m = *static_cast<const Model<real>*>(a.model);
+  Sym5<real> qw{};
+  if (WALLS) qw = {(real)a.q_wall[0], (real)a.q_wall[1], (real)a.q_wall[2], (real)a.q_wall[3], (real)a.q_wall[4]};
   if (a.events) cudaEventRecord(a.events[0], s);
-  k_qside<real, TY, SPT><<<grid, qside_threads<TY, SPT>(), QsideSmem<real, TY>::bytes, s>>>(
+  k_qside<real, TY, SPT, WALLS><<<grid, qside_threads<TY, SPT>(), QsideSmem<real, TY>::bytes, s>>>(
       *a.tm_q, *a.tm_u, G, m, static_cast<const real*>(a.q), static_cast<const real*>(a.rhou),
       static_cast<const real*>(a.bext), static_cast<real*>(a.sigma), static_cast<real*>(a.b),
-      static_cast<real*>(a.qs), a.err);
+      static_cast<real*>(a.qs), a.err, qw);
   if (a.events) cudaEventRecord(a.events[1], s);
-  k_lbq<real, TY, SPT><<<grid, ZM_TX * TY / SPT, LbqSmem<real, TY>::bytes, s>>>(
+  k_lbq<real, TY, SPT, WALLS><<<grid, ZM_TX * TY / SPT, LbqSmem<real, TY>::bytes, s>>>(
       *a.tm_u, *a.tm_sigma, *a.tm_b, *a.tm_qs, G, m, static_cast<const real*>(a.f),
       static_cast<const real*>(a.rhou), static_cast<const real*>(a.sigma), static_cast<const real*>(a.b),
       static_cast<const real*>(a.qs), static_cast<const real*>(a.q), static_cast<real*>(a.fnew),
-      static_cast<real*>(a.rhou_new), static_cast<real*>(a.qout ? a.qout : a.q), a.err);
+      static_cast<real*>(a.rhou_new), static_cast<real*>(a.qout ? a.qout : a.q), a.err, qw);
   if (a.events) cudaEventRecord(a.events[2], s);
   return cudaGetLastError();
 }
 
 template <typename real>
 cudaError_t launch_step_zm(const ZmArgs& a, cudaStream_t s) {
+  if (a.q_wall) return launch_step_zm_spt<real, 1, true>(a, s);
   if constexpr (zm_max_spt<real>() == 2)
-    if (a.spt == 2) return launch_step_zm_spt<real, 2>(a, s);
-  return launch_step_zm_spt<real, 1>(a, s);
+    if (a.spt == 2) return launch_step_zm_spt<real, 2, false>(a, s);
+  return launch_step_zm_spt<real, 1, false>(a, s);
 }
 
 template <typename real>
