@@ -19,6 +19,8 @@
 // global memory (each is used once).
 #include <cuda.h>
 
+#include <type_traits>
+
 #include "common.cuh"
 #include "kernels.h"
 #include "tma.cuh"
@@ -305,10 +307,6 @@ __device__ __forceinline__ void qside_body(const CUtensorMap* tmQ, const CUtenso
     }
   };
   auto patch_q = [&](int p) {
-    if (ghost(p)) {
-      fill_q(p);
-      return;
-    }
     for (int t = threadIdx.x; t < items_q; t += blockDim.x) {
       int d;
       const real v = patch_item(t, p, p, d);
@@ -454,6 +452,11 @@ __device__ __forceinline__ void qside_body(const CUtensorMap* tmQ, const CUtenso
   if (wait_u(z0)) patch_u(z0);
   __syncthreads();
   aborted = *abort_flag != 0;
+  if (WALLS && !aborted && (z0 < 2 || z0 + 1 >= nz)) {
+    for (int p = z0 - 2; p <= z0 + 1; ++p)
+      if (ghost(p)) fill_q(p);
+    __syncthreads();
+  }
   if (!aborted) {
     field_plane(z0 - 1);
     field_plane(z0);
@@ -474,7 +477,7 @@ __device__ __forceinline__ void qside_body(const CUtensorMap* tmQ, const CUtenso
     for (int q = 0; q < KP; ++q) {
       const int t = threadIdx.x + q * blockDim.x;
       pd[q] = -1;
-      if (t < items && !(t < items_q && ghost(z + 2))) pv[q] = patch_item(t, z + 2, z + 1, pd[q]);
+      if (t < items) pv[q] = patch_item(t, z + 2, z + 1, pd[q]);
     }
     const bool okq = wait_q(z + 2), oku = wait_u(z + 1);
     if (okq && oku) {
@@ -482,17 +485,19 @@ __device__ __forceinline__ void qside_body(const CUtensorMap* tmQ, const CUtenso
       for (int q = 0; q < KP; ++q)
         if (pd[q] >= 0) base[pd[q]] = pv[q];
       for (int t = threadIdx.x + KP * blockDim.x; t < items; t += blockDim.x) {
-        if (t < items_q && ghost(z + 2)) continue;
         int d;
         const real v = patch_item(t, z + 2, z + 1, d);
         base[d] = v;
       }
-      if (ghost(z + 2)) fill_q(z + 2);
     }
     __syncthreads();
     if (*abort_flag) {
       aborted = true;
       break;
+    }
+    if (ghost(z + 2)) {  // after the periodic images of that plane: a wall's ghost plane
+      fill_q(z + 2);
+      __syncthreads();
     }
     if (threadIdx.x == 0) {
       fence_proxy_async();
@@ -782,10 +787,6 @@ __device__ __forceinline__ void lbq_body(const CUtensorMap* tmU, const CUtensorM
     }
   };
   auto patch = [&](int p) {
-    if (ghost(p)) {
-      fill(p);
-      return;
-    }
     for (int t = threadIdx.x; t < items; t += blockDim.x) {
       int d;
       const real v = patch_item(t, p, d);
@@ -831,7 +832,11 @@ __device__ __forceinline__ void lbq_body(const CUtensorMap* tmU, const CUtensorM
     // populations f_i(y - e_i), issued before the barrier wait so that they overlap it
     real fin_l[SPT][NV];
     const bool wlo = WALLS && z == 0, whi = WALLS && z == nz - 1;
-    if (valid) {
+    // beside a wall, the bounce-back directions read the reflected population
+    // of the site itself (a build of its own; every other plane pulls)
+    auto pull = [&](auto wall_plane) {
+      constexpr bool WP = decltype(wall_plane)::value;
+      const bool wl = WP && wlo, wh = WP && whi;
       const int zm = z == 0 ? nz - 1 : z - 1, zp = z + 1 == nz ? 0 : z + 1;
 #pragma unroll
       for (int k = 0; k < SPT; ++k) {
@@ -843,10 +848,14 @@ __device__ __forceinline__ void lbq_body(const CUtensorMap* tmU, const CUtensorM
 #pragma unroll
         for (int i = 0; i < NV; ++i) {
           const int sx = ex(i) > 0 ? xm : ex(i) < 0 ? xp : gx;
-          if ((ez(i) > 0 && wlo) || (ez(i) < 0 && whi)) fin_l[k][i] = __ldg(f + opp(i) * n + rb[1][1] + gx);
+          if ((ez(i) > 0 && wl) || (ez(i) < 0 && wh)) fin_l[k][i] = __ldg(f + opp(i) * n + rb[1][1] + gx);
           else fin_l[k][i] = __ldg(f + i * n + rb[1 - ez(i)][1 - ey(i)] + sx);
         }
       }
+    };
+    if (valid) {
+      if (WALLS && (wlo || whi)) pull(std::true_type{});
+      else pull(std::false_type{});
     }
     // Periodic images of edge tiles.  Small frames (one value per thread):
     // the value for plane z+2 is read here and stored after the wait of the
@@ -860,14 +869,14 @@ __device__ __forceinline__ void lbq_body(const CUtensorMap* tmU, const CUtensorM
     for (int q = 0; q < KP; ++q) {
       const int t = threadIdx.x + q * blockDim.x;
       pd[q] = -1;
-      if (small_frame ? q == 0 && z + 2 <= z1 && t < items && !ghost(z + 2) : t < items && !ghost(z + 1))
+      if (small_frame ? q == 0 && z + 2 <= z1 && t < items : t < items)
         pv[q] = patch_item(t, small_frame ? z + 2 : z + 1, pd[q]);
     }
     const bool landed = wait(z + 1);
     if (landed && small_frame && d_ahead >= 0) ring[d_ahead] = v_ahead;
     v_ahead = pv[0];
     d_ahead = small_frame ? pd[0] : -1;
-    if (landed && !small_frame && !ghost(z + 1)) {
+    if (landed && !small_frame) {
 #pragma unroll
       for (int q = 0; q < KP; ++q)
         if (pd[q] >= 0) ring[pd[q]] = pv[q];
@@ -877,7 +886,6 @@ __device__ __forceinline__ void lbq_body(const CUtensorMap* tmU, const CUtensorM
         ring[d] = v;
       }
     }
-    if (landed && ghost(z + 1)) fill(z + 1);
     __syncthreads();
     if (*abort_flag) {
       aborted = true;
@@ -887,7 +895,17 @@ __device__ __forceinline__ void lbq_body(const CUtensorMap* tmU, const CUtensorM
       fence_proxy_async();
       if (z + 2 <= z1) issue(z + 2);
     }
-    if (valid) {
+    // a wall's ghost plane, after its periodic images: the anchored Q*
+    if (WALLS && (ghost(z + 1) || (z == z0 && ghost(z0 - 1)))) {
+      if (ghost(z + 1)) fill(z + 1);
+      if (z == z0 && ghost(z0 - 1)) fill(z0 - 1);
+      __syncthreads();
+    }
+    // a plane beside a wall runs a build of the plane's work with the
+    // bounce-back; every other plane runs the periodic build
+    auto plane_work = [&](auto wall_plane) {
+      constexpr bool WP = decltype(wall_plane)::value;
+      const bool wl = WP && wlo, wh = WP && whi;
       long long s[SPT];
 #pragma unroll
       for (int k = 0; k < SPT; ++k) s[k] = ((long long)z * ny + gy[k]) * nx + gx;
@@ -905,7 +923,7 @@ __device__ __forceinline__ void lbq_body(const CUtensorMap* tmU, const CUtensorM
       V b_y[3], drho_y, u_y[3];
 #pragma unroll
       for (int i = 0; i < NV; ++i) {
-        if ((ez(i) > 0 && wlo) || (ez(i) < 0 && whi)) {
+        if ((ez(i) > 0 && wl) || (ez(i) < 0 && wh)) {
           // half-way bounce-back: [f + C]_opp(i) of this site (i = 0 came first)
           const int o = opp(i);
           const V usq = u_y[0] * u_y[0] + u_y[1] * u_y[1] + u_y[2] * u_y[2];
@@ -997,8 +1015,8 @@ __device__ __forceinline__ void lbq_body(const CUtensorMap* tmU, const CUtensorM
         w[a][0] = half * (Nv(nc, a + 1, ci + 1) - Nv(nc, a + 1, ci - 1));
         w[a][1] = half * (Nv(nc, a + 1, ci + ZM_BX) - Nv(nc, a + 1, ci - ZM_BX));
         V upz = Nv(np, a + 1, ci), umz = Nv(nm, a + 1, ci);
-        if (wlo) umz = -u[a];  // no slip half a spacing beyond the wall
-        if (whi) upz = -u[a];
+        if (wl) umz = -u[a];  // no slip half a spacing beyond the wall
+        if (wh) upz = -u[a];
         w[a][2] = half * (upz - umz);
       }
       const Sym5<V> r = be_rate(st.c, h, dq, u, w, mv, true);
@@ -1014,6 +1032,10 @@ __device__ __forceinline__ void lbq_body(const CUtensorMap* tmU, const CUtensorM
 #pragma unroll
       for (int k = 0; k < SPT; ++k)
         if (lane_ok[k]) store5_lane<SPT, real>(Qout, n, s[k], q1, k);
+    };
+    if (valid) {
+      if (WALLS && (wlo || whi)) plane_work(std::true_type{});
+      else plane_work(std::false_type{});
     }
   }
   if (aborted && threadIdx.x == 0) {
