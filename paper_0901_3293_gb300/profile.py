@@ -1,11 +1,12 @@
 """Run a few coupled steps on an L^3 BPII lattice, for profilers.
 
-    python -m paper_0901_3293_gb300.profile --size 128 --steps 4 [--dtype f32]
+    python -m paper_0901_3293_gb300.profile --size 128 --steps 4 [--dtype f32] [--walls]
     python -m paper_0901_3293_gb300.profile --conv --dims 64 64 256 --steps 3
 
 Each step launches the step kernels once (no CUDA graph), so a profiler can
 select them by name and launch index.  --conv instead runs surrogate calls
-(ten tensor-core convolutions each) on a lattice of the given dims.
+(ten tensor-core convolutions each) on a lattice of the given dims.  --walls
+puts walls in z with a planar anchored Q (S (x x - I/3), S = 0.3).
 """
 
 from __future__ import annotations
@@ -25,6 +26,7 @@ def main():
     ap.add_argument("--dtype", default="f32")
     ap.add_argument("--conv", action="store_true")
     ap.add_argument("--dims", type=int, nargs=3, default=[64, 64, 256])
+    ap.add_argument("--walls", action="store_true")
     args = ap.parse_args()
     build.build()
     torch.cuda.set_device(0)
@@ -46,8 +48,10 @@ def main():
     lat = lcbp.Lattice(n, n, n, dtype=args.dtype)
     lat.set_ldg(0.01, 3.1, 0.01, 2 * math.pi / 32)
     lat.init_q(lcbp.BPII, 0.3, noise=1e-4, seed=20090119).init_f_equilibrium(1.0)
+    if args.walls:
+        lat.set_walls(True, (0.2, 0.0, 0.0, -0.1, 0.0))
     ms = lat.profile_steps(args.steps)
-    print({"size": n, "steps": args.steps, "kernel_ms": ms, "F": lat.free_energy()})
+    print({"size": n, "steps": args.steps, "walls": args.walls, "kernel_ms": ms, "F": lat.free_energy()})
 
 
 if __name__ == "__main__":
