@@ -2,11 +2,14 @@
 
     python -m paper_0901_3293_gb300.profile --size 128 --steps 4 [--dtype f32] [--walls]
     python -m paper_0901_3293_gb300.profile --conv --dims 64 64 256 --steps 3
+    python -m paper_0901_3293_gb300.profile --texture --dims 256 256 256 --steps 3
 
 Each step launches the step kernels once (no CUDA graph), so a profiler can
 select them by name and launch index.  --conv instead runs surrogate calls
 (ten tensor-core convolutions each) on a lattice of the given dims.  --walls
-puts walls in z with a planar anchored Q (S (x x - I/3), S = 0.3).
+puts walls in z with a planar anchored Q (S (x x - I/3), S = 0.3).  --texture
+renders the polarised-light texture of a BPII lattice of the given dims
+(pitch 32) `steps` times.
 """
 
 from __future__ import annotations
@@ -27,6 +30,7 @@ def main():
     ap.add_argument("--conv", action="store_true")
     ap.add_argument("--dims", type=int, nargs=3, default=[64, 64, 256])
     ap.add_argument("--walls", action="store_true")
+    ap.add_argument("--texture", action="store_true")
     args = ap.parse_args()
     build.build()
     torch.cuda.set_device(0)
@@ -43,6 +47,19 @@ def main():
         t0 = time.perf_counter()
         sur.step(lat, 1.0, -0.5, args.steps)
         print({"dims": args.dims, "calls": args.steps, "ms_per_call": 1e3 * (time.perf_counter() - t0) / args.steps})
+        return
+    if args.texture:
+        import time
+        nx, ny, nz = args.dims
+        lat = lcbp.Lattice(nx, ny, nz, dtype=args.dtype)
+        lat.set_ldg(0.01, 3.1, 0.01, 2 * math.pi / 32)
+        lat.init_q(lcbp.BPII, 0.3, noise=1e-4, seed=20090119)
+        lat.texture()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            img = lat.texture()
+        print({"dims": args.dims, "images": args.steps, "ms_per_image": 1e3 * (time.perf_counter() - t0) / args.steps,
+               "mean": float(img.mean())})
         return
     n = args.size
     lat = lcbp.Lattice(n, n, n, dtype=args.dtype)

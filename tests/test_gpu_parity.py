@@ -385,3 +385,45 @@ def test_full_size_sampled_parity_256(lcbp):
         du = np.abs(u1[:, z, y, x] - np.moveaxis(lbq.moments(fo)[1], -1, 0)[:, r, r, r]).max()
         assert dq < 1e-6 and du < 1e-6, ((z, y, x), dq, du)
     assert abs(m1 - m0) < 1e-6 * m0
+
+
+def test_full_size_sampled_parity_256_walls(lcbp):
+    """The same at 256^3 between walls in z (the walled fast kernels, as the
+    benchmark's walled line runs them).  A site within 4 planes of a wall is
+    compared with the walled oracle on a cube cut at that wall (the cube's
+    other, artificial wall lies beyond the step's reach); other sites with
+    the periodic oracle as above."""
+    qw = (0.2, 0.0, 0.0, -0.1, 0.0)
+    p = lbq.Params(q0=2 * np.pi / 32)
+    pw = lbq.Params(q0=2 * np.pi / 32, walls_z=True, q_wall=qw)
+    n = 256
+    lat = make(lcbp, (n, n, n), "f32", p)
+    lat.set_walls(True, qw)
+    lat.init_q(lcbp.BPII, 0.3, noise=1e-4, seed=SEED)
+    lat.init_f_equilibrium(1.0)
+    lat.step(2)
+    assert lat.path()[0]
+    q0 = lat.read_q(dtype=np.float32)
+    f0 = lat.read_f(dtype=np.float32)
+    lat.step(1)
+    q1 = lat.read_q(dtype=np.float32)
+    u1 = lat.read_u(dtype=np.float32)
+    rng = np.random.default_rng(11)
+    sites = [tuple(int(v) for v in rng.integers(0, n, 3)) for _ in range(6)]
+    sites += [(0, 0, 0), (1, 17, 200), (3, 255, 31), (255, 255, 255), (254, 3, 128), (252, 100, 0)]
+    r = 4
+    for (z, y, x) in sites:
+        iy, ix = (np.arange(c - r, c + r + 1) % n for c in (y, x))
+        if z < r:
+            iz, cz, pp = np.arange(0, 2 * r + 1), z, pw
+        elif z > n - 1 - r:
+            iz, cz, pp = np.arange(n - 1 - 2 * r, n), z - (n - 1 - 2 * r), pw
+        else:
+            iz, cz, pp = np.arange(z - r, z + r + 1), r, p
+        cube = np.ix_(iz, iy, ix)
+        Qc = lbq.q5_to_q9(q0[(slice(None),) + cube].astype(np.float64))
+        fc = lbq.f_from_soa(f0[(slice(None),) + cube].astype(np.float64))
+        fo, Qo = lbq.step(fc, Qc, pp)
+        dq = np.abs(q1[:, z, y, x] - lbq.q9_to_q5(Qo)[:, cz, r, r]).max()
+        du = np.abs(u1[:, z, y, x] - np.moveaxis(lbq.moments(fo)[1], -1, 0)[:, cz, r, r]).max()
+        assert dq < 1e-6 and du < 1e-6, ((z, y, x), dq, du)

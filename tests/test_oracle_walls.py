@@ -95,3 +95,31 @@ def test_coupled_step_with_walls_reduces_to_poiseuille_lb():
         f2 = lbq.lb_step(f2, np.zeros(shape + (3, 3)), g, p.tau_f, walls_z=True)
     assert np.abs(Q).max() == 0.0
     assert np.abs(f - f2).max() < 1e-17
+
+
+def test_walled_step_is_local():
+    """One coupled step at a site depends on the state within 4 sites: a cube
+    of 9 planes cut at a wall (with a second, artificial wall 5 or more planes
+    away) or, away from the walls, a periodic 9^3 cube reproduces the full
+    walled lattice's step at its sample site.  This is what the full-size
+    sampled parity of the GPU path rests on."""
+    p = lbq.Params(q0=2 * np.pi / 32)
+    pw = lbq.Params(q0=2 * np.pi / 32, walls_z=True, q_wall=PLANAR)
+    nz, n, r = 14, 9, 4
+    shape = (nz, n, n)
+    q5 = synth.smooth_q5(shape, 0.3, 1) + synth.random_q5(shape, 1e-2, 2)
+    f15 = synth.random_distributions(shape, 3, amp=2e-3)
+    f, Q = lbq.step(lbq.f_from_soa(f15), lbq.q5_to_q9(q5), pw)
+    qf, uf = lbq.q9_to_q5(Q), np.moveaxis(lbq.moments(f)[1], -1, 0)
+    for z, y, x in [(0, 3, 7), (2, 0, 0), (4, 8, 1), (6, 4, 4), (9, 2, 5), (11, 6, 8), (13, 1, 3)]:
+        iy, ix = (np.arange(c - r, c + r + 1) % n for c in (y, x))
+        if z < r:
+            iz, cz, pp = np.arange(0, 2 * r + 1), z, pw
+        elif z > nz - 1 - r:
+            iz, cz, pp = np.arange(nz - 1 - 2 * r, nz), z - (nz - 1 - 2 * r), pw
+        else:
+            iz, cz, pp = np.arange(z - r, z + r + 1), r, p
+        cube = np.ix_(iz, iy, ix)
+        fo, Qo = lbq.step(lbq.f_from_soa(f15[(slice(None),) + cube]), lbq.q5_to_q9(q5[(slice(None),) + cube]), pp)
+        assert np.abs(qf[:, z, y, x] - lbq.q9_to_q5(Qo)[:, cz, r, r]).max() < 1e-15
+        assert np.abs(uf[:, z, y, x] - np.moveaxis(lbq.moments(fo)[1], -1, 0)[:, cz, r, r]).max() < 1e-15
