@@ -86,20 +86,33 @@ struct Frame {
       r = rb + q;
       c = C0 + m;
     } else if (t < n_tbl) {
+      // a side column block is H wide on a lattice whose nx is a multiple of 4
+      // (the constant divisor); the division covers any other width
       const int u = t - n_tb;
-      r = ra + u / lw;
-      c = C0 + u % lw;
+      const int q = lw == H ? u / H : u / lw;
+      r = ra + q;
+      c = C0 + u - q * lw;
     } else {
       const int u = t - n_tbl;
-      r = ra + u / rw;
-      c = C0 + w - rw + u % rw;
+      const int q = rw == H ? u / H : u / rw;
+      r = ra + q;
+      c = C0 + w - rw + u - q * rw;
     }
   }
 };
 
-// site of the periodic image of frame cell (r, c) on plane gz
-__device__ __forceinline__ long long image_site(int r, int c, int nx, int ny, int gz, int x0, int gy0) {
-  return ((long long)gz * ny + wrap(gy0 + r, ny)) * nx + wrap(x0 - ZM_XOFF + c, nx);
+// Periodic coordinates of a CTA's staged box, wrapped once per CTA: xw[c] for
+// box column c (global x = x0 - ZM_XOFF + c), yw[r] for box row r (global
+// y = gy0 + r).  The periodic image of frame cell (r, c) of plane gz is then
+// two shared-memory reads away instead of two divisions.
+__device__ __forceinline__ void fill_wrap_tables(int* xw, int* yw, int rows, int nx, int ny, int x0, int gy0) {
+  for (int i = threadIdx.x; i < ZM_BX + rows; i += blockDim.x) {
+    if (i < ZM_BX) xw[i] = wrap(x0 - ZM_XOFF + i, nx);
+    else yw[i - ZM_BX] = wrap(gy0 + i - ZM_BX, ny);
+  }
+}
+__device__ __forceinline__ long long image_site(int r, int c, int nx, int ny, int gz, const int* xw, const int* yw) {
+  return ((long long)gz * ny + yw[r]) * nx + xw[c];
 }
 
 // TMA tile load of plane z of a field: 4-D (x, y, z, component) for one
@@ -192,7 +205,8 @@ struct QsideSmem {
   static constexpr int TSLOT = 3 * TROWS * TCOLS, HSLOT = 5 * TY * ZM_TX;
   static constexpr int OFF_U = QSLOTS * QSLOT, OFF_T = OFF_U + USLOTS * USLOT;
   static constexpr int OFF_H = OFF_T + 3 * TSLOT, OFF_BAR = align_elems(OFF_H + 2 * HSLOT, sizeof(real));
-  static constexpr size_t bytes = sizeof(real) * (size_t)OFF_BAR + 16 * 8 + 16;
+  // barriers, the abort flag, then the wrapped box columns and rows (Q box)
+  static constexpr size_t bytes = sizeof(real) * (size_t)OFF_BAR + 16 * 8 + 16 + sizeof(int) * (ZM_BX + QROWS);
 };
 
 // Threads of a k_qside CTA: enough to cover the H / tau ring of a plane
@@ -227,6 +241,8 @@ __device__ __forceinline__ void qside_body(const CUtensorMap* tmQ, const CUtenso
   real* hbuf = base + L::OFF_H;
   uint64_t* bars = reinterpret_cast<uint64_t*>(base + L::OFF_BAR);  // 5 Q + 4 u
   int* abort_flag = reinterpret_cast<int*>(bars + 16);
+  int* xw = abort_flag + 4;  // wrapped box columns, then rows of the Q box (y0 - 2 ...)
+  int* yw = xw + ZM_BX;
 
   const int nx = G.nx, ny = G.ny, nz = G.nz;
   const long long n = G.n;
@@ -247,6 +263,7 @@ __device__ __forceinline__ void qside_body(const CUtensorMap* tmQ, const CUtenso
     tma_prefetch_desc(tmQ);
     tma_prefetch_desc(tmU);
   }
+  fill_wrap_tables(xw, yw, L::QROWS, nx, ny, x0, y0 - 2);
   __syncthreads();
 
   // plane p of Q lives in slot (p - (z0-2)) % 5, of rho u in slot (p - (z0-1)) % 4
@@ -290,12 +307,12 @@ __device__ __forceinline__ void qside_body(const CUtensorMap* tmQ, const CUtenso
       const int cell = t / 5, k = t - 5 * cell;
       FQ.cell(cell, r, c);
       dst = (int)(qslot(pq) - base) + (k * L::QROWS + r) * ZM_BX + c;
-      return Q[k * n + image_site(r, c, nx, ny, wrap(pq, nz), x0, y0 - 2)];
+      return Q[k * n + image_site(r, c, nx, ny, wrap(pq, nz), xw, yw)];
     }
     const int u = t - items_q, cell = u / 4, k = u - 4 * cell;
     FU.cell(cell, r, c);
     dst = (int)(uslot(pu) - base) + (k * L::UROWS + r) * ZM_BX + c;
-    return rhou[k * n + image_site(r, c, nx, ny, wrap(pu, nz), x0, y0 - 1)];
+    return rhou[k * n + image_site(r, c, nx, ny, wrap(pu, nz), xw, yw + 1)];
   };
   // a staged Q plane beyond a wall: qw in every cell (no periodic images)
   auto ghost = [&](int p) { return WALLS && (p < 0 || p >= nz); };
@@ -672,7 +689,8 @@ struct LbqSmem {
   static constexpr int OFF_B = OFF_S + align_elems(5 * CS, sizeof(real));
   static constexpr int OFF_Q = OFF_B + align_elems(3 * CS, sizeof(real));
   static constexpr int SLOT = OFF_Q + align_elems(5 * CS, sizeof(real));
-  static constexpr size_t bytes = sizeof(real) * (size_t)SLOTS * SLOT + 8 * 8 + 16;
+  // barriers, the abort flag, then the wrapped box columns and rows
+  static constexpr size_t bytes = sizeof(real) * (size_t)SLOTS * SLOT + 8 * 8 + 16 + sizeof(int) * (ZM_BX + ROWS);
 };
 
 // WALLS: walls half a spacing below z = 0 and above z = nz-1.  A population
@@ -694,6 +712,8 @@ __device__ __forceinline__ void lbq_body(const CUtensorMap* tmU, const CUtensorM
   real* ring = reinterpret_cast<real*>(smem_raw);
   uint64_t* bars = reinterpret_cast<uint64_t*>(ring + L::SLOTS * L::SLOT);
   int* abort_flag = reinterpret_cast<int*>(bars + 8);
+  int* xw = abort_flag + 4;  // wrapped box columns, then rows (y0 - 1 ...)
+  int* yw = xw + ZM_BX;
 
   const int nx = G.nx, ny = G.ny, nz = G.nz;
   const long long n = G.n;
@@ -725,6 +745,7 @@ __device__ __forceinline__ void lbq_body(const CUtensorMap* tmU, const CUtensorM
     tma_prefetch_desc(tmB);
     tma_prefetch_desc(tmQs);
   }
+  fill_wrap_tables(xw, yw, L::ROWS, nx, ny, x0, y0 - 1);
   __syncthreads();
 
   auto slot = [&](int p) { return ring + ((p - (z0 - 1)) % L::SLOTS) * L::SLOT; };
@@ -775,7 +796,7 @@ __device__ __forceinline__ void lbq_body(const CUtensorMap* tmU, const CUtensorM
       off = L::OFF_Q;
     }
     dst = (int)(slot(p) - ring) + off + (k * L::ROWS + r) * ZM_BX + c;
-    return g[k * n + image_site(r, c, nx, ny, wrap(p, nz), x0, y0 - 1)];
+    return g[k * n + image_site(r, c, nx, ny, wrap(p, nz), xw, yw)];
   };
   // a staged plane beyond a wall: only its Q* is read (the anchored qw)
   auto ghost = [&](int p) { return WALLS && (p < 0 || p >= nz); };
