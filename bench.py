@@ -53,12 +53,12 @@ STATE_BYTES = (15 + 5) * 2 * 4  # read + write of f and Q once per site-step (FP
 MEASURED_TRAFFIC = {
     "sources": ["paper_0901_3293_gb300/csrc/zmarch.cu", "paper_0901_3293_gb300/csrc/common.cuh",
                 "paper_0901_3293_gb300/csrc/tma.cuh"],
-    "sha256_16": "0c6b82d2c267915b",
+    "sha256_16": "10a96bb51b515a70",
     # mean of the two launches of each kernel in the capture
-    "bytes_per_site": {"qside": (163052288 + 169490944 + 162989056 + 166867200) / 2 / 160 ** 3,
-                       "lbq": (650430208 + 358712320 + 652419328 + 359530496) / 2 / 160 ** 3},
+    "bytes_per_site": {"qside": (162189312 + 168708352 + 162051072 + 166233344) / 2 / 160 ** 3,
+                       "lbq": (643585280 + 357165312 + 644718592 + 358393088) / 2 / 160 ** 3},
     # smsp__inst_executed.sum (warp instructions) x 32 of one launch (ncu --set full on the same case)
-    "thread_instr_per_site": {"qside": 151784048 * 32 / 160 ** 3, "lbq": 190925460 * 32 / 160 ** 3},
+    "thread_instr_per_site": {"qside": 145553136 * 32 / 160 ** 3, "lbq": 187514228 * 32 / 160 ** 3},
 }
 ORACLE_SAMPLE = 32  # side of the periodic cube the oracle steps (two BPII unit cells)
 WALL_Q = (0.2, 0.0, 0.0, -0.1, 0.0)  # planar anchoring S (x x - I/3), S = 0.3, on the ghost planes
@@ -361,20 +361,27 @@ def run_ours(args):
     u_h = torch.empty((3, n, n, n), dtype=torch.float32, pin_memory=True)
     lat.read_f(out=f_h)
     lat.read_q(out=q_h)
-    barrier()
-    t0 = time.perf_counter()
-    for _ in range(k_e2e):
+
+    def e2e_step():
         lat.set_f(f_h)
         lat.set_q(q_h)
         lat.step(1)
         lat.read_q(out=q_h)
         lat.read_u(out=u_h)
+
+    for _ in range(2):  # untimed: the first copies through freshly pinned buffers run slow
+        e2e_step()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(k_e2e):
+        e2e_step()
     barrier()
     e2e_s = allmax(time.perf_counter() - t0)
     e2e = {"value": sites * k_e2e * world / e2e_s / 1e6, "unit": "MLUPS",
            "h2d_bytes_per_step": (15 + 5) * 4 * sites, "d2h_bytes_per_step": (5 + 3) * 4 * sites,
-           "steps": k_e2e, "note": "lcbp_set_f + lcbp_set_q from pinned host memory, lcbp_step(1), "
-                                   "lcbp_read_q + lcbp_read_u to pinned host memory"}
+           "steps": k_e2e, "warmup": 2,
+           "note": "lcbp_set_f + lcbp_set_q from pinned host memory, lcbp_step(1), "
+                   "lcbp_read_q + lcbp_read_u to pinned host memory"}
     launches = (2 if fast else 3) * args.steps
 
     # ---- the same lattice between walls in z (half-way bounce-back, Q anchored
