@@ -59,3 +59,13 @@ def test_reference_arm_prints_from_rank_zero_only():
                         "--steps", "3", "--warmup", "3"], env=env, capture_output=True, text=True, timeout=300)
     assert r.returncode == 0, r.stderr
     assert r.stdout.strip() == ""
+
+
+def test_oracle_baseline_copies_run_together():
+    """The all-cores CPU baseline: independent oracle samples in child
+    processes whose timed loops start together; the value counts every copy."""
+    m1, dt1 = bench.oracle_in_subprocess(1, 0)
+    m2, dt2 = bench.oracle_in_subprocess(1, 0, copies=2)
+    sites = bench.ORACLE_SAMPLE ** 3
+    assert m1 == pytest.approx(sites / dt1 / 1e6)
+    assert m2 == pytest.approx(2 * sites / dt2 / 1e6)
