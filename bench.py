@@ -457,19 +457,9 @@ def run_ours(args):
     tex_lat.close()
 
     # ---- the 48-replica sweep (32^3 / 48^3, per-replica kappa and tau) in one batch
-    from paper_0901_3293_gb300 import synth
-    sweep = synth.replica_sweep(48, SEED)
-    bparams = []
-    for sw in sweep:
-        g = 27.0 / (9.0 + sw["tau"])
-        q0 = 2 * np.pi / 16
-        bparams.append(dict(A0=0.01, gamma=g, K=sw["kappa"] ** 2 * 0.01 * g / (108 * q0 * q0), q0=q0,
-                            tau_f=2.0, xi=0.7, Gamma=0.3))
-    batch = lcbp.Batch([sw["dims"] for sw in sweep], bparams, dtype="f32")
-    for r, sw in enumerate(sweep):
-        kind = (lcbp.BPII, lcbp.CHOL_Z, lcbp.ISO_NOISE)[sw["kind"]]
-        batch.init_q(r, kind, 0.3 if sw["kind"] == 0 else 0.4, noise=1e-2, seed=sw["seed"])
-    batch.init_f_equilibrium(1.0).step(max(4, args.warmup))
+    from paper_0901_3293_gb300 import workloads
+    batch = workloads.replica_sweep_batch(48, SEED, "f32")
+    batch.step(max(4, args.warmup))
     batch.synchronize()
     bsites = batch.info()["sites"]
     bs = torch.cuda.Stream()

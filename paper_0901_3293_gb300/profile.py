@@ -3,13 +3,17 @@
     python -m paper_0901_3293_gb300.profile --size 128 --steps 4 [--dtype f32] [--walls]
     python -m paper_0901_3293_gb300.profile --conv --dims 64 64 256 --steps 3
     python -m paper_0901_3293_gb300.profile --texture --dims 256 256 256 --steps 3
+    python -m paper_0901_3293_gb300.profile --batch --steps 4
 
 Each step launches the step kernels once (no CUDA graph), so a profiler can
 select them by name and launch index.  --conv instead runs surrogate calls
 (ten tensor-core convolutions each) on a lattice of the given dims.  --walls
 puts walls in z with a planar anchored Q (S (x x - I/3), S = 0.3).  --texture
 renders the polarised-light texture of a BPII lattice of the given dims
-(pitch 32) `steps` times.
+(pitch 32) `steps` times.  --batch steps the 48-replica chirality/temperature
+sweep (24 x 32^3 + 24 x 48^3) in one batch: ten steps (kernel selection and
+tuning), then `steps` single steps inside the NVTX range "timed", so that a
+profiler can take exactly those launches (--nvtx --nvtx-include "timed/").
 """
 
 from __future__ import annotations
@@ -31,6 +35,7 @@ def main():
     ap.add_argument("--dims", type=int, nargs=3, default=[64, 64, 256])
     ap.add_argument("--walls", action="store_true")
     ap.add_argument("--texture", action="store_true")
+    ap.add_argument("--batch", action="store_true")
     args = ap.parse_args()
     build.build()
     torch.cuda.set_device(0)
@@ -47,6 +52,22 @@ def main():
         t0 = time.perf_counter()
         sur.step(lat, 1.0, -0.5, args.steps)
         print({"dims": args.dims, "calls": args.steps, "ms_per_call": 1e3 * (time.perf_counter() - t0) / args.steps})
+        return
+    if args.batch:
+        import time
+
+        from . import workloads
+        batch = workloads.replica_sweep_batch(48, dtype=args.dtype)
+        batch.step(10)
+        batch.synchronize()
+        torch.cuda.nvtx.range_push("timed")
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            batch.step(1)
+        batch.synchronize()
+        dt = time.perf_counter() - t0
+        torch.cuda.nvtx.range_pop()
+        print({"replicas": 48, "steps": args.steps, "path": batch.path(), "ms_per_step": 1e3 * dt / args.steps})
         return
     if args.texture:
         import time
