@@ -272,36 +272,64 @@ template cudaError_t launch_shift<float>(const void*, void*, long long, int, int
 template cudaError_t launch_shift<double>(const void*, void*, long long, int, int, int, cudaStream_t);
 
 // ---------------------------------------------------------------------------
-// Diagnostics in FP64.  Largest eigenvalue of a symmetric 3x3 matrix by the
-// trigonometric closed form (O. K. Smith, CACM 4(4):168, 1961).
+// Diagnostics: F_h (Sec. 2.1, the lattice energy whose gradient is H), mass,
+// momentum, the defect fraction #(lambda_max(Q) < threshold) / N (Sec. 2.1)
+// and a count of non-finite sites, in one pass.  The per-site arithmetic runs
+// in the state's precision (C = real); every sum over sites is FP64.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double lambda_max(const double a[3][3]) {
-  const double p1 = a[0][1] * a[0][1] + a[0][2] * a[0][2] + a[1][2] * a[1][2];
-  const double qm = (a[0][0] + a[1][1] + a[2][2]) / 3.0;
-  const double d0 = a[0][0] - qm, d1 = a[1][1] - qm, d2 = a[2][2] - qm;
-  const double p2 = d0 * d0 + d1 * d1 + d2 * d2 + 2.0 * p1;
-  if (p2 <= 0.0) return qm;
-  const double p = sqrt(p2 / 6.0);
-  const double b00 = d0 / p, b11 = d1 / p, b22 = d2 / p;
-  const double b01 = a[0][1] / p, b02 = a[0][2] / p, b12 = a[1][2] / p;
-  const double det = b00 * (b11 * b22 - b12 * b12) - b01 * (b01 * b22 - b12 * b02) + b02 * (b01 * b12 - b11 * b02);
-  double r = 0.5 * det;
-  r = r < -1.0 ? -1.0 : (r > 1.0 ? 1.0 : r);
-  const double phi = acos(r) / 3.0;
-  return qm + 2.0 * p * cos(phi);
+// lambda_max(a) < t  <=>  t I - a is positive definite  <=>  the leading
+// principal minors of t I - a are all positive (Sylvester's criterion)
+__device__ __forceinline__ bool top_eigenvalue_below(double xx, double xy, double xz, double yy, double yz,
+                                                     double t) {
+  const double zz = -xx - yy;
+  const double b00 = t - xx, b11 = t - yy, b22 = t - zz;
+  const double m2 = b00 * b11 - xy * xy;
+  const double m3 = b00 * (b11 * b22 - yz * yz) - xy * (xy * b22 + yz * xz) - xz * (xy * yz + b11 * xz);
+  return b00 > 0.0 && m2 > 0.0 && m3 > 0.0;
 }
 
-template <typename real>
-__device__ __forceinline__ void q9(const real* __restrict__ qp, long long n, long long s, double m[3][3]) {
-  const double xx = qp[s], xy = qp[n + s], xz = qp[2 * n + s], yy = qp[3 * n + s], yz = qp[4 * n + s];
-  m[0][0] = xx; m[0][1] = xy; m[0][2] = xz;
-  m[1][0] = xy; m[1][1] = yy; m[1][2] = yz;
-  m[2][0] = xz; m[2][1] = yz; m[2][2] = -xx - yy;
+// The same decision for a site of the state's precision.  FP32: the minors in
+// FP32 decide unless one lies within 1e-4 m^k of zero (m: the largest entry of
+// t I - Q in size, k: the minor's order), far above their rounding error (a
+// few ulp of m^k); such sites are decided in FP64 as above.
+template <typename C>
+__device__ __forceinline__ bool top_eigenvalue_below(const Sym5<C>& q, double t) {
+  if constexpr (sizeof(C) == 8) {
+    return top_eigenvalue_below(q.xx, q.xy, q.xz, q.yy, q.yz, t);
+  } else {
+    const float tf = (float)t, zz = -q.xx - q.yy;
+    const float b00 = tf - q.xx, b11 = tf - q.yy, b22 = tf - zz;
+    const float m = fmaxf(fmaxf(fmaxf(fabsf(b00), fabsf(b11)), fmaxf(fabsf(b22), fabsf(q.xy))),
+                          fmaxf(fabsf(q.xz), fabsf(q.yz)));
+    const float m2 = b00 * b11 - q.xy * q.xy;
+    const float m3 =
+        b00 * (b11 * b22 - q.yz * q.yz) - q.xy * (q.xy * b22 + q.yz * q.xz) - q.xz * (q.xy * q.yz + b11 * q.xz);
+    const float e1 = 1e-4f * m, e2 = e1 * m, e3 = e2 * m;
+    if (b00 < -e1 || m2 < -e2 || m3 < -e3) return false;
+    if (b00 > e1 && m2 > e2 && m3 > e3) return true;
+    return top_eigenvalue_below((double)q.xx, (double)q.xy, (double)q.xz, (double)q.yy, (double)q.yz, t);
+  }
+}
+
+template <typename C>
+__device__ __forceinline__ void full3(const Sym5<C>& q, C m[3][3]) {
+  m[0][0] = q.xx; m[0][1] = q.xy; m[0][2] = q.xz;
+  m[1][0] = q.xy; m[1][1] = q.yy; m[1][2] = q.yz;
+  m[2][0] = q.xz; m[2][1] = q.yz; m[2][2] = -q.xx - q.yy;
+}
+
+// |b - a|^2 over all nine components of two traceless symmetric tensors
+template <typename C>
+__device__ __forceinline__ C dist2(const Sym5<C>& a, const Sym5<C>& b) {
+  const C dxx = b.xx - a.xx, dyy = b.yy - a.yy, dzz = -dxx - dyy;
+  const C dxy = b.xy - a.xy, dxz = b.xz - a.xz, dyz = b.yz - a.yz;
+  return dxx * dxx + dyy * dyy + dzz * dzz + C(2) * (dxy * dxy + dxz * dxz + dyz * dyz);
 }
 
 // A_ab eps_agd B_db for one direction g
-__device__ __forceinline__ double eps_contract(const double A[3][3], const double B[3][3], int g) {
-  double v = 0;
+template <typename C>
+__device__ __forceinline__ C eps_contract(const C A[3][3], const C B[3][3], int g) {
+  C v = C(0);
   for (int b = 0; b < 3; ++b) {
     if (g == 0) v += A[2][b] * B[1][b] - A[1][b] * B[2][b];
     else if (g == 1) v += A[0][b] * B[2][b] - A[2][b] * B[0][b];
@@ -311,104 +339,120 @@ __device__ __forceinline__ double eps_contract(const double A[3][3], const doubl
 }
 
 // energy of the bond from A (at r) to B (at r + e_g): (K/2)|B - A|^2 + K q0 (A:eps_g B - B:eps_g A)
-__device__ __forceinline__ double bond_energy(const double A[3][3], const double B[3][3], int g, double K,
-                                              double q0) {
-  double d2 = 0;
-  for (int a = 0; a < 3; ++a)
-    for (int b = 0; b < 3; ++b) d2 += (B[a][b] - A[a][b]) * (B[a][b] - A[a][b]);
-  return 0.5 * K * d2 + K * q0 * (eps_contract(A, B, g) - eps_contract(B, A, g));
+template <typename C>
+__device__ __forceinline__ C bond_energy(const Sym5<C>& a, const Sym5<C>& b, int g, C K, C q0) {
+  C A[3][3], B[3][3];
+  full3(a, A);
+  full3(b, B);
+  return C(0.5) * K * dist2(a, b) + K * q0 * (eps_contract(A, B, g) - eps_contract(B, A, g));
 }
 
 // sums per block: [F_h, mass, Px, Py, Pz, defects, nonfinite, 0]
 template <typename real>
 __global__ void __launch_bounds__(256) k_diag(DiagGeom g, const real* __restrict__ Q, const real* __restrict__ f,
                                               int with_f, double threshold, double* __restrict__ partials) {
-  double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+  using C = real;
+  // F_h, then sum(rho - 1), P: FP64; the sites, defects and non-finite sites counted
+  double aF = 0.0, aR = 0.0, aJx = 0.0, aJy = 0.0, aJz = 0.0;
+  int sites = 0, defects = 0, bad = 0;
   const real* qp = Q + 5 * g.base;
   const real* fp = f ? f + 15 * g.base : nullptr;
   const long long n = g.n;
+  const C A0 = (C)g.A0, gam = (C)g.gamma, K = (C)g.K, q0 = (C)g.q0, c_div = (C)g.c_div;
+  const C a2 = C(0.5) * A0 * (C(1) - gam / C(3)), a3 = A0 * gam, a4 = C(0.25) * A0 * gam;
+  const C kq0 = C(2) * K * q0, kq0sq = C(2) * K * q0 * q0;
+  const Sym5<C> qw = {(C)g.qw[0], (C)g.qw[1], (C)g.qw[2], (C)g.qw[3], (C)g.qw[4]};
+  const bool small = n < (1ll << 31);
   for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < n; s += (long long)gridDim.x * blockDim.x) {
-    const int x = (int)(s % g.nx);
-    const int y = (int)((s / g.nx) % g.ny);
-    const int z = (int)(s / ((long long)g.nx * g.ny));
+    int x, y, z;
+    if (small) {  // 32-bit index arithmetic
+      const int si = (int)s, row = si / g.nx;
+      x = si - row * g.nx;
+      z = row / g.ny;
+      y = row - z * g.ny;
+    } else {
+      const long long row = s / g.nx;
+      x = (int)(s - row * g.nx);
+      z = (int)(row / g.ny);
+      y = (int)(row - (long long)z * g.ny);
+    }
     const int xp = x + 1 == g.nx ? 0 : x + 1, xm = x == 0 ? g.nx - 1 : x - 1;
     const int yp = y + 1 == g.ny ? 0 : y + 1, ym = y == 0 ? g.ny - 1 : y - 1;
     const int zp = z + 1 == g.nz ? 0 : z + 1, zm = z == 0 ? g.nz - 1 : z - 1;
     auto at = [&](int xx, int yy, int zz) { return ((long long)zz * g.ny + yy) * g.nx + xx; };
-    double Qc[3][3], Qp[3][3][3], Qm[3][3][3];
-    q9(qp, n, s, Qc);
-    q9(qp, n, at(xp, y, z), Qp[0]);
-    q9(qp, n, at(x, yp, z), Qp[1]);
-    q9(qp, n, at(x, y, zp), Qp[2]);
-    q9(qp, n, at(xm, y, z), Qm[0]);
-    q9(qp, n, at(x, ym, z), Qm[1]);
-    q9(qp, n, at(x, y, zm), Qm[2]);
-    double tr2 = 0, tr3 = 0, grad2 = 0, chiral = 0;
-    bool finite = true;
-    for (int a = 0; a < 3; ++a)
-      for (int b = 0; b < 3; ++b) {
-        finite = finite && isfinite(Qc[a][b]);
-        tr2 += Qc[a][b] * Qc[a][b];
-        for (int c = 0; c < 3; ++c) tr3 += Qc[a][b] * Qc[b][c] * Qc[c][a];
-        for (int d = 0; d < 3; ++d) {
-          const double fd = Qp[d][a][b] - Qc[a][b];
-          grad2 += fd * fd;
-        }
-      }
-    // C_ab = eps_agd D0_g Q_db
-    for (int b = 0; b < 3; ++b) {
-      const double Cx = 0.5 * (Qp[1][2][b] - Qm[1][2][b]) - 0.5 * (Qp[2][1][b] - Qm[2][1][b]);
-      const double Cy = 0.5 * (Qp[2][0][b] - Qm[2][0][b]) - 0.5 * (Qp[0][2][b] - Qm[0][2][b]);
-      const double Cz = 0.5 * (Qp[0][1][b] - Qm[0][1][b]) - 0.5 * (Qp[1][0][b] - Qm[1][0][b]);
-      chiral += Qc[0][b] * Cx + Qc[1][b] * Cy + Qc[2][b] * Cz;
-    }
-    const double bulk = 0.5 * g.A0 * (1.0 - g.gamma / 3.0) * tr2 - g.A0 * g.gamma / 3.0 * tr3 +
-                        0.25 * g.A0 * g.gamma * tr2 * tr2;
+    const Sym5<C> qc = load5(qp, n, s);
+    const Sym5<C> qn[3] = {load5(qp, n, at(xp, y, z)), load5(qp, n, at(x, yp, z)), load5(qp, n, at(x, y, zp))};
+    const Sym5<C> qs[3] = {load5(qp, n, at(xm, y, z)), load5(qp, n, at(x, ym, z)), load5(qp, n, at(x, y, zm))};
+    const bool finite = isfinite(qc.xx) && isfinite(qc.xy) && isfinite(qc.xz) && isfinite(qc.yy) && isfinite(qc.yz);
+    const C qzz = -qc.xx - qc.yy;
+    const C tr2 = qc.xx * qc.xx + qc.yy * qc.yy + qzz * qzz + C(2) * (qc.xy * qc.xy + qc.xz * qc.xz + qc.yz * qc.yz);
+    // Tr Q^3 = 3 det Q for a traceless Q
+    const C det = qc.xx * (qc.yy * qzz - qc.yz * qc.yz) - qc.xy * (qc.xy * qzz - qc.yz * qc.xz) +
+                  qc.xz * (qc.xy * qc.yz - qc.yy * qc.xz);
+    const C bulk = a2 * tr2 - a3 * det + a4 * tr2 * tr2;
+    C Fs;
     if (!g.walls) {
-      acc[0] += bulk + 0.5 * g.K * grad2 + 2.0 * g.K * g.q0 * chiral + 2.0 * g.K * g.q0 * g.q0 * tr2;
+      const C grad2 = dist2(qc, qn[0]) + dist2(qc, qn[1]) + dist2(qc, qn[2]);
+      // Q_ab C_ab with C_ab = eps_agd D0_g Q_db
+      C Qc[3][3], P[3][3][3], M[3][3][3];
+      full3(qc, Qc);
+      for (int d = 0; d < 3; ++d) {
+        full3(qn[d], P[d]);
+        full3(qs[d], M[d]);
+      }
+      C chiral = C(0);
+      for (int b = 0; b < 3; ++b) {
+        const C Cx = C(0.5) * (P[1][2][b] - M[1][2][b]) - C(0.5) * (P[2][1][b] - M[2][1][b]);
+        const C Cy = C(0.5) * (P[2][0][b] - M[2][0][b]) - C(0.5) * (P[0][2][b] - M[0][2][b]);
+        const C Cz = C(0.5) * (P[0][1][b] - M[0][1][b]) - C(0.5) * (P[1][0][b] - M[1][0][b]);
+        chiral += Qc[0][b] * Cx + Qc[1][b] * Cy + Qc[2][b] * Cz;
+      }
+      Fs = bulk + C(0.5) * K * grad2 + kq0 * chiral + kq0sq * tr2;
       if (g.c_div != 0.0) {
         // div_a = sum_b D0_b Q_ab from the face neighbours
-        double d2 = 0;
+        C d2 = C(0);
         for (int a = 0; a < 3; ++a) {
-          double dv = 0;
-          for (int b = 0; b < 3; ++b) dv += 0.5 * (Qp[b][a][b] - Qm[b][a][b]);
+          C dv = C(0);
+          for (int b = 0; b < 3; ++b) dv += C(0.5) * (P[b][a][b] - M[b][a][b]);
           d2 += dv * dv;
         }
-        acc[0] -= g.c_div * d2;
+        Fs -= c_div * d2;
       }
     } else {
       // bond form: this site's three forward bonds (the z bond of the top plane
       // ends on the anchored ghost) and, on the bottom plane, the bond from the
       // ghost below; every bond touching the lattice is counted once
-      double Qw[3][3];
-      Qw[0][0] = g.qw[0]; Qw[0][1] = g.qw[1]; Qw[0][2] = g.qw[2];
-      Qw[1][0] = g.qw[1]; Qw[1][1] = g.qw[3]; Qw[1][2] = g.qw[4];
-      Qw[2][0] = g.qw[2]; Qw[2][1] = g.qw[4]; Qw[2][2] = -g.qw[0] - g.qw[3];
-      double Fb = bond_energy(Qc, Qp[0], 0, g.K, g.q0) + bond_energy(Qc, Qp[1], 1, g.K, g.q0);
-      Fb += bond_energy(Qc, z == g.nz - 1 ? Qw : Qp[2], 2, g.K, g.q0);
-      if (z == 0) Fb += bond_energy(Qw, Qc, 2, g.K, g.q0);
-      acc[0] += bulk + Fb + 2.0 * g.K * g.q0 * g.q0 * tr2;
+      C Fb = bond_energy(qc, qn[0], 0, K, q0) + bond_energy(qc, qn[1], 1, K, q0);
+      Fb += bond_energy(qc, z == g.nz - 1 ? qw : qn[2], 2, K, q0);
+      if (z == 0) Fb += bond_energy(qw, qc, 2, K, q0);
+      Fs = bulk + Fb + kq0sq * tr2;
     }
-    acc[5] += finite && lambda_max(Qc) < threshold ? 1.0 : 0.0;
+    aF += (double)Fs;
+    defects += finite && top_eigenvalue_below(qc, threshold) ? 1 : 0;
+    ++sites;
+    bool ffin = true;
     if (with_f) {
-      double r = 1.0, jx = 0, jy = 0, jz = 0;  // deviation storage: rho = 1 + sum df_i
+      // deviation storage: rho = 1 + sum df_i; the per-site sums of the small
+      // deviations in the state's precision, the sum over sites in FP64
+      C r = C(0), jx = C(0), jy = C(0), jz = C(0);
 #pragma unroll
       for (int i = 0; i < NV; ++i) {
-        const double fi = fp[i * n + s];
-        finite = finite && isfinite(fi);
+        const C fi = fp[i * n + s];
+        ffin = ffin && isfinite(fi);
         r += fi;
-        jx += ex(i) * fi;
-        jy += ey(i) * fi;
-        jz += ez(i) * fi;
+        if (ex(i) > 0) jx += fi; else if (ex(i) < 0) jx -= fi;
+        if (ey(i) > 0) jy += fi; else if (ey(i) < 0) jy -= fi;
+        if (ez(i) > 0) jz += fi; else if (ez(i) < 0) jz -= fi;
       }
-      acc[1] += r;
-      acc[2] += jx;
-      acc[3] += jy;
-      acc[4] += jz;
+      aR += (double)r;
+      aJx += (double)jx;
+      aJy += (double)jy;
+      aJz += (double)jz;
     }
-    acc[6] += finite ? 0.0 : 1.0;
+    bad += finite && ffin ? 0 : 1;
   }
-  // block reduction in a fixed order
+  // mass = sites + sum(rho - 1); block reduction in a fixed order
+  const double acc[7] = {aF, with_f ? aR + (double)sites : 0.0, aJx, aJy, aJz, (double)defects, (double)bad};
   __shared__ double red[8][256];
   for (int k = 0; k < 7; ++k) red[k][threadIdx.x] = acc[k];
   __syncthreads();
@@ -423,12 +467,14 @@ __global__ void __launch_bounds__(256) k_diag(DiagGeom g, const real* __restrict
   }
 }
 
+// the block partials summed per quantity: warp k sums quantity k, lanes
+// striding over the blocks, then a shuffle tree (a fixed order)
 __global__ void k_diag_final(const double* __restrict__ partials, int nblocks, double* __restrict__ out) {
-  if (threadIdx.x < 8) {
-    double s = 0.0;
-    for (int b = 0; b < nblocks; ++b) s += partials[b * 8 + threadIdx.x];
-    out[threadIdx.x] = s;
-  }
+  const int k = threadIdx.x / 32, lane = threadIdx.x % 32;
+  double s = 0.0;
+  for (int b = lane; b < nblocks; b += 32) s += partials[b * 8 + k];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if (lane == 0) out[k] = s;
 }
 
 constexpr int kDiagBlocks = 512;
@@ -438,7 +484,7 @@ cudaError_t launch_diag_one(const DiagGeom& g, const void* q, const void* f, int
                             double* partials, double* out, cudaStream_t s) {
   k_diag<real><<<kDiagBlocks, 256, 0, s>>>(g, static_cast<const real*>(q), static_cast<const real*>(f), with_f,
                                            threshold, partials);
-  k_diag_final<<<1, 32, 0, s>>>(partials, kDiagBlocks, out);
+  k_diag_final<<<1, 256, 0, s>>>(partials, kDiagBlocks, out);
   return cudaGetLastError();
 }
 template cudaError_t launch_diag_one<float>(const DiagGeom&, const void*, const void*, int, double, double*, double*,

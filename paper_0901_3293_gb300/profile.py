@@ -4,6 +4,7 @@
     python -m paper_0901_3293_gb300.profile --conv --dims 64 64 256 --steps 3
     python -m paper_0901_3293_gb300.profile --texture --dims 256 256 256 --steps 3
     python -m paper_0901_3293_gb300.profile --batch --steps 4
+    python -m paper_0901_3293_gb300.profile --diag --size 160 --steps 3
 
 Each step launches the step kernels once (no CUDA graph), so a profiler can
 select them by name and launch index.  --conv instead runs surrogate calls
@@ -14,6 +15,8 @@ renders the polarised-light texture of a BPII lattice of the given dims
 sweep (24 x 32^3 + 24 x 48^3) in one batch: ten steps (kernel selection and
 tuning), then `steps` single steps inside the NVTX range "timed", so that a
 profiler can take exactly those launches (--nvtx --nvtx-include "timed/").
+--diag runs the FP64 diagnostics (free energy, mass and momentum, defect
+fraction: one pass) `steps` times on the L^3 lattice after one step.
 """
 
 from __future__ import annotations
@@ -36,6 +39,7 @@ def main():
     ap.add_argument("--walls", action="store_true")
     ap.add_argument("--texture", action="store_true")
     ap.add_argument("--batch", action="store_true")
+    ap.add_argument("--diag", action="store_true")
     args = ap.parse_args()
     build.build()
     torch.cuda.set_device(0)
@@ -88,6 +92,17 @@ def main():
     lat.init_q(lcbp.BPII, 0.3, noise=1e-4, seed=20090119).init_f_equilibrium(1.0)
     if args.walls:
         lat.set_walls(True, (0.2, 0.0, 0.0, -0.1, 0.0))
+    if args.diag:
+        import time
+        lat.step(1)
+        lat.free_energy()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            F = lat.free_energy()
+        dt = time.perf_counter() - t0
+        print({"size": n, "calls": args.steps, "ms_per_call": 1e3 * dt / args.steps, "F": F,
+               "defects": lat.defect_fraction(0.19)})
+        return
     ms = lat.profile_steps(args.steps)
     print({"size": n, "steps": args.steps, "walls": args.walls, "kernel_ms": ms, "F": lat.free_energy()})
 
