@@ -296,6 +296,18 @@ LCBP_API int lcbp_reequilibrate_f(lcbp_lattice *h);
  * bounded device-side wait of the fast path gave up (results invalid). */
 LCBP_API int lcbp_synchronize(lcbp_lattice *h);
 
+/*
+ * Self-test of the bounded device-side wait that every barrier wait of the
+ * fast kernels uses.  One CTA on the current device waits, for at most
+ * limit_ms milliseconds (0 < limit_ms <= 1000), on a shared-memory barrier
+ * that nothing arrives on.  *timed_out is set to 1 when the wait gave up
+ * and reported it to the host, as the fast kernels' waits do before the
+ * stepping calls return LCBP_ETIMEOUT; the CUDA context stays usable.
+ * Not part of the method; no lattice is needed.  Errors: LCBP_EINVAL (bad
+ * limit or NULL), LCBP_ECUDA.
+ */
+LCBP_API int lcbp_check_wait_timeout(double limit_ms, int *timed_out);
+
 /* Copy out Q (5 * N), u (3 * N), rho (N) or f (15 * N) values.  Errors: LCBP_EINVAL. */
 LCBP_API int lcbp_read_q(lcbp_lattice *h, void *dst, int dtype);
 LCBP_API int lcbp_read_u(lcbp_lattice *h, void *dst, int dtype);

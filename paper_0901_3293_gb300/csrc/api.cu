@@ -1024,6 +1024,23 @@ int lcbp_synchronize(lcbp_lattice* h) {
   return check_device_error(h);
 }
 
+int lcbp_check_wait_timeout(double limit_ms, int* timed_out) {
+  if (!timed_out || !(limit_ms > 0.0 && limit_ms <= 1000.0))
+    return fail(LCBP_EINVAL, "need 0 < limit_ms <= 1000 and an output");
+  int* d_flag = nullptr;
+  cudaError_t e = cudaMalloc(&d_flag, sizeof(int));
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+  e = cudaMemset(d_flag, 0xff, sizeof(int));
+  if (e == cudaSuccess) e = launch_wait_probe((uint64_t)(limit_ms * 1e6), d_flag, nullptr);
+  int flag = -1;
+  if (e == cudaSuccess) e = cudaMemcpy(&flag, d_flag, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaFree(d_flag);
+  if (e != cudaSuccess) return cuda_fail(e, "wait self-test");
+  if (flag != 0 && flag != 1) return fail(LCBP_ECUDA, "wait self-test: the probe did not report");
+  *timed_out = flag;
+  return LCBP_OK;
+}
+
 int lcbp_read_q(lcbp_lattice* h, void* dst, int dtype) {
   CHECK_H(h);
   if (!dst || !valid_dtype(dtype)) return fail(LCBP_EINVAL, "bad buffer or dtype");

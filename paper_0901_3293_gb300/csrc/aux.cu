@@ -3,6 +3,7 @@
 
 #include "common.cuh"
 #include "kernels.h"
+#include "tma.cuh"
 
 namespace lcbp {
 
@@ -475,6 +476,27 @@ __global__ void k_diag_final(const double* __restrict__ partials, int nblocks, d
   for (int b = lane; b < nblocks; b += 32) s += partials[b * 8 + k];
   for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
   if (lane == 0) out[k] = s;
+}
+
+// ---------------------------------------------------------------------------
+// Self-test of the bounded barrier wait: a barrier that expects one arrival
+// which never comes, so the wait runs into its limit and reports it.
+// ---------------------------------------------------------------------------
+__global__ void k_wait_probe(uint64_t limit_ns, int* flag) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    mbar_init_fence();
+  }
+  __syncthreads();
+  const bool ok = mbar_wait_bounded(&bar, 0, limit_ns);
+  __syncthreads();
+  if (threadIdx.x == 0) *flag = ok ? 0 : 1;
+}
+
+cudaError_t launch_wait_probe(uint64_t limit_ns, int* flag, cudaStream_t s) {
+  k_wait_probe<<<1, 32, 0, s>>>(limit_ns, flag);
+  return cudaGetLastError();
 }
 
 constexpr int kDiagBlocks = 512;

@@ -92,6 +92,8 @@ struct DiagGeom {
   double qw[5];    // anchored Q (q5 order)
   double c_div;    // (K - L2) / 2: F_h gains -c_div |div Q|^2 per site
 };
+// one CTA waits on a barrier nothing arrives on, for at most limit_ns; *flag = 1 if it gave up
+cudaError_t launch_wait_probe(uint64_t limit_ns, int* flag, cudaStream_t s);
 template <typename real>
 cudaError_t launch_diag_one(const DiagGeom& g, const void* q, const void* f, int with_f, double threshold,
                             double* partials, double* out, cudaStream_t s);

@@ -54,6 +54,7 @@ _SIGNATURES = {
     "lcbp_set_body_force": (_c_int, [_P, _c_void_p, _c_int]),
     "lcbp_step": (_c_int, [_P, _c_int]),
     "lcbp_synchronize": (_c_int, [_P]),
+    "lcbp_check_wait_timeout": (_c_int, [_c_double, ctypes.POINTER(_c_int)]),
     "lcbp_set_path": (_c_int, [_P, _c_int]),
     "lcbp_get_path": (_c_int, [_P, ctypes.POINTER(_c_int), ctypes.POINTER(_c_int), ctypes.POINTER(_c_int)]),
     "lcbp_profile_steps": (_c_int, [_P, _c_int, ctypes.POINTER(_c_double), _c_int, ctypes.POINTER(_c_int)]),
@@ -515,6 +516,14 @@ class Batch:
                                         ctypes.byref(st)))
         return {"R": R.value, "sites": tot.value, "tile": tuple(tile), "persistent_ctas": ctas.value,
                 "step": st.value}
+
+
+def check_wait_timeout(limit_ms: float) -> bool:
+    """Self-test of the bounded device-side wait: True if a wait on a barrier
+    that nothing arrives on gave up after limit_ms and reported it."""
+    out = _c_int()
+    check(lib().lcbp_check_wait_timeout(limit_ms, ctypes.byref(out)))
+    return bool(out.value)
 
 
 def free_energy_noalloc(q5_device, nx: int, ny: int, nz: int, A0: float, gamma: float, K: float, q0: float,

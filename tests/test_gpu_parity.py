@@ -338,6 +338,24 @@ def test_errors_are_status_codes(lcbp):
     assert lat.free_energy() == 0.0
 
 
+def test_bounded_wait_gives_up_and_reports(lcbp):
+    """Failure detection without a fault: the bounded barrier wait of the
+    fast kernels, on a barrier that nothing arrives on, gives up after its
+    limit, reports it to the host, and leaves the context usable."""
+    import time
+    L = lcbp
+    with pytest.raises(L.LcbpError) as e:
+        L.check_wait_timeout(0.0)
+    assert e.value.code == L.EINVAL
+    t0 = time.perf_counter()
+    assert L.check_wait_timeout(50.0)
+    dt = time.perf_counter() - t0
+    assert 0.05 <= dt < 2.0, dt
+    lat = make(L, (8, 8, 8), "f32", lbq.Params())
+    lat.init_q(L.BPII, 0.3, noise=1e-4, seed=1).init_f_equilibrium(1.0).step(4)
+    assert lat.path()[0] and np.isfinite(lat.free_energy())
+
+
 def test_torch_device_buffers(lcbp):
     import torch
     p = lbq.Params()
