@@ -942,16 +942,17 @@ __device__ __forceinline__ void lbq_body(const CUtensorMap* tmU, const CUtensorM
       }
       Sym5<V> sig_y;
       V b_y[3], drho_y, u_y[3];
+      // the part of each collision term that does not involve the pulled
+      // population, f^eq / tau_f + p_i, first: the pulls land meanwhile
+      V pre[NV];
 #pragma unroll
       for (int i = 0; i < NV; ++i) {
         if ((ez(i) > 0 && wl) || (ez(i) < 0 && wh)) {
           // half-way bounce-back: [f + C]_opp(i) of this site (i = 0 came first)
           const int o = opp(i);
           const V usq = u_y[0] * u_y[0] + u_y[1] * u_y[1] + u_y[2] * u_y[2];
-          V C = (feq_delta(o, drho_y, V(1) + drho_y, u_y[0], u_y[1], u_y[2], usq, sig_y) - fin[i]) * inv_tau;
-          C += force_dir(o, b_y[0], b_y[1], b_y[2]);
-          ds[i] = fin[i] + C;
-          dh[i] = fin[i] + V(0.5) * C;
+          pre[i] = feq_delta(o, drho_y, V(1) + drho_y, u_y[0], u_y[1], u_y[2], usq, sig_y) * inv_tau +
+                   force_dir(o, b_y[0], b_y[1], b_y[2]);
           continue;
         }
         const real* sl = ez(i) > 0 ? nm : ez(i) < 0 ? np : nc;
@@ -971,8 +972,13 @@ __device__ __forceinline__ void lbq_body(const CUtensorMap* tmU, const CUtensorM
           u_y[2] = uz;
         }
         const V usq = ux * ux + uy * uy + uz * uz;
-        V C = (feq_delta(i, drho, V(1) + drho, ux, uy, uz, usq, sv) - fin[i]) * inv_tau;
-        if (i != 0) C += force_dir(i, bx, by, bz);
+        pre[i] = feq_delta(i, drho, V(1) + drho, ux, uy, uz, usq, sv) * inv_tau;
+        if (i != 0) pre[i] += force_dir(i, bx, by, bz);
+      }
+      // C_i = (f^eq - f_i) / tau_f + p_i; predictor f* = f + C, and f + C / 2
+#pragma unroll
+      for (int i = 0; i < NV; ++i) {
+        const V C = pre[i] - fin[i] * inv_tau;
         ds[i] = fin[i] + C;
         dh[i] = fin[i] + V(0.5) * C;
       }
