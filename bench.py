@@ -45,6 +45,7 @@ KERNEL_BYTES = {
 KERNELS_FAST = ["qside", "lbq"]
 KERNELS_GENERIC = ["field", "force_predict", "lb_correct"]
 STATE_BYTES = (15 + 5) * 2 * 4  # read + write of f and Q once per site-step (FP32)
+HBM_NOMINAL_GBS = 7900.0  # GB300 HBM3e data-sheet bandwidth (the measured copy peak is the roofline)
 # DRAM bytes per site of one launch of each fast kernel (dram__bytes_read.sum +
 # dram__bytes_write.sum), from an ncu capture of 160^3 FP32 near the 256^3
 # tuning (20 planes per CTA, one site per thread); summary and command in
@@ -364,7 +365,9 @@ def run_ours(args):
             "no capture for these kernel sources", "kernel": dom,
             "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs, burst copy)",
             "step_algorithmic_frac": STATE_BYTES * sites * args.steps / (ms * 1e-3) / 1e9 / peak,
-            "note": "step_algorithmic_frac counts only the 160 B/site of reading and writing f and Q once"}
+            "frac_of_nominal": per_kernel[dom]["GBps"] / HBM_NOMINAL_GBS, "nominal_peak": HBM_NOMINAL_GBS,
+            "note": "step_algorithmic_frac counts only the 160 B/site of reading and writing f and Q once; "
+                    "frac_of_nominal is against the 7.9 TB/s HBM3e data-sheet figure"}
 
     # ---- end to end through the C ABI with pinned host buffers: upload f and Q,
     # one step, read back Q and u, every step
@@ -475,7 +478,6 @@ def run_ours(args):
     batch.step(max(4, args.warmup))
     batch.synchronize()
     bsites = batch.info()["sites"]
-    bs = torch.cuda.Stream()
     t0 = time.perf_counter()
     batch.step(args.steps)
     batch.synchronize()
