@@ -315,20 +315,22 @@ LCBP_API int lcbp_read_rho(lcbp_lattice *h, void *dst, int dtype);
 LCBP_API int lcbp_read_f(lcbp_lattice *h, void *dst, int dtype);
 
 /*
- * Total lattice free energy F_h = sum_x f_h(x), accumulated in FP64 on the
- * device, with the lattice density
+ * Total lattice free energy F_h = sum_x f_h(x), the per-site density in the
+ * state's precision and the sum over sites in FP64 on the device, with the
+ * lattice density
  *   f_h = bulk(Q) + (K/2) sum_g |D+_g Q|^2 + 2 K q0 Q:(eps D0 Q) + 2 K q0^2 |Q|^2
  * whose exact gradient is -H (Sec. 2.1 Eq. free_energy).
  * Errors: LCBP_ENONFINITE if Q holds NaN/Inf.
  */
 LCBP_API int lcbp_free_energy(lcbp_lattice *h, double *F);
 
-/* Sum of rho and of rho u over the lattice (FP64 on the device).  LCBP_ENONFINITE on NaN/Inf. */
+/* Sum of rho and of rho u over the lattice (sums over sites in FP64 on the device).  LCBP_ENONFINITE on NaN/Inf. */
 LCBP_API int lcbp_totals(lcbp_lattice *h, double *mass, double momentum[3]);
 
 /*
  * Fraction of sites whose scalar order q (largest eigenvalue of Q, Sec. 2.1)
- * is below `threshold` (the paper uses 0.19 to mark disclinations).
+ * is below `threshold` (the paper uses 0.19 to mark disclinations).  Each
+ * site is decided as in FP64 (Sylvester's criterion on threshold I - Q).
  */
 LCBP_API int lcbp_defect_fraction(lcbp_lattice *h, double threshold, double *fraction);
 
