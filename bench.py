@@ -420,6 +420,21 @@ def run_ours(args):
                                         "frac_of_" + peak_kind: KERNEL_BYTES[name] * sites / (t * 1e-3) / 1e9 / peak}
                                  for name, t in zip(KERNELS_FAST if wfast else KERNELS_GENERIC, wkms)},
                   "q_wall": list(WALL_Q)}
+
+    # ---- the same periodic lattice on the generic kernels (one thread per
+    # site, neighbours through L1/L2), which serve the modes the fast path
+    # does not (Gauss-Seidel coupling, flow off, L2 != K, nx % 4 != 0)
+    lat.set_walls(False)
+    lat.set_path(lcbp.PATH_GENERIC)
+    lat.step(3)
+    lat.synchronize()
+    gkms = lat.profile_steps(max(3, min(args.steps, 10)))
+    generic_line = {"ms_per_step": sum(gkms), "MLUPS": sites / (sum(gkms) * 1e-3) / 1e6,
+                    "per_kernel": {name: {"ms": t, "algorithmic_bytes_per_site": KERNEL_BYTES[name],
+                                          "GBps": KERNEL_BYTES[name] * sites / (t * 1e-3) / 1e9,
+                                          "frac_of_" + peak_kind: KERNEL_BYTES[name] * sites / (t * 1e-3) / 1e9 / peak}
+                                   for name, t in zip(KERNELS_GENERIC, gkms)},
+                    "note": "per-kernel event times of lcbp_profile_steps; eager launches"}
     lat.close()
 
     # ---- the 64x64x256 thin slab (BPII seed for z < 32 inside an x-helix)
@@ -512,7 +527,7 @@ def run_ours(args):
                    "planes_per_cta": zc, "sites_per_thread": spt},
         "roofline": roof, "per_kernel": per_kernel, "cpu_baseline": cpu, "e2e": e2e,
         "gpu_launches": launches, "clocks": clk, "free_energy_after": F,
-        "diagnostics_256cube": diag_line, "walls_256cube": walls_line, "slab_64x64x256": slab_line, "surrogate_slab_64x64x256": sur_line, "texture_slab_64x64x256": tex_line,
+        "diagnostics_256cube": diag_line, "walls_256cube": walls_line, "generic_kernels_256cube": generic_line, "slab_64x64x256": slab_line, "surrogate_slab_64x64x256": sur_line, "texture_slab_64x64x256": tex_line,
         "batched_48_replicas": batch_line,
     }
     print(json.dumps(line), flush=True)
