@@ -347,6 +347,7 @@ def test_bounded_wait_gives_up_and_reports(lcbp):
     with pytest.raises(L.LcbpError) as e:
         L.check_wait_timeout(0.0)
     assert e.value.code == L.EINVAL
+    assert L.check_wait_timeout(1.0)  # also brings up the context, untimed
     t0 = time.perf_counter()
     assert L.check_wait_timeout(50.0)
     dt = time.perf_counter() - t0
