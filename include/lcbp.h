@@ -273,9 +273,19 @@ LCBP_API int lcbp_set_path(lcbp_lattice *h, int path);
  * shape and dtype, writing scratch buffers only; AUTO results persist in the
  * file named by the environment variable LCBP_AUTOTUNE_CACHE, if set
  * (lines "nx ny nz dtype planes sites", dtype + 100 for a lattice with
- * walls).  Any pointer may be NULL.
+ * walls; see lcbp_get_tuning for the sites field).  Any pointer may be NULL.
  */
 LCBP_API int lcbp_get_path(lcbp_lattice *h, int *fast, int *planes_per_cta, int *sites_per_thread);
+
+/*
+ * The fast path's tuning in full: the two kernels share the planes per CTA
+ * but take their sites per thread separately.  *spt_lb = that of the LB /
+ * Heun-corrector kernel (what lcbp_get_path reports), *spt_q = that of the
+ * molecular-field / stress / predictor kernel; all 0 before the first step or
+ * on the generic path.  The autotune cache line holds spt_lb + 10 * spt_q in
+ * its last field.  Any pointer may be NULL.
+ */
+LCBP_API int lcbp_get_tuning(lcbp_lattice *h, int *planes_per_cta, int *spt_lb, int *spt_q);
 
 /*
  * Copy out the Beris-Edwards rate dQ/dt = R(Q, u) = Gamma H + S(W, Q) - u.grad Q
@@ -441,22 +451,24 @@ LCBP_API int lcbp_batch_get_info(lcbp_batch *b, int *R, long long *total_sites, 
 
 /* ------------------------------------------------------------------------
  * Allocation-free free energy.  For callers that cannot allocate device
- * memory when they need the free energy -- code running while its stream is
- * being captured into a CUDA graph, code whose framework allocator owns the
- * device heap, real-time loops that must not touch an allocator -- this
- * computes F_h (as lcbp_free_energy) of a caller-owned device Q field without
- * any cudaMalloc, cudaFree or other allocating call.  Its scratch, the
+ * memory when they need the free energy -- code whose framework allocator
+ * owns the device heap, real-time loops that must not touch an allocator --
+ * this computes F_h of a caller-owned device Q field without any cudaMalloc,
+ * cudaFree or other allocating call.  It covers a periodic lattice with the
+ * one-constant energy: it equals lcbp_free_energy of a lattice without walls
+ * and with L2 = K (no lcbp_set_walls, no lcbp_set_l2).  Its scratch, the
  * per-block partial sums of the FP64 reduction (32.8 KB), is a fixed device
  * array that every GPU loading the library holds until exit.
  *   q5: device pointer, 5 * N values in the layout above (dtype LCBP_F32 or
  *       LCBP_F64); A0, gamma, K, q0: as lcbp_set_ldg; stream: a cudaStream_t
- *       (NULL = legacy default stream); *F receives the result (the call
- *       synchronises the stream).
- * The first call on a device looks up the array's device address on that
- * device; make that first call before any stream capture begins.  All calls
- * share the one array (its contents are those of the last call; every slot
- * is rewritten by each call, so nothing needs clearing), hence calls that
- * overlap on the GPU -- from several threads or streams at once -- race.
+ *       (NULL = legacy default stream).  *F receives the result: the call
+ *       copies it to host memory and synchronises the stream.
+ * The first call in each CUDA context of a device looks up the array's device
+ * address there (again after cudaDeviceReset); make that first call before
+ * any stream capture begins.  All calls share the one array (its contents are
+ * those of the last call; every slot is rewritten by each call, so nothing
+ * needs clearing), hence calls that overlap on the GPU -- from several
+ * threads or streams at once -- race.
  * Errors: LCBP_EINVAL (NULL pointers, bad dtype, sizes < 1, more than
  * LCBP_NOALLOC_MAX_SITES sites), LCBP_ENONFINITE, LCBP_ECUDA.
  * There is no counterpart of this call in the paper.

@@ -184,6 +184,7 @@ struct lcbp_lattice {
   bool own_ws;
   // state and scratch (device)
   void *f[2], *rhou[2], *q, *qs, *h, *sig, *tau, *b, *bext, *staging;
+  void* pq;  // the fast kernels' padded scratch (overlays h, sig, tau, b)
   long long staging_elems;
   void* d_rep;
   Tile* d_tiles;
@@ -202,8 +203,10 @@ struct lcbp_lattice {
   int path_req;   // LCBP_PATH_*
   bool tmaps_ok;  // tensor maps built
   int zc;         // planes per CTA, 0 until tuned
-  int spt;        // sites per thread of the fast kernels, set by the tuner
-  CUtensorMap tm[6];  // Q, rho u [0], rho u [1], sigma, b, Q*
+  int spt;        // sites per thread of k_lbq, set by the tuner
+  int spt_q;      // sites per thread of k_qside, set by the tuner
+  // Q, rho u [0], rho u [1], padded scratch, u [0], u [1] (rho u components 1..3), f [0], f [1]
+  CUtensorMap tm[8];
   int* d_err;
 };
 
@@ -218,19 +221,31 @@ constexpr long long kStagingMax = 1ll << 22;  // elements of the conversion buff
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
-// offsets of: f0 f1 rhou0 rhou1 q qs h sig tau b bext staging rep tiles q0/shelix/seed partials
+// offsets of: f0 f1 rhou0 rhou1 q qs h sig tau b bext staging rep tiles q0/shelix/seed partials.
+// h, sig, tau and b (the generic kernels' scratch) lie back to back in one
+// block, and the fast kernels' padded scratch overlays that block from its
+// start: the two kernel sets never run within one step, and no scratch
+// outlives a step.
 Layout layout(int nx, int ny, int nz, int dtype) {
   const long long n = (long long)nx * ny * nz;
   const size_t es = dtype_size(dtype);
   const TileShape ts = default_tile(nx, ny, nz);
   const long long nt = tile_count(nx, ny, nz, ts);
-  const long long comps[11] = {15, 15, 4, 4, 5, 5, 5, 5, 3, 3, 3};
+  const long long comps[6] = {15, 15, 4, 4, 5, 5};
   Layout L{};
   size_t o = 0;
-  for (int i = 0; i < 11; ++i) {
+  for (int i = 0; i < 6; ++i) {
     L.off[i] = o;
     o = align256(o + (size_t)(comps[i] * n) * es);
   }
+  const long long scr = std::max(16 * n, zm_pq_elems(nx, ny, nz));
+  L.off[6] = o;
+  L.off[7] = o + (size_t)(5 * n) * es;
+  L.off[8] = o + (size_t)(10 * n) * es;
+  L.off[9] = o + (size_t)(13 * n) * es;
+  o = align256(o + (size_t)scr * es);
+  L.off[10] = o;  // external body force
+  o = align256(o + (size_t)(3 * n) * es);
   L.off[11] = o;  // staging (doubles)
   o = align256(o + (size_t)std::min(kStagingMax, 15 * n) * 8);
   L.off[12] = o;  // replica table
@@ -279,6 +294,7 @@ int finish_create(lcbp_lattice* h) {
   h->tau = w + L.off[8];
   h->b = w + L.off[9];
   h->bext = w + L.off[10];
+  h->pq = h->h;
   h->staging = w + L.off[11];
   h->staging_elems = std::min(kStagingMax, 15 * h->n);
   h->d_rep = w + L.off[12];
@@ -339,6 +355,16 @@ bool make_field_tmap(CUtensorMap* tm, void* base, int comps, int nx, int ny, int
   return encode_tiled(tm, base, 4, dims, strides, box, dtype);
 }
 
+// the padded scratch [15][nz][ny + 2][nx + 4] as a 4-D tensor, box = 36 x rows x 1 x 15
+bool make_pq_tmap(CUtensorMap* tm, void* base, int nx, int ny, int nz, int rows, int dtype) {
+  const cuuint64_t es = dtype_size(dtype);
+  const cuuint64_t nxp = nx + kZmPadX, nyp = ny + 2;
+  const cuuint64_t dims[4] = {nxp, nyp, (cuuint64_t)nz, (cuuint64_t)kZmPQ};
+  const cuuint64_t strides[3] = {nxp * es, nxp * nyp * es, nxp * nyp * nz * es};
+  const cuuint32_t box[4] = {(cuuint32_t)kZmBoxXP, (cuuint32_t)rows, 1, (cuuint32_t)kZmPQ};
+  return encode_tiled(tm, base, 4, dims, strides, box, dtype);
+}
+
 bool fast_shape_ok(const lcbp_lattice* h) { return h->nx % 4 == 0; }
 
 bool use_fast(lcbp_lattice* h) {
@@ -353,9 +379,12 @@ bool use_fast(lcbp_lattice* h) {
     bool ok = make_field_tmap(&h->tm[0], h->q, 5, h->nx, h->ny, h->nz, ty + 4, h->dtype);
     ok = ok && make_field_tmap(&h->tm[1], h->rhou[0], 4, h->nx, h->ny, h->nz, ty + 2, h->dtype);
     ok = ok && make_field_tmap(&h->tm[2], h->rhou[1], 4, h->nx, h->ny, h->nz, ty + 2, h->dtype);
-    ok = ok && make_field_tmap(&h->tm[3], h->sig, 5, h->nx, h->ny, h->nz, ty + 2, h->dtype);
-    ok = ok && make_field_tmap(&h->tm[4], h->b, 3, h->nx, h->ny, h->nz, ty + 2, h->dtype);
-    ok = ok && make_field_tmap(&h->tm[5], h->qs, 5, h->nx, h->ny, h->nz, ty + 2, h->dtype);
+    ok = ok && make_pq_tmap(&h->tm[3], h->pq, h->nx, h->ny, h->nz, ty + 2, h->dtype);
+    for (int k = 0; k < 2; ++k)  // the velocity components of rho u
+      ok = ok && make_field_tmap(&h->tm[4 + k], static_cast<char*>(h->rhou[k]) + h->n * h->es, 3, h->nx, h->ny,
+                                 h->nz, ty + 2, h->dtype);
+    for (int k = 0; k < 2; ++k)  // the populations (L2 prefetches only)
+      ok = ok && make_field_tmap(&h->tm[6 + k], h->f[k], NV, h->nx, h->ny, h->nz, ty + 2, h->dtype);
     if (!ok) {
       h->path_req = LCBP_PATH_GENERIC;  // tensor maps unavailable: stay on the generic kernels
       return false;
@@ -372,17 +401,16 @@ ZmArgs zm_args(lcbp_lattice* h, const void* model) {
   a.nz = h->nz;
   a.zc = h->zc > 0 ? h->zc : std::min(h->nz, 32);
   a.spt = h->spt > 0 ? h->spt : 1;
+  a.spt_q = h->spt_q > 0 ? h->spt_q : a.spt;
   a.model = model;
   a.tm_q = &h->tm[0];
   a.tm_u = &h->tm[1 + h->cur];
-  a.tm_sigma = &h->tm[3];
-  a.tm_b = &h->tm[4];
-  a.tm_qs = &h->tm[5];
+  a.tm_pq = &h->tm[3];
+  a.tm_u3 = &h->tm[4 + h->cur];
+  a.tm_f = &h->tm[6 + h->cur];
   a.q = h->q;
   a.qout = nullptr;
-  a.qs = h->qs;
-  a.sigma = h->sig;
-  a.b = h->b;
+  a.pq = h->pq;
   a.bext = h->has_bext ? h->bext : nullptr;
   a.f = h->f[h->cur];
   a.fnew = h->f[h->cur ^ 1];
@@ -415,10 +443,11 @@ cudaError_t launch_zm(lcbp_lattice* h, const ZmArgs& a) {
 }
 
 // planes per CTA and sites per thread, chosen by timing each candidate once per
-// lattice shape and dtype; the runs write only scratch buffers (Q* to the H
-// scratch), so the state is untouched.  Results are kept per process and, if
+// lattice shape and dtype; the runs write only scratch buffers (Q^{n+1} to the
+// generic kernels' Q* scratch), so the state is untouched.  Results are kept per process and, if
 // the environment variable LCBP_AUTOTUNE_CACHE names a file, in that file
-// ("nx ny nz dtype zc spt" per line, dtype + 100 with walls).
+// ("nx ny nz dtype zc spt" per line, dtype + 100 with walls, spt = sites per
+// thread of k_lbq + 10 x those of k_qside).
 std::mutex g_tune_mu;
 std::map<std::string, std::pair<int, int>> g_tune;
 bool g_tune_loaded = false;
@@ -473,16 +502,17 @@ int tune_zc(lcbp_lattice* h) {
       while (std::fscanf(fp, "%d %d %d %d %d %d", &a, &b, &c, &d, &z, &sp) == 6) {
         char k[64];
         snprintf(k, sizeof(k), "%d %d %d %d", a, b, c, d);
-        if (z >= 1 && sp >= 1 && sp <= 2) g_tune[k] = {z, sp};
+        if (z >= 1 && sp % 10 >= 1 && sp % 10 <= 2 && sp / 10 >= 1 && sp / 10 <= 2) g_tune[k] = {z, sp};
       }
       std::fclose(fp);
     }
   }
   const std::string key = tune_key(h);
   auto it = g_tune.find(key);
-  if (!pinned && it != g_tune.end() && it->second.second <= spt_max) {
+  if (!pinned && it != g_tune.end() && it->second.second % 10 <= spt_max && it->second.second / 10 <= spt_max) {
     h->zc = it->second.first;
-    h->spt = it->second.second;
+    h->spt = it->second.second % 10;
+    h->spt_q = it->second.second / 10;
     return LCBP_OK;
   }
   const ModelBuf mb = host_model(h);
@@ -490,32 +520,37 @@ int tune_zc(lcbp_lattice* h) {
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
     return fail(LCBP_ECUDA, "event create");
   float best = 1e30f;
-  int best_zc = std::min(h->nz, 32), best_spt = spt_lo;
+  int best_zc = std::min(h->nz, 32), best_spt = spt_lo, best_sq = spt_lo;
+  // every pair of sites per thread (k_lbq, k_qside), each with its planes-per-CTA candidates
   for (int spt = spt_lo; spt <= spt_hi; ++spt) {
-    for (int zc : zc_candidates(h, spt)) {
-      ZmArgs a = zm_args(h, mb.bytes);
-      a.zc = zc;
-      a.spt = spt;
-      a.qout = h->h;  // scratch
-      float t = 1e30f;
-      for (int rep = 0; rep < 3; ++rep) {
-        cudaEventRecord(e0, h->stream);
-        cudaError_t e = launch_zm(h, a);
-        cudaEventRecord(e1, h->stream);
-        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-        if (e != cudaSuccess) {
-          cudaEventDestroy(e0);
-          cudaEventDestroy(e1);
-          return cuda_fail(e, "autotune");
+    for (int sq = spt_lo; sq <= spt_hi; ++sq) {
+      for (int zc : zc_candidates(h, spt)) {
+        ZmArgs a = zm_args(h, mb.bytes);
+        a.zc = zc;
+        a.spt = spt;
+        a.spt_q = sq;
+        a.qout = h->qs;  // scratch the fast kernels do not use
+        float t = 1e30f;
+        for (int rep = 0; rep < 3; ++rep) {
+          cudaEventRecord(e0, h->stream);
+          cudaError_t e = launch_zm(h, a);
+          cudaEventRecord(e1, h->stream);
+          if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+          if (e != cudaSuccess) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return cuda_fail(e, "autotune");
+          }
+          float ms = 0.f;
+          cudaEventElapsedTime(&ms, e0, e1);
+          t = std::min(t, ms);
         }
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        t = std::min(t, ms);
-      }
-      if (t < best) {
-        best = t;
-        best_zc = a.zc;
-        best_spt = spt;
+        if (t < best) {
+          best = t;
+          best_zc = a.zc;
+          best_spt = spt;
+          best_sq = sq;
+        }
       }
     }
   }
@@ -523,11 +558,12 @@ int tune_zc(lcbp_lattice* h) {
   cudaEventDestroy(e1);
   h->zc = best_zc;
   h->spt = best_spt;
+  h->spt_q = best_sq;
   if (pinned) return LCBP_OK;
-  g_tune[key] = {best_zc, best_spt};
+  g_tune[key] = {best_zc, best_spt + 10 * best_sq};
   if (path) {
     if (FILE* fp = std::fopen(path, "a")) {
-      std::fprintf(fp, "%s %d %d\n", key.c_str(), best_zc, best_spt);
+      std::fprintf(fp, "%s %d %d\n", key.c_str(), best_zc, best_spt + 10 * best_sq);
       std::fclose(fp);
     }
   }
@@ -834,6 +870,7 @@ int lcbp_set_walls(lcbp_lattice* h, int walls_z, const double* q_wall5) {
   if (p.walls_z != h->p.walls_z) {
     h->zc = 0;  // tuned separately with walls
     h->spt = 0;
+    h->spt_q = 0;
   }
   h->p = p;
   return upload_replica(h);
@@ -1005,6 +1042,16 @@ int lcbp_set_path(lcbp_lattice* h, int path) {
   h->path_req = path;
   h->zc = 0;  // retune for the new choice
   h->spt = 0;
+  h->spt_q = 0;
+  return LCBP_OK;
+}
+
+int lcbp_get_tuning(lcbp_lattice* h, int* planes_per_cta, int* spt_lb, int* spt_q) {
+  CHECK_H(h);
+  const bool f = use_fast(h) && h->zc > 0;
+  if (planes_per_cta) *planes_per_cta = f ? h->zc : 0;
+  if (spt_lb) *spt_lb = f ? h->spt : 0;
+  if (spt_q) *spt_q = f ? (h->spt_q > 0 ? h->spt_q : h->spt) : 0;
   return LCBP_OK;
 }
 

@@ -38,6 +38,7 @@ struct lcbp_batch {
   cudaStream_t stream;
   char* ws;
   void *f[2], *rhou[2], *q, *qs, *h, *sig, *tau, *b, *staging;
+  void* pq;  // the fast kernels' padded scratch, class by class (overlays h, sig, tau, b)
   long long staging_elems;
   void* d_rep;
   Tile* d_tiles;
@@ -98,7 +99,8 @@ bool use_fast(const lcbp_batch* b) {
 }
 
 // 5-D tensor maps of every class: field [c][z][y][x] per replica, replicas of
-// a class back to back (stride comps * padded sites)
+// a class back to back (stride comps * padded sites); the padded scratch of a
+// class holds its replicas back to back too (stride 15 * (nx+4)(ny+2)nz)
 bool build_maps(lcbp_batch* b) {
   const int ty = b->dtype == LCBP_F64 ? zm_tile_rows<double>() : zm_tile_rows<float>();
   for (int k = 0; k < b->zb.nclass; ++k) {
@@ -107,21 +109,27 @@ bool build_maps(lcbp_batch* b) {
     const cuuint64_t es = b->es;
     const cuuint64_t nx = c.G.nx, ny = c.G.ny, nz = c.G.nz, n = c.G.n;
     const cuuint64_t npad = c.count > 1 ? (cuuint64_t)(b->base[b->order[c.rep0 + 1]] - b->base[r0]) : (cuuint64_t)n;
-    auto map = [&](CUtensorMap* tm, void* field, int comps, int rows) {
+    // comps of a field starting at component c0 of a C-component field
+    auto map = [&](CUtensorMap* tm, void* field, int C, int c0, int comps, int rows) {
       const cuuint64_t dims[5] = {nx, ny, nz, (cuuint64_t)comps, (cuuint64_t)c.count};
-      const cuuint64_t strides[4] = {nx * es, nx * ny * es, n * es, (cuuint64_t)comps * npad * es};
+      const cuuint64_t strides[4] = {nx * es, nx * ny * es, n * es, (cuuint64_t)C * npad * es};
       const cuuint32_t box[5] = {(cuuint32_t)kZmBoxX, (cuuint32_t)rows, 1, (cuuint32_t)comps, 1};
-      void* base = static_cast<char*>(field) + (size_t)comps * b->base[r0] * b->es;
+      void* base = static_cast<char*>(field) + ((size_t)C * b->base[r0] + (size_t)c0 * n) * b->es;
       return encode_tiled(tm, base, 5, dims, strides, box, b->dtype);
     };
-    bool ok = map(&b->maps[0].q[k], b->q, 5, ty + 4) && map(&b->maps[0].u[k], b->rhou[0], 4, ty + 2) &&
-              map(&b->maps[1].u[k], b->rhou[1], 4, ty + 2) && map(&b->maps[0].s[k], b->sig, 5, ty + 2) &&
-              map(&b->maps[0].b[k], b->b, 3, ty + 2) && map(&b->maps[0].qs[k], b->qs, 5, ty + 2);
+    const cuuint64_t nxp = nx + kZmPadX, nyp = ny + 2, cp = nxp * nyp * nz;
+    const cuuint64_t pdims[5] = {nxp, nyp, nz, (cuuint64_t)kZmPQ, (cuuint64_t)c.count};
+    const cuuint64_t pstr[4] = {nxp * es, nxp * nyp * es, cp * es, (cuuint64_t)kZmPQ * cp * es};
+    const cuuint32_t pbox[5] = {(cuuint32_t)kZmBoxXP, (cuuint32_t)(ty + 2), 1, (cuuint32_t)kZmPQ, 1};
+    bool ok = map(&b->maps[0].q[k], b->q, 5, 0, 5, ty + 4) && map(&b->maps[0].u[k], b->rhou[0], 4, 0, 4, ty + 2) &&
+              map(&b->maps[1].u[k], b->rhou[1], 4, 0, 4, ty + 2) &&
+              map(&b->maps[0].u3[k], b->rhou[0], 4, 1, 3, ty + 2) &&
+              map(&b->maps[1].u3[k], b->rhou[1], 4, 1, 3, ty + 2) &&
+              encode_tiled(&b->maps[0].pq[k], static_cast<char*>(b->pq) + (size_t)c.pq0 * b->es, 5, pdims, pstr,
+                           pbox, b->dtype);
     if (!ok) return false;
     b->maps[1].q[k] = b->maps[0].q[k];
-    b->maps[1].s[k] = b->maps[0].s[k];
-    b->maps[1].b[k] = b->maps[0].b[k];
-    b->maps[1].qs[k] = b->maps[0].qs[k];
+    b->maps[1].pq[k] = b->maps[0].pq[k];
   }
   return true;
 }
@@ -137,6 +145,9 @@ void set_zc(lcbp_batch* b, const int* zc) {
     c.G.tiles_y = (c.G.ny + ty - 1) / ty;
     c.G.tiles_z = (c.G.nz + c.G.zc - 1) / c.G.zc;
     c.ctas_per_rep = c.G.tiles_x * c.G.tiles_y * c.G.tiles_z;
+    c.G.nxp = c.G.nx + kZmPadX;
+    c.G.nyp = c.G.ny + 2;
+    c.G.cp = (long long)c.G.nxp * c.G.nyp * c.G.nz;
     c.cta0 = cta;
     cta += c.ctas_per_rep * c.count;
   }
@@ -152,9 +163,7 @@ ZmBatchArgs zm_args(lcbp_batch* b) {
   a.order = b->d_order;
   a.q = b->q;
   a.qout = nullptr;
-  a.qs = b->qs;
-  a.sigma = b->sig;
-  a.b = b->b;
+  a.pq = b->pq;
   a.f = b->f[b->cur];
   a.fnew = b->f[b->cur ^ 1];
   a.rhou = b->rhou[b->cur];
@@ -277,7 +286,7 @@ int tune_fast(lcbp_batch* b, float* best_ms) {
   auto time_zc = [&](const int* zc) {
     set_zc(b, zc);
     ZmBatchArgs a = zm_args(b);
-    a.qout = b->h;  // scratch: the state is left untouched
+    a.qout = b->qs;  // scratch the fast kernels do not use: the state is left untouched
     float t = 1e30f;
     for (int rep = 0; rep < 3 && err == cudaSuccess; ++rep) {
       cudaEventRecord(e0, b->stream);
@@ -505,6 +514,13 @@ int lcbp_batch_create(int R, const int* dims, const lcbp_params* params, int dty
   }
   if ((int)members.size() > kZmMaxClasses) b->fast_ok = false;
   b->zb.nclass = std::min((int)members.size(), kZmMaxClasses);
+  // the fast kernels' padded scratch, class by class (64-element aligned blocks)
+  long long pq_tot = 0;
+  for (int k = 0; k < b->zb.nclass; ++k) {
+    ZmClass& c = b->zb.c[k];
+    c.pq0 = pq_tot;
+    pq_tot += ((long long)c.count * zm_pq_elems(c.G.nx, c.G.ny, c.G.nz) + 63) / 64 * 64;
+  }
   b->path_req = LCBP_PATH_AUTO;
   b->fast_pick = true;
   b->zc = 0;
@@ -516,12 +532,20 @@ int lcbp_batch_create(int R, const int* dims, const lcbp_params* params, int dty
   b->tile_cap = cap;
   b->flow_on = 1;
   b->coupling = LCBP_JACOBI;
-  const long long comps[10] = {15, 15, 4, 4, 5, 5, 5, 5, 3, 3};
+  // f0 f1 rhou0 rhou1 q qs, then h sig tau b back to back in one block that
+  // the fast kernels' padded scratch overlays (the two kernel sets never run
+  // within one step, and no scratch outlives a step)
+  const long long comps[6] = {15, 15, 4, 4, 5, 5};
   size_t off[10], o = 0;
-  for (int i = 0; i < 10; ++i) {
+  for (int i = 0; i < 6; ++i) {
     off[i] = o;
     o = a256(o + (size_t)comps[i] * tot * b->es);
   }
+  off[6] = o;
+  off[7] = o + (size_t)5 * tot * b->es;
+  off[8] = o + (size_t)10 * tot * b->es;
+  off[9] = o + (size_t)13 * tot * b->es;
+  o = a256(o + (size_t)std::max(16 * tot, pq_tot) * b->es);
   const size_t off_stage = o;
   b->staging_elems = std::min(kStaging, 15 * tot);
   o = a256(o + (size_t)b->staging_elems * 8);
@@ -554,6 +578,7 @@ int lcbp_batch_create(int R, const int* dims, const lcbp_params* params, int dty
   b->sig = w + off[7];
   b->tau = w + off[8];
   b->b = w + off[9];
+  b->pq = w + off[6];
   b->staging = w + off_stage;
   b->d_rep = w + off_rep;
   b->d_tiles = reinterpret_cast<Tile*>(w + off_tiles);

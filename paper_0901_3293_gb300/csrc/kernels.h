@@ -103,19 +103,38 @@ constexpr int kDiagPartials = 512 * 8;
 // Fast path (flow on, Jacobi coupling, nx % 4 == 0): two z-marching kernels
 // with TMA-staged planes.  Tensor maps describe one field as a 4-D tensor
 // (x, y, z, component) and are built by the host (make_field_tmap).
+//
+// Between the two kernels the step's intermediate fields live in a
+// periodically padded scratch ("LB-ready" scratch): 15 components
+// [F_x F_y F_z V_x V_y V_z C W_xy W_xz W_yz | Q*_xx Q*_xy Q*_xz Q*_yy Q*_yz],
+// each an (nx + 4) x (ny + 2) x nz array in which site (x, y, z) sits at
+// (x + 1, y + 1, z) and the columns x = -1, nx and rows y = -1, ny hold the
+// periodic images.  The second kernel then stages them by TMA with no halo
+// patching.  The first ten are the per-site coefficients of the LB
+// pre-collision terms (f^eq_i / tau_f + p_i of Sec. 2.2 Eq. feq, coeff, eq4):
+// a face direction +-e_a has F_a +- V_a, a corner direction s has
+// C + (s . V) / 8 + s_x s_y W_xy + s_x s_z W_xz + s_y s_z W_yz.
 // ---------------------------------------------------------------------------
+constexpr int kZmPadX = 4;   // padded scratch: columns added to nx (one left, three right)
+constexpr int kZmPQ = 15;    // components of the padded scratch
+
 struct ZmGeom {
   int nx, ny, nz, zc;
   long long n;
   int tiles_x, tiles_y, tiles_z;
+  int nxp, nyp;    // padded scratch extents: nx + 4, ny + 2
+  long long cp;    // padded scratch component stride: nxp * nyp * nz
 };
 
 struct ZmArgs {
   int nx, ny, nz, zc;
-  int spt;            // sites per thread, 1 or 2 (2 only where zm_spt_max allows)
+  int spt;            // sites per thread of k_lbq, 1 or 2 (2 only where zm_spt_max allows)
+  int spt_q;          // sites per thread of k_qside (0: as spt)
   const void* model;  // host copy of Model<real>
-  const CUtensorMap *tm_q, *tm_u, *tm_sigma, *tm_b, *tm_qs;
-  void *q, *qout, *qs, *sigma, *b;  // qout: nullptr = update Q in place
+  // Q (box rows TY + 4), rho u (4 components), the padded scratch (15), u (rho u components 1..3)
+  const CUtensorMap *tm_q, *tm_u, *tm_pq, *tm_u3;
+  const CUtensorMap* tm_f;  // f^n (15 components), for L2 prefetches of the pulled populations
+  void *q, *qout, *pq;  // qout: nullptr = update Q in place; pq: padded scratch
   const void* bext;
   void *f, *fnew, *rhou, *rhou_new;
   int* err;              // set to 1 if a bounded barrier wait timed out
@@ -123,7 +142,13 @@ struct ZmArgs {
   const double* q_wall;  // walls in z with this anchored Q (5 values), or nullptr: periodic
 };
 
-constexpr int kZmBoxX = 40;  // elements per TMA box row
+// elements of the padded scratch of one nx x ny x nz lattice
+inline long long zm_pq_elems(int nx, int ny, int nz) {
+  return (long long)kZmPQ * (nx + kZmPadX) * (ny + 2) * nz;
+}
+
+constexpr int kZmBoxX = 40;  // elements per TMA box row of the unpadded fields
+constexpr int kZmBoxXP = 36; // elements per TMA box row of the padded scratch
 
 // Fast path over a batch: replicas of equal dims form a class whose fields are
 // stored back to back, so that each field of a class is one 5-D tensor
@@ -136,22 +161,24 @@ struct ZmClass {
   int ctas_per_rep;  // tiles_x * tiles_y * tiles_z
   int rep0;          // first entry of the class in the replica order table
   int count;         // replicas in the class
+  long long pq0;     // first element of the class's padded scratch (replica j at pq0 + j * 15 * cp)
 };
 struct ZmBatch {
   int nclass;
   int total_ctas;
   ZmClass c[kZmMaxClasses];
 };
-// per class: Q (box rows TY + 4), rho u, sigma, b, Q* (box rows TY + 2); 5-D
+// per class: Q (box rows TY + 4), rho u (4 components), the padded scratch
+// (15), u (rho u components 1..3); box rows TY + 2 but for Q; 5-D
 struct ZmBatchMaps {
-  CUtensorMap q[kZmMaxClasses], u[kZmMaxClasses], s[kZmMaxClasses], b[kZmMaxClasses], qs[kZmMaxClasses];
+  CUtensorMap q[kZmMaxClasses], u[kZmMaxClasses], pq[kZmMaxClasses], u3[kZmMaxClasses];
 };
 struct ZmBatchArgs {
   ZmBatch B;
   const ZmBatchMaps* maps;  // host copy (rho u maps of the current buffer)
   const void* reps;         // device Replica<real>[R]: base offsets and models
   const int* order;         // device: replica indices, class by class in storage order
-  void *q, *qout, *qs, *sigma, *b;  // qout: nullptr = update Q in place
+  void *q, *qout, *pq;      // qout: nullptr = update Q in place; pq: padded scratch of all classes
   void *f, *fnew, *rhou, *rhou_new;
   int* err;
 };

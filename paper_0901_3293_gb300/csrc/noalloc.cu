@@ -1,15 +1,17 @@
 // Allocation-free free-energy reduction.
 //
 // Some callers cannot allocate device memory at the moment they need the
-// free energy: code running while a stream is being captured into a CUDA
-// graph (cudaMalloc is not capturable), code inside a framework whose caching
-// allocator owns the whole device heap, or a real-time loop that must never
-// touch the allocator.  This entry point serves them: it reduces a
-// caller-owned device Q field with the same FP64 diagnostics kernel as
-// lcbp_free_energy, but its scratch (the per-block partial sums) lives in a
-// fixed file-scope device array instead of memory obtained with cudaMalloc.
+// free energy: code inside a framework whose caching allocator owns the whole
+// device heap, or a real-time loop that must never touch the allocator.  This
+// entry point serves them: it reduces a caller-owned device Q field with the
+// same FP64 diagnostics kernel as lcbp_free_energy, but its scratch (the
+// per-block partial sums) lives in a fixed file-scope device array instead of
+// memory obtained with cudaMalloc.  It covers a periodic lattice with the
+// one-constant energy (L2 = K, no walls).
 #include <cstdint>
 #include <mutex>
+
+#include <cuda.h>
 
 #include "../../include/lcbp.h"
 #include "kernels.h"
@@ -24,23 +26,69 @@ static __device__ __align__(256) double g_noalloc_scratch[kScratchDoubles];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
-double* g_scratch_ptr[kMaxDevices] = {};
+// per device: the unique ID of the context the address was looked up in
+// (a context handle can be reused after a reset; the ID is not), and the address
+struct ScratchAddr {
+  unsigned long long ctx_id;
+  double* ptr;
+};
+ScratchAddr g_scratch[kMaxDevices] = {};
 
-// Device address of the scratch on the current device, looked up once per
-// device (the symbol name in host code is only a stand-in, not an address).
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long*);
+
+// driver entry points, found once through the runtime
+template <typename Fn>
+Fn driver_fn(const char* name) {
+  void* p = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  if (cudaGetDriverEntryPointByVersion(name, &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+      q == cudaDriverEntryPointSuccess)
+    return reinterpret_cast<Fn>(p);
+  return nullptr;
+}
+
+// ID of the current context; 0 if none is current
+int current_context_id(unsigned long long* id) {
+  static CtxGetCurrentFn get = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    get = driver_fn<CtxGetCurrentFn>("cuCtxGetCurrent");
+    get_id = driver_fn<CtxGetIdFn>("cuCtxGetId");
+  });
+  if (!get || !get_id) return lcbp::fail(LCBP_ECUDA, "cuCtxGetCurrent / cuCtxGetId unavailable");
+  CUcontext ctx = nullptr;
+  if (get(&ctx) != CUDA_SUCCESS) return lcbp::fail(LCBP_ECUDA, "cuCtxGetCurrent failed");
+  *id = 0;
+  if (ctx && get_id(ctx, id) != CUDA_SUCCESS) return lcbp::fail(LCBP_ECUDA, "cuCtxGetId failed");
+  return LCBP_OK;
+}
+
+// Device address of the scratch on the current device (the symbol name in
+// host code is only a stand-in, not an address).  It is looked up on the
+// first call in each context of a device: a call after cudaDeviceReset, which
+// ends the context and unloads the module, looks it up again.
 int scratch_for_current_device(double** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return lcbp::cuda_fail(e, "cudaGetDevice");
   if (dev < 0 || dev >= kMaxDevices) return lcbp::fail(LCBP_EINVAL, "device ordinal %d out of range", dev);
+  unsigned long long id = 0;
+  int rc = current_context_id(&id);
+  if (rc) return rc;
   std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_scratch_ptr[dev]) {
+  if (id == 0 || !g_scratch[dev].ptr || g_scratch[dev].ctx_id != id) {
+    // the lookup also brings up the device's primary context if none is current
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return lcbp::cuda_fail(e, "cudaGetSymbolAddress");
-    g_scratch_ptr[dev] = static_cast<double*>(p);
+    rc = current_context_id(&id);
+    if (rc) return rc;
+    if (id == 0) return lcbp::fail(LCBP_ECUDA, "no current CUDA context");
+    g_scratch[dev] = {id, static_cast<double*>(p)};
   }
-  *out = g_scratch_ptr[dev];
+  *out = g_scratch[dev].ptr;
   return LCBP_OK;
 }
 

@@ -1,10 +1,12 @@
 // Fast path of the coupled step: two z-marching kernels with TMA-staged planes.
 //
-//   k_qside  (Q^n, rho u^n)            -> sigma_LC, b, Q*            (88 B/site FP32)
+//   k_qside  (Q^n, rho u^n)            -> P, Q*                      (96 B/site FP32)
 //            H, sigma_LC, tau and the body force b = D0_b tau_ab - H_gn D0_a Q_gn,
 //            then the Heun predictor Q* = Q + R(Q, u)   (Sec. 2.1 Eq. Qevolution,
-//            mat_der, BEstress; Sec. 2.2 Eq. eq7a, spurious)
-//   k_lbq    (f^n, rho u^n, sigma, b, Q*, Q^n) -> f^{n+1}, rho u^{n+1}, Q^{n+1}   (244 B/site FP32)
+//            mat_der, BEstress; Sec. 2.2 Eq. eq7a, spurious), and P: the ten
+//            coefficients of the site's LB pre-collision terms f^eq_i / tau_f + p_i
+//            (Sec. 2.2 Eq. feq, coeff, eq4), built from rho^n, u^n, sigma_LC and b
+//   k_lbq    (f^n, rho u^n, P, Q*, Q^n) -> f^{n+1}, rho u^{n+1}, Q^{n+1}   (252 B/site FP32)
 //            predictor-corrector D3Q15 LB (Sec. 2.2 Eq. eq2, eq4, feq, coeff) and the
 //            Heun corrector Q^{n+1} = (Q + Q* + R(Q*)) / 2
 //
@@ -12,11 +14,13 @@
 // Planes of the fields it reads with a halo are brought into shared memory
 // by 4-D TMA tile loads (x, y, z, component) into a ring of slots, each slot
 // with its own mbarrier; the load of a plane is issued one or two planes
-// before the CTA needs it, so HBM traffic overlaps compute.  A TMA box is 40
-// elements wide (x0-4 .. x0+35, 16-byte aligned start); out-of-range halo
-// cells of edge tiles are zero-filled by TMA and then overwritten with their
-// periodic images by plain loads.  Populations are pulled straight from
-// global memory (each is used once).
+// before the CTA needs it, so HBM traffic overlaps compute.  A TMA box of the
+// state fields is 40 elements wide (x0-4 .. x0+35, 16-byte aligned start);
+// out-of-range halo cells of edge tiles are zero-filled by TMA and then
+// overwritten with their periodic images by plain loads.  P and Q* go from
+// k_qside to k_lbq through a scratch padded with their periodic images (see
+// kernels.h), so their boxes (36 wide, x0-1 .. x0+34) need no patching.
+// Populations are pulled straight from global memory (each is used once).
 #include <cuda.h>
 
 #include <type_traits>
@@ -202,7 +206,8 @@ struct QsideSmem {
   static constexpr int QSLOTS = 5, USLOTS = 4;
   static constexpr int QCS = QROWS * ZM_BX, UCS = UROWS * ZM_BX;  // per-component strides
   static constexpr int QSLOT = align_elems(5 * QCS, sizeof(real)), USLOT = align_elems(4 * UCS, sizeof(real));
-  static constexpr int TSLOT = 3 * TROWS * TCOLS, HSLOT = 5 * TY * ZM_TX;
+  // own cells of a plane: H (5 components) then sigma_LC (5)
+  static constexpr int TSLOT = 3 * TROWS * TCOLS, HSLOT = 10 * TY * ZM_TX;
   static constexpr int OFF_U = QSLOTS * QSLOT, OFF_T = OFF_U + USLOTS * USLOT;
   static constexpr int OFF_H = OFF_T + 3 * TSLOT, OFF_BAR = align_elems(OFF_H + 2 * HSLOT, sizeof(real));
   // barriers, the abort flag, then the wrapped box columns and rows (Q box)
@@ -227,8 +232,7 @@ template <typename real, int TY, int SPT, bool BATCH, bool WALLS>
 __device__ __forceinline__ void qside_body(const CUtensorMap* tmQ, const CUtensorMap* tmU, const ZmGeom G,
                                            const Model<real> m, int bt, int rc, const real* __restrict__ Q,
                                            const real* __restrict__ rhou, const real* __restrict__ bext,
-                                           real* __restrict__ sigma, real* __restrict__ bout,
-                                           real* __restrict__ Qs, int* __restrict__ err, const Sym5<real> qw) {
+                                           real* __restrict__ pq, int* __restrict__ err, const Sym5<real> qw) {
   using L = QsideSmem<real, TY>;
   using V = typename LaneT<real, SPT>::V;
   constexpr int TYH = TY / SPT;  // rows handled by one pass of the CTA
@@ -267,16 +271,18 @@ __device__ __forceinline__ void qside_body(const CUtensorMap* tmQ, const CUtenso
   __syncthreads();
 
   // plane p of Q lives in slot (p - (z0-2)) % 5, of rho u in slot (p - (z0-1)) % 4
-  auto qslot = [&](int p) { return qring + ((p - (z0 - 2)) % L::QSLOTS) * L::QSLOT; };
-  auto uslot = [&](int p) { return uring + ((p - (z0 - 1)) % L::USLOTS) * L::USLOT; };
+  // (the plane offsets below are never negative: unsigned arithmetic keeps the ring
+  // index a plain multiply-shift or mask)
+  auto qslot = [&](int p) { return qring + ((unsigned)(p - (z0 - 2)) % L::QSLOTS) * L::QSLOT; };
+  auto uslot = [&](int p) { return uring + ((unsigned)(p - (z0 - 1)) % L::USLOTS) * L::USLOT; };
   auto issue_q = [&](int p) {
-    const int k = p - (z0 - 2);
+    const unsigned k = p - (z0 - 2);
     uint64_t* bar = &bars[k % L::QSLOTS];
     mbar_arrive_expect_tx(bar, qbytes);
     zm_load<BATCH>(qslot(p), tmQ, x0 - ZM_XOFF, y0 - 2, wrap(p, nz), rc, bar);
   };
   auto issue_u = [&](int p) {
-    const int k = p - (z0 - 1);
+    const unsigned k = p - (z0 - 1);
     uint64_t* bar = &bars[L::QSLOTS + k % L::USLOTS];
     mbar_arrive_expect_tx(bar, ubytes);
     zm_load<BATCH>(uslot(p), tmU, x0 - ZM_XOFF, y0 - 1, wrap(p, nz), rc, bar);
@@ -284,13 +290,13 @@ __device__ __forceinline__ void qside_body(const CUtensorMap* tmQ, const CUtenso
   // Wait for a plane.  Every thread reaches the __syncthreads that follows a
   // wait, so a timeout cannot strand part of the CTA.
   auto wait_q = [&](int p) {
-    const int k = p - (z0 - 2);
+    const unsigned k = p - (z0 - 2);
     const bool ok = mbar_wait_bounded(&bars[k % L::QSLOTS], (k / L::QSLOTS) & 1, kWaitLimitNs);
     if (!ok) *abort_flag = 1;
     return ok;
   };
   auto wait_u = [&](int p) {
-    const int k = p - (z0 - 1);
+    const unsigned k = p - (z0 - 1);
     const bool ok = mbar_wait_bounded(&bars[L::QSLOTS + k % L::USLOTS], (k / L::USLOTS) & 1, kWaitLimitNs);
     if (!ok) *abort_flag = 1;
     return ok;
@@ -337,8 +343,8 @@ __device__ __forceinline__ void qside_body(const CUtensorMap* tmQ, const CUtenso
       base[d] = v;
     }
   };
-  auto tslot = [&](int p) { return tring + wrap(p - z0, 3) * L::TSLOT; };
-  auto hslot = [&](int p) { return hbuf + ((p - z0 + 2) & 1) * L::HSLOT; };
+  auto tslot = [&](int p) { return tring + ((unsigned)(p - z0 + 3) % 3u) * L::TSLOT; };
+  auto hslot = [&](int p) { return hbuf + ((unsigned)(p - z0 + 2) & 1u) * L::HSLOT; };
 
   // H and tau of plane p on the tile plus a one-site ring (Q planes p-1..p+1);
   // a thread takes cells (r, c) and (r + TROWS / SPT, c) together
@@ -354,7 +360,6 @@ __device__ __forceinline__ void qside_body(const CUtensorMap* tmQ, const CUtenso
       for (int t = threadIdx.x; t < L::TSLOT; t += blockDim.x) tslot(p)[t] = real(0);
       return;
     }
-    const bool own = p >= z0 && p < z1;
     const real* qm = qslot(p - 1);
     const real* qc = qslot(p);
     const real* qp = qslot(p + 1);
@@ -408,11 +413,14 @@ __device__ __forceinline__ void qside_body(const CUtensorMap* tmQ, const CUtenso
           hp[2 * NIN + t] = h.xz;
           hp[3 * NIN + t] = h.yy;
           hp[4 * NIN + t] = h.yz;
+          hp[5 * NIN + t] = sg.xx;
+          hp[6 * NIN + t] = sg.xy;
+          hp[7 * NIN + t] = sg.xz;
+          hp[8 * NIN + t] = sg.yy;
+          hp[9 * NIN + t] = sg.yz;
           dq_next[0] = dq[0];
           dq_next[1] = dq[1];
           dq_next[2] = dq[2];
-          const int sx = x0 + c - 1, sy = y0 + r - 1;
-          if (own && sx < nx && sy < ny) store5_lane<1, real>(sigma, n, ((long long)p * ny + sy) * nx + sx, sg, 0);
         }
       }
       return;
@@ -449,9 +457,11 @@ __device__ __forceinline__ void qside_body(const CUtensorMap* tmQ, const CUtenso
           hp[2 * TY * ZM_TX + i] = lane<SPT, real>(h.xz, k);
           hp[3 * TY * ZM_TX + i] = lane<SPT, real>(h.yy, k);
           hp[4 * TY * ZM_TX + i] = lane<SPT, real>(h.yz, k);
-          // sigma of an interior site of a plane this CTA owns goes straight out
-          const int sx = x0 + c - 1, sy = y0 + r - 1;
-          if (own && sx < nx && sy < ny) store5_lane<SPT, real>(sigma, n, ((long long)p * ny + sy) * nx + sx, sg, k);
+          hp[5 * TY * ZM_TX + i] = lane<SPT, real>(sg.xx, k);
+          hp[6 * TY * ZM_TX + i] = lane<SPT, real>(sg.xy, k);
+          hp[7 * TY * ZM_TX + i] = lane<SPT, real>(sg.xz, k);
+          hp[8 * TY * ZM_TX + i] = lane<SPT, real>(sg.yy, k);
+          hp[9 * TY * ZM_TX + i] = lane<SPT, real>(sg.yz, k);
         }
       }
     }
@@ -579,23 +589,80 @@ __device__ __forceinline__ void qside_body(const CUtensorMap* tmQ, const CUtenso
         w[a][2] = half * (upz - umz);
       }
       const Sym5<V> r = be_rate(q, h, dq, u, w, mv, true);
-      const Sym5<V> qs = {q.xx + r.xx, q.xy + r.xy, q.xz + r.xz, q.yy + r.yy, q.yz + r.yz};
+      // Components c0 .. c0 + cnt of the padded scratch for lane k: at the
+      // site's padded position, and at its periodic images in the ghost columns
+      // and rows where the site lies on a lattice face.
+      const int nxp = G.nxp, nyp = G.nyp;
+      const long long cp = G.cp;
+      auto put = [&](int c0, const V* v, int cnt) {
 #pragma unroll
-      for (int k = 0; k < SPT; ++k) {
-        const int gy = y0 + ty + k * TYH;
-        if (gy >= ny) continue;
-        const long long s = ((long long)z * ny + gy) * nx + gx;
-        real ex_b[3] = {real(0), real(0), real(0)};
-        if (bext) {
-          ex_b[0] = bext[s];
-          ex_b[1] = bext[n + s];
-          ex_b[2] = bext[2 * n + s];
+        for (int k = 0; k < SPT; ++k) {
+          const int gy = y0 + ty + k * TYH;
+          if (gy >= ny) continue;
+          auto put1 = [&](int xx, int yy) {
+            real* d = pq + c0 * cp + ((long long)z * nyp + yy) * nxp + xx;
+#pragma unroll
+            for (int c = 0; c < cnt; ++c) d[c * cp] = lane<SPT, real>(v[c], k);
+          };
+          put1(gx + 1, gy + 1);
+          if (gx == 0 || gx == nx - 1 || gy == 0 || gy == ny - 1) {
+            const int xg = gx == 0 ? nx + 1 : (gx == nx - 1 ? 0 : -1);  // nx >= 4: not both
+            const int yg[2] = {gy == 0 ? ny + 1 : -1, gy == ny - 1 ? 0 : -1};
+            if (xg >= 0) put1(xg, gy + 1);
+            for (int j = 0; j < 2; ++j)
+              if (yg[j] >= 0) {
+                put1(gx + 1, yg[j]);
+                if (xg >= 0) put1(xg, yg[j]);
+              }
+          }
         }
-        bout[s] = lane<SPT, real>(bx, k) + ex_b[0];
-        bout[n + s] = lane<SPT, real>(by, k) + ex_b[1];
-        bout[2 * n + s] = lane<SPT, real>(bz, k) + ex_b[2];
-        store5_lane<SPT, real>(Qs, n, s, qs, k);
+      };
+      {
+        const V qv[5] = {q.xx + r.xx, q.xy + r.xy, q.xz + r.xz, q.yy + r.yy, q.yz + r.yz};
+        put(10, qv, 5);
       }
+      // The site's LB pre-collision coefficients from rho^n, u^n, sigma_LC and
+      // b (the external force included): with j = rho u,
+      //   F_a = [drho/30 - rho u^2/12 + (j_a u_a - sigma_aa)/2] / tau_f,
+      //   V_a = (j_a / tau_f + b_a) / 3,   C = [drho/30 + rho u^2/48] / tau_f,
+      //   W_ab = (j_a u_b - sigma_ab) / (8 tau_f),
+      // so that f^eq_i / tau_f + p_i (Sec. 2.2 Eq. feq, coeff, eq4; T = 1/3,
+      // sigma traceless, deviations from the rest weights) is F_a + s V_a for the
+      // face direction s e_a and C + (s . V) / 8 + sum_{a<b} s_a s_b W_ab for the
+      // corner direction s.
+      V bt[3] = {bx, by, bz};
+      if (bext) {
+        long long sb[SPT];
+#pragma unroll
+        for (int k = 0; k < SPT; ++k) {
+          const int gyk = y0 + ty + k * TYH;
+          sb[k] = ((long long)z * ny + (gyk < ny ? gyk : y0 + ty)) * nx + gx;
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a) bt[a] += vld<SPT>(bext, a * n + sb[0], a * n + sb[SPT - 1]);
+      }
+      const int hs0 = ty * ZM_TX + tx;
+      const Sym5<V> sg = ld5v<SPT>(hslot(z) + 5 * TY * ZM_TX, TY * ZM_TX, hs0, hs0 + TYH * ZM_TX);
+      const V drho = vld<SPT>(uc, u0, u1);
+      const V it = mv.inv_tau;
+      const V rho = V(1) + drho;
+      const V jx = rho * u[0], jy = rho * u[1], jz = rho * u[2];
+      const V rusq = jx * u[0] + jy * u[1] + jz * u[2];
+      const V d30 = drho * LCBP_Q(1, 30);
+      const V fb = d30 - rusq * LCBP_Q(1, 12);
+      const V it8 = it * LCBP_Q(1, 8);
+      V P[10];
+      P[0] = (fb + half * (jx * u[0] - sg.xx)) * it;
+      P[1] = (fb + half * (jy * u[1] - sg.yy)) * it;
+      P[2] = (fb + half * (jz * u[2] + (sg.xx + sg.yy))) * it;
+      P[3] = (jx * it + bt[0]) * LCBP_Q(1, 3);
+      P[4] = (jy * it + bt[1]) * LCBP_Q(1, 3);
+      P[5] = (jz * it + bt[2]) * LCBP_Q(1, 3);
+      P[6] = (d30 + rusq * LCBP_Q(1, 48)) * it;
+      P[7] = (jx * u[1] - sg.xy) * it8;
+      P[8] = (jx * u[2] - sg.xz) * it8;
+      P[9] = (jy * u[2] - sg.yz) * it8;
+      put(0, P, 10);
     }
   }
   if (aborted && threadIdx.x == 0) {
@@ -614,9 +681,8 @@ template <typename real, int TY, int SPT, bool WALLS>
 __global__ void __launch_bounds__(qside_threads<TY, SPT>(), sizeof(real) == 4 ? 2 : 1)
     k_qside(const __grid_constant__ CUtensorMap tmQ, const __grid_constant__ CUtensorMap tmU, ZmGeom G,
             Model<real> m, const real* __restrict__ Q, const real* __restrict__ rhou,
-            const real* __restrict__ bext, real* __restrict__ sigma, real* __restrict__ bout,
-            real* __restrict__ Qs, int* __restrict__ err, Sym5<real> qw) {
-  qside_body<real, TY, SPT, false, WALLS>(&tmQ, &tmU, G, m, blockIdx.x, 0, Q, rhou, bext, sigma, bout, Qs, err, qw);
+            const real* __restrict__ bext, real* __restrict__ pq, int* __restrict__ err, Sym5<real> qw) {
+  qside_body<real, TY, SPT, false, WALLS>(&tmQ, &tmU, G, m, blockIdx.x, 0, Q, rhou, bext, pq, err, qw);
 }
 
 // The CTA's batch class, its replica and tile: classes own consecutive CTA ranges.
@@ -654,13 +720,17 @@ template <typename real, int TY>
 __global__ void __launch_bounds__(qside_threads<TY, 1>(), sizeof(real) == 4 ? 2 : 1)
     k_qside_batch(const __grid_constant__ ZmBatchMaps maps, ZmBatch B, const Replica<real>* __restrict__ reps,
                   const int* __restrict__ order, const real* __restrict__ Q, const real* __restrict__ rhou,
-                  real* __restrict__ sigma, real* __restrict__ bout, real* __restrict__ Qs, int* __restrict__ err) {
+                  real* __restrict__ pq, int* __restrict__ err) {
   const ZmItem it = zm_item(B);
   const ZmGeom G = zm_class_geom(B, it.k);
   int rep0 = B.c[0].rep0;
+  long long pq0 = B.c[0].pq0;
 #pragma unroll
   for (int i = 1; i < kZmMaxClasses; ++i)
-    if (i == it.k) rep0 = B.c[i].rep0;
+    if (i == it.k) {
+      rep0 = B.c[i].rep0;
+      pq0 = B.c[i].pq0;
+    }
   const int r = order[rep0 + it.j];
   const long long o = reps[r].base;
   const Model<real> m = reps[r].m;
@@ -673,8 +743,8 @@ __global__ void __launch_bounds__(qside_threads<TY, 1>(), sizeof(real) == 4 ? 2 
       mq = &maps.q[i];
       mu = &maps.u[i];
     }
-  qside_body<real, TY, 1, true, false>(mq, mu, G, m, it.bt, it.j, Q + 5 * o, rhou + 4 * o, nullptr, sigma + 5 * o,
-                                       bout + 3 * o, Qs + 5 * o, err, Sym5<real>{});
+  qside_body<real, TY, 1, true, false>(mq, mu, G, m, it.bt, it.j, Q + 5 * o, rhou + 4 * o, nullptr,
+                                       pq + pq0 + (long long)it.j * kZmPQ * G.cp, err, Sym5<real>{});
 }
 
 // ---------------------------------------------------------------------------
@@ -683,12 +753,13 @@ __global__ void __launch_bounds__(qside_threads<TY, 1>(), sizeof(real) == 4 ? 2 
 template <typename real, int TY>
 struct LbqSmem {
   static constexpr int ROWS = TY + 2, SLOTS = 4;
-  static constexpr int CS = ROWS * ZM_BX;  // per-component stride
-  // one slot: [drho ux uy uz] [sigma 5] [b 3] [Q* 5], each group 128-byte aligned
-  static constexpr int OFF_S = align_elems(4 * CS, sizeof(real));
-  static constexpr int OFF_B = OFF_S + align_elems(5 * CS, sizeof(real));
-  static constexpr int OFF_Q = OFF_B + align_elems(3 * CS, sizeof(real));
-  static constexpr int SLOT = OFF_Q + align_elems(5 * CS, sizeof(real));
+  static constexpr int CSA = ROWS * kZmBoxXP;  // per-component stride of the P / Q* box (padded scratch)
+  static constexpr int CSU = ROWS * ZM_BX;     // per-component stride of the u box (rho u components 1..3)
+  // one slot: [P 10 | Q* 5] then [u_x u_y u_z], each group 128-byte aligned
+  static constexpr int OFF_QS = 10 * CSA;
+  static constexpr int OFF_U = align_elems(kZmPQ * CSA, sizeof(real));
+  static constexpr int SLOT = OFF_U + align_elems(3 * CSU, sizeof(real));
+  static constexpr uint32_t TX_BYTES = (uint32_t)((kZmPQ * CSA + 3 * CSU) * sizeof(real));
   // barriers, the abort flag, then the wrapped box columns and rows
   static constexpr size_t bytes = sizeof(real) * (size_t)SLOTS * SLOT + 8 * 8 + 16 + sizeof(int) * (ZM_BX + ROWS);
 };
@@ -697,22 +768,24 @@ struct LbqSmem {
 // that would arrive from beyond a wall is the reflected one of the same site
 // (half-way bounce-back); the staged Q* of a ghost plane is the anchored qw and
 // its velocity is -u of the adjacent plane.
+// tmF, tmQ (single lattices; null for batches): maps of f^n and Q^n, whose
+// planes are prefetched into L2 one plane before the pulls read them
 template <typename real, int TY, int SPT, bool BATCH, bool WALLS>
-__device__ __forceinline__ void lbq_body(const CUtensorMap* tmU, const CUtensorMap* tmS, const CUtensorMap* tmB,
-                                         const CUtensorMap* tmQs, const ZmGeom& G, const Model<real>& m, int bt,
-                                         int rc, const real* __restrict__ f, const real* __restrict__ rhou,
-                                         const real* __restrict__ sigma, const real* __restrict__ bf,
-                                         const real* __restrict__ Qs, const real* __restrict__ Qin,
+__device__ __forceinline__ void lbq_body(const CUtensorMap* tmPQ, const CUtensorMap* tmU3, const CUtensorMap* tmF,
+                                         const CUtensorMap* tmQ, const ZmGeom& G,
+                                         const Model<real>& m, int bt, int rc, const real* __restrict__ f,
+                                         const real* __restrict__ rhou, const real* __restrict__ Qin,
                                          real* __restrict__ fnew, real* __restrict__ rhou_new,
                                          real* __restrict__ Qout, int* __restrict__ err, const Sym5<real> qw) {
   using L = LbqSmem<real, TY>;
   using V = typename LaneT<real, SPT>::V;
   constexpr int TYH = TY / SPT;  // a thread takes rows ty + k * TYH, k < SPT
+  constexpr int AW = kZmBoxXP;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   real* ring = reinterpret_cast<real*>(smem_raw);
   uint64_t* bars = reinterpret_cast<uint64_t*>(ring + L::SLOTS * L::SLOT);
   int* abort_flag = reinterpret_cast<int*>(bars + 8);
-  int* xw = abort_flag + 4;  // wrapped box columns, then rows (y0 - 1 ...)
+  int* xw = abort_flag + 4;  // wrapped u-box columns, then rows (y0 - 1 ...)
   int* yw = xw + ZM_BX;
 
   const int nx = G.nx, ny = G.ny, nz = G.nz;
@@ -733,77 +806,64 @@ __device__ __forceinline__ void lbq_body(const CUtensorMap* tmU, const CUtensorM
   }
   const bool valid = lane_ok[0];
   const bool edge = x0 - 1 < 0 || x0 + ZM_TX + 1 > nx || y0 - 1 < 0 || y0 + TY + 1 > ny;
-  constexpr int CS = L::CS;
-  constexpr uint32_t slot_bytes = (uint32_t)(17 * CS * sizeof(real));
 
   if (threadIdx.x == 0) {
     for (int i = 0; i < L::SLOTS; ++i) mbar_init(&bars[i], 1);
     *abort_flag = 0;
     mbar_init_fence();
-    tma_prefetch_desc(tmU);
-    tma_prefetch_desc(tmS);
-    tma_prefetch_desc(tmB);
-    tma_prefetch_desc(tmQs);
+    tma_prefetch_desc(tmPQ);
+    tma_prefetch_desc(tmU3);
+    if constexpr (!BATCH) {
+      tma_prefetch_desc(tmF);
+      tma_prefetch_desc(tmQ);
+    }
   }
   fill_wrap_tables(xw, yw, L::ROWS, nx, ny, x0, y0 - 1);
   __syncthreads();
 
-  auto slot = [&](int p) { return ring + ((p - (z0 - 1)) % L::SLOTS) * L::SLOT; };
+  auto slot = [&](int p) { return ring + ((unsigned)(p - (z0 - 1)) % L::SLOTS) * L::SLOT; };
+  // plane p: the padded P / Q* box (site (x, y) at padded (x + 1, y + 1), so the
+  // box starting at padded (x0, y0) covers x0-1 .. x0+34) and the u box of rho u
   auto issue = [&](int p) {
-    const int k = p - (z0 - 1);
+    const unsigned k = p - (z0 - 1);
     uint64_t* bar = &bars[k % L::SLOTS];
     real* sl = slot(p);
     const int zz = wrap(p, nz);
-    mbar_arrive_expect_tx(bar, slot_bytes);
-    zm_load<BATCH>(sl, tmU, x0 - ZM_XOFF, y0 - 1, zz, rc, bar);
-    zm_load<BATCH>(sl + L::OFF_S, tmS, x0 - ZM_XOFF, y0 - 1, zz, rc, bar);
-    zm_load<BATCH>(sl + L::OFF_B, tmB, x0 - ZM_XOFF, y0 - 1, zz, rc, bar);
-    zm_load<BATCH>(sl + L::OFF_Q, tmQs, x0 - ZM_XOFF, y0 - 1, zz, rc, bar);
+    mbar_arrive_expect_tx(bar, L::TX_BYTES);
+    zm_load<BATCH>(sl, tmPQ, x0, y0, zz, rc, bar);
+    zm_load<BATCH>(sl + L::OFF_U, tmU3, x0 - ZM_XOFF, y0 - 1, zz, rc, bar);
+    if constexpr (!BATCH) {
+      // the populations of plane p (pulled from plane p-1 on) and Q^n of plane
+      // p-1, into L2 a plane ahead of their plain loads
+      tma_prefetch_l2_4d(tmF, x0 - ZM_XOFF, y0 - 1, zz, 0);
+      tma_prefetch_l2_4d(tmQ, x0 - ZM_XOFF, y0 - 2, wrap(p - 1, nz), 0);
+    }
   };
   auto wait = [&](int p) {
-    const int k = p - (z0 - 1);
+    const unsigned k = p - (z0 - 1);
     const bool ok = mbar_wait_bounded(&bars[k % L::SLOTS], (k / L::SLOTS) & 1, kWaitLimitNs);
     if (!ok) *abort_flag = 1;
     return ok;
   };
-  // Periodic halo of edge tiles: item t is component t % 17 of frame cell
-  // t / 17 of plane p, over the slot's groups [drho ux uy uz | sigma | b | Q*].
-  // patch_item returns its value and its index in the ring.
+  // Periodic halo of the u box of edge tiles: item t is component t % 3 of
+  // frame cell t / 3 of plane p.  patch_item returns its value and its index
+  // in the ring.
   const Frame<L::ROWS, 3, ZM_TX + 5, 1, true> F(nx, ny, x0, y0 - 1);
-  const int items = edge ? F.cells() * 17 : 0;
+  const int items = edge ? F.cells() * 3 : 0;
   const bool small_frame = items <= (int)blockDim.x;  // one value per thread in the loop
   auto patch_item = [&](int t, int p, int& dst) -> real {
-    const int cell = t / 17, comp = t - 17 * cell;
+    const int cell = t / 3, k = t - 3 * cell;
     int r, c;
     F.cell(cell, r, c);
-    const real* g;
-    int k, off;
-    if (comp < 4) {
-      g = rhou;
-      k = comp;
-      off = 0;
-    } else if (comp < 9) {
-      g = sigma;
-      k = comp - 4;
-      off = L::OFF_S;
-    } else if (comp < 12) {
-      g = bf;
-      k = comp - 9;
-      off = L::OFF_B;
-    } else {
-      g = Qs;
-      k = comp - 12;
-      off = L::OFF_Q;
-    }
-    dst = (int)(slot(p) - ring) + off + (k * L::ROWS + r) * ZM_BX + c;
-    return g[k * n + image_site(r, c, nx, ny, wrap(p, nz), xw, yw)];
+    dst = (int)(slot(p) - ring) + L::OFF_U + (k * L::ROWS + r) * ZM_BX + c;
+    return rhou[(k + 1) * n + image_site(r, c, nx, ny, wrap(p, nz), xw, yw)];
   };
   // a staged plane beyond a wall: only its Q* is read (the anchored qw)
   auto ghost = [&](int p) { return WALLS && (p < 0 || p >= nz); };
   auto fill = [&](int p) {
-    real* sl = slot(p) + L::OFF_Q;
-    for (int t = threadIdx.x; t < 5 * CS; t += blockDim.x) {
-      const int k = t / CS;
+    real* sl = slot(p) + L::OFF_QS;
+    for (int t = threadIdx.x; t < 5 * L::CSA; t += blockDim.x) {
+      const int k = t / L::CSA;
       sl[t] = k == 0 ? qw.xx : k == 1 ? qw.xy : k == 2 ? qw.xz : k == 3 ? qw.yy : qw.yz;
     }
   };
@@ -814,11 +874,13 @@ __device__ __forceinline__ void lbq_body(const CUtensorMap* tmU, const CUtensorM
       ring[d] = v;
     }
   };
-  // neighbour data: component k of [drho ux uy uz | sigma | b] at box index idx
-  // for lane 0 and idx + TYH rows for lane 1
-  auto Nv = [&](const real* sl, int k, int idx) {
-    const int off = k < 4 ? k * CS : (k < 9 ? L::OFF_S + (k - 4) * CS : L::OFF_B + (k - 9) * CS);
-    return vld<SPT>(sl, off + idx, off + idx + TYH * ZM_BX);
+  // component k of the P / Q* box at box index idx (lane 0) and idx + TYH rows
+  // (lane 1); the same for the u box
+  auto PA = [&](const real* sl, int k, int idx) {
+    return vld<SPT>(sl, k * L::CSA + idx, k * L::CSA + idx + TYH * AW);
+  };
+  auto UB = [&](const real* sl, int k, int idx) {
+    return vld<SPT>(sl, L::OFF_U + k * L::CSU + idx, L::OFF_U + k * L::CSU + idx + TYH * ZM_BX);
   };
   // acc +/- v by the sign of e (compile-time after unrolling)
   auto acc = [](V& a, int e, V v) {
@@ -844,14 +906,17 @@ __device__ __forceinline__ void lbq_body(const CUtensorMap* tmU, const CUtensorM
     yp[k] = wrap(gy[k] + 1, ny);
   }
   const V inv_tau = V(m.inv_tau);
+  const V it3 = V(m.inv_tau) * LCBP_Q(1, 3), it8 = V(m.inv_tau) * LCBP_Q(1, 8);
   const Model<V> mv = widen<V>(m);
 
   // One CTA barrier per plane, after the wait: past it every thread has
   // finished plane z-1, the last reader of the slot that the load of plane
   // z+2 overwrites (plane z-2), so that load is issued right after it.
   for (int z = z0; z < z1; ++z) {
-    // populations f_i(y - e_i), issued before the barrier wait so that they overlap it
+    // populations f_i(y - e_i) and the site's rho - 1, issued before the
+    // barrier wait so that they overlap it
     real fin_l[SPT][NV];
+    real dl[SPT];
     const bool wlo = WALLS && z == 0, whi = WALLS && z == nz - 1;
     // beside a wall, the bounce-back directions read the reflected population
     // of the site itself (a build of its own; every other plane pulls)
@@ -866,6 +931,7 @@ __device__ __forceinline__ void lbq_body(const CUtensorMap* tmU, const CUtensorM
             {((long long)zm * ny + ym[k]) * nx, ((long long)zm * ny + gy[k]) * nx, ((long long)zm * ny + yp[k]) * nx},
             {((long long)z * ny + ym[k]) * nx, ((long long)z * ny + gy[k]) * nx, ((long long)z * ny + yp[k]) * nx},
             {((long long)zp * ny + ym[k]) * nx, ((long long)zp * ny + gy[k]) * nx, ((long long)zp * ny + yp[k]) * nx}};
+        dl[k] = __ldg(rhou + rb[1][1] + gx);
 #pragma unroll
         for (int i = 0; i < NV; ++i) {
           const int sx = ex(i) > 0 ? xm : ex(i) < 0 ? xp : gx;
@@ -878,11 +944,11 @@ __device__ __forceinline__ void lbq_body(const CUtensorMap* tmU, const CUtensorM
       if (WALLS && (wlo || whi)) pull(std::true_type{});
       else pull(std::false_type{});
     }
-    // Periodic images of edge tiles.  Small frames (one value per thread):
-    // the value for plane z+2 is read here and stored after the wait of the
-    // next iteration, so that its latency hides behind this plane's work.
-    // Larger frames: the values for plane z+1 are read here, beside the
-    // pulled populations, and stored after its wait.
+    // Periodic images of the u box of edge tiles.  Small frames (one value
+    // per thread): the value for plane z+2 is read here and stored after the
+    // wait of the next iteration, so that its latency hides behind this
+    // plane's work.  Larger frames: the values for plane z+1 are read here,
+    // beside the pulled populations, and stored after its wait.
     constexpr int KP = 3;
     real pv[KP];
     int pd[KP];
@@ -916,7 +982,7 @@ __device__ __forceinline__ void lbq_body(const CUtensorMap* tmU, const CUtensorM
       fence_proxy_async();
       if (z + 2 <= z1) issue(z + 2);
     }
-    // a wall's ghost plane, after its periodic images: the anchored Q*
+    // a wall's ghost plane: the anchored Q*
     if (WALLS && (ghost(z + 1) || (z == z0 && ghost(z0 - 1)))) {
       if (ghost(z + 1)) fill(z + 1);
       if (z == z0 && ghost(z0 - 1)) fill(z0 - 1);
@@ -933,47 +999,42 @@ __device__ __forceinline__ void lbq_body(const CUtensorMap* tmU, const CUtensorM
       const real* nm = slot(z - 1);
       const real* nc = slot(z);
       const real* np = slot(z + 1);
-      const int ci = (ty + 1) * ZM_BX + (tx + ZM_XOFF);
+      const int ca = (ty + 1) * AW + (tx + 1);          // the site in the P / Q* box
+      const int cu = (ty + 1) * ZM_BX + (tx + ZM_XOFF); // the site in the u box
       V fin[NV], ds[NV], dh[NV];
 #pragma unroll
       for (int i = 0; i < NV; ++i) {
         if constexpr (SPT == 1) fin[i] = fin_l[0][i];
         else fin[i] = V(fin_l[0][i], fin_l[SPT - 1][i], 0);
       }
-      Sym5<V> sig_y;
-      V b_y[3], drho_y, u_y[3];
-      // the part of each collision term that does not involve the pulled
-      // population, f^eq / tau_f + p_i, first: the pulls land meanwhile
+      V drho_y;
+      if constexpr (SPT == 1) drho_y = dl[0];
+      else drho_y = V(dl[0], dl[SPT - 1], 0);
+      const V u_y[3] = {UB(nc, 0, cu), UB(nc, 1, cu), UB(nc, 2, cu)};
+      const V rho_y = V(1) + drho_y;
+      const V jn[3] = {rho_y * u_y[0], rho_y * u_y[1], rho_y * u_y[2]};
+      const V rusq_n = jn[0] * u_y[0] + jn[1] * u_y[1] + jn[2] * u_y[2];
+      // f^eq_i / tau_f + p_i at the source site y - e_i from its staged
+      // coefficients; at a wall the bounce-back directions take the site's own
+      // term of the opposite direction (all signs flipped)
       V pre[NV];
+      pre[0] = (drho_y * LCBP_Q(8, 15) - rusq_n * LCBP_Q(2, 3)) * inv_tau;
 #pragma unroll
-      for (int i = 0; i < NV; ++i) {
-        if ((ez(i) > 0 && wl) || (ez(i) < 0 && wh)) {
-          // half-way bounce-back: [f + C]_opp(i) of this site (i = 0 came first)
-          const int o = opp(i);
-          const V usq = u_y[0] * u_y[0] + u_y[1] * u_y[1] + u_y[2] * u_y[2];
-          pre[i] = feq_delta(o, drho_y, V(1) + drho_y, u_y[0], u_y[1], u_y[2], usq, sig_y) * inv_tau +
-                   force_dir(o, b_y[0], b_y[1], b_y[2]);
-          continue;
+      for (int i = 1; i < NV; ++i) {
+        const bool bb = (ez(i) > 0 && wl) || (ez(i) < 0 && wh);
+        const real* sl = bb ? nc : (ez(i) > 0 ? nm : ez(i) < 0 ? np : nc);
+        const int idx = bb ? ca : ca - ey(i) * AW - ex(i);
+        if (i <= 6) {
+          const int a = (i - 1) / 2;
+          const V Fa = PA(sl, a, idx), Va = PA(sl, 3 + a, idx);
+          pre[i] = ((i & 1) != 0) != bb ? Fa + Va : Fa - Va;  // odd i: the + direction
+        } else {
+          const V c0 = PA(sl, 6, idx);
+          const V vs = signed_sum(ex(i), PA(sl, 3, idx), ey(i), PA(sl, 4, idx), ez(i), PA(sl, 5, idx));
+          const V ws = signed_sum(ex(i) * ey(i), PA(sl, 7, idx), ex(i) * ez(i), PA(sl, 8, idx), ey(i) * ez(i),
+                                  PA(sl, 9, idx));
+          pre[i] = bb ? (c0 + ws) - LCBP_Q(1, 8) * vs : (c0 + ws) + LCBP_Q(1, 8) * vs;
         }
-        const real* sl = ez(i) > 0 ? nm : ez(i) < 0 ? np : nc;
-        const int idx = ci - ey(i) * ZM_BX - ex(i);
-        const V drho = Nv(sl, 0, idx);
-        const V ux = Nv(sl, 1, idx), uy = Nv(sl, 2, idx), uz = Nv(sl, 3, idx);
-        const Sym5<V> sv = {Nv(sl, 4, idx), Nv(sl, 5, idx), Nv(sl, 6, idx), Nv(sl, 7, idx), Nv(sl, 8, idx)};
-        const V bx = Nv(sl, 9, idx), by = Nv(sl, 10, idx), bz = Nv(sl, 11, idx);
-        if (i == 0) {
-          sig_y = sv;
-          b_y[0] = bx;
-          b_y[1] = by;
-          b_y[2] = bz;
-          drho_y = drho;
-          u_y[0] = ux;
-          u_y[1] = uy;
-          u_y[2] = uz;
-        }
-        const V usq = ux * ux + uy * uy + uz * uz;
-        pre[i] = feq_delta(i, drho, V(1) + drho, ux, uy, uz, usq, sv) * inv_tau;
-        if (i != 0) pre[i] += force_dir(i, bx, by, bz);
       }
       // C_i = (f^eq - f_i) / tau_f + p_i; predictor f* = f + C, and f + C / 2
 #pragma unroll
@@ -992,13 +1053,37 @@ __device__ __forceinline__ void lbq_body(const CUtensorMap* tmU, const CUtensorM
       }
       const V rs = V(1) + drs;
       const V inv_rs = recip(rs);
-      const V usx = jx * inv_rs, usy = jy * inv_rs, usz = jz * inv_rs;
-      const V ussq = usx * usx + usy * usy + usz * usz;
+      const V us[3] = {jx * inv_rs, jy * inv_rs, jz * inv_rs};
+      const V js[3] = {jx, jy, jz};
+      const V rusq_s = jx * us[0] + jy * us[1] + jz * us[2];
+      // Corrector: the same coefficients for (rho*, u*) with sigma and b held
+      // at the site's step-n values.  P(y) holds them for (rho^n, u^n), so
+      // each takes the change of its moment part.
+      const V dd = (drs - drho_y) * LCBP_Q(1, 30) - (rusq_s - rusq_n) * LCBP_Q(1, 12);
+      V Fs[3], Vs[3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        Fs[a] = PA(nc, a, ca) + (dd + V(0.5) * (js[a] * us[a] - jn[a] * u_y[a])) * inv_tau;
+        Vs[a] = PA(nc, 3 + a, ca) + (js[a] - jn[a]) * it3;
+      }
+      const V Ws[3] = {PA(nc, 7, ca) + (js[0] * us[1] - jn[0] * u_y[1]) * it8,
+                       PA(nc, 8, ca) + (js[0] * us[2] - jn[0] * u_y[2]) * it8,
+                       PA(nc, 9, ca) + (js[1] * us[2] - jn[1] * u_y[2]) * it8};
+      const V Cs0 = (drs * LCBP_Q(1, 30) + rusq_s * LCBP_Q(1, 48)) * inv_tau;
       V dr1 = V(0), j1x = V(0), j1y = V(0), j1z = V(0);
 #pragma unroll
       for (int i = 0; i < NV; ++i) {
-        V Cs = (feq_delta(i, drs, rs, usx, usy, usz, ussq, sig_y) - ds[i]) * inv_tau;
-        if (i != 0) Cs += force_dir(i, b_y[0], b_y[1], b_y[2]);
+        V prs;
+        if (i == 0) {
+          prs = (drs * LCBP_Q(8, 15) - rusq_s * LCBP_Q(2, 3)) * inv_tau;
+        } else if (i <= 6) {
+          const int a = (i - 1) / 2;
+          prs = (i & 1) ? Fs[a] + Vs[a] : Fs[a] - Vs[a];
+        } else {
+          prs = (Cs0 + signed_sum(ex(i) * ey(i), Ws[0], ex(i) * ez(i), Ws[1], ey(i) * ez(i), Ws[2])) +
+                LCBP_Q(1, 8) * signed_sum(ex(i), Vs[0], ey(i), Vs[1], ez(i), Vs[2]);
+        }
+        const V Cs = prs - ds[i] * inv_tau;
         const V fo = dh[i] + V(0.5) * Cs;
 #pragma unroll
         for (int k = 0; k < SPT; ++k)
@@ -1020,33 +1105,32 @@ __device__ __forceinline__ void lbq_body(const CUtensorMap* tmU, const CUtensorM
       }
 
       // Heun corrector with u^n
-      const real* sm = nm + L::OFF_Q;
-      const real* sc = nc + L::OFF_Q;
-      const real* sp = np + L::OFF_Q;
-      const int c1 = ci + TYH * ZM_BX;
+      const real* sm = nm + L::OFF_QS;
+      const real* sc = nc + L::OFF_QS;
+      const real* sp = np + L::OFF_QS;
+      const int c1 = ca + TYH * AW;
       Stencil7<V> st;
-      st.c = ld5v<SPT>(sc, CS, ci, c1);
-      st.xm = ld5v<SPT>(sc, CS, ci - 1, c1 - 1);
-      st.xp = ld5v<SPT>(sc, CS, ci + 1, c1 + 1);
-      st.ym = ld5v<SPT>(sc, CS, ci - ZM_BX, c1 - ZM_BX);
-      st.yp = ld5v<SPT>(sc, CS, ci + ZM_BX, c1 + ZM_BX);
-      st.zm = ld5v<SPT>(sm, CS, ci, c1);
-      st.zp = ld5v<SPT>(sp, CS, ci, c1);
+      st.c = ld5v<SPT>(sc, L::CSA, ca, c1);
+      st.xm = ld5v<SPT>(sc, L::CSA, ca - 1, c1 - 1);
+      st.xp = ld5v<SPT>(sc, L::CSA, ca + 1, c1 + 1);
+      st.ym = ld5v<SPT>(sc, L::CSA, ca - AW, c1 - AW);
+      st.yp = ld5v<SPT>(sc, L::CSA, ca + AW, c1 + AW);
+      st.zm = ld5v<SPT>(sm, L::CSA, ca, c1);
+      st.zp = ld5v<SPT>(sp, L::CSA, ca, c1);
       Sym5<V> dq[3];
       const Sym5<V> h = molecular_field(st, mv, dq);
-      V u[3], w[3][3];
+      V w[3][3];
       const V half = V(0.5);
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
-        u[a] = Nv(nc, a + 1, ci);
-        w[a][0] = half * (Nv(nc, a + 1, ci + 1) - Nv(nc, a + 1, ci - 1));
-        w[a][1] = half * (Nv(nc, a + 1, ci + ZM_BX) - Nv(nc, a + 1, ci - ZM_BX));
-        V upz = Nv(np, a + 1, ci), umz = Nv(nm, a + 1, ci);
-        if (wl) umz = -u[a];  // no slip half a spacing beyond the wall
-        if (wh) upz = -u[a];
+        w[a][0] = half * (UB(nc, a, cu + 1) - UB(nc, a, cu - 1));
+        w[a][1] = half * (UB(nc, a, cu + ZM_BX) - UB(nc, a, cu - ZM_BX));
+        V upz = UB(np, a, cu), umz = UB(nm, a, cu);
+        if (wl) umz = -u_y[a];  // no slip half a spacing beyond the wall
+        if (wh) upz = -u_y[a];
         w[a][2] = half * (upz - umz);
       }
-      const Sym5<V> r = be_rate(st.c, h, dq, u, w, mv, true);
+      const Sym5<V> r = be_rate(st.c, h, dq, u_y, w, mv, true);
       Sym5<V> q0;
       q0.xx = vld<SPT>(Qin, s[0], s[SPT - 1]);
       q0.xy = vld<SPT>(Qin, n + s[0], n + s[SPT - 1]);
@@ -1076,21 +1160,19 @@ __device__ __forceinline__ void lbq_body(const CUtensorMap* tmU, const CUtensorM
 
 template <typename real, int TY, int SPT, bool WALLS>
 __global__ void __launch_bounds__(ZM_TX* TY / SPT, 2)
-    k_lbq(const __grid_constant__ CUtensorMap tmU, const __grid_constant__ CUtensorMap tmS,
-          const __grid_constant__ CUtensorMap tmB, const __grid_constant__ CUtensorMap tmQs, ZmGeom G, Model<real> m,
-          const real* __restrict__ f, const real* __restrict__ rhou, const real* __restrict__ sigma,
-          const real* __restrict__ bf, const real* __restrict__ Qs, const real* __restrict__ Qin,
+    k_lbq(const __grid_constant__ CUtensorMap tmPQ, const __grid_constant__ CUtensorMap tmU3,
+          const __grid_constant__ CUtensorMap tmF, const __grid_constant__ CUtensorMap tmQ, ZmGeom G,
+          Model<real> m, const real* __restrict__ f, const real* __restrict__ rhou, const real* __restrict__ Qin,
           real* __restrict__ fnew, real* __restrict__ rhou_new, real* __restrict__ Qout, int* __restrict__ err,
           Sym5<real> qw) {
-  lbq_body<real, TY, SPT, false, WALLS>(&tmU, &tmS, &tmB, &tmQs, G, m, blockIdx.x, 0, f, rhou, sigma, bf, Qs, Qin,
-                                        fnew, rhou_new, Qout, err, qw);
+  lbq_body<real, TY, SPT, false, WALLS>(&tmPQ, &tmU3, &tmF, &tmQ, G, m, blockIdx.x, 0, f, rhou, Qin, fnew, rhou_new,
+                                        Qout, err, qw);
 }
 
 template <typename real, int TY>
 __global__ void __launch_bounds__(ZM_TX* TY, 2)
     k_lbq_batch(const __grid_constant__ ZmBatchMaps maps, ZmBatch B, const Replica<real>* __restrict__ reps,
                 const int* __restrict__ order, const real* __restrict__ f, const real* __restrict__ rhou,
-                const real* __restrict__ sigma, const real* __restrict__ bf, const real* __restrict__ Qs,
                 const real* __restrict__ Qin, real* __restrict__ fnew, real* __restrict__ rhou_new,
                 real* __restrict__ Qout, int* __restrict__ err) {
   const ZmItem it = zm_item(B);
@@ -1102,18 +1184,15 @@ __global__ void __launch_bounds__(ZM_TX* TY, 2)
   const int r = order[rep0 + it.j];
   const long long o = reps[r].base;
   const Model<real> m = reps[r].m;
-  const CUtensorMap *mu = &maps.u[0], *ms = &maps.s[0], *mb = &maps.b[0], *mqs = &maps.qs[0];
+  const CUtensorMap *mpq = &maps.pq[0], *mu3 = &maps.u3[0];
 #pragma unroll
   for (int i = 1; i < kZmMaxClasses; ++i)
     if (i == it.k) {
-      mu = &maps.u[i];
-      ms = &maps.s[i];
-      mb = &maps.b[i];
-      mqs = &maps.qs[i];
+      mpq = &maps.pq[i];
+      mu3 = &maps.u3[i];
     }
-  lbq_body<real, TY, 1, true, false>(mu, ms, mb, mqs, G, m, it.bt, it.j, f + NV * o, rhou + 4 * o, sigma + 5 * o,
-                                     bf + 3 * o, Qs + 5 * o, Qin + 5 * o, fnew + NV * o, rhou_new + 4 * o,
-                                     Qout + 5 * o, err, Sym5<real>{});
+  lbq_body<real, TY, 1, true, false>(mpq, mu3, nullptr, nullptr, G, m, it.bt, it.j, f + NV * o, rhou + 4 * o, Qin + 5 * o,
+                                     fnew + NV * o, rhou_new + 4 * o, Qout + 5 * o, err, Sym5<real>{});
 }
 
 // ---------------------------------------------------------------------------
@@ -1189,10 +1268,13 @@ ZmGeom zm_geom(int nx, int ny, int nz, int zc, int ty) {
   G.tiles_x = (nx + ZM_TX - 1) / ZM_TX;
   G.tiles_y = (ny + ty - 1) / ty;
   G.tiles_z = (nz + zc - 1) / zc;
+  G.nxp = nx + kZmPadX;
+  G.nyp = ny + 2;
+  G.cp = (long long)G.nxp * G.nyp * nz;
   return G;
 }
 
-template <typename real, int SPT, bool WALLS>
+template <typename real, int SQ, int SPT, bool WALLS>
 cudaError_t launch_step_zm_spt(const ZmArgs& a, cudaStream_t s) {
   constexpr int TY = zm_ty<real>();
   const ZmGeom G = zm_geom(a.nx, a.ny, a.nz, a.zc, TY);
@@ -1201,26 +1283,29 @@ cudaError_t launch_step_zm_spt(const ZmArgs& a, cudaStream_t s) {
   Sym5<real> qw{};
   if (WALLS) qw = {(real)a.q_wall[0], (real)a.q_wall[1], (real)a.q_wall[2], (real)a.q_wall[3], (real)a.q_wall[4]};
   if (a.events) cudaEventRecord(a.events[0], s);
-  k_qside<real, TY, SPT, WALLS><<<grid, qside_threads<TY, SPT>(), QsideSmem<real, TY>::bytes, s>>>(
+  k_qside<real, TY, SQ, WALLS><<<grid, qside_threads<TY, SQ>(), QsideSmem<real, TY>::bytes, s>>>(
       *a.tm_q, *a.tm_u, G, m, static_cast<const real*>(a.q), static_cast<const real*>(a.rhou),
-      static_cast<const real*>(a.bext), static_cast<real*>(a.sigma), static_cast<real*>(a.b),
-      static_cast<real*>(a.qs), a.err, qw);
+      static_cast<const real*>(a.bext), static_cast<real*>(a.pq), a.err, qw);
   if (a.events) cudaEventRecord(a.events[1], s);
   k_lbq<real, TY, SPT, WALLS><<<grid, ZM_TX * TY / SPT, LbqSmem<real, TY>::bytes, s>>>(
-      *a.tm_u, *a.tm_sigma, *a.tm_b, *a.tm_qs, G, m, static_cast<const real*>(a.f),
-      static_cast<const real*>(a.rhou), static_cast<const real*>(a.sigma), static_cast<const real*>(a.b),
-      static_cast<const real*>(a.qs), static_cast<const real*>(a.q), static_cast<real*>(a.fnew),
-      static_cast<real*>(a.rhou_new), static_cast<real*>(a.qout ? a.qout : a.q), a.err, qw);
+      *a.tm_pq, *a.tm_u3, *a.tm_f, *a.tm_q, G, m, static_cast<const real*>(a.f), static_cast<const real*>(a.rhou),
+      static_cast<const real*>(a.q), static_cast<real*>(a.fnew), static_cast<real*>(a.rhou_new),
+      static_cast<real*>(a.qout ? a.qout : a.q), a.err, qw);
   if (a.events) cudaEventRecord(a.events[2], s);
   return cudaGetLastError();
 }
 
+// sites per thread chosen for each kernel separately (FP32: 1 or 2 each; walls and FP64: 1)
 template <typename real>
 cudaError_t launch_step_zm(const ZmArgs& a, cudaStream_t s) {
-  if (a.q_wall) return launch_step_zm_spt<real, 1, true>(a, s);
-  if constexpr (zm_max_spt<real>() == 2)
-    if (a.spt == 2) return launch_step_zm_spt<real, 2, false>(a, s);
-  return launch_step_zm_spt<real, 1, false>(a, s);
+  if (a.q_wall) return launch_step_zm_spt<real, 1, 1, true>(a, s);
+  if constexpr (zm_max_spt<real>() == 2) {
+    const int sq = a.spt_q > 0 ? a.spt_q : a.spt;
+    if (sq == 2 && a.spt == 2) return launch_step_zm_spt<real, 2, 2, false>(a, s);
+    if (sq == 2) return launch_step_zm_spt<real, 2, 1, false>(a, s);
+    if (a.spt == 2) return launch_step_zm_spt<real, 1, 2, false>(a, s);
+  }
+  return launch_step_zm_spt<real, 1, 1, false>(a, s);
 }
 
 template <typename real>
@@ -1241,10 +1326,9 @@ cudaError_t launch_step_zm_batch(const ZmBatchArgs& a, cudaStream_t s) {
   const auto* reps = static_cast<const Replica<real>*>(a.reps);
   k_qside_batch<real, TY><<<grid, qside_threads<TY, 1>(), QsideSmem<real, TY>::bytes, s>>>(
       *a.maps, a.B, reps, a.order, static_cast<const real*>(a.q), static_cast<const real*>(a.rhou),
-      static_cast<real*>(a.sigma), static_cast<real*>(a.b), static_cast<real*>(a.qs), a.err);
+      static_cast<real*>(a.pq), a.err);
   k_lbq_batch<real, TY><<<grid, ZM_TX * TY, LbqSmem<real, TY>::bytes, s>>>(
       *a.maps, a.B, reps, a.order, static_cast<const real*>(a.f), static_cast<const real*>(a.rhou),
-      static_cast<const real*>(a.sigma), static_cast<const real*>(a.b), static_cast<const real*>(a.qs),
       static_cast<const real*>(a.q), static_cast<real*>(a.fnew), static_cast<real*>(a.rhou_new),
       static_cast<real*>(a.qout ? a.qout : a.q), a.err);
   return cudaGetLastError();

@@ -72,6 +72,7 @@ _SIGNATURES = {
     "lcbp_save": (_c_int, [_P, ctypes.c_char_p]),
     "lcbp_load": (_c_int, [_P, ctypes.c_char_p]),
     "lcbp_reequilibrate_f": (_c_int, [_P]),
+    "lcbp_get_tuning": (_c_int, [_P, ctypes.POINTER(_c_int), ctypes.POINTER(_c_int), ctypes.POINTER(_c_int)]),
     "lcbp_free_energy_noalloc": (_c_int, [_c_void_p, _c_int, _c_int, _c_int, _c_int, _c_double, _c_double,
                                           _c_double, _c_double, _c_void_p, ctypes.POINTER(_c_double)]),
     "lcbp_surrogate_param_count": (_c_size_t, []),
@@ -335,6 +336,14 @@ class Lattice:
         spt = _c_int()
         check(lib().lcbp_get_path(self._h, ctypes.byref(fast), ctypes.byref(zc), ctypes.byref(spt)))
         return bool(fast.value), zc.value, spt.value
+
+    def tuning(self):
+        """(planes per CTA, sites per thread of the LB kernel, of the field kernel)."""
+        zc = _c_int()
+        sl = _c_int()
+        sq = _c_int()
+        check(lib().lcbp_get_tuning(self._h, ctypes.byref(zc), ctypes.byref(sl), ctypes.byref(sq)))
+        return zc.value, sl.value, sq.value
 
     def synchronize(self) -> None:
         check(lib().lcbp_synchronize(self._h))

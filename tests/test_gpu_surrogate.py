@@ -94,13 +94,27 @@ def test_training_gradients_match_oracle(lcbp, kernel):
     # the network learns the correction to ten Euler steps of the rate
     loss_o, dout = S.masked_mse(y, (dq - 10.0 * r5) / S_DQ, mask)
     G, _ = S.backward(P, acts, dout, BLOCKS, quant=S.bf16)
+    # the same gradients with no BF16 rounding anywhere (plain FP64 network)
+    y_e, acts_e = S.forward(P, x, BLOCKS)
+    _, dout_e = S.masked_mse(y_e, (dq - 10.0 * r5) / S_DQ, mask)
+    G_e, _ = S.backward(P, acts_e, dout_e, BLOCKS)
     assert abs(loss - loss_o) < 1e-3 * loss_o
+    # Element-wise bounds, per layer, relative to the layer's largest gradient.
+    # BF16 keeps 8 significant bits (unit roundoff u = 2^-8).  Against the
+    # oracle that rounds where the kernels store, only the FP32 accumulation
+    # order differs: a stored value can land one BF16 ulp (2u) away, and those
+    # flips propagate, so 2e-2 (about 5u) bounds every element.  Against the
+    # unrounded FP64 network the gradient of each weight passes through about
+    # twenty BF16 roundings (ten stored activations, ten stored gradients);
+    # to first order that is 20u = 8e-2, so every element is held to 1e-1.
     for name in S.layer_names(BLOCKS):
         for k in (0, 1):
-            ref = G[name][k]
-            rel = np.linalg.norm(g[name][k] - ref) / np.linalg.norm(ref)
-            print(name, "W" if k == 0 else "b", f"rel {rel:.2e}")
-            assert rel < 2e-2, (name, k, rel)
+            got, ref, ref_e = g[name][k], G[name][k], G_e[name][k]
+            err_q = np.abs(got - ref).max() / np.abs(ref).max()
+            err_e = np.abs(got - ref_e).max() / np.abs(ref_e).max()
+            print(name, "W" if k == 0 else "b", f"max err / max|g|: vs BF16 oracle {err_q:.2e}, vs FP64 {err_e:.2e}")
+            assert err_q < 2e-2, (name, k, err_q)
+            assert err_e < 1e-1, (name, k, err_e)
     # Adam moved the parameters by about lr
     step = sur.get_params().astype(np.float64) - S.flatten(P, BLOCKS)
     assert 0 < np.abs(step).max() < 1.5e-6
