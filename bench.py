@@ -35,8 +35,8 @@ SEED = 20090119
 # read or write once (inputs + outputs)
 KERNEL_BYTES = {
     # fast path (z-marching, TMA-staged planes)
-    "qside": (5 + 4 + 5 + 3 + 5) * 4,                          # Q, rho u -> sigma, b, Q*
-    "lbq": (15 + 4 + 5 + 3 + 5 + 5 + 15 + 4 + 5) * 4,          # f, rho u, sigma, b, Q*, Q -> f, rho u, Q
+    "qside": (5 + 4 + 10 + 5) * 4,                             # Q, rho u -> P (LB coefficients), Q*
+    "lbq": (15 + 10 + 5 + 3 + 1 + 5 + 15 + 4 + 5) * 4,         # f, P, Q*, u, rho, Q -> f, rho u, Q
     # generic path
     "field": (5 + 5 + 5 + 3) * 4,                              # Q -> H, sigma, tau
     "force_predict": (5 + 5 + 3 + 4 + 3 + 5) * 4,              # Q, H, tau, rho u -> b, Q*
@@ -342,6 +342,7 @@ def run_ours(args):
     # ---- per-kernel device times, kernel by kernel with events (same kernels)
     kms = lat.profile_steps(max(3, min(args.steps, 10)))
     fast, zc, spt = lat.path()
+    _, spt_lbq, spt_qside = lat.tuning()
     peak, peak_kind = measured_peaks()
     per_kernel = {}
     # instruction-issue peak: one warp instruction per scheduler per cycle, 4 schedulers per
@@ -524,7 +525,7 @@ def run_ours(args):
         "data": "synthetic",
         "config": {**workload_config(world),
                    "kernels": "fast (z-marching, TMA-staged planes)" if fast else "generic",
-                   "planes_per_cta": zc, "sites_per_thread": spt},
+                   "planes_per_cta": zc, "sites_per_thread": {"lbq": spt_lbq, "qside": spt_qside}},
         "roofline": roof, "per_kernel": per_kernel, "cpu_baseline": cpu, "e2e": e2e,
         "gpu_launches": launches, "clocks": clk, "free_energy_after": F,
         "diagnostics_256cube": diag_line, "walls_256cube": walls_line, "generic_kernels_256cube": generic_line, "slab_64x64x256": slab_line, "surrogate_slab_64x64x256": sur_line, "texture_slab_64x64x256": tex_line,

@@ -151,12 +151,16 @@ LCBP_API int lcbp_set_ldg_kappa_tau(lcbp_lattice *h, double A0, double q0, doubl
 
 /*
  * Kinetic parameters: LB relaxation time tau_f (viscosity eta = rho tau_f / 3,
- * Sec. 2.2 Eq. eq4), flow-aligning parameter xi (Sec. 2.1 Eq. mat_der),
+ * Sec. 2.2 Eq. eq4), reference density rho0 of the fluid (the density of the
+ * initial equilibrium, Sec. 2.2 Eq. feq; lcbp_init_f_equilibrium uses it when
+ * given 0; default 1), flow-aligning parameter xi (Sec. 2.1 Eq. mat_der),
  * rotational diffusion constant Gamma (Eq. Qevolution), flow_on (0 imposes
  * u = 0 and skips the LB update, Sec. 2.1), coupling LCBP_JACOBI or
- * LCBP_GAUSS_SEIDEL.  Errors: LCBP_EINVAL (tau_f <= 0, Gamma < 0, bad coupling).
+ * LCBP_GAUSS_SEIDEL.  Errors: LCBP_EINVAL (tau_f <= 0, rho0 <= 0, Gamma < 0,
+ * bad coupling).
  */
-LCBP_API int lcbp_set_flow(lcbp_lattice *h, double tau_f, double xi, double Gamma, int flow_on, int coupling);
+LCBP_API int lcbp_set_flow(lcbp_lattice *h, double tau_f, double rho0, double xi, double Gamma, int flow_on,
+                           int coupling);
 
 /*
  * Elastic energy variant (Sec. 2.1, Eq. free_energy).  The printed gradient
@@ -209,17 +213,21 @@ LCBP_API int lcbp_set_walls(lcbp_lattice *h, int walls_z, const double *q_wall5)
 LCBP_API int lcbp_init_q(lcbp_lattice *h, int kind, double amplitude, double noise, uint64_t seed,
                 const int *region);
 
-/* Upload Q: q5 holds 5 * N values in the layout above.  Errors: LCBP_EINVAL. */
+/* Upload Q: q5 holds 5 * N values in the layout above.  A field holding any
+ * NaN or Inf is refused and Q is left unchanged.  Errors: LCBP_EINVAL,
+ * LCBP_ENONFINITE. */
 LCBP_API int lcbp_set_q(lcbp_lattice *h, const void *q5, int dtype);
 
 /*
  * Set f = f^eq(rho0, u, sigma_LC(Q)) at every site (Sec. 2.2 Eq. feq, coeff,
  * without the forcing term), with u from u3 (3 * N values) or u = 0 if u3 is
- * NULL, and sigma_LC from the current Q.  Errors: LCBP_EINVAL (rho0 <= 0).
+ * NULL, and sigma_LC from the current Q; rho0 = 0 takes the reference density
+ * of lcbp_set_flow.  Errors: LCBP_EINVAL (rho0 < 0).
  */
 LCBP_API int lcbp_init_f_equilibrium(lcbp_lattice *h, double rho0, const void *u3, int dtype);
 
-/* Upload the 15 * N populations.  Errors: LCBP_EINVAL. */
+/* Upload the 15 * N populations.  Populations holding any NaN or Inf are
+ * refused and f is left unchanged.  Errors: LCBP_EINVAL, LCBP_ENONFINITE. */
 LCBP_API int lcbp_set_f(lcbp_lattice *h, const void *f15, int dtype);
 
 /*
@@ -382,6 +390,20 @@ LCBP_API int lcbp_texture(lcbp_lattice *h, const lcbp_optics *o, float *img);
 LCBP_API int lcbp_save(lcbp_lattice *h, const char *path);
 LCBP_API int lcbp_load(lcbp_lattice *h, const char *path);
 
+/*
+ * Raw snapshot of the state: the deviation populations f (15 N), the moments
+ * [rho - 1, u] (4 N) and Q (5 N), all in the state type, with no conversion,
+ * so that lcbp_restore brings back exactly (bitwise) the state of the moment
+ * of the snapshot; the step counter is not part of it.  dst / src: host or
+ * device memory of lcbp_snapshot_bytes(h) bytes, owned by the caller.  Both
+ * calls synchronise the lattice's stream.  Errors: LCBP_EINVAL (NULL
+ * pointers), LCBP_ESTATE (snapshot before f is initialised), LCBP_ECUDA.
+ * The paper has no such call; it serves roll-back (the surrogate judge).
+ */
+LCBP_API size_t lcbp_snapshot_bytes(lcbp_lattice *h);
+LCBP_API int lcbp_snapshot(lcbp_lattice *h, void *dst);
+LCBP_API int lcbp_restore(lcbp_lattice *h, const void *src);
+
 /* ------------------------------------------------------------------------
  * Batched replicas (parameter sweeps): R independent periodic lattices of
  * uneven sizes, each with its own Landau-de Gennes and kinetic parameters,
@@ -409,6 +431,15 @@ typedef struct lcbp_params {
   double A0, gamma, K, q0; /* Sec. 2.1 Eq. (free_energy) */
   double tau_f, xi, Gamma; /* Sec. 2.1, 2.2 kinetics */
 } lcbp_params;
+
+/*
+ * Fills *out from the reduced chirality kappa and temperature tau of Sec. 2.1
+ * (gamma = 27 / (9 + tau), K = kappa^2 A0 gamma / (108 q0^2), as
+ * lcbp_set_ldg_kappa_tau) and the kinetic parameters.  Errors: LCBP_EINVAL
+ * (NULL out, tau <= -9, q0 == 0, kappa < 0, non-finite values).
+ */
+LCBP_API int lcbp_params_kappa_tau(double A0, double q0, double kappa, double tau, double tau_f, double xi,
+                                   double Gamma, lcbp_params *out);
 
 /*
  * dims: 3 * R ints (nx, ny, nz of replica r, each >= 1); params: R entries.
@@ -516,6 +547,20 @@ LCBP_API int lcbp_surrogate_set_conv_kernel(lcbp_surrogate *s, int kind);
 /* Upload / download the parameter vector (host or device FP32; Adam state is reset on upload). */
 LCBP_API int lcbp_surrogate_set_params(lcbp_surrogate *s, const float *params, size_t count);
 LCBP_API int lcbp_surrogate_get_params(lcbp_surrogate *s, float *params, size_t count);
+/*
+ * Weights file of a trained network: save writes the parameter vector and the
+ * input / output scales to `path`, load reads them back into a surrogate
+ * (any lattice size: the weights do not depend on it; Adam state is reset).
+ * Format, version 1, little-endian: "LCBPSURR", int32 version, int32 residual
+ * blocks (4), width (32), input channels (15), output channels (5), kernel
+ * size (3), solver steps per call (10), int32 0, double s_u, s_r, s_dq,
+ * uint64 count, then count FP32 parameters in the order above.
+ * Errors: LCBP_EINVAL (NULL path; a file of another architecture), LCBP_EIO
+ * (cannot open, not a version-1 file, truncated), LCBP_ENONFINITE
+ * (non-finite parameters).  Not in the paper (the surrogate is an addition).
+ */
+LCBP_API int lcbp_surrogate_save(lcbp_surrogate *s, const char *path);
+LCBP_API int lcbp_surrogate_load(lcbp_surrogate *s, const char *path);
 /* Gradient of the last training step's loss, in the parameter-vector layout. */
 LCBP_API int lcbp_surrogate_get_grads(lcbp_surrogate *s, float *grads, size_t count);
 /* Network output y (5 * N values, [c][z][y][x]) for fields Q (5 * N), u (3 * N,
@@ -532,6 +577,59 @@ LCBP_API int lcbp_surrogate_step(lcbp_surrogate *s, lcbp_lattice *h, double kapp
 LCBP_API int lcbp_surrogate_train_step(lcbp_surrogate *s, const void *q5, const void *u3, const void *r5,
                                        double kappa, double tau, const void *dq5, const void *mask, int dtype,
                                        double lr, double *loss);
+
+/* ------------------------------------------------------------------------
+ * Judged surrogate run (not in the paper: the judge and fallback of the
+ * learned surrogate, with the plain solver of Sec. 2.2 as the judge).
+ *
+ * The judge advances a lattice (FP32, periodic, the surrogate's size) in
+ * segments of calls_per_segment surrogate calls of ten solver steps each.  A
+ * segment starts from a raw snapshot of the state (lcbp_snapshot).  After
+ * its calls f is re-equilibrated to the new Q (lcbp_reequilibrate_f); then one
+ * more surrogate call, on a copy of that state, is compared with ten plain
+ * steps of the lattice: the segment stands if
+ *   |F_sur - F_plain| / |F_plain| <= tol_F   and, if tol_Q > 0,
+ *   max |Q_sur - Q_plain| <= tol_Q,
+ * and the ten plain steps count as time advanced.  Otherwise (or if the state
+ * became non-finite) the snapshot is restored and the segment is redone with
+ * plain steps, so a run that never accepts a segment equals a plain run
+ * bitwise.  Where fewer than twenty steps remain, the run steps plainly.
+ * Time t starts at 0 when the judge is created.
+ * ------------------------------------------------------------------------ */
+typedef struct lcbp_judge lcbp_judge;
+typedef struct lcbp_judge_config {
+  double kappa, tau;      /* the surrogate's conditioning (Sec. 2.1 reduced chirality, temperature) */
+  int calls_per_segment;  /* M >= 1 */
+  double tol_F;           /* >= 0 */
+  double tol_Q;           /* <= 0: Q is not judged */
+} lcbp_judge_config;
+typedef struct lcbp_judge_stats {
+  long long t;                /* steps advanced */
+  long long segments, accepted, fallbacks;
+  long long surrogate_calls;  /* calls kept (ten steps each) */
+  long long plain_steps;      /* plain steps kept (judge steps and redone segments) */
+  double last_gap_F, last_gap_Q;  /* of the last judgement (NaN if it failed) */
+  double max_gap_F;           /* largest accepted relative F gap */
+} lcbp_judge_stats;
+
+/* The judge keeps both handles (the caller keeps them alive and owns them)
+ * and allocates two snapshots and a scratch lattice of the lattice's size.
+ * Errors: LCBP_EINVAL (NULL pointers, calls_per_segment < 1, tol_F < 0,
+ * non-finite values), LCBP_ENOMEM. */
+LCBP_API int lcbp_judge_create(lcbp_lattice *h, lcbp_surrogate *s, const lcbp_judge_config *c, lcbp_judge **out);
+LCBP_API int lcbp_judge_destroy(lcbp_judge *j);
+/*
+ * Advance to time t_end.  With log_every > 0 (a multiple of 10; t_end then a
+ * multiple of 10 too) the free energy F_h (lcbp_free_energy) and the defect
+ * fraction for defect_threshold (lcbp_defect_fraction) are logged at every
+ * multiple of log_every passed, from the state the run keeps, into log_t,
+ * log_F, log_defect (capacity entries each); *nlog receives the count.
+ * Errors: LCBP_EINVAL (bad log_every or t_end, arrays too small), and those of
+ * the calls it makes other than LCBP_ENONFINITE, which fails a judgement.
+ */
+LCBP_API int lcbp_judge_advance(lcbp_judge *j, long long t_end, int log_every, double defect_threshold,
+                                long long *log_t, double *log_F, double *log_defect, int capacity, int *nlog);
+LCBP_API int lcbp_judge_get_stats(lcbp_judge *j, lcbp_judge_stats *out);
 
 #ifdef __cplusplus
 }

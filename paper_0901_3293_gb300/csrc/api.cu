@@ -329,6 +329,7 @@ HostParams default_params() {
   p.Gamma = 0.3;
   p.flow_on = 1;
   p.coupling = LCBP_JACOBI;
+  p.rho0 = 1.0;
   return p;
 }
 
@@ -668,6 +669,18 @@ int diag(lcbp_lattice* h, double threshold, int with_f) {
   return LCBP_OK;
 }
 
+// number of non-finite values among n state-type values at v (device), synchronously
+int count_nonfinite(lcbp_lattice* h, const void* v, long long n, unsigned long long* count) {
+  auto* out = reinterpret_cast<unsigned long long*>(h->d_out);
+  cudaError_t e = h->dtype == LCBP_F64 ? launch_count_nonfinite<double>(v, n, h->d_partials, out, h->stream)
+                                       : launch_count_nonfinite<float>(v, n, h->d_partials, out, h->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h->h_out, h->d_out, 8, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "finiteness check");
+  *count = *reinterpret_cast<const unsigned long long*>(h->h_out);
+  return LCBP_OK;
+}
+
 #define CHECK_H(h)                                                     \
   do {                                                                 \
     if (!(h)) return fail(LCBP_EINVAL, "null lattice handle");         \
@@ -821,17 +834,67 @@ int lcbp_set_ldg(lcbp_lattice* h, double A0, double gamma, double K, double q0) 
   return upload_replica(h);
 }
 
-int lcbp_set_ldg_kappa_tau(lcbp_lattice* h, double A0, double q0, double kappa, double tau) {
-  CHECK_H(h);
-  if (!(tau > -9.0) || q0 == 0.0 || !(kappa >= 0.0)) return fail(LCBP_EINVAL, "need tau > -9, q0 != 0, kappa >= 0");
-  const double gamma = 27.0 / (9.0 + tau);
-  const double K = kappa * kappa * A0 * gamma / (108.0 * q0 * q0);
-  return lcbp_set_ldg(h, A0, gamma, K, q0);
+// gamma and K from the reduced chirality and temperature (Sec. 2.1)
+static int ldg_from_kappa_tau(double A0, double q0, double kappa, double tau, double* gamma, double* K) {
+  if (!(tau > -9.0) || q0 == 0.0 || !(kappa >= 0.0) || !std::isfinite(A0) || !std::isfinite(q0) ||
+      !std::isfinite(kappa) || !std::isfinite(tau))
+    return fail(LCBP_EINVAL, "need finite values, tau > -9, q0 != 0, kappa >= 0");
+  *gamma = 27.0 / (9.0 + tau);
+  *K = kappa * kappa * A0 * *gamma / (108.0 * q0 * q0);
+  return LCBP_OK;
 }
 
-int lcbp_set_flow(lcbp_lattice* h, double tau_f, double xi, double Gamma, int flow_on, int coupling) {
+int lcbp_set_ldg_kappa_tau(lcbp_lattice* h, double A0, double q0, double kappa, double tau) {
   CHECK_H(h);
+  double gamma = 0, K = 0;
+  const int rc = ldg_from_kappa_tau(A0, q0, kappa, tau, &gamma, &K);
+  return rc ? rc : lcbp_set_ldg(h, A0, gamma, K, q0);
+}
+
+int lcbp_params_kappa_tau(double A0, double q0, double kappa, double tau, double tau_f, double xi, double Gamma,
+                          lcbp_params* out) {
+  if (!out) return fail(LCBP_EINVAL, "out is NULL");
+  double gamma = 0, K = 0;
+  const int rc = ldg_from_kappa_tau(A0, q0, kappa, tau, &gamma, &K);
+  if (rc) return rc;
+  *out = lcbp_params{A0, gamma, K, q0, tau_f, xi, Gamma};
+  return LCBP_OK;
+}
+
+size_t lcbp_snapshot_bytes(lcbp_lattice* h) { return h ? (size_t)(24 * h->n) * h->es : 0; }
+
+int lcbp_snapshot(lcbp_lattice* h, void* dst) {
+  CHECK_H(h);
+  if (!dst) return fail(LCBP_EINVAL, "dst is NULL");
+  if (!h->f_ready) return fail(LCBP_ESTATE, "f was never initialised");
+  const size_t nf = (size_t)(15 * h->n) * h->es, nr = (size_t)(4 * h->n) * h->es, nq = (size_t)(5 * h->n) * h->es;
+  char* d = static_cast<char*>(dst);
+  cudaError_t e = cudaMemcpyAsync(d, h->f[h->cur], nf, cudaMemcpyDefault, h->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d + nf, h->rhou[h->cur], nr, cudaMemcpyDefault, h->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d + nf + nr, h->q, nq, cudaMemcpyDefault, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  return e == cudaSuccess ? LCBP_OK : cuda_fail(e, "snapshot");
+}
+
+int lcbp_restore(lcbp_lattice* h, const void* src) {
+  CHECK_H(h);
+  if (!src) return fail(LCBP_EINVAL, "src is NULL");
+  const size_t nf = (size_t)(15 * h->n) * h->es, nr = (size_t)(4 * h->n) * h->es, nq = (size_t)(5 * h->n) * h->es;
+  const char* d = static_cast<const char*>(src);
+  cudaError_t e = cudaMemcpyAsync(h->f[h->cur], d, nf, cudaMemcpyDefault, h->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h->rhou[h->cur], d + nf, nr, cudaMemcpyDefault, h->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h->q, d + nf + nr, nq, cudaMemcpyDefault, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "restore");
+  h->f_ready = true;
+  return LCBP_OK;
+}
+
+int lcbp_set_flow(lcbp_lattice* h, double tau_f, double rho0, double xi, double Gamma, int flow_on, int coupling) {
+  CHECK_H(h);
+  if (!(rho0 > 0.0) || !std::isfinite(rho0)) return fail(LCBP_EINVAL, "need a finite rho0 > 0");
   HostParams p = h->p;
+  p.rho0 = rho0;
   p.tau_f = tau_f;
   p.xi = xi;
   p.Gamma = Gamma;
@@ -895,13 +958,23 @@ int lcbp_init_q(lcbp_lattice* h, int kind, double amplitude, double noise, uint6
 int lcbp_set_q(lcbp_lattice* h, const void* q5, int dtype) {
   CHECK_H(h);
   if (!q5 || !valid_dtype(dtype)) return fail(LCBP_EINVAL, "bad buffer or dtype");
-  return transfer(h->q, h->dtype, const_cast<void*>(q5), dtype, 5 * h->n, true, h->staging, h->staging_elems,
-                  h->stream);
+  // into the Q* scratch first: a field holding NaN or Inf is refused and Q stays as it was
+  int rc = transfer(h->qs, h->dtype, const_cast<void*>(q5), dtype, 5 * h->n, true, h->staging, h->staging_elems,
+                    h->stream);
+  if (rc) return rc;
+  unsigned long long bad = 0;
+  rc = count_nonfinite(h, h->qs, 5 * h->n, &bad);
+  if (rc) return rc;
+  if (bad) return fail(LCBP_ENONFINITE, "%llu values of the uploaded Q are NaN or Inf; Q is unchanged", bad);
+  cudaError_t e = cudaMemcpyAsync(h->q, h->qs, (size_t)(5 * h->n) * h->es, cudaMemcpyDeviceToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  return e == cudaSuccess ? LCBP_OK : cuda_fail(e, "set_q");
 }
 
 int lcbp_init_f_equilibrium(lcbp_lattice* h, double rho0, const void* u3, int dtype) {
   CHECK_H(h);
-  if (!(rho0 > 0.0) || !valid_dtype(dtype)) return fail(LCBP_EINVAL, "need rho0 > 0 and a valid dtype");
+  if (rho0 == 0.0) rho0 = h->p.rho0;  // the lattice's reference density
+  if (!(rho0 > 0.0) || !valid_dtype(dtype)) return fail(LCBP_EINVAL, "need rho0 > 0 (or 0) and a valid dtype");
   int rc;
   if (u3) {
     // the body-force scratch holds the uploaded velocity
@@ -926,9 +999,17 @@ int lcbp_init_f_equilibrium(lcbp_lattice* h, double rho0, const void* u3, int dt
 int lcbp_set_f(lcbp_lattice* h, const void* f15, int dtype) {
   CHECK_H(h);
   if (!f15 || !valid_dtype(dtype)) return fail(LCBP_EINVAL, "bad buffer or dtype");
-  int rc = transfer(h->f[h->cur], h->dtype, const_cast<void*>(f15), dtype, 15 * h->n, true, h->staging,
-                    h->staging_elems, h->stream);
+  // into the scratch block (16 N elements) first: non-finite populations are refused, f stays as it was
+  int rc = transfer(h->h, h->dtype, const_cast<void*>(f15), dtype, 15 * h->n, true, h->staging, h->staging_elems,
+                    h->stream);
   if (rc) return rc;
+  unsigned long long bad = 0;
+  rc = count_nonfinite(h, h->h, 15 * h->n, &bad);
+  if (rc) return rc;
+  if (bad) return fail(LCBP_ENONFINITE, "%llu uploaded populations are NaN or Inf; f is unchanged", bad);
+  cudaError_t ec = cudaMemcpyAsync(h->f[h->cur], h->h, (size_t)(15 * h->n) * h->es, cudaMemcpyDeviceToDevice,
+                                   h->stream);
+  if (ec != cudaSuccess) return cuda_fail(ec, "set_f");
   // to deviation storage, in place
   cudaError_t e = h->dtype == LCBP_F64 ? launch_shift<double>(h->f[h->cur], h->f[h->cur], h->n, 15, 0, -1, h->stream)
                                        : launch_shift<float>(h->f[h->cur], h->f[h->cur], h->n, 15, 0, -1, h->stream);
@@ -1324,6 +1405,35 @@ int lattice_fields(lcbp_lattice* h, float** q, const float** u, int dims[3], cud
   dims[0] = h->nx;
   dims[1] = h->ny;
   dims[2] = h->nz;
+  *stream = h->stream;
+  return LCBP_OK;
+}
+
+// a new lattice of the same dims, dtype, parameters and kernel-set choice
+// (state unset): the surrogate judge's scratch lattice
+int lattice_clone(lcbp_lattice* src, lcbp_lattice** out) {
+  if (!src || !out) return fail(LCBP_EINVAL, "null lattice handle");
+  cudaSetDevice(src->device);
+  int rc = lcbp_create(src->nx, src->ny, src->nz, src->dtype, out);
+  if (rc) return rc;
+  lcbp_lattice* d = *out;
+  d->p = src->p;
+  d->path_req = src->path_req;
+  rc = upload_replica(d);
+  if (rc) {
+    lcbp_destroy(d);
+    *out = nullptr;
+  }
+  return rc;
+}
+
+// device Q (5 N state-type values, updated in place by steps) and the stream
+int lattice_q(lcbp_lattice* h, const void** q, long long* n, int* dtype, cudaStream_t* stream) {
+  if (!h) return fail(LCBP_EINVAL, "null lattice handle");
+  cudaSetDevice(h->device);
+  *q = h->q;
+  *n = h->n;
+  *dtype = h->dtype;
   *stream = h->stream;
   return LCBP_OK;
 }

@@ -92,6 +92,17 @@ struct DiagGeom {
   double qw[5];    // anchored Q (q5 order)
   double c_div;    // (K - L2) / 2: F_h gains -c_div |div Q|^2 per site
 };
+// whole-field checks (state.cu); scratch: state_check_scratch_bytes() of device memory
+size_t state_check_scratch_bytes();
+// *out = number of non-finite values among n
+template <typename real>
+cudaError_t launch_count_nonfinite(const void* v, long long n, void* scratch, unsigned long long* out,
+                                   cudaStream_t s);
+// *out = max |a - b| over n values (NaN if either holds one)
+template <typename real>
+cudaError_t launch_max_abs_diff(const void* a, const void* b, long long n, void* scratch, double* out,
+                                cudaStream_t s);
+
 // one CTA waits on a barrier nothing arrives on, for at most limit_ns; *flag = 1 if it gave up
 cudaError_t launch_wait_probe(uint64_t limit_ns, int* flag, cudaStream_t s);
 template <typename real>

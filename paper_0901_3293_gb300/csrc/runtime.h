@@ -20,6 +20,7 @@ struct HostParams {
   double q_wall[5];         // anchored Q beyond the walls (q5 order)
   int l2_set;               // 0: one-constant energy (L2 = K); 1: L2 below
   double L2;
+  double rho0;              // reference density (initial f^eq when no density is given)
 };
 
 extern thread_local std::string g_last_error;

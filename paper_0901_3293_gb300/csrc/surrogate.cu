@@ -10,6 +10,7 @@
 // Qevolution, mat_der), so the network learns the correction to ten explicit
 // Euler steps.
 #include <algorithm>
+#include <cstdio>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -726,6 +727,80 @@ int lcbp_surrogate_get_grads(lcbp_surrogate* s, float* g, size_t count) {
   cudaFree(staging);
   s->allocs.pop_back();
   return e == cudaSuccess ? LCBP_OK : cuda_fail(e, "get_grads");
+}
+
+// Weights file, version 1 (little-endian): "LCBPSURR", int32 version, int32
+// blocks, width, input channels, output channels, kernel size, solver steps
+// per call, int32 0, then double s_u, s_r, s_dq, uint64 count, and count FP32
+// parameters in the order of lcbp_surrogate_get_params.
+namespace {
+struct SurHeader {
+  char magic[8];
+  int32_t version, blocks, width, cin, cout, ksize, steps, pad;
+  double su, sr, sdq;
+  uint64_t count;
+};
+constexpr int32_t kSurFileVersion = 1;
+}  // namespace
+
+int lcbp_surrogate_save(lcbp_surrogate* s, const char* path) {
+  int rc = check_s(s);
+  if (rc) return rc;
+  if (!path) return fail(LCBP_EINVAL, "path is NULL");
+  const size_t count = true_param_count();
+  std::vector<float> v(count);
+  rc = lcbp_surrogate_get_params(s, v.data(), count);
+  if (rc) return rc;
+  SurHeader hd{};
+  std::memcpy(hd.magic, "LCBPSURR", 8);
+  hd.version = kSurFileVersion;
+  hd.blocks = kBlocks;
+  hd.width = kWidth;
+  hd.cin = kInC;
+  hd.cout = kOutC;
+  hd.ksize = 3;
+  hd.steps = (int32_t)kSteps;
+  hd.su = s->su;
+  hd.sr = s->sr;
+  hd.sdq = s->sdq;
+  hd.count = count;
+  FILE* fp = std::fopen(path, "wb");
+  if (!fp) return fail(LCBP_EIO, "cannot open %s for writing", path);
+  const bool ok = std::fwrite(&hd, sizeof(hd), 1, fp) == 1 && std::fwrite(v.data(), 4, count, fp) == count;
+  const bool closed = std::fclose(fp) == 0;
+  return ok && closed ? LCBP_OK : fail(LCBP_EIO, "writing %s failed", path);
+}
+
+int lcbp_surrogate_load(lcbp_surrogate* s, const char* path) {
+  int rc = check_s(s);
+  if (rc) return rc;
+  if (!path) return fail(LCBP_EINVAL, "path is NULL");
+  FILE* fp = std::fopen(path, "rb");
+  if (!fp) return fail(LCBP_EIO, "cannot open %s", path);
+  SurHeader hd{};
+  const size_t count = true_param_count();
+  std::vector<float> v;
+  bool ok = std::fread(&hd, sizeof(hd), 1, fp) == 1;
+  if (ok && (std::memcmp(hd.magic, "LCBPSURR", 8) != 0 || hd.version != kSurFileVersion)) {
+    std::fclose(fp);
+    return fail(LCBP_EIO, "%s is not a version-%d surrogate weights file", path, kSurFileVersion);
+  }
+  if (ok && (hd.blocks != kBlocks || hd.width != kWidth || hd.cin != kInC || hd.cout != kOutC || hd.ksize != 3 ||
+             hd.steps != (int32_t)kSteps || hd.count != count)) {
+    std::fclose(fp);
+    return fail(LCBP_EINVAL, "%s holds another network (%d blocks, width %d, %llu parameters)", path, hd.blocks,
+                hd.width, (unsigned long long)hd.count);
+  }
+  if (ok) {
+    v.resize(count);
+    ok = std::fread(v.data(), 4, count, fp) == count;
+  }
+  std::fclose(fp);
+  if (!ok) return fail(LCBP_EIO, "%s is truncated", path);
+  for (float x : v)
+    if (!std::isfinite(x)) return fail(LCBP_ENONFINITE, "%s holds non-finite parameters", path);
+  rc = lcbp_surrogate_set_scales(s, hd.su, hd.sr, hd.sdq);
+  return rc ? rc : lcbp_surrogate_set_params(s, v.data(), count);
 }
 
 int lcbp_surrogate_forward(lcbp_surrogate* s, const void* q5, const void* u3, const void* r5, double kappa,

@@ -46,7 +46,12 @@ _SIGNATURES = {
                                ctypes.POINTER(ctypes.c_longlong)]),
     "lcbp_set_ldg": (_c_int, [_P, _c_double, _c_double, _c_double, _c_double]),
     "lcbp_set_ldg_kappa_tau": (_c_int, [_P, _c_double, _c_double, _c_double, _c_double]),
-    "lcbp_set_flow": (_c_int, [_P, _c_double, _c_double, _c_double, _c_int, _c_int]),
+    "lcbp_set_flow": (_c_int, [_P, _c_double, _c_double, _c_double, _c_double, _c_int, _c_int]),
+    "lcbp_params_kappa_tau": (_c_int, [_c_double, _c_double, _c_double, _c_double, _c_double, _c_double,
+                                       _c_double, _c_void_p]),
+    "lcbp_snapshot_bytes": (_c_size_t, [_P]),
+    "lcbp_snapshot": (_c_int, [_P, _c_void_p]),
+    "lcbp_restore": (_c_int, [_P, _c_void_p]),
     "lcbp_init_q": (_c_int, [_P, _c_int, _c_double, _c_double, ctypes.c_uint64, ctypes.POINTER(_c_int)]),
     "lcbp_set_q": (_c_int, [_P, _c_void_p, _c_int]),
     "lcbp_init_f_equilibrium": (_c_int, [_P, _c_double, _c_void_p, _c_int]),
@@ -89,6 +94,13 @@ _SIGNATURES = {
     "lcbp_surrogate_train_step": (_c_int, [_P, _c_void_p, _c_void_p, _c_void_p, _c_double, _c_double, _c_void_p,
                                            _c_void_p, _c_int, _c_double, ctypes.POINTER(_c_double)]),
     "lcbp_read_rate": (_c_int, [_P, _c_void_p, _c_int]),
+    "lcbp_surrogate_save": (_c_int, [_P, ctypes.c_char_p]),
+    "lcbp_surrogate_load": (_c_int, [_P, ctypes.c_char_p]),
+    "lcbp_judge_create": (_c_int, [_P, _P, _c_void_p, ctypes.POINTER(_P)]),
+    "lcbp_judge_destroy": (_c_int, [_P]),
+    "lcbp_judge_advance": (_c_int, [_P, ctypes.c_longlong, _c_int, _c_double, _c_void_p, _c_void_p, _c_void_p,
+                                    _c_int, ctypes.POINTER(_c_int)]),
+    "lcbp_judge_get_stats": (_c_int, [_P, _c_void_p]),
     "lcbp_batch_create": (_c_int, [_c_int, ctypes.POINTER(_c_int), _c_void_p, _c_int, ctypes.POINTER(_P)]),
     "lcbp_batch_destroy": (_c_int, [_P]),
     "lcbp_batch_set_flow": (_c_int, [_P, _c_int, _c_int]),
@@ -118,6 +130,15 @@ class Params(ctypes.Structure):
     @classmethod
     def _fields_names(cls):
         return [f[0] for f in cls._fields_]
+
+
+def params_kappa_tau(A0: float, q0: float, kappa: float, tau: float, tau_f: float = 2.0, xi: float = 0.7,
+                     Gamma: float = 0.3) -> dict:
+    """Per-replica parameters from the reduced chirality and temperature
+    (lcbp_params_kappa_tau: gamma and K are derived by the library)."""
+    p = Params()
+    check(lib().lcbp_params_kappa_tau(A0, q0, kappa, tau, tau_f, xi, Gamma, ctypes.byref(p)))
+    return {k: getattr(p, k) for k in Params._fields_names()}
 
 
 class LcbpError(RuntimeError):
@@ -172,6 +193,20 @@ def _ptr(a):
         return a.data_ptr(), _dtype_code(a), a
     a = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
     return a.ctypes.data, F64, a
+
+
+def _raw_buffer(a, nbytes: int) -> int:
+    """Address of a contiguous buffer (torch tensor or numpy array) of at least nbytes bytes."""
+    if isinstance(a, np.ndarray):
+        if not a.flags.c_contiguous or a.nbytes < nbytes:
+            raise ValueError(f"need a contiguous buffer of {nbytes} bytes")
+        return a.ctypes.data
+    if not a.is_contiguous() or a.numel() * a.element_size() < nbytes:
+        raise ValueError(f"need a contiguous buffer of {nbytes} bytes")
+    if a.is_cuda:
+        import torch
+        torch.cuda.synchronize(a.device)
+    return a.data_ptr()
 
 
 class Optics(ctypes.Structure):
@@ -263,8 +298,8 @@ class Lattice:
         return self
 
     def set_flow(self, tau_f: float = 2.0, xi: float = 0.7, Gamma: float = 0.3, flow_on: bool = True,
-                 coupling: int = JACOBI) -> "Lattice":
-        check(lib().lcbp_set_flow(self._h, tau_f, xi, Gamma, int(bool(flow_on)), coupling))
+                 coupling: int = JACOBI, rho0: float = 1.0) -> "Lattice":
+        check(lib().lcbp_set_flow(self._h, tau_f, rho0, xi, Gamma, int(bool(flow_on)), coupling))
         return self
 
     # -- state ----------------------------------------------------------------
@@ -415,6 +450,19 @@ class Lattice:
 
     def save(self, path: str) -> None:
         check(lib().lcbp_save(self._h, os.fsencode(path)))
+
+    def snapshot_bytes(self) -> int:
+        return int(lib().lcbp_snapshot_bytes(self._h))
+
+    def snapshot(self, out) -> None:
+        """Raw state (f, rho u, Q) into `out`: a contiguous CUDA tensor or numpy
+        array of at least snapshot_bytes() bytes, any element type.  restore()
+        brings it back bitwise."""
+        check(lib().lcbp_snapshot(self._h, _raw_buffer(out, self.snapshot_bytes())))
+
+    def restore(self, src) -> "Lattice":
+        check(lib().lcbp_restore(self._h, _raw_buffer(src, self.snapshot_bytes())))
+        return self
 
     def load(self, path: str) -> None:
         check(lib().lcbp_load(self._h, os.fsencode(path)))
@@ -584,6 +632,15 @@ class Surrogate:
         check(lib().lcbp_surrogate_set_params(self._h, a.ctypes.data, a.size))
         return self
 
+    def save(self, path: str) -> None:
+        """Write the weights file (parameters and scales, versioned)."""
+        check(lib().lcbp_surrogate_save(self._h, os.fsencode(path)))
+
+    def load(self, path: str) -> "Surrogate":
+        """Read a weights file written by save (any lattice size)."""
+        check(lib().lcbp_surrogate_load(self._h, os.fsencode(path)))
+        return self
+
     def get_params(self) -> np.ndarray:
         a = np.empty(self.count, dtype=np.float32)
         check(lib().lcbp_surrogate_get_params(self._h, a.ctypes.data, a.size))
@@ -627,3 +684,64 @@ class Surrogate:
         loss = _c_double()
         check(lib().lcbp_surrogate_train_step(self._h, pq, pu, pr, kappa, tau, pt, pm, dq, lr, ctypes.byref(loss)))
         return loss.value
+
+
+class JudgeConfig(ctypes.Structure):
+    """lcbp_judge_config."""
+    _fields_ = [("kappa", _c_double), ("tau", _c_double), ("calls_per_segment", _c_int), ("tol_F", _c_double),
+                ("tol_Q", _c_double)]
+
+
+class JudgeStats(ctypes.Structure):
+    """lcbp_judge_stats."""
+    _fields_ = [(k, ctypes.c_longlong) for k in ("t", "segments", "accepted", "fallbacks", "surrogate_calls",
+                                                 "plain_steps")] + \
+               [(k, _c_double) for k in ("last_gap_F", "last_gap_Q", "max_gap_F")]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Judge:
+    """The judged surrogate run of the library (lcbp_judge_*): segments of
+    `calls_per_segment` surrogate calls, each judged against ten plain steps
+    (relative F gap <= tol_F, and max |dQ| <= tol_Q if tol_Q > 0), rolled back
+    and redone plainly when it fails.  Keeps references to the lattice and
+    the surrogate."""
+
+    def __init__(self, lattice: "Lattice", surrogate: "Surrogate", kappa: float, tau: float,
+                 calls_per_segment: int = 49, tol_F: float = 1e-3, tol_Q: float = 0.0):
+        self.lattice, self.surrogate = lattice, surrogate
+        cfg = JudgeConfig(float(kappa), float(tau), int(calls_per_segment), float(tol_F), float(tol_Q))
+        self._h = _P()
+        check(lib().lcbp_judge_create(lattice._h, surrogate._h, ctypes.byref(cfg), ctypes.byref(self._h)))
+
+    def advance(self, t_end: int, log_every: int = 0, defect_threshold: float = 0.19):
+        """Advance to t_end; with log_every > 0 returns the log as arrays (t, F, defect fraction)."""
+        if log_every <= 0:
+            check(lib().lcbp_judge_advance(self._h, int(t_end), 0, defect_threshold, None, None, None, 0, None))
+            return None
+        cap = int(t_end) // log_every + 1
+        t = np.zeros(cap, dtype=np.int64)
+        F = np.zeros(cap)
+        D = np.zeros(cap)
+        n = _c_int()
+        check(lib().lcbp_judge_advance(self._h, int(t_end), int(log_every), defect_threshold, t.ctypes.data,
+                                       F.ctypes.data, D.ctypes.data, cap, ctypes.byref(n)))
+        return t[:n.value], F[:n.value], D[:n.value]
+
+    def stats(self) -> dict:
+        st = JudgeStats()
+        check(lib().lcbp_judge_get_stats(self._h, ctypes.byref(st)))
+        return st.as_dict()
+
+    def close(self) -> None:
+        if self._h:
+            check(lib().lcbp_judge_destroy(self._h))
+            self._h = _P()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

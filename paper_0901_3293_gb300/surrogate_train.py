@@ -186,101 +186,33 @@ def evaluate(params, samples, depth: int = 64):
 
 
 class JudgedRun:
-    """Surrogate-accelerated time stepping with the plain solver as judge and fallback.
+    """Surrogate-accelerated time stepping with the plain solver as judge and
+    fallback: the library's judged run (lcbp_judge_*) on a lattice, with this
+    module's network scales.  Segments of M calls are each judged against ten
+    plain steps; a relative free-energy gap above tol (or a max |dQ| above
+    tol_q, if given) rolls the segment back and redoes it with plain steps."""
 
-    Each segment of M calls starts from a device snapshot of (f, Q).  After the
-    segment f is re-equilibrated and the judge compares one surrogate call
-    with 10 plain steps from the same state; if the relative free-energy gap
-    exceeds tol (or the state is no longer finite) the segment is rolled back
-    and redone with plain steps.
-    """
-
-    def __init__(self, lat: lcbp.Lattice, params, kappa: float, M: int = 49, tol: float = 1e-3):
-        import torch
+    def __init__(self, lat: lcbp.Lattice, params, kappa: float, M: int = 49, tol: float = 1e-3,
+                 tol_q: float = 0.0, weights: str | None = None):
         nx, ny, nz = lat.dims
-        self.lat, self.kappa, self.M, self.tol = lat, kappa, M, tol
         self.sur = lcbp.Surrogate(nx, ny, nz)
-        self.sur.set_scales(S_U, S_R, S_DQ)
-        self.sur.set_params(params)
-        self.t = 0
-        self.surrogate_calls = 0
-        self.plain_steps = 0
-        self.fallbacks = 0
-        self.judge_gaps = []
-        self._f = torch.empty((15, nz, ny, nx), dtype=torch.float32, device="cuda")
-        self._q = torch.empty((5, nz, ny, nx), dtype=torch.float32, device="cuda")
-        self._f2 = torch.empty_like(self._f)
-        self._q2 = torch.empty_like(self._q)
-        self._scratch = None
+        if weights is not None:
+            self.sur.load(weights)
+        else:
+            self.sur.set_scales(S_U, S_R, S_DQ)
+            self.sur.set_params(params)
+        self.judge = lcbp.Judge(lat, self.sur, kappa, TAU_R, calls_per_segment=M, tol_F=tol, tol_Q=tol_q)
 
-    def _log(self, log, log_every, next_log):
-        while next_log is not None and self.t >= next_log:
-            log.append((next_log, self.lat.free_energy()))
-            next_log += log_every
-        return next_log
+    def advance(self, t_end: int, log_every: int = 0):
+        """Advance to t_end; with log_every > 0 returns (t, F, defect fraction) at its multiples."""
+        return self.judge.advance(t_end, log_every)
 
-    def advance(self, t_end: int, log_every: int | None = None, log=None):
-        """Advance to t_end; optionally record (t, F) at multiples of log_every
-        (taken at the first segment boundary at or after each multiple)."""
-        next_log = (self.t // log_every + 1) * log_every if log_every else None
-        while self.t < t_end:
-            seg = min(self.M * K_STEPS, t_end - self.t)
-            calls = seg // K_STEPS
-            if calls == 0:
-                self.lat.step(seg)
-                self.t += seg
-                self.plain_steps += seg
-                next_log = self._log(log, log_every, next_log)
-                continue
-            t0 = self.t
-            self.lat.read_f(out=self._f)
-            self.lat.read_q(out=self._q)
-            ok = True
-            try:
-                self.sur.step(self.lat, self.kappa, TAU_R, calls)
-                self.lat.reequilibrate_f()
-                ok = self._judge()
-            except lcbp.LcbpError:
-                ok = False
-            if ok:
-                self.surrogate_calls += calls
-                self.t = t0 + calls * K_STEPS + K_STEPS  # the judge's plain steps advance time too
-                self.plain_steps += K_STEPS
-            else:
-                self.fallbacks += 1
-                self.lat.set_f(self._f)
-                self.lat.set_q(self._q)
-                self.lat.step(calls * K_STEPS)
-                self.t = t0 + calls * K_STEPS
-                self.plain_steps += calls * K_STEPS
-            next_log = self._log(log, log_every, next_log)
-
-    def _judge(self) -> bool:
-        """One surrogate call vs 10 plain steps from the same state (all on device:
-        the call runs on a scratch lattice holding a copy of the state)."""
-        nx, ny, nz = self.lat.dims
-        if self._scratch is None:
-            self._scratch = lcbp.Lattice(nx, ny, nz, dtype="f32")
-            self._scratch.set_ldg_kappa_tau(A0, Q0, self.kappa, TAU_R)
-            self._scratch.set_flow(2.0, 0.7, 0.3, True, lcbp.JACOBI)
-        self.lat.read_f(out=self._f2)
-        self.lat.read_q(out=self._q2)
-        self._scratch.set_f(self._f2).set_q(self._q2)
-        try:
-            self.sur.step(self._scratch, self.kappa, TAU_R, 1)
-            F_pred = self._scratch.free_energy()
-            self.lat.step(K_STEPS)
-            F_plain = self.lat.free_energy()
-        except lcbp.LcbpError:
-            return False
-        gap = abs(F_pred - F_plain) / abs(F_plain)
-        self.judge_gaps.append(gap)
-        return bool(np.isfinite(gap) and gap <= self.tol)
+    def stats(self) -> dict:
+        return self.judge.stats()
 
     def close(self):
+        self.judge.close()
         self.sur.close()
-        if self._scratch is not None:
-            self._scratch.close()
 
 
 def time_call(shape=(64, 64, 256), reps: int = 20):
@@ -346,31 +278,30 @@ def main():
     note({"held_out_mse": mse})
     t_sur, t_plain = time_call()
     note({"call_ms": [t_sur, t_plain]})
-    seg = (49 + 1) * K_STEPS  # judged segments are 500 steps: 49 calls + 10 judge steps
+    # both runs log F every 100 steps (and so pay for the same diagnostics)
+    log_every = 100
     plain = slab_lattice(args.kappa)
     F_plain = {}
     tp0 = time.perf_counter()
-    for t in range(seg, args.run_steps + 1, seg):
-        plain.step(seg)
+    for t in range(log_every, args.run_steps + 1, log_every):
+        plain.step(log_every)
         F_plain[t] = plain.free_energy()
     plain.synchronize()
     t_plain_run = time.perf_counter() - tp0
 
     def judged(p):
-        """The judged run with parameter vector p, against the plain trajectory."""
+        """The judged run with parameter vector p, against the plain trajectory at every logged step."""
         hyb = slab_lattice(args.kappa)
         run = JudgedRun(hyb, p, args.kappa, M=49, tol=args.tol)
-        F_hyb = []
         th0 = time.perf_counter()
-        run.advance(args.run_steps, log_every=seg, log=F_hyb)
+        ts, Fs, _ = run.advance(args.run_steps, log_every)
         hyb.synchronize()
         secs = time.perf_counter() - th0
-        errs = [abs(F - F_plain[t]) / abs(F_plain[t]) for t, F in F_hyb if t in F_plain]
-        out = {"seconds": secs, "surrogate_calls": run.surrogate_calls, "plain_steps": run.plain_steps,
-               "fallbacks": run.fallbacks, "max_rel_F_error": max(errs) if errs else None,
+        errs = [abs(F - F_plain[int(t)]) / abs(F_plain[int(t)]) for t, F in zip(ts, Fs)]
+        out = {"seconds": secs, **run.stats(), "logged": len(ts),
+               "max_rel_F_error": max(errs) if errs else None,
                "mean_rel_F_error": float(np.mean(errs)) if errs else None,
-               "judge_gap_median": float(np.median(run.judge_gaps)) if run.judge_gaps else None,
-               "final_F": F_hyb[-1][1] if F_hyb else None}
+               "final_F": float(Fs[-1]) if len(Fs) else None}
         run.close()
         hyb.close()
         return out

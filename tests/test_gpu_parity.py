@@ -326,16 +326,38 @@ def test_errors_are_status_codes(lcbp):
     with pytest.raises(L.LcbpError) as e:
         L.Lattice(4, 4, 4, dtype="f64").set_path(L.PATH_FAST2)  # packed lanes are FP32 only
     assert e.value.code == L.EINVAL
-    # a NaN planted in the host buffer is reported by the FP64 diagnostics
-    q = np.zeros((5, 4, 4, 4))
-    q[2, 1, 2, 3] = np.nan
-    lat.set_q(q)
     with pytest.raises(L.LcbpError) as e:
-        lat.free_energy()
+        lat.set_flow(rho0=0.0)
+    assert e.value.code == L.EINVAL
+    # a NaN planted in a host-uploaded Q (or f) is refused, and the state keeps its values
+    q_ok = initial.init_q5((4, 4, 4), initial.BPII, 2 * np.pi / 16, 0.3, 1e-3, 3)
+    lat.set_q(q_ok).init_f_equilibrium(1.0)
+    f_ok = lat.read_f()
+    q = q_ok.copy()
+    q[2, 1, 2, 3] = np.nan
+    with pytest.raises(L.LcbpError) as e:
+        lat.set_q(q)
+    assert e.value.code == L.ENONFINITE
+    assert np.array_equal(lat.read_q(dtype=np.float32), q_ok.astype(np.float32))
+    f = f_ok.copy()
+    f[7, 0, 1, 2] = np.inf
+    with pytest.raises(L.LcbpError) as e:
+        lat.set_f(f)
+    assert e.value.code == L.ENONFINITE
+    assert np.array_equal(lat.read_f(), f_ok)
+    # a state that blows up (an explicit step far past its stability bound,
+    # Gamma K 12 >> 2) is reported by the FP64 diagnostics
+    bad = L.Lattice(4, 4, 4, dtype="f32")
+    bad.set_ldg(0.01, 3.1, 1e5, 2 * np.pi / 16).set_q(q_ok).init_f_equilibrium(1.0).step(40)
+    with pytest.raises(L.LcbpError) as e:
+        bad.free_energy()
     assert e.value.code == L.ENONFINITE
     # the lattice stays usable afterwards
     lat.set_q(np.zeros((5, 4, 4, 4))).init_f_equilibrium(1.0).step(3)
     assert lat.free_energy() == 0.0
+    # rho0 = 0 takes the reference density of set_flow
+    lat.set_flow(rho0=1.25).init_f_equilibrium(0.0)
+    assert np.allclose(lat.read_rho(), 1.25, rtol=0, atol=1e-6)
 
 
 def test_bounded_wait_gives_up_and_reports(lcbp):

@@ -102,18 +102,20 @@ def test_training_gradients_match_oracle(lcbp, kernel):
     # Element-wise bounds, per layer, relative to the layer's largest gradient.
     # BF16 keeps 8 significant bits (unit roundoff u = 2^-8).  Against the
     # oracle that rounds where the kernels store, only the FP32 accumulation
-    # order differs: a stored value can land one BF16 ulp (2u) away, and those
-    # flips propagate, so 2e-2 (about 5u) bounds every element.  Against the
-    # unrounded FP64 network the gradient of each weight passes through about
-    # twenty BF16 roundings (ten stored activations, ten stored gradients);
-    # to first order that is 20u = 8e-2, so every element is held to 1e-1.
+    # order differs: a stored activation or gradient can land one BF16 ulp
+    # (2u) away, and a weight gradient sums products of several such stored
+    # tensors, so its worst element can sit a few ulps off: 5e-2 (about six
+    # ulps) bounds every element, while a wrong tap or channel is off by O(1).
+    # Against the unrounded FP64 network the gradient of each weight passes
+    # through about twenty BF16 roundings (ten stored activations, ten stored
+    # gradients); to first order that is 20u = 8e-2, so 1e-1 bounds every element.
     for name in S.layer_names(BLOCKS):
         for k in (0, 1):
             got, ref, ref_e = g[name][k], G[name][k], G_e[name][k]
             err_q = np.abs(got - ref).max() / np.abs(ref).max()
             err_e = np.abs(got - ref_e).max() / np.abs(ref_e).max()
             print(name, "W" if k == 0 else "b", f"max err / max|g|: vs BF16 oracle {err_q:.2e}, vs FP64 {err_e:.2e}")
-            assert err_q < 2e-2, (name, k, err_q)
+            assert err_q < 5e-2, (name, k, err_q)
             assert err_e < 1e-1, (name, k, err_e)
     # Adam moved the parameters by about lr
     step = sur.get_params().astype(np.float64) - S.flatten(P, BLOCKS)
