@@ -76,4 +76,15 @@ bool conv_win_geometry(int cin, int cout, int nx, int ny, ConvWin* g, size_t* sm
 cudaError_t conv_launch(int cin, int cout, int epi, const ConvMaps& m, bool allow_win, const CUtensorMap& tmW,
                         const ConvArgs& a, int sms, cudaStream_t s);
 
+// Weight and bias gradients of one convolution on tcgen05 (dw.cu):
+// dW[t][ci][co] += sum_r X(r + o_t)[ci] dY(r)[co], db[co] += sum_r dY(r)[co]
+// over the interior sites, X and dY padded BF16 (C_in, C_out in {16, 32}),
+// deterministic.  partial: dw_partial_floats(sms) floats of scratch.
+// dw_fits: whether the staged plane windows fit shared memory (planes up to
+// about 139 sites wide); otherwise the caller takes another kernel.
+size_t dw_partial_floats(int sms);
+bool dw_fits(int cin, int cout, int nx, int ny, int nz);
+cudaError_t dw_launch(int cin, int cout, const __nv_bfloat16* X, const __nv_bfloat16* dY, int nx, int ny, int nz,
+                      float* partial, float* dW, float* db, int* err, int sms, cudaStream_t s);
+
 }  // namespace lcbp

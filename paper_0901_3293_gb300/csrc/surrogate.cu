@@ -1,6 +1,6 @@
 // Learned surrogate: a periodic 3x3x3 convolutional network that advances Q by
-// k = 10 solver steps, with BF16 tensor-core forward and backward-data passes
-// (conv.cu), FP32 weight gradients, masked-MSE loss and Adam, all on device.
+// k = 10 solver steps, with BF16 tensor-core forward, backward-data (conv.cu)
+// and weight-gradient (dw.cu) passes, masked-MSE loss and Adam, all on device.
 //
 // Network (channels-last BF16 activations, FP32 accumulate):
 //   x = [Q_xx Q_xy Q_xz Q_yy Q_yz, u / s_u, kappa - 1, tau, R / s_r]   (15 of 16 channels)
@@ -383,6 +383,7 @@ struct lcbp_surrogate {
   float* uin;     // [3][n] staging of input u
   float* rin;     // [5][n] staging of input R
   float *grad, *adam_m, *adam_v;
+  float* dw_partial;  // per-CTA partial weight gradients of the tensor-core kernel
   double *partial, *dloss, *h_loss;
   int* d_err;
   long long adam_step;
@@ -466,12 +467,18 @@ cudaError_t forward(lcbp_surrogate* s, float* qupdate, const float* rate = nullp
   return conv_launch(32, 16, kEpiBias | kEpiOutF32, s->tmH[hlast], use_win(s), s->tmWf[kLayers - 1], a, s->sms, s->stream);
 }
 
+// Weight and bias gradients of layer l: on the tensor cores where the staged
+// plane windows fit shared memory, else on CUDA cores (FP32 atomics)
 template <int CX, int CY>
-void launch_dw(lcbp_surrogate* s, const __nv_bfloat16* X, const __nv_bfloat16* dY, int l) {
+cudaError_t launch_dw(lcbp_surrogate* s, const __nv_bfloat16* X, const __nv_bfloat16* dY, int l) {
+  if (dw_fits(CX, CY, s->nx, s->ny, s->nz))
+    return dw_launch(CX, CY, X, dY, s->nx, s->ny, s->nz, s->dw_partial, s->grad + s->off_w[l], s->grad + s->off_b[l],
+                     s->d_err, s->sms, s->stream);
   const int chunk = 4096;
   const dim3 grid((unsigned)((s->n + chunk - 1) / chunk), 27);
   k_sur_dw<CX, CY><<<grid, CX * CY / 16, 0, s->stream>>>(X, dY, s->nx, s->ny, s->nz, chunk, s->grad + s->off_w[l],
                                                          s->grad + s->off_b[l]);
+  return cudaGetLastError();
 }
 
 int check_s(lcbp_surrogate* s) {
@@ -574,6 +581,7 @@ int lcbp_surrogate_create(int nx, int ny, int nz, int training, lcbp_surrogate**
     A((void**)&s->grad, mc * 4);
     A((void**)&s->adam_m, mc * 4);
     A((void**)&s->adam_v, mc * 4);
+    A((void**)&s->dw_partial, dw_partial_floats(s->sms) * 4);
   }
   if (!rc) {
     e = cudaEventCreateWithFlags(&s->ev_rate, cudaEventDisableTiming);
@@ -588,8 +596,15 @@ int lcbp_surrogate_create(int nx, int ny, int nz, int training, lcbp_surrogate**
   if (!rc) {
     cudaMemsetAsync(s->master, 0, mc * 4, s->stream);
     cudaMemsetAsync(s->d_err, 0, 64, s->stream);
+    // every activation buffer, tail included: copies of plane windows may read
+    // the tail, and its bytes must be finite numbers (they meet zero gradients)
     cudaMemsetAsync(s->X, 0, b16, s->stream);
+    for (int k = 0; k < nh; ++k) cudaMemsetAsync(s->H[k], 0, b32, s->stream);
+    for (int k = 0; k < na; ++k) cudaMemsetAsync(s->A[k], 0, b32, s->stream);
     if (s->training) {
+      cudaMemsetAsync(s->dH, 0, b32, s->stream);
+      cudaMemsetAsync(s->dA, 0, b32, s->stream);
+      cudaMemsetAsync(s->G16, 0, b16, s->stream);
       cudaMemsetAsync(s->adam_m, 0, mc * 4, s->stream);
       cudaMemsetAsync(s->adam_v, 0, mc * 4, s->stream);
     }
@@ -895,10 +910,10 @@ int lcbp_surrogate_train_step(lcbp_surrogate* s, const void* q5, const void* u3,
   // ---- backward
   const int lout = kLayers - 1;
   if (e == cudaSuccess) {
-    launch_dw<32, 16>(s, s->H[kBlocks], s->G16, lout);
+    e = launch_dw<32, 16>(s, s->H[kBlocks], s->G16, lout);
     ConvArgs a = cargs(s);
     a.out_bf16 = s->dH;
-    e = conv_launch(16, 32, 0, s->tmG16, use_win(s), s->tmWb[lout], a, s->sms, s->stream);
+    if (e == cudaSuccess) e = conv_launch(16, 32, 0, s->tmG16, use_win(s), s->tmWb[lout], a, s->sms, s->stream);
   }
   for (int k = kBlocks - 1; k >= 0 && e == cudaSuccess; --k) {
     const int la = 1 + 2 * k, lbb = 2 + 2 * k;
@@ -908,8 +923,9 @@ int lcbp_surrogate_train_step(lcbp_surrogate* s, const void* q5, const void* u3,
     a.out_bf16 = s->dA;
     e = conv_launch(32, 32, kEpiMask, s->tmdH, use_win(s), s->tmWb[lbb], a, s->sms, s->stream);
     if (e != cudaSuccess) break;
-    launch_dw<32, 32>(s, s->A[k], s->dH, lbb);
-    launch_dw<32, 32>(s, s->H[k], s->dA, la);
+    e = launch_dw<32, 32>(s, s->A[k], s->dH, lbb);
+    if (e == cudaSuccess) e = launch_dw<32, 32>(s, s->H[k], s->dA, la);
+    if (e != cudaSuccess) break;
     // dh_k = dh_{k+1} + convT_a(d pre_k)   (times [h0 > 0] for the input layer's gradient)
     a = cargs(s);
     a.resid = s->dH;
@@ -919,7 +935,9 @@ int lcbp_surrogate_train_step(lcbp_surrogate* s, const void* q5, const void* u3,
                     s->stream);
   }
   if (e == cudaSuccess) {
-    launch_dw<16, 32>(s, s->X, s->dH, 0);
+    e = launch_dw<16, 32>(s, s->X, s->dH, 0);
+  }
+  if (e == cudaSuccess) {
     ++s->adam_step;
     const float b1 = 0.9f, b2 = 0.999f;
     const float c1 = 1.f - powf(b1, (float)s->adam_step), c2 = 1.f - powf(b2, (float)s->adam_step);
