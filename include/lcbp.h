@@ -510,14 +510,15 @@ LCBP_API int lcbp_free_energy_noalloc(const void *q5, int dtype, int nx, int ny,
 
 /* ------------------------------------------------------------------------
  * Learned surrogate (not part of the paper's method): a periodic 3x3x3
- * convolutional network that advances Q by k = 10 solver steps as a learned
- * correction to ten explicit Euler steps of the Beris-Edwards rate R:
+ * convolutional network that advances Q by k solver steps (k = 10 unless
+ * set) as a learned correction to k explicit Euler steps of the
+ * Beris-Edwards rate R:
  *   x = [Q (5), u / s_u (3), kappa - 1, tau, R / s_r (5)]  ->  h0 = relu(conv x),
  *   4 x { a = relu(conv h);  h = h + conv a },  y = conv h (5 channels),
- *   Q(t + 10) = Q(t) + 10 R(t) + s_dq * y,
+ *   Q(t + k) = Q(t) + k R(t) + s_dq * y,
  * with 32 hidden channels, BF16 weights and activations and FP32
- * accumulation on tcgen05 tensor cores (forward and backward-data), FP32
- * weight gradients, masked MSE loss and Adam.  A surrogate object is built
+ * accumulation on tcgen05 tensor cores (forward, backward-data and weight
+ * gradients), masked MSE loss and Adam.  A surrogate object is built
  * for one lattice size.  Parameters cross the boundary as one FP32 vector:
  * for each layer in the order in, b0a, b0b, ..., b3a, b3b, out the weights
  * W[t][c_in][c_out] (t = 9 (dz+1) + 3 (dy+1) + (dx+1), tap offset (dx, dy, dz),
@@ -553,7 +554,7 @@ LCBP_API int lcbp_surrogate_get_params(lcbp_surrogate *s, float *params, size_t 
  * (any lattice size: the weights do not depend on it; Adam state is reset).
  * Format, version 1, little-endian: "LCBPSURR", int32 version, int32 residual
  * blocks (4), width (32), input channels (15), output channels (5), kernel
- * size (3), solver steps per call (10), int32 0, double s_u, s_r, s_dq,
+ * size (3), solver steps per call k, int32 0, double s_u, s_r, s_dq,
  * uint64 count, then count FP32 parameters in the order above.
  * Errors: LCBP_EINVAL (NULL path; a file of another architecture), LCBP_EIO
  * (cannot open, not a version-1 file, truncated), LCBP_ENONFINITE
@@ -567,12 +568,16 @@ LCBP_API int lcbp_surrogate_get_grads(lcbp_surrogate *s, float *grads, size_t co
  * NULL = 0) and rate R (5 * N, NULL = 0) in the same dtype. */
 LCBP_API int lcbp_surrogate_forward(lcbp_surrogate *s, const void *q5, const void *u3, const void *r5, double kappa,
                                     double tau, int dtype, float *y5);
+/* Solver steps k that one call stands for (1..1000; default 10).  Set it
+ * before training: the network learns the correction to k Euler steps. */
+LCBP_API int lcbp_surrogate_set_steps(lcbp_surrogate *s, int k);
+LCBP_API int lcbp_surrogate_get_steps(lcbp_surrogate *s, int *k);
 /* ncalls times: R = R(Q, u) of the lattice (FP32 state, same size), then
- * Q += 10 R + s_dq * net(Q, u, kappa, tau, R).  u is not advanced and f is left
+ * Q += k R + s_dq * net(Q, u, kappa, tau, R).  u is not advanced and f is left
  * as it was: call lcbp_reequilibrate_f before plain stepping resumes. */
 LCBP_API int lcbp_surrogate_step(lcbp_surrogate *s, lcbp_lattice *h, double kappa, double tau, int ncalls);
 /* One Adam step (learning rate lr) on the masked MSE between y and
- * (dq5 - 10 R) / s_dq (dq5: the true 10-step change of Q, 5 * N values; mask:
+ * (dq5 - k R) / s_dq (dq5: the true k-step change of Q, 5 * N values; mask:
  * N values or NULL); *loss receives the loss. */
 LCBP_API int lcbp_surrogate_train_step(lcbp_surrogate *s, const void *q5, const void *u3, const void *r5,
                                        double kappa, double tau, const void *dq5, const void *mask, int dtype,
@@ -583,17 +588,19 @@ LCBP_API int lcbp_surrogate_train_step(lcbp_surrogate *s, const void *q5, const 
  * learned surrogate, with the plain solver of Sec. 2.2 as the judge).
  *
  * The judge advances a lattice (FP32, periodic, the surrogate's size) in
- * segments of calls_per_segment surrogate calls of ten solver steps each.  A
+ * segments of calls_per_segment surrogate calls of k solver steps each (k of
+ * the surrogate, lcbp_surrogate_set_steps, fixed when the judge is made).  A
  * segment starts from a raw snapshot of the state (lcbp_snapshot).  After
  * its calls f is re-equilibrated to the new Q (lcbp_reequilibrate_f); then one
- * more surrogate call, on a copy of that state, is compared with ten plain
+ * more surrogate call, on a copy of that state, is compared with k plain
  * steps of the lattice: the segment stands if
  *   |F_sur - F_plain| / |F_plain| <= tol_F   and, if tol_Q > 0,
  *   max |Q_sur - Q_plain| <= tol_Q,
- * and the ten plain steps count as time advanced.  Otherwise (or if the state
+ * and the k plain steps count as time advanced.  Otherwise (or if the state
  * became non-finite) the snapshot is restored and the segment is redone with
  * plain steps, so a run that never accepts a segment equals a plain run
- * bitwise.  Where fewer than twenty steps remain, the run steps plainly.
+ * bitwise.  The first warmup_steps of the run, and the end where fewer than
+ * 2k steps remain, are stepped plainly.
  * Time t starts at 0 when the judge is created.
  * ------------------------------------------------------------------------ */
 typedef struct lcbp_judge lcbp_judge;
@@ -602,6 +609,7 @@ typedef struct lcbp_judge_config {
   int calls_per_segment;  /* M >= 1 */
   double tol_F;           /* >= 0 */
   double tol_Q;           /* <= 0: Q is not judged */
+  long long warmup_steps; /* plain steps before the first segment (the fast initial relaxation) */
 } lcbp_judge_config;
 typedef struct lcbp_judge_stats {
   long long t;                /* steps advanced */
@@ -610,6 +618,8 @@ typedef struct lcbp_judge_stats {
   long long plain_steps;      /* plain steps kept (judge steps and redone segments) */
   double last_gap_F, last_gap_Q;  /* of the last judgement (NaN if it failed) */
   double max_gap_F;           /* largest accepted relative F gap */
+  double mean_gap_F, mean_gap_Q;  /* over the judgements with finite gaps */
+  long long judged;           /* judgements with finite gaps */
 } lcbp_judge_stats;
 
 /* The judge keeps both handles (the caller keeps them alive and owns them)
@@ -619,8 +629,8 @@ typedef struct lcbp_judge_stats {
 LCBP_API int lcbp_judge_create(lcbp_lattice *h, lcbp_surrogate *s, const lcbp_judge_config *c, lcbp_judge **out);
 LCBP_API int lcbp_judge_destroy(lcbp_judge *j);
 /*
- * Advance to time t_end.  With log_every > 0 (a multiple of 10; t_end then a
- * multiple of 10 too) the free energy F_h (lcbp_free_energy) and the defect
+ * Advance to time t_end.  With log_every > 0 (a multiple of k; t_end then a
+ * multiple of k too) the free energy F_h (lcbp_free_energy) and the defect
  * fraction for defect_threshold (lcbp_defect_fraction) are logged at every
  * multiple of log_every passed, from the state the run keeps, into log_t,
  * log_F, log_defect (capacity entries each); *nlog receives the count.

@@ -1,12 +1,12 @@
 // Judged surrogate run: the learned surrogate advances a lattice, and the
 // plain solver judges it and takes over where it fails.
 //
-// The lattice advances in segments of M surrogate calls (ten solver steps
-// each).  A segment starts from a raw device snapshot of (f, rho u, Q).  After
+// The lattice advances in segments of M surrogate calls (k solver steps
+// each, k of the surrogate).  A segment starts from a raw device snapshot of (f, rho u, Q).  After
 // its calls f is re-equilibrated to the new Q, and the judge compares one more
-// surrogate call with ten plain steps from that same state: the relative gap
+// surrogate call with k plain steps from that same state: the relative gap
 // of the free energy F_h (and, if asked, the largest |Delta Q|).  Within the
-// tolerances the segment stands and the ten plain steps count as time
+// tolerances the segment stands and the k plain steps count as time
 // advanced; otherwise the snapshot is restored and the segment is redone with
 // plain steps.  Free energy and defect fraction are logged at every multiple
 // of a log interval, from the state the run actually keeps (a rolled-back
@@ -29,11 +29,9 @@ int lattice_q(lcbp_lattice* h, const void** q, long long* n, int* dtype, cudaStr
 
 using namespace lcbp;
 
-namespace {
-constexpr long long kStepsPerCall = 10;  // solver steps one lcbp_surrogate_step call stands for
-}
 
 struct lcbp_judge {
+  long long k;  // solver steps one surrogate call stands for
   lcbp_lattice* lat;
   lcbp_surrogate* sur;
   lcbp_judge_config c;
@@ -130,12 +128,12 @@ int segment(lcbp_judge* j, long long t, int calls, int log_every, double thr, bo
   bool ok = true;
   int done = 0;
   while (ok && done < calls) {
-    const long long tt = t + done * kStepsPerCall;
+    const long long tt = t + done * j->k;
     int n = calls - done;
-    if (log_every > 0) n = (int)std::min<long long>(n, ((tt / log_every + 1) * log_every - tt) / kStepsPerCall);
+    if (log_every > 0) n = (int)std::min<long long>(n, ((tt / log_every + 1) * log_every - tt) / j->k);
     ok = soft(lcbp_surrogate_step(j->sur, j->lat, j->c.kappa, j->c.tau, n));
     done += n;
-    const long long te = t + done * kStepsPerCall;
+    const long long te = t + done * j->k;
     if (ok && log_every > 0 && te % log_every == 0) {
       double F = 0, D = 0;
       ok = soft(measure(j, thr, &F, &D));
@@ -150,7 +148,7 @@ int segment(lcbp_judge* j, long long t, int calls, int log_every, double thr, bo
   ok = ok && soft(lcbp_snapshot(j->lat, j->snap2)) && soft(lcbp_restore(j->scratch, j->snap2));
   ok = ok && soft(lcbp_surrogate_step(j->sur, j->scratch, j->c.kappa, j->c.tau, 1));
   ok = ok && soft(lcbp_free_energy(j->scratch, &Fs));
-  ok = ok && soft(lcbp_step(j->lat, (int)kStepsPerCall)) && soft(lcbp_free_energy(j->lat, &Fp));
+  ok = ok && soft(lcbp_step(j->lat, (int)j->k)) && soft(lcbp_free_energy(j->lat, &Fp));
   if (ok) {
     gF = std::fabs(Fs - Fp) / std::fabs(Fp);
     ok = soft(q_gap(j, &gQ));
@@ -159,15 +157,20 @@ int segment(lcbp_judge* j, long long t, int calls, int log_every, double thr, bo
   j->st.segments += 1;
   j->st.last_gap_F = gF;
   j->st.last_gap_Q = gQ;
+  if (std::isfinite(gF) && std::isfinite(gQ)) {
+    j->st.judged += 1;
+    j->st.mean_gap_F += (gF - j->st.mean_gap_F) / (double)j->st.judged;
+    j->st.mean_gap_Q += (gQ - j->st.mean_gap_Q) / (double)j->st.judged;
+  }
   const bool pass = ok && std::isfinite(gF) && gF <= j->c.tol_F &&
                     (j->c.tol_Q <= 0.0 || (std::isfinite(gQ) && gQ <= j->c.tol_Q));
-  const long long seg = calls * kStepsPerCall;
+  const long long seg = calls * j->k;
   if (pass) {
     j->st.accepted += 1;
     j->st.surrogate_calls += calls;
-    j->st.plain_steps += kStepsPerCall;
+    j->st.plain_steps += j->k;
     if (gF > j->st.max_gap_F) j->st.max_gap_F = gF;
-    const long long te = t + seg + kStepsPerCall;
+    const long long te = t + seg + j->k;
     if (log_every > 0 && te % log_every == 0) {
       double F = 0, D = 0;
       rc = measure(j, thr, &F, &D);
@@ -199,9 +202,14 @@ int lcbp_judge_create(lcbp_lattice* h, lcbp_surrogate* s, const lcbp_judge_confi
   *out = nullptr;
   if (!h || !s || !c) return fail(LCBP_EINVAL, "lattice, surrogate and config must not be NULL");
   if (c->calls_per_segment < 1) return fail(LCBP_EINVAL, "calls_per_segment must be >= 1");
-  if (!std::isfinite(c->kappa) || !std::isfinite(c->tau) || !(c->tol_F >= 0.0) || !std::isfinite(c->tol_Q))
-    return fail(LCBP_EINVAL, "need finite kappa, tau, tol_Q and tol_F >= 0");
+  if (!std::isfinite(c->kappa) || !std::isfinite(c->tau) || !(c->tol_F >= 0.0) || !std::isfinite(c->tol_Q) ||
+      c->warmup_steps < 0)
+    return fail(LCBP_EINVAL, "need finite kappa, tau, tol_Q, tol_F >= 0 and warmup_steps >= 0");
+  int k = 0;
+  int rc0 = lcbp_surrogate_get_steps(s, &k);
+  if (rc0) return rc0;
   auto* j = new lcbp_judge();
+  j->k = k;
   j->lat = h;
   j->sur = s;
   j->c = *c;
@@ -240,13 +248,13 @@ int lcbp_judge_advance(lcbp_judge* j, long long t_end, int log_every, double def
                        double* log_F, double* log_defect, int capacity, int* nlog) {
   if (!j) return fail(LCBP_EINVAL, "null judge handle");
   if (nlog) *nlog = 0;
-  if (log_every < 0 || log_every % kStepsPerCall != 0)
-    return fail(LCBP_EINVAL, "log_every must be a multiple of %lld (or 0)", kStepsPerCall);
+  if (log_every < 0 || log_every % j->k != 0)
+    return fail(LCBP_EINVAL, "log_every must be a multiple of %lld (or 0)", j->k);
   long long t = j->st.t;
   if (t_end < t) return fail(LCBP_EINVAL, "t_end %lld is before the run's time %lld", t_end, t);
   if (log_every > 0) {
-    if (t_end % kStepsPerCall != 0)
-      return fail(LCBP_EINVAL, "with logging, t_end must be a multiple of %lld", kStepsPerCall);
+    if (t_end % j->k != 0)
+      return fail(LCBP_EINVAL, "with logging, t_end must be a multiple of %lld", j->k);
     if (!log_t || !log_F || !log_defect || !nlog) return fail(LCBP_EINVAL, "log arrays and nlog must not be NULL");
     const long long marks = t_end / log_every - t / log_every;
     if (marks > capacity) return fail(LCBP_EINVAL, "%lld log entries do not fit capacity %d", marks, capacity);
@@ -262,11 +270,18 @@ int lcbp_judge_advance(lcbp_judge* j, long long t_end, int log_every, double def
     if (nlog) *nlog = written;
   };
   while (t < t_end) {
-    // a segment that stands also takes the judge's ten plain steps: it must fit before t_end
-    const int calls = (int)std::min<long long>(j->c.calls_per_segment, (t_end - t) / kStepsPerCall - 1);
+    // a segment that stands also takes the judge's k plain steps: it must fit before t_end
+    const int calls = (int)std::min<long long>(j->c.calls_per_segment, (t_end - t) / j->k - 1);
     int rc;
     long long adv;
-    if (calls < 1) {  // fewer than twenty steps left: plain
+    if (t < j->c.warmup_steps) {  // the plain warm-up (to a multiple of k, so segments stay aligned)
+      j->pt.clear();
+      j->pF.clear();
+      j->pD.clear();
+      const long long w = (j->c.warmup_steps + j->k - 1) / j->k * j->k;
+      adv = std::min(w, t_end) - t;
+      rc = plain(j, t, adv, log_every, defect_threshold, j->pt, j->pF, j->pD);
+    } else if (calls < 1) {  // fewer than 2k steps left: plain
       j->pt.clear();
       j->pF.clear();
       j->pD.clear();
@@ -275,7 +290,7 @@ int lcbp_judge_advance(lcbp_judge* j, long long t_end, int log_every, double def
     } else {
       bool accepted = false;
       rc = segment(j, t, calls, log_every, defect_threshold, &accepted);
-      adv = calls * kStepsPerCall + (accepted ? kStepsPerCall : 0);
+      adv = calls * j->k + (accepted ? j->k : 0);
     }
     if (rc) return rc;
     commit();

@@ -38,7 +38,7 @@ constexpr int kBlocks = 4;
 constexpr int kLayers = 2 + 2 * kBlocks;
 constexpr int kWidth = 32;
 constexpr int kInC = 15, kOutC = 5, kPadC = 16;
-constexpr float kSteps = 10.f;  // solver steps per call
+constexpr int kDefaultSteps = 10;  // solver steps per call unless set otherwise
 
 struct LayerDim {
   int cin, cout;          // true channels
@@ -114,7 +114,7 @@ __global__ void k_sur_input(const float* __restrict__ q, const float* __restrict
 // masked MSE on y (FP32 [n][16], first 5 channels) against (dq - 10 R) / s_dq
 // (FP32 [5][n]); writes the BF16 padded (chunk-planar) gradient d loss / d y and per-block partial sums
 __global__ void k_sur_loss(const float* __restrict__ y, const float* __restrict__ target,
-                           const float* __restrict__ rate, const float* __restrict__ mask, float inv_sdq,
+                           const float* __restrict__ rate, float ksteps, const float* __restrict__ mask, float inv_sdq,
                            double inv_den, int nx, int ny, int nz, __nv_bfloat16* __restrict__ grad,
                            double* __restrict__ partial) {
   const long long n = (long long)nx * ny * nz;
@@ -132,7 +132,7 @@ __global__ void k_sur_loss(const float* __restrict__ y, const float* __restrict_
     for (int c = 0; c < 16; ++c) g[c] = 0.f;
 #pragma unroll
     for (int c = 0; c < 5; ++c) {
-      const float tc = target[c * n + s] - (rate ? kSteps * rate[c * n + s] : 0.f);
+      const float tc = target[c * n + s] - (rate ? ksteps * rate[c * n + s] : 0.f);
       const float d = y[s * 16 + c] - tc * inv_sdq;
       g[c] = (float)(2.0 * w * d * inv_den);
       if (interior) acc += (double)w * d * d;
@@ -364,6 +364,7 @@ struct lcbp_surrogate {
   int device;
   cudaStream_t stream;
   float su, sr, sdq;
+  int ksteps;  // solver steps one call stands for
   int sms;
   int conv_kernel;  // LCBP_CONV_*
   // parameters: FP32 master (padded) per layer, BF16 forward / backward copies
@@ -459,7 +460,7 @@ cudaError_t forward(lcbp_surrogate* s, float* qupdate, const float* rate = nullp
     a.qstate = qupdate;
     a.qscale = s->sdq;
     a.rate = rate;
-    a.rate_scale = kSteps;
+    a.rate_scale = (float)s->ksteps;
     return conv_launch(32, 16, kEpiBias | kEpiUpdateQ, s->tmH[hlast], use_win(s), s->tmWf[kLayers - 1], a, s->sms,
                        s->stream);
   }
@@ -532,6 +533,7 @@ int lcbp_surrogate_create(int nx, int ny, int nz, int training, lcbp_surrogate**
   s->su = 1e-3f;
   s->sr = 1e-3f;
   s->sdq = 1e-3f;
+  s->ksteps = kDefaultSteps;
   cudaGetDevice(&s->device);
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
@@ -658,6 +660,22 @@ int lcbp_surrogate_set_scales(lcbp_surrogate* s, double s_u, double s_r, double 
   return LCBP_OK;
 }
 
+int lcbp_surrogate_set_steps(lcbp_surrogate* s, int k) {
+  int rc = check_s(s);
+  if (rc) return rc;
+  if (k < 1 || k > 1000) return fail(LCBP_EINVAL, "steps per call must be in 1..1000, got %d", k);
+  s->ksteps = k;
+  return LCBP_OK;
+}
+
+int lcbp_surrogate_get_steps(lcbp_surrogate* s, int* k) {
+  int rc = check_s(s);
+  if (rc) return rc;
+  if (!k) return fail(LCBP_EINVAL, "k is NULL");
+  *k = s->ksteps;
+  return LCBP_OK;
+}
+
 int lcbp_surrogate_set_conv_kernel(lcbp_surrogate* s, int kind) {
   int rc = check_s(s);
   if (rc) return rc;
@@ -774,7 +792,7 @@ int lcbp_surrogate_save(lcbp_surrogate* s, const char* path) {
   hd.cin = kInC;
   hd.cout = kOutC;
   hd.ksize = 3;
-  hd.steps = (int32_t)kSteps;
+  hd.steps = s->ksteps;
   hd.su = s->su;
   hd.sr = s->sr;
   hd.sdq = s->sdq;
@@ -801,7 +819,7 @@ int lcbp_surrogate_load(lcbp_surrogate* s, const char* path) {
     return fail(LCBP_EIO, "%s is not a version-%d surrogate weights file", path, kSurFileVersion);
   }
   if (ok && (hd.blocks != kBlocks || hd.width != kWidth || hd.cin != kInC || hd.cout != kOutC || hd.ksize != 3 ||
-             hd.steps != (int32_t)kSteps || hd.count != count)) {
+             hd.steps < 1 || hd.count != count)) {
     std::fclose(fp);
     return fail(LCBP_EINVAL, "%s holds another network (%d blocks, width %d, %llu parameters)", path, hd.blocks,
                 hd.width, (unsigned long long)hd.count);
@@ -815,6 +833,7 @@ int lcbp_surrogate_load(lcbp_surrogate* s, const char* path) {
   for (float x : v)
     if (!std::isfinite(x)) return fail(LCBP_ENONFINITE, "%s holds non-finite parameters", path);
   rc = lcbp_surrogate_set_scales(s, hd.su, hd.sr, hd.sdq);
+  if (!rc) rc = lcbp_surrogate_set_steps(s, hd.steps);
   return rc ? rc : lcbp_surrogate_set_params(s, v.data(), count);
 }
 
@@ -901,7 +920,8 @@ int lcbp_surrogate_train_step(lcbp_surrogate* s, const void* q5, const void* u3,
   if (e == cudaSuccess) e = forward(s, nullptr);
   const int lb = 1024;
   if (e == cudaSuccess) {
-    k_sur_loss<<<lb, 256, 0, s->stream>>>(s->y16, s->tgt, r5 ? s->rin : nullptr, mask ? s->msk : nullptr,
+    k_sur_loss<<<lb, 256, 0, s->stream>>>(s->y16, s->tgt, r5 ? s->rin : nullptr, (float)s->ksteps,
+                                           mask ? s->msk : nullptr,
                                            1.f / s->sdq, 1.0 / den, s->nx, s->ny, s->nz, s->G16, s->partial);
     k_sum<<<1, 32, 0, s->stream>>>(s->partial, lb, 1.0 / den, s->dloss);
     k_zero<<<256, 256, 0, s->stream>>>(s->grad, (long long)s->master_count);

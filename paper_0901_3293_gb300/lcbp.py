@@ -94,6 +94,8 @@ _SIGNATURES = {
     "lcbp_surrogate_train_step": (_c_int, [_P, _c_void_p, _c_void_p, _c_void_p, _c_double, _c_double, _c_void_p,
                                            _c_void_p, _c_int, _c_double, ctypes.POINTER(_c_double)]),
     "lcbp_read_rate": (_c_int, [_P, _c_void_p, _c_int]),
+    "lcbp_surrogate_set_steps": (_c_int, [_P, _c_int]),
+    "lcbp_surrogate_get_steps": (_c_int, [_P, ctypes.POINTER(_c_int)]),
     "lcbp_surrogate_save": (_c_int, [_P, ctypes.c_char_p]),
     "lcbp_surrogate_load": (_c_int, [_P, ctypes.c_char_p]),
     "lcbp_judge_create": (_c_int, [_P, _P, _c_void_p, ctypes.POINTER(_P)]),
@@ -632,6 +634,16 @@ class Surrogate:
         check(lib().lcbp_surrogate_set_params(self._h, a.ctypes.data, a.size))
         return self
 
+    def set_steps(self, k: int) -> "Surrogate":
+        """Solver steps one call stands for (default 10)."""
+        check(lib().lcbp_surrogate_set_steps(self._h, int(k)))
+        return self
+
+    def steps(self) -> int:
+        k = _c_int()
+        check(lib().lcbp_surrogate_get_steps(self._h, ctypes.byref(k)))
+        return k.value
+
     def save(self, path: str) -> None:
         """Write the weights file (parameters and scales, versioned)."""
         check(lib().lcbp_surrogate_save(self._h, os.fsencode(path)))
@@ -689,30 +701,33 @@ class Surrogate:
 class JudgeConfig(ctypes.Structure):
     """lcbp_judge_config."""
     _fields_ = [("kappa", _c_double), ("tau", _c_double), ("calls_per_segment", _c_int), ("tol_F", _c_double),
-                ("tol_Q", _c_double)]
+                ("tol_Q", _c_double), ("warmup_steps", ctypes.c_longlong)]
 
 
 class JudgeStats(ctypes.Structure):
     """lcbp_judge_stats."""
     _fields_ = [(k, ctypes.c_longlong) for k in ("t", "segments", "accepted", "fallbacks", "surrogate_calls",
                                                  "plain_steps")] + \
-               [(k, _c_double) for k in ("last_gap_F", "last_gap_Q", "max_gap_F")]
+               [(k, _c_double) for k in ("last_gap_F", "last_gap_Q", "max_gap_F", "mean_gap_F", "mean_gap_Q")] + \
+               [("judged", ctypes.c_longlong)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class Judge:
-    """The judged surrogate run of the library (lcbp_judge_*): segments of
-    `calls_per_segment` surrogate calls, each judged against ten plain steps
+    """The judged surrogate run of the library (lcbp_judge_*): after
+    `warmup_steps` plain steps, segments of `calls_per_segment` surrogate
+    calls, each judged against k plain steps
     (relative F gap <= tol_F, and max |dQ| <= tol_Q if tol_Q > 0), rolled back
     and redone plainly when it fails.  Keeps references to the lattice and
     the surrogate."""
 
     def __init__(self, lattice: "Lattice", surrogate: "Surrogate", kappa: float, tau: float,
-                 calls_per_segment: int = 49, tol_F: float = 1e-3, tol_Q: float = 0.0):
+                 calls_per_segment: int = 49, tol_F: float = 1e-3, tol_Q: float = 0.0, warmup_steps: int = 0):
         self.lattice, self.surrogate = lattice, surrogate
-        cfg = JudgeConfig(float(kappa), float(tau), int(calls_per_segment), float(tol_F), float(tol_Q))
+        cfg = JudgeConfig(float(kappa), float(tau), int(calls_per_segment), float(tol_F), float(tol_Q),
+                          int(warmup_steps))
         self._h = _P()
         check(lib().lcbp_judge_create(lattice._h, surrogate._h, ctypes.byref(cfg), ctypes.byref(self._h)))
 

@@ -1,23 +1,26 @@
 """Training data, training loop and judged inference for the learned surrogate.
 
 Everything numerical runs in liblcbp (solver kernels, tensor-core network
-kernels, loss and Adam); this module only orchestrates:
+kernels, loss and Adam, the judged run); this module only orchestrates:
 
 * ``generate``: plain FP32 runs of the thin-slab domain-growth problem
   (64 x 64 x 256, BPII seed for z < 32 inside an x-helix, tau = -0.5) at
   several chiralities; every ``every`` steps the state (Q, u) at t and
-  Q(t + 10) are kept as a training pair.
+  Q(t + k) are kept as a training pair (k solver steps per surrogate call).
 * ``train``: Adam on random 64^3 crops (full x, y; a z-window) of those pairs;
   the loss is masked within the network's receptive field (10 sites) of the
   crop's z-faces, where the periodic padding of the crop is not physical.
-* ``JudgedRun``: advances a lattice with the surrogate in segments of M calls
-  (10 steps each).  After each segment the judge re-equilibrates f, runs 10
-  plain steps from the surrogate state and compares the free energy with one
-  surrogate call from the same state; a relative gap above ``tol`` rolls the
-  segment back and redoes it with plain steps.
+* ``JudgedRun``: the library's judged run (lcbp_judge_*): segments of M
+  calls, each judged against k plain steps from the same re-equilibrated
+  state by the relative free-energy gap, rolled back and redone plainly when
+  the gap exceeds ``tol``.
+* ``main``: train at a given k, write the weights file, and compare the
+  judged runs of the trained network and of the zero network (k plain Euler
+  steps of the rate per call) with the plain solver on the slab workload at
+  several chiralities, logging F and the defect fraction every 100 steps.
 
-The surrogate predicts a correction to ten explicit Euler steps of the exact
-FP32 Beris-Edwards rate R(Q, u): Q(t + 10) = Q + 10 R + s_dq * net(Q, u, kappa, tau, R).
+The surrogate predicts a correction to k explicit Euler steps of the exact
+FP32 Beris-Edwards rate R(Q, u): Q(t + k) = Q + k R + s_dq * net(Q, u, kappa, tau, R).
 """
 
 from __future__ import annotations
@@ -56,21 +59,22 @@ class Sample:
     t: int
 
 
-def generate(kappas, steps: int, every: int, t_min: int = 0, seed: int = 20090119, shape=(64, 64, 256)):
-    """Plain runs; a sample (state, rate, 10-step change) every `every` steps from t_min."""
+def generate(kappas, steps: int, every: int, t_min: int = 0, seed: int = 20090119, shape=(64, 64, 256),
+             k: int = K_STEPS):
+    """Plain runs; a sample (state, rate, k-step change) every `every` steps from t_min."""
     out = []
     for i, kappa in enumerate(kappas):
         lat = slab_lattice(kappa, seed + i, shape)
         lat.step(t_min)
         t = t_min
-        while t + K_STEPS <= steps:
+        while t + k <= steps:
             q0 = lat.read_q(dtype=np.float32)
             u0 = lat.read_u(dtype=np.float32)
             r0 = lat.read_rate(dtype=np.float32)
-            lat.step(K_STEPS)
+            lat.step(k)
             q1 = lat.read_q(dtype=np.float32)
             out.append(Sample(q0, u0, r0, q1 - q0, float(kappa), t))
-            lat.step(every - K_STEPS)
+            lat.step(every - k)
             t += every
         lat.close()
     return out
@@ -119,35 +123,64 @@ class TrainLog:
 S_U, S_R, S_DQ = 1e-3, 1e-4, 3e-6
 
 
+def rotate_z_device(q5, u3, turns: int):
+    """rotate_z on CUDA tensors ([C, z, y, x], square x-y planes): the same
+    gather and sign changes, done where the training crops live."""
+    import torch
+    for _ in range(turns % 4):
+        n = q5.shape[-1]
+        yp, xp = torch.meshgrid(torch.arange(n, device=q5.device), torch.arange(n, device=q5.device), indexing="ij")
+        src_y, src_x = (-xp) % n, yp
+
+        def move(a):
+            return a[..., src_y, src_x]
+
+        q5 = torch.stack([move(q5[3]), -move(q5[1]), -move(q5[4]), move(q5[0]), move(q5[2])])
+        if u3 is not None:
+            u3 = torch.stack([-move(u3[1]), move(u3[0]), move(u3[2])])
+    return q5, u3
+
+
 def train(samples, iters: int, lr: float = 1e-3, depth: int = 64, seed: int = 0, params=None,
-          augment: bool = True):
+          augment: bool = True, k: int = K_STEPS):
     """Adam on random crops (rotated by a random quarter turn about z when
-    `augment`); returns (parameter vector, TrainLog)."""
+    `augment`); returns (parameter vector, TrainLog).  The samples are moved
+    to the device once; crops and rotations are gathers there."""
+    import torch
     rng = np.random.default_rng(seed)
     nx, ny = samples[0].q.shape[3], samples[0].q.shape[2]
     sur = lcbp.Surrogate(nx, ny, depth, training=True)
-    sur.set_scales(S_U, S_R, S_DQ)
+    sur.set_scales(S_U, S_R, S_DQ).set_steps(k)
     if params is None:
         params = init_params(rng)
     sur.set_params(params)
+    dev = [tuple(torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (sm.q, sm.u, sm.r, sm.dq))
+           for sm in samples]
+    nz = samples[0].q.shape[1]
+    mask = torch.ones((depth, ny, nx), dtype=torch.float32, device="cuda")
+    if depth < nz:
+        mask[:RECEPTIVE] = 0.0
+        mask[depth - RECEPTIVE:] = 0.0
     log = TrainLog()
     t0 = time.perf_counter()
     for it in range(iters):
-        s = samples[rng.integers(len(samples))]
-        z0 = int(rng.integers(s.q.shape[1]))
-        q, u, r, dq, mask = crop(s, z0, depth)
-        if augment and q.shape[-1] == q.shape[-2]:
-            k = int(rng.integers(4))
-            q, u = rotate_z(q, u, k)
-            r, _ = rotate_z(r, None, k)
-            dq, _ = rotate_z(dq, None, k)
-            q, u, r, dq = (np.ascontiguousarray(a) for a in (q, u, r, dq))
+        j = int(rng.integers(len(samples)))
+        z0 = int(rng.integers(nz))
+        idx = torch.arange(z0, z0 + depth, device="cuda") % nz
+        q, u, r, dq = (a.index_select(1, idx) for a in dev[j])
+        if augment and nx == ny:
+            turns = int(rng.integers(4))
+            q, u = rotate_z_device(q, u, turns)
+            r, _ = rotate_z_device(r, None, turns)
+            dq, _ = rotate_z_device(dq, None, turns)
+        q, u, r, dq = (a.contiguous() for a in (q, u, r, dq))
         lr_it = lr if it < iters // 2 else (lr * 0.3 if it < 3 * iters // 4 else lr * 0.1)
-        log.losses.append(sur.train_step(q, u, r, s.kappa, TAU_R, dq, mask, lr=lr_it))
+        log.losses.append(sur.train_step(q, u, r, samples[j].kappa, TAU_R, dq, mask, lr=lr_it))
     log.seconds = time.perf_counter() - t0
     log.iters = iters
     p = sur.get_params()
     sur.close()
+    del dev
     return p, log
 
 
@@ -164,22 +197,22 @@ def init_params(rng, blocks: int = 4, width: int = 32):
     return np.concatenate(parts).astype(np.float32)
 
 
-def evaluate(params, samples, depth: int = 64):
-    """Mean masked MSE of the predicted 10-step change on the given samples for
-    the network, for ten Euler steps of the rate (the integrator the network
+def evaluate(params, samples, depth: int = 64, k: int = K_STEPS):
+    """Mean masked MSE of the predicted k-step change on the given samples for
+    the network, for k Euler steps of the rate (the integrator the network
     corrects) and for persistence (dQ = 0)."""
     nx, ny = samples[0].q.shape[3], samples[0].q.shape[2]
     sur = lcbp.Surrogate(nx, ny, depth)
-    sur.set_scales(S_U, S_R, S_DQ)
+    sur.set_scales(S_U, S_R, S_DQ).set_steps(k)
     sur.set_params(params)
-    err = {"network": [], "euler10": [], "persistence": []}
+    err = {"network": [], "euler": [], "persistence": []}
     for s in samples:
         q, u, r, dq, mask = crop(s, 0, depth)
-        pred = 10.0 * r + S_DQ * sur.forward(q, u, r, s.kappa, TAU_R)
+        pred = k * r + S_DQ * sur.forward(q, u, r, s.kappa, TAU_R)
         w = mask[None]
         den = 5 * w.sum()
         err["network"].append(float((w * (pred - dq) ** 2).sum() / den))
-        err["euler10"].append(float((w * (10.0 * r - dq) ** 2).sum() / den))
+        err["euler"].append(float((w * (k * r - dq) ** 2).sum() / den))
         err["persistence"].append(float((w * dq ** 2).sum() / den))
     sur.close()
     return {k: float(np.mean(v)) for k, v in err.items()}
@@ -193,15 +226,16 @@ class JudgedRun:
     tol_q, if given) rolls the segment back and redoes it with plain steps."""
 
     def __init__(self, lat: lcbp.Lattice, params, kappa: float, M: int = 49, tol: float = 1e-3,
-                 tol_q: float = 0.0, weights: str | None = None):
+                 tol_q: float = 0.0, weights: str | None = None, k: int = K_STEPS, warmup: int = 0):
         nx, ny, nz = lat.dims
         self.sur = lcbp.Surrogate(nx, ny, nz)
         if weights is not None:
             self.sur.load(weights)
         else:
-            self.sur.set_scales(S_U, S_R, S_DQ)
+            self.sur.set_scales(S_U, S_R, S_DQ).set_steps(k)
             self.sur.set_params(params)
-        self.judge = lcbp.Judge(lat, self.sur, kappa, TAU_R, calls_per_segment=M, tol_F=tol, tol_Q=tol_q)
+        self.judge = lcbp.Judge(lat, self.sur, kappa, TAU_R, calls_per_segment=M, tol_F=tol, tol_Q=tol_q,
+                                warmup_steps=warmup)
 
     def advance(self, t_end: int, log_every: int = 0):
         """Advance to t_end; with log_every > 0 returns (t, F, defect fraction) at its multiples."""
@@ -215,14 +249,14 @@ class JudgedRun:
         self.sur.close()
 
 
-def time_call(shape=(64, 64, 256), reps: int = 20):
-    """Device time of one surrogate call and of 10 plain steps on the slab (ms)."""
+def time_call(shape=(64, 64, 256), reps: int = 20, k: int = K_STEPS):
+    """Device time of one surrogate call and of k plain steps on the slab (ms)."""
     import torch
     lat = slab_lattice(1.0, shape=shape)
     lat.step(20)
     lat.synchronize()
     sur = lcbp.Surrogate(*shape)
-    sur.set_scales(S_U, S_R, S_DQ)
+    sur.set_scales(S_U, S_R, S_DQ).set_steps(k)
     sur.set_params(init_params(np.random.default_rng(0)))
     sur.step(lat, 1.0, TAU_R, 2)  # warm-up
     t0 = time.perf_counter()
@@ -232,7 +266,7 @@ def time_call(shape=(64, 64, 256), reps: int = 20):
     lat.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(lat._stream)
-    lat.step(10 * reps)
+    lat.step(k * reps)
     e1.record(lat._stream)
     e1.synchronize()
     t_plain = e0.elapsed_time(e1) / reps
@@ -241,20 +275,55 @@ def time_call(shape=(64, 64, 256), reps: int = 20):
     return t_sur, t_plain
 
 
+def plain_log(kappa: float, steps: int, log_every: int = 100, threshold: float = 0.19):
+    """The slab workload run plainly: (t, F, defect fraction) every log_every steps, and seconds."""
+    lat = slab_lattice(kappa)
+    rows = []
+    t0 = time.perf_counter()
+    for t in range(log_every, steps + 1, log_every):
+        lat.step(log_every)
+        rows.append((t, lat.free_energy(), lat.defect_fraction(threshold)))
+    lat.synchronize()
+    secs = time.perf_counter() - t0
+    lat.close()
+    return rows, secs
+
+
+def judged_log(params, kappa: float, steps: int, k: int, M: int, tol: float, log_every: int = 100,
+               weights: str | None = None, warmup: int = 0):
+    """The judged run on the slab: its log, statistics and seconds."""
+    hyb = slab_lattice(kappa)
+    run = JudgedRun(hyb, params, kappa, M=M, tol=tol, k=k, weights=weights, warmup=warmup)
+    t0 = time.perf_counter()
+    ts, Fs, Ds = run.advance(steps, log_every)
+    hyb.synchronize()
+    secs = time.perf_counter() - t0
+    st = run.stats()
+    run.close()
+    hyb.close()
+    return list(zip(ts.tolist(), Fs.tolist(), Ds.tolist())), st, secs
+
+
 def main():
     import argparse
     import json
     import sys
     import torch
     ap = argparse.ArgumentParser(description="train the surrogate on slab runs and judge it against the solver")
+    ap.add_argument("--k", type=int, default=K_STEPS, help="solver steps per surrogate call")
     ap.add_argument("--data-steps", type=int, default=12000)
     ap.add_argument("--every", type=int, default=400)
     ap.add_argument("--t-min", type=int, default=500)
     ap.add_argument("--iters", type=int, default=2000)
-    ap.add_argument("--run-steps", type=int, default=20000)
-    ap.add_argument("--kappa", type=float, default=1.0)
-    ap.add_argument("--tol", type=float, default=1e-3)
     ap.add_argument("--train-kappas", type=int, default=6, help="training chiralities, evenly in [0.5, 2]")
+    ap.add_argument("--run-steps", type=int, default=20000)
+    ap.add_argument("--kappas", type=float, nargs="+", default=[0.5, 1.0, 2.0], help="chiralities of the judged runs")
+    ap.add_argument("--M", type=int, default=49, help="surrogate calls per judged segment")
+    ap.add_argument("--tol", type=float, default=1e-3)
+    ap.add_argument("--warmup", type=int, default=1000, help="plain steps before the first surrogate segment")
+    ap.add_argument("--out", default=None, help="write the trained weights file here")
+    ap.add_argument("--weights", default=None, help="skip training: judge this weights file")
+    ap.add_argument("--log-out", default=None, help="write the per-100-step logs here (JSON lines)")
     ap.add_argument("--s-r", type=float, default=None, help="input scale of the rate R")
     ap.add_argument("--s-dq", type=float, default=None, help="output scale of the correction")
     args = ap.parse_args()
@@ -262,62 +331,80 @@ def main():
     S_R = args.s_r if args.s_r is not None else S_R
     S_DQ = args.s_dq if args.s_dq is not None else S_DQ
     torch.cuda.set_device(0)
+    k = args.k
 
     def note(d):
         print(json.dumps(d), file=sys.stderr, flush=True)
 
     t0 = time.perf_counter()
-    data = generate(list(np.linspace(0.5, 2.0, args.train_kappas)), args.data_steps, args.every, t_min=args.t_min)
-    held = generate([1.5], args.data_steps, args.every * 4, t_min=args.t_min, seed=7)
-    t_gen = time.perf_counter() - t0
-    note({"samples": len(data), "held_out": len(held), "gen_s": t_gen})
-    params, log = train(data, args.iters)
-    note({"train_s": log.seconds, "loss_first": float(np.mean(log.losses[:20])),
-          "loss_last": float(np.mean(log.losses[-20:]))})
-    mse = evaluate(params, held, depth=held[0].q.shape[1])
+    held = generate([1.5], args.data_steps, args.every * 4, t_min=args.t_min, seed=7, k=k)
+    if args.weights:
+        sur = lcbp.Surrogate(held[0].q.shape[3], held[0].q.shape[2], 8).load(args.weights)
+        params = sur.get_params()
+        if sur.steps() != k:
+            raise SystemExit(f"{args.weights} was trained for k = {sur.steps()}, not {k}")
+        sur.close()
+        log, n_data = TrainLog(), 0
+        note({"k": k, "weights": args.weights})
+    else:
+        data = generate(list(np.linspace(0.5, 2.0, args.train_kappas)), args.data_steps, args.every,
+                        t_min=args.t_min, k=k)
+        n_data = len(data)
+        note({"k": k, "samples": n_data, "held_out": len(held), "gen_s": time.perf_counter() - t0})
+        params, log = train(data, args.iters, k=k)
+        del data
+        note({"train_s": log.seconds, "loss_first": float(np.mean(log.losses[:20])),
+              "loss_last": float(np.mean(log.losses[-20:]))})
+    t_gen = time.perf_counter() - t0 - log.seconds
+    mse = evaluate(params, held, depth=held[0].q.shape[1], k=k)
     note({"held_out_mse": mse})
-    t_sur, t_plain = time_call()
+    if args.out:
+        nx, ny = held[0].q.shape[3], held[0].q.shape[2]
+        sur = lcbp.Surrogate(nx, ny, 8)
+        sur.set_scales(S_U, S_R, S_DQ).set_steps(k).set_params(params)
+        sur.save(args.out)
+        sur.close()
+    t_sur, t_plain = time_call(k=k)
     note({"call_ms": [t_sur, t_plain]})
-    # both runs log F every 100 steps (and so pay for the same diagnostics)
-    log_every = 100
-    plain = slab_lattice(args.kappa)
-    F_plain = {}
-    tp0 = time.perf_counter()
-    for t in range(log_every, args.run_steps + 1, log_every):
-        plain.step(log_every)
-        F_plain[t] = plain.free_energy()
-    plain.synchronize()
-    t_plain_run = time.perf_counter() - tp0
-
-    def judged(p):
-        """The judged run with parameter vector p, against the plain trajectory at every logged step."""
-        hyb = slab_lattice(args.kappa)
-        run = JudgedRun(hyb, p, args.kappa, M=49, tol=args.tol)
-        th0 = time.perf_counter()
-        ts, Fs, _ = run.advance(args.run_steps, log_every)
-        hyb.synchronize()
-        secs = time.perf_counter() - th0
-        errs = [abs(F - F_plain[int(t)]) / abs(F_plain[int(t)]) for t, F in zip(ts, Fs)]
-        out = {"seconds": secs, **run.stats(), "logged": len(ts),
-               "max_rel_F_error": max(errs) if errs else None,
-               "mean_rel_F_error": float(np.mean(errs)) if errs else None,
-               "final_F": float(Fs[-1]) if len(Fs) else None}
-        run.close()
-        hyb.close()
-        return out
-
-    res = judged(params)
-    # the same pipeline without the learned correction: ten explicit Euler steps per call
-    res0 = judged(np.zeros_like(params))
-    note({"judged_network": res, "judged_euler10": res0})
+    runs = {}
+    logf = open(args.log_out, "w") if args.log_out else None
+    for kappa in args.kappas:
+        rows, t_pl = plain_log(kappa, args.run_steps)
+        F_plain = {t: F for t, F, _ in rows}
+        F_scale = max(abs(F) for _, F, _ in rows)
+        out = {"plain_s": t_pl, "final_F": rows[-1][1], "final_defect_fraction": rows[-1][2], "F_scale": F_scale}
+        # judged (tol) and accept-all (equal cost: every segment kept), trained and zero network
+        for mode, tol in (("judged", args.tol), ("accept_all", 1e30)):
+            for name, p in (("network", params), ("zero_network", np.zeros_like(params))):
+                jrows, st, secs = judged_log(p, kappa, args.run_steps, k, args.M, tol, warmup=args.warmup)
+                errs = [abs(F - F_plain[t]) / abs(F_plain[t]) for t, F, _ in jrows]
+                errs_s = [abs(F - F_plain[t]) / F_scale for t, F, _ in jrows]
+                out[mode + "_" + name] = {"seconds": secs, "speedup_vs_plain": t_pl / secs, "logged": len(jrows),
+                                          "max_rel_F_error": max(errs), "mean_rel_F_error": float(np.mean(errs)),
+                                          "max_F_error_of_scale": max(errs_s), **st}
+                if logf:
+                    for (t, F, D), e in zip(jrows, errs):
+                        logf.write(json.dumps({"run": mode + "_" + name, "kappa": kappa, "k": k, "t": t, "F": F,
+                                               "defect_fraction": D, "rel_F_error_vs_plain": e}) + "\n")
+        if logf:
+            for t, F, D in rows:
+                logf.write(json.dumps({"run": "plain", "kappa": kappa, "t": t, "F": F, "defect_fraction": D}) + "\n")
+        runs[str(kappa)] = out
+        note({"kappa": kappa, **out})
+    if logf:
+        logf.close()
     print(json.dumps({
-        "data": {"samples": len(data), "held_out": len(held), "seconds": t_gen},
-        "train": {"iters": log.iters, "seconds": log.seconds, "ms_per_iter": 1e3 * log.seconds / log.iters,
-                  "loss_first": float(np.mean(log.losses[:20])), "loss_last": float(np.mean(log.losses[-20:]))},
+        "k": k,
+        "data": {"samples": n_data, "seconds": t_gen},
+        "train": {"iters": log.iters, "seconds": log.seconds,
+                  "ms_per_iter": 1e3 * log.seconds / log.iters if log.iters else None,
+                  "loss_first": float(np.mean(log.losses[:20])) if log.losses else None,
+                  "loss_last": float(np.mean(log.losses[-20:])) if log.losses else None,
+                  "weights": args.weights},
         "held_out_mse": mse,
-        "call_ms": {"surrogate_10_steps": t_sur, "plain_10_steps": t_plain},
-        "run": {"steps": args.run_steps, "kappa": args.kappa, "plain_s": t_plain_run,
-                "final_F_plain": F_plain[max(F_plain)], "network": res, "euler10_without_network": res0},
+        "call_ms": {"surrogate_call": t_sur, "plain_k_steps": t_plain},
+        "judged_runs": {"steps": args.run_steps, "M": args.M, "tol": args.tol, "warmup": args.warmup,
+                        "by_kappa": runs},
     }))
 
 
