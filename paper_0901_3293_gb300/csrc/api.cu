@@ -185,6 +185,9 @@ struct lcbp_lattice {
   // state and scratch (device)
   void *f[2], *rhou[2], *q, *qs, *h, *sig, *tau, *b, *bext, *staging;
   void* pq;  // the fast kernels' padded scratch (overlays h, sig, tau, b)
+  void *qm, *um[2];  // padded mirrors of Q and rho u [0] / [1] (fast path)
+  bool flat_ok;      // q and rhou[cur] hold the current state
+  bool mirror_ok;    // qm and um[cur] hold the current state
   long long staging_elems;
   void* d_rep;
   Tile* d_tiles;
@@ -213,7 +216,7 @@ struct lcbp_lattice {
 namespace {
 
 struct Layout {
-  size_t off[16];
+  size_t off[19];
   size_t total;
 };
 
@@ -238,7 +241,8 @@ Layout layout(int nx, int ny, int nz, int dtype) {
     L.off[i] = o;
     o = align256(o + (size_t)(comps[i] * n) * es);
   }
-  const long long scr = std::max(16 * n, zm_pq_elems(nx, ny, nz));
+  // (the padded scratch, then a Q-mirror-sized buffer for the tuner's output)
+  const long long scr = std::max(16 * n, zm_pq_elems(nx, ny, nz) + zm_qmirror_elems(nx, ny, nz));
   L.off[6] = o;
   L.off[7] = o + (size_t)(5 * n) * es;
   L.off[8] = o + (size_t)(10 * n) * es;
@@ -256,6 +260,14 @@ Layout layout(int nx, int ny, int nz, int dtype) {
   o = align256(o + 64);
   L.off[15] = o;  // partials + out
   o = align256(o + (kDiagPartials + 8) * 8);
+  // padded mirrors of Q and rho u [0], [1] (lattices the fast path can serve)
+  const bool fast_shape = nx % 4 == 0;
+  L.off[16] = o;
+  o = align256(o + (fast_shape ? (size_t)zm_qmirror_elems(nx, ny, nz) * es : 0));
+  L.off[17] = o;
+  o = align256(o + (fast_shape ? (size_t)zm_umirror_elems(nx, ny, nz) * es : 0));
+  L.off[18] = o;
+  o = align256(o + (fast_shape ? (size_t)zm_umirror_elems(nx, ny, nz) * es : 0));
   L.total = o;
   return L;
 }
@@ -295,6 +307,11 @@ int finish_create(lcbp_lattice* h) {
   h->b = w + L.off[9];
   h->bext = w + L.off[10];
   h->pq = h->h;
+  h->qm = w + L.off[16];
+  h->um[0] = w + L.off[17];
+  h->um[1] = w + L.off[18];
+  h->flat_ok = true;
+  h->mirror_ok = false;
   h->staging = w + L.off[11];
   h->staging_elems = std::min(kStagingMax, 15 * h->n);
   h->d_rep = w + L.off[12];
@@ -356,13 +373,14 @@ bool make_field_tmap(CUtensorMap* tm, void* base, int comps, int nx, int ny, int
   return encode_tiled(tm, base, 4, dims, strides, box, dtype);
 }
 
-// the padded scratch [15][nz][ny + 2][nx + 4] as a 4-D tensor, box = 36 x rows x 1 x 15
-bool make_pq_tmap(CUtensorMap* tm, void* base, int nx, int ny, int nz, int rows, int dtype) {
+// a padded array [comps][nz][nym][nxm] (component stride cs elements) as a 4-D
+// tensor, box = width x rows x 1 x comps
+bool make_padded_tmap(CUtensorMap* tm, void* base, int comps, int nxm, int nym, int nz, long long cs, int rows,
+                      int width, int dtype) {
   const cuuint64_t es = dtype_size(dtype);
-  const cuuint64_t nxp = nx + kZmPadX, nyp = ny + 2;
-  const cuuint64_t dims[4] = {nxp, nyp, (cuuint64_t)nz, (cuuint64_t)kZmPQ};
-  const cuuint64_t strides[3] = {nxp * es, nxp * nyp * es, nxp * nyp * nz * es};
-  const cuuint32_t box[4] = {(cuuint32_t)kZmBoxXP, (cuuint32_t)rows, 1, (cuuint32_t)kZmPQ};
+  const cuuint64_t dims[4] = {(cuuint64_t)nxm, (cuuint64_t)nym, (cuuint64_t)nz, (cuuint64_t)comps};
+  const cuuint64_t strides[3] = {nxm * es, (cuuint64_t)nxm * nym * es, (cuuint64_t)cs * es};
+  const cuuint32_t box[4] = {(cuuint32_t)width, (cuuint32_t)rows, 1, (cuuint32_t)comps};
   return encode_tiled(tm, base, 4, dims, strides, box, dtype);
 }
 
@@ -377,13 +395,19 @@ bool use_fast(lcbp_lattice* h) {
     if (h->dtype == LCBP_F64) std::call_once(prep64, [] { zm_prepare<double>(); });
     else std::call_once(prep32, [] { zm_prepare<float>(); });
     const int ty = h->dtype == LCBP_F64 ? zm_tile_rows<double>() : zm_tile_rows<float>();
-    bool ok = make_field_tmap(&h->tm[0], h->q, 5, h->nx, h->ny, h->nz, ty + 4, h->dtype);
-    ok = ok && make_field_tmap(&h->tm[1], h->rhou[0], 4, h->nx, h->ny, h->nz, ty + 2, h->dtype);
-    ok = ok && make_field_tmap(&h->tm[2], h->rhou[1], 4, h->nx, h->ny, h->nz, ty + 2, h->dtype);
-    ok = ok && make_pq_tmap(&h->tm[3], h->pq, h->nx, h->ny, h->nz, ty + 2, h->dtype);
-    for (int k = 0; k < 2; ++k)  // the velocity components of rho u
-      ok = ok && make_field_tmap(&h->tm[4 + k], static_cast<char*>(h->rhou[k]) + h->n * h->es, 3, h->nx, h->ny,
-                                 h->nz, ty + 2, h->dtype);
+    // Q and rho u from their padded mirrors (40-wide boxes), u = rho u components
+    // 1..3, and the LB-ready scratch (36-wide boxes)
+    const int nxm = h->nx + 2 * kZmMirX, nyq = h->ny + 4, nyu = h->ny + 2;
+    const long long cq = (long long)nxm * nyq * h->nz, cu = (long long)nxm * nyu * h->nz;
+    bool ok = make_padded_tmap(&h->tm[0], h->qm, 5, nxm, nyq, h->nz, cq, ty + 4, kZmBoxX, h->dtype);
+    for (int k = 0; k < 2; ++k) {
+      ok = ok && make_padded_tmap(&h->tm[1 + k], h->um[k], 4, nxm, nyu, h->nz, cu, ty + 2, kZmBoxX, h->dtype);
+      ok = ok && make_padded_tmap(&h->tm[4 + k], static_cast<char*>(h->um[k]) + cu * h->es, 3, nxm, nyu, h->nz, cu,
+                                  ty + 2, kZmBoxX, h->dtype);
+    }
+    const int nxp = h->nx + kZmPadX;
+    ok = ok && make_padded_tmap(&h->tm[3], h->pq, kZmPQ, nxp, nyu, h->nz, (long long)nxp * nyu * h->nz, ty + 2,
+                                kZmBoxXP, h->dtype);
     for (int k = 0; k < 2; ++k)  // the populations (L2 prefetches only)
       ok = ok && make_field_tmap(&h->tm[6 + k], h->f[k], NV, h->nx, h->ny, h->nz, ty + 2, h->dtype);
     if (!ok) {
@@ -409,14 +433,14 @@ ZmArgs zm_args(lcbp_lattice* h, const void* model) {
   a.tm_pq = &h->tm[3];
   a.tm_u3 = &h->tm[4 + h->cur];
   a.tm_f = &h->tm[6 + h->cur];
-  a.q = h->q;
+  a.q = h->qm;
   a.qout = nullptr;
   a.pq = h->pq;
   a.bext = h->has_bext ? h->bext : nullptr;
   a.f = h->f[h->cur];
   a.fnew = h->f[h->cur ^ 1];
-  a.rhou = h->rhou[h->cur];
-  a.rhou_new = h->rhou[h->cur ^ 1];
+  a.rhou = h->um[h->cur];
+  a.rhou_new = h->um[h->cur ^ 1];
   a.err = h->d_err;
   a.events = nullptr;
   a.q_wall = h->p.walls_z ? h->p.q_wall : nullptr;
@@ -530,7 +554,8 @@ int tune_zc(lcbp_lattice* h) {
         a.zc = zc;
         a.spt = spt;
         a.spt_q = sq;
-        a.qout = h->qs;  // scratch the fast kernels do not use
+        // Q^{n+1} to the Q-mirror-sized buffer after the padded scratch: the state is untouched
+      a.qout = static_cast<char*>(h->pq) + (size_t)zm_pq_elems(h->nx, h->ny, h->nz) * h->es;
         float t = 1e30f;
         for (int rep = 0; rep < 3; ++rep) {
           cudaEventRecord(e0, h->stream);
@@ -651,7 +676,11 @@ int build_graph(lcbp_lattice* h) {
   return LCBP_OK;
 }
 
+int sync_flat(lcbp_lattice* h);
+
 int diag(lcbp_lattice* h, double threshold, int with_f) {
+  const int rs = sync_flat(h);
+  if (rs) return rs;
   DiagGeom g{h->nx, h->ny, h->nz, h->n, 0, h->p.A0, h->p.gamma, h->p.K, h->p.q0, h->p.walls_z, {}, 0.0};
   for (int c = 0; c < 5; ++c) g.qw[c] = h->p.q_wall[c];
   g.c_div = h->p.l2_set ? 0.5 * (h->p.K - h->p.L2) : 0.0;
@@ -695,6 +724,47 @@ int refresh_moments(lcbp_lattice* h) {
                                               h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   return e == cudaSuccess ? LCBP_OK : cuda_fail(e, "moments");
+}
+
+// The fast path keeps Q and rho u[cur] in padded mirrors with periodic
+// ghosts (so its kernels stage them with no patching); every other kernel and
+// every copy to or from the caller uses the flat arrays.  flat_ok / mirror_ok
+// tell which copy is current (at least one is): fast steps make the mirrors
+// current (sync_mirror before them), anything else reads or writes the flat
+// arrays (sync_flat before, and a write makes the mirrors stale).
+int sync_flat(lcbp_lattice* h) {
+  if (h->flat_ok) return LCBP_OK;
+  const int nxm = h->nx + 2 * kZmMirX, X = kZmMirX;
+  cudaError_t e =
+      h->dtype == LCBP_F64
+          ? launch_unpack<double>(h->qm, h->q, 5, h->nx, h->ny, h->nz, X, 2, nxm, h->ny + 4, h->stream)
+          : launch_unpack<float>(h->qm, h->q, 5, h->nx, h->ny, h->nz, X, 2, nxm, h->ny + 4, h->stream);
+  if (e == cudaSuccess)
+    e = h->dtype == LCBP_F64
+            ? launch_unpack<double>(h->um[h->cur], h->rhou[h->cur], 4, h->nx, h->ny, h->nz, X, 1, nxm, h->ny + 2,
+                                    h->stream)
+            : launch_unpack<float>(h->um[h->cur], h->rhou[h->cur], 4, h->nx, h->ny, h->nz, X, 1, nxm, h->ny + 2,
+                                   h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "state from the padded mirrors");
+  h->flat_ok = true;
+  return LCBP_OK;
+}
+
+int sync_mirror(lcbp_lattice* h) {
+  if (h->mirror_ok) return LCBP_OK;
+  const int nxm = h->nx + 2 * kZmMirX, X = kZmMirX;
+  cudaError_t e = h->dtype == LCBP_F64
+                      ? launch_pack<double>(h->q, h->qm, 5, h->nx, h->ny, h->nz, X, 2, nxm, h->ny + 4, h->stream)
+                      : launch_pack<float>(h->q, h->qm, 5, h->nx, h->ny, h->nz, X, 2, nxm, h->ny + 4, h->stream);
+  if (e == cudaSuccess)
+    e = h->dtype == LCBP_F64
+            ? launch_pack<double>(h->rhou[h->cur], h->um[h->cur], 4, h->nx, h->ny, h->nz, X, 1, nxm, h->ny + 2,
+                                  h->stream)
+            : launch_pack<float>(h->rhou[h->cur], h->um[h->cur], 4, h->nx, h->ny, h->nz, X, 1, nxm, h->ny + 2,
+                                 h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "padded mirrors of the state");
+  h->mirror_ok = true;
+  return LCBP_OK;
 }
 
 struct CkptHeader {
@@ -865,6 +935,10 @@ size_t lcbp_snapshot_bytes(lcbp_lattice* h) { return h ? (size_t)(24 * h->n) * h
 
 int lcbp_snapshot(lcbp_lattice* h, void* dst) {
   CHECK_H(h);
+  {
+    const int rs = sync_flat(h);
+    if (rs) return rs;
+  }
   if (!dst) return fail(LCBP_EINVAL, "dst is NULL");
   if (!h->f_ready) return fail(LCBP_ESTATE, "f was never initialised");
   const size_t nf = (size_t)(15 * h->n) * h->es, nr = (size_t)(4 * h->n) * h->es, nq = (size_t)(5 * h->n) * h->es;
@@ -887,6 +961,8 @@ int lcbp_restore(lcbp_lattice* h, const void* src) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return cuda_fail(e, "restore");
   h->f_ready = true;
+  h->flat_ok = true;
+  h->mirror_ok = false;
   return LCBP_OK;
 }
 
@@ -941,6 +1017,11 @@ int lcbp_set_walls(lcbp_lattice* h, int walls_z, const double* q_wall5) {
 
 int lcbp_init_q(lcbp_lattice* h, int kind, double amplitude, double noise, uint64_t seed, const int* region) {
   CHECK_H(h);
+  {
+    const int rs = sync_flat(h);
+    if (rs) return rs;
+  }
+  h->mirror_ok = false;  // the flat state is written below
   if (kind < LCBP_BPII || kind > LCBP_SLAB_BPII_IN_CHOL_Z) return fail(LCBP_EINVAL, "unknown initial kind %d", kind);
   if (!(noise >= 0.0) || !std::isfinite(amplitude)) return fail(LCBP_EINVAL, "need noise >= 0, finite amplitude");
   if (kind >= LCBP_SLAB_BPII_IN_CHOL && !region) return fail(LCBP_EINVAL, "slab kinds need region[0] = z0");
@@ -957,6 +1038,11 @@ int lcbp_init_q(lcbp_lattice* h, int kind, double amplitude, double noise, uint6
 
 int lcbp_set_q(lcbp_lattice* h, const void* q5, int dtype) {
   CHECK_H(h);
+  {
+    const int rs = sync_flat(h);
+    if (rs) return rs;
+  }
+  h->mirror_ok = false;  // the flat state is written below
   if (!q5 || !valid_dtype(dtype)) return fail(LCBP_EINVAL, "bad buffer or dtype");
   // into the Q* scratch first: a field holding NaN or Inf is refused and Q stays as it was
   int rc = transfer(h->qs, h->dtype, const_cast<void*>(q5), dtype, 5 * h->n, true, h->staging, h->staging_elems,
@@ -973,6 +1059,11 @@ int lcbp_set_q(lcbp_lattice* h, const void* q5, int dtype) {
 
 int lcbp_init_f_equilibrium(lcbp_lattice* h, double rho0, const void* u3, int dtype) {
   CHECK_H(h);
+  {
+    const int rs = sync_flat(h);
+    if (rs) return rs;
+  }
+  h->mirror_ok = false;  // the flat state is written below
   if (rho0 == 0.0) rho0 = h->p.rho0;  // the lattice's reference density
   if (!(rho0 > 0.0) || !valid_dtype(dtype)) return fail(LCBP_EINVAL, "need rho0 > 0 (or 0) and a valid dtype");
   int rc;
@@ -998,6 +1089,11 @@ int lcbp_init_f_equilibrium(lcbp_lattice* h, double rho0, const void* u3, int dt
 
 int lcbp_set_f(lcbp_lattice* h, const void* f15, int dtype) {
   CHECK_H(h);
+  {
+    const int rs = sync_flat(h);
+    if (rs) return rs;
+  }
+  h->mirror_ok = false;  // the flat state is written below
   if (!f15 || !valid_dtype(dtype)) return fail(LCBP_EINVAL, "bad buffer or dtype");
   // into the scratch block (16 N elements) first: non-finite populations are refused, f stays as it was
   int rc = transfer(h->h, h->dtype, const_cast<void*>(f15), dtype, 15 * h->n, true, h->staging, h->staging_elems,
@@ -1041,10 +1137,18 @@ int lcbp_step(lcbp_lattice* h, int nsteps) {
   if (nsteps < 0) return fail(LCBP_EINVAL, "nsteps < 0");
   if (h->p.flow_on && !h->f_ready) return fail(LCBP_ESTATE, "initialise f before stepping with flow on");
   if (nsteps == 0) return LCBP_OK;
-  if (use_fast(h) && h->zc == 0) {
+  const bool fast = use_fast(h);
+  {
+    const int rs = fast ? sync_mirror(h) : sync_flat(h);
+    if (rs) return rs;
+  }
+  if (fast && h->zc == 0) {
     int rc = tune_zc(h);
     if (rc) return rc;
   }
+  // the kernel set's copy of the state is the one that changes
+  if (fast) h->flat_ok = false;
+  else h->mirror_ok = false;
   cudaError_t e = cudaSuccess;
   int left = nsteps;
   if (h->cur == 1) {
@@ -1075,10 +1179,16 @@ int lcbp_profile_steps(lcbp_lattice* h, int nsteps, double* kernel_ms, int capac
   if (nsteps < 1 || !kernel_ms || !nkernels) return fail(LCBP_EINVAL, "need nsteps >= 1 and output arrays");
   if (h->p.flow_on && !h->f_ready) return fail(LCBP_ESTATE, "initialise f before stepping with flow on");
   const bool fast = use_fast(h);
+  {
+    const int rs = fast ? sync_mirror(h) : sync_flat(h);
+    if (rs) return rs;
+  }
   if (fast && h->zc == 0) {
     int rc = tune_zc(h);
     if (rc) return rc;
   }
+  if (fast) h->flat_ok = false;
+  else h->mirror_ok = false;
   const int nk = fast ? 2 : kernels_per_step(h->p.flow_on, h->p.coupling);
   *nkernels = nk;
   if (capacity < nk) return fail(LCBP_EINVAL, "kernel_ms holds %d values, need %d", capacity, nk);
@@ -1171,12 +1281,20 @@ int lcbp_check_wait_timeout(double limit_ms, int* timed_out) {
 
 int lcbp_read_q(lcbp_lattice* h, void* dst, int dtype) {
   CHECK_H(h);
+  {
+    const int rs = sync_flat(h);
+    if (rs) return rs;
+  }
   if (!dst || !valid_dtype(dtype)) return fail(LCBP_EINVAL, "bad buffer or dtype");
   return transfer(h->q, h->dtype, dst, dtype, 5 * h->n, false, h->staging, h->staging_elems, h->stream);
 }
 
 int lcbp_read_u(lcbp_lattice* h, void* dst, int dtype) {
   CHECK_H(h);
+  {
+    const int rs = sync_flat(h);
+    if (rs) return rs;
+  }
   if (!dst || !valid_dtype(dtype)) return fail(LCBP_EINVAL, "bad buffer or dtype");
   return transfer(static_cast<char*>(h->rhou[h->cur]) + h->n * h->es, h->dtype, dst, dtype, 3 * h->n, false,
                   h->staging, h->staging_elems, h->stream);
@@ -1184,6 +1302,10 @@ int lcbp_read_u(lcbp_lattice* h, void* dst, int dtype) {
 
 int lcbp_read_rho(lcbp_lattice* h, void* dst, int dtype) {
   CHECK_H(h);
+  {
+    const int rs = sync_flat(h);
+    if (rs) return rs;
+  }
   if (!dst || !valid_dtype(dtype)) return fail(LCBP_EINVAL, "bad buffer or dtype");
   // rho = 1 + drho, assembled in the (free between steps) predictor scratch
   cudaError_t e = h->dtype == LCBP_F64 ? launch_shift<double>(h->rhou[h->cur], h->qs, h->n, 1, 1, 1, h->stream)
@@ -1236,6 +1358,10 @@ int lcbp_defect_fraction(lcbp_lattice* h, double threshold, double* fraction) {
 
 int lcbp_texture(lcbp_lattice* h, const lcbp_optics* o, float* img) {
   CHECK_H(h);
+  {
+    const int rs = sync_flat(h);
+    if (rs) return rs;
+  }
   if (!o || !img) return fail(LCBP_EINVAL, "o and img must not be NULL");
   if (o->nlambda < 1 || o->nlambda > 4) return fail(LCBP_EINVAL, "nlambda must be 1..4, got %d", o->nlambda);
   for (int l = 0; l < o->nlambda; ++l)
@@ -1258,6 +1384,10 @@ int lcbp_texture(lcbp_lattice* h, const lcbp_optics* o, float* img) {
 // state type, so that a resumed run is bitwise identical to an uninterrupted one.
 int lcbp_save(lcbp_lattice* h, const char* path) {
   CHECK_H(h);
+  {
+    const int rs = sync_flat(h);
+    if (rs) return rs;
+  }
   if (!path) return fail(LCBP_EINVAL, "path is NULL");
   CkptHeader hd{};
   std::memcpy(hd.magic, "LCBPCKP2", 8);
@@ -1349,12 +1479,18 @@ int lcbp_load(lcbp_lattice* h, const char* path) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return cuda_fail(e, "load");
   h->f_ready = true;
+  h->flat_ok = true;
+  h->mirror_ok = false;
   h->step = hd.step;
   return LCBP_OK;
 }
 
 int lcbp_read_rate(lcbp_lattice* h, void* dst, int dtype) {
   CHECK_H(h);
+  {
+    const int rs = sync_flat(h);
+    if (rs) return rs;
+  }
   if (!dst || !valid_dtype(dtype)) return fail(LCBP_EINVAL, "bad buffer or dtype");
   if (h->p.flow_on && !h->f_ready) return fail(LCBP_ESTATE, "initialise f first (u comes from f)");
   StepArgs a = step_args(h);
@@ -1365,6 +1501,11 @@ int lcbp_read_rate(lcbp_lattice* h, void* dst, int dtype) {
 
 int lcbp_reequilibrate_f(lcbp_lattice* h) {
   CHECK_H(h);
+  {
+    const int rs = sync_flat(h);
+    if (rs) return rs;
+  }
+  h->mirror_ok = false;  // the flat state is written below
   if (!h->f_ready) return fail(LCBP_ESTATE, "f was never initialised");
   StepArgs a = step_args(h);
   cudaError_t e = h->dtype == LCBP_F64 ? launch_field<double>(a, h->stream) : launch_field<float>(a, h->stream);
@@ -1387,6 +1528,8 @@ int lattice_rate(lcbp_lattice* h, const float** rate, cudaEvent_t done) {
   if (!h) return fail(LCBP_EINVAL, "null lattice handle");
   if (h->dtype != LCBP_F32) return fail(LCBP_EINVAL, "the surrogate works on FP32 lattice state");
   cudaSetDevice(h->device);
+  const int rs = sync_flat(h);
+  if (rs) return rs;
   StepArgs a = step_args(h);
   cudaError_t e = launch_rate<float>(a, h->stream);
   if (e == cudaSuccess) e = cudaEventRecord(done, h->stream);
@@ -1400,6 +1543,9 @@ int lattice_fields(lcbp_lattice* h, float** q, const float** u, int dims[3], cud
   if (h->dtype != LCBP_F32) return fail(LCBP_EINVAL, "the surrogate works on FP32 lattice state");
   if (h->p.walls_z) return fail(LCBP_EINVAL, "the surrogate's convolutions are periodic: no walls");
   cudaSetDevice(h->device);
+  const int rs = sync_flat(h);
+  if (rs) return rs;
+  h->mirror_ok = false;  // the surrogate updates Q in place
   *q = static_cast<float*>(h->q);
   *u = reinterpret_cast<const float*>(static_cast<const char*>(h->rhou[h->cur]) + h->n * sizeof(float));
   dims[0] = h->nx;
@@ -1431,6 +1577,8 @@ int lattice_clone(lcbp_lattice* src, lcbp_lattice** out) {
 int lattice_q(lcbp_lattice* h, const void** q, long long* n, int* dtype, cudaStream_t* stream) {
   if (!h) return fail(LCBP_EINVAL, "null lattice handle");
   cudaSetDevice(h->device);
+  const int rs = sync_flat(h);
+  if (rs) return rs;
   *q = h->q;
   *n = h->n;
   *dtype = h->dtype;

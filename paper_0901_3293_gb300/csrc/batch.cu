@@ -148,6 +148,11 @@ void set_zc(lcbp_batch* b, const int* zc) {
     c.G.nxp = c.G.nx + kZmPadX;
     c.G.nyp = c.G.ny + 2;
     c.G.cp = (long long)c.G.nxp * c.G.nyp * c.G.nz;
+    c.G.nxm = c.G.nx + 2 * kZmMirX;  // (batches keep flat state: no mirrors)
+    c.G.nyq = c.G.ny + 4;
+    c.G.nyu = c.G.ny + 2;
+    c.G.cq = (long long)c.G.nxm * c.G.nyq * c.G.nz;
+    c.G.cu = (long long)c.G.nxm * c.G.nyu * c.G.nz;
     c.cta0 = cta;
     cta += c.ctas_per_rep * c.count;
   }

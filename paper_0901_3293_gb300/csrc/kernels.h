@@ -92,6 +92,16 @@ struct DiagGeom {
   double qw[5];    // anchored Q (q5 order)
   double c_div;    // (K - L2) / 2: F_h gains -c_div |div Q|^2 per site
 };
+// padded mirror <-> flat field (state.cu): C components of an nx x ny x nz
+// field, site (x, y) at column x + hx and row y + hy of a mirror of nxp x nyp;
+// pack fills every mirror position with its periodic image
+template <typename real>
+cudaError_t launch_pack(const void* flat, void* padded, int C, int nx, int ny, int nz, int hx, int hy, int nxp,
+                        int nyp, cudaStream_t s);
+template <typename real>
+cudaError_t launch_unpack(const void* padded, void* flat, int C, int nx, int ny, int nz, int hx, int hy, int nxp,
+                          int nyp, cudaStream_t s);
+
 // whole-field checks (state.cu); scratch: state_check_scratch_bytes() of device memory
 size_t state_check_scratch_bytes();
 // *out = number of non-finite values among n
@@ -133,9 +143,23 @@ struct ZmGeom {
   int nx, ny, nz, zc;
   long long n;
   int tiles_x, tiles_y, tiles_z;
-  int nxp, nyp;    // padded scratch extents: nx + 4, ny + 2
-  long long cp;    // padded scratch component stride: nxp * nyp * nz
+  int nxp, nyp;    // padded scratch and rho u mirror extents: nx + 4, ny + 2
+  long long cp;    // their component stride: nxp * nyp * nz
+  int nxm;         // mirror row length: nx + 16
+  int nyq, nyu;    // mirror rows per plane: ny + 4 (Q), ny + 2 (rho u)
+  long long cq, cu;  // mirror component strides: nxm * nyq * nz, nxm * nyu * nz
 };
+
+// Padded mirrors of the state (single lattices on the fast path): Q and rho u
+// with eight columns added on each side of a row (site x at column x + 8, so
+// that a row of 32 sites starts on a 32-byte sector) and two (Q) or one
+// (rho u) rows added on each side; the ghost columns and rows next to the
+// lattice hold the periodic images (x = -2, -1, nx, nx + 1 for Q, -1 and nx
+// for rho u).  k_lbq writes Q^{n+1} and rho u^{n+1} there, images included, so
+// the next step stages them with no patching.
+constexpr int kZmMirX = 8;  // columns added on each side of a mirror row
+inline long long zm_qmirror_elems(int nx, int ny, int nz) { return 5LL * (nx + 2 * kZmMirX) * (ny + 4) * nz; }
+inline long long zm_umirror_elems(int nx, int ny, int nz) { return 4LL * (nx + 2 * kZmMirX) * (ny + 2) * nz; }
 
 struct ZmArgs {
   int nx, ny, nz, zc;

@@ -1,7 +1,8 @@
-// Whole-field checks on device arrays: the count of non-finite values (used
-// to refuse uploads) and the largest absolute difference of two fields (used
-// by the surrogate judge to compare a surrogate call with plain steps).
-// Both reduce in a fixed order, so a result never depends on scheduling.
+// Whole-field operations on device arrays: the count of non-finite values
+// (used to refuse uploads), the largest absolute difference of two fields
+// (used by the surrogate judge to compare a surrogate call with plain steps),
+// both reduced in a fixed order, and the copies between a field and its
+// padded mirror with periodic ghosts (the fast step's state layout).
 #include <cmath>
 
 #include "kernels.h"
@@ -99,6 +100,60 @@ cudaError_t launch_max_abs_diff(const void* a, const void* b, long long n, void*
   k_final_max<<<1, 32, 0, s>>>(partial, nb, out);
   return cudaGetLastError();
 }
+
+// padded[c][z][Y][X] = flat[c][z][wrap(Y - hy)][wrap(X - hx)] over every padded position
+template <typename real>
+__global__ void k_pack(const real* __restrict__ flat, real* __restrict__ padded, int C, int nx, int ny, int nz, int hx,
+                       int hy, int nxp, int nyp) {
+  const long long total = (long long)C * nz * nyp * nxp;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int X = (int)(i % nxp);
+    const long long r = i / nxp;
+    const int Y = (int)(r % nyp);
+    const long long cz = r / nyp;  // c * nz + z
+    int x = (X - hx) % nx, y = (Y - hy) % ny;
+    x += x < 0 ? nx : 0;
+    y += y < 0 ? ny : 0;
+    padded[i] = flat[(cz * ny + y) * nx + x];
+  }
+}
+
+// flat[c][z][y][x] = padded[c][z][y + hy][x + hx]
+template <typename real>
+__global__ void k_unpack(const real* __restrict__ padded, real* __restrict__ flat, int C, int nx, int ny, int nz,
+                         int hx, int hy, int nxp, int nyp) {
+  const long long total = (long long)C * nz * ny * nx;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(i % nx);
+    const long long r = i / nx;
+    const int y = (int)(r % ny);
+    const long long cz = r / ny;
+    flat[i] = padded[(cz * nyp + y + hy) * nxp + x + hx];
+  }
+}
+
+template <typename real>
+cudaError_t launch_pack(const void* flat, void* padded, int C, int nx, int ny, int nz, int hx, int hy, int nxp,
+                        int nyp, cudaStream_t s) {
+  k_pack<real><<<4096, 256, 0, s>>>(static_cast<const real*>(flat), static_cast<real*>(padded), C, nx, ny, nz, hx, hy,
+                                    nxp, nyp);
+  return cudaGetLastError();
+}
+
+template <typename real>
+cudaError_t launch_unpack(const void* padded, void* flat, int C, int nx, int ny, int nz, int hx, int hy, int nxp,
+                          int nyp, cudaStream_t s) {
+  k_unpack<real><<<4096, 256, 0, s>>>(static_cast<const real*>(padded), static_cast<real*>(flat), C, nx, ny, nz, hx,
+                                      hy, nxp, nyp);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_pack<float>(const void*, void*, int, int, int, int, int, int, int, int, cudaStream_t);
+template cudaError_t launch_pack<double>(const void*, void*, int, int, int, int, int, int, int, int, cudaStream_t);
+template cudaError_t launch_unpack<float>(const void*, void*, int, int, int, int, int, int, int, int, cudaStream_t);
+template cudaError_t launch_unpack<double>(const void*, void*, int, int, int, int, int, int, int, int, cudaStream_t);
 
 template cudaError_t launch_count_nonfinite<float>(const void*, long long, void*, unsigned long long*, cudaStream_t);
 template cudaError_t launch_count_nonfinite<double>(const void*, long long, void*, unsigned long long*, cudaStream_t);

@@ -36,6 +36,17 @@ constexpr int ZM_BX = 40;   // TMA box width in elements
 constexpr int ZM_XOFF = 4;  // box column of global x0
 constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s bound on any barrier wait
 
+// Staged boxes of the state fields Q (halo 2) and rho u (halo 1), 40 wide with
+// x0 at column 4 (a 16-byte aligned start): from the flat fields (batches) or
+// from their padded mirrors (single lattices; site x at mirror column x + 8,
+// y at row y + 2 (Q) or y + 1 (rho u)), whose ghosts hold the periodic images.
+// QPX, QPY, UPX, UPY: the mirror offsets of a site (0 for flat fields).
+template <bool PAD>
+struct StateBox {
+  static constexpr int QW = ZM_BX, QX = ZM_XOFF, QPX = PAD ? kZmMirX : 0, QPY = PAD ? 2 : 0;
+  static constexpr int UW = ZM_BX, UX = ZM_XOFF, UPX = PAD ? kZmMirX : 0, UPY = PAD ? 1 : 0;
+};
+
 __host__ __device__ constexpr int align_elems(int elems, int esize) {
   // round an element count up so that it spans a multiple of 128 bytes
   return ((elems * esize + 127) / 128) * 128 / esize;
@@ -200,11 +211,12 @@ __device__ __forceinline__ Model<V> widen(const Model<real>& m) {
 // ---------------------------------------------------------------------------
 // Kernel A: H, sigma, tau, b and the Heun predictor
 // ---------------------------------------------------------------------------
-template <typename real, int TY>
+template <typename real, int TY, bool PAD>
 struct QsideSmem {
+  using B = StateBox<PAD>;
   static constexpr int QROWS = TY + 4, UROWS = TY + 2, TROWS = TY + 2, TCOLS = ZM_TX + 2;
   static constexpr int QSLOTS = 5, USLOTS = 4;
-  static constexpr int QCS = QROWS * ZM_BX, UCS = UROWS * ZM_BX;  // per-component strides
+  static constexpr int QCS = QROWS * B::QW, UCS = UROWS * B::UW;  // per-component strides
   static constexpr int QSLOT = align_elems(5 * QCS, sizeof(real)), USLOT = align_elems(4 * UCS, sizeof(real));
   // own cells of a plane: H (5 components) then sigma_LC (5)
   static constexpr int TSLOT = 3 * TROWS * TCOLS, HSLOT = 10 * TY * ZM_TX;
@@ -233,7 +245,9 @@ __device__ __forceinline__ void qside_body(const CUtensorMap* tmQ, const CUtenso
                                            const Model<real> m, int bt, int rc, const real* __restrict__ Q,
                                            const real* __restrict__ rhou, const real* __restrict__ bext,
                                            real* __restrict__ pq, int* __restrict__ err, const Sym5<real> qw) {
-  using L = QsideSmem<real, TY>;
+  constexpr bool PAD = !BATCH;  // a single lattice stages its padded mirrors: no patching
+  using L = QsideSmem<real, TY, PAD>;
+  using B = StateBox<PAD>;
   using V = typename LaneT<real, SPT>::V;
   constexpr int TYH = TY / SPT;  // rows handled by one pass of the CTA
   static_assert(TY % SPT == 0 && (TY + 2) % SPT == 0, "tile rows must split evenly between the lanes");
@@ -279,13 +293,13 @@ __device__ __forceinline__ void qside_body(const CUtensorMap* tmQ, const CUtenso
     const unsigned k = p - (z0 - 2);
     uint64_t* bar = &bars[k % L::QSLOTS];
     mbar_arrive_expect_tx(bar, qbytes);
-    zm_load<BATCH>(qslot(p), tmQ, x0 - ZM_XOFF, y0 - 2, wrap(p, nz), rc, bar);
+    zm_load<BATCH>(qslot(p), tmQ, x0 - B::QX + B::QPX, y0 - 2 + B::QPY, wrap(p, nz), rc, bar);
   };
   auto issue_u = [&](int p) {
     const unsigned k = p - (z0 - 1);
     uint64_t* bar = &bars[L::QSLOTS + k % L::USLOTS];
     mbar_arrive_expect_tx(bar, ubytes);
-    zm_load<BATCH>(uslot(p), tmU, x0 - ZM_XOFF, y0 - 1, wrap(p, nz), rc, bar);
+    zm_load<BATCH>(uslot(p), tmU, x0 - B::UX + B::UPX, y0 - 1 + B::UPY, wrap(p, nz), rc, bar);
   };
   // Wait for a plane.  Every thread reaches the __syncthreads that follows a
   // wait, so a timeout cannot strand part of the CTA.
@@ -306,18 +320,18 @@ __device__ __forceinline__ void qside_body(const CUtensorMap* tmQ, const CUtenso
   // patch_item returns its value and its index in shared memory.
   const Frame<L::QROWS, 2, ZM_TX + 6, 2, true> FQ(nx, ny, x0, y0 - 2);
   const Frame<L::UROWS, 3, ZM_TX + 5, 1, true> FU(nx, ny, x0, y0 - 1);
-  const int items_q = edge_q ? FQ.cells() * 5 : 0, items = items_q + (edge_u ? FU.cells() * 4 : 0);
+  const int items_q = !PAD && edge_q ? FQ.cells() * 5 : 0, items = items_q + (!PAD && edge_u ? FU.cells() * 4 : 0);
   auto patch_item = [&](int t, int pq, int pu, int& dst) -> real {
     int r, c;
     if (t < items_q) {
       const int cell = t / 5, k = t - 5 * cell;
       FQ.cell(cell, r, c);
-      dst = (int)(qslot(pq) - base) + (k * L::QROWS + r) * ZM_BX + c;
+      dst = (int)(qslot(pq) - base) + (k * L::QROWS + r) * B::QW + c;
       return Q[k * n + image_site(r, c, nx, ny, wrap(pq, nz), xw, yw)];
     }
     const int u = t - items_q, cell = u / 4, k = u - 4 * cell;
     FU.cell(cell, r, c);
-    dst = (int)(uslot(pu) - base) + (k * L::UROWS + r) * ZM_BX + c;
+    dst = (int)(uslot(pu) - base) + (k * L::UROWS + r) * B::UW + c;
     return rhou[k * n + image_site(r, c, nx, ny, wrap(pu, nz), xw, yw + 1)];
   };
   // a staged Q plane beyond a wall: qw in every cell (no periodic images)
@@ -389,13 +403,13 @@ __device__ __forceinline__ void qside_body(const CUtensorMap* tmQ, const CUtenso
         }
       }
       if (r >= 0) {
-        const int i0 = (r + 1) * ZM_BX + (c + 3);  // position in the Q box
+        const int i0 = (r + 1) * B::QW + (c + B::QX - 1);  // position in the Q box
         Stencil7<V> st;
         st.c = ld5v<1>(qc, L::QCS, i0, i0);
         st.xm = ld5v<1>(qc, L::QCS, i0 - 1, i0 - 1);
         st.xp = ld5v<1>(qc, L::QCS, i0 + 1, i0 + 1);
-        st.ym = ld5v<1>(qc, L::QCS, i0 - ZM_BX, i0 - ZM_BX);
-        st.yp = ld5v<1>(qc, L::QCS, i0 + ZM_BX, i0 + ZM_BX);
+        st.ym = ld5v<1>(qc, L::QCS, i0 - B::QW, i0 - B::QW);
+        st.yp = ld5v<1>(qc, L::QCS, i0 + B::QW, i0 + B::QW);
         st.zm = ld5v<1>(qm, L::QCS, i0, i0);
         st.zp = ld5v<1>(qp, L::QCS, i0, i0);
         Sym5<V> dq[3];
@@ -428,14 +442,14 @@ __device__ __forceinline__ void qside_body(const CUtensorMap* tmQ, const CUtenso
     constexpr int RH = L::TROWS / SPT;
     for (int t = threadIdx.x; t < RH * L::TCOLS; t += blockDim.x) {
       const int r0 = t / L::TCOLS, c = t % L::TCOLS;
-      const int i0 = (r0 + 1) * ZM_BX + (c + 3);  // position in the Q box
-      const int i1 = i0 + RH * ZM_BX;
+      const int i0 = (r0 + 1) * B::QW + (c + B::QX - 1);  // position in the Q box
+      const int i1 = i0 + RH * B::QW;
       Stencil7<V> st;
       st.c = ld5v<SPT>(qc, L::QCS, i0, i1);
       st.xm = ld5v<SPT>(qc, L::QCS, i0 - 1, i1 - 1);
       st.xp = ld5v<SPT>(qc, L::QCS, i0 + 1, i1 + 1);
-      st.ym = ld5v<SPT>(qc, L::QCS, i0 - ZM_BX, i1 - ZM_BX);
-      st.yp = ld5v<SPT>(qc, L::QCS, i0 + ZM_BX, i1 + ZM_BX);
+      st.ym = ld5v<SPT>(qc, L::QCS, i0 - B::QW, i1 - B::QW);
+      st.yp = ld5v<SPT>(qc, L::QCS, i0 + B::QW, i1 + B::QW);
       st.zm = ld5v<SPT>(qm, L::QCS, i0, i1);
       st.zp = ld5v<SPT>(qp, L::QCS, i0, i1);
       Sym5<V> dq[3];
@@ -539,7 +553,7 @@ __device__ __forceinline__ void qside_body(const CUtensorMap* tmQ, const CUtenso
       const real* qm = qslot(z - 1);
       const real* qc = qslot(z);
       const real* qp = qslot(z + 1);
-      const int qi0 = (ty + 2) * ZM_BX + (tx + ZM_XOFF), qi1 = qi0 + TYH * ZM_BX;
+      const int qi0 = (ty + 2) * B::QW + (tx + B::QX), qi1 = qi0 + TYH * B::QW;
       const Sym5<V> q = ld5v<SPT>(qc, L::QCS, qi0, qi1);
       Sym5<V> dq[3], h;
       if constexpr (SPT == 1 && !BATCH) {  // (a batch CTA has no registers to spare for the carry)
@@ -550,8 +564,8 @@ __device__ __forceinline__ void qside_body(const CUtensorMap* tmQ, const CUtenso
         h = ld5v<SPT>(hslot(z), TY * ZM_TX, hi0, hi0);
       } else {
         dq[0] = half_diff(ld5v<SPT>(qc, L::QCS, qi0 + 1, qi1 + 1), ld5v<SPT>(qc, L::QCS, qi0 - 1, qi1 - 1));
-        dq[1] = half_diff(ld5v<SPT>(qc, L::QCS, qi0 + ZM_BX, qi1 + ZM_BX),
-                          ld5v<SPT>(qc, L::QCS, qi0 - ZM_BX, qi1 - ZM_BX));
+        dq[1] = half_diff(ld5v<SPT>(qc, L::QCS, qi0 + B::QW, qi1 + B::QW),
+                          ld5v<SPT>(qc, L::QCS, qi0 - B::QW, qi1 - B::QW));
         dq[2] = half_diff(ld5v<SPT>(qp, L::QCS, qi0, qi1), ld5v<SPT>(qm, L::QCS, qi0, qi1));
         const int hi0 = ty * ZM_TX + tx;
         h = ld5v<SPT>(hslot(z), TY * ZM_TX, hi0, hi0 + TYH * ZM_TX);
@@ -575,14 +589,14 @@ __device__ __forceinline__ void qside_body(const CUtensorMap* tmQ, const CUtenso
       const real* um = uslot(z - 1);
       const real* uc = uslot(z);
       const real* up = uslot(z + 1);
-      const int u0 = (ty + 1) * ZM_BX + (tx + ZM_XOFF), u1 = u0 + TYH * ZM_BX;
+      const int u0 = (ty + 1) * B::UW + (tx + B::UX), u1 = u0 + TYH * B::UW;
       V u[3], w[3][3];
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
         const int o = (a + 1) * L::UCS;
         u[a] = vld<SPT>(uc, o + u0, o + u1);
         w[a][0] = half * (vld<SPT>(uc, o + u0 + 1, o + u1 + 1) - vld<SPT>(uc, o + u0 - 1, o + u1 - 1));
-        w[a][1] = half * (vld<SPT>(uc, o + u0 + ZM_BX, o + u1 + ZM_BX) - vld<SPT>(uc, o + u0 - ZM_BX, o + u1 - ZM_BX));
+        w[a][1] = half * (vld<SPT>(uc, o + u0 + B::UW, o + u1 + B::UW) - vld<SPT>(uc, o + u0 - B::UW, o + u1 - B::UW));
         V upz = vld<SPT>(up, o + u0, o + u1), umz = vld<SPT>(um, o + u0, o + u1);
         if (WALLS && z == 0) umz = -u[a];  // no slip half a spacing beyond the wall
         if (WALLS && z == nz - 1) upz = -u[a];
@@ -747,14 +761,46 @@ __global__ void __launch_bounds__(qside_threads<TY, 1>(), sizeof(real) == 4 ? 2 
                                        pq + pq0 + (long long)it.j * kZmPQ * G.cp, err, Sym5<real>{});
 }
 
+// Lane k's values v[0 .. C) of site (gx, gy, z) into a padded mirror (site x
+// at column x + px, y at row y + h; components cs apart, rows of nxm, nym rows
+// per plane) whose h ghost columns and rows next to the lattice hold periodic
+// images: at the site's position, and at each ghost position whose image the
+// site is (lattice faces only; nx >= 2h gives a site at most one x image).
+template <int C, int SPT, typename real, typename V>
+__device__ __forceinline__ void put_mirror(real* __restrict__ m, long long cs, int nxm, int nym, int px, int h,
+                                           int nx, int ny, int z, int gx, int gy, const V* v, int k) {
+  auto put1 = [&](int X, int Y) {
+    real* d = m + ((long long)z * nym + Y) * nxm + X;
+#pragma unroll
+    for (int c = 0; c < C; ++c) d[c * cs] = lane<SPT, real>(v[c], k);
+  };
+  const int X = gx + px, Y = gy + h;
+  put1(X, Y);
+  if (gx >= h && gx < nx - h && gy >= h && gy < ny - h) return;
+  // x = nx + gx (site gx < h) or x = gx - nx (site gx >= nx - h)
+  const int xg = gx < h ? nx + px + gx : (gx >= nx - h ? gx - nx + px : -1);
+  if (xg >= 0) put1(xg, Y);
+  for (int g = 0; g < h; ++g) {  // ghost rows y = g - h and y = ny + g (several when ny < 2h)
+    const int ya = wrap(g - h, ny) == gy ? g : -1, yb = wrap(ny + g, ny) == gy ? ny + h + g : -1;
+    if (ya >= 0) {
+      put1(X, ya);
+      if (xg >= 0) put1(xg, ya);
+    }
+    if (yb >= 0) {
+      put1(X, yb);
+      if (xg >= 0) put1(xg, yb);
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Kernel B: LB predictor-corrector and the Heun corrector
 // ---------------------------------------------------------------------------
-template <typename real, int TY>
+template <typename real, int TY, bool PAD>
 struct LbqSmem {
   static constexpr int ROWS = TY + 2, SLOTS = 4;
-  static constexpr int CSA = ROWS * kZmBoxXP;  // per-component stride of the P / Q* box (padded scratch)
-  static constexpr int CSU = ROWS * ZM_BX;     // per-component stride of the u box (rho u components 1..3)
+  static constexpr int CSA = ROWS * kZmBoxXP;           // per-component stride of the P / Q* box (padded scratch)
+  static constexpr int CSU = ROWS * StateBox<PAD>::UW;  // per-component stride of the u box (rho u components 1..3)
   // one slot: [P 10 | Q* 5] then [u_x u_y u_z], each group 128-byte aligned
   static constexpr int OFF_QS = 10 * CSA;
   static constexpr int OFF_U = align_elems(kZmPQ * CSA, sizeof(real));
@@ -777,7 +823,9 @@ __device__ __forceinline__ void lbq_body(const CUtensorMap* tmPQ, const CUtensor
                                          const real* __restrict__ rhou, const real* __restrict__ Qin,
                                          real* __restrict__ fnew, real* __restrict__ rhou_new,
                                          real* __restrict__ Qout, int* __restrict__ err, const Sym5<real> qw) {
-  using L = LbqSmem<real, TY>;
+  constexpr bool PAD = !BATCH;  // a single lattice reads and writes the padded mirrors of Q and rho u
+  using L = LbqSmem<real, TY, PAD>;
+  using B = StateBox<PAD>;
   using V = typename LaneT<real, SPT>::V;
   constexpr int TYH = TY / SPT;  // a thread takes rows ty + k * TYH, k < SPT
   constexpr int AW = kZmBoxXP;
@@ -831,12 +879,12 @@ __device__ __forceinline__ void lbq_body(const CUtensorMap* tmPQ, const CUtensor
     const int zz = wrap(p, nz);
     mbar_arrive_expect_tx(bar, L::TX_BYTES);
     zm_load<BATCH>(sl, tmPQ, x0, y0, zz, rc, bar);
-    zm_load<BATCH>(sl + L::OFF_U, tmU3, x0 - ZM_XOFF, y0 - 1, zz, rc, bar);
+    zm_load<BATCH>(sl + L::OFF_U, tmU3, x0 - B::UX + B::UPX, y0 - 1 + B::UPY, zz, rc, bar);
     if constexpr (!BATCH) {
       // the populations of plane p (pulled from plane p-1 on) and Q^n of plane
       // p-1, into L2 a plane ahead of their plain loads
       tma_prefetch_l2_4d(tmF, x0 - ZM_XOFF, y0 - 1, zz, 0);
-      tma_prefetch_l2_4d(tmQ, x0 - ZM_XOFF, y0 - 2, wrap(p - 1, nz), 0);
+      tma_prefetch_l2_4d(tmQ, x0 - B::QX + B::QPX, y0 - 2 + B::QPY, wrap(p - 1, nz), 0);
     }
   };
   auto wait = [&](int p) {
@@ -849,13 +897,13 @@ __device__ __forceinline__ void lbq_body(const CUtensorMap* tmPQ, const CUtensor
   // frame cell t / 3 of plane p.  patch_item returns its value and its index
   // in the ring.
   const Frame<L::ROWS, 3, ZM_TX + 5, 1, true> F(nx, ny, x0, y0 - 1);
-  const int items = edge ? F.cells() * 3 : 0;
+  const int items = !PAD && edge ? F.cells() * 3 : 0;
   const bool small_frame = items <= (int)blockDim.x;  // one value per thread in the loop
   auto patch_item = [&](int t, int p, int& dst) -> real {
     const int cell = t / 3, k = t - 3 * cell;
     int r, c;
     F.cell(cell, r, c);
-    dst = (int)(slot(p) - ring) + L::OFF_U + (k * L::ROWS + r) * ZM_BX + c;
+    dst = (int)(slot(p) - ring) + L::OFF_U + (k * L::ROWS + r) * B::UW + c;
     return rhou[(k + 1) * n + image_site(r, c, nx, ny, wrap(p, nz), xw, yw)];
   };
   // a staged plane beyond a wall: only its Q* is read (the anchored qw)
@@ -880,7 +928,7 @@ __device__ __forceinline__ void lbq_body(const CUtensorMap* tmPQ, const CUtensor
     return vld<SPT>(sl, k * L::CSA + idx, k * L::CSA + idx + TYH * AW);
   };
   auto UB = [&](const real* sl, int k, int idx) {
-    return vld<SPT>(sl, L::OFF_U + k * L::CSU + idx, L::OFF_U + k * L::CSU + idx + TYH * ZM_BX);
+    return vld<SPT>(sl, L::OFF_U + k * L::CSU + idx, L::OFF_U + k * L::CSU + idx + TYH * B::UW);
   };
   // acc +/- v by the sign of e (compile-time after unrolling)
   auto acc = [](V& a, int e, V v) {
@@ -931,7 +979,8 @@ __device__ __forceinline__ void lbq_body(const CUtensorMap* tmPQ, const CUtensor
             {((long long)zm * ny + ym[k]) * nx, ((long long)zm * ny + gy[k]) * nx, ((long long)zm * ny + yp[k]) * nx},
             {((long long)z * ny + ym[k]) * nx, ((long long)z * ny + gy[k]) * nx, ((long long)z * ny + yp[k]) * nx},
             {((long long)zp * ny + ym[k]) * nx, ((long long)zp * ny + gy[k]) * nx, ((long long)zp * ny + yp[k]) * nx}};
-        dl[k] = __ldg(rhou + rb[1][1] + gx);
+        if constexpr (PAD) dl[k] = __ldg(rhou + ((long long)z * G.nyu + gy[k] + B::UPY) * G.nxm + gx + B::UPX);
+        else dl[k] = __ldg(rhou + rb[1][1] + gx);
 #pragma unroll
         for (int i = 0; i < NV; ++i) {
           const int sx = ex(i) > 0 ? xm : ex(i) < 0 ? xp : gx;
@@ -1000,7 +1049,7 @@ __device__ __forceinline__ void lbq_body(const CUtensorMap* tmPQ, const CUtensor
       const real* nc = slot(z);
       const real* np = slot(z + 1);
       const int ca = (ty + 1) * AW + (tx + 1);          // the site in the P / Q* box
-      const int cu = (ty + 1) * ZM_BX + (tx + ZM_XOFF); // the site in the u box
+      const int cu = (ty + 1) * B::UW + (tx + B::UX);   // the site in the u box
       V fin[NV], ds[NV], dh[NV];
 #pragma unroll
       for (int i = 0; i < NV; ++i) {
@@ -1098,10 +1147,15 @@ __device__ __forceinline__ void lbq_body(const CUtensorMap* tmPQ, const CUtensor
 #pragma unroll
       for (int k = 0; k < SPT; ++k) {
         if (!lane_ok[k]) continue;
-        rhou_new[s[k]] = lane<SPT, real>(dr1, k);
-        rhou_new[n + s[k]] = lane<SPT, real>(u1x, k);
-        rhou_new[2 * n + s[k]] = lane<SPT, real>(u1y, k);
-        rhou_new[3 * n + s[k]] = lane<SPT, real>(u1z, k);
+        if constexpr (PAD) {
+          const V ru[4] = {dr1, u1x, u1y, u1z};
+          put_mirror<4, SPT, real>(rhou_new, G.cu, G.nxm, G.nyu, B::UPX, 1, nx, ny, z, gx, gy[k], ru, k);
+        } else {
+          rhou_new[s[k]] = lane<SPT, real>(dr1, k);
+          rhou_new[n + s[k]] = lane<SPT, real>(u1x, k);
+          rhou_new[2 * n + s[k]] = lane<SPT, real>(u1y, k);
+          rhou_new[3 * n + s[k]] = lane<SPT, real>(u1z, k);
+        }
       }
 
       // Heun corrector with u^n
@@ -1124,25 +1178,41 @@ __device__ __forceinline__ void lbq_body(const CUtensorMap* tmPQ, const CUtensor
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
         w[a][0] = half * (UB(nc, a, cu + 1) - UB(nc, a, cu - 1));
-        w[a][1] = half * (UB(nc, a, cu + ZM_BX) - UB(nc, a, cu - ZM_BX));
+        w[a][1] = half * (UB(nc, a, cu + B::UW) - UB(nc, a, cu - B::UW));
         V upz = UB(np, a, cu), umz = UB(nm, a, cu);
         if (wl) umz = -u_y[a];  // no slip half a spacing beyond the wall
         if (wh) upz = -u_y[a];
         w[a][2] = half * (upz - umz);
       }
       const Sym5<V> r = be_rate(st.c, h, dq, u_y, w, mv, true);
+      // Q^n of the site: the flat field, or the Q mirror (two ghosts each side)
+      long long sq[SPT];
+      long long qcs = n;
+#pragma unroll
+      for (int k = 0; k < SPT; ++k) {
+        if constexpr (PAD) sq[k] = ((long long)z * G.nyq + gy[k] + B::QPY) * G.nxm + gx + B::QPX;
+        else sq[k] = s[k];
+      }
+      if constexpr (PAD) qcs = G.cq;
       Sym5<V> q0;
-      q0.xx = vld<SPT>(Qin, s[0], s[SPT - 1]);
-      q0.xy = vld<SPT>(Qin, n + s[0], n + s[SPT - 1]);
-      q0.xz = vld<SPT>(Qin, 2 * n + s[0], 2 * n + s[SPT - 1]);
-      q0.yy = vld<SPT>(Qin, 3 * n + s[0], 3 * n + s[SPT - 1]);
-      q0.yz = vld<SPT>(Qin, 4 * n + s[0], 4 * n + s[SPT - 1]);
+      q0.xx = vld<SPT>(Qin, sq[0], sq[SPT - 1]);
+      q0.xy = vld<SPT>(Qin, qcs + sq[0], qcs + sq[SPT - 1]);
+      q0.xz = vld<SPT>(Qin, 2 * qcs + sq[0], 2 * qcs + sq[SPT - 1]);
+      q0.yy = vld<SPT>(Qin, 3 * qcs + sq[0], 3 * qcs + sq[SPT - 1]);
+      q0.yz = vld<SPT>(Qin, 4 * qcs + sq[0], 4 * qcs + sq[SPT - 1]);
       const Sym5<V> q1 = {half * (q0.xx + st.c.xx + r.xx), half * (q0.xy + st.c.xy + r.xy),
                           half * (q0.xz + st.c.xz + r.xz), half * (q0.yy + st.c.yy + r.yy),
                           half * (q0.yz + st.c.yz + r.yz)};
 #pragma unroll
-      for (int k = 0; k < SPT; ++k)
-        if (lane_ok[k]) store5_lane<SPT, real>(Qout, n, s[k], q1, k);
+      for (int k = 0; k < SPT; ++k) {
+        if (!lane_ok[k]) continue;
+        if constexpr (PAD) {
+          const V qv[5] = {q1.xx, q1.xy, q1.xz, q1.yy, q1.yz};
+          put_mirror<5, SPT, real>(Qout, G.cq, G.nxm, G.nyq, B::QPX, 2, nx, ny, z, gx, gy[k], qv, k);
+        } else {
+          store5_lane<SPT, real>(Qout, n, s[k], q1, k);
+        }
+      }
     };
     if (valid) {
       if (WALLS && (wlo || whi)) plane_work(std::true_type{});
@@ -1218,10 +1288,10 @@ template <typename real, int SPT, bool WALLS>
 cudaError_t zm_prepare_spt() {
   constexpr int TY = zm_ty<real>();
   cudaError_t e = cudaFuncSetAttribute(k_qside<real, TY, SPT, WALLS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)QsideSmem<real, TY>::bytes);
+                                       (int)QsideSmem<real, TY, true>::bytes);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_lbq<real, TY, SPT, WALLS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)LbqSmem<real, TY>::bytes);
+                             (int)LbqSmem<real, TY, true>::bytes);
   return e;
 }
 
@@ -1246,7 +1316,7 @@ int zm_resident_spt() {
   constexpr int TY = zm_ty<real>();
   int n = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_lbq<real, TY, SPT, false>, ZM_TX * TY / SPT,
-                                                    LbqSmem<real, TY>::bytes) != cudaSuccess)
+                                                    LbqSmem<real, TY, true>::bytes) != cudaSuccess)
     n = 1;
   return n > 0 ? n : 1;
 }
@@ -1271,6 +1341,11 @@ ZmGeom zm_geom(int nx, int ny, int nz, int zc, int ty) {
   G.nxp = nx + kZmPadX;
   G.nyp = ny + 2;
   G.cp = (long long)G.nxp * G.nyp * nz;
+  G.nxm = nx + 2 * kZmMirX;
+  G.nyq = ny + 4;
+  G.nyu = ny + 2;
+  G.cq = (long long)G.nxm * G.nyq * nz;
+  G.cu = (long long)G.nxm * G.nyu * nz;
   return G;
 }
 
@@ -1283,11 +1358,11 @@ cudaError_t launch_step_zm_spt(const ZmArgs& a, cudaStream_t s) {
   Sym5<real> qw{};
   if (WALLS) qw = {(real)a.q_wall[0], (real)a.q_wall[1], (real)a.q_wall[2], (real)a.q_wall[3], (real)a.q_wall[4]};
   if (a.events) cudaEventRecord(a.events[0], s);
-  k_qside<real, TY, SQ, WALLS><<<grid, qside_threads<TY, SQ>(), QsideSmem<real, TY>::bytes, s>>>(
+  k_qside<real, TY, SQ, WALLS><<<grid, qside_threads<TY, SQ>(), QsideSmem<real, TY, true>::bytes, s>>>(
       *a.tm_q, *a.tm_u, G, m, static_cast<const real*>(a.q), static_cast<const real*>(a.rhou),
       static_cast<const real*>(a.bext), static_cast<real*>(a.pq), a.err, qw);
   if (a.events) cudaEventRecord(a.events[1], s);
-  k_lbq<real, TY, SPT, WALLS><<<grid, ZM_TX * TY / SPT, LbqSmem<real, TY>::bytes, s>>>(
+  k_lbq<real, TY, SPT, WALLS><<<grid, ZM_TX * TY / SPT, LbqSmem<real, TY, true>::bytes, s>>>(
       *a.tm_pq, *a.tm_u3, *a.tm_f, *a.tm_q, G, m, static_cast<const real*>(a.f), static_cast<const real*>(a.rhou),
       static_cast<const real*>(a.q), static_cast<real*>(a.fnew), static_cast<real*>(a.rhou_new),
       static_cast<real*>(a.qout ? a.qout : a.q), a.err, qw);
@@ -1312,10 +1387,10 @@ template <typename real>
 cudaError_t zm_batch_prepare() {
   constexpr int TY = zm_ty<real>();
   cudaError_t e = cudaFuncSetAttribute(k_qside_batch<real, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)QsideSmem<real, TY>::bytes);
+                                       (int)QsideSmem<real, TY, false>::bytes);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_lbq_batch<real, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)LbqSmem<real, TY>::bytes);
+                             (int)LbqSmem<real, TY, false>::bytes);
   return e;
 }
 
@@ -1324,10 +1399,10 @@ cudaError_t launch_step_zm_batch(const ZmBatchArgs& a, cudaStream_t s) {
   constexpr int TY = zm_ty<real>();
   const int grid = a.B.total_ctas;
   const auto* reps = static_cast<const Replica<real>*>(a.reps);
-  k_qside_batch<real, TY><<<grid, qside_threads<TY, 1>(), QsideSmem<real, TY>::bytes, s>>>(
+  k_qside_batch<real, TY><<<grid, qside_threads<TY, 1>(), QsideSmem<real, TY, false>::bytes, s>>>(
       *a.maps, a.B, reps, a.order, static_cast<const real*>(a.q), static_cast<const real*>(a.rhou),
       static_cast<real*>(a.pq), a.err);
-  k_lbq_batch<real, TY><<<grid, ZM_TX * TY, LbqSmem<real, TY>::bytes, s>>>(
+  k_lbq_batch<real, TY><<<grid, ZM_TX * TY, LbqSmem<real, TY, false>::bytes, s>>>(
       *a.maps, a.B, reps, a.order, static_cast<const real*>(a.f), static_cast<const real*>(a.rhou),
       static_cast<const real*>(a.q), static_cast<real*>(a.fnew), static_cast<real*>(a.rhou_new),
       static_cast<real*>(a.qout ? a.qout : a.q), a.err);
