@@ -261,7 +261,7 @@ Layout layout(int nx, int ny, int nz, int dtype) {
   L.off[15] = o;  // partials + out
   o = align256(o + (kDiagPartials + 8) * 8);
   // padded mirrors of Q and rho u [0], [1] (lattices the fast path can serve)
-  const bool fast_shape = nx % 4 == 0;
+  const bool fast_shape = zm_shape_ok(nx, ny, nz);
   L.off[16] = o;
   o = align256(o + (fast_shape ? (size_t)zm_qmirror_elems(nx, ny, nz) * es : 0));
   L.off[17] = o;
@@ -384,7 +384,7 @@ bool make_padded_tmap(CUtensorMap* tm, void* base, int comps, int nxm, int nym, 
   return encode_tiled(tm, base, 4, dims, strides, box, dtype);
 }
 
-bool fast_shape_ok(const lcbp_lattice* h) { return h->nx % 4 == 0; }
+bool fast_shape_ok(const lcbp_lattice* h) { return zm_shape_ok(h->nx, h->ny, h->nz); }
 
 bool use_fast(lcbp_lattice* h) {
   if (h->path_req == LCBP_PATH_GENERIC || !h->p.flow_on || h->p.coupling != LCBP_JACOBI || !fast_shape_ok(h) ||

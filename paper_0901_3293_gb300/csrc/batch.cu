@@ -510,7 +510,7 @@ int lcbp_batch_create(int R, const int* dims, const lcbp_params* params, int dty
       c.rep0 = (int)b->order.size();
       c.count = (int)members[k].size();
     }
-    if (b->nx[q] % 4 != 0) b->fast_ok = false;
+    if (!zm_shape_ok(b->nx[q], b->ny[q], b->nz[q])) b->fast_ok = false;
     for (int r : members[k]) {
       b->order.push_back(r);
       b->base[r] = tot;

@@ -378,45 +378,38 @@ __device__ __forceinline__ Sym5<real> be_rate(const Sym5<real>& q, const Sym5<re
   if (!flow) return r;
   const real xi = m.xi;
   const Mat3<real> Q = full(q);
-  real D[3][3], O[3][3], P[3][3];
+  // S = xi (D P + P D) + (O P - P O) - 2 xi P Tr(QW), with D and O the
+  // symmetric and antisymmetric parts of W and P = Q + I/3.  With
+  // A = xi D + O, i.e. A_ab = ((xi + 1) W_ab + (xi - 1) W_ba) / 2, the first two
+  // terms are A P + (A P)^T, and A P = A Q + A / 3, so only A Q is a product.
+  // Tr S = (2 xi / 3) Tr D exactly (Tr P = 1, Tr(A Q) = Q:D = Tr(QW)), which the
+  // traceless projection removes from the diagonal.
+  const real cpl = real(0.5) * (xi + real(1)), cmi = real(0.5) * (xi - real(1));
+  real A[3][3];
 #pragma unroll
   for (int a = 0; a < 3; ++a)
 #pragma unroll
-    for (int b = 0; b < 3; ++b) {
-      D[a][b] = real(0.5) * (w[a][b] + w[b][a]);
-      O[a][b] = real(0.5) * (w[a][b] - w[b][a]);
-      P[a][b] = a == b ? Q.a[a][b] + LCBP_Q(1, 3) : Q.a[a][b];
-    }
-  real trQW = real(0);
-#pragma unroll
-  for (int a = 0; a < 3; ++a)
-#pragma unroll
-    for (int b = 0; b < 3; ++b) trQW += Q.a[a][b] * w[b][a];
-  // S = xi (D P + P D) + (O P - P O) - 2 xi P Tr(QW); only the five
-  // independent entries are formed.  Its trace is (2 xi / 3) Tr D exactly
-  // (Tr P = 1, Tr(DP) = Q:D + Tr D / 3), which the traceless projection removes.
+    for (int b = 0; b < 3; ++b) A[a][b] = a == b ? xi * w[a][a] : cpl * w[a][b] + cmi * w[b][a];
+  const real trQW = Q.a[0][0] * w[0][0] + Q.a[1][1] * w[1][1] + Q.a[2][2] * w[2][2] +
+                    Q.a[0][1] * (w[0][1] + w[1][0]) + Q.a[0][2] * (w[0][2] + w[2][0]) +
+                    Q.a[1][2] * (w[1][2] + w[2][1]);
+  auto AQ = [&](int a, int b) { return A[a][0] * Q.a[0][b] + A[a][1] * Q.a[1][b] + A[a][2] * Q.a[2][b]; };
+  const real two_xi_tr = real(2) * xi * trQW;
+  const real xi3 = LCBP_Q(1, 3) * xi;
+  // diagonal: 2 (AQ)_aa + (2 xi / 3) W_aa - 2 xi (Q_aa + 1/3) Tr(QW) - (2 xi / 9) Tr W
+  const real diag0 = LCBP_Q(2, 9) * xi * (w[0][0] + w[1][1] + w[2][2]) + LCBP_Q(1, 3) * two_xi_tr;
   real S[3][3];
-#pragma unroll
-  for (int a = 0; a < 2; ++a)
-#pragma unroll
-    for (int b = a; b < 3; ++b) {
-      real dp = real(0), pd = real(0), op = real(0), po = real(0);
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        dp += D[a][c] * P[c][b];
-        pd += P[a][c] * D[c][b];
-        op += O[a][c] * P[c][b];
-        po += P[a][c] * O[c][b];
-      }
-      S[a][b] = xi * (dp + pd) + (op - po) - real(2) * xi * P[a][b] * trQW;
-    }
-  const real trS3 = LCBP_Q(2, 9) * xi * (D[0][0] + D[1][1] + D[2][2]);
+  S[0][0] = real(2) * (AQ(0, 0) + xi3 * w[0][0]) - two_xi_tr * Q.a[0][0] - diag0;
+  S[1][1] = real(2) * (AQ(1, 1) + xi3 * w[1][1]) - two_xi_tr * Q.a[1][1] - diag0;
+  S[0][1] = (AQ(0, 1) + AQ(1, 0)) + xi3 * (w[0][1] + w[1][0]) - two_xi_tr * Q.a[0][1];
+  S[0][2] = (AQ(0, 2) + AQ(2, 0)) + xi3 * (w[0][2] + w[2][0]) - two_xi_tr * Q.a[0][2];
+  S[1][2] = (AQ(1, 2) + AQ(2, 1)) + xi3 * (w[1][2] + w[2][1]) - two_xi_tr * Q.a[1][2];
   const real ux = u[0], uy = u[1], uz = u[2];
   auto adv = [&](real gx, real gy, real gz) { return ux * gx + uy * gy + uz * gz; };
-  r.xx += (S[0][0] - trS3) - adv(dq[0].xx, dq[1].xx, dq[2].xx);
+  r.xx += S[0][0] - adv(dq[0].xx, dq[1].xx, dq[2].xx);
   r.xy += S[0][1] - adv(dq[0].xy, dq[1].xy, dq[2].xy);
   r.xz += S[0][2] - adv(dq[0].xz, dq[1].xz, dq[2].xz);
-  r.yy += (S[1][1] - trS3) - adv(dq[0].yy, dq[1].yy, dq[2].yy);
+  r.yy += S[1][1] - adv(dq[0].yy, dq[1].yy, dq[2].yy);
   r.yz += S[1][2] - adv(dq[0].yz, dq[1].yz, dq[2].yz);
   return r;
 }

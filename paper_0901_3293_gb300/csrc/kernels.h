@@ -161,6 +161,16 @@ constexpr int kZmMirX = 8;  // columns added on each side of a mirror row
 inline long long zm_qmirror_elems(int nx, int ny, int nz) { return 5LL * (nx + 2 * kZmMirX) * (ny + 4) * nz; }
 inline long long zm_umirror_elems(int nx, int ny, int nz) { return 4LL * (nx + 2 * kZmMirX) * (ny + 2) * nz; }
 
+// Shapes the fast kernels serve: rows of whole 16-byte groups (nx % 4 == 0 for
+// the TMA boxes) and element offsets within one lattice that fit in 32 bits
+// (the kernels index with int; the largest offsets are those of the 15
+// population or scratch components and of the 5 components of the Q mirror).
+inline bool zm_shape_ok(int nx, int ny, int nz) {
+  const long long n = (long long)nx * ny * nz, cp = (long long)(nx + kZmPadX) * (ny + 2) * nz;
+  const long long cq = (long long)(nx + 2 * kZmMirX) * (ny + 4) * nz, lim = 2147483647LL;
+  return nx % 4 == 0 && 15 * n < lim && 15 * cp < lim && 5 * cq < lim;
+}
+
 struct ZmArgs {
   int nx, ny, nz, zc;
   int spt;            // sites per thread of k_lbq, 1 or 2 (2 only where zm_spt_max allows)

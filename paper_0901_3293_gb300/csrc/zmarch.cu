@@ -126,8 +126,8 @@ __device__ __forceinline__ void fill_wrap_tables(int* xw, int* yw, int rows, int
     else yw[i - ZM_BX] = wrap(gy0 + i - ZM_BX, ny);
   }
 }
-__device__ __forceinline__ long long image_site(int r, int c, int nx, int ny, int gz, const int* xw, const int* yw) {
-  return ((long long)gz * ny + yw[r]) * nx + xw[c];
+__device__ __forceinline__ int image_site(int r, int c, int nx, int ny, int gz, const int* xw, const int* yw) {
+  return (gz * ny + yw[r]) * nx + xw[c];
 }
 
 // TMA tile load of plane z of a field: 4-D (x, y, z, component) for one
@@ -166,7 +166,7 @@ struct LaneT<real, 2> {
 
 // value at element i0 (lane 0) and i1 (lane 1) of a shared or global array
 template <int SPT, typename real>
-__device__ __forceinline__ typename LaneT<real, SPT>::V vld(const real* p, long long i0, long long i1) {
+__device__ __forceinline__ typename LaneT<real, SPT>::V vld(const real* p, int i0, int i1) {
   if constexpr (SPT == 1) return p[i0];
   else return Vec2<real>(p[i0], p[i1], 0);
 }
@@ -186,7 +186,7 @@ __device__ __forceinline__ Sym5<typename LaneT<real, SPT>::V> ld5v(const real* s
   return v;
 }
 template <int SPT, typename real, typename V>
-__device__ __forceinline__ void store5_lane(real* p, long long n, long long s, const Sym5<V>& q, int k) {
+__device__ __forceinline__ void store5_lane(real* p, int n, int s, const Sym5<V>& q, int k) {
   p[s] = lane<SPT, real>(q.xx, k);
   p[n + s] = lane<SPT, real>(q.xy, k);
   p[2 * n + s] = lane<SPT, real>(q.xz, k);
@@ -262,8 +262,10 @@ __device__ __forceinline__ void qside_body(const CUtensorMap* tmQ, const CUtenso
   int* xw = abort_flag + 4;  // wrapped box columns, then rows of the Q box (y0 - 2 ...)
   int* yw = xw + ZM_BX;
 
+  // element offsets within one lattice (or replica) fit in 32 bits: the host
+  // takes this path only where 15 components of every field do
   const int nx = G.nx, ny = G.ny, nz = G.nz;
-  const long long n = G.n;
+  const int n = (int)G.n;
   const int x0 = (bt % G.tiles_x) * ZM_TX;
   const int y0 = ((bt / G.tiles_x) % G.tiles_y) * TY;
   const int z0 = (bt / (G.tiles_x * G.tiles_y)) * G.zc;
@@ -607,14 +609,14 @@ __device__ __forceinline__ void qside_body(const CUtensorMap* tmQ, const CUtenso
       // site's padded position, and at its periodic images in the ghost columns
       // and rows where the site lies on a lattice face.
       const int nxp = G.nxp, nyp = G.nyp;
-      const long long cp = G.cp;
+      const int cp = (int)G.cp;
       auto put = [&](int c0, const V* v, int cnt) {
 #pragma unroll
         for (int k = 0; k < SPT; ++k) {
           const int gy = y0 + ty + k * TYH;
           if (gy >= ny) continue;
           auto put1 = [&](int xx, int yy) {
-            real* d = pq + c0 * cp + ((long long)z * nyp + yy) * nxp + xx;
+            real* d = pq + (c0 * cp + (z * nyp + yy) * nxp + xx);
 #pragma unroll
             for (int c = 0; c < cnt; ++c) d[c * cp] = lane<SPT, real>(v[c], k);
           };
@@ -646,11 +648,11 @@ __device__ __forceinline__ void qside_body(const CUtensorMap* tmQ, const CUtenso
       // corner direction s.
       V bt[3] = {bx, by, bz};
       if (bext) {
-        long long sb[SPT];
+        int sb[SPT];
 #pragma unroll
         for (int k = 0; k < SPT; ++k) {
           const int gyk = y0 + ty + k * TYH;
-          sb[k] = ((long long)z * ny + (gyk < ny ? gyk : y0 + ty)) * nx + gx;
+          sb[k] = (z * ny + (gyk < ny ? gyk : y0 + ty)) * nx + gx;
         }
 #pragma unroll
         for (int a = 0; a < 3; ++a) bt[a] += vld<SPT>(bext, a * n + sb[0], a * n + sb[SPT - 1]);
@@ -767,10 +769,10 @@ __global__ void __launch_bounds__(qside_threads<TY, 1>(), sizeof(real) == 4 ? 2 
 // images: at the site's position, and at each ghost position whose image the
 // site is (lattice faces only; nx >= 2h gives a site at most one x image).
 template <int C, int SPT, typename real, typename V>
-__device__ __forceinline__ void put_mirror(real* __restrict__ m, long long cs, int nxm, int nym, int px, int h,
+__device__ __forceinline__ void put_mirror(real* __restrict__ m, int cs, int nxm, int nym, int px, int h,
                                            int nx, int ny, int z, int gx, int gy, const V* v, int k) {
   auto put1 = [&](int X, int Y) {
-    real* d = m + ((long long)z * nym + Y) * nxm + X;
+    real* d = m + ((z * nym + Y) * nxm + X);
 #pragma unroll
     for (int c = 0; c < C; ++c) d[c * cs] = lane<SPT, real>(v[c], k);
   };
@@ -837,7 +839,7 @@ __device__ __forceinline__ void lbq_body(const CUtensorMap* tmPQ, const CUtensor
   int* yw = xw + ZM_BX;
 
   const int nx = G.nx, ny = G.ny, nz = G.nz;
-  const long long n = G.n;
+  const int n = (int)G.n;  // (32-bit element offsets, as in k_qside)
   const int x0 = (bt % G.tiles_x) * ZM_TX;
   const int y0 = ((bt / G.tiles_x) % G.tiles_y) * TY;
   const int z0 = (bt / (G.tiles_x * G.tiles_y)) * G.zc;
@@ -975,17 +977,16 @@ __device__ __forceinline__ void lbq_body(const CUtensorMap* tmPQ, const CUtensor
 #pragma unroll
       for (int k = 0; k < SPT; ++k) {
         // three row bases per plane: rows y-1, y, y+1 of planes z-1, z, z+1
-        const long long rb[3][3] = {
-            {((long long)zm * ny + ym[k]) * nx, ((long long)zm * ny + gy[k]) * nx, ((long long)zm * ny + yp[k]) * nx},
-            {((long long)z * ny + ym[k]) * nx, ((long long)z * ny + gy[k]) * nx, ((long long)z * ny + yp[k]) * nx},
-            {((long long)zp * ny + ym[k]) * nx, ((long long)zp * ny + gy[k]) * nx, ((long long)zp * ny + yp[k]) * nx}};
-        if constexpr (PAD) dl[k] = __ldg(rhou + ((long long)z * G.nyu + gy[k] + B::UPY) * G.nxm + gx + B::UPX);
-        else dl[k] = __ldg(rhou + rb[1][1] + gx);
+        const int rb[3][3] = {{(zm * ny + ym[k]) * nx, (zm * ny + gy[k]) * nx, (zm * ny + yp[k]) * nx},
+                              {(z * ny + ym[k]) * nx, (z * ny + gy[k]) * nx, (z * ny + yp[k]) * nx},
+                              {(zp * ny + ym[k]) * nx, (zp * ny + gy[k]) * nx, (zp * ny + yp[k]) * nx}};
+        if constexpr (PAD) dl[k] = __ldg(rhou + ((z * G.nyu + gy[k] + B::UPY) * G.nxm + gx + B::UPX));
+        else dl[k] = __ldg(rhou + (rb[1][1] + gx));
 #pragma unroll
         for (int i = 0; i < NV; ++i) {
           const int sx = ex(i) > 0 ? xm : ex(i) < 0 ? xp : gx;
-          if ((ez(i) > 0 && wl) || (ez(i) < 0 && wh)) fin_l[k][i] = __ldg(f + opp(i) * n + rb[1][1] + gx);
-          else fin_l[k][i] = __ldg(f + i * n + rb[1 - ez(i)][1 - ey(i)] + sx);
+          if ((ez(i) > 0 && wl) || (ez(i) < 0 && wh)) fin_l[k][i] = __ldg(f + (opp(i) * n + rb[1][1] + gx));
+          else fin_l[k][i] = __ldg(f + (i * n + rb[1 - ez(i)][1 - ey(i)] + sx));
         }
       }
     };
@@ -1042,9 +1043,9 @@ __device__ __forceinline__ void lbq_body(const CUtensorMap* tmPQ, const CUtensor
     auto plane_work = [&](auto wall_plane) {
       constexpr bool WP = decltype(wall_plane)::value;
       const bool wl = WP && wlo, wh = WP && whi;
-      long long s[SPT];
+      int s[SPT];
 #pragma unroll
-      for (int k = 0; k < SPT; ++k) s[k] = ((long long)z * ny + gy[k]) * nx + gx;
+      for (int k = 0; k < SPT; ++k) s[k] = (z * ny + gy[k]) * nx + gx;
       const real* nm = slot(z - 1);
       const real* nc = slot(z);
       const real* np = slot(z + 1);
@@ -1149,7 +1150,7 @@ __device__ __forceinline__ void lbq_body(const CUtensorMap* tmPQ, const CUtensor
         if (!lane_ok[k]) continue;
         if constexpr (PAD) {
           const V ru[4] = {dr1, u1x, u1y, u1z};
-          put_mirror<4, SPT, real>(rhou_new, G.cu, G.nxm, G.nyu, B::UPX, 1, nx, ny, z, gx, gy[k], ru, k);
+          put_mirror<4, SPT, real>(rhou_new, (int)G.cu, G.nxm, G.nyu, B::UPX, 1, nx, ny, z, gx, gy[k], ru, k);
         } else {
           rhou_new[s[k]] = lane<SPT, real>(dr1, k);
           rhou_new[n + s[k]] = lane<SPT, real>(u1x, k);
@@ -1186,14 +1187,14 @@ __device__ __forceinline__ void lbq_body(const CUtensorMap* tmPQ, const CUtensor
       }
       const Sym5<V> r = be_rate(st.c, h, dq, u_y, w, mv, true);
       // Q^n of the site: the flat field, or the Q mirror (two ghosts each side)
-      long long sq[SPT];
-      long long qcs = n;
+      int sq[SPT];
+      int qcs = n;
 #pragma unroll
       for (int k = 0; k < SPT; ++k) {
-        if constexpr (PAD) sq[k] = ((long long)z * G.nyq + gy[k] + B::QPY) * G.nxm + gx + B::QPX;
+        if constexpr (PAD) sq[k] = (z * G.nyq + gy[k] + B::QPY) * G.nxm + gx + B::QPX;
         else sq[k] = s[k];
       }
-      if constexpr (PAD) qcs = G.cq;
+      if constexpr (PAD) qcs = (int)G.cq;
       Sym5<V> q0;
       q0.xx = vld<SPT>(Qin, sq[0], sq[SPT - 1]);
       q0.xy = vld<SPT>(Qin, qcs + sq[0], qcs + sq[SPT - 1]);
@@ -1208,7 +1209,7 @@ __device__ __forceinline__ void lbq_body(const CUtensorMap* tmPQ, const CUtensor
         if (!lane_ok[k]) continue;
         if constexpr (PAD) {
           const V qv[5] = {q1.xx, q1.xy, q1.xz, q1.yy, q1.yz};
-          put_mirror<5, SPT, real>(Qout, G.cq, G.nxm, G.nyq, B::QPX, 2, nx, ny, z, gx, gy[k], qv, k);
+          put_mirror<5, SPT, real>(Qout, (int)G.cq, G.nxm, G.nyq, B::QPX, 2, nx, ny, z, gx, gy[k], qv, k);
         } else {
           store5_lane<SPT, real>(Qout, n, s[k], q1, k);
         }
