@@ -370,10 +370,16 @@ __device__ __forceinline__ void qside_body(const CUtensorMap* tmQ, const CUtenso
   // registers for it (dq_next); H goes through hslot; the ring cells go to
   // the threads after them.  With two sites per thread the output pass
   // recomputes the gradients from the staged Q.
+  // With one site per thread the own cell's tau_xz, tau_yz of the plane just
+  // computed stay in registers too (tz_next): the output pass of plane z reads
+  // tau of plane z+1 only in its own column, so it needs no barrier after the
+  // pass over plane z+1.
   Sym5<V> dq_next[3];
+  V tz_next[2];
   auto field_plane = [&](int p) {
     if (ghost(p)) {  // tau = 0 beyond a wall; H there is never read
       for (int t = threadIdx.x; t < L::TSLOT; t += blockDim.x) tslot(p)[t] = real(0);
+      tz_next[0] = tz_next[1] = V(0);
       return;
     }
     const real* qm = qslot(p - 1);
@@ -437,6 +443,8 @@ __device__ __forceinline__ void qside_body(const CUtensorMap* tmQ, const CUtenso
           dq_next[0] = dq[0];
           dq_next[1] = dq[1];
           dq_next[2] = dq[2];
+          tz_next[0] = tu[1];
+          tz_next[1] = tu[2];
         }
       }
       return;
@@ -505,11 +513,16 @@ __device__ __forceinline__ void qside_body(const CUtensorMap* tmQ, const CUtenso
     field_plane(z0);
   }
 
-  // Per plane two CTA barriers: after the waits (patched halos, a uniform abort
-  // decision) and after the H / tau pass.  A thread past the first barrier of
-  // plane z knows every thread has finished plane z-1, the last reader of the
-  // Q and u slots the next loads overwrite (planes z-2) and of the tau / H
-  // slots this plane's pass overwrites, so no barrier closes the plane.
+  // Per plane one CTA barrier, after the waits (patched halos, a uniform abort
+  // decision), and with two sites per thread a second one after the H / tau
+  // pass.  A thread past the first barrier of plane z knows every thread has
+  // finished plane z-1, the last reader of the Q and u slots the next loads
+  // overwrite (planes z-2) and of the tau / H slots this plane's pass
+  // overwrites (planes z-2 and z-1), so no barrier closes the plane.  The
+  // output pass of plane z reads tau of planes z-1 and z and H of plane z,
+  // written in earlier planes' passes, and tau of plane z+1 in its own column
+  // (one site per thread: from registers; two: from the slot, after the
+  // second barrier).
   for (int z = z0; z < z1 && !aborted; ++z) {
     // the periodic images for the planes waited for are loaded before the
     // waits (they do not depend on the copies), and stored after them
@@ -550,7 +563,7 @@ __device__ __forceinline__ void qside_body(const CUtensorMap* tmQ, const CUtenso
     // H and the gradients of plane z, kept from the previous pass (one site per thread)
     const Sym5<V> dq_cur[3] = {dq_next[0], dq_next[1], dq_next[2]};
     field_plane(z + 1);
-    __syncthreads();
+    if constexpr (SPT != 1) __syncthreads();
     if (ty < TYH && gx < nx && y0 + ty < ny) {
       const real* qm = qslot(z - 1);
       const real* qc = qslot(z);
@@ -580,8 +593,16 @@ __device__ __forceinline__ void qside_body(const CUtensorMap* tmQ, const CUtenso
       const int t0 = (ty + 1) * L::TCOLS + (tx + 1), t1 = t0 + TYH * L::TCOLS;
       auto T = [&](const real* sl, int off) { return vld<SPT>(sl, t0 + off, t1 + off); };
       const V half = V(0.5);
-      V bx = half * (T(tc, L::TCOLS) - T(tc, -L::TCOLS)) + half * (T(tpz, TCS) - T(tm, TCS));
-      V by = -(half * (T(tc, 1) - T(tc, -1))) + half * (T(tpz, 2 * TCS) - T(tm, 2 * TCS));
+      V tz_p[2];  // tau_xz, tau_yz of plane z+1 at the site
+      if constexpr (SPT == 1) {
+        tz_p[0] = tz_next[0];
+        tz_p[1] = tz_next[1];
+      } else {
+        tz_p[0] = T(tpz, TCS);
+        tz_p[1] = T(tpz, 2 * TCS);
+      }
+      V bx = half * (T(tc, L::TCOLS) - T(tc, -L::TCOLS)) + half * (tz_p[0] - T(tm, TCS));
+      V by = -(half * (T(tc, 1) - T(tc, -1))) + half * (tz_p[1] - T(tm, 2 * TCS));
       V bz = -(half * (T(tc, TCS + 1) - T(tc, TCS - 1))) -
              half * (T(tc, 2 * TCS + L::TCOLS) - T(tc, 2 * TCS - L::TCOLS));
       bx -= ddot(h, dq[0]);
