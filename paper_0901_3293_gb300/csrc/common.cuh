@@ -361,6 +361,18 @@ __device__ __forceinline__ void lc_stress(const Sym5<real>& q, const Sym5<real>&
   tau[2] = QH[1][2] - QH[2][1];
 }
 
+// tau = Q H - H Q alone, as [xy, xz, yz]: (QH)_ab - (QH)_ba from the six
+// off-diagonal entries of Q H
+template <typename real>
+__device__ __forceinline__ void lc_tau(const Sym5<real>& q, const Sym5<real>& h, real tau[3]) {
+  const Mat3<real> Q = full(q);
+  const Mat3<real> H = full(h);
+  auto QH = [&](int a, int b) { return Q.a[a][0] * H.a[0][b] + Q.a[a][1] * H.a[1][b] + Q.a[a][2] * H.a[2][b]; };
+  tau[0] = QH(0, 1) - QH(1, 0);
+  tau[1] = QH(0, 2) - QH(2, 0);
+  tau[2] = QH(1, 2) - QH(2, 1);
+}
+
 // ---------------------------------------------------------------------------
 // dQ/dt of Eq. (Qevolution) + (mat_der):  Gamma H + S_traceless(W, Q) - u . D0 Q
 // with W_ab = D0_b u_a given as w[a][b].

@@ -424,7 +424,9 @@ __device__ __forceinline__ void qside_body(const CUtensorMap* tmQ, const CUtenso
         const Sym5<V> h = molecular_field(st, mv, dq);
         Sym5<V> sg;
         V tu[3];
-        lc_stress(st.c, h, mv.xi, sg, tu);
+        // the ring warps (t >= NIN, a warp-uniform split) need tau only
+        if (t < NIN) lc_stress(st.c, h, mv.xi, sg, tu);
+        else lc_tau(st.c, h, tu);
         const int ti = r * TC + c;
         tp[ti] = tu[0];
         tp[L::TROWS * TC + ti] = tu[1];

@@ -275,7 +275,22 @@ def time_call(shape=(64, 64, 256), reps: int = 20, k: int = K_STEPS):
     return t_sur, t_plain
 
 
-def plain_log(kappa: float, steps: int, log_every: int = 100, threshold: float = 0.19):
+def final_fields(lat: lcbp.Lattice, fields: dict | None) -> None:
+    """Q and u of the lattice's current state into ``fields`` (if given)."""
+    if fields is not None:
+        fields["q"] = lat.read_q(np.float64)
+        fields["u"] = lat.read_u(np.float64)
+
+
+def field_errors(a: dict, b: dict) -> dict:
+    """max |Delta Q| over sites and components, and the r.m.s. |Delta u| over sites."""
+    du = a["u"] - b["u"]
+    return {"max_abs_dQ": float(np.abs(a["q"] - b["q"]).max()),
+            "rms_du": float(np.sqrt(np.mean(np.sum(du * du, axis=0)))),
+            "rms_u": float(np.sqrt(np.mean(np.sum(b["u"] * b["u"], axis=0))))}
+
+
+def plain_log(kappa: float, steps: int, log_every: int = 100, threshold: float = 0.19, fields: dict | None = None):
     """The slab workload run plainly: (t, F, defect fraction) every log_every steps, and seconds."""
     lat = slab_lattice(kappa)
     rows = []
@@ -285,12 +300,13 @@ def plain_log(kappa: float, steps: int, log_every: int = 100, threshold: float =
         rows.append((t, lat.free_energy(), lat.defect_fraction(threshold)))
     lat.synchronize()
     secs = time.perf_counter() - t0
+    final_fields(lat, fields)
     lat.close()
     return rows, secs
 
 
 def judged_log(params, kappa: float, steps: int, k: int, M: int, tol: float, log_every: int = 100,
-               weights: str | None = None, warmup: int = 0):
+               weights: str | None = None, warmup: int = 0, fields: dict | None = None):
     """The judged run on the slab: its log, statistics and seconds."""
     hyb = slab_lattice(kappa)
     run = JudgedRun(hyb, params, kappa, M=M, tol=tol, k=k, weights=weights, warmup=warmup)
@@ -299,6 +315,7 @@ def judged_log(params, kappa: float, steps: int, k: int, M: int, tol: float, log
     hyb.synchronize()
     secs = time.perf_counter() - t0
     st = run.stats()
+    final_fields(hyb, fields)
     run.close()
     hyb.close()
     return list(zip(ts.tolist(), Fs.tolist(), Ds.tolist())), st, secs
@@ -369,19 +386,22 @@ def main():
     runs = {}
     logf = open(args.log_out, "w") if args.log_out else None
     for kappa in args.kappas:
-        rows, t_pl = plain_log(kappa, args.run_steps)
+        plain_fields = {}
+        rows, t_pl = plain_log(kappa, args.run_steps, fields=plain_fields)
         F_plain = {t: F for t, F, _ in rows}
         F_scale = max(abs(F) for _, F, _ in rows)
         out = {"plain_s": t_pl, "final_F": rows[-1][1], "final_defect_fraction": rows[-1][2], "F_scale": F_scale}
         # judged (tol) and accept-all (equal cost: every segment kept), trained and zero network
         for mode, tol in (("judged", args.tol), ("accept_all", 1e30)):
             for name, p in (("network", params), ("zero_network", np.zeros_like(params))):
-                jrows, st, secs = judged_log(p, kappa, args.run_steps, k, args.M, tol, warmup=args.warmup)
+                jf = {}
+                jrows, st, secs = judged_log(p, kappa, args.run_steps, k, args.M, tol, warmup=args.warmup, fields=jf)
                 errs = [abs(F - F_plain[t]) / abs(F_plain[t]) for t, F, _ in jrows]
                 errs_s = [abs(F - F_plain[t]) / F_scale for t, F, _ in jrows]
                 out[mode + "_" + name] = {"seconds": secs, "speedup_vs_plain": t_pl / secs, "logged": len(jrows),
                                           "max_rel_F_error": max(errs), "mean_rel_F_error": float(np.mean(errs)),
-                                          "max_F_error_of_scale": max(errs_s), **st}
+                                          "max_F_error_of_scale": max(errs_s),
+                                          "final_fields_vs_plain": field_errors(jf, plain_fields), **st}
                 if logf:
                     for (t, F, D), e in zip(jrows, errs):
                         logf.write(json.dumps({"run": mode + "_" + name, "kappa": kappa, "k": k, "t": t, "F": F,
