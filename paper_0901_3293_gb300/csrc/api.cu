@@ -384,6 +384,16 @@ bool make_padded_tmap(CUtensorMap* tm, void* base, int comps, int nxm, int nym, 
   return encode_tiled(tm, base, 4, dims, strides, box, dtype);
 }
 
+// the LB-ready scratch [z][group][nyp][nxp][4] as a 4-D tensor (4 nxp, nyp,
+// group, z), box = 4 * 36 x rows x 4 groups x 1
+bool make_scratch_tmap(CUtensorMap* tm, void* base, int nxp, int nyp, int nz, int rows, int dtype) {
+  const cuuint64_t es = dtype_size(dtype), X = 4 * (cuuint64_t)nxp;
+  const cuuint64_t dims[4] = {X, (cuuint64_t)nyp, (cuuint64_t)kZmPQG, (cuuint64_t)nz};
+  const cuuint64_t strides[3] = {X * es, X * nyp * es, (cuuint64_t)kZmPQ * nxp * nyp * es};
+  const cuuint32_t box[4] = {(cuuint32_t)(4 * kZmBoxXP), (cuuint32_t)rows, (cuuint32_t)kZmPQG, 1};
+  return encode_tiled(tm, base, 4, dims, strides, box, dtype);
+}
+
 bool fast_shape_ok(const lcbp_lattice* h) { return zm_shape_ok(h->nx, h->ny, h->nz); }
 
 bool use_fast(lcbp_lattice* h) {
@@ -406,8 +416,7 @@ bool use_fast(lcbp_lattice* h) {
                                   ty + 2, kZmBoxX, h->dtype);
     }
     const int nxp = h->nx + kZmPadX;
-    ok = ok && make_padded_tmap(&h->tm[3], h->pq, kZmPQ, nxp, nyu, h->nz, (long long)nxp * nyu * h->nz, ty + 2,
-                                kZmBoxXP, h->dtype);
+    ok = ok && make_scratch_tmap(&h->tm[3], h->pq, nxp, nyu, h->nz, ty + 2, h->dtype);
     for (int k = 0; k < 2; ++k)  // the populations (L2 prefetches only)
       ok = ok && make_field_tmap(&h->tm[6 + k], h->f[k], NV, h->nx, h->ny, h->nz, ty + 2, h->dtype);
     if (!ok) {

@@ -118,9 +118,11 @@ bool build_maps(lcbp_batch* b) {
       return encode_tiled(tm, base, 5, dims, strides, box, b->dtype);
     };
     const cuuint64_t nxp = nx + kZmPadX, nyp = ny + 2, cp = nxp * nyp * nz;
-    const cuuint64_t pdims[5] = {nxp, nyp, nz, (cuuint64_t)kZmPQ, (cuuint64_t)c.count};
-    const cuuint64_t pstr[4] = {nxp * es, nxp * nyp * es, cp * es, (cuuint64_t)kZmPQ * cp * es};
-    const cuuint32_t pbox[5] = {(cuuint32_t)kZmBoxXP, (cuuint32_t)(ty + 2), 1, (cuuint32_t)kZmPQ, 1};
+    // the scratch [replica][z][group][Y][X][4] as (4 X, Y, group, z, replica)
+    const cuuint64_t pdims[5] = {4 * nxp, nyp, (cuuint64_t)kZmPQG, nz, (cuuint64_t)c.count};
+    const cuuint64_t pstr[4] = {4 * nxp * es, 4 * nxp * nyp * es, (cuuint64_t)kZmPQ * nxp * nyp * es,
+                                (cuuint64_t)kZmPQ * cp * es};
+    const cuuint32_t pbox[5] = {(cuuint32_t)(4 * kZmBoxXP), (cuuint32_t)(ty + 2), (cuuint32_t)kZmPQG, 1, 1};
     bool ok = map(&b->maps[0].q[k], b->q, 5, 0, 5, ty + 4) && map(&b->maps[0].u[k], b->rhou[0], 4, 0, 4, ty + 2) &&
               map(&b->maps[1].u[k], b->rhou[1], 4, 0, 4, ty + 2) &&
               map(&b->maps[0].u3[k], b->rhou[0], 4, 1, 3, ty + 2) &&

@@ -126,18 +126,23 @@ constexpr int kDiagPartials = 512 * 8;
 // (x, y, z, component) and are built by the host (make_field_tmap).
 //
 // Between the two kernels the step's intermediate fields live in a
-// periodically padded scratch ("LB-ready" scratch): 15 components
-// [F_x F_y F_z V_x V_y V_z C W_xy W_xz W_yz | Q*_xx Q*_xy Q*_xz Q*_yy Q*_yz],
-// each an (nx + 4) x (ny + 2) x nz array in which site (x, y, z) sits at
-// (x + 1, y + 1, z) and the columns x = -1, nx and rows y = -1, ny hold the
-// periodic images.  The second kernel then stages them by TMA with no halo
-// patching.  The first ten are the per-site coefficients of the LB
+// periodically padded scratch ("LB-ready" scratch) of 16 values per site in
+// four groups of four, interleaved per site ([z][group][Y][X][4], one 16-byte
+// vector per site and group):
+//   G0 = [C, V_x, V_y, V_z], G1 = [W_xy, W_xz, W_yz, F_x],
+//   G2 = [F_y, F_z, Q*_yz, rho - 1], G3 = [Q*_xx, Q*_xy, Q*_xz, Q*_yy],
+// over an (nx + 4) x (ny + 2) x nz array in which site (x, y, z) sits at
+// (X, Y) = (x + 1, y + 1) and the columns x = -1, nx and rows y = -1, ny hold
+// the periodic images.  The second kernel then stages them by TMA with no halo
+// patching.  F, V, C and W are the per-site coefficients of the LB
 // pre-collision terms (f^eq_i / tau_f + p_i of Sec. 2.2 Eq. feq, coeff, eq4):
 // a face direction +-e_a has F_a +- V_a, a corner direction s has
-// C + (s . V) / 8 + s_x s_y W_xy + s_x s_z W_xz + s_y s_z W_yz.
+// C + (s . V) / 8 + s_x s_y W_xy + s_x s_z W_xz + s_y s_z W_yz.  A corner
+// thus reads G0 and G1 of its source site, and the Q* stencil G3 and G2.
 // ---------------------------------------------------------------------------
 constexpr int kZmPadX = 4;   // padded scratch: columns added to nx (one left, three right)
-constexpr int kZmPQ = 15;    // components of the padded scratch
+constexpr int kZmPQ = 16;    // values per site of the padded scratch (four groups of four)
+constexpr int kZmPQG = 4;    // groups
 
 struct ZmGeom {
   int nx, ny, nz, zc;
@@ -164,11 +169,11 @@ inline long long zm_umirror_elems(int nx, int ny, int nz) { return 4LL * (nx + 2
 // Shapes the fast kernels serve: rows of whole 16-byte groups (nx % 4 == 0 for
 // the TMA boxes) and element offsets within one lattice that fit in 32 bits
 // (the kernels index with int; the largest offsets are those of the 15
-// population or scratch components and of the 5 components of the Q mirror).
+// populations, the 16 scratch values and the 5 components of the Q mirror).
 inline bool zm_shape_ok(int nx, int ny, int nz) {
   const long long n = (long long)nx * ny * nz, cp = (long long)(nx + kZmPadX) * (ny + 2) * nz;
   const long long cq = (long long)(nx + 2 * kZmMirX) * (ny + 4) * nz, lim = 2147483647LL;
-  return nx % 4 == 0 && 15 * n < lim && 15 * cp < lim && 5 * cq < lim;
+  return nx % 4 == 0 && 15 * n < lim && kZmPQ * cp < lim && 5 * cq < lim;
 }
 
 struct ZmArgs {
@@ -206,7 +211,7 @@ struct ZmClass {
   int ctas_per_rep;  // tiles_x * tiles_y * tiles_z
   int rep0;          // first entry of the class in the replica order table
   int count;         // replicas in the class
-  long long pq0;     // first element of the class's padded scratch (replica j at pq0 + j * 15 * cp)
+  long long pq0;     // first element of the class's padded scratch (replica j at pq0 + j * 16 * cp)
 };
 struct ZmBatch {
   int nclass;

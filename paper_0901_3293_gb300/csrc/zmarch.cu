@@ -185,6 +185,41 @@ __device__ __forceinline__ Sym5<typename LaneT<real, SPT>::V> ld5v(const real* s
   v.yz = vld<SPT>(sl, 4 * cs + i0, 4 * cs + i1);
   return v;
 }
+// The four values at 16-byte aligned element i (a group of the padded
+// scratch), as one vector access: float4, or two double2 for FP64.
+template <typename real>
+__device__ __forceinline__ void ld4(const real* p, int i, real v[4]) {
+  if constexpr (sizeof(real) == 4) {
+    const float4 a = *reinterpret_cast<const float4*>(p + i);
+    v[0] = a.x, v[1] = a.y, v[2] = a.z, v[3] = a.w;
+  } else {
+    const double2 a = *reinterpret_cast<const double2*>(p + i), c = *reinterpret_cast<const double2*>(p + i + 2);
+    v[0] = a.x, v[1] = a.y, v[2] = c.x, v[3] = c.y;
+  }
+}
+template <typename real>
+__device__ __forceinline__ void st4(real* p, real a, real b, real c, real d) {
+  if constexpr (sizeof(real) == 4) {
+    *reinterpret_cast<float4*>(p) = make_float4(a, b, c, d);
+  } else {
+    *reinterpret_cast<double2*>(p) = make_double2(a, b);
+    *reinterpret_cast<double2*>(p + 2) = make_double2(c, d);
+  }
+}
+// a group at element i0 (lane 0) and i1 (lane 1)
+template <int SPT, typename real>
+__device__ __forceinline__ void ld4v(const real* p, int i0, int i1, typename LaneT<real, SPT>::V v[4]) {
+  if constexpr (SPT == 1) {
+    ld4(p, i0, v);
+  } else {
+    real a[4], c[4];
+    ld4(p, i0, a);
+    ld4(p, i1, c);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) v[j] = Vec2<real>(a[j], c[j], 0);
+  }
+}
+
 template <int SPT, typename real, typename V>
 __device__ __forceinline__ void store5_lane(real* p, int n, int s, const Sym5<V>& q, int k) {
   p[s] = lane<SPT, real>(q.xx, k);
@@ -628,20 +663,27 @@ __device__ __forceinline__ void qside_body(const CUtensorMap* tmQ, const CUtenso
         w[a][2] = half * (upz - umz);
       }
       const Sym5<V> r = be_rate(q, h, dq, u, w, mv, true);
-      // Components c0 .. c0 + cnt of the padded scratch for lane k: at the
-      // site's padded position, and at its periodic images in the ghost columns
-      // and rows where the site lies on a lattice face.
-      const int nxp = G.nxp, nyp = G.nyp;
-      const int cp = (int)G.cp;
-      auto put = [&](int c0, const V* v, int cnt) {
+      // The site's 16 values (four groups; rho - 1 in the last place) of the
+      // padded scratch for lane k:
+      // at the site's padded position, and at its periodic images in the ghost
+      // columns and rows where the site lies on a lattice face.
+      const int nxp = G.nxp, nyp = G.nyp, gs = 4 * G.nxp * G.nyp;  // gs: group stride
+      auto put = [&](const V* P, const V* qs, const V& dr) {
 #pragma unroll
         for (int k = 0; k < SPT; ++k) {
           const int gy = y0 + ty + k * TYH;
           if (gy >= ny) continue;
+          auto L = [&](const V& v) { return lane<SPT, real>(v, k); };
+          const real g0[4] = {L(P[6]), L(P[3]), L(P[4]), L(P[5])};
+          const real g1[4] = {L(P[7]), L(P[8]), L(P[9]), L(P[0])};
+          const real g2[4] = {L(P[1]), L(P[2]), L(qs[4]), L(dr)};
+          const real g3[4] = {L(qs[0]), L(qs[1]), L(qs[2]), L(qs[3])};
           auto put1 = [&](int xx, int yy) {
-            real* d = pq + (c0 * cp + (z * nyp + yy) * nxp + xx);
-#pragma unroll
-            for (int c = 0; c < cnt; ++c) d[c * cp] = lane<SPT, real>(v[c], k);
+            real* d = pq + ((z * kZmPQG * nyp + yy) * nxp + xx) * 4;
+            st4(d, g0[0], g0[1], g0[2], g0[3]);
+            st4(d + gs, g1[0], g1[1], g1[2], g1[3]);
+            st4(d + 2 * gs, g2[0], g2[1], g2[2], g2[3]);
+            st4(d + 3 * gs, g3[0], g3[1], g3[2], g3[3]);
           };
           put1(gx + 1, gy + 1);
           if (gx == 0 || gx == nx - 1 || gy == 0 || gy == ny - 1) {
@@ -656,10 +698,7 @@ __device__ __forceinline__ void qside_body(const CUtensorMap* tmQ, const CUtenso
           }
         }
       };
-      {
-        const V qv[5] = {q.xx + r.xx, q.xy + r.xy, q.xz + r.xz, q.yy + r.yy, q.yz + r.yz};
-        put(10, qv, 5);
-      }
+      const V qv[5] = {q.xx + r.xx, q.xy + r.xy, q.xz + r.xz, q.yy + r.yy, q.yz + r.yz};
       // The site's LB pre-collision coefficients from rho^n, u^n, sigma_LC and
       // b (the external force included): with j = rho u,
       //   F_a = [drho/30 - rho u^2/12 + (j_a u_a - sigma_aa)/2] / tau_f,
@@ -701,7 +740,7 @@ __device__ __forceinline__ void qside_body(const CUtensorMap* tmQ, const CUtenso
       P[7] = (jx * u[1] - sg.xy) * it8;
       P[8] = (jx * u[2] - sg.xz) * it8;
       P[9] = (jy * u[2] - sg.yz) * it8;
-      put(0, P, 10);
+      put(P, qv, drho);
     }
   }
   if (aborted && threadIdx.x == 0) {
@@ -824,13 +863,12 @@ __device__ __forceinline__ void put_mirror(real* __restrict__ m, int cs, int nxm
 template <typename real, int TY, bool PAD>
 struct LbqSmem {
   static constexpr int ROWS = TY + 2, SLOTS = 4;
-  static constexpr int CSA = ROWS * kZmBoxXP;           // per-component stride of the P / Q* box (padded scratch)
+  static constexpr int GS = ROWS * kZmBoxXP * 4;        // one group of the P / Q* box: [row][36][4]
   static constexpr int CSU = ROWS * StateBox<PAD>::UW;  // per-component stride of the u box (rho u components 1..3)
-  // one slot: [P 10 | Q* 5] then [u_x u_y u_z], each group 128-byte aligned
-  static constexpr int OFF_QS = 10 * CSA;
-  static constexpr int OFF_U = align_elems(kZmPQ * CSA, sizeof(real));
+  // one slot: the four groups of the padded scratch, then [u_x u_y u_z]
+  static constexpr int OFF_U = align_elems(kZmPQG * GS, sizeof(real));
   static constexpr int SLOT = OFF_U + align_elems(3 * CSU, sizeof(real));
-  static constexpr uint32_t TX_BYTES = (uint32_t)((kZmPQ * CSA + 3 * CSU) * sizeof(real));
+  static constexpr uint32_t TX_BYTES = (uint32_t)((kZmPQG * GS + 3 * CSU) * sizeof(real));
   // barriers, the abort flag, then the wrapped box columns and rows
   static constexpr size_t bytes = sizeof(real) * (size_t)SLOTS * SLOT + 8 * 8 + 16 + sizeof(int) * (ZM_BX + ROWS);
 };
@@ -903,7 +941,9 @@ __device__ __forceinline__ void lbq_body(const CUtensorMap* tmPQ, const CUtensor
     real* sl = slot(p);
     const int zz = wrap(p, nz);
     mbar_arrive_expect_tx(bar, L::TX_BYTES);
-    zm_load<BATCH>(sl, tmPQ, x0, y0, zz, rc, bar);
+    // the scratch as (4 X, Y, group, z): x coordinate in elements of 4 per site
+    if constexpr (BATCH) tma_load_5d(sl, tmPQ, 4 * x0, y0, 0, zz, rc, bar);
+    else tma_load_4d(sl, tmPQ, 4 * x0, y0, 0, zz, bar);
     zm_load<BATCH>(sl + L::OFF_U, tmU3, x0 - B::UX + B::UPX, y0 - 1 + B::UPY, zz, rc, bar);
     if constexpr (!BATCH) {
       // the populations of plane p (pulled from plane p-1 on) and Q^n of plane
@@ -934,10 +974,10 @@ __device__ __forceinline__ void lbq_body(const CUtensorMap* tmPQ, const CUtensor
   // a staged plane beyond a wall: only its Q* is read (the anchored qw)
   auto ghost = [&](int p) { return WALLS && (p < 0 || p >= nz); };
   auto fill = [&](int p) {
-    real* sl = slot(p) + L::OFF_QS;
-    for (int t = threadIdx.x; t < 5 * L::CSA; t += blockDim.x) {
-      const int k = t / L::CSA;
-      sl[t] = k == 0 ? qw.xx : k == 1 ? qw.xy : k == 2 ? qw.xz : k == 3 ? qw.yy : qw.yz;
+    real* sl = slot(p);
+    for (int t = threadIdx.x; t < L::GS / 4; t += blockDim.x) {  // Q*_yz in G2, the rest in G3
+      sl[2 * L::GS + 4 * t + 2] = qw.yz;
+      st4(sl + 3 * L::GS + 4 * t, qw.xx, qw.xy, qw.xz, qw.yy);
     }
   };
   auto patch = [&](int p) {
@@ -947,10 +987,13 @@ __device__ __forceinline__ void lbq_body(const CUtensorMap* tmPQ, const CUtensor
       ring[d] = v;
     }
   };
-  // component k of the P / Q* box at box index idx (lane 0) and idx + TYH rows
-  // (lane 1); the same for the u box
-  auto PA = [&](const real* sl, int k, int idx) {
-    return vld<SPT>(sl, k * L::CSA + idx, k * L::CSA + idx + TYH * AW);
+  // group g of the P / Q* box at box index idx (lane 0) and idx + TYH rows
+  // (lane 1), and value l of it; the same for the u box
+  auto PG = [&](const real* sl, int g, int idx, V v[4]) {
+    ld4v<SPT>(sl, g * L::GS + 4 * idx, g * L::GS + 4 * (idx + TYH * AW), v);
+  };
+  auto PS = [&](const real* sl, int g, int l, int idx) {
+    return vld<SPT>(sl, g * L::GS + 4 * idx + l, g * L::GS + 4 * (idx + TYH * AW) + l);
   };
   auto UB = [&](const real* sl, int k, int idx) {
     return vld<SPT>(sl, L::OFF_U + k * L::CSU + idx, L::OFF_U + k * L::CSU + idx + TYH * B::UW);
@@ -989,7 +1032,6 @@ __device__ __forceinline__ void lbq_body(const CUtensorMap* tmPQ, const CUtensor
     // populations f_i(y - e_i) and the site's rho - 1, issued before the
     // barrier wait so that they overlap it
     real fin_l[SPT][NV];
-    real dl[SPT];
     const bool wlo = WALLS && z == 0, whi = WALLS && z == nz - 1;
     // beside a wall, the bounce-back directions read the reflected population
     // of the site itself (a build of its own; every other plane pulls)
@@ -1003,8 +1045,6 @@ __device__ __forceinline__ void lbq_body(const CUtensorMap* tmPQ, const CUtensor
         const int rb[3][3] = {{(zm * ny + ym[k]) * nx, (zm * ny + gy[k]) * nx, (zm * ny + yp[k]) * nx},
                               {(z * ny + ym[k]) * nx, (z * ny + gy[k]) * nx, (z * ny + yp[k]) * nx},
                               {(zp * ny + ym[k]) * nx, (zp * ny + gy[k]) * nx, (zp * ny + yp[k]) * nx}};
-        if constexpr (PAD) dl[k] = __ldg(rhou + ((z * G.nyu + gy[k] + B::UPY) * G.nxm + gx + B::UPX));
-        else dl[k] = __ldg(rhou + (rb[1][1] + gx));
 #pragma unroll
         for (int i = 0; i < NV; ++i) {
           const int sx = ex(i) > 0 ? xm : ex(i) < 0 ? xp : gx;
@@ -1080,9 +1120,12 @@ __device__ __forceinline__ void lbq_body(const CUtensorMap* tmPQ, const CUtensor
         if constexpr (SPT == 1) fin[i] = fin_l[0][i];
         else fin[i] = V(fin_l[0][i], fin_l[SPT - 1][i], 0);
       }
-      V drho_y;
-      if constexpr (SPT == 1) drho_y = dl[0];
-      else drho_y = V(dl[0], dl[SPT - 1], 0);
+      // the site's G0 .. G2 of the scratch: [C V], [W F_x], [F_y F_z Q*_yz rho-1]
+      V c0[4], c1[4], c2[4];
+      PG(nc, 0, ca, c0);
+      PG(nc, 1, ca, c1);
+      PG(nc, 2, ca, c2);
+      const V drho_y = c2[3];
       const V u_y[3] = {UB(nc, 0, cu), UB(nc, 1, cu), UB(nc, 2, cu)};
       const V rho_y = V(1) + drho_y;
       const V jn[3] = {rho_y * u_y[0], rho_y * u_y[1], rho_y * u_y[2]};
@@ -1099,14 +1142,16 @@ __device__ __forceinline__ void lbq_body(const CUtensorMap* tmPQ, const CUtensor
         const int idx = bb ? ca : ca - ey(i) * AW - ex(i);
         if (i <= 6) {
           const int a = (i - 1) / 2;
-          const V Fa = PA(sl, a, idx), Va = PA(sl, 3 + a, idx);
+          // F_a: G1.3 (x), G2.0 (y), G2.1 (z); V_a: G0.(1 + a)
+          const V Fa = a == 0 ? PS(sl, 1, 3, idx) : PS(sl, 2, a - 1, idx), Va = PS(sl, 0, 1 + a, idx);
           pre[i] = ((i & 1) != 0) != bb ? Fa + Va : Fa - Va;  // odd i: the + direction
         } else {
-          const V c0 = PA(sl, 6, idx);
-          const V vs = signed_sum(ex(i), PA(sl, 3, idx), ey(i), PA(sl, 4, idx), ez(i), PA(sl, 5, idx));
-          const V ws = signed_sum(ex(i) * ey(i), PA(sl, 7, idx), ex(i) * ez(i), PA(sl, 8, idx), ey(i) * ez(i),
-                                  PA(sl, 9, idx));
-          pre[i] = bb ? (c0 + ws) - LCBP_Q(1, 8) * vs : (c0 + ws) + LCBP_Q(1, 8) * vs;
+          V g0[4], g1[4];  // [C, V_x, V_y, V_z], [W_xy, W_xz, W_yz, F_x]
+          PG(sl, 0, idx, g0);
+          PG(sl, 1, idx, g1);
+          const V vs = signed_sum(ex(i), g0[1], ey(i), g0[2], ez(i), g0[3]);
+          const V ws = signed_sum(ex(i) * ey(i), g1[0], ex(i) * ez(i), g1[1], ey(i) * ez(i), g1[2]);
+          pre[i] = bb ? (g0[0] + ws) - LCBP_Q(1, 8) * vs : (g0[0] + ws) + LCBP_Q(1, 8) * vs;
         }
       }
       // C_i = (f^eq - f_i) / tau_f + p_i; predictor f* = f + C, and f + C / 2
@@ -1133,15 +1178,16 @@ __device__ __forceinline__ void lbq_body(const CUtensorMap* tmPQ, const CUtensor
       // at the site's step-n values.  P(y) holds them for (rho^n, u^n), so
       // each takes the change of its moment part.
       const V dd = (drs - drho_y) * LCBP_Q(1, 30) - (rusq_s - rusq_n) * LCBP_Q(1, 12);
+      const V Fn[3] = {c1[3], c2[0], c2[1]};
       V Fs[3], Vs[3];
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
-        Fs[a] = PA(nc, a, ca) + (dd + V(0.5) * (js[a] * us[a] - jn[a] * u_y[a])) * inv_tau;
-        Vs[a] = PA(nc, 3 + a, ca) + (js[a] - jn[a]) * it3;
+        Fs[a] = Fn[a] + (dd + V(0.5) * (js[a] * us[a] - jn[a] * u_y[a])) * inv_tau;
+        Vs[a] = c0[1 + a] + (js[a] - jn[a]) * it3;
       }
-      const V Ws[3] = {PA(nc, 7, ca) + (js[0] * us[1] - jn[0] * u_y[1]) * it8,
-                       PA(nc, 8, ca) + (js[0] * us[2] - jn[0] * u_y[2]) * it8,
-                       PA(nc, 9, ca) + (js[1] * us[2] - jn[1] * u_y[2]) * it8};
+      const V Ws[3] = {c1[0] + (js[0] * us[1] - jn[0] * u_y[1]) * it8,
+                       c1[1] + (js[0] * us[2] - jn[0] * u_y[2]) * it8,
+                       c1[2] + (js[1] * us[2] - jn[1] * u_y[2]) * it8};
       const V Cs0 = (drs * LCBP_Q(1, 30) + rusq_s * LCBP_Q(1, 48)) * inv_tau;
       V dr1 = V(0), j1x = V(0), j1y = V(0), j1z = V(0);
 #pragma unroll
@@ -1183,18 +1229,22 @@ __device__ __forceinline__ void lbq_body(const CUtensorMap* tmPQ, const CUtensor
       }
 
       // Heun corrector with u^n
-      const real* sm = nm + L::OFF_QS;
-      const real* sc = nc + L::OFF_QS;
-      const real* sp = np + L::OFF_QS;
-      const int c1 = ca + TYH * AW;
+      // Q* at a box index: G3 = [xx xy xz yy] and G2.2 = yz
+      auto QS = [&](const real* sl, int idx) {
+        V g3[4];
+        PG(sl, 3, idx, g3);
+        return Sym5<V>{g3[0], g3[1], g3[2], g3[3], PS(sl, 2, 2, idx)};
+      };
       Stencil7<V> st;
-      st.c = ld5v<SPT>(sc, L::CSA, ca, c1);
-      st.xm = ld5v<SPT>(sc, L::CSA, ca - 1, c1 - 1);
-      st.xp = ld5v<SPT>(sc, L::CSA, ca + 1, c1 + 1);
-      st.ym = ld5v<SPT>(sc, L::CSA, ca - AW, c1 - AW);
-      st.yp = ld5v<SPT>(sc, L::CSA, ca + AW, c1 + AW);
-      st.zm = ld5v<SPT>(sm, L::CSA, ca, c1);
-      st.zp = ld5v<SPT>(sp, L::CSA, ca, c1);
+      V g3c[4];
+      PG(nc, 3, ca, g3c);
+      st.c = Sym5<V>{g3c[0], g3c[1], g3c[2], g3c[3], c2[2]};
+      st.xm = QS(nc, ca - 1);
+      st.xp = QS(nc, ca + 1);
+      st.ym = QS(nc, ca - AW);
+      st.yp = QS(nc, ca + AW);
+      st.zm = QS(nm, ca);
+      st.zp = QS(np, ca);
       Sym5<V> dq[3];
       const Sym5<V> h = molecular_field(st, mv, dq);
       V w[3][3];

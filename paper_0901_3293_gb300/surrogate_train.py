@@ -30,7 +30,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from . import lcbp
+from . import lcbp, synth
 
 Q0 = 2 * np.pi / 16
 A0 = 0.01
@@ -290,13 +290,20 @@ def field_errors(a: dict, b: dict) -> dict:
             "rms_u": float(np.sqrt(np.mean(np.sum(b["u"] * b["u"], axis=0))))}
 
 
-def plain_log(kappa: float, steps: int, log_every: int = 100, threshold: float = 0.19, fields: dict | None = None):
-    """The slab workload run plainly: (t, F, defect fraction) every log_every steps, and seconds."""
+def plain_log(kappa: float, steps: int, log_every: int = 100, threshold: float = 0.19, fields: dict | None = None,
+              perturb: tuple | None = None):
+    """The slab workload run plainly: (t, F, defect fraction) every log_every steps, and seconds.
+    perturb = (t_p, eps, seed): at step t_p (a multiple of log_every) add
+    uniform noise of amplitude eps to every Q component (the solver's own
+    sensitivity, as a yardstick for the judged run's field errors)."""
     lat = slab_lattice(kappa)
     rows = []
     t0 = time.perf_counter()
     for t in range(log_every, steps + 1, log_every):
         lat.step(log_every)
+        if perturb is not None and t == perturb[0]:
+            q = lat.read_q(np.float64)
+            lat.set_q(q + synth.random_q5(q.shape[1:], perturb[1], perturb[2]))
         rows.append((t, lat.free_energy(), lat.defect_fraction(threshold)))
     lat.synchronize()
     secs = time.perf_counter() - t0
@@ -391,7 +398,14 @@ def main():
         F_plain = {t: F for t, F, _ in rows}
         F_scale = max(abs(F) for _, F, _ in rows)
         out = {"plain_s": t_pl, "final_F": rows[-1][1], "final_defect_fraction": rows[-1][2], "F_scale": F_scale}
+        # the plain solver's own sensitivity: Q perturbed by 1e-7 after the warm-up
+        pert_fields = {}
+        prow, _ = plain_log(kappa, args.run_steps, fields=pert_fields, perturb=(args.warmup, 1e-7, 99))
+        out["plain_perturbed_1e-7"] = {
+            "max_rel_F_error": max(abs(F - F_plain[t]) / abs(F_plain[t]) for t, F, _ in prow),
+            "final_fields_vs_plain": field_errors(pert_fields, plain_fields)}
         # judged (tol) and accept-all (equal cost: every segment kept), trained and zero network
+        logged = {}
         for mode, tol in (("judged", args.tol), ("accept_all", 1e30)):
             for name, p in (("network", params), ("zero_network", np.zeros_like(params))):
                 jf = {}
@@ -402,13 +416,17 @@ def main():
                                           "max_rel_F_error": max(errs), "mean_rel_F_error": float(np.mean(errs)),
                                           "max_F_error_of_scale": max(errs_s),
                                           "final_fields_vs_plain": field_errors(jf, plain_fields), **st}
-                if logf:
-                    for (t, F, D), e in zip(jrows, errs):
-                        logf.write(json.dumps({"run": mode + "_" + name, "kappa": kappa, "k": k, "t": t, "F": F,
-                                               "defect_fraction": D, "rel_F_error_vs_plain": e}) + "\n")
+                if mode == "judged":
+                    logged[name] = {t: (F, D, e) for (t, F, D), e in zip(jrows, errs)}
         if logf:
+            # one line per logged step: the plain run, and the judged runs of the
+            # trained and the zero network with their relative F error
             for t, F, D in rows:
-                logf.write(json.dumps({"run": "plain", "kappa": kappa, "t": t, "F": F, "defect_fraction": D}) + "\n")
+                line = {"kappa": kappa, "k": k, "t": t, "F_plain": F, "defect_plain": D}
+                for name, key in (("network", "judged"), ("zero_network", "judged_zero")):
+                    Fj, Dj, e = logged[name][t]
+                    line.update({"F_" + key: Fj, "defect_" + key: Dj, "rel_F_err_" + key: float("%.4g" % e)})
+                logf.write(json.dumps(line) + "\n")
         runs[str(kappa)] = out
         note({"kappa": kappa, **out})
     if logf:
