@@ -208,8 +208,8 @@ struct lcbp_lattice {
   int zc;         // planes per CTA, 0 until tuned
   int spt;        // sites per thread of k_lbq, set by the tuner
   int spt_q;      // sites per thread of k_qside, set by the tuner
-  // Q, rho u [0], rho u [1], padded scratch, u [0], u [1] (rho u components 1..3), f [0], f [1]
-  CUtensorMap tm[8];
+  // Q mirror vectors, rho u mirror [0], [1], padded scratch, (unused), (unused), f [0], f [1], Q mirror yz
+  CUtensorMap tm[9];
   int* d_err;
 };
 
@@ -373,19 +373,18 @@ bool make_field_tmap(CUtensorMap* tm, void* base, int comps, int nx, int ny, int
   return encode_tiled(tm, base, 4, dims, strides, box, dtype);
 }
 
-// a padded array [comps][nz][nym][nxm] (component stride cs elements) as a 4-D
-// tensor, box = width x rows x 1 x comps
-bool make_padded_tmap(CUtensorMap* tm, void* base, int comps, int nxm, int nym, int nz, long long cs, int rows,
-                      int width, int dtype) {
+// one plane-interleaved mirror array [nz][nym][w] (w elements per row) as a
+// 3-D tensor, box = inner x rows x 1
+bool make_mirror_tmap(CUtensorMap* tm, void* base, int w, int nym, int nz, int inner, int rows, int dtype) {
   const cuuint64_t es = dtype_size(dtype);
-  const cuuint64_t dims[4] = {(cuuint64_t)nxm, (cuuint64_t)nym, (cuuint64_t)nz, (cuuint64_t)comps};
-  const cuuint64_t strides[3] = {nxm * es, (cuuint64_t)nxm * nym * es, (cuuint64_t)cs * es};
-  const cuuint32_t box[4] = {(cuuint32_t)width, (cuuint32_t)rows, 1, (cuuint32_t)comps};
-  return encode_tiled(tm, base, 4, dims, strides, box, dtype);
+  const cuuint64_t dims[3] = {(cuuint64_t)w, (cuuint64_t)nym, (cuuint64_t)nz};
+  const cuuint64_t strides[2] = {(cuuint64_t)w * es, (cuuint64_t)w * nym * es};
+  const cuuint32_t box[3] = {(cuuint32_t)inner, (cuuint32_t)rows, 1};
+  return encode_tiled(tm, base, 3, dims, strides, box, dtype);
 }
 
 // the LB-ready scratch [z][group][nyp][nxp][4] as a 4-D tensor (4 nxp, nyp,
-// group, z), box = 4 * 36 x rows x 4 groups x 1
+// group, z), box = 4 * 34 x rows x 4 groups x 1
 bool make_scratch_tmap(CUtensorMap* tm, void* base, int nxp, int nyp, int nz, int rows, int dtype) {
   const cuuint64_t es = dtype_size(dtype), X = 4 * (cuuint64_t)nxp;
   const cuuint64_t dims[4] = {X, (cuuint64_t)nyp, (cuuint64_t)kZmPQG, (cuuint64_t)nz};
@@ -405,16 +404,16 @@ bool use_fast(lcbp_lattice* h) {
     if (h->dtype == LCBP_F64) std::call_once(prep64, [] { zm_prepare<double>(); });
     else std::call_once(prep32, [] { zm_prepare<float>(); });
     const int ty = h->dtype == LCBP_F64 ? zm_tile_rows<double>() : zm_tile_rows<float>();
-    // Q and rho u from their padded mirrors (40-wide boxes), u = rho u components
-    // 1..3, and the LB-ready scratch (36-wide boxes)
-    const int nxm = h->nx + 2 * kZmMirX, nyq = h->ny + 4, nyu = h->ny + 2;
-    const long long cq = (long long)nxm * nyq * h->nz, cu = (long long)nxm * nyu * h->nz;
-    bool ok = make_padded_tmap(&h->tm[0], h->qm, 5, nxm, nyq, h->nz, cq, ty + 4, kZmBoxX, h->dtype);
-    for (int k = 0; k < 2; ++k) {
-      ok = ok && make_padded_tmap(&h->tm[1 + k], h->um[k], 4, nxm, nyu, h->nz, cu, ty + 2, kZmBoxX, h->dtype);
-      ok = ok && make_padded_tmap(&h->tm[4 + k], static_cast<char*>(h->um[k]) + cu * h->es, 3, nxm, nyu, h->nz, cu,
-                                  ty + 2, kZmBoxX, h->dtype);
-    }
+    // Q and rho u from their padded mirrors (40- and 34-site boxes; Q as its
+    // [xx xy xz yy] vectors and its yz array), and the LB-ready scratch
+    // (34-site boxes)
+    const int nxm = zm_mirror_nx(h->nx), nyq = h->ny + 4, nyu = h->ny + 2;
+    const long long cq = (long long)nxm * nyq * h->nz;
+    bool ok = make_mirror_tmap(&h->tm[0], h->qm, 4 * nxm, nyq, h->nz, 4 * kZmBoxX, ty + 4, h->dtype) &&
+              make_mirror_tmap(&h->tm[8], static_cast<char*>(h->qm) + 4 * cq * h->es, nxm, nyq, h->nz, kZmBoxX,
+                               ty + 4, h->dtype);
+    for (int k = 0; k < 2; ++k)
+      ok = ok && make_mirror_tmap(&h->tm[1 + k], h->um[k], 4 * nxm, nyu, h->nz, 4 * kZmBoxXU, ty + 2, h->dtype);
     const int nxp = h->nx + kZmPadX;
     ok = ok && make_scratch_tmap(&h->tm[3], h->pq, nxp, nyu, h->nz, ty + 2, h->dtype);
     for (int k = 0; k < 2; ++k)  // the populations (L2 prefetches only)
@@ -438,9 +437,10 @@ ZmArgs zm_args(lcbp_lattice* h, const void* model) {
   a.spt_q = h->spt_q > 0 ? h->spt_q : a.spt;
   a.model = model;
   a.tm_q = &h->tm[0];
+  a.tm_q1 = &h->tm[8];
   a.tm_u = &h->tm[1 + h->cur];
   a.tm_pq = &h->tm[3];
-  a.tm_u3 = &h->tm[4 + h->cur];
+  a.tm_u3 = &h->tm[1 + h->cur];
   a.tm_f = &h->tm[6 + h->cur];
   a.q = h->qm;
   a.qout = nullptr;
@@ -743,16 +743,16 @@ int refresh_moments(lcbp_lattice* h) {
 // arrays (sync_flat before, and a write makes the mirrors stale).
 int sync_flat(lcbp_lattice* h) {
   if (h->flat_ok) return LCBP_OK;
-  const int nxm = h->nx + 2 * kZmMirX, X = kZmMirX;
+  const int nxm = zm_mirror_nx(h->nx), X = kZmMirX;
   cudaError_t e =
       h->dtype == LCBP_F64
-          ? launch_unpack<double>(h->qm, h->q, 5, h->nx, h->ny, h->nz, X, 2, nxm, h->ny + 4, h->stream)
-          : launch_unpack<float>(h->qm, h->q, 5, h->nx, h->ny, h->nz, X, 2, nxm, h->ny + 4, h->stream);
+          ? launch_unpack<double>(h->qm, h->q, 5, 1, h->nx, h->ny, h->nz, X, 2, nxm, h->ny + 4, h->stream)
+          : launch_unpack<float>(h->qm, h->q, 5, 1, h->nx, h->ny, h->nz, X, 2, nxm, h->ny + 4, h->stream);
   if (e == cudaSuccess)
     e = h->dtype == LCBP_F64
-            ? launch_unpack<double>(h->um[h->cur], h->rhou[h->cur], 4, h->nx, h->ny, h->nz, X, 1, nxm, h->ny + 2,
+            ? launch_unpack<double>(h->um[h->cur], h->rhou[h->cur], 4, 1, h->nx, h->ny, h->nz, X, 1, nxm, h->ny + 2,
                                     h->stream)
-            : launch_unpack<float>(h->um[h->cur], h->rhou[h->cur], 4, h->nx, h->ny, h->nz, X, 1, nxm, h->ny + 2,
+            : launch_unpack<float>(h->um[h->cur], h->rhou[h->cur], 4, 1, h->nx, h->ny, h->nz, X, 1, nxm, h->ny + 2,
                                    h->stream);
   if (e != cudaSuccess) return cuda_fail(e, "state from the padded mirrors");
   h->flat_ok = true;
@@ -761,15 +761,15 @@ int sync_flat(lcbp_lattice* h) {
 
 int sync_mirror(lcbp_lattice* h) {
   if (h->mirror_ok) return LCBP_OK;
-  const int nxm = h->nx + 2 * kZmMirX, X = kZmMirX;
+  const int nxm = zm_mirror_nx(h->nx), X = kZmMirX;
   cudaError_t e = h->dtype == LCBP_F64
-                      ? launch_pack<double>(h->q, h->qm, 5, h->nx, h->ny, h->nz, X, 2, nxm, h->ny + 4, h->stream)
-                      : launch_pack<float>(h->q, h->qm, 5, h->nx, h->ny, h->nz, X, 2, nxm, h->ny + 4, h->stream);
+                      ? launch_pack<double>(h->q, h->qm, 5, 1, h->nx, h->ny, h->nz, X, 2, nxm, h->ny + 4, h->stream)
+                      : launch_pack<float>(h->q, h->qm, 5, 1, h->nx, h->ny, h->nz, X, 2, nxm, h->ny + 4, h->stream);
   if (e == cudaSuccess)
     e = h->dtype == LCBP_F64
-            ? launch_pack<double>(h->rhou[h->cur], h->um[h->cur], 4, h->nx, h->ny, h->nz, X, 1, nxm, h->ny + 2,
+            ? launch_pack<double>(h->rhou[h->cur], h->um[h->cur], 4, 1, h->nx, h->ny, h->nz, X, 1, nxm, h->ny + 2,
                                   h->stream)
-            : launch_pack<float>(h->rhou[h->cur], h->um[h->cur], 4, h->nx, h->ny, h->nz, X, 1, nxm, h->ny + 2,
+            : launch_pack<float>(h->rhou[h->cur], h->um[h->cur], 4, 1, h->nx, h->ny, h->nz, X, 1, nxm, h->ny + 2,
                                  h->stream);
   if (e != cudaSuccess) return cuda_fail(e, "padded mirrors of the state");
   h->mirror_ok = true;

@@ -150,7 +150,7 @@ void set_zc(lcbp_batch* b, const int* zc) {
     c.G.nxp = c.G.nx + kZmPadX;
     c.G.nyp = c.G.ny + 2;
     c.G.cp = (long long)c.G.nxp * c.G.nyp * c.G.nz;
-    c.G.nxm = c.G.nx + 2 * kZmMirX;  // (batches keep flat state: no mirrors)
+    c.G.nxm = zm_mirror_nx(c.G.nx);  // (batches keep flat state: no mirrors)
     c.G.nyq = c.G.ny + 4;
     c.G.nyu = c.G.ny + 2;
     c.G.cq = (long long)c.G.nxm * c.G.nyq * c.G.nz;

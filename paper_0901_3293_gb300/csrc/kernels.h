@@ -93,14 +93,16 @@ struct DiagGeom {
   double c_div;    // (K - L2) / 2: F_h gains -c_div |div Q|^2 per site
 };
 // padded mirror <-> flat field (state.cu): C components of an nx x ny x nz
-// field, site (x, y) at column x + hx and row y + hy of a mirror of nxp x nyp;
-// pack fills every mirror position with its periodic image
+// field, site (x, y) at column x + hx and row y + hy of a mirror of nxp x nyp
+// whose first 4G components are interleaved by fours ([group][z][Y][X][4])
+// and whose others are plain arrays; pack fills every mirror position with
+// its periodic image
 template <typename real>
-cudaError_t launch_pack(const void* flat, void* padded, int C, int nx, int ny, int nz, int hx, int hy, int nxp,
-                        int nyp, cudaStream_t s);
+cudaError_t launch_pack(const void* flat, void* padded, int C, int G, int nx, int ny, int nz, int hx, int hy,
+                        int nxp, int nyp, cudaStream_t s);
 template <typename real>
-cudaError_t launch_unpack(const void* padded, void* flat, int C, int nx, int ny, int nz, int hx, int hy, int nxp,
-                          int nyp, cudaStream_t s);
+cudaError_t launch_unpack(const void* padded, void* flat, int C, int G, int nx, int ny, int nz, int hx, int hy,
+                          int nxp, int nyp, cudaStream_t s);
 
 // whole-field checks (state.cu); scratch: state_check_scratch_bytes() of device memory
 size_t state_check_scratch_bytes();
@@ -150,21 +152,25 @@ struct ZmGeom {
   int tiles_x, tiles_y, tiles_z;
   int nxp, nyp;    // padded scratch and rho u mirror extents: nx + 4, ny + 2
   long long cp;    // their component stride: nxp * nyp * nz
-  int nxm;         // mirror row length: nx + 16
+  int nxm;         // mirror row length: zm_mirror_nx(nx)
   int nyq, nyu;    // mirror rows per plane: ny + 4 (Q), ny + 2 (rho u)
   long long cq, cu;  // mirror component strides: nxm * nyq * nz, nxm * nyu * nz
 };
 
 // Padded mirrors of the state (single lattices on the fast path): Q and rho u
-// with eight columns added on each side of a row (site x at column x + 8, so
-// that a row of 32 sites starts on a 32-byte sector) and two (Q) or one
-// (rho u) rows added on each side; the ghost columns and rows next to the
-// lattice hold the periodic images (x = -2, -1, nx, nx + 1 for Q, -1 and nx
-// for rho u).  k_lbq writes Q^{n+1} and rho u^{n+1} there, images included, so
-// the next step stages them with no patching.
-constexpr int kZmMirX = 8;  // columns added on each side of a mirror row
-inline long long zm_qmirror_elems(int nx, int ny, int nz) { return 5LL * (nx + 2 * kZmMirX) * (ny + 4) * nz; }
-inline long long zm_umirror_elems(int nx, int ny, int nz) { return 4LL * (nx + 2 * kZmMirX) * (ny + 2) * nz; }
+// with 32 columns before each row and rows of a whole number of 128-byte
+// lines in FP32 (site x at column x + 32, so that a warp's row of 32 sites is
+// one aligned line), and two (Q) or one (rho u) rows added on each side; the
+// ghost columns and rows next to the lattice hold the periodic images
+// (x = -2, -1, nx, nx + 1 for Q, -1 and nx for rho u).  Components are
+// interleaved by fours, one 16-byte vector per site: rho u as
+// [z][Y][X][rho-1, u_x, u_y, u_z], Q as [z][Y][X][xx, xy, xz, yy] followed by
+// the plain array [z][Y][X] of yz.  k_lbq writes Q^{n+1} and rho u^{n+1} there,
+// images included, so the next step stages them with no patching.
+constexpr int kZmMirX = 32;  // columns before x = 0 in a mirror row
+inline int zm_mirror_nx(int nx) { return (nx + 31) / 32 * 32 + 2 * kZmMirX; }  // mirror row length
+inline long long zm_qmirror_elems(int nx, int ny, int nz) { return 5LL * zm_mirror_nx(nx) * (ny + 4) * nz; }
+inline long long zm_umirror_elems(int nx, int ny, int nz) { return 4LL * zm_mirror_nx(nx) * (ny + 2) * nz; }
 
 // Shapes the fast kernels serve: rows of whole 16-byte groups (nx % 4 == 0 for
 // the TMA boxes) and element offsets within one lattice that fit in 32 bits
@@ -172,7 +178,7 @@ inline long long zm_umirror_elems(int nx, int ny, int nz) { return 4LL * (nx + 2
 // populations, the 16 scratch values and the 5 components of the Q mirror).
 inline bool zm_shape_ok(int nx, int ny, int nz) {
   const long long n = (long long)nx * ny * nz, cp = (long long)(nx + kZmPadX) * (ny + 2) * nz;
-  const long long cq = (long long)(nx + 2 * kZmMirX) * (ny + 4) * nz, lim = 2147483647LL;
+  const long long cq = (long long)zm_mirror_nx(nx) * (ny + 4) * nz, lim = 2147483647LL;
   return nx % 4 == 0 && 15 * n < lim && kZmPQ * cp < lim && 5 * cq < lim;
 }
 
@@ -181,8 +187,10 @@ struct ZmArgs {
   int spt;            // sites per thread of k_lbq, 1 or 2 (2 only where zm_spt_max allows)
   int spt_q;          // sites per thread of k_qside (0: as spt)
   const void* model;  // host copy of Model<real>
-  // Q (box rows TY + 4), rho u (4 components), the padded scratch (15), u (rho u components 1..3)
-  const CUtensorMap *tm_q, *tm_u, *tm_pq, *tm_u3;
+  // the Q mirror as [xx xy xz yy] vectors (tm_q) and yz (tm_q1), box rows
+  // TY + 4; the rho u mirror (tm_u, 4-vectors; tm_u3 the same for k_lbq); the
+  // padded scratch (16 values per site)
+  const CUtensorMap *tm_q, *tm_q1, *tm_u, *tm_pq, *tm_u3;
   const CUtensorMap* tm_f;  // f^n (15 components), for L2 prefetches of the pulled populations
   void *q, *qout, *pq;  // qout: nullptr = update Q in place; pq: padded scratch
   const void* bext;
@@ -197,8 +205,9 @@ inline long long zm_pq_elems(int nx, int ny, int nz) {
   return (long long)kZmPQ * (nx + kZmPadX) * (ny + 2) * nz;
 }
 
-constexpr int kZmBoxX = 40;  // elements per TMA box row of the unpadded fields
-constexpr int kZmBoxXP = 36; // elements per TMA box row of the padded scratch
+constexpr int kZmBoxX = 40;   // sites per TMA box row of the flat fields and of the Q mirror (x0 - 4 ..)
+constexpr int kZmBoxXP = 34;  // sites per TMA box row of the padded scratch (x0 - 1 .. x0 + 32)
+constexpr int kZmBoxXU = 34;  // sites per TMA box row of the rho u mirror (x0 - 1 .. x0 + 32)
 
 // Fast path over a batch: replicas of equal dims form a class whose fields are
 // stored back to back, so that each field of a class is one 5-D tensor

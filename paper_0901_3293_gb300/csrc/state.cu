@@ -101,10 +101,18 @@ cudaError_t launch_max_abs_diff(const void* a, const void* b, long long n, void*
   return cudaGetLastError();
 }
 
-// padded[c][z][Y][X] = flat[c][z][wrap(Y - hy)][wrap(X - hx)] over every padded position
+// Element of component c at padded position (X, Y) of plane z in a padded
+// mirror whose first 4G components are interleaved by fours
+// ([group][z][Y][X][4]) and whose others follow as plain arrays ([z][Y][X]).
+__device__ __forceinline__ long long mirror_at(int c, int z, int Y, int X, int G, int nz, int nxp, int nyp) {
+  if (c < 4 * G) return ((((long long)(c >> 2) * nz + z) * nyp + Y) * nxp + X) * 4 + (c & 3);
+  return 4LL * G * nz * nyp * nxp + (((long long)(c - 4 * G) * nz + z) * nyp + Y) * nxp + X;
+}
+
+// every padded position of component c: flat[c][z][wrap(Y - hy)][wrap(X - hx)]
 template <typename real>
-__global__ void k_pack(const real* __restrict__ flat, real* __restrict__ padded, int C, int nx, int ny, int nz, int hx,
-                       int hy, int nxp, int nyp) {
+__global__ void k_pack(const real* __restrict__ flat, real* __restrict__ padded, int C, int G, int nx, int ny, int nz,
+                       int hx, int hy, int nxp, int nyp) {
   const long long total = (long long)C * nz * nyp * nxp;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
        i += (long long)gridDim.x * blockDim.x) {
@@ -112,17 +120,18 @@ __global__ void k_pack(const real* __restrict__ flat, real* __restrict__ padded,
     const long long r = i / nxp;
     const int Y = (int)(r % nyp);
     const long long cz = r / nyp;  // c * nz + z
+    const int z = (int)(cz % nz), c = (int)(cz / nz);
     int x = (X - hx) % nx, y = (Y - hy) % ny;
     x += x < 0 ? nx : 0;
     y += y < 0 ? ny : 0;
-    padded[i] = flat[(cz * ny + y) * nx + x];
+    padded[mirror_at(c, z, Y, X, G, nz, nxp, nyp)] = flat[(cz * ny + y) * nx + x];
   }
 }
 
-// flat[c][z][y][x] = padded[c][z][y + hy][x + hx]
+// flat[c][z][y][x] = the padded value at (x + hx, y + hy)
 template <typename real>
-__global__ void k_unpack(const real* __restrict__ padded, real* __restrict__ flat, int C, int nx, int ny, int nz,
-                         int hx, int hy, int nxp, int nyp) {
+__global__ void k_unpack(const real* __restrict__ padded, real* __restrict__ flat, int C, int G, int nx, int ny,
+                         int nz, int hx, int hy, int nxp, int nyp) {
   const long long total = (long long)C * nz * ny * nx;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
        i += (long long)gridDim.x * blockDim.x) {
@@ -130,30 +139,33 @@ __global__ void k_unpack(const real* __restrict__ padded, real* __restrict__ fla
     const long long r = i / nx;
     const int y = (int)(r % ny);
     const long long cz = r / ny;
-    flat[i] = padded[(cz * nyp + y + hy) * nxp + x + hx];
+    const int z = (int)(cz % nz), c = (int)(cz / nz);
+    flat[i] = padded[mirror_at(c, z, y + hy, x + hx, G, nz, nxp, nyp)];
   }
 }
 
 template <typename real>
-cudaError_t launch_pack(const void* flat, void* padded, int C, int nx, int ny, int nz, int hx, int hy, int nxp,
-                        int nyp, cudaStream_t s) {
-  k_pack<real><<<4096, 256, 0, s>>>(static_cast<const real*>(flat), static_cast<real*>(padded), C, nx, ny, nz, hx, hy,
-                                    nxp, nyp);
+cudaError_t launch_pack(const void* flat, void* padded, int C, int G, int nx, int ny, int nz, int hx, int hy,
+                        int nxp, int nyp, cudaStream_t s) {
+  k_pack<real><<<4096, 256, 0, s>>>(static_cast<const real*>(flat), static_cast<real*>(padded), C, G, nx, ny, nz, hx,
+                                    hy, nxp, nyp);
   return cudaGetLastError();
 }
 
 template <typename real>
-cudaError_t launch_unpack(const void* padded, void* flat, int C, int nx, int ny, int nz, int hx, int hy, int nxp,
-                          int nyp, cudaStream_t s) {
-  k_unpack<real><<<4096, 256, 0, s>>>(static_cast<const real*>(padded), static_cast<real*>(flat), C, nx, ny, nz, hx,
-                                      hy, nxp, nyp);
+cudaError_t launch_unpack(const void* padded, void* flat, int C, int G, int nx, int ny, int nz, int hx, int hy,
+                          int nxp, int nyp, cudaStream_t s) {
+  k_unpack<real><<<4096, 256, 0, s>>>(static_cast<const real*>(padded), static_cast<real*>(flat), C, G, nx, ny, nz,
+                                      hx, hy, nxp, nyp);
   return cudaGetLastError();
 }
 
-template cudaError_t launch_pack<float>(const void*, void*, int, int, int, int, int, int, int, int, cudaStream_t);
-template cudaError_t launch_pack<double>(const void*, void*, int, int, int, int, int, int, int, int, cudaStream_t);
-template cudaError_t launch_unpack<float>(const void*, void*, int, int, int, int, int, int, int, int, cudaStream_t);
-template cudaError_t launch_unpack<double>(const void*, void*, int, int, int, int, int, int, int, int, cudaStream_t);
+template cudaError_t launch_pack<float>(const void*, void*, int, int, int, int, int, int, int, int, int, cudaStream_t);
+template cudaError_t launch_pack<double>(const void*, void*, int, int, int, int, int, int, int, int, int, cudaStream_t);
+template cudaError_t launch_unpack<float>(const void*, void*, int, int, int, int, int, int, int, int, int,
+                                          cudaStream_t);
+template cudaError_t launch_unpack<double>(const void*, void*, int, int, int, int, int, int, int, int, int,
+                                           cudaStream_t);
 
 template cudaError_t launch_count_nonfinite<float>(const void*, long long, void*, unsigned long long*, cudaStream_t);
 template cudaError_t launch_count_nonfinite<double>(const void*, long long, void*, unsigned long long*, cudaStream_t);

@@ -36,15 +36,18 @@ constexpr int ZM_BX = 40;   // TMA box width in elements
 constexpr int ZM_XOFF = 4;  // box column of global x0
 constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s bound on any barrier wait
 
-// Staged boxes of the state fields Q (halo 2) and rho u (halo 1), 40 wide with
-// x0 at column 4 (a 16-byte aligned start): from the flat fields (batches) or
-// from their padded mirrors (single lattices; site x at mirror column x + 8,
-// y at row y + 2 (Q) or y + 1 (rho u)), whose ghosts hold the periodic images.
+// Staged boxes of the state fields Q (halo 2) and rho u (halo 1): from the
+// flat fields (batches) or from their padded mirrors (single lattices; site x
+// at mirror column x + 32, y at row y + 2 (Q) or y + 1 (rho u)), whose ghosts
+// hold the periodic images.  QW, UW: box widths; QX, UX: the box column of x0.
+// Boxes of plain arrays are 40 wide from x0 - 4 (a 16-byte aligned start);
+// the rho u mirror, 16 bytes per site, stages just x0 - 1 .. x0 + 32.
 // QPX, QPY, UPX, UPY: the mirror offsets of a site (0 for flat fields).
 template <bool PAD>
 struct StateBox {
   static constexpr int QW = ZM_BX, QX = ZM_XOFF, QPX = PAD ? kZmMirX : 0, QPY = PAD ? 2 : 0;
-  static constexpr int UW = ZM_BX, UX = ZM_XOFF, UPX = PAD ? kZmMirX : 0, UPY = PAD ? 1 : 0;
+  static constexpr int UW = PAD ? kZmBoxXU : ZM_BX, UX = PAD ? 1 : ZM_XOFF, UPX = PAD ? kZmMirX : 0,
+                       UPY = PAD ? 1 : 0;
 };
 
 __host__ __device__ constexpr int align_elems(int elems, int esize) {
@@ -276,7 +279,8 @@ constexpr int qside_threads() {
 // planes z = -1 and z = nz hold the anchored qw in every Q stencil, carry no
 // molecular field (tau = 0 there) and the velocity -u of the adjacent plane.
 template <typename real, int TY, int SPT, bool BATCH, bool WALLS>
-__device__ __forceinline__ void qside_body(const CUtensorMap* tmQ, const CUtensorMap* tmU, const ZmGeom G,
+__device__ __forceinline__ void qside_body(const CUtensorMap* tmQ, const CUtensorMap* tmQ1, const CUtensorMap* tmU,
+                                           const ZmGeom G,
                                            const Model<real> m, int bt, int rc, const real* __restrict__ Q,
                                            const real* __restrict__ rhou, const real* __restrict__ bext,
                                            real* __restrict__ pq, int* __restrict__ err, const Sym5<real> qw) {
@@ -316,6 +320,7 @@ __device__ __forceinline__ void qside_body(const CUtensorMap* tmQ, const CUtenso
     *abort_flag = 0;
     mbar_init_fence();
     tma_prefetch_desc(tmQ);
+    if constexpr (PAD) tma_prefetch_desc(tmQ1);
     tma_prefetch_desc(tmU);
   }
   fill_wrap_tables(xw, yw, L::QROWS, nx, ny, x0, y0 - 2);
@@ -330,13 +335,40 @@ __device__ __forceinline__ void qside_body(const CUtensorMap* tmQ, const CUtenso
     const unsigned k = p - (z0 - 2);
     uint64_t* bar = &bars[k % L::QSLOTS];
     mbar_arrive_expect_tx(bar, qbytes);
-    zm_load<BATCH>(qslot(p), tmQ, x0 - B::QX + B::QPX, y0 - 2 + B::QPY, wrap(p, nz), rc, bar);
+    if constexpr (PAD) {  // the mirror's [xx xy xz yy] vectors, then its yz array
+      const int X = x0 - B::QX + B::QPX, Y = y0 - 2 + B::QPY;
+      tma_load_3d(qslot(p), tmQ, 4 * X, Y, wrap(p, nz), bar);
+      tma_load_3d(qslot(p) + 4 * L::QCS, tmQ1, X, Y, wrap(p, nz), bar);
+    } else {
+      zm_load<BATCH>(qslot(p), tmQ, x0 - B::QX + B::QPX, y0 - 2 + B::QPY, wrap(p, nz), rc, bar);
+    }
   };
   auto issue_u = [&](int p) {
     const unsigned k = p - (z0 - 1);
     uint64_t* bar = &bars[L::QSLOTS + k % L::USLOTS];
     mbar_arrive_expect_tx(bar, ubytes);
-    zm_load<BATCH>(uslot(p), tmU, x0 - B::UX + B::UPX, y0 - 1 + B::UPY, wrap(p, nz), rc, bar);
+    if constexpr (PAD) tma_load_3d(uslot(p), tmU, 4 * (x0 - B::UX + B::UPX), y0 - 1 + B::UPY, wrap(p, nz), bar);
+    else zm_load<BATCH>(uslot(p), tmU, x0 - B::UX + B::UPX, y0 - 1 + B::UPY, wrap(p, nz), rc, bar);
+  };
+  // Q and rho u at box index i0 (lane 0) and i1 (lane 1) of a staged slot:
+  // the padded mirrors stage [row][col][4] vectors (Q: then its yz as
+  // [row][col]), the flat fields [component][row][col]
+  auto ldq = [&](const real* sl, int i0, int i1) -> Sym5<V> {
+    if constexpr (PAD) {
+      V a[4];
+      ld4v<SPT>(sl, 4 * i0, 4 * i1, a);
+      return {a[0], a[1], a[2], a[3], vld<SPT>(sl, 4 * L::QCS + i0, 4 * L::QCS + i1)};
+    } else {
+      return ld5v<SPT>(sl, L::QCS, i0, i1);
+    }
+  };
+  auto ldu = [&](const real* sl, int i0, int i1, V v[4]) {  // [rho - 1, u_x, u_y, u_z]
+    if constexpr (PAD) {
+      ld4v<SPT>(sl, 4 * i0, 4 * i1, v);
+    } else {
+#pragma unroll
+      for (int c = 0; c < 4; ++c) v[c] = vld<SPT>(sl, c * L::UCS + i0, c * L::UCS + i1);
+    }
   };
   // Wait for a plane.  Every thread reaches the __syncthreads that follows a
   // wait, so a timeout cannot strand part of the CTA.
@@ -375,9 +407,16 @@ __device__ __forceinline__ void qside_body(const CUtensorMap* tmQ, const CUtenso
   auto ghost = [&](int p) { return WALLS && (p < 0 || p >= nz); };
   auto fill_q = [&](int p) {
     real* sl = qslot(p);
-    for (int t = threadIdx.x; t < 5 * L::QCS; t += blockDim.x) {
-      const int k = t / L::QCS;
-      sl[t] = k == 0 ? qw.xx : k == 1 ? qw.xy : k == 2 ? qw.xz : k == 3 ? qw.yy : qw.yz;
+    if constexpr (PAD) {
+      for (int t = threadIdx.x; t < L::QCS; t += blockDim.x) {
+        st4(sl + 4 * t, qw.xx, qw.xy, qw.xz, qw.yy);
+        sl[4 * L::QCS + t] = qw.yz;
+      }
+    } else {
+      for (int t = threadIdx.x; t < 5 * L::QCS; t += blockDim.x) {
+        const int k = t / L::QCS;
+        sl[t] = k == 0 ? qw.xx : k == 1 ? qw.xy : k == 2 ? qw.xz : k == 3 ? qw.yy : qw.yz;
+      }
     }
   };
   auto patch_q = [&](int p) {
@@ -448,13 +487,13 @@ __device__ __forceinline__ void qside_body(const CUtensorMap* tmQ, const CUtenso
       if (r >= 0) {
         const int i0 = (r + 1) * B::QW + (c + B::QX - 1);  // position in the Q box
         Stencil7<V> st;
-        st.c = ld5v<1>(qc, L::QCS, i0, i0);
-        st.xm = ld5v<1>(qc, L::QCS, i0 - 1, i0 - 1);
-        st.xp = ld5v<1>(qc, L::QCS, i0 + 1, i0 + 1);
-        st.ym = ld5v<1>(qc, L::QCS, i0 - B::QW, i0 - B::QW);
-        st.yp = ld5v<1>(qc, L::QCS, i0 + B::QW, i0 + B::QW);
-        st.zm = ld5v<1>(qm, L::QCS, i0, i0);
-        st.zp = ld5v<1>(qp, L::QCS, i0, i0);
+        st.c = ldq(qc, i0, i0);
+        st.xm = ldq(qc, i0 - 1, i0 - 1);
+        st.xp = ldq(qc, i0 + 1, i0 + 1);
+        st.ym = ldq(qc, i0 - B::QW, i0 - B::QW);
+        st.yp = ldq(qc, i0 + B::QW, i0 + B::QW);
+        st.zm = ldq(qm, i0, i0);
+        st.zp = ldq(qp, i0, i0);
         Sym5<V> dq[3];
         const Sym5<V> h = molecular_field(st, mv, dq);
         Sym5<V> sg;
@@ -492,13 +531,13 @@ __device__ __forceinline__ void qside_body(const CUtensorMap* tmQ, const CUtenso
       const int i0 = (r0 + 1) * B::QW + (c + B::QX - 1);  // position in the Q box
       const int i1 = i0 + RH * B::QW;
       Stencil7<V> st;
-      st.c = ld5v<SPT>(qc, L::QCS, i0, i1);
-      st.xm = ld5v<SPT>(qc, L::QCS, i0 - 1, i1 - 1);
-      st.xp = ld5v<SPT>(qc, L::QCS, i0 + 1, i1 + 1);
-      st.ym = ld5v<SPT>(qc, L::QCS, i0 - B::QW, i1 - B::QW);
-      st.yp = ld5v<SPT>(qc, L::QCS, i0 + B::QW, i1 + B::QW);
-      st.zm = ld5v<SPT>(qm, L::QCS, i0, i1);
-      st.zp = ld5v<SPT>(qp, L::QCS, i0, i1);
+      st.c = ldq(qc, i0, i1);
+      st.xm = ldq(qc, i0 - 1, i1 - 1);
+      st.xp = ldq(qc, i0 + 1, i1 + 1);
+      st.ym = ldq(qc, i0 - B::QW, i1 - B::QW);
+      st.yp = ldq(qc, i0 + B::QW, i1 + B::QW);
+      st.zm = ldq(qm, i0, i1);
+      st.zp = ldq(qp, i0, i1);
       Sym5<V> dq[3];
       const Sym5<V> h = molecular_field(st, mv, dq);
       Sym5<V> sg;
@@ -606,7 +645,7 @@ __device__ __forceinline__ void qside_body(const CUtensorMap* tmQ, const CUtenso
       const real* qc = qslot(z);
       const real* qp = qslot(z + 1);
       const int qi0 = (ty + 2) * B::QW + (tx + B::QX), qi1 = qi0 + TYH * B::QW;
-      const Sym5<V> q = ld5v<SPT>(qc, L::QCS, qi0, qi1);
+      const Sym5<V> q = ldq(qc, qi0, qi1);
       Sym5<V> dq[3], h;
       if constexpr (SPT == 1 && !BATCH) {  // (a batch CTA has no registers to spare for the carry)
         dq[0] = dq_cur[0];
@@ -615,10 +654,9 @@ __device__ __forceinline__ void qside_body(const CUtensorMap* tmQ, const CUtenso
         const int hi0 = ty * ZM_TX + tx;
         h = ld5v<SPT>(hslot(z), TY * ZM_TX, hi0, hi0);
       } else {
-        dq[0] = half_diff(ld5v<SPT>(qc, L::QCS, qi0 + 1, qi1 + 1), ld5v<SPT>(qc, L::QCS, qi0 - 1, qi1 - 1));
-        dq[1] = half_diff(ld5v<SPT>(qc, L::QCS, qi0 + B::QW, qi1 + B::QW),
-                          ld5v<SPT>(qc, L::QCS, qi0 - B::QW, qi1 - B::QW));
-        dq[2] = half_diff(ld5v<SPT>(qp, L::QCS, qi0, qi1), ld5v<SPT>(qm, L::QCS, qi0, qi1));
+        dq[0] = half_diff(ldq(qc, qi0 + 1, qi1 + 1), ldq(qc, qi0 - 1, qi1 - 1));
+        dq[1] = half_diff(ldq(qc, qi0 + B::QW, qi1 + B::QW), ldq(qc, qi0 - B::QW, qi1 - B::QW));
+        dq[2] = half_diff(ldq(qp, qi0, qi1), ldq(qm, qi0, qi1));
         const int hi0 = ty * ZM_TX + tx;
         h = ld5v<SPT>(hslot(z), TY * ZM_TX, hi0, hi0 + TYH * ZM_TX);
       }
@@ -650,17 +688,27 @@ __device__ __forceinline__ void qside_body(const CUtensorMap* tmQ, const CUtenso
       const real* uc = uslot(z);
       const real* up = uslot(z + 1);
       const int u0 = (ty + 1) * B::UW + (tx + B::UX), u1 = u0 + TYH * B::UW;
-      V u[3], w[3][3];
+      V u[3], w[3][3], drho;
+      {
+        V c[4], xp[4], xm[4], yp[4], ym[4], zp[4], zm[4];  // [rho - 1, u_x, u_y, u_z]
+        ldu(uc, u0, u1, c);
+        ldu(uc, u0 + 1, u1 + 1, xp);
+        ldu(uc, u0 - 1, u1 - 1, xm);
+        ldu(uc, u0 + B::UW, u1 + B::UW, yp);
+        ldu(uc, u0 - B::UW, u1 - B::UW, ym);
+        ldu(up, u0, u1, zp);
+        ldu(um, u0, u1, zm);
+        drho = c[0];
 #pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        const int o = (a + 1) * L::UCS;
-        u[a] = vld<SPT>(uc, o + u0, o + u1);
-        w[a][0] = half * (vld<SPT>(uc, o + u0 + 1, o + u1 + 1) - vld<SPT>(uc, o + u0 - 1, o + u1 - 1));
-        w[a][1] = half * (vld<SPT>(uc, o + u0 + B::UW, o + u1 + B::UW) - vld<SPT>(uc, o + u0 - B::UW, o + u1 - B::UW));
-        V upz = vld<SPT>(up, o + u0, o + u1), umz = vld<SPT>(um, o + u0, o + u1);
-        if (WALLS && z == 0) umz = -u[a];  // no slip half a spacing beyond the wall
-        if (WALLS && z == nz - 1) upz = -u[a];
-        w[a][2] = half * (upz - umz);
+        for (int a = 0; a < 3; ++a) {
+          u[a] = c[1 + a];
+          w[a][0] = half * (xp[1 + a] - xm[1 + a]);
+          w[a][1] = half * (yp[1 + a] - ym[1 + a]);
+          V upz = zp[1 + a], umz = zm[1 + a];
+          if (WALLS && z == 0) umz = -u[a];  // no slip half a spacing beyond the wall
+          if (WALLS && z == nz - 1) upz = -u[a];
+          w[a][2] = half * (upz - umz);
+        }
       }
       const Sym5<V> r = be_rate(q, h, dq, u, w, mv, true);
       // The site's 16 values (four groups; rho - 1 in the last place) of the
@@ -721,7 +769,6 @@ __device__ __forceinline__ void qside_body(const CUtensorMap* tmQ, const CUtenso
       }
       const int hs0 = ty * ZM_TX + tx;
       const Sym5<V> sg = ld5v<SPT>(hslot(z) + 5 * TY * ZM_TX, TY * ZM_TX, hs0, hs0 + TYH * ZM_TX);
-      const V drho = vld<SPT>(uc, u0, u1);
       const V it = mv.inv_tau;
       const V rho = V(1) + drho;
       const V jx = rho * u[0], jy = rho * u[1], jz = rho * u[2];
@@ -757,10 +804,11 @@ __device__ __forceinline__ void qside_body(const CUtensorMap* tmQ, const CUtenso
 // FP32: two CTAs per SM (shared memory allows two; the bound keeps the registers within it)
 template <typename real, int TY, int SPT, bool WALLS>
 __global__ void __launch_bounds__(qside_threads<TY, SPT>(), sizeof(real) == 4 ? 2 : 1)
-    k_qside(const __grid_constant__ CUtensorMap tmQ, const __grid_constant__ CUtensorMap tmU, ZmGeom G,
+    k_qside(const __grid_constant__ CUtensorMap tmQ, const __grid_constant__ CUtensorMap tmQ1,
+            const __grid_constant__ CUtensorMap tmU, ZmGeom G,
             Model<real> m, const real* __restrict__ Q, const real* __restrict__ rhou,
             const real* __restrict__ bext, real* __restrict__ pq, int* __restrict__ err, Sym5<real> qw) {
-  qside_body<real, TY, SPT, false, WALLS>(&tmQ, &tmU, G, m, blockIdx.x, 0, Q, rhou, bext, pq, err, qw);
+  qside_body<real, TY, SPT, false, WALLS>(&tmQ, &tmQ1, &tmU, G, m, blockIdx.x, 0, Q, rhou, bext, pq, err, qw);
 }
 
 // The CTA's batch class, its replica and tile: classes own consecutive CTA ranges.
@@ -821,23 +869,17 @@ __global__ void __launch_bounds__(qside_threads<TY, 1>(), sizeof(real) == 4 ? 2 
       mq = &maps.q[i];
       mu = &maps.u[i];
     }
-  qside_body<real, TY, 1, true, false>(mq, mu, G, m, it.bt, it.j, Q + 5 * o, rhou + 4 * o, nullptr,
+  qside_body<real, TY, 1, true, false>(mq, nullptr, mu, G, m, it.bt, it.j, Q + 5 * o, rhou + 4 * o, nullptr,
                                        pq + pq0 + (long long)it.j * kZmPQ * G.cp, err, Sym5<real>{});
 }
 
-// Lane k's values v[0 .. C) of site (gx, gy, z) into a padded mirror (site x
-// at column x + px, y at row y + h; components cs apart, rows of nxm, nym rows
-// per plane) whose h ghost columns and rows next to the lattice hold periodic
-// images: at the site's position, and at each ghost position whose image the
-// site is (lattice faces only; nx >= 2h gives a site at most one x image).
-template <int C, int SPT, typename real, typename V>
-__device__ __forceinline__ void put_mirror(real* __restrict__ m, int cs, int nxm, int nym, int px, int h,
-                                           int nx, int ny, int z, int gx, int gy, const V* v, int k) {
-  auto put1 = [&](int X, int Y) {
-    real* d = m + ((z * nym + Y) * nxm + X);
-#pragma unroll
-    for (int c = 0; c < C; ++c) d[c * cs] = lane<SPT, real>(v[c], k);
-  };
+// The positions of a padded mirror (site x at column x + px, y at row y + h)
+// that hold the value of site (gx, gy): its own, and each ghost position in
+// the h columns and rows next to the lattice whose periodic image it is
+// (lattice faces only; nx >= 2h gives a site at most one x image).  put1(X, Y)
+// is called for each.
+template <typename F>
+__device__ __forceinline__ void mirror_positions(int px, int h, int nx, int ny, int gx, int gy, F&& put1) {
   const int X = gx + px, Y = gy + h;
   put1(X, Y);
   if (gx >= h && gx < nx - h && gy >= h && gy < ny - h) return;
@@ -863,12 +905,15 @@ __device__ __forceinline__ void put_mirror(real* __restrict__ m, int cs, int nxm
 template <typename real, int TY, bool PAD>
 struct LbqSmem {
   static constexpr int ROWS = TY + 2, SLOTS = 4;
-  static constexpr int GS = ROWS * kZmBoxXP * 4;        // one group of the P / Q* box: [row][36][4]
-  static constexpr int CSU = ROWS * StateBox<PAD>::UW;  // per-component stride of the u box (rho u components 1..3)
-  // one slot: the four groups of the padded scratch, then [u_x u_y u_z]
+  static constexpr int GS = ROWS * kZmBoxXP * 4;        // one group of the P / Q* box: [row][34][4]
+  static constexpr int CSU = ROWS * StateBox<PAD>::UW;  // per-component stride of the u box
+  // u box components: the rho u mirror's [rho-1 u_x u_y u_z] vectors, or
+  // components 1..3 of the flat field
+  static constexpr int UC = PAD ? 4 : 3;
+  // one slot: the four groups of the padded scratch, then the u box
   static constexpr int OFF_U = align_elems(kZmPQG * GS, sizeof(real));
-  static constexpr int SLOT = OFF_U + align_elems(3 * CSU, sizeof(real));
-  static constexpr uint32_t TX_BYTES = (uint32_t)((kZmPQG * GS + 3 * CSU) * sizeof(real));
+  static constexpr int SLOT = OFF_U + align_elems(UC * CSU, sizeof(real));
+  static constexpr uint32_t TX_BYTES = (uint32_t)((kZmPQG * GS + UC * CSU) * sizeof(real));
   // barriers, the abort flag, then the wrapped box columns and rows
   static constexpr size_t bytes = sizeof(real) * (size_t)SLOTS * SLOT + 8 * 8 + 16 + sizeof(int) * (ZM_BX + ROWS);
 };
@@ -877,11 +922,12 @@ struct LbqSmem {
 // that would arrive from beyond a wall is the reflected one of the same site
 // (half-way bounce-back); the staged Q* of a ghost plane is the anchored qw and
 // its velocity is -u of the adjacent plane.
-// tmF, tmQ (single lattices; null for batches): maps of f^n and Q^n, whose
-// planes are prefetched into L2 one plane before the pulls read them
+// tmF, tmQ, tmQ1 (single lattices; null for batches): maps of f^n and of the
+// Q^n mirror, whose planes are prefetched into L2 one plane before the loads
+// read them
 template <typename real, int TY, int SPT, bool BATCH, bool WALLS>
 __device__ __forceinline__ void lbq_body(const CUtensorMap* tmPQ, const CUtensorMap* tmU3, const CUtensorMap* tmF,
-                                         const CUtensorMap* tmQ, const ZmGeom& G,
+                                         const CUtensorMap* tmQ, const CUtensorMap* tmQ1, const ZmGeom& G,
                                          const Model<real>& m, int bt, int rc, const real* __restrict__ f,
                                          const real* __restrict__ rhou, const real* __restrict__ Qin,
                                          real* __restrict__ fnew, real* __restrict__ rhou_new,
@@ -927,6 +973,7 @@ __device__ __forceinline__ void lbq_body(const CUtensorMap* tmPQ, const CUtensor
     if constexpr (!BATCH) {
       tma_prefetch_desc(tmF);
       tma_prefetch_desc(tmQ);
+      tma_prefetch_desc(tmQ1);
     }
   }
   fill_wrap_tables(xw, yw, L::ROWS, nx, ny, x0, y0 - 1);
@@ -944,12 +991,16 @@ __device__ __forceinline__ void lbq_body(const CUtensorMap* tmPQ, const CUtensor
     // the scratch as (4 X, Y, group, z): x coordinate in elements of 4 per site
     if constexpr (BATCH) tma_load_5d(sl, tmPQ, 4 * x0, y0, 0, zz, rc, bar);
     else tma_load_4d(sl, tmPQ, 4 * x0, y0, 0, zz, bar);
-    zm_load<BATCH>(sl + L::OFF_U, tmU3, x0 - B::UX + B::UPX, y0 - 1 + B::UPY, zz, rc, bar);
-    if constexpr (!BATCH) {
+    if constexpr (PAD) {
+      tma_load_3d(sl + L::OFF_U, tmU3, 4 * (x0 - B::UX + B::UPX), y0 - 1 + B::UPY, zz, bar);
       // the populations of plane p (pulled from plane p-1 on) and Q^n of plane
       // p-1, into L2 a plane ahead of their plain loads
       tma_prefetch_l2_4d(tmF, x0 - ZM_XOFF, y0 - 1, zz, 0);
-      tma_prefetch_l2_4d(tmQ, x0 - B::QX + B::QPX, y0 - 2 + B::QPY, wrap(p - 1, nz), 0);
+      const int X = x0 - B::QX + B::QPX, Y = y0 - 2 + B::QPY;
+      tma_prefetch_l2_3d(tmQ, 4 * X, Y, wrap(p - 1, nz));
+      tma_prefetch_l2_3d(tmQ1, X, Y, wrap(p - 1, nz));
+    } else {
+      zm_load<BATCH>(sl + L::OFF_U, tmU3, x0 - B::UX + B::UPX, y0 - 1 + B::UPY, zz, rc, bar);
     }
   };
   auto wait = [&](int p) {
@@ -995,8 +1046,17 @@ __device__ __forceinline__ void lbq_body(const CUtensorMap* tmPQ, const CUtensor
   auto PS = [&](const real* sl, int g, int l, int idx) {
     return vld<SPT>(sl, g * L::GS + 4 * idx + l, g * L::GS + 4 * (idx + TYH * AW) + l);
   };
-  auto UB = [&](const real* sl, int k, int idx) {
-    return vld<SPT>(sl, L::OFF_U + k * L::CSU + idx, L::OFF_U + k * L::CSU + idx + TYH * B::UW);
+  // u = (u_x, u_y, u_z) at u-box index idx (lane 0) and idx + TYH rows (lane 1)
+  auto U3 = [&](const real* sl, int idx, V u[3]) {
+    if constexpr (PAD) {
+      V v[4];
+      ld4v<SPT>(sl + L::OFF_U, 4 * idx, 4 * (idx + TYH * B::UW), v);
+      u[0] = v[1], u[1] = v[2], u[2] = v[3];
+    } else {
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+        u[k] = vld<SPT>(sl, L::OFF_U + k * L::CSU + idx, L::OFF_U + k * L::CSU + idx + TYH * B::UW);
+    }
   };
   // acc +/- v by the sign of e (compile-time after unrolling)
   auto acc = [](V& a, int e, V v) {
@@ -1126,7 +1186,8 @@ __device__ __forceinline__ void lbq_body(const CUtensorMap* tmPQ, const CUtensor
       PG(nc, 1, ca, c1);
       PG(nc, 2, ca, c2);
       const V drho_y = c2[3];
-      const V u_y[3] = {UB(nc, 0, cu), UB(nc, 1, cu), UB(nc, 2, cu)};
+      V u_y[3];
+      U3(nc, cu, u_y);
       const V rho_y = V(1) + drho_y;
       const V jn[3] = {rho_y * u_y[0], rho_y * u_y[1], rho_y * u_y[2]};
       const V rusq_n = jn[0] * u_y[0] + jn[1] * u_y[1] + jn[2] * u_y[2];
@@ -1218,8 +1279,11 @@ __device__ __forceinline__ void lbq_body(const CUtensorMap* tmPQ, const CUtensor
       for (int k = 0; k < SPT; ++k) {
         if (!lane_ok[k]) continue;
         if constexpr (PAD) {
-          const V ru[4] = {dr1, u1x, u1y, u1z};
-          put_mirror<4, SPT, real>(rhou_new, (int)G.cu, G.nxm, G.nyu, B::UPX, 1, nx, ny, z, gx, gy[k], ru, k);
+          const real a = lane<SPT, real>(dr1, k), b = lane<SPT, real>(u1x, k), c = lane<SPT, real>(u1y, k),
+                     d = lane<SPT, real>(u1z, k);
+          const int nxm = G.nxm, nyu = G.nyu;
+          mirror_positions(B::UPX, 1, nx, ny, gx, gy[k],
+                           [&](int X, int Y) { st4(rhou_new + 4 * ((z * nyu + Y) * nxm + X), a, b, c, d); });
         } else {
           rhou_new[s[k]] = lane<SPT, real>(dr1, k);
           rhou_new[n + s[k]] = lane<SPT, real>(u1x, k);
@@ -1249,31 +1313,41 @@ __device__ __forceinline__ void lbq_body(const CUtensorMap* tmPQ, const CUtensor
       const Sym5<V> h = molecular_field(st, mv, dq);
       V w[3][3];
       const V half = V(0.5);
+      V uxp[3], uxm[3], uyp[3], uym[3], uzp[3], uzm[3];
+      U3(nc, cu + 1, uxp);
+      U3(nc, cu - 1, uxm);
+      U3(nc, cu + B::UW, uyp);
+      U3(nc, cu - B::UW, uym);
+      U3(np, cu, uzp);
+      U3(nm, cu, uzm);
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
-        w[a][0] = half * (UB(nc, a, cu + 1) - UB(nc, a, cu - 1));
-        w[a][1] = half * (UB(nc, a, cu + B::UW) - UB(nc, a, cu - B::UW));
-        V upz = UB(np, a, cu), umz = UB(nm, a, cu);
+        w[a][0] = half * (uxp[a] - uxm[a]);
+        w[a][1] = half * (uyp[a] - uym[a]);
+        V upz = uzp[a], umz = uzm[a];
         if (wl) umz = -u_y[a];  // no slip half a spacing beyond the wall
         if (wh) upz = -u_y[a];
         w[a][2] = half * (upz - umz);
       }
       const Sym5<V> r = be_rate(st.c, h, dq, u_y, w, mv, true);
-      // Q^n of the site: the flat field, or the Q mirror (two ghosts each side)
-      int sq[SPT];
-      int qcs = n;
-#pragma unroll
-      for (int k = 0; k < SPT; ++k) {
-        if constexpr (PAD) sq[k] = (z * G.nyq + gy[k] + B::QPY) * G.nxm + gx + B::QPX;
-        else sq[k] = s[k];
-      }
-      if constexpr (PAD) qcs = (int)G.cq;
+      // Q^n of the site: the flat field, or the Q mirror ([xx xy xz yy]
+      // vectors, then the yz array)
       Sym5<V> q0;
-      q0.xx = vld<SPT>(Qin, sq[0], sq[SPT - 1]);
-      q0.xy = vld<SPT>(Qin, qcs + sq[0], qcs + sq[SPT - 1]);
-      q0.xz = vld<SPT>(Qin, 2 * qcs + sq[0], 2 * qcs + sq[SPT - 1]);
-      q0.yy = vld<SPT>(Qin, 3 * qcs + sq[0], 3 * qcs + sq[SPT - 1]);
-      q0.yz = vld<SPT>(Qin, 4 * qcs + sq[0], 4 * qcs + sq[SPT - 1]);
+      if constexpr (PAD) {
+        int sq[SPT];
+#pragma unroll
+        for (int k = 0; k < SPT; ++k) sq[k] = (z * G.nyq + gy[k] + B::QPY) * G.nxm + gx + B::QPX;
+        const int cq = (int)G.cq;
+        V a[4];
+        ld4v<SPT>(Qin, 4 * sq[0], 4 * sq[SPT - 1], a);
+        q0 = {a[0], a[1], a[2], a[3], vld<SPT>(Qin, 4 * cq + sq[0], 4 * cq + sq[SPT - 1])};
+      } else {
+        q0.xx = vld<SPT>(Qin, s[0], s[SPT - 1]);
+        q0.xy = vld<SPT>(Qin, n + s[0], n + s[SPT - 1]);
+        q0.xz = vld<SPT>(Qin, 2 * n + s[0], 2 * n + s[SPT - 1]);
+        q0.yy = vld<SPT>(Qin, 3 * n + s[0], 3 * n + s[SPT - 1]);
+        q0.yz = vld<SPT>(Qin, 4 * n + s[0], 4 * n + s[SPT - 1]);
+      }
       const Sym5<V> q1 = {half * (q0.xx + st.c.xx + r.xx), half * (q0.xy + st.c.xy + r.xy),
                           half * (q0.xz + st.c.xz + r.xz), half * (q0.yy + st.c.yy + r.yy),
                           half * (q0.yz + st.c.yz + r.yz)};
@@ -1281,8 +1355,14 @@ __device__ __forceinline__ void lbq_body(const CUtensorMap* tmPQ, const CUtensor
       for (int k = 0; k < SPT; ++k) {
         if (!lane_ok[k]) continue;
         if constexpr (PAD) {
-          const V qv[5] = {q1.xx, q1.xy, q1.xz, q1.yy, q1.yz};
-          put_mirror<5, SPT, real>(Qout, (int)G.cq, G.nxm, G.nyq, B::QPX, 2, nx, ny, z, gx, gy[k], qv, k);
+          const real a = lane<SPT, real>(q1.xx, k), b = lane<SPT, real>(q1.xy, k), c = lane<SPT, real>(q1.xz, k),
+                     d = lane<SPT, real>(q1.yy, k), e = lane<SPT, real>(q1.yz, k);
+          const int nxm = G.nxm, nyq = G.nyq, cq4 = 4 * (int)G.cq;
+          mirror_positions(B::QPX, 2, nx, ny, gx, gy[k], [&](int X, int Y) {
+            const int o = (z * nyq + Y) * nxm + X;
+            st4(Qout + 4 * o, a, b, c, d);
+            Qout[cq4 + o] = e;
+          });
         } else {
           store5_lane<SPT, real>(Qout, n, s[k], q1, k);
         }
@@ -1305,12 +1385,12 @@ __device__ __forceinline__ void lbq_body(const CUtensorMap* tmPQ, const CUtensor
 template <typename real, int TY, int SPT, bool WALLS>
 __global__ void __launch_bounds__(ZM_TX* TY / SPT, 2)
     k_lbq(const __grid_constant__ CUtensorMap tmPQ, const __grid_constant__ CUtensorMap tmU3,
-          const __grid_constant__ CUtensorMap tmF, const __grid_constant__ CUtensorMap tmQ, ZmGeom G,
-          Model<real> m, const real* __restrict__ f, const real* __restrict__ rhou, const real* __restrict__ Qin,
+          const __grid_constant__ CUtensorMap tmF, const __grid_constant__ CUtensorMap tmQ,
+          const __grid_constant__ CUtensorMap tmQ1, ZmGeom G, Model<real> m, const real* __restrict__ f, const real* __restrict__ rhou, const real* __restrict__ Qin,
           real* __restrict__ fnew, real* __restrict__ rhou_new, real* __restrict__ Qout, int* __restrict__ err,
           Sym5<real> qw) {
-  lbq_body<real, TY, SPT, false, WALLS>(&tmPQ, &tmU3, &tmF, &tmQ, G, m, blockIdx.x, 0, f, rhou, Qin, fnew, rhou_new,
-                                        Qout, err, qw);
+  lbq_body<real, TY, SPT, false, WALLS>(&tmPQ, &tmU3, &tmF, &tmQ, &tmQ1, G, m, blockIdx.x, 0, f, rhou, Qin, fnew,
+                                        rhou_new, Qout, err, qw);
 }
 
 template <typename real, int TY>
@@ -1335,7 +1415,7 @@ __global__ void __launch_bounds__(ZM_TX* TY, 2)
       mpq = &maps.pq[i];
       mu3 = &maps.u3[i];
     }
-  lbq_body<real, TY, 1, true, false>(mpq, mu3, nullptr, nullptr, G, m, it.bt, it.j, f + NV * o, rhou + 4 * o, Qin + 5 * o,
+  lbq_body<real, TY, 1, true, false>(mpq, mu3, nullptr, nullptr, nullptr, G, m, it.bt, it.j, f + NV * o, rhou + 4 * o, Qin + 5 * o,
                                      fnew + NV * o, rhou_new + 4 * o, Qout + 5 * o, err, Sym5<real>{});
 }
 
@@ -1415,7 +1495,7 @@ ZmGeom zm_geom(int nx, int ny, int nz, int zc, int ty) {
   G.nxp = nx + kZmPadX;
   G.nyp = ny + 2;
   G.cp = (long long)G.nxp * G.nyp * nz;
-  G.nxm = nx + 2 * kZmMirX;
+  G.nxm = zm_mirror_nx(nx);
   G.nyq = ny + 4;
   G.nyu = ny + 2;
   G.cq = (long long)G.nxm * G.nyq * nz;
@@ -1433,11 +1513,11 @@ cudaError_t launch_step_zm_spt(const ZmArgs& a, cudaStream_t s) {
   if (WALLS) qw = {(real)a.q_wall[0], (real)a.q_wall[1], (real)a.q_wall[2], (real)a.q_wall[3], (real)a.q_wall[4]};
   if (a.events) cudaEventRecord(a.events[0], s);
   k_qside<real, TY, SQ, WALLS><<<grid, qside_threads<TY, SQ>(), QsideSmem<real, TY, true>::bytes, s>>>(
-      *a.tm_q, *a.tm_u, G, m, static_cast<const real*>(a.q), static_cast<const real*>(a.rhou),
+      *a.tm_q, *a.tm_q1, *a.tm_u, G, m, static_cast<const real*>(a.q), static_cast<const real*>(a.rhou),
       static_cast<const real*>(a.bext), static_cast<real*>(a.pq), a.err, qw);
   if (a.events) cudaEventRecord(a.events[1], s);
   k_lbq<real, TY, SPT, WALLS><<<grid, ZM_TX * TY / SPT, LbqSmem<real, TY, true>::bytes, s>>>(
-      *a.tm_pq, *a.tm_u3, *a.tm_f, *a.tm_q, G, m, static_cast<const real*>(a.f), static_cast<const real*>(a.rhou),
+      *a.tm_pq, *a.tm_u3, *a.tm_f, *a.tm_q, *a.tm_q1, G, m, static_cast<const real*>(a.f), static_cast<const real*>(a.rhou),
       static_cast<const real*>(a.q), static_cast<real*>(a.fnew), static_cast<real*>(a.rhou_new),
       static_cast<real*>(a.qout ? a.qout : a.q), a.err, qw);
   if (a.events) cudaEventRecord(a.events[2], s);
