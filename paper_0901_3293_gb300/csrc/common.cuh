@@ -271,19 +271,33 @@ __device__ __forceinline__ Sym5<real> half_diff(const Sym5<real>& p, const Sym5<
   return {h * (p.xx - m.xx), h * (p.xy - m.xy), h * (p.xz - m.xz), h * (p.yy - m.yy), h * (p.yz - m.yz)};
 }
 
+// p - m: twice the central difference
+template <typename real>
+__device__ __forceinline__ Sym5<real> diff5(const Sym5<real>& p, const Sym5<real>& m) {
+  return {p.xx - m.xx, p.xy - m.xy, p.xz - m.xz, p.yy - m.yy, p.yz - m.yz};
+}
+
 // ---------------------------------------------------------------------------
 // Molecular field, Sec. 2.1 Eq. (Qevolution) with the one-constant energy:
 // H = -A0(1-g/3) Q + A0 g (QQ - Tr(Q^2)/3 I) - A0 g Tr(Q^2) Q
 //     + K Lap7 Q - 2 K q0 (C + C^T) - 4 K q0^2 Q,   C_ab = eps_agd D0_g Q_db.
-// Also returns the three central derivatives D0_g Q for reuse.
+// Also returns the three central derivatives D0_g Q for reuse (RAW: twice
+// them, the plain differences Q(+) - Q(-), which saves the halving; the
+// chiral coefficient takes the factor instead).
 // ---------------------------------------------------------------------------
-template <typename real>
+template <bool RAW = false, typename real>
 __device__ __forceinline__ Sym5<real> molecular_field(const Stencil7<real>& st, const Model<real>& m,
                                                       Sym5<real> dq[3]) {
   const Sym5<real>& q = st.c;
-  dq[0] = half_diff(st.xp, st.xm);
-  dq[1] = half_diff(st.yp, st.ym);
-  dq[2] = half_diff(st.zp, st.zm);
+  if constexpr (RAW) {
+    dq[0] = diff5(st.xp, st.xm);
+    dq[1] = diff5(st.yp, st.ym);
+    dq[2] = diff5(st.zp, st.zm);
+  } else {
+    dq[0] = half_diff(st.xp, st.xm);
+    dq[1] = half_diff(st.yp, st.ym);
+    dq[2] = half_diff(st.zp, st.zm);
+  }
   const real qzz = q.zz();
   // Q.Q (symmetric)
   const real qq_xx = q.xx * q.xx + q.xy * q.xy + q.xz * q.xz;
@@ -319,12 +333,13 @@ __device__ __forceinline__ Sym5<real> molecular_field(const Stencil7<real>& st, 
   const real c_zz = dx.yz - dy.xz;
   (void)c_zz;
   const real bulk_iso = m.a_bulk + m.b_bulk * trq2 + m.kq0sq4;  // coefficient of -Q
+  const real kc = RAW ? real(0.5) * m.kq0x2 : m.kq0x2;           // of C + C^T
   Sym5<real> H;
-  H.xx = -bulk_iso * q.xx + m.b_bulk * (qq_xx - third * trq2) + m.K * l_xx - m.kq0x2 * (c_xx + c_xx);
-  H.xy = -bulk_iso * q.xy + m.b_bulk * qq_xy + m.K * l_xy - m.kq0x2 * (c_xy + c_yx);
-  H.xz = -bulk_iso * q.xz + m.b_bulk * qq_xz + m.K * l_xz - m.kq0x2 * (c_xz + c_zx);
-  H.yy = -bulk_iso * q.yy + m.b_bulk * (qq_yy - third * trq2) + m.K * l_yy - m.kq0x2 * (c_yy + c_yy);
-  H.yz = -bulk_iso * q.yz + m.b_bulk * qq_yz + m.K * l_yz - m.kq0x2 * (c_yz + c_zy);
+  H.xx = -bulk_iso * q.xx + m.b_bulk * (qq_xx - third * trq2) + m.K * l_xx - kc * (c_xx + c_xx);
+  H.xy = -bulk_iso * q.xy + m.b_bulk * qq_xy + m.K * l_xy - kc * (c_xy + c_yx);
+  H.xz = -bulk_iso * q.xz + m.b_bulk * qq_xz + m.K * l_xz - kc * (c_xz + c_zx);
+  H.yy = -bulk_iso * q.yy + m.b_bulk * (qq_yy - third * trq2) + m.K * l_yy - kc * (c_yy + c_yy);
+  H.yz = -bulk_iso * q.yz + m.b_bulk * qq_yz + m.K * l_yz - kc * (c_yz + c_zy);
   return H;
 }
 
@@ -375,9 +390,10 @@ __device__ __forceinline__ void lc_tau(const Sym5<real>& q, const Sym5<real>& h,
 
 // ---------------------------------------------------------------------------
 // dQ/dt of Eq. (Qevolution) + (mat_der):  Gamma H + S_traceless(W, Q) - u . D0 Q
-// with W_ab = D0_b u_a given as w[a][b].
+// with W_ab = D0_b u_a given as w[a][b] (RAW: dq and w are twice the central
+// derivatives, the plain differences; the factor 1/2 goes into the constants).
 // ---------------------------------------------------------------------------
-template <typename real>
+template <bool RAW = false, typename real>
 __device__ __forceinline__ Sym5<real> be_rate(const Sym5<real>& q, const Sym5<real>& h, const Sym5<real> dq[3],
                                               const real u[3], const real w[3][3], const Model<real>& m,
                                               bool flow) {
@@ -396,20 +412,21 @@ __device__ __forceinline__ Sym5<real> be_rate(const Sym5<real>& q, const Sym5<re
   // terms are A P + (A P)^T, and A P = A Q + A / 3, so only A Q is a product.
   // Tr S = (2 xi / 3) Tr D exactly (Tr P = 1, Tr(A Q) = Q:D = Tr(QW)), which the
   // traceless projection removes from the diagonal.
-  const real cpl = real(0.5) * (xi + real(1)), cmi = real(0.5) * (xi - real(1));
+  const real hw = RAW ? real(0.5) : real(1);  // w holds hw^-1 W
+  const real xw = hw * xi, cpl = real(0.5) * hw * (xi + real(1)), cmi = real(0.5) * hw * (xi - real(1));
   real A[3][3];
 #pragma unroll
   for (int a = 0; a < 3; ++a)
 #pragma unroll
-    for (int b = 0; b < 3; ++b) A[a][b] = a == b ? xi * w[a][a] : cpl * w[a][b] + cmi * w[b][a];
+    for (int b = 0; b < 3; ++b) A[a][b] = a == b ? xw * w[a][a] : cpl * w[a][b] + cmi * w[b][a];
   const real trQW = Q.a[0][0] * w[0][0] + Q.a[1][1] * w[1][1] + Q.a[2][2] * w[2][2] +
                     Q.a[0][1] * (w[0][1] + w[1][0]) + Q.a[0][2] * (w[0][2] + w[2][0]) +
-                    Q.a[1][2] * (w[1][2] + w[2][1]);
+                    Q.a[1][2] * (w[1][2] + w[2][1]);  // (times hw^-1)
   auto AQ = [&](int a, int b) { return A[a][0] * Q.a[0][b] + A[a][1] * Q.a[1][b] + A[a][2] * Q.a[2][b]; };
-  const real two_xi_tr = real(2) * xi * trQW;
-  const real xi3 = LCBP_Q(1, 3) * xi;
+  const real two_xi_tr = real(2) * xw * trQW;
+  const real xi3 = LCBP_Q(1, 3) * xw;
   // diagonal: 2 (AQ)_aa + (2 xi / 3) W_aa - 2 xi (Q_aa + 1/3) Tr(QW) - (2 xi / 9) Tr W
-  const real diag0 = LCBP_Q(2, 9) * xi * (w[0][0] + w[1][1] + w[2][2]) + LCBP_Q(1, 3) * two_xi_tr;
+  const real diag0 = LCBP_Q(2, 9) * xw * (w[0][0] + w[1][1] + w[2][2]) + LCBP_Q(1, 3) * two_xi_tr;
   real S[3][3];
   S[0][0] = real(2) * (AQ(0, 0) + xi3 * w[0][0]) - two_xi_tr * Q.a[0][0] - diag0;
   S[1][1] = real(2) * (AQ(1, 1) + xi3 * w[1][1]) - two_xi_tr * Q.a[1][1] - diag0;
@@ -417,12 +434,12 @@ __device__ __forceinline__ Sym5<real> be_rate(const Sym5<real>& q, const Sym5<re
   S[0][2] = (AQ(0, 2) + AQ(2, 0)) + xi3 * (w[0][2] + w[2][0]) - two_xi_tr * Q.a[0][2];
   S[1][2] = (AQ(1, 2) + AQ(2, 1)) + xi3 * (w[1][2] + w[2][1]) - two_xi_tr * Q.a[1][2];
   const real ux = u[0], uy = u[1], uz = u[2];
-  auto adv = [&](real gx, real gy, real gz) { return ux * gx + uy * gy + uz * gz; };
-  r.xx += S[0][0] - adv(dq[0].xx, dq[1].xx, dq[2].xx);
-  r.xy += S[0][1] - adv(dq[0].xy, dq[1].xy, dq[2].xy);
-  r.xz += S[0][2] - adv(dq[0].xz, dq[1].xz, dq[2].xz);
-  r.yy += S[1][1] - adv(dq[0].yy, dq[1].yy, dq[2].yy);
-  r.yz += S[1][2] - adv(dq[0].yz, dq[1].yz, dq[2].yz);
+  auto adv = [&](real gx, real gy, real gz) { return ux * gx + uy * gy + uz * gz; };  // (times hw^-1)
+  r.xx += S[0][0] - hw * adv(dq[0].xx, dq[1].xx, dq[2].xx);
+  r.xy += S[0][1] - hw * adv(dq[0].xy, dq[1].xy, dq[2].xy);
+  r.xz += S[0][2] - hw * adv(dq[0].xz, dq[1].xz, dq[2].xz);
+  r.yy += S[1][1] - hw * adv(dq[0].yy, dq[1].yy, dq[2].yy);
+  r.yz += S[1][2] - hw * adv(dq[0].yz, dq[1].yz, dq[2].yz);
   return r;
 }
 

@@ -495,7 +495,7 @@ __device__ __forceinline__ void qside_body(const CUtensorMap* tmQ, const CUtenso
         st.zm = ldq(qm, i0, i0);
         st.zp = ldq(qp, i0, i0);
         Sym5<V> dq[3];
-        const Sym5<V> h = molecular_field(st, mv, dq);
+        const Sym5<V> h = molecular_field<true>(st, mv, dq);
         Sym5<V> sg;
         V tu[3];
         // the ring warps (t >= NIN, a warp-uniform split) need tau only
@@ -539,7 +539,7 @@ __device__ __forceinline__ void qside_body(const CUtensorMap* tmQ, const CUtenso
       st.zm = ldq(qm, i0, i1);
       st.zp = ldq(qp, i0, i1);
       Sym5<V> dq[3];
-      const Sym5<V> h = molecular_field(st, mv, dq);
+      const Sym5<V> h = molecular_field<true>(st, mv, dq);
       Sym5<V> sg;
       V tu[3];
       lc_stress(st.c, h, mv.xi, sg, tu);
@@ -654,9 +654,9 @@ __device__ __forceinline__ void qside_body(const CUtensorMap* tmQ, const CUtenso
         const int hi0 = ty * ZM_TX + tx;
         h = ld5v<SPT>(hslot(z), TY * ZM_TX, hi0, hi0);
       } else {
-        dq[0] = half_diff(ldq(qc, qi0 + 1, qi1 + 1), ldq(qc, qi0 - 1, qi1 - 1));
-        dq[1] = half_diff(ldq(qc, qi0 + B::QW, qi1 + B::QW), ldq(qc, qi0 - B::QW, qi1 - B::QW));
-        dq[2] = half_diff(ldq(qp, qi0, qi1), ldq(qm, qi0, qi1));
+        dq[0] = diff5(ldq(qc, qi0 + 1, qi1 + 1), ldq(qc, qi0 - 1, qi1 - 1));
+        dq[1] = diff5(ldq(qc, qi0 + B::QW, qi1 + B::QW), ldq(qc, qi0 - B::QW, qi1 - B::QW));
+        dq[2] = diff5(ldq(qp, qi0, qi1), ldq(qm, qi0, qi1));
         const int hi0 = ty * ZM_TX + tx;
         h = ld5v<SPT>(hslot(z), TY * ZM_TX, hi0, hi0 + TYH * ZM_TX);
       }
@@ -680,9 +680,9 @@ __device__ __forceinline__ void qside_body(const CUtensorMap* tmQ, const CUtenso
       V by = -(half * (T(tc, 1) - T(tc, -1))) + half * (tz_p[1] - T(tm, 2 * TCS));
       V bz = -(half * (T(tc, TCS + 1) - T(tc, TCS - 1))) -
              half * (T(tc, 2 * TCS + L::TCOLS) - T(tc, 2 * TCS - L::TCOLS));
-      bx -= ddot(h, dq[0]);
-      by -= ddot(h, dq[1]);
-      bz -= ddot(h, dq[2]);
+      bx -= half * ddot(h, dq[0]);  // (dq: twice the central derivatives)
+      by -= half * ddot(h, dq[1]);
+      bz -= half * ddot(h, dq[2]);
       // velocity and its gradient from the rho u ring (components 1..3)
       const real* um = uslot(z - 1);
       const real* uc = uslot(z);
@@ -702,15 +702,15 @@ __device__ __forceinline__ void qside_body(const CUtensorMap* tmQ, const CUtenso
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
           u[a] = c[1 + a];
-          w[a][0] = half * (xp[1 + a] - xm[1 + a]);
-          w[a][1] = half * (yp[1 + a] - ym[1 + a]);
+          w[a][0] = xp[1 + a] - xm[1 + a];  // twice the central derivatives
+          w[a][1] = yp[1 + a] - ym[1 + a];
           V upz = zp[1 + a], umz = zm[1 + a];
           if (WALLS && z == 0) umz = -u[a];  // no slip half a spacing beyond the wall
           if (WALLS && z == nz - 1) upz = -u[a];
-          w[a][2] = half * (upz - umz);
+          w[a][2] = upz - umz;
         }
       }
-      const Sym5<V> r = be_rate(q, h, dq, u, w, mv, true);
+      const Sym5<V> r = be_rate<true>(q, h, dq, u, w, mv, true);
       // The site's 16 values (four groups; rho - 1 in the last place) of the
       // padded scratch for lane k:
       // at the site's padded position, and at its periodic images in the ghost
@@ -1310,7 +1310,7 @@ __device__ __forceinline__ void lbq_body(const CUtensorMap* tmPQ, const CUtensor
       st.zm = QS(nm, ca);
       st.zp = QS(np, ca);
       Sym5<V> dq[3];
-      const Sym5<V> h = molecular_field(st, mv, dq);
+      const Sym5<V> h = molecular_field<true>(st, mv, dq);
       V w[3][3];
       const V half = V(0.5);
       V uxp[3], uxm[3], uyp[3], uym[3], uzp[3], uzm[3];
@@ -1322,14 +1322,14 @@ __device__ __forceinline__ void lbq_body(const CUtensorMap* tmPQ, const CUtensor
       U3(nm, cu, uzm);
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
-        w[a][0] = half * (uxp[a] - uxm[a]);
-        w[a][1] = half * (uyp[a] - uym[a]);
+        w[a][0] = uxp[a] - uxm[a];  // twice the central derivatives
+        w[a][1] = uyp[a] - uym[a];
         V upz = uzp[a], umz = uzm[a];
         if (wl) umz = -u_y[a];  // no slip half a spacing beyond the wall
         if (wh) upz = -u_y[a];
-        w[a][2] = half * (upz - umz);
+        w[a][2] = upz - umz;
       }
-      const Sym5<V> r = be_rate(st.c, h, dq, u_y, w, mv, true);
+      const Sym5<V> r = be_rate<true>(st.c, h, dq, u_y, w, mv, true);
       // Q^n of the site: the flat field, or the Q mirror ([xx xy xz yy]
       // vectors, then the yz array)
       Sym5<V> q0;
