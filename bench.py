@@ -35,8 +35,8 @@ SEED = 20090119
 # read or write once (inputs + outputs)
 KERNEL_BYTES = {
     # fast path (z-marching, TMA-staged planes)
-    "qside": (5 + 4 + 10 + 5) * 4,                             # Q, rho u -> P (LB coefficients), Q*
-    "lbq": (15 + 10 + 5 + 3 + 1 + 5 + 15 + 4 + 5) * 4,         # f, P, Q*, u, rho, Q -> f, rho u, Q
+    "qside": (5 + 4 + 16) * 4,                                 # Q, rho u -> scratch (P, Q*, rho - 1)
+    "lbq": (15 + 16 + 4 + 5 + 15 + 4 + 5) * 4,                 # f, scratch, rho u, Q -> f, rho u, Q
     # generic path
     "field": (5 + 5 + 5 + 3) * 4,                              # Q -> H, sigma, tau
     "force_predict": (5 + 5 + 3 + 4 + 3 + 5) * 4,              # Q, H, tau, rho u -> b, Q*
@@ -48,18 +48,19 @@ STATE_BYTES = (15 + 5) * 2 * 4  # read + write of f and Q once per site-step (FP
 HBM_NOMINAL_GBS = 7900.0  # GB300 HBM3e data-sheet bandwidth (the measured copy peak is the roofline)
 # DRAM bytes per site of one launch of each fast kernel (dram__bytes_read.sum +
 # dram__bytes_write.sum), from an ncu capture of 160^3 FP32 near the 256^3
-# tuning (20 planes per CTA, one site per thread); summary and command in
-# profiles/step_256cube_fast_path.md.  Traffic per launch scales with the sites.
-# Valid only for the kernel sources it was taken on (hash below); otherwise null.
+# tuning (13 planes per CTA at 160^3, 14 at 256^3; one site per thread);
+# summary and command in profiles/step_256cube_fast_path.md.  Traffic per
+# launch scales with the sites.  Valid only for the kernel sources it was
+# taken on (hash below); otherwise null.
 MEASURED_TRAFFIC = {
     "sources": ["paper_0901_3293_gb300/csrc/zmarch.cu", "paper_0901_3293_gb300/csrc/common.cuh",
-                "paper_0901_3293_gb300/csrc/tma.cuh"],
-    "sha256_16": "d0d482438cf4c884",
-    # mean of the two launches of each kernel in the capture
-    "bytes_per_site": {"qside": (161966336 + 168289280 + 161996288 + 166206208) / 2 / 160 ** 3,
-                       "lbq": (641930752 + 357291520 + 643030784 + 358607360) / 2 / 160 ** 3},
-    # smsp__inst_executed.sum (warp instructions) x 32 of one launch (ncu --set full on the same case)
-    "thread_instr_per_site": {"qside": 145553136 * 32 / 160 ** 3, "lbq": 187514224 * 32 / 160 ** 3},
+                "paper_0901_3293_gb300/csrc/tma.cuh", "paper_0901_3293_gb300/csrc/kernels.h"],
+    "sha256_16": "b9914be038550aa1",
+    # one launch of each kernel in the capture (ncu --set full)
+    "bytes_per_site": {"qside": (179473152 + 215394048) / 160 ** 3,
+                       "lbq": (807546880 + 368372992) / 160 ** 3},
+    # smsp__inst_executed.sum (warp instructions) x 32 of the same launches
+    "thread_instr_per_site": {"qside": 108106052 * 32 / 160 ** 3, "lbq": 116463340 * 32 / 160 ** 3},
 }
 ORACLE_SAMPLE = 32  # side of the periodic cube the oracle steps (two BPII unit cells)
 WALL_Q = (0.2, 0.0, 0.0, -0.1, 0.0)  # planar anchoring S (x x - I/3), S = 0.3, on the ghost planes
