@@ -5,6 +5,7 @@
     python -m paper_0901_3293_gb300.profile --texture --dims 256 256 256 --steps 3
     python -m paper_0901_3293_gb300.profile --batch --steps 4
     python -m paper_0901_3293_gb300.profile --diag --size 160 --steps 3
+    python -m paper_0901_3293_gb300.profile --train --dims 64 64 64 --steps 10
 
 Each step launches the step kernels once (no CUDA graph), so a profiler can
 select them by name and launch index.  --conv instead runs surrogate calls
@@ -17,6 +18,9 @@ tuning), then `steps` single steps inside the NVTX range "timed", so that a
 profiler can take exactly those launches (--nvtx --nvtx-include "timed/").
 --diag runs the FP64 diagnostics (free energy, mass and momentum, defect
 fraction: one pass) `steps` times on the L^3 lattice after one step.
+--train runs `steps` surrogate training steps (forward, backward, weight
+gradients on the tensor cores, masked loss and Adam) on a random crop of the
+given dims, after three untimed ones, inside the NVTX range "timed".
 """
 
 from __future__ import annotations
@@ -40,6 +44,7 @@ def main():
     ap.add_argument("--texture", action="store_true")
     ap.add_argument("--batch", action="store_true")
     ap.add_argument("--diag", action="store_true")
+    ap.add_argument("--train", action="store_true")
     args = ap.parse_args()
     build.build()
     torch.cuda.set_device(0)
@@ -56,6 +61,32 @@ def main():
         t0 = time.perf_counter()
         sur.step(lat, 1.0, -0.5, args.steps)
         print({"dims": args.dims, "calls": args.steps, "ms_per_call": 1e3 * (time.perf_counter() - t0) / args.steps})
+        return
+    if args.train:
+        import time
+
+        import numpy as np
+        nx, ny, nz = args.dims
+        sur = lcbp.Surrogate(nx, ny, nz, training=True)
+        rng = np.random.default_rng(0)
+        sur.set_params((rng.normal(size=sur.count) * 0.02).astype(np.float32))
+        dev = dict(device="cuda", dtype=torch.float32)
+        q = torch.from_numpy(rng.uniform(-0.3, 0.3, (5, nz, ny, nx)).astype(np.float32)).to(**dev)
+        u = torch.from_numpy(rng.uniform(-1e-3, 1e-3, (3, nz, ny, nx)).astype(np.float32)).to(**dev)
+        r = torch.from_numpy(rng.uniform(-1e-4, 1e-4, (5, nz, ny, nx)).astype(np.float32)).to(**dev)
+        dq = torch.from_numpy(rng.uniform(-1e-3, 1e-3, (5, nz, ny, nx)).astype(np.float32)).to(**dev)
+        mask = torch.ones((nz, ny, nx), **dev)
+        for _ in range(3):
+            sur.train_step(q, u, r, 1.0, -0.5, dq, mask)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("timed")
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            loss = sur.train_step(q, u, r, 1.0, -0.5, dq, mask)
+        dt = time.perf_counter() - t0
+        torch.cuda.nvtx.range_pop()
+        print({"dims": args.dims, "train_steps": args.steps, "ms_per_step": 1e3 * dt / args.steps, "loss": loss})
+        sur.close()
         return
     if args.batch:
         import time

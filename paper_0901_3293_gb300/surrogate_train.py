@@ -421,11 +421,12 @@ def main():
         if logf:
             # one line per logged step: the plain run, and the judged runs of the
             # trained and the zero network with their relative F error
+            g7 = lambda v: float("%.7g" % v)  # noqa: E731  (seven significant digits in the log)
             for t, F, D in rows:
-                line = {"kappa": kappa, "k": k, "t": t, "F_plain": F, "defect_plain": D}
+                line = {"kappa": kappa, "k": k, "t": t, "F_plain": g7(F), "defect_plain": g7(D)}
                 for name, key in (("network", "judged"), ("zero_network", "judged_zero")):
                     Fj, Dj, e = logged[name][t]
-                    line.update({"F_" + key: Fj, "defect_" + key: Dj, "rel_F_err_" + key: float("%.4g" % e)})
+                    line.update({"F_" + key: g7(Fj), "defect_" + key: g7(Dj), "rel_F_err_" + key: float("%.3g" % e)})
                 logf.write(json.dumps(line) + "\n")
         runs[str(kappa)] = out
         note({"kappa": kappa, **out})
