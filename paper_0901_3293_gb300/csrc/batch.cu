@@ -39,6 +39,11 @@ struct lcbp_batch {
   char* ws;
   void *f[2], *rhou[2], *q, *qs, *h, *sig, *tau, *b, *staging;
   void* pq;  // the fast kernels' padded scratch, class by class (overlays h, sig, tau, b)
+  // the fast kernels' state: padded mirrors of Q and rho u (two buffers),
+  // class by class, and a Q mirror the tuner writes; the flat fields and the
+  // mirrors are kept in step lazily (flat_ok / mirror_ok)
+  void *qm, *qm_tune, *um[2];
+  bool flat_ok, mirror_ok;
   long long staging_elems;
   void* d_rep;
   Tile* d_tiles;
@@ -98,24 +103,24 @@ bool use_fast(const lcbp_batch* b) {
   return fast_eligible(b) && (b->path_req == LCBP_PATH_FAST1 || b->fast_pick);
 }
 
-// 5-D tensor maps of every class: field [c][z][y][x] per replica, replicas of
-// a class back to back (stride comps * padded sites); the padded scratch of a
-// class holds its replicas back to back too (stride 15 * (nx+4)(ny+2)nz)
+// Tensor maps of every class, the replica outermost (replicas of a class back
+// to back): the Q mirrors as their [xx xy xz yy] vectors and their yz arrays
+// (replica stride 5 cq), the rho u mirrors (stride 4 cu) and the padded
+// scratch (stride 16 (nx+4)(ny+2)nz)
 bool build_maps(lcbp_batch* b) {
   const int ty = b->dtype == LCBP_F64 ? zm_tile_rows<double>() : zm_tile_rows<float>();
   for (int k = 0; k < b->zb.nclass; ++k) {
     const ZmClass& c = b->zb.c[k];
-    const int r0 = b->order[c.rep0];
     const cuuint64_t es = b->es;
-    const cuuint64_t nx = c.G.nx, ny = c.G.ny, nz = c.G.nz, n = c.G.n;
-    const cuuint64_t npad = c.count > 1 ? (cuuint64_t)(b->base[b->order[c.rep0 + 1]] - b->base[r0]) : (cuuint64_t)n;
-    // comps of a field starting at component c0 of a C-component field
-    auto map = [&](CUtensorMap* tm, void* field, int C, int c0, int comps, int rows) {
-      const cuuint64_t dims[5] = {nx, ny, nz, (cuuint64_t)comps, (cuuint64_t)c.count};
-      const cuuint64_t strides[4] = {nx * es, nx * ny * es, n * es, (cuuint64_t)C * npad * es};
-      const cuuint32_t box[5] = {(cuuint32_t)kZmBoxX, (cuuint32_t)rows, 1, (cuuint32_t)comps, 1};
-      void* base = static_cast<char*>(field) + ((size_t)C * b->base[r0] + (size_t)c0 * n) * b->es;
-      return encode_tiled(tm, base, 5, dims, strides, box, b->dtype);
+    const cuuint64_t nx = c.G.nx, ny = c.G.ny, nz = c.G.nz;
+    const cuuint64_t nxm = zm_mirror_nx(c.G.nx), nyq = ny + 4, nyu = ny + 2, cq = nxm * nyq * nz, cu = nxm * nyu * nz;
+    // a plane-interleaved mirror array [replica][nz][nym][w] with replica stride rs elements
+    auto mirror = [&](CUtensorMap* tm, void* arr, long long off, cuuint64_t w, cuuint64_t nym, cuuint64_t rs,
+                      int inner, int rows) {
+      const cuuint64_t dims[4] = {w, nym, nz, (cuuint64_t)c.count};
+      const cuuint64_t strides[3] = {w * es, w * nym * es, rs * es};
+      const cuuint32_t box[4] = {(cuuint32_t)inner, (cuuint32_t)rows, 1, 1};
+      return encode_tiled(tm, static_cast<char*>(arr) + (size_t)off * es, 4, dims, strides, box, b->dtype);
     };
     const cuuint64_t nxp = nx + kZmPadX, nyp = ny + 2, cp = nxp * nyp * nz;
     // the scratch [replica][z][group][Y][X][4] as (4 X, Y, group, z, replica)
@@ -123,14 +128,17 @@ bool build_maps(lcbp_batch* b) {
     const cuuint64_t pstr[4] = {4 * nxp * es, 4 * nxp * nyp * es, (cuuint64_t)kZmPQ * nxp * nyp * es,
                                 (cuuint64_t)kZmPQ * cp * es};
     const cuuint32_t pbox[5] = {(cuuint32_t)(4 * kZmBoxXP), (cuuint32_t)(ty + 2), (cuuint32_t)kZmPQG, 1, 1};
-    bool ok = map(&b->maps[0].q[k], b->q, 5, 0, 5, ty + 4) && map(&b->maps[0].u[k], b->rhou[0], 4, 0, 4, ty + 2) &&
-              map(&b->maps[1].u[k], b->rhou[1], 4, 0, 4, ty + 2) &&
-              map(&b->maps[0].u3[k], b->rhou[0], 4, 1, 3, ty + 2) &&
-              map(&b->maps[1].u3[k], b->rhou[1], 4, 1, 3, ty + 2) &&
+    bool ok = mirror(&b->maps[0].q[k], b->qm, c.qm0, 4 * nxm, nyq, 5 * cq, 4 * kZmBoxX, ty + 4) &&
+              mirror(&b->maps[0].q1[k], b->qm, c.qm0 + 4 * (long long)cq, nxm, nyq, 5 * cq, kZmBoxX, ty + 4) &&
+              mirror(&b->maps[0].u[k], b->um[0], c.um0, 4 * nxm, nyu, 4 * cu, 4 * kZmBoxXU, ty + 2) &&
+              mirror(&b->maps[1].u[k], b->um[1], c.um0, 4 * nxm, nyu, 4 * cu, 4 * kZmBoxXU, ty + 2) &&
               encode_tiled(&b->maps[0].pq[k], static_cast<char*>(b->pq) + (size_t)c.pq0 * b->es, 5, pdims, pstr,
                            pbox, b->dtype);
     if (!ok) return false;
+    b->maps[0].u3[k] = b->maps[0].u[k];
+    b->maps[1].u3[k] = b->maps[1].u[k];
     b->maps[1].q[k] = b->maps[0].q[k];
+    b->maps[1].q1[k] = b->maps[0].q1[k];
     b->maps[1].pq[k] = b->maps[0].pq[k];
   }
   return true;
@@ -150,7 +158,7 @@ void set_zc(lcbp_batch* b, const int* zc) {
     c.G.nxp = c.G.nx + kZmPadX;
     c.G.nyp = c.G.ny + 2;
     c.G.cp = (long long)c.G.nxp * c.G.nyp * c.G.nz;
-    c.G.nxm = zm_mirror_nx(c.G.nx);  // (batches keep flat state: no mirrors)
+    c.G.nxm = zm_mirror_nx(c.G.nx);
     c.G.nyq = c.G.ny + 4;
     c.G.nyu = c.G.ny + 2;
     c.G.cq = (long long)c.G.nxm * c.G.nyq * c.G.nz;
@@ -168,15 +176,67 @@ ZmBatchArgs zm_args(lcbp_batch* b) {
   a.maps = &b->maps[b->cur];
   a.reps = b->d_rep;
   a.order = b->d_order;
-  a.q = b->q;
+  a.q = b->qm;
   a.qout = nullptr;
   a.pq = b->pq;
   a.f = b->f[b->cur];
   a.fnew = b->f[b->cur ^ 1];
-  a.rhou = b->rhou[b->cur];
-  a.rhou_new = b->rhou[b->cur ^ 1];
+  a.rhou = b->um[b->cur];
+  a.rhou_new = b->um[b->cur ^ 1];
   a.err = b->d_err;
   return a;
+}
+
+// Q and rho u (the current buffer) of every replica of the fast-path classes,
+// between the flat fields and the padded mirrors: unpack (mirrors -> flat) or
+// pack (flat -> mirrors, periodic images included)
+cudaError_t mirror_copy(lcbp_batch* b, bool to_flat) {
+  cudaError_t e = cudaSuccess;
+  for (int k = 0; k < b->zb.nclass && e == cudaSuccess; ++k) {
+    const ZmClass& c = b->zb.c[k];
+    const int nx = c.G.nx, ny = c.G.ny, nz = c.G.nz, nxm = zm_mirror_nx(nx), X = kZmMirX;
+    const long long cq = (long long)nxm * (ny + 4) * nz, cu = (long long)nxm * (ny + 2) * nz;
+    for (int j = 0; j < c.count && e == cudaSuccess; ++j) {
+      const int r = b->order[c.rep0 + j];
+      char* qm = static_cast<char*>(b->qm) + (size_t)(c.qm0 + j * 5 * cq) * b->es;
+      char* um = static_cast<char*>(b->um[b->cur]) + (size_t)(c.um0 + j * 4 * cu) * b->es;
+      void* q = static_cast<char*>(b->q) + (size_t)5 * b->base[r] * b->es;
+      void* ru = static_cast<char*>(b->rhou[b->cur]) + (size_t)4 * b->base[r] * b->es;
+      const bool d = b->dtype == LCBP_F64;
+      if (to_flat) {
+        e = d ? launch_unpack<double>(qm, q, 5, 1, nx, ny, nz, X, 2, nxm, ny + 4, b->stream)
+              : launch_unpack<float>(qm, q, 5, 1, nx, ny, nz, X, 2, nxm, ny + 4, b->stream);
+        if (e == cudaSuccess)
+          e = d ? launch_unpack<double>(um, ru, 4, 1, nx, ny, nz, X, 1, nxm, ny + 2, b->stream)
+                : launch_unpack<float>(um, ru, 4, 1, nx, ny, nz, X, 1, nxm, ny + 2, b->stream);
+      } else {
+        e = d ? launch_pack<double>(q, qm, 5, 1, nx, ny, nz, X, 2, nxm, ny + 4, b->stream)
+              : launch_pack<float>(q, qm, 5, 1, nx, ny, nz, X, 2, nxm, ny + 4, b->stream);
+        if (e == cudaSuccess)
+          e = d ? launch_pack<double>(ru, um, 4, 1, nx, ny, nz, X, 1, nxm, ny + 2, b->stream)
+                : launch_pack<float>(ru, um, 4, 1, nx, ny, nz, X, 1, nxm, ny + 2, b->stream);
+      }
+    }
+  }
+  return e;
+}
+
+// the flat fields current (readers, writers and the generic kernels)
+int sync_flat(lcbp_batch* b) {
+  if (b->flat_ok) return LCBP_OK;
+  const cudaError_t e = mirror_copy(b, true);
+  if (e != cudaSuccess) return cuda_fail(e, "mirror unpack");
+  b->flat_ok = true;
+  return LCBP_OK;
+}
+
+// the mirrors current (the fast kernels)
+int sync_mirror(lcbp_batch* b) {
+  if (b->mirror_ok || !b->fast_ok) return LCBP_OK;
+  const cudaError_t e = mirror_copy(b, false);
+  if (e != cudaSuccess) return cuda_fail(e, "mirror pack");
+  b->mirror_ok = true;
+  return LCBP_OK;
 }
 
 cudaError_t launch_zm(lcbp_batch* b, const ZmBatchArgs& a) {
@@ -293,7 +353,7 @@ int tune_fast(lcbp_batch* b, float* best_ms) {
   auto time_zc = [&](const int* zc) {
     set_zc(b, zc);
     ZmBatchArgs a = zm_args(b);
-    a.qout = b->qs;  // scratch the fast kernels do not use: the state is left untouched
+    a.qout = b->qm_tune;  // a mirror the state does not use: the state is left untouched
     float t = 1e30f;
     for (int rep = 0; rep < 3 && err == cudaSuccess; ++rep) {
       cudaEventRecord(e0, b->stream);
@@ -381,7 +441,8 @@ int tune_generic(lcbp_batch* b, float* best_ms) {
 // tune both and keep the faster.
 int tune(lcbp_batch* b) {
   float t_fast = 1e30f, t_gen = 1e30f;
-  int rc = LCBP_OK;
+  int rc = sync_flat(b);  // the generic tuner reads the flat fields, the fast one the mirrors
+  if (!rc && fast_eligible(b)) rc = sync_mirror(b);
   if (fast_eligible(b)) rc = tune_fast(b, &t_fast);
   if (!rc && (!fast_eligible(b) || b->path_req == LCBP_PATH_AUTO)) rc = tune_generic(b, &t_gen);
   if (rc) return rc;
@@ -424,6 +485,8 @@ int moments_all(lcbp_batch* b) {
 }
 
 int diag(lcbp_batch* b, int r, double threshold, int with_f) {
+  const int rs = sync_flat(b);
+  if (rs) return rs;
   DiagGeom g{b->nx[r], b->ny[r], b->nz[r], b->n[r], b->base[r], b->p[r].A0, b->p[r].gamma, b->p[r].K, b->p[r].q0};
   cudaError_t e = b->dtype == LCBP_F64 ? launch_diag_one<double>(g, b->q, b->f[b->cur], with_f, threshold,
                                                                  b->d_partials, b->d_out, b->stream)
@@ -528,6 +591,18 @@ int lcbp_batch_create(int R, const int* dims, const lcbp_params* params, int dty
     c.pq0 = pq_tot;
     pq_tot += ((long long)c.count * zm_pq_elems(c.G.nx, c.G.ny, c.G.nz) + 63) / 64 * 64;
   }
+  // the fast path's mirrors of Q and rho u, class by class (64-element aligned blocks)
+  long long qm_tot = 0, um_tot = 0;
+  for (int k = 0; k < b->zb.nclass && b->fast_ok; ++k) {
+    ZmClass& c = b->zb.c[k];
+    const long long nxm = zm_mirror_nx(c.G.nx), cq = nxm * (c.G.ny + 4) * c.G.nz, cu = nxm * (c.G.ny + 2) * c.G.nz;
+    c.qm0 = qm_tot;
+    qm_tot += ((long long)c.count * 5 * cq + 63) / 64 * 64;
+    c.um0 = um_tot;
+    um_tot += ((long long)c.count * 4 * cu + 63) / 64 * 64;
+  }
+  b->flat_ok = true;
+  b->mirror_ok = false;
   b->path_req = LCBP_PATH_AUTO;
   b->fast_pick = true;
   b->zc = 0;
@@ -566,6 +641,11 @@ int lcbp_batch_create(int R, const int* dims, const lcbp_params* params, int dty
   o = a256(o + (kDiagPartials + 8) * 8);
   const size_t off_order = o;
   o = a256(o + (size_t)R * sizeof(int) + sizeof(int));
+  size_t off_mir[4];
+  for (int i = 0; i < 4; ++i) {  // Q mirrors, the tuner's Q mirrors, rho u mirrors 0 and 1
+    off_mir[i] = o;
+    o = a256(o + (size_t)(i < 2 ? qm_tot : um_tot) * b->es);
+  }
   cudaError_t e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaMalloc(&b->ws, o);
   if (e != cudaSuccess) {
@@ -595,6 +675,10 @@ int lcbp_batch_create(int R, const int* dims, const lcbp_params* params, int dty
   b->d_partials = reinterpret_cast<double*>(w + off_part);
   b->d_out = b->d_partials + kDiagPartials;
   b->d_order = reinterpret_cast<int*>(w + off_order);
+  b->qm = w + off_mir[0];
+  b->qm_tune = w + off_mir[1];
+  b->um[0] = w + off_mir[2];
+  b->um[1] = w + off_mir[3];
   b->d_err = b->d_order + R;
   e = cudaMemsetAsync(b->ws, 0, off_stage, b->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(b->d_err, 0, sizeof(int), b->stream);
@@ -672,6 +756,9 @@ int lcbp_batch_init_q(lcbp_batch* b, int r, int kind, double amplitude, double n
   if (kind < LCBP_BPII || kind > LCBP_SLAB_BPII_IN_CHOL_Z) return fail(LCBP_EINVAL, "unknown initial kind %d", kind);
   if (!(noise >= 0.0)) return fail(LCBP_EINVAL, "noise < 0");
   if (kind >= LCBP_SLAB_BPII_IN_CHOL && !region) return fail(LCBP_EINVAL, "slab kinds need region");
+  rc = sync_flat(b);  // the other replicas' flat Q stays current
+  if (rc) return rc;
+  b->mirror_ok = false;
   InitQArgs a{kind, amplitude, noise, seed, region ? region[0] : 0};
   cudaError_t e = cudaMemcpyAsync(b->d_seed + r, &seed, 8, cudaMemcpyHostToDevice, b->stream);
   const Tile* t0 = b->d_tiles + b->tile_begin[r];
@@ -689,6 +776,9 @@ int lcbp_batch_set_q(lcbp_batch* b, int r, const void* q5, int dtype) {
   if (!rc) rc = check_r(b, r);
   if (rc) return rc;
   if (!q5 || !valid_dtype(dtype)) return fail(LCBP_EINVAL, "bad buffer or dtype");
+  rc = sync_flat(b);
+  if (rc) return rc;
+  b->mirror_ok = false;
   return transfer(field(b, b->q, 5, r), b->dtype, const_cast<void*>(q5), dtype, 5 * b->n[r], true, b->staging,
                   b->staging_elems, b->stream);
 }
@@ -697,6 +787,9 @@ int lcbp_batch_init_f_equilibrium(lcbp_batch* b, double rho0) {
   int rc = check_b(b);
   if (rc) return rc;
   if (!(rho0 > 0)) return fail(LCBP_EINVAL, "rho0 <= 0");
+  rc = sync_flat(b);
+  if (rc) return rc;
+  b->mirror_ok = false;
   StepArgs a = args(b);
   cudaError_t e = b->dtype == LCBP_F64 ? launch_field<double>(a, b->stream) : launch_field<float>(a, b->stream);
   if (e == cudaSuccess)
@@ -722,6 +815,11 @@ int lcbp_batch_step(lcbp_batch* b, int nsteps) {
     if (rc) return rc;
     drop_graph(b);
   }
+  const bool fast = use_fast(b);
+  rc = fast ? sync_mirror(b) : sync_flat(b);
+  if (rc) return rc;
+  if (fast) b->flat_ok = false;
+  else b->mirror_ok = false;
   cudaError_t e = cudaSuccess;
   int left = nsteps;
   if (b->cur == 1) {
@@ -755,6 +853,8 @@ int lcbp_batch_read_q(lcbp_batch* b, int r, void* dst, int dtype) {
   if (!rc) rc = check_r(b, r);
   if (rc) return rc;
   if (!dst || !valid_dtype(dtype)) return fail(LCBP_EINVAL, "bad buffer or dtype");
+  rc = sync_flat(b);
+  if (rc) return rc;
   return transfer(field(b, b->q, 5, r), b->dtype, dst, dtype, 5 * b->n[r], false, b->staging, b->staging_elems,
                   b->stream);
 }
@@ -764,6 +864,8 @@ int lcbp_batch_read_u(lcbp_batch* b, int r, void* dst, int dtype) {
   if (!rc) rc = check_r(b, r);
   if (rc) return rc;
   if (!dst || !valid_dtype(dtype)) return fail(LCBP_EINVAL, "bad buffer or dtype");
+  rc = sync_flat(b);
+  if (rc) return rc;
   void* u = static_cast<char*>(field(b, b->rhou[b->cur], 4, r)) + b->n[r] * b->es;
   return transfer(u, b->dtype, dst, dtype, 3 * b->n[r], false, b->staging, b->staging_elems, b->stream);
 }

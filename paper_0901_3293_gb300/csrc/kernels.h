@@ -221,6 +221,8 @@ struct ZmClass {
   int rep0;          // first entry of the class in the replica order table
   int count;         // replicas in the class
   long long pq0;     // first element of the class's padded scratch (replica j at pq0 + j * 16 * cp)
+  long long qm0;     // first element of the class's Q mirrors (replica j at qm0 + j * 5 * cq)
+  long long um0;     // first element of the class's rho u mirrors (replica j at um0 + j * 4 * cu)
 };
 struct ZmBatch {
   int nclass;
@@ -229,16 +231,20 @@ struct ZmBatch {
 };
 // per class: Q (box rows TY + 4), rho u (4 components), the padded scratch
 // (15), u (rho u components 1..3); box rows TY + 2 but for Q; 5-D
+// Per class, with the replica as the outermost coordinate: the Q mirrors'
+// [xx xy xz yy] vectors (q) and yz arrays (q1), the rho u mirrors (u; u3 the
+// same for k_lbq) and the padded scratch (pq)
 struct ZmBatchMaps {
-  CUtensorMap q[kZmMaxClasses], u[kZmMaxClasses], pq[kZmMaxClasses], u3[kZmMaxClasses];
+  CUtensorMap q[kZmMaxClasses], q1[kZmMaxClasses], u[kZmMaxClasses], pq[kZmMaxClasses], u3[kZmMaxClasses];
 };
 struct ZmBatchArgs {
   ZmBatch B;
   const ZmBatchMaps* maps;  // host copy (rho u maps of the current buffer)
   const void* reps;         // device Replica<real>[R]: base offsets and models
   const int* order;         // device: replica indices, class by class in storage order
-  void *q, *qout, *pq;      // qout: nullptr = update Q in place; pq: padded scratch of all classes
-  void *f, *fnew, *rhou, *rhou_new;
+  void *q, *qout, *pq;      // Q mirrors of all classes; qout: nullptr = update them in place; pq: padded scratch
+  void *f, *fnew;           // the flat populations
+  void *rhou, *rhou_new;    // rho u mirrors of all classes (current, next)
   int* err;
 };
 template <typename real>

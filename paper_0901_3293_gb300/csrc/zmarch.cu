@@ -284,7 +284,7 @@ __device__ __forceinline__ void qside_body(const CUtensorMap* tmQ, const CUtenso
                                            const Model<real> m, int bt, int rc, const real* __restrict__ Q,
                                            const real* __restrict__ rhou, const real* __restrict__ bext,
                                            real* __restrict__ pq, int* __restrict__ err, const Sym5<real> qw) {
-  constexpr bool PAD = !BATCH;  // a single lattice stages its padded mirrors: no patching
+  constexpr bool PAD = true;  // the state is staged from its padded mirrors: no patching
   using L = QsideSmem<real, TY, PAD>;
   using B = StateBox<PAD>;
   using V = typename LaneT<real, SPT>::V;
@@ -320,7 +320,7 @@ __device__ __forceinline__ void qside_body(const CUtensorMap* tmQ, const CUtenso
     *abort_flag = 0;
     mbar_init_fence();
     tma_prefetch_desc(tmQ);
-    if constexpr (PAD) tma_prefetch_desc(tmQ1);
+    if constexpr (PAD) tma_prefetch_desc(tmQ1);  // (null only where PAD is off)
     tma_prefetch_desc(tmU);
   }
   fill_wrap_tables(xw, yw, L::QROWS, nx, ny, x0, y0 - 2);
@@ -337,8 +337,13 @@ __device__ __forceinline__ void qside_body(const CUtensorMap* tmQ, const CUtenso
     mbar_arrive_expect_tx(bar, qbytes);
     if constexpr (PAD) {  // the mirror's [xx xy xz yy] vectors, then its yz array
       const int X = x0 - B::QX + B::QPX, Y = y0 - 2 + B::QPY;
-      tma_load_3d(qslot(p), tmQ, 4 * X, Y, wrap(p, nz), bar);
-      tma_load_3d(qslot(p) + 4 * L::QCS, tmQ1, X, Y, wrap(p, nz), bar);
+      if constexpr (BATCH) {  // (replica rc of the class)
+        tma_load_4d(qslot(p), tmQ, 4 * X, Y, wrap(p, nz), rc, bar);
+        tma_load_4d(qslot(p) + 4 * L::QCS, tmQ1, X, Y, wrap(p, nz), rc, bar);
+      } else {
+        tma_load_3d(qslot(p), tmQ, 4 * X, Y, wrap(p, nz), bar);
+        tma_load_3d(qslot(p) + 4 * L::QCS, tmQ1, X, Y, wrap(p, nz), bar);
+      }
     } else {
       zm_load<BATCH>(qslot(p), tmQ, x0 - B::QX + B::QPX, y0 - 2 + B::QPY, wrap(p, nz), rc, bar);
     }
@@ -347,8 +352,12 @@ __device__ __forceinline__ void qside_body(const CUtensorMap* tmQ, const CUtenso
     const unsigned k = p - (z0 - 1);
     uint64_t* bar = &bars[L::QSLOTS + k % L::USLOTS];
     mbar_arrive_expect_tx(bar, ubytes);
-    if constexpr (PAD) tma_load_3d(uslot(p), tmU, 4 * (x0 - B::UX + B::UPX), y0 - 1 + B::UPY, wrap(p, nz), bar);
-    else zm_load<BATCH>(uslot(p), tmU, x0 - B::UX + B::UPX, y0 - 1 + B::UPY, wrap(p, nz), rc, bar);
+    if constexpr (PAD && BATCH)
+      tma_load_4d(uslot(p), tmU, 4 * (x0 - B::UX + B::UPX), y0 - 1 + B::UPY, wrap(p, nz), rc, bar);
+    else if constexpr (PAD)
+      tma_load_3d(uslot(p), tmU, 4 * (x0 - B::UX + B::UPX), y0 - 1 + B::UPY, wrap(p, nz), bar);
+    else
+      zm_load<BATCH>(uslot(p), tmU, x0 - B::UX + B::UPX, y0 - 1 + B::UPY, wrap(p, nz), rc, bar);
   };
   // Q and rho u at box index i0 (lane 0) and i1 (lane 1) of a staged slot:
   // the padded mirrors stage [row][col][4] vectors (Q: then its yz as
@@ -845,8 +854,7 @@ __device__ __forceinline__ ZmGeom zm_class_geom(const ZmBatch& B, int k) {
 template <typename real, int TY>
 __global__ void __launch_bounds__(qside_threads<TY, 1>(), sizeof(real) == 4 ? 2 : 1)
     k_qside_batch(const __grid_constant__ ZmBatchMaps maps, ZmBatch B, const Replica<real>* __restrict__ reps,
-                  const int* __restrict__ order, const real* __restrict__ Q, const real* __restrict__ rhou,
-                  real* __restrict__ pq, int* __restrict__ err) {
+                  const int* __restrict__ order, real* __restrict__ pq, int* __restrict__ err) {
   const ZmItem it = zm_item(B);
   const ZmGeom G = zm_class_geom(B, it.k);
   int rep0 = B.c[0].rep0;
@@ -858,18 +866,19 @@ __global__ void __launch_bounds__(qside_threads<TY, 1>(), sizeof(real) == 4 ? 2 
       pq0 = B.c[i].pq0;
     }
   const int r = order[rep0 + it.j];
-  const long long o = reps[r].base;
   const Model<real> m = reps[r].m;
-  // the class's maps, selected at compile-time offsets (a runtime index into
-  // the parameter arrays would copy them to local memory)
-  const CUtensorMap *mq = &maps.q[0], *mu = &maps.u[0];
+  // the class's maps (replica it.j is their outermost coordinate), selected at
+  // compile-time offsets (a runtime index into the parameter arrays would copy
+  // them to local memory)
+  const CUtensorMap *mq = &maps.q[0], *mq1 = &maps.q1[0], *mu = &maps.u[0];
 #pragma unroll
   for (int i = 1; i < kZmMaxClasses; ++i)
     if (i == it.k) {
       mq = &maps.q[i];
+      mq1 = &maps.q1[i];
       mu = &maps.u[i];
     }
-  qside_body<real, TY, 1, true, false>(mq, nullptr, mu, G, m, it.bt, it.j, Q + 5 * o, rhou + 4 * o, nullptr,
+  qside_body<real, TY, 1, true, false>(mq, mq1, mu, G, m, it.bt, it.j, nullptr, nullptr, nullptr,
                                        pq + pq0 + (long long)it.j * kZmPQ * G.cp, err, Sym5<real>{});
 }
 
@@ -932,7 +941,7 @@ __device__ __forceinline__ void lbq_body(const CUtensorMap* tmPQ, const CUtensor
                                          const real* __restrict__ rhou, const real* __restrict__ Qin,
                                          real* __restrict__ fnew, real* __restrict__ rhou_new,
                                          real* __restrict__ Qout, int* __restrict__ err, const Sym5<real> qw) {
-  constexpr bool PAD = !BATCH;  // a single lattice reads and writes the padded mirrors of Q and rho u
+  constexpr bool PAD = true;  // the state is read from and written to its padded mirrors
   using L = LbqSmem<real, TY, PAD>;
   using B = StateBox<PAD>;
   using V = typename LaneT<real, SPT>::V;
@@ -991,7 +1000,9 @@ __device__ __forceinline__ void lbq_body(const CUtensorMap* tmPQ, const CUtensor
     // the scratch as (4 X, Y, group, z): x coordinate in elements of 4 per site
     if constexpr (BATCH) tma_load_5d(sl, tmPQ, 4 * x0, y0, 0, zz, rc, bar);
     else tma_load_4d(sl, tmPQ, 4 * x0, y0, 0, zz, bar);
-    if constexpr (PAD) {
+    if constexpr (PAD && BATCH) {
+      tma_load_4d(sl + L::OFF_U, tmU3, 4 * (x0 - B::UX + B::UPX), y0 - 1 + B::UPY, zz, rc, bar);
+    } else if constexpr (PAD) {
       tma_load_3d(sl + L::OFF_U, tmU3, 4 * (x0 - B::UX + B::UPX), y0 - 1 + B::UPY, zz, bar);
       // the populations of plane p (pulled from plane p-1 on) and Q^n of plane
       // p-1, into L2 a plane ahead of their plain loads
@@ -1396,17 +1407,23 @@ __global__ void __launch_bounds__(ZM_TX* TY / SPT, 2)
 template <typename real, int TY>
 __global__ void __launch_bounds__(ZM_TX* TY, 2)
     k_lbq_batch(const __grid_constant__ ZmBatchMaps maps, ZmBatch B, const Replica<real>* __restrict__ reps,
-                const int* __restrict__ order, const real* __restrict__ f, const real* __restrict__ rhou,
-                const real* __restrict__ Qin, real* __restrict__ fnew, real* __restrict__ rhou_new,
-                real* __restrict__ Qout, int* __restrict__ err) {
+                const int* __restrict__ order, const real* __restrict__ f, const real* __restrict__ Qin,
+                real* __restrict__ fnew, real* __restrict__ rhou_new, real* __restrict__ Qout,
+                int* __restrict__ err) {
   const ZmItem it = zm_item(B);
   const ZmGeom G = zm_class_geom(B, it.k);
   int rep0 = B.c[0].rep0;
+  long long qm0 = B.c[0].qm0, um0 = B.c[0].um0;
 #pragma unroll
   for (int i = 1; i < kZmMaxClasses; ++i)
-    if (i == it.k) rep0 = B.c[i].rep0;
+    if (i == it.k) {
+      rep0 = B.c[i].rep0;
+      qm0 = B.c[i].qm0;
+      um0 = B.c[i].um0;
+    }
   const int r = order[rep0 + it.j];
-  const long long o = reps[r].base;
+  const long long o = reps[r].base;  // the flat populations of the replica
+  const long long qo = qm0 + (long long)it.j * 5 * G.cq, uo = um0 + (long long)it.j * 4 * G.cu;  // its mirrors
   const Model<real> m = reps[r].m;
   const CUtensorMap *mpq = &maps.pq[0], *mu3 = &maps.u3[0];
 #pragma unroll
@@ -1415,8 +1432,8 @@ __global__ void __launch_bounds__(ZM_TX* TY, 2)
       mpq = &maps.pq[i];
       mu3 = &maps.u3[i];
     }
-  lbq_body<real, TY, 1, true, false>(mpq, mu3, nullptr, nullptr, nullptr, G, m, it.bt, it.j, f + NV * o, rhou + 4 * o, Qin + 5 * o,
-                                     fnew + NV * o, rhou_new + 4 * o, Qout + 5 * o, err, Sym5<real>{});
+  lbq_body<real, TY, 1, true, false>(mpq, mu3, nullptr, nullptr, nullptr, G, m, it.bt, it.j, f + NV * o, nullptr,
+                                     Qin + qo, fnew + NV * o, rhou_new + uo, Qout + qo, err, Sym5<real>{});
 }
 
 // ---------------------------------------------------------------------------
@@ -1541,10 +1558,10 @@ template <typename real>
 cudaError_t zm_batch_prepare() {
   constexpr int TY = zm_ty<real>();
   cudaError_t e = cudaFuncSetAttribute(k_qside_batch<real, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)QsideSmem<real, TY, false>::bytes);
+                                       (int)QsideSmem<real, TY, true>::bytes);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_lbq_batch<real, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)LbqSmem<real, TY, false>::bytes);
+                             (int)LbqSmem<real, TY, true>::bytes);
   return e;
 }
 
@@ -1553,13 +1570,11 @@ cudaError_t launch_step_zm_batch(const ZmBatchArgs& a, cudaStream_t s) {
   constexpr int TY = zm_ty<real>();
   const int grid = a.B.total_ctas;
   const auto* reps = static_cast<const Replica<real>*>(a.reps);
-  k_qside_batch<real, TY><<<grid, qside_threads<TY, 1>(), QsideSmem<real, TY, false>::bytes, s>>>(
-      *a.maps, a.B, reps, a.order, static_cast<const real*>(a.q), static_cast<const real*>(a.rhou),
-      static_cast<real*>(a.pq), a.err);
-  k_lbq_batch<real, TY><<<grid, ZM_TX * TY, LbqSmem<real, TY, false>::bytes, s>>>(
-      *a.maps, a.B, reps, a.order, static_cast<const real*>(a.f), static_cast<const real*>(a.rhou),
-      static_cast<const real*>(a.q), static_cast<real*>(a.fnew), static_cast<real*>(a.rhou_new),
-      static_cast<real*>(a.qout ? a.qout : a.q), a.err);
+  k_qside_batch<real, TY><<<grid, qside_threads<TY, 1>(), QsideSmem<real, TY, true>::bytes, s>>>(
+      *a.maps, a.B, reps, a.order, static_cast<real*>(a.pq), a.err);
+  k_lbq_batch<real, TY><<<grid, ZM_TX * TY, LbqSmem<real, TY, true>::bytes, s>>>(
+      *a.maps, a.B, reps, a.order, static_cast<const real*>(a.f), static_cast<const real*>(a.q),
+      static_cast<real*>(a.fnew), static_cast<real*>(a.rhou_new), static_cast<real*>(a.qout ? a.qout : a.q), a.err);
   return cudaGetLastError();
 }
 
