@@ -1,25 +1,24 @@
 // Fast path of the coupled step: two z-marching kernels with TMA-staged planes.
 //
-//   k_qside  (Q^n, rho u^n)            -> P, Q*                      (96 B/site FP32)
+//   k_qside  (Q^n, rho u^n)            -> P, Q*, rho - 1             (100 B/site FP32)
 //            H, sigma_LC, tau and the body force b = D0_b tau_ab - H_gn D0_a Q_gn,
 //            then the Heun predictor Q* = Q + R(Q, u)   (Sec. 2.1 Eq. Qevolution,
 //            mat_der, BEstress; Sec. 2.2 Eq. eq7a, spurious), and P: the ten
 //            coefficients of the site's LB pre-collision terms f^eq_i / tau_f + p_i
 //            (Sec. 2.2 Eq. feq, coeff, eq4), built from rho^n, u^n, sigma_LC and b
-//   k_lbq    (f^n, rho u^n, P, Q*, Q^n) -> f^{n+1}, rho u^{n+1}, Q^{n+1}   (252 B/site FP32)
+//   k_lbq    (f^n, rho u^n, P, Q*, Q^n) -> f^{n+1}, rho u^{n+1}, Q^{n+1}   (256 B/site FP32)
 //            predictor-corrector D3Q15 LB (Sec. 2.2 Eq. eq2, eq4, feq, coeff) and the
 //            Heun corrector Q^{n+1} = (Q + Q* + R(Q*)) / 2
 //
 // A CTA owns a column tile of TX x TY sites and marches through ZC planes.
-// Planes of the fields it reads with a halo are brought into shared memory
-// by 4-D TMA tile loads (x, y, z, component) into a ring of slots, each slot
-// with its own mbarrier; the load of a plane is issued one or two planes
-// before the CTA needs it, so HBM traffic overlaps compute.  A TMA box of the
-// state fields is 40 elements wide (x0-4 .. x0+35, 16-byte aligned start);
-// out-of-range halo cells of edge tiles are zero-filled by TMA and then
-// overwritten with their periodic images by plain loads.  P and Q* go from
-// k_qside to k_lbq through a scratch padded with their periodic images (see
-// kernels.h), so their boxes (36 wide, x0-1 .. x0+34) need no patching.
+// Planes of the fields it reads with a halo are brought into shared memory by
+// TMA tile loads into a ring of slots, each slot with its own mbarrier; the
+// load of a plane is issued one or two planes before the CTA needs it, so HBM
+// traffic overlaps compute.  The state Q and rho u lives in padded mirrors
+// whose ghost columns and rows hold the periodic images, and P, Q* go from
+// k_qside to k_lbq through a scratch padded the same way (kernels.h), so no
+// staged box needs patching; k_qside writes the scratch's images and k_lbq the
+// mirrors'.  Mirrors and scratch hold a site's values as 16-byte vectors.
 // Populations are pulled straight from global memory (each is used once).
 #include <cuda.h>
 
@@ -36,18 +35,16 @@ constexpr int ZM_BX = 40;   // TMA box width in elements
 constexpr int ZM_XOFF = 4;  // box column of global x0
 constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s bound on any barrier wait
 
-// Staged boxes of the state fields Q (halo 2) and rho u (halo 1): from the
-// flat fields (batches) or from their padded mirrors (single lattices; site x
-// at mirror column x + 32, y at row y + 2 (Q) or y + 1 (rho u)), whose ghosts
-// hold the periodic images.  QW, UW: box widths; QX, UX: the box column of x0.
-// Boxes of plain arrays are 40 wide from x0 - 4 (a 16-byte aligned start);
-// the rho u mirror, 16 bytes per site, stages just x0 - 1 .. x0 + 32.
-// QPX, QPY, UPX, UPY: the mirror offsets of a site (0 for flat fields).
-template <bool PAD>
+// Staged boxes of the state fields Q (halo 2) and rho u (halo 1) from their
+// padded mirrors (site x at mirror column x + 32, y at row y + 2 (Q) or y + 1
+// (rho u)), whose ghosts hold the periodic images.  QW, UW: box widths in
+// sites; QX, UX: the box column of x0.  The Q box (for its plain yz array) is
+// 40 wide from x0 - 4, a 16-byte aligned start; the rho u mirror, 16 bytes
+// per site, stages just x0 - 1 .. x0 + 32.  QPX, QPY, UPX, UPY: the mirror
+// offsets of a site.
 struct StateBox {
-  static constexpr int QW = ZM_BX, QX = ZM_XOFF, QPX = PAD ? kZmMirX : 0, QPY = PAD ? 2 : 0;
-  static constexpr int UW = PAD ? kZmBoxXU : ZM_BX, UX = PAD ? 1 : ZM_XOFF, UPX = PAD ? kZmMirX : 0,
-                       UPY = PAD ? 1 : 0;
+  static constexpr int QW = ZM_BX, QX = ZM_XOFF, QPX = kZmMirX, QPY = 2;
+  static constexpr int UW = kZmBoxXU, UX = 1, UPX = kZmMirX, UPY = 1;
 };
 
 __host__ __device__ constexpr int align_elems(int elems, int esize) {
@@ -58,99 +55,6 @@ __host__ __device__ constexpr int align_elems(int elems, int esize) {
 __device__ __forceinline__ int wrap(int v, int n) {
   v %= n;
   return v < 0 ? v + n : v;
-}
-
-// The out-of-range cells of a staged plane (edge tiles) that the tile reads.
-// Layout [comp][row][ZM_BX]; row r <-> global y = gy0 + r, column c <->
-// global x = x0 - ZM_XOFF + c.  The kernel reads rows [0, ROWS) and columns
-// [C0, C1), but with a halo of H only up to y = ny - 1 + H and x = nx - 1 + H
-// (a ragged tile's lanes past the lattice edge store nothing), so the window
-// is cut there.  The window's cells inside the lattice form one rectangle,
-// and the frame around it is enumerated as the rows above and below it, then
-// the columns left and right of it.  TMA zero-fills these cells; the kernels
-// overwrite them with their periodic images.
-template <int ROWS, int C0, int C1, int H, bool FAST_DIV>
-struct Frame {
-  int rmax, w, ra, rb, lw, rw;  // window rows [0, rmax), columns [C0, C0 + w); in-lattice rows [ra, rb)
-  __device__ __forceinline__ Frame(int nx, int ny, int x0, int gy0) {
-    rmax = min(ROWS, ny + H - gy0);
-    w = min(C1, nx + H - x0 + ZM_XOFF) - C0;
-    ra = max(0, -gy0);
-    rb = min(rmax, ny - gy0);
-    lw = max(C0, ZM_XOFF - x0) - C0;
-    rw = C0 + w - min(C0 + w, nx - x0 + ZM_XOFF);
-  }
-  __device__ __forceinline__ int cells() const { return (rmax - (rb - ra)) * w + (rb - ra) * (lw + rw); }
-  // t / w and t % w (FAST_DIV: with a constant divisor when the window is not cut)
-  __device__ __forceinline__ void divw(int t, int& q, int& m) const {
-    if (FAST_DIV && w == C1 - C0) {
-      q = t / (C1 - C0);
-      m = t % (C1 - C0);
-    } else {
-      q = t / w;
-      m = t - q * w;
-    }
-  }
-  // row and column of cell t < cells()
-  __device__ __forceinline__ void cell(int t, int& r, int& c) const {
-    const int n_top = ra * w, n_tb = n_top + (rmax - rb) * w, n_tbl = n_tb + (rb - ra) * lw;
-    int q, m;
-    if (t < n_top) {
-      divw(t, q, m);
-      r = q;
-      c = C0 + m;
-    } else if (t < n_tb) {
-      divw(t - n_top, q, m);
-      r = rb + q;
-      c = C0 + m;
-    } else if (t < n_tbl) {
-      // a side column block is H wide on a lattice whose nx is a multiple of 4
-      // (the constant divisor); the division covers any other width
-      const int u = t - n_tb;
-      const int q = lw == H ? u / H : u / lw;
-      r = ra + q;
-      c = C0 + u - q * lw;
-    } else {
-      const int u = t - n_tbl;
-      const int q = rw == H ? u / H : u / rw;
-      r = ra + q;
-      c = C0 + w - rw + u - q * rw;
-    }
-  }
-};
-
-// Periodic coordinates of a CTA's staged box, wrapped once per CTA: xw[c] for
-// box column c (global x = x0 - ZM_XOFF + c), yw[r] for box row r (global
-// y = gy0 + r).  The periodic image of frame cell (r, c) of plane gz is then
-// two shared-memory reads away instead of two divisions.
-__device__ __forceinline__ void fill_wrap_tables(int* xw, int* yw, int rows, int nx, int ny, int x0, int gy0) {
-  for (int i = threadIdx.x; i < ZM_BX + rows; i += blockDim.x) {
-    if (i < ZM_BX) xw[i] = wrap(x0 - ZM_XOFF + i, nx);
-    else yw[i - ZM_BX] = wrap(gy0 + i - ZM_BX, ny);
-  }
-}
-__device__ __forceinline__ int image_site(int r, int c, int nx, int ny, int gz, const int* xw, const int* yw) {
-  return (gz * ny + yw[r]) * nx + xw[c];
-}
-
-// TMA tile load of plane z of a field: 4-D (x, y, z, component) for one
-// lattice, 5-D with the replica rc outermost for a batch class
-template <bool BATCH>
-__device__ __forceinline__ void zm_load(void* dst, const CUtensorMap* map, int x, int y, int z, int rc,
-                                        uint64_t* bar) {
-  if constexpr (BATCH) tma_load_5d(dst, map, x, y, z, 0, rc, bar);
-  else tma_load_4d(dst, map, x, y, z, 0, bar);
-}
-
-template <typename real>
-__device__ __forceinline__ Sym5<real> ld5(const real* sl, int comp_stride, int idx) {
-  Sym5<real> v;
-  v.xx = sl[idx];
-  v.xy = sl[comp_stride + idx];
-  v.xz = sl[2 * comp_stride + idx];
-  v.yy = sl[3 * comp_stride + idx];
-  v.yz = sl[4 * comp_stride + idx];
-  return v;
 }
 
 // Sites per thread (SPT): with SPT = 2 a thread computes rows y and y + TY/2 of
@@ -223,14 +127,6 @@ __device__ __forceinline__ void ld4v(const real* p, int i0, int i1, typename Lan
   }
 }
 
-template <int SPT, typename real, typename V>
-__device__ __forceinline__ void store5_lane(real* p, int n, int s, const Sym5<V>& q, int k) {
-  p[s] = lane<SPT, real>(q.xx, k);
-  p[n + s] = lane<SPT, real>(q.xy, k);
-  p[2 * n + s] = lane<SPT, real>(q.xz, k);
-  p[3 * n + s] = lane<SPT, real>(q.yy, k);
-  p[4 * n + s] = lane<SPT, real>(q.yz, k);
-}
 template <typename V, typename real>
 __device__ __forceinline__ Model<V> widen(const Model<real>& m) {
   Model<V> w;
@@ -249,9 +145,9 @@ __device__ __forceinline__ Model<V> widen(const Model<real>& m) {
 // ---------------------------------------------------------------------------
 // Kernel A: H, sigma, tau, b and the Heun predictor
 // ---------------------------------------------------------------------------
-template <typename real, int TY, bool PAD>
+template <typename real, int TY>
 struct QsideSmem {
-  using B = StateBox<PAD>;
+  using B = StateBox;
   static constexpr int QROWS = TY + 4, UROWS = TY + 2, TROWS = TY + 2, TCOLS = ZM_TX + 2;
   static constexpr int QSLOTS = 5, USLOTS = 4;
   static constexpr int QCS = QROWS * B::QW, UCS = UROWS * B::UW;  // per-component strides
@@ -260,8 +156,8 @@ struct QsideSmem {
   static constexpr int TSLOT = 3 * TROWS * TCOLS, HSLOT = 10 * TY * ZM_TX;
   static constexpr int OFF_U = QSLOTS * QSLOT, OFF_T = OFF_U + USLOTS * USLOT;
   static constexpr int OFF_H = OFF_T + 3 * TSLOT, OFF_BAR = align_elems(OFF_H + 2 * HSLOT, sizeof(real));
-  // barriers, the abort flag, then the wrapped box columns and rows (Q box)
-  static constexpr size_t bytes = sizeof(real) * (size_t)OFF_BAR + 16 * 8 + 16 + sizeof(int) * (ZM_BX + QROWS);
+  // barriers, then the abort flag
+  static constexpr size_t bytes = sizeof(real) * (size_t)OFF_BAR + 16 * 8 + 16;
 };
 
 // Threads of a k_qside CTA: enough to cover the H / tau ring of a plane
@@ -281,12 +177,10 @@ constexpr int qside_threads() {
 template <typename real, int TY, int SPT, bool BATCH, bool WALLS>
 __device__ __forceinline__ void qside_body(const CUtensorMap* tmQ, const CUtensorMap* tmQ1, const CUtensorMap* tmU,
                                            const ZmGeom G,
-                                           const Model<real> m, int bt, int rc, const real* __restrict__ Q,
-                                           const real* __restrict__ rhou, const real* __restrict__ bext,
+                                           const Model<real> m, int bt, int rc, const real* __restrict__ bext,
                                            real* __restrict__ pq, int* __restrict__ err, const Sym5<real> qw) {
-  constexpr bool PAD = true;  // the state is staged from its padded mirrors: no patching
-  using L = QsideSmem<real, TY, PAD>;
-  using B = StateBox<PAD>;
+  using L = QsideSmem<real, TY>;
+  using B = StateBox;
   using V = typename LaneT<real, SPT>::V;
   constexpr int TYH = TY / SPT;  // rows handled by one pass of the CTA
   static_assert(TY % SPT == 0 && (TY + 2) % SPT == 0, "tile rows must split evenly between the lanes");
@@ -298,8 +192,6 @@ __device__ __forceinline__ void qside_body(const CUtensorMap* tmQ, const CUtenso
   real* hbuf = base + L::OFF_H;
   uint64_t* bars = reinterpret_cast<uint64_t*>(base + L::OFF_BAR);  // 5 Q + 4 u
   int* abort_flag = reinterpret_cast<int*>(bars + 16);
-  int* xw = abort_flag + 4;  // wrapped box columns, then rows of the Q box (y0 - 2 ...)
-  int* yw = xw + ZM_BX;
 
   // element offsets within one lattice (or replica) fit in 32 bits: the host
   // takes this path only where 15 components of every field do
@@ -311,8 +203,6 @@ __device__ __forceinline__ void qside_body(const CUtensorMap* tmQ, const CUtenso
   const int z1 = min(z0 + G.zc, nz);
   const int tx = threadIdx.x % ZM_TX, ty = threadIdx.x / ZM_TX;  // rows ty + k * TYH, k < SPT
   const int gx = x0 + tx;
-  const bool edge_q = x0 - 2 < 0 || x0 + ZM_TX + 2 > nx || y0 - 2 < 0 || y0 + TY + 2 > ny;
-  const bool edge_u = x0 - 1 < 0 || x0 + ZM_TX + 1 > nx || y0 - 1 < 0 || y0 + TY + 1 > ny;
   constexpr uint32_t qbytes = 5 * L::QCS * sizeof(real), ubytes = 4 * L::UCS * sizeof(real);
 
   if (threadIdx.x == 0) {
@@ -320,10 +210,9 @@ __device__ __forceinline__ void qside_body(const CUtensorMap* tmQ, const CUtenso
     *abort_flag = 0;
     mbar_init_fence();
     tma_prefetch_desc(tmQ);
-    if constexpr (PAD) tma_prefetch_desc(tmQ1);  // (null only where PAD is off)
+    tma_prefetch_desc(tmQ1);
     tma_prefetch_desc(tmU);
   }
-  fill_wrap_tables(xw, yw, L::QROWS, nx, ny, x0, y0 - 2);
   __syncthreads();
 
   // plane p of Q lives in slot (p - (z0-2)) % 5, of rho u in slot (p - (z0-1)) % 4
@@ -335,49 +224,34 @@ __device__ __forceinline__ void qside_body(const CUtensorMap* tmQ, const CUtenso
     const unsigned k = p - (z0 - 2);
     uint64_t* bar = &bars[k % L::QSLOTS];
     mbar_arrive_expect_tx(bar, qbytes);
-    if constexpr (PAD) {  // the mirror's [xx xy xz yy] vectors, then its yz array
-      const int X = x0 - B::QX + B::QPX, Y = y0 - 2 + B::QPY;
-      if constexpr (BATCH) {  // (replica rc of the class)
-        tma_load_4d(qslot(p), tmQ, 4 * X, Y, wrap(p, nz), rc, bar);
-        tma_load_4d(qslot(p) + 4 * L::QCS, tmQ1, X, Y, wrap(p, nz), rc, bar);
-      } else {
-        tma_load_3d(qslot(p), tmQ, 4 * X, Y, wrap(p, nz), bar);
-        tma_load_3d(qslot(p) + 4 * L::QCS, tmQ1, X, Y, wrap(p, nz), bar);
-      }
+    // the mirror's [xx xy xz yy] vectors, then its yz array (replica rc of a batch class)
+    const int X = x0 - B::QX + B::QPX, Y = y0 - 2 + B::QPY;
+    if constexpr (BATCH) {
+      tma_load_4d(qslot(p), tmQ, 4 * X, Y, wrap(p, nz), rc, bar);
+      tma_load_4d(qslot(p) + 4 * L::QCS, tmQ1, X, Y, wrap(p, nz), rc, bar);
     } else {
-      zm_load<BATCH>(qslot(p), tmQ, x0 - B::QX + B::QPX, y0 - 2 + B::QPY, wrap(p, nz), rc, bar);
+      tma_load_3d(qslot(p), tmQ, 4 * X, Y, wrap(p, nz), bar);
+      tma_load_3d(qslot(p) + 4 * L::QCS, tmQ1, X, Y, wrap(p, nz), bar);
     }
   };
   auto issue_u = [&](int p) {
     const unsigned k = p - (z0 - 1);
     uint64_t* bar = &bars[L::QSLOTS + k % L::USLOTS];
     mbar_arrive_expect_tx(bar, ubytes);
-    if constexpr (PAD && BATCH)
+    if constexpr (BATCH)
       tma_load_4d(uslot(p), tmU, 4 * (x0 - B::UX + B::UPX), y0 - 1 + B::UPY, wrap(p, nz), rc, bar);
-    else if constexpr (PAD)
-      tma_load_3d(uslot(p), tmU, 4 * (x0 - B::UX + B::UPX), y0 - 1 + B::UPY, wrap(p, nz), bar);
     else
-      zm_load<BATCH>(uslot(p), tmU, x0 - B::UX + B::UPX, y0 - 1 + B::UPY, wrap(p, nz), rc, bar);
+      tma_load_3d(uslot(p), tmU, 4 * (x0 - B::UX + B::UPX), y0 - 1 + B::UPY, wrap(p, nz), bar);
   };
   // Q and rho u at box index i0 (lane 0) and i1 (lane 1) of a staged slot:
-  // the padded mirrors stage [row][col][4] vectors (Q: then its yz as
-  // [row][col]), the flat fields [component][row][col]
+  // the mirrors stage [row][col][4] vectors (Q: then its yz as [row][col])
   auto ldq = [&](const real* sl, int i0, int i1) -> Sym5<V> {
-    if constexpr (PAD) {
-      V a[4];
-      ld4v<SPT>(sl, 4 * i0, 4 * i1, a);
-      return {a[0], a[1], a[2], a[3], vld<SPT>(sl, 4 * L::QCS + i0, 4 * L::QCS + i1)};
-    } else {
-      return ld5v<SPT>(sl, L::QCS, i0, i1);
-    }
+    V a[4];
+    ld4v<SPT>(sl, 4 * i0, 4 * i1, a);
+    return {a[0], a[1], a[2], a[3], vld<SPT>(sl, 4 * L::QCS + i0, 4 * L::QCS + i1)};
   };
   auto ldu = [&](const real* sl, int i0, int i1, V v[4]) {  // [rho - 1, u_x, u_y, u_z]
-    if constexpr (PAD) {
-      ld4v<SPT>(sl, 4 * i0, 4 * i1, v);
-    } else {
-#pragma unroll
-      for (int c = 0; c < 4; ++c) v[c] = vld<SPT>(sl, c * L::UCS + i0, c * L::UCS + i1);
-    }
+    ld4v<SPT>(sl, 4 * i0, 4 * i1, v);
   };
   // Wait for a plane.  Every thread reaches the __syncthreads that follows a
   // wait, so a timeout cannot strand part of the CTA.
@@ -393,53 +267,13 @@ __device__ __forceinline__ void qside_body(const CUtensorMap* tmQ, const CUtenso
     if (!ok) *abort_flag = 1;
     return ok;
   };
-  // Periodic halo of edge tiles: item t is one component of a frame cell of
-  // the Q plane pq (t < items_q, 5 components) or of the rho u plane pu (4).
-  // patch_item returns its value and its index in shared memory.
-  const Frame<L::QROWS, 2, ZM_TX + 6, 2, true> FQ(nx, ny, x0, y0 - 2);
-  const Frame<L::UROWS, 3, ZM_TX + 5, 1, true> FU(nx, ny, x0, y0 - 1);
-  const int items_q = !PAD && edge_q ? FQ.cells() * 5 : 0, items = items_q + (!PAD && edge_u ? FU.cells() * 4 : 0);
-  auto patch_item = [&](int t, int pq, int pu, int& dst) -> real {
-    int r, c;
-    if (t < items_q) {
-      const int cell = t / 5, k = t - 5 * cell;
-      FQ.cell(cell, r, c);
-      dst = (int)(qslot(pq) - base) + (k * L::QROWS + r) * B::QW + c;
-      return Q[k * n + image_site(r, c, nx, ny, wrap(pq, nz), xw, yw)];
-    }
-    const int u = t - items_q, cell = u / 4, k = u - 4 * cell;
-    FU.cell(cell, r, c);
-    dst = (int)(uslot(pu) - base) + (k * L::UROWS + r) * B::UW + c;
-    return rhou[k * n + image_site(r, c, nx, ny, wrap(pu, nz), xw, yw + 1)];
-  };
   // a staged Q plane beyond a wall: qw in every cell (no periodic images)
   auto ghost = [&](int p) { return WALLS && (p < 0 || p >= nz); };
   auto fill_q = [&](int p) {
     real* sl = qslot(p);
-    if constexpr (PAD) {
-      for (int t = threadIdx.x; t < L::QCS; t += blockDim.x) {
-        st4(sl + 4 * t, qw.xx, qw.xy, qw.xz, qw.yy);
-        sl[4 * L::QCS + t] = qw.yz;
-      }
-    } else {
-      for (int t = threadIdx.x; t < 5 * L::QCS; t += blockDim.x) {
-        const int k = t / L::QCS;
-        sl[t] = k == 0 ? qw.xx : k == 1 ? qw.xy : k == 2 ? qw.xz : k == 3 ? qw.yy : qw.yz;
-      }
-    }
-  };
-  auto patch_q = [&](int p) {
-    for (int t = threadIdx.x; t < items_q; t += blockDim.x) {
-      int d;
-      const real v = patch_item(t, p, p, d);
-      base[d] = v;
-    }
-  };
-  auto patch_u = [&](int p) {
-    for (int t = items_q + threadIdx.x; t < items; t += blockDim.x) {
-      int d;
-      const real v = patch_item(t, p, p, d);
-      base[d] = v;
+    for (int t = threadIdx.x; t < L::QCS; t += blockDim.x) {
+      st4(sl + 4 * t, qw.xx, qw.xy, qw.xz, qw.yy);
+      sl[4 * L::QCS + t] = qw.yz;
     }
   };
   auto tslot = [&](int p) { return tring + ((unsigned)(p - z0 + 3) % 3u) * L::TSLOT; };
@@ -582,10 +416,9 @@ __device__ __forceinline__ void qside_body(const CUtensorMap* tmQ, const CUtenso
     for (int p = z0 - 2; p <= z0 + 2; ++p) issue_q(p);
     for (int p = z0 - 1; p <= z0 + 1; ++p) issue_u(p);
   }
-  for (int p = z0 - 2; p <= z0 + 1; ++p)
-    if (wait_q(p)) patch_q(p);
-  if (wait_u(z0 - 1)) patch_u(z0 - 1);
-  if (wait_u(z0)) patch_u(z0);
+  for (int p = z0 - 2; p <= z0 + 1; ++p) wait_q(p);
+  wait_u(z0 - 1);
+  wait_u(z0);
   __syncthreads();
   aborted = *abort_flag != 0;
   if (WALLS && !aborted && (z0 < 2 || z0 + 1 >= nz)) {
@@ -598,8 +431,8 @@ __device__ __forceinline__ void qside_body(const CUtensorMap* tmQ, const CUtenso
     field_plane(z0);
   }
 
-  // Per plane one CTA barrier, after the waits (patched halos, a uniform abort
-  // decision), and with two sites per thread a second one after the H / tau
+  // Per plane one CTA barrier, after the waits (a uniform abort decision),
+  // and with two sites per thread a second one after the H / tau
   // pass.  A thread past the first barrier of plane z knows every thread has
   // finished plane z-1, the last reader of the Q and u slots the next loads
   // overwrite (planes z-2) and of the tau / H slots this plane's pass
@@ -609,34 +442,14 @@ __device__ __forceinline__ void qside_body(const CUtensorMap* tmQ, const CUtenso
   // (one site per thread: from registers; two: from the slot, after the
   // second barrier).
   for (int z = z0; z < z1 && !aborted; ++z) {
-    // the periodic images for the planes waited for are loaded before the
-    // waits (they do not depend on the copies), and stored after them
-    constexpr int KP = 2;
-    real pv[KP];
-    int pd[KP];
-#pragma unroll
-    for (int q = 0; q < KP; ++q) {
-      const int t = threadIdx.x + q * blockDim.x;
-      pd[q] = -1;
-      if (t < items) pv[q] = patch_item(t, z + 2, z + 1, pd[q]);
-    }
-    const bool okq = wait_q(z + 2), oku = wait_u(z + 1);
-    if (okq && oku) {
-#pragma unroll
-      for (int q = 0; q < KP; ++q)
-        if (pd[q] >= 0) base[pd[q]] = pv[q];
-      for (int t = threadIdx.x + KP * blockDim.x; t < items; t += blockDim.x) {
-        int d;
-        const real v = patch_item(t, z + 2, z + 1, d);
-        base[d] = v;
-      }
-    }
+    wait_q(z + 2);
+    wait_u(z + 1);
     __syncthreads();
     if (*abort_flag) {
       aborted = true;
       break;
     }
-    if (ghost(z + 2)) {  // after the periodic images of that plane: a wall's ghost plane
+    if (ghost(z + 2)) {  // a wall's ghost plane
       fill_q(z + 2);
       __syncthreads();
     }
@@ -656,7 +469,7 @@ __device__ __forceinline__ void qside_body(const CUtensorMap* tmQ, const CUtenso
       const int qi0 = (ty + 2) * B::QW + (tx + B::QX), qi1 = qi0 + TYH * B::QW;
       const Sym5<V> q = ldq(qc, qi0, qi1);
       Sym5<V> dq[3], h;
-      if constexpr (SPT == 1 && !BATCH) {  // (a batch CTA has no registers to spare for the carry)
+      if constexpr (SPT == 1) {
         dq[0] = dq_cur[0];
         dq[1] = dq_cur[1];
         dq[2] = dq_cur[2];
@@ -814,10 +627,9 @@ __device__ __forceinline__ void qside_body(const CUtensorMap* tmQ, const CUtenso
 template <typename real, int TY, int SPT, bool WALLS>
 __global__ void __launch_bounds__(qside_threads<TY, SPT>(), sizeof(real) == 4 ? 2 : 1)
     k_qside(const __grid_constant__ CUtensorMap tmQ, const __grid_constant__ CUtensorMap tmQ1,
-            const __grid_constant__ CUtensorMap tmU, ZmGeom G,
-            Model<real> m, const real* __restrict__ Q, const real* __restrict__ rhou,
-            const real* __restrict__ bext, real* __restrict__ pq, int* __restrict__ err, Sym5<real> qw) {
-  qside_body<real, TY, SPT, false, WALLS>(&tmQ, &tmQ1, &tmU, G, m, blockIdx.x, 0, Q, rhou, bext, pq, err, qw);
+            const __grid_constant__ CUtensorMap tmU, ZmGeom G, Model<real> m, const real* __restrict__ bext,
+            real* __restrict__ pq, int* __restrict__ err, Sym5<real> qw) {
+  qside_body<real, TY, SPT, false, WALLS>(&tmQ, &tmQ1, &tmU, G, m, blockIdx.x, 0, bext, pq, err, qw);
 }
 
 // The CTA's batch class, its replica and tile: classes own consecutive CTA ranges.
@@ -878,7 +690,7 @@ __global__ void __launch_bounds__(qside_threads<TY, 1>(), sizeof(real) == 4 ? 2 
       mq1 = &maps.q1[i];
       mu = &maps.u[i];
     }
-  qside_body<real, TY, 1, true, false>(mq, mq1, mu, G, m, it.bt, it.j, nullptr, nullptr, nullptr,
+  qside_body<real, TY, 1, true, false>(mq, mq1, mu, G, m, it.bt, it.j, nullptr,
                                        pq + pq0 + (long long)it.j * kZmPQ * G.cp, err, Sym5<real>{});
 }
 
@@ -911,20 +723,18 @@ __device__ __forceinline__ void mirror_positions(int px, int h, int nx, int ny, 
 // ---------------------------------------------------------------------------
 // Kernel B: LB predictor-corrector and the Heun corrector
 // ---------------------------------------------------------------------------
-template <typename real, int TY, bool PAD>
+template <typename real, int TY>
 struct LbqSmem {
   static constexpr int ROWS = TY + 2, SLOTS = 4;
-  static constexpr int GS = ROWS * kZmBoxXP * 4;        // one group of the P / Q* box: [row][34][4]
-  static constexpr int CSU = ROWS * StateBox<PAD>::UW;  // per-component stride of the u box
-  // u box components: the rho u mirror's [rho-1 u_x u_y u_z] vectors, or
-  // components 1..3 of the flat field
-  static constexpr int UC = PAD ? 4 : 3;
-  // one slot: the four groups of the padded scratch, then the u box
+  static constexpr int GS = ROWS * kZmBoxXP * 4;   // one group of the P / Q* box: [row][34][4]
+  static constexpr int CSU = ROWS * StateBox::UW;  // sites of the u box
+  // one slot: the four groups of the padded scratch, then the u box of the
+  // rho u mirror's [rho-1 u_x u_y u_z] vectors
   static constexpr int OFF_U = align_elems(kZmPQG * GS, sizeof(real));
-  static constexpr int SLOT = OFF_U + align_elems(UC * CSU, sizeof(real));
-  static constexpr uint32_t TX_BYTES = (uint32_t)((kZmPQG * GS + UC * CSU) * sizeof(real));
-  // barriers, the abort flag, then the wrapped box columns and rows
-  static constexpr size_t bytes = sizeof(real) * (size_t)SLOTS * SLOT + 8 * 8 + 16 + sizeof(int) * (ZM_BX + ROWS);
+  static constexpr int SLOT = OFF_U + align_elems(4 * CSU, sizeof(real));
+  static constexpr uint32_t TX_BYTES = (uint32_t)((kZmPQG * GS + 4 * CSU) * sizeof(real));
+  // barriers, then the abort flag
+  static constexpr size_t bytes = sizeof(real) * (size_t)SLOTS * SLOT + 8 * 8 + 16;
 };
 
 // WALLS: walls half a spacing below z = 0 and above z = nz-1.  A population
@@ -938,12 +748,11 @@ template <typename real, int TY, int SPT, bool BATCH, bool WALLS>
 __device__ __forceinline__ void lbq_body(const CUtensorMap* tmPQ, const CUtensorMap* tmU3, const CUtensorMap* tmF,
                                          const CUtensorMap* tmQ, const CUtensorMap* tmQ1, const ZmGeom& G,
                                          const Model<real>& m, int bt, int rc, const real* __restrict__ f,
-                                         const real* __restrict__ rhou, const real* __restrict__ Qin,
-                                         real* __restrict__ fnew, real* __restrict__ rhou_new,
-                                         real* __restrict__ Qout, int* __restrict__ err, const Sym5<real> qw) {
-  constexpr bool PAD = true;  // the state is read from and written to its padded mirrors
-  using L = LbqSmem<real, TY, PAD>;
-  using B = StateBox<PAD>;
+                                         const real* __restrict__ Qin, real* __restrict__ fnew,
+                                         real* __restrict__ rhou_new, real* __restrict__ Qout,
+                                         int* __restrict__ err, const Sym5<real> qw) {
+  using L = LbqSmem<real, TY>;
+  using B = StateBox;
   using V = typename LaneT<real, SPT>::V;
   constexpr int TYH = TY / SPT;  // a thread takes rows ty + k * TYH, k < SPT
   constexpr int AW = kZmBoxXP;
@@ -951,8 +760,6 @@ __device__ __forceinline__ void lbq_body(const CUtensorMap* tmPQ, const CUtensor
   real* ring = reinterpret_cast<real*>(smem_raw);
   uint64_t* bars = reinterpret_cast<uint64_t*>(ring + L::SLOTS * L::SLOT);
   int* abort_flag = reinterpret_cast<int*>(bars + 8);
-  int* xw = abort_flag + 4;  // wrapped u-box columns, then rows (y0 - 1 ...)
-  int* yw = xw + ZM_BX;
 
   const int nx = G.nx, ny = G.ny, nz = G.nz;
   const int n = (int)G.n;  // (32-bit element offsets, as in k_qside)
@@ -971,7 +778,6 @@ __device__ __forceinline__ void lbq_body(const CUtensorMap* tmPQ, const CUtensor
     gy[k] = lane_ok[k] ? y0 + ty + k * TYH : y0 + ty;
   }
   const bool valid = lane_ok[0];
-  const bool edge = x0 - 1 < 0 || x0 + ZM_TX + 1 > nx || y0 - 1 < 0 || y0 + TY + 1 > ny;
 
   if (threadIdx.x == 0) {
     for (int i = 0; i < L::SLOTS; ++i) mbar_init(&bars[i], 1);
@@ -985,12 +791,11 @@ __device__ __forceinline__ void lbq_body(const CUtensorMap* tmPQ, const CUtensor
       tma_prefetch_desc(tmQ1);
     }
   }
-  fill_wrap_tables(xw, yw, L::ROWS, nx, ny, x0, y0 - 1);
   __syncthreads();
 
   auto slot = [&](int p) { return ring + ((unsigned)(p - (z0 - 1)) % L::SLOTS) * L::SLOT; };
   // plane p: the padded P / Q* box (site (x, y) at padded (x + 1, y + 1), so the
-  // box starting at padded (x0, y0) covers x0-1 .. x0+34) and the u box of rho u
+  // box starting at padded (x0, y0) covers x0-1 .. x0+32) and the u box of rho u
   auto issue = [&](int p) {
     const unsigned k = p - (z0 - 1);
     uint64_t* bar = &bars[k % L::SLOTS];
@@ -1000,9 +805,9 @@ __device__ __forceinline__ void lbq_body(const CUtensorMap* tmPQ, const CUtensor
     // the scratch as (4 X, Y, group, z): x coordinate in elements of 4 per site
     if constexpr (BATCH) tma_load_5d(sl, tmPQ, 4 * x0, y0, 0, zz, rc, bar);
     else tma_load_4d(sl, tmPQ, 4 * x0, y0, 0, zz, bar);
-    if constexpr (PAD && BATCH) {
+    if constexpr (BATCH) {
       tma_load_4d(sl + L::OFF_U, tmU3, 4 * (x0 - B::UX + B::UPX), y0 - 1 + B::UPY, zz, rc, bar);
-    } else if constexpr (PAD) {
+    } else {
       tma_load_3d(sl + L::OFF_U, tmU3, 4 * (x0 - B::UX + B::UPX), y0 - 1 + B::UPY, zz, bar);
       // the populations of plane p (pulled from plane p-1 on) and Q^n of plane
       // p-1, into L2 a plane ahead of their plain loads
@@ -1010,8 +815,6 @@ __device__ __forceinline__ void lbq_body(const CUtensorMap* tmPQ, const CUtensor
       const int X = x0 - B::QX + B::QPX, Y = y0 - 2 + B::QPY;
       tma_prefetch_l2_3d(tmQ, 4 * X, Y, wrap(p - 1, nz));
       tma_prefetch_l2_3d(tmQ1, X, Y, wrap(p - 1, nz));
-    } else {
-      zm_load<BATCH>(sl + L::OFF_U, tmU3, x0 - B::UX + B::UPX, y0 - 1 + B::UPY, zz, rc, bar);
     }
   };
   auto wait = [&](int p) {
@@ -1020,19 +823,6 @@ __device__ __forceinline__ void lbq_body(const CUtensorMap* tmPQ, const CUtensor
     if (!ok) *abort_flag = 1;
     return ok;
   };
-  // Periodic halo of the u box of edge tiles: item t is component t % 3 of
-  // frame cell t / 3 of plane p.  patch_item returns its value and its index
-  // in the ring.
-  const Frame<L::ROWS, 3, ZM_TX + 5, 1, true> F(nx, ny, x0, y0 - 1);
-  const int items = !PAD && edge ? F.cells() * 3 : 0;
-  const bool small_frame = items <= (int)blockDim.x;  // one value per thread in the loop
-  auto patch_item = [&](int t, int p, int& dst) -> real {
-    const int cell = t / 3, k = t - 3 * cell;
-    int r, c;
-    F.cell(cell, r, c);
-    dst = (int)(slot(p) - ring) + L::OFF_U + (k * L::ROWS + r) * B::UW + c;
-    return rhou[(k + 1) * n + image_site(r, c, nx, ny, wrap(p, nz), xw, yw)];
-  };
   // a staged plane beyond a wall: only its Q* is read (the anchored qw)
   auto ghost = [&](int p) { return WALLS && (p < 0 || p >= nz); };
   auto fill = [&](int p) {
@@ -1040,13 +830,6 @@ __device__ __forceinline__ void lbq_body(const CUtensorMap* tmPQ, const CUtensor
     for (int t = threadIdx.x; t < L::GS / 4; t += blockDim.x) {  // Q*_yz in G2, the rest in G3
       sl[2 * L::GS + 4 * t + 2] = qw.yz;
       st4(sl + 3 * L::GS + 4 * t, qw.xx, qw.xy, qw.xz, qw.yy);
-    }
-  };
-  auto patch = [&](int p) {
-    for (int t = threadIdx.x; t < items; t += blockDim.x) {
-      int d;
-      const real v = patch_item(t, p, d);
-      ring[d] = v;
     }
   };
   // group g of the P / Q* box at box index idx (lane 0) and idx + TYH rows
@@ -1059,15 +842,9 @@ __device__ __forceinline__ void lbq_body(const CUtensorMap* tmPQ, const CUtensor
   };
   // u = (u_x, u_y, u_z) at u-box index idx (lane 0) and idx + TYH rows (lane 1)
   auto U3 = [&](const real* sl, int idx, V u[3]) {
-    if constexpr (PAD) {
-      V v[4];
-      ld4v<SPT>(sl + L::OFF_U, 4 * idx, 4 * (idx + TYH * B::UW), v);
-      u[0] = v[1], u[1] = v[2], u[2] = v[3];
-    } else {
-#pragma unroll
-      for (int k = 0; k < 3; ++k)
-        u[k] = vld<SPT>(sl, L::OFF_U + k * L::CSU + idx, L::OFF_U + k * L::CSU + idx + TYH * B::UW);
-    }
+    V v[4];
+    ld4v<SPT>(sl + L::OFF_U, 4 * idx, 4 * (idx + TYH * B::UW), v);
+    u[0] = v[1], u[1] = v[2], u[2] = v[3];
   };
   // acc +/- v by the sign of e (compile-time after unrolling)
   auto acc = [](V& a, int e, V v) {
@@ -1078,11 +855,8 @@ __device__ __forceinline__ void lbq_body(const CUtensorMap* tmPQ, const CUtensor
   bool aborted = false;
   if (threadIdx.x == 0)
     for (int p = z0 - 1; p <= z0 + 1; ++p) issue(p);
-  if (wait(z0 - 1)) patch(z0 - 1);
-  if (wait(z0)) patch(z0);
-  if (small_frame && wait(z0 + 1)) patch(z0 + 1);
-  real v_ahead = real(0);  // small frames: the image value read one plane ahead
-  int d_ahead = -1;
+  wait(z0 - 1);
+  wait(z0);
 
   // periodic source coordinates of the pull
   const int xm = wrap(gx - 1, nx), xp = wrap(gx + 1, nx);
@@ -1128,35 +902,7 @@ __device__ __forceinline__ void lbq_body(const CUtensorMap* tmPQ, const CUtensor
       if (WALLS && (wlo || whi)) pull(std::true_type{});
       else pull(std::false_type{});
     }
-    // Periodic images of the u box of edge tiles.  Small frames (one value
-    // per thread): the value for plane z+2 is read here and stored after the
-    // wait of the next iteration, so that its latency hides behind this
-    // plane's work.  Larger frames: the values for plane z+1 are read here,
-    // beside the pulled populations, and stored after its wait.
-    constexpr int KP = 3;
-    real pv[KP];
-    int pd[KP];
-#pragma unroll
-    for (int q = 0; q < KP; ++q) {
-      const int t = threadIdx.x + q * blockDim.x;
-      pd[q] = -1;
-      if (small_frame ? q == 0 && z + 2 <= z1 && t < items : t < items)
-        pv[q] = patch_item(t, small_frame ? z + 2 : z + 1, pd[q]);
-    }
-    const bool landed = wait(z + 1);
-    if (landed && small_frame && d_ahead >= 0) ring[d_ahead] = v_ahead;
-    v_ahead = pv[0];
-    d_ahead = small_frame ? pd[0] : -1;
-    if (landed && !small_frame) {
-#pragma unroll
-      for (int q = 0; q < KP; ++q)
-        if (pd[q] >= 0) ring[pd[q]] = pv[q];
-      for (int t = threadIdx.x + KP * blockDim.x; t < items; t += blockDim.x) {
-        int d;
-        const real v = patch_item(t, z + 1, d);
-        ring[d] = v;
-      }
-    }
+    wait(z + 1);
     __syncthreads();
     if (*abort_flag) {
       aborted = true;
@@ -1289,18 +1035,11 @@ __device__ __forceinline__ void lbq_body(const CUtensorMap* tmPQ, const CUtensor
 #pragma unroll
       for (int k = 0; k < SPT; ++k) {
         if (!lane_ok[k]) continue;
-        if constexpr (PAD) {
-          const real a = lane<SPT, real>(dr1, k), b = lane<SPT, real>(u1x, k), c = lane<SPT, real>(u1y, k),
-                     d = lane<SPT, real>(u1z, k);
-          const int nxm = G.nxm, nyu = G.nyu;
-          mirror_positions(B::UPX, 1, nx, ny, gx, gy[k],
-                           [&](int X, int Y) { st4(rhou_new + 4 * ((z * nyu + Y) * nxm + X), a, b, c, d); });
-        } else {
-          rhou_new[s[k]] = lane<SPT, real>(dr1, k);
-          rhou_new[n + s[k]] = lane<SPT, real>(u1x, k);
-          rhou_new[2 * n + s[k]] = lane<SPT, real>(u1y, k);
-          rhou_new[3 * n + s[k]] = lane<SPT, real>(u1z, k);
-        }
+        const real a = lane<SPT, real>(dr1, k), b = lane<SPT, real>(u1x, k), c = lane<SPT, real>(u1y, k),
+                   d = lane<SPT, real>(u1z, k);
+        const int nxm = G.nxm, nyu = G.nyu;
+        mirror_positions(B::UPX, 1, nx, ny, gx, gy[k],
+                         [&](int X, int Y) { st4(rhou_new + 4 * ((z * nyu + Y) * nxm + X), a, b, c, d); });
       }
 
       // Heun corrector with u^n
@@ -1343,40 +1082,27 @@ __device__ __forceinline__ void lbq_body(const CUtensorMap* tmPQ, const CUtensor
       const Sym5<V> r = be_rate<true>(st.c, h, dq, u_y, w, mv, true);
       // Q^n of the site: the flat field, or the Q mirror ([xx xy xz yy]
       // vectors, then the yz array)
-      Sym5<V> q0;
-      if constexpr (PAD) {
-        int sq[SPT];
+      int sq[SPT];
 #pragma unroll
-        for (int k = 0; k < SPT; ++k) sq[k] = (z * G.nyq + gy[k] + B::QPY) * G.nxm + gx + B::QPX;
-        const int cq = (int)G.cq;
-        V a[4];
-        ld4v<SPT>(Qin, 4 * sq[0], 4 * sq[SPT - 1], a);
-        q0 = {a[0], a[1], a[2], a[3], vld<SPT>(Qin, 4 * cq + sq[0], 4 * cq + sq[SPT - 1])};
-      } else {
-        q0.xx = vld<SPT>(Qin, s[0], s[SPT - 1]);
-        q0.xy = vld<SPT>(Qin, n + s[0], n + s[SPT - 1]);
-        q0.xz = vld<SPT>(Qin, 2 * n + s[0], 2 * n + s[SPT - 1]);
-        q0.yy = vld<SPT>(Qin, 3 * n + s[0], 3 * n + s[SPT - 1]);
-        q0.yz = vld<SPT>(Qin, 4 * n + s[0], 4 * n + s[SPT - 1]);
-      }
+      for (int k = 0; k < SPT; ++k) sq[k] = (z * G.nyq + gy[k] + B::QPY) * G.nxm + gx + B::QPX;
+      const int cq = (int)G.cq;
+      V qa[4];
+      ld4v<SPT>(Qin, 4 * sq[0], 4 * sq[SPT - 1], qa);
+      const Sym5<V> q0 = {qa[0], qa[1], qa[2], qa[3], vld<SPT>(Qin, 4 * cq + sq[0], 4 * cq + sq[SPT - 1])};
       const Sym5<V> q1 = {half * (q0.xx + st.c.xx + r.xx), half * (q0.xy + st.c.xy + r.xy),
                           half * (q0.xz + st.c.xz + r.xz), half * (q0.yy + st.c.yy + r.yy),
                           half * (q0.yz + st.c.yz + r.yz)};
 #pragma unroll
       for (int k = 0; k < SPT; ++k) {
         if (!lane_ok[k]) continue;
-        if constexpr (PAD) {
-          const real a = lane<SPT, real>(q1.xx, k), b = lane<SPT, real>(q1.xy, k), c = lane<SPT, real>(q1.xz, k),
-                     d = lane<SPT, real>(q1.yy, k), e = lane<SPT, real>(q1.yz, k);
-          const int nxm = G.nxm, nyq = G.nyq, cq4 = 4 * (int)G.cq;
-          mirror_positions(B::QPX, 2, nx, ny, gx, gy[k], [&](int X, int Y) {
-            const int o = (z * nyq + Y) * nxm + X;
-            st4(Qout + 4 * o, a, b, c, d);
-            Qout[cq4 + o] = e;
-          });
-        } else {
-          store5_lane<SPT, real>(Qout, n, s[k], q1, k);
-        }
+        const real a = lane<SPT, real>(q1.xx, k), b = lane<SPT, real>(q1.xy, k), c = lane<SPT, real>(q1.xz, k),
+                   d = lane<SPT, real>(q1.yy, k), e = lane<SPT, real>(q1.yz, k);
+        const int nxm = G.nxm, nyq = G.nyq, cq4 = 4 * (int)G.cq;
+        mirror_positions(B::QPX, 2, nx, ny, gx, gy[k], [&](int X, int Y) {
+          const int o = (z * nyq + Y) * nxm + X;
+          st4(Qout + 4 * o, a, b, c, d);
+          Qout[cq4 + o] = e;
+        });
       }
     };
     if (valid) {
@@ -1397,11 +1123,11 @@ template <typename real, int TY, int SPT, bool WALLS>
 __global__ void __launch_bounds__(ZM_TX* TY / SPT, 2)
     k_lbq(const __grid_constant__ CUtensorMap tmPQ, const __grid_constant__ CUtensorMap tmU3,
           const __grid_constant__ CUtensorMap tmF, const __grid_constant__ CUtensorMap tmQ,
-          const __grid_constant__ CUtensorMap tmQ1, ZmGeom G, Model<real> m, const real* __restrict__ f, const real* __restrict__ rhou, const real* __restrict__ Qin,
-          real* __restrict__ fnew, real* __restrict__ rhou_new, real* __restrict__ Qout, int* __restrict__ err,
-          Sym5<real> qw) {
-  lbq_body<real, TY, SPT, false, WALLS>(&tmPQ, &tmU3, &tmF, &tmQ, &tmQ1, G, m, blockIdx.x, 0, f, rhou, Qin, fnew,
-                                        rhou_new, Qout, err, qw);
+          const __grid_constant__ CUtensorMap tmQ1, ZmGeom G, Model<real> m, const real* __restrict__ f,
+          const real* __restrict__ Qin, real* __restrict__ fnew, real* __restrict__ rhou_new, real* __restrict__ Qout,
+          int* __restrict__ err, Sym5<real> qw) {
+  lbq_body<real, TY, SPT, false, WALLS>(&tmPQ, &tmU3, &tmF, &tmQ, &tmQ1, G, m, blockIdx.x, 0, f, Qin, fnew, rhou_new,
+                                        Qout, err, qw);
 }
 
 template <typename real, int TY>
@@ -1432,8 +1158,8 @@ __global__ void __launch_bounds__(ZM_TX* TY, 2)
       mpq = &maps.pq[i];
       mu3 = &maps.u3[i];
     }
-  lbq_body<real, TY, 1, true, false>(mpq, mu3, nullptr, nullptr, nullptr, G, m, it.bt, it.j, f + NV * o, nullptr,
-                                     Qin + qo, fnew + NV * o, rhou_new + uo, Qout + qo, err, Sym5<real>{});
+  lbq_body<real, TY, 1, true, false>(mpq, mu3, nullptr, nullptr, nullptr, G, m, it.bt, it.j, f + NV * o, Qin + qo,
+                                     fnew + NV * o, rhou_new + uo, Qout + qo, err, Sym5<real>{});
 }
 
 // ---------------------------------------------------------------------------
@@ -1459,10 +1185,10 @@ template <typename real, int SPT, bool WALLS>
 cudaError_t zm_prepare_spt() {
   constexpr int TY = zm_ty<real>();
   cudaError_t e = cudaFuncSetAttribute(k_qside<real, TY, SPT, WALLS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)QsideSmem<real, TY, true>::bytes);
+                                       (int)QsideSmem<real, TY>::bytes);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_lbq<real, TY, SPT, WALLS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)LbqSmem<real, TY, true>::bytes);
+                             (int)LbqSmem<real, TY>::bytes);
   return e;
 }
 
@@ -1487,7 +1213,7 @@ int zm_resident_spt() {
   constexpr int TY = zm_ty<real>();
   int n = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_lbq<real, TY, SPT, false>, ZM_TX * TY / SPT,
-                                                    LbqSmem<real, TY, true>::bytes) != cudaSuccess)
+                                                    LbqSmem<real, TY>::bytes) != cudaSuccess)
     n = 1;
   return n > 0 ? n : 1;
 }
@@ -1529,12 +1255,11 @@ cudaError_t launch_step_zm_spt(const ZmArgs& a, cudaStream_t s) {
   Sym5<real> qw{};
   if (WALLS) qw = {(real)a.q_wall[0], (real)a.q_wall[1], (real)a.q_wall[2], (real)a.q_wall[3], (real)a.q_wall[4]};
   if (a.events) cudaEventRecord(a.events[0], s);
-  k_qside<real, TY, SQ, WALLS><<<grid, qside_threads<TY, SQ>(), QsideSmem<real, TY, true>::bytes, s>>>(
-      *a.tm_q, *a.tm_q1, *a.tm_u, G, m, static_cast<const real*>(a.q), static_cast<const real*>(a.rhou),
-      static_cast<const real*>(a.bext), static_cast<real*>(a.pq), a.err, qw);
+  k_qside<real, TY, SQ, WALLS><<<grid, qside_threads<TY, SQ>(), QsideSmem<real, TY>::bytes, s>>>(
+      *a.tm_q, *a.tm_q1, *a.tm_u, G, m, static_cast<const real*>(a.bext), static_cast<real*>(a.pq), a.err, qw);
   if (a.events) cudaEventRecord(a.events[1], s);
-  k_lbq<real, TY, SPT, WALLS><<<grid, ZM_TX * TY / SPT, LbqSmem<real, TY, true>::bytes, s>>>(
-      *a.tm_pq, *a.tm_u3, *a.tm_f, *a.tm_q, *a.tm_q1, G, m, static_cast<const real*>(a.f), static_cast<const real*>(a.rhou),
+  k_lbq<real, TY, SPT, WALLS><<<grid, ZM_TX * TY / SPT, LbqSmem<real, TY>::bytes, s>>>(
+      *a.tm_pq, *a.tm_u3, *a.tm_f, *a.tm_q, *a.tm_q1, G, m, static_cast<const real*>(a.f),
       static_cast<const real*>(a.q), static_cast<real*>(a.fnew), static_cast<real*>(a.rhou_new),
       static_cast<real*>(a.qout ? a.qout : a.q), a.err, qw);
   if (a.events) cudaEventRecord(a.events[2], s);
@@ -1558,10 +1283,10 @@ template <typename real>
 cudaError_t zm_batch_prepare() {
   constexpr int TY = zm_ty<real>();
   cudaError_t e = cudaFuncSetAttribute(k_qside_batch<real, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)QsideSmem<real, TY, true>::bytes);
+                                       (int)QsideSmem<real, TY>::bytes);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_lbq_batch<real, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)LbqSmem<real, TY, true>::bytes);
+                             (int)LbqSmem<real, TY>::bytes);
   return e;
 }
 
@@ -1570,9 +1295,9 @@ cudaError_t launch_step_zm_batch(const ZmBatchArgs& a, cudaStream_t s) {
   constexpr int TY = zm_ty<real>();
   const int grid = a.B.total_ctas;
   const auto* reps = static_cast<const Replica<real>*>(a.reps);
-  k_qside_batch<real, TY><<<grid, qside_threads<TY, 1>(), QsideSmem<real, TY, true>::bytes, s>>>(
+  k_qside_batch<real, TY><<<grid, qside_threads<TY, 1>(), QsideSmem<real, TY>::bytes, s>>>(
       *a.maps, a.B, reps, a.order, static_cast<real*>(a.pq), a.err);
-  k_lbq_batch<real, TY><<<grid, ZM_TX * TY, LbqSmem<real, TY, true>::bytes, s>>>(
+  k_lbq_batch<real, TY><<<grid, ZM_TX * TY, LbqSmem<real, TY>::bytes, s>>>(
       *a.maps, a.B, reps, a.order, static_cast<const real*>(a.f), static_cast<const real*>(a.q),
       static_cast<real*>(a.fnew), static_cast<real*>(a.rhou_new), static_cast<real*>(a.qout ? a.qout : a.q), a.err);
   return cudaGetLastError();
