@@ -313,10 +313,10 @@ def plain_log(kappa: float, steps: int, log_every: int = 100, threshold: float =
 
 
 def judged_log(params, kappa: float, steps: int, k: int, M: int, tol: float, log_every: int = 100,
-               weights: str | None = None, warmup: int = 0, fields: dict | None = None):
+               weights: str | None = None, warmup: int = 0, fields: dict | None = None, tol_q: float = 0.0):
     """The judged run on the slab: its log, statistics and seconds."""
     hyb = slab_lattice(kappa)
-    run = JudgedRun(hyb, params, kappa, M=M, tol=tol, k=k, weights=weights, warmup=warmup)
+    run = JudgedRun(hyb, params, kappa, M=M, tol=tol, k=k, weights=weights, warmup=warmup, tol_q=tol_q)
     t0 = time.perf_counter()
     ts, Fs, Ds = run.advance(steps, log_every)
     hyb.synchronize()
@@ -326,6 +326,35 @@ def judged_log(params, kappa: float, steps: int, k: int, M: int, tol: float, log
     run.close()
     hyb.close()
     return list(zip(ts.tolist(), Fs.tolist(), Ds.tolist())), st, secs
+
+
+def field_track(params, kappa: float, steps: int, k: int, M: int, tol: float, warmup: int, tol_q: float = 0.0):
+    """max |Delta Q| and r.m.s. |Delta u| of the judged run against the plain run
+    at every segment boundary (t = warmup + i (M + 1) k, where the judged run's
+    state is its own), with the plain run's r.m.s. |u|: (t, dQ, du, u) rows.
+    Advancing the judge to segment boundaries leaves its segmentation as in
+    one call."""
+    plain = slab_lattice(kappa)
+    hyb = slab_lattice(kappa)
+    run = JudgedRun(hyb, params, kappa, M=M, tol=tol, k=k, warmup=warmup, tol_q=tol_q)
+    rows, t = [], 0
+    seg = (M + 1) * k
+    stops = [warmup] + list(range(warmup + seg, steps, seg)) + [steps]
+    for t_next in stops:
+        if t_next <= t:
+            continue
+        run.advance(t_next)
+        plain.step(t_next - t)
+        t = t_next
+        a, b = {}, {}
+        final_fields(hyb, a)
+        final_fields(plain, b)
+        e = field_errors(a, b)
+        rows.append((t, e["max_abs_dQ"], e["rms_du"], e["rms_u"]))
+    run.close()
+    hyb.close()
+    plain.close()
+    return rows
 
 
 def main():
@@ -344,6 +373,7 @@ def main():
     ap.add_argument("--kappas", type=float, nargs="+", default=[0.5, 1.0, 2.0], help="chiralities of the judged runs")
     ap.add_argument("--M", type=int, default=49, help="surrogate calls per judged segment")
     ap.add_argument("--tol", type=float, default=1e-3)
+    ap.add_argument("--tol-q", type=float, default=0.0, help="judge bound on max |dQ| of one call (0: off)")
     ap.add_argument("--warmup", type=int, default=1000, help="plain steps before the first surrogate segment")
     ap.add_argument("--out", default=None, help="write the trained weights file here")
     ap.add_argument("--weights", default=None, help="skip training: judge this weights file")
@@ -398,6 +428,11 @@ def main():
         F_plain = {t: F for t, F, _ in rows}
         F_scale = max(abs(F) for _, F, _ in rows)
         out = {"plain_s": t_pl, "final_F": rows[-1][1], "final_defect_fraction": rows[-1][2], "F_scale": F_scale}
+        # field errors of the trained network's judged run along the trajectory
+        out["judged_network_fields_along_run"] = [
+            {"t": t, "max_abs_dQ": dq, "rms_du": du, "rms_u_plain": uu}
+            for t, dq, du, uu in field_track(params, kappa, args.run_steps, k, args.M, args.tol, args.warmup,
+                                             args.tol_q)]
         # the plain solver's own sensitivity: Q perturbed by 1e-7 after the warm-up
         pert_fields = {}
         prow, _ = plain_log(kappa, args.run_steps, fields=pert_fields, perturb=(args.warmup, 1e-7, 99))
@@ -409,7 +444,8 @@ def main():
         for mode, tol in (("judged", args.tol), ("accept_all", 1e30)):
             for name, p in (("network", params), ("zero_network", np.zeros_like(params))):
                 jf = {}
-                jrows, st, secs = judged_log(p, kappa, args.run_steps, k, args.M, tol, warmup=args.warmup, fields=jf)
+                jrows, st, secs = judged_log(p, kappa, args.run_steps, k, args.M, tol, warmup=args.warmup, fields=jf,
+                                             tol_q=args.tol_q if mode == "judged" else 0.0)
                 errs = [abs(F - F_plain[t]) / abs(F_plain[t]) for t, F, _ in jrows]
                 errs_s = [abs(F - F_plain[t]) / F_scale for t, F, _ in jrows]
                 out[mode + "_" + name] = {"seconds": secs, "speedup_vs_plain": t_pl / secs, "logged": len(jrows),
@@ -442,7 +478,8 @@ def main():
                   "weights": args.weights},
         "held_out_mse": mse,
         "call_ms": {"surrogate_call": t_sur, "plain_k_steps": t_plain},
-        "judged_runs": {"steps": args.run_steps, "M": args.M, "tol": args.tol, "warmup": args.warmup,
+        "judged_runs": {"steps": args.run_steps, "M": args.M, "tol": args.tol, "tol_q": args.tol_q,
+                        "warmup": args.warmup,
                         "by_kappa": runs},
     }))
 
