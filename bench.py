@@ -55,12 +55,12 @@ HBM_NOMINAL_GBS = 7900.0  # GB300 HBM3e data-sheet bandwidth (the measured copy 
 MEASURED_TRAFFIC = {
     "sources": ["paper_0901_3293_gb300/csrc/zmarch.cu", "paper_0901_3293_gb300/csrc/common.cuh",
                 "paper_0901_3293_gb300/csrc/tma.cuh", "paper_0901_3293_gb300/csrc/kernels.h"],
-    "sha256_16": "b9914be038550aa1",
+    "sha256_16": "099d5edb583ed07a",
     # one launch of each kernel in the capture (ncu --set full)
-    "bytes_per_site": {"qside": (179473152 + 215394048) / 160 ** 3,
-                       "lbq": (807546880 + 368372992) / 160 ** 3},
+    "bytes_per_site": {"qside": (180492032 + 215591424) / 160 ** 3,
+                       "lbq": (809950464 + 368454656) / 160 ** 3},
     # smsp__inst_executed.sum (warp instructions) x 32 of the same launches
-    "thread_instr_per_site": {"qside": 108106052 * 32 / 160 ** 3, "lbq": 116463340 * 32 / 160 ** 3},
+    "thread_instr_per_site": {"qside": 107762852 * 32 / 160 ** 3, "lbq": 115976660 * 32 / 160 ** 3},
 }
 ORACLE_SAMPLE = 32  # side of the periodic cube the oracle steps (two BPII unit cells)
 WALL_Q = (0.2, 0.0, 0.0, -0.1, 0.0)  # planar anchoring S (x x - I/3), S = 0.3, on the ghost planes
