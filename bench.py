@@ -55,7 +55,7 @@ HBM_NOMINAL_GBS = 7900.0  # GB300 HBM3e data-sheet bandwidth (the measured copy 
 MEASURED_TRAFFIC = {
     "sources": ["paper_0901_3293_gb300/csrc/zmarch.cu", "paper_0901_3293_gb300/csrc/common.cuh",
                 "paper_0901_3293_gb300/csrc/tma.cuh", "paper_0901_3293_gb300/csrc/kernels.h"],
-    "sha256_16": "099d5edb583ed07a",
+    "sha256_16": "d4ce5520b7de73f5",
     # one launch of each kernel in the capture (ncu --set full)
     "bytes_per_site": {"qside": (180492032 + 215591424) / 160 ** 3,
                        "lbq": (809950464 + 368454656) / 160 ** 3},

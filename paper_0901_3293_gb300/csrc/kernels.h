@@ -123,9 +123,11 @@ cudaError_t launch_diag_one(const DiagGeom& g, const void* q, const void* f, int
 constexpr int kDiagPartials = 512 * 8;
 
 // ---------------------------------------------------------------------------
-// Fast path (flow on, Jacobi coupling, nx % 4 == 0): two z-marching kernels
-// with TMA-staged planes.  Tensor maps describe one field as a 4-D tensor
-// (x, y, z, component) and are built by the host (make_field_tmap).
+// Fast path (flow on, Jacobi coupling, zm_shape_ok): two z-marching kernels
+// with TMA-staged planes.  The host builds the tensor maps: the padded mirrors
+// of Q and rho u as 3-D tensors (4-D with the replica outermost for a batch
+// class), the scratch below as (4 X, Y, group, z), and the populations as a
+// 4-D tensor (x, y, z, component) for L2 prefetches.
 //
 // Between the two kernels the step's intermediate fields live in a
 // periodically padded scratch ("LB-ready" scratch) of 16 values per site in
