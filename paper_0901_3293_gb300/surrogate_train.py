@@ -377,6 +377,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=1000, help="plain steps before the first surrogate segment")
     ap.add_argument("--out", default=None, help="write the trained weights file here")
     ap.add_argument("--weights", default=None, help="skip training: judge this weights file")
+    ap.add_argument("--init-weights", default=None, help="start the training from this weights file")
+    ap.add_argument("--lr", type=float, default=1e-3, help="Adam learning rate (0.3x after half, 0.1x after 3/4)")
     ap.add_argument("--log-out", default=None, help="write the per-100-step logs here (JSON lines)")
     ap.add_argument("--s-r", type=float, default=None, help="input scale of the rate R")
     ap.add_argument("--s-dq", type=float, default=None, help="output scale of the correction")
@@ -405,7 +407,14 @@ def main():
                         t_min=args.t_min, k=k)
         n_data = len(data)
         note({"k": k, "samples": n_data, "held_out": len(held), "gen_s": time.perf_counter() - t0})
-        params, log = train(data, args.iters, k=k)
+        init = None
+        if args.init_weights:
+            sur0 = lcbp.Surrogate(data[0].q.shape[3], data[0].q.shape[2], 8).load(args.init_weights)
+            if sur0.steps() != k:
+                raise SystemExit(f"{args.init_weights} was trained for k = {sur0.steps()}, not {k}")
+            init = sur0.get_params()
+            sur0.close()
+        params, log = train(data, args.iters, lr=args.lr, k=k, params=init)
         del data
         note({"train_s": log.seconds, "loss_first": float(np.mean(log.losses[:20])),
               "loss_last": float(np.mean(log.losses[-20:]))})
