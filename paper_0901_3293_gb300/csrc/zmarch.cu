@@ -113,6 +113,18 @@ __device__ __forceinline__ void st4(real* p, real a, real b, real c, real d) {
     *reinterpret_cast<double2*>(p + 2) = make_double2(c, d);
   }
 }
+// st4 to global memory as a streaming store (evict-first in L2): the
+// step's outputs, which no CTA of the kernel reads again, leave L2 to the
+// staged halos and pulled populations that neighbouring tiles share
+template <typename real>
+__device__ __forceinline__ void st4g(real* p, real a, real b, real c, real d) {
+  if constexpr (sizeof(real) == 4) {
+    __stcs(reinterpret_cast<float4*>(p), make_float4(a, b, c, d));
+  } else {
+    __stcs(reinterpret_cast<double2*>(p), make_double2(a, b));
+    __stcs(reinterpret_cast<double2*>(p + 2), make_double2(c, d));
+  }
+}
 // a group at element i0 (lane 0) and i1 (lane 1)
 template <int SPT, typename real>
 __device__ __forceinline__ void ld4v(const real* p, int i0, int i1, typename LaneT<real, SPT>::V v[4]) {
@@ -550,10 +562,10 @@ __device__ __forceinline__ void qside_body(const CUtensorMap* tmQ, const CUtenso
           const real g3[4] = {L(qs[0]), L(qs[1]), L(qs[2]), L(qs[3])};
           auto put1 = [&](int xx, int yy) {
             real* d = pq + ((z * kZmPQG * nyp + yy) * nxp + xx) * 4;
-            st4(d, g0[0], g0[1], g0[2], g0[3]);
-            st4(d + gs, g1[0], g1[1], g1[2], g1[3]);
-            st4(d + 2 * gs, g2[0], g2[1], g2[2], g2[3]);
-            st4(d + 3 * gs, g3[0], g3[1], g3[2], g3[3]);
+            st4g(d, g0[0], g0[1], g0[2], g0[3]);
+            st4g(d + gs, g1[0], g1[1], g1[2], g1[3]);
+            st4g(d + 2 * gs, g2[0], g2[1], g2[2], g2[3]);
+            st4g(d + 3 * gs, g3[0], g3[1], g3[2], g3[3]);
           };
           put1(gx + 1, gy + 1);
           if (gx == 0 || gx == nx - 1 || gy == 0 || gy == ny - 1) {
@@ -1024,7 +1036,7 @@ __device__ __forceinline__ void lbq_body(const CUtensorMap* tmPQ, const CUtensor
         const V fo = dh[i] + V(0.5) * Cs;
 #pragma unroll
         for (int k = 0; k < SPT; ++k)
-          if (lane_ok[k]) fnew[i * n + s[k]] = lane<SPT, real>(fo, k);
+          if (lane_ok[k]) __stcs(&fnew[i * n + s[k]], lane<SPT, real>(fo, k));  // (streaming: not re-read here)
         dr1 = i == 0 ? fo : dr1 + fo;
         acc(j1x, ex(i), fo);
         acc(j1y, ey(i), fo);
@@ -1039,7 +1051,7 @@ __device__ __forceinline__ void lbq_body(const CUtensorMap* tmPQ, const CUtensor
                    d = lane<SPT, real>(u1z, k);
         const int nxm = G.nxm, nyu = G.nyu;
         mirror_positions(B::UPX, 1, nx, ny, gx, gy[k],
-                         [&](int X, int Y) { st4(rhou_new + 4 * ((z * nyu + Y) * nxm + X), a, b, c, d); });
+                         [&](int X, int Y) { st4g(rhou_new + 4 * ((z * nyu + Y) * nxm + X), a, b, c, d); });
       }
 
       // Heun corrector with u^n
@@ -1100,8 +1112,8 @@ __device__ __forceinline__ void lbq_body(const CUtensorMap* tmPQ, const CUtensor
         const int nxm = G.nxm, nyq = G.nyq, cq4 = 4 * (int)G.cq;
         mirror_positions(B::QPX, 2, nx, ny, gx, gy[k], [&](int X, int Y) {
           const int o = (z * nyq + Y) * nxm + X;
-          st4(Qout + 4 * o, a, b, c, d);
-          Qout[cq4 + o] = e;
+          st4g(Qout + 4 * o, a, b, c, d);
+          __stcs(&Qout[cq4 + o], e);
         });
       }
     };
