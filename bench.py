@@ -343,7 +343,7 @@ def run_ours(args):
     # ---- per-kernel device times, kernel by kernel with events (same kernels)
     kms = lat.profile_steps(max(3, min(args.steps, 10)))
     fast, zc, spt = lat.path()
-    _, spt_lbq, spt_qside = lat.tuning()
+    zc_lbq, spt_lbq, spt_qside, zc_qside = lat.tuning()
     peak, peak_kind = measured_peaks()
     per_kernel = {}
     # instruction-issue peak: one warp instruction per scheduler per cycle, 4 schedulers per
@@ -544,7 +544,8 @@ def run_ours(args):
         "data": "synthetic",
         "config": {**workload_config(world),
                    "kernels": "fast (z-marching, TMA-staged planes)" if fast else "generic",
-                   "planes_per_cta": zc, "sites_per_thread": {"lbq": spt_lbq, "qside": spt_qside}},
+                   "planes_per_cta": {"lbq": zc_lbq, "qside": zc_qside},
+                   "sites_per_thread": {"lbq": spt_lbq, "qside": spt_qside}},
         "roofline": roof, "per_kernel": per_kernel, "cpu_baseline": cpu, "e2e": e2e,
         "gpu_launches": launches, "clocks": clk, "free_energy_after": F,
         "diagnostics_256cube": diag_line, "walls_256cube": walls_line, "generic_kernels_256cube": generic_line, "slab_64x64x256": slab_line, "surrogate_slab_64x64x256": sur_line, "texture_slab_64x64x256": tex_line,

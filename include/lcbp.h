@@ -280,20 +280,22 @@ LCBP_API int lcbp_set_path(lcbp_lattice *h, int path);
  * on the generic path).  The tuning times each candidate once per lattice
  * shape and dtype, writing scratch buffers only; AUTO results persist in the
  * file named by the environment variable LCBP_AUTOTUNE_CACHE, if set
- * (lines "nx ny nz dtype planes sites", dtype + 100 for a lattice with
- * walls; see lcbp_get_tuning for the sites field).  Any pointer may be NULL.
+ * (lines "nx ny nz dtype planes sites planes_q", dtype + 100 for a lattice
+ * with walls; see lcbp_get_tuning for the last two fields; a line without
+ * planes_q gives both kernels the same planes).  Any pointer may be NULL.
  */
 LCBP_API int lcbp_get_path(lcbp_lattice *h, int *fast, int *planes_per_cta, int *sites_per_thread);
 
 /*
- * The fast path's tuning in full: the two kernels share the planes per CTA
- * but take their sites per thread separately.  *spt_lb = that of the LB /
- * Heun-corrector kernel (what lcbp_get_path reports), *spt_q = that of the
- * molecular-field / stress / predictor kernel; all 0 before the first step or
- * on the generic path.  The autotune cache line holds spt_lb + 10 * spt_q in
- * its last field.  Any pointer may be NULL.
+ * The fast path's tuning in full: each of the two kernels has its own planes
+ * per CTA and sites per thread.  *planes_per_cta and *spt_lb = those of the
+ * LB / Heun-corrector kernel (what lcbp_get_path reports), *planes_per_cta_q
+ * and *spt_q = those of the molecular-field / stress / predictor kernel; all
+ * 0 before the first step or on the generic path.  The autotune cache line
+ * holds spt_lb + 10 * spt_q in its sites field and planes_per_cta_q after it.
+ * Any pointer may be NULL.
  */
-LCBP_API int lcbp_get_tuning(lcbp_lattice *h, int *planes_per_cta, int *spt_lb, int *spt_q);
+LCBP_API int lcbp_get_tuning(lcbp_lattice *h, int *planes_per_cta, int *spt_lb, int *spt_q, int *planes_per_cta_q);
 
 /*
  * Copy out the Beris-Edwards rate dQ/dt = R(Q, u) = Gamma H + S(W, Q) - u.grad Q

@@ -205,7 +205,8 @@ struct lcbp_lattice {
   // fast path (z-marching TMA kernels)
   int path_req;   // LCBP_PATH_*
   bool tmaps_ok;  // tensor maps built
-  int zc;         // planes per CTA, 0 until tuned
+  int zc;         // planes per CTA of k_lbq, 0 until tuned
+  int zc_q;       // planes per CTA of k_qside, set by the tuner
   int spt;        // sites per thread of k_lbq, set by the tuner
   int spt_q;      // sites per thread of k_qside, set by the tuner
   // Q mirror vectors, rho u mirror [0], [1], padded scratch, (unused), (unused), f [0], f [1], Q mirror yz
@@ -433,6 +434,7 @@ ZmArgs zm_args(lcbp_lattice* h, const void* model) {
   a.ny = h->ny;
   a.nz = h->nz;
   a.zc = h->zc > 0 ? h->zc : std::min(h->nz, 32);
+  a.zc_q = h->zc_q > 0 ? h->zc_q : a.zc;
   a.spt = h->spt > 0 ? h->spt : 1;
   a.spt_q = h->spt_q > 0 ? h->spt_q : a.spt;
   a.model = model;
@@ -476,14 +478,19 @@ cudaError_t launch_zm(lcbp_lattice* h, const ZmArgs& a) {
   return h->dtype == LCBP_F64 ? launch_step_zm<double>(a, h->stream) : launch_step_zm<float>(a, h->stream);
 }
 
-// planes per CTA and sites per thread, chosen by timing each candidate once per
-// lattice shape and dtype; the runs write only scratch buffers (Q^{n+1} to the
-// generic kernels' Q* scratch), so the state is untouched.  Results are kept per process and, if
-// the environment variable LCBP_AUTOTUNE_CACHE names a file, in that file
-// ("nx ny nz dtype zc spt" per line, dtype + 100 with walls, spt = sites per
-// thread of k_lbq + 10 x those of k_qside).
+// planes per CTA and sites per thread of each fast kernel, chosen by timing
+// each candidate once per lattice shape and dtype (each kernel by its own
+// events, so each takes its own best); the runs write only scratch buffers
+// (Q^{n+1} to a Q-mirror-sized scratch), so the state is untouched.  Results
+// are kept per process and, if the environment variable LCBP_AUTOTUNE_CACHE
+// names a file, in that file ("nx ny nz dtype zc spt [zc_q]" per line, dtype +
+// 100 with walls, zc / zc_q = planes per CTA of k_lbq / k_qside (zc_q as zc
+// if absent), spt = sites per thread of k_lbq + 10 x those of k_qside).
+struct Tuning {
+  int zc, spt, zc_q;
+};
 std::mutex g_tune_mu;
-std::map<std::string, std::pair<int, int>> g_tune;
+std::map<std::string, Tuning> g_tune;
 bool g_tune_loaded = false;
 
 // "nx ny nz dtype", with 100 added to dtype for a lattice with walls
@@ -532,73 +539,86 @@ int tune_zc(lcbp_lattice* h) {
   if (path && !g_tune_loaded) {
     g_tune_loaded = true;
     if (FILE* fp = std::fopen(path, "r")) {
-      int a, b, c, d, z, sp;
-      while (std::fscanf(fp, "%d %d %d %d %d %d", &a, &b, &c, &d, &z, &sp) == 6) {
+      char line[256];
+      while (std::fgets(line, sizeof(line), fp)) {
+        int a, b, c, d, z, sp, zq = 0;
+        const int got = std::sscanf(line, "%d %d %d %d %d %d %d", &a, &b, &c, &d, &z, &sp, &zq);
+        if (got < 6) continue;
+        if (got == 6) zq = z;
         char k[64];
         snprintf(k, sizeof(k), "%d %d %d %d", a, b, c, d);
-        if (z >= 1 && sp % 10 >= 1 && sp % 10 <= 2 && sp / 10 >= 1 && sp / 10 <= 2) g_tune[k] = {z, sp};
+        if (z >= 1 && zq >= 1 && sp % 10 >= 1 && sp % 10 <= 2 && sp / 10 >= 1 && sp / 10 <= 2)
+          g_tune[k] = {z, sp, zq};
       }
       std::fclose(fp);
     }
   }
   const std::string key = tune_key(h);
   auto it = g_tune.find(key);
-  if (!pinned && it != g_tune.end() && it->second.second % 10 <= spt_max && it->second.second / 10 <= spt_max) {
-    h->zc = it->second.first;
-    h->spt = it->second.second % 10;
-    h->spt_q = it->second.second / 10;
+  if (!pinned && it != g_tune.end() && it->second.spt % 10 <= spt_max && it->second.spt / 10 <= spt_max) {
+    h->zc = it->second.zc;
+    h->zc_q = it->second.zc_q;
+    h->spt = it->second.spt % 10;
+    h->spt_q = it->second.spt / 10;
     return LCBP_OK;
   }
   const ModelBuf mb = host_model(h);
-  cudaEvent_t e0, e1;
-  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
-    return fail(LCBP_ECUDA, "event create");
-  float best = 1e30f;
-  int best_zc = std::min(h->nz, 32), best_spt = spt_lo, best_sq = spt_lo;
-  // every pair of sites per thread (k_lbq, k_qside), each with its planes-per-CTA candidates
+  cudaEvent_t ev[3];
+  for (int i = 0; i < 3; ++i)
+    if (cudaEventCreate(&ev[i]) != cudaSuccess) return fail(LCBP_ECUDA, "event create");
+  auto destroy = [&]() {
+    for (int i = 0; i < 3; ++i) cudaEventDestroy(ev[i]);
+  };
+  // each kernel keeps its own best: k_lbq over (spt, zc), k_qside over (spt_q, zc)
+  float best_l = 1e30f, best_q = 1e30f;
+  int best_zc = std::min(h->nz, 32), best_zq = best_zc, best_spt = spt_lo, best_sq = spt_lo;
   for (int spt = spt_lo; spt <= spt_hi; ++spt) {
     for (int sq = spt_lo; sq <= spt_hi; ++sq) {
       for (int zc : zc_candidates(h, spt)) {
         ZmArgs a = zm_args(h, mb.bytes);
-        a.zc = zc;
+        a.zc = a.zc_q = zc;
         a.spt = spt;
         a.spt_q = sq;
+        a.events = ev;  // before k_qside, between the kernels, after k_lbq
         // Q^{n+1} to the Q-mirror-sized buffer after the padded scratch: the state is untouched
-      a.qout = static_cast<char*>(h->pq) + (size_t)zm_pq_elems(h->nx, h->ny, h->nz) * h->es;
-        float t = 1e30f;
+        a.qout = static_cast<char*>(h->pq) + (size_t)zm_pq_elems(h->nx, h->ny, h->nz) * h->es;
+        float tq = 1e30f, tl = 1e30f;
         for (int rep = 0; rep < 3; ++rep) {
-          cudaEventRecord(e0, h->stream);
           cudaError_t e = launch_zm(h, a);
-          cudaEventRecord(e1, h->stream);
-          if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+          if (e == cudaSuccess) e = cudaEventSynchronize(ev[2]);
           if (e != cudaSuccess) {
-            cudaEventDestroy(e0);
-            cudaEventDestroy(e1);
+            destroy();
             return cuda_fail(e, "autotune");
           }
-          float ms = 0.f;
-          cudaEventElapsedTime(&ms, e0, e1);
-          t = std::min(t, ms);
+          float mq = 0.f, ml = 0.f;
+          cudaEventElapsedTime(&mq, ev[0], ev[1]);
+          cudaEventElapsedTime(&ml, ev[1], ev[2]);
+          tq = std::min(tq, mq);
+          tl = std::min(tl, ml);
         }
-        if (t < best) {
-          best = t;
-          best_zc = a.zc;
+        if (tl < best_l) {
+          best_l = tl;
+          best_zc = zc;
           best_spt = spt;
+        }
+        if (tq < best_q) {
+          best_q = tq;
+          best_zq = zc;
           best_sq = sq;
         }
       }
     }
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
+  destroy();
   h->zc = best_zc;
+  h->zc_q = best_zq;
   h->spt = best_spt;
   h->spt_q = best_sq;
   if (pinned) return LCBP_OK;
-  g_tune[key] = {best_zc, best_spt + 10 * best_sq};
+  g_tune[key] = {best_zc, best_spt + 10 * best_sq, best_zq};
   if (path) {
     if (FILE* fp = std::fopen(path, "a")) {
-      std::fprintf(fp, "%s %d %d\n", key.c_str(), best_zc, best_spt + 10 * best_sq);
+      std::fprintf(fp, "%s %d %d %d\n", key.c_str(), best_zc, best_spt + 10 * best_sq, best_zq);
       std::fclose(fp);
     }
   }
@@ -1246,10 +1266,11 @@ int lcbp_set_path(lcbp_lattice* h, int path) {
   return LCBP_OK;
 }
 
-int lcbp_get_tuning(lcbp_lattice* h, int* planes_per_cta, int* spt_lb, int* spt_q) {
+int lcbp_get_tuning(lcbp_lattice* h, int* planes_per_cta, int* spt_lb, int* spt_q, int* planes_per_cta_q) {
   CHECK_H(h);
   const bool f = use_fast(h) && h->zc > 0;
   if (planes_per_cta) *planes_per_cta = f ? h->zc : 0;
+  if (planes_per_cta_q) *planes_per_cta_q = f ? (h->zc_q > 0 ? h->zc_q : h->zc) : 0;
   if (spt_lb) *spt_lb = f ? h->spt : 0;
   if (spt_q) *spt_q = f ? (h->spt_q > 0 ? h->spt_q : h->spt) : 0;
   return LCBP_OK;

@@ -185,7 +185,8 @@ inline bool zm_shape_ok(int nx, int ny, int nz) {
 }
 
 struct ZmArgs {
-  int nx, ny, nz, zc;
+  int nx, ny, nz, zc;  // zc: planes per CTA of k_lbq
+  int zc_q;           // planes per CTA of k_qside (0: as zc)
   int spt;            // sites per thread of k_lbq, 1 or 2 (2 only where zm_spt_max allows)
   int spt_q;          // sites per thread of k_qside (0: as spt)
   const void* model;  // host copy of Model<real>

@@ -1261,14 +1261,15 @@ ZmGeom zm_geom(int nx, int ny, int nz, int zc, int ty) {
 template <typename real, int SQ, int SPT, bool WALLS>
 cudaError_t launch_step_zm_spt(const ZmArgs& a, cudaStream_t s) {
   constexpr int TY = zm_ty<real>();
-  const ZmGeom G = zm_geom(a.nx, a.ny, a.nz, a.zc, TY);
-  const int grid = G.tiles_x * G.tiles_y * G.tiles_z;
+  // each kernel marches its own planes per CTA
+  const ZmGeom G = zm_geom(a.nx, a.ny, a.nz, a.zc, TY), Gq = zm_geom(a.nx, a.ny, a.nz, a.zc_q > 0 ? a.zc_q : a.zc, TY);
+  const int grid = G.tiles_x * G.tiles_y * G.tiles_z, grid_q = Gq.tiles_x * Gq.tiles_y * Gq.tiles_z;
   const Model<real> m = *static_cast<const Model<real>*>(a.model);
   Sym5<real> qw{};
   if (WALLS) qw = {(real)a.q_wall[0], (real)a.q_wall[1], (real)a.q_wall[2], (real)a.q_wall[3], (real)a.q_wall[4]};
   if (a.events) cudaEventRecord(a.events[0], s);
-  k_qside<real, TY, SQ, WALLS><<<grid, qside_threads<TY, SQ>(), QsideSmem<real, TY>::bytes, s>>>(
-      *a.tm_q, *a.tm_q1, *a.tm_u, G, m, static_cast<const real*>(a.bext), static_cast<real*>(a.pq), a.err, qw);
+  k_qside<real, TY, SQ, WALLS><<<grid_q, qside_threads<TY, SQ>(), QsideSmem<real, TY>::bytes, s>>>(
+      *a.tm_q, *a.tm_q1, *a.tm_u, Gq, m, static_cast<const real*>(a.bext), static_cast<real*>(a.pq), a.err, qw);
   if (a.events) cudaEventRecord(a.events[1], s);
   k_lbq<real, TY, SPT, WALLS><<<grid, ZM_TX * TY / SPT, LbqSmem<real, TY>::bytes, s>>>(
       *a.tm_pq, *a.tm_u3, *a.tm_f, *a.tm_q, *a.tm_q1, G, m, static_cast<const real*>(a.f),

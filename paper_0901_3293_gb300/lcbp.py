@@ -77,7 +77,8 @@ _SIGNATURES = {
     "lcbp_save": (_c_int, [_P, ctypes.c_char_p]),
     "lcbp_load": (_c_int, [_P, ctypes.c_char_p]),
     "lcbp_reequilibrate_f": (_c_int, [_P]),
-    "lcbp_get_tuning": (_c_int, [_P, ctypes.POINTER(_c_int), ctypes.POINTER(_c_int), ctypes.POINTER(_c_int)]),
+    "lcbp_get_tuning": (_c_int, [_P, ctypes.POINTER(_c_int), ctypes.POINTER(_c_int), ctypes.POINTER(_c_int),
+                                 ctypes.POINTER(_c_int)]),
     "lcbp_free_energy_noalloc": (_c_int, [_c_void_p, _c_int, _c_int, _c_int, _c_int, _c_double, _c_double,
                                           _c_double, _c_double, _c_void_p, ctypes.POINTER(_c_double)]),
     "lcbp_surrogate_param_count": (_c_size_t, []),
@@ -375,12 +376,11 @@ class Lattice:
         return bool(fast.value), zc.value, spt.value
 
     def tuning(self):
-        """(planes per CTA, sites per thread of the LB kernel, of the field kernel)."""
-        zc = _c_int()
-        sl = _c_int()
-        sq = _c_int()
-        check(lib().lcbp_get_tuning(self._h, ctypes.byref(zc), ctypes.byref(sl), ctypes.byref(sq)))
-        return zc.value, sl.value, sq.value
+        """(planes per CTA and sites per thread of the LB kernel, sites per
+        thread and planes per CTA of the field kernel)."""
+        zc, sl, sq, zq = _c_int(), _c_int(), _c_int(), _c_int()
+        check(lib().lcbp_get_tuning(self._h, ctypes.byref(zc), ctypes.byref(sl), ctypes.byref(sq), ctypes.byref(zq)))
+        return zc.value, sl.value, sq.value, zq.value
 
     def synchronize(self) -> None:
         check(lib().lcbp_synchronize(self._h))
