@@ -542,10 +542,15 @@ LCBP_API int lcbp_surrogate_set_scales(lcbp_surrogate *s, double s_u, double s_r
  * where that window fits shared memory (nx <= 101), else loads one shifted
  * tile per tap (LCBP_CONV_TAPS).  LCBP_CONV_WINDOW
  * requires the window kernel (LCBP_EINVAL where it does not fit).  Both
- * compute the same sums (FP32 accumulation in a different order). */
+ * compute the same sums (FP32 accumulation in a different order).
+ * OR-ing LCBP_CONV_DW_CUDA_CORES into the kind moves the weight gradients of
+ * training from the tensor-core kernel (used where its staged plane windows
+ * fit shared memory, nx <= 177) to the CUDA-core kernel (FP32 atomics, not
+ * bitwise reproducible); both compute the same sums. */
 #define LCBP_CONV_AUTO 0
 #define LCBP_CONV_TAPS 1
 #define LCBP_CONV_WINDOW 2
+#define LCBP_CONV_DW_CUDA_CORES 4
 LCBP_API int lcbp_surrogate_set_conv_kernel(lcbp_surrogate *s, int kind);
 /* Upload / download the parameter vector (host or device FP32; Adam state is reset on upload). */
 LCBP_API int lcbp_surrogate_set_params(lcbp_surrogate *s, const float *params, size_t count);

@@ -1132,12 +1132,9 @@ int lcbp_set_f(lcbp_lattice* h, const void* f15, int dtype) {
   rc = count_nonfinite(h, h->h, 15 * h->n, &bad);
   if (rc) return rc;
   if (bad) return fail(LCBP_ENONFINITE, "%llu uploaded populations are NaN or Inf; f is unchanged", bad);
-  cudaError_t ec = cudaMemcpyAsync(h->f[h->cur], h->h, (size_t)(15 * h->n) * h->es, cudaMemcpyDeviceToDevice,
-                                   h->stream);
-  if (ec != cudaSuccess) return cuda_fail(ec, "set_f");
-  // to deviation storage, in place
-  cudaError_t e = h->dtype == LCBP_F64 ? launch_shift<double>(h->f[h->cur], h->f[h->cur], h->n, 15, 0, -1, h->stream)
-                                       : launch_shift<float>(h->f[h->cur], h->f[h->cur], h->n, 15, 0, -1, h->stream);
+  // into f as deviations from the rest weights, in one pass from the scratch
+  cudaError_t e = h->dtype == LCBP_F64 ? launch_shift<double>(h->h, h->f[h->cur], h->n, 15, 0, -1, h->stream)
+                                       : launch_shift<float>(h->h, h->f[h->cur], h->n, 15, 0, -1, h->stream);
   if (e != cudaSuccess) return cuda_fail(e, "set_f");
   rc = refresh_moments(h);
   if (rc) return rc;

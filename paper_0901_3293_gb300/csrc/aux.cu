@@ -249,24 +249,23 @@ cudaError_t launch_convert(const void* src, int sd, void* dst, int dd, long long
 // rest weight w_c (populations) or 1 (density).  In place is allowed.
 // ---------------------------------------------------------------------------
 template <typename real>
-__global__ void k_shift(const real* src, real* dst, long long n, int comps, int kind, real sign) {
-  const long long total = n * comps;
-  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < total;
-       k += (long long)gridDim.x * blockDim.x) {
-    const int c = (int)(k / n);
-    const real w = kind == 0 ? (real)rest_weight(c) : real(1);
-    dst[k] = src[k] + sign * w;
-  }
+__global__ void k_shift(const real* src, real* dst, long long n, int kind, real sign) {
+  // component c = blockIdx.y: no thread divides a 64-bit index
+  const int c = blockIdx.y;
+  const real w = sign * (kind == 0 ? (real)rest_weight(c) : real(1));
+  const real* s = src + (long long)c * n;
+  real* d = dst + (long long)c * n;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x)
+    d[k] = s[k] + w;
 }
 
 template <typename real>
 cudaError_t launch_shift(const void* src, void* dst, long long n, int comps, int kind, int sign, cudaStream_t s) {
-  const long long total = n * comps;
-  if (total <= 0) return cudaSuccess;
-  const long long want = (total + 255) / 256;
-  const int grid = (int)(want < 65536 ? want : 65536);
-  k_shift<real><<<grid, 256, 0, s>>>(static_cast<const real*>(src), static_cast<real*>(dst), n, comps, kind,
-                                      (real)sign);
+  if (n <= 0 || comps <= 0) return cudaSuccess;
+  const long long want = (n + 255) / 256;
+  const int grid = (int)(want < 4096 ? want : 4096);
+  k_shift<real><<<dim3(grid, comps), 256, 0, s>>>(static_cast<const real*>(src), static_cast<real*>(dst), n, kind,
+                                                   (real)sign);
   return cudaGetLastError();
 }
 template cudaError_t launch_shift<float>(const void*, void*, long long, int, int, int, cudaStream_t);

@@ -23,8 +23,15 @@
 // items; the CTA then writes its partial sums, and a second kernel adds the
 // partials of all CTAs in a fixed order (deterministic).
 //
-// Warp roles (192 threads): warps 0-3 mask dY and run the epilogue (TMEM
-// lanes 0..127), warp 4 copies (cp.async.bulk), warp 5 issues the MMAs.
+// Only slots 0..12 are staged per stage; rows 104..127 of the A operand (the
+// spare slots 13..15) read whatever follows (the stage's dY tile, the next
+// stage, or padding) into accumulator rows that are never read.  That keeps
+// three stages in shared memory for planes up to 64 sites wide.
+//
+// Warp roles (256 threads): warps 0-3 mask dY and run the epilogue (TMEM
+// lanes 0..127), warp 4 copies (cp.async.bulk), warps 5-7 issue the MMAs,
+// each the three shifts of one dx into its own accumulator blocks: one
+// issuing thread cannot keep the tensor core busy with N = C_out MMAs.
 // Every barrier wait is bounded; a timeout sets the error flag.
 #include <cuda_bf16.h>
 
@@ -35,10 +42,12 @@ namespace lcbp {
 
 namespace {
 
-constexpr int kDwThreads = 192;
-constexpr int kDwStages = 2;
-constexpr int kDwSlots = 16;    // A slots of W sites each (rows 8 slot .. 8 slot + 7)
-constexpr int kDwOnesSlot = 12; // rows 96..103: ones
+constexpr int kDwIssuers = 3;  // MMA-issuing warps (one per dx)
+constexpr int kDwThreads = 32 * (5 + kDwIssuers);
+constexpr int kDwMaxStages = 3;
+constexpr int kDwSlots = 16;     // A operand rows: 16 slots of W sites (rows 8 slot .. 8 slot + 7)
+constexpr int kDwStaged = 13;    // slots staged per stage (the last is the ones slot)
+constexpr int kDwOnesSlot = 12;  // rows 96..103: ones
 constexpr uint64_t kDwWaitNs = 2000000000ull;
 
 struct DwGeom {
@@ -47,6 +56,7 @@ struct DwGeom {
   int tiles;            // 128-position items per plane
   int items;            // tiles * nz
   int W;                // window sites per slot (multiple of 8)
+  int stages;           // pipeline stages (3 where they fit, else 2)
   uint32_t a_bytes, b_bytes, stage_bytes, off_bars;
 };
 
@@ -59,10 +69,11 @@ __global__ void __launch_bounds__(kDwThreads, 1) k_dw_tc(const __nv_bfloat16* __
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + g.off_bars);
-  uint64_t* full = bars;                   // [stages]: copies landed
-  uint64_t* masked = bars + kDwStages;     // [stages]: dY masked (128 arrivals)
-  uint64_t* empty = bars + 2 * kDwStages;  // [stages]: MMAs done with the stage
-  uint64_t* done = bars + 3 * kDwStages;   // all MMAs done
+  const int stages = g.stages;
+  uint64_t* full = bars;                      // [stages]: copies landed
+  uint64_t* masked = bars + kDwMaxStages;     // [stages]: dY masked (128 arrivals)
+  uint64_t* empty = bars + 2 * kDwMaxStages;  // [stages]: every issuer's MMAs done with the stage
+  uint64_t* done = bars + 3 * kDwMaxStages;   // all MMAs done
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
@@ -73,12 +84,12 @@ __global__ void __launch_bounds__(kDwThreads, 1) k_dw_tc(const __nv_bfloat16* __
   const long long plane = (long long)g.px * g.py;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kDwStages; ++s) {
+    for (int s = 0; s < stages; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&masked[s], 128);
-      mbar_init(&empty[s], 1);
+      mbar_init(&empty[s], kDwIssuers);
     }
-    mbar_init(done, 1);
+    mbar_init(done, kDwIssuers);
     *abort_flag = 0;
     mbar_init_fence();
   }
@@ -89,7 +100,7 @@ __global__ void __launch_bounds__(kDwThreads, 1) k_dw_tc(const __nv_bfloat16* __
   // the ones slot of every stage (read by the MMAs through the async proxy)
   if (warp < 4) {
     const uint4 one = make_uint4(0x3F803F80u, 0x3F803F80u, 0x3F803F80u, 0x3F803F80u);  // eight BF16 1.0
-    for (int s = 0; s < kDwStages; ++s) {
+    for (int s = 0; s < stages; ++s) {
       uint4* o = reinterpret_cast<uint4*>(smem + s * g.stage_bytes + (size_t)kDwOnesSlot * g.W * 16);
       for (int k = threadIdx.x; k < g.W; k += 128) o[k] = one;
     }
@@ -117,8 +128,8 @@ __global__ void __launch_bounds__(kDwThreads, 1) k_dw_tc(const __nv_bfloat16* __
     if (lane == 0) {
       const uint32_t tx = (uint32_t)(3 * CG * g.W * 16 + OG * 128 * 16);
       for (int it = 0; it < nit; ++it) {
-        const int s = it % kDwStages;
-        if (it >= kDwStages && !bounded_wait(&empty[s], ((it / kDwStages) - 1) & 1)) break;
+        const int s = it % stages;
+        if (it >= stages && !bounded_wait(&empty[s], ((it / stages) - 1) & 1)) break;
         const int item = i0 + it, Z = item_Z(item), l0 = item_l0(item);
         unsigned char* st = smem + s * g.stage_bytes;
         mbar_arrive_expect_tx(&full[s], tx);
@@ -133,25 +144,31 @@ __global__ void __launch_bounds__(kDwThreads, 1) k_dw_tc(const __nv_bfloat16* __
         }
       }
     }
-  } else if (warp == 5) {
-    // ---------------- MMA issuer
+  } else if (warp >= 5) {
+    // ---------------- MMA issuers: warp 5 + j issues the shifts sh = 3 (dy + 1) + j
+    // (dx = j - 1) into accumulator blocks sh of C_out columns
     if (lane == 0) {
+      const int j = warp - 5;
       constexpr uint32_t idesc = umma_idesc_bf16(128, COUT) | (1u << 15) | (1u << 16);  // A, B MN-major
+      // MN-major, no swizzle: 8-site core-matrix columns 128 B apart along K,
+      // 8-row groups one slot (A) / one channel group (B) apart along M / N.
+      // A shifted or later operand is the same descriptor with its start
+      // address (bits 0-13, in 16-byte units) advanced: shared addresses stay
+      // below 256 KB, so the sum never carries out of that field.
+      const uint64_t ad0 = umma_sdesc_noswz(smem_addr(smem), 128u, (uint32_t)g.W * 16u);
+      const uint64_t bd0 = umma_sdesc_noswz(smem_addr(smem) + g.a_bytes, 128u, 2048u);
       for (int it = 0; it < nit; ++it) {
-        const int s = it % kDwStages;
-        if (!bounded_wait(&masked[s], (it / kDwStages) & 1)) break;
+        const int s = it % stages;
+        if (!bounded_wait(&masked[s], (it / stages) & 1)) break;
         tc_fence_after();
-        const uint32_t a0 = smem_addr(smem + s * g.stage_bytes), b0 = a0 + g.a_bytes;
-        for (int sh = 0; sh < 9; ++sh) {
-          const int woff = (sh / 3) * g.px + (sh % 3);  // (dy + 1) px + (dx + 1)
+        const uint64_t so = (uint64_t)((s * g.stage_bytes) >> 4);
 #pragma unroll
-          for (int kk = 0; kk < 8; ++kk) {
-            // MN-major, no swizzle: 8-site core-matrix columns 128 B apart along K,
-            // 8-row groups one slot (A) / one channel group (B) apart along M / N
-            const uint64_t ad = umma_sdesc_noswz(a0 + (uint32_t)(woff + kk * 16) * 16u, 128u, (uint32_t)g.W * 16u);
-            const uint64_t bd = umma_sdesc_noswz(b0 + (uint32_t)kk * 256u, 128u, 2048u);
-            umma_bf16(tmem_base + sh * COUT, ad, bd, idesc, (it > 0 || kk > 0) ? 1u : 0u);
-          }
+        for (int r = 0; r < 3; ++r) {
+          const uint64_t ad = ad0 + so + (uint64_t)(r * g.px + j);  // window offset (dy + 1) px + (dx + 1)
+          const uint32_t d = tmem_base + (uint32_t)(3 * r + j) * COUT;
+#pragma unroll
+          for (int kk = 0; kk < 8; ++kk)
+            umma_bf16(d, ad + (uint64_t)(kk * 16), bd0 + so + (uint64_t)(kk * 16), idesc, (it > 0 || kk > 0) ? 1u : 0u);
         }
         umma_commit(&empty[s]);
       }
@@ -162,8 +179,8 @@ __global__ void __launch_bounds__(kDwThreads, 1) k_dw_tc(const __nv_bfloat16* __
     // interior position, then (after all items) the epilogue
     const int k = threadIdx.x;  // position within the item
     for (int it = 0; it < nit; ++it) {
-      const int s = it % kDwStages;
-      if (!bounded_wait(&full[s], (it / kDwStages) & 1)) break;
+      const int s = it % stages;
+      if (!bounded_wait(&full[s], (it / stages) & 1)) break;
       const int l = item_l0(i0 + it) + k, xg = l % g.px;
       if (l > g.l_last || xg == 0 || xg == g.px - 1) {
         unsigned char* b = smem + s * g.stage_bytes + g.a_bytes;
@@ -202,7 +219,7 @@ __global__ void __launch_bounds__(kDwThreads, 1) k_dw_tc(const __nv_bfloat16* __
         if (m < 3 * CIN) {
           const int t = 9 * (m / CIN) + sh, ci = m % CIN;
 #pragma unroll
-          for (int c = 0; c < COUT; ++c) out[((size_t)t * CIN + ci) * COUT + c] = v[c];
+          for (int c = 0; c < COUT; ++c) out[((size_t)t * COUT + c) * CIN + ci] = v[c];  // lanes: consecutive ci
         } else if (m == 8 * kDwOnesSlot && sh == 0) {
 #pragma unroll
           for (int c = 0; c < COUT; ++c) out[27 * CIN * COUT + c] = v[c];
@@ -218,16 +235,41 @@ __global__ void __launch_bounds__(kDwThreads, 1) k_dw_tc(const __nv_bfloat16* __
   }
 }
 
-// dW += sum over parts of the partials (fixed order), db likewise
-__global__ void k_dw_reduce(const float* __restrict__ partial, int nparts, int nw, int nb, float* __restrict__ dW,
-                            float* __restrict__ db) {
-  const int count = nw + nb;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
-    float s = 0.f;
-    for (int p = 0; p < nparts; ++p) s += partial[(size_t)p * count + i];
-    if (i < nw) dW[i] += s;
-    else db[i - nw] += s;
+// dW += sum over parts of the partials, db likewise, in a fixed order: a
+// block takes 32 consecutive values; warp w adds parts w, w + 8, w + 16, ...
+// in turn (coalesced 128-byte rows), then thread l of warp 0 adds the eight
+// warps' sums in warp order.  A CTA's partial holds the weight gradients as
+// [tap][C_out][C_in] (its epilogue threads are the C_in rows, so each of its
+// stores is one coalesced row) and then the C_out bias gradients.
+constexpr int kRedWarps = 8;
+__global__ void __launch_bounds__(32 * kRedWarps) k_dw_reduce(const float* __restrict__ partial, int nparts, int cin,
+                                                              int cout, float* __restrict__ dW, float* __restrict__ db) {
+  __shared__ float red[kRedWarps][32];
+  const int nw = 27 * cin * cout, count = nw + cout;
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int i = blockIdx.x * 32 + lane;
+  float s = 0.f;
+  if (i < count) {
+#pragma unroll 4
+    for (int p = warp; p < nparts; p += kRedWarps) s += partial[(size_t)p * count + i];
   }
+  red[warp][lane] = s;
+  __syncthreads();
+  if (warp == 0 && i < count) {
+    float t = red[0][lane];
+#pragma unroll
+    for (int w = 1; w < kRedWarps; ++w) t += red[w][lane];
+    if (i < nw) {
+      const int tap = i / (cin * cout), r = i % (cin * cout), co = r / cin, ci = r % cin;
+      dW[((size_t)tap * cin + ci) * cout + co] += t;
+    } else {
+      db[i - nw] += t;
+    }
+  }
+}
+
+size_t dw_smem_bytes(const DwGeom& g) {
+  return (size_t)g.off_bars + (3 * kDwMaxStages + 1) * 8 + 16 + 1024;
 }
 
 bool dw_geometry(int cin, int cout, int nx, int ny, int nz, DwGeom* g, size_t* smem) {
@@ -238,15 +280,19 @@ bool dw_geometry(int cin, int cout, int nx, int ny, int nz, DwGeom* g, size_t* s
   g->tiles = (g->l_last - g->l_first + 128) / 128;
   g->items = g->tiles * nz;
   g->W = ((128 + 2 * g->px + 2) + 7) / 8 * 8;
-  g->a_bytes = (uint32_t)kDwSlots * g->W * 16;
+  g->a_bytes = (uint32_t)kDwStaged * g->W * 16;
   g->b_bytes = (uint32_t)(cout / 8) * 2048;
-  g->stage_bytes = g->a_bytes + g->b_bytes;
-  // 4 KB after the stages: the last B core matrices of a stage stay inside the
-  // allocation under either reading of the operand strides
-  g->off_bars = kDwStages * g->stage_bytes + 4096;
-  *smem = (size_t)g->off_bars + (3 * kDwStages + 1) * 8 + 16 + 1024;
+  g->stage_bytes = (g->a_bytes + g->b_bytes + 1023) / 1024 * 1024;
+  for (g->stages = kDwMaxStages; g->stages >= 2; --g->stages) {
+    // after the last stage: its spare A slots (13..15), which the MMAs read,
+    // and 4 KB so that the last B core matrices of a stage stay inside the
+    // allocation under either reading of the operand strides
+    g->off_bars = g->stages * g->stage_bytes + (uint32_t)(kDwSlots - kDwStaged) * g->W * 16 + 4096;
+    *smem = dw_smem_bytes(*g);
+    if (*smem <= 227 * 1024) break;
+  }
   (void)cin;
-  return *smem <= 227 * 1024 && g->W < 16384;
+  return g->stages >= 2 && *smem <= 227 * 1024 && g->W < 16384;
 }
 
 }  // namespace
@@ -272,7 +318,7 @@ static cudaError_t dw_launch_t(const __nv_bfloat16* X, const __nv_bfloat16* dY, 
   const int grid = g.items < sms ? g.items : sms;
   k_dw_tc<CIN, COUT><<<grid, kDwThreads, smem, s>>>(X, dY, g, partial, err);
   const int nw = 27 * CIN * COUT;
-  k_dw_reduce<<<(nw + COUT + 255) / 256, 256, 0, s>>>(partial, grid, nw, COUT, dW, db);
+  k_dw_reduce<<<(nw + COUT + 31) / 32, 32 * kRedWarps, 0, s>>>(partial, grid, CIN, COUT, dW, db);
   return cudaGetLastError();
 }
 

@@ -101,30 +101,63 @@ cudaError_t launch_max_abs_diff(const void* a, const void* b, long long n, void*
   return cudaGetLastError();
 }
 
-// Element of component c at padded position (X, Y) of plane z in a padded
-// mirror whose first 4G components are interleaved by fours
-// ([group][z][Y][X][4]) and whose others follow as plain arrays ([z][Y][X]).
-__device__ __forceinline__ long long mirror_at(int c, int z, int Y, int X, int G, int nz, int nxp, int nyp) {
-  if (c < 4 * G) return ((((long long)(c >> 2) * nz + z) * nyp + Y) * nxp + X) * 4 + (c & 3);
-  return 4LL * G * nz * nyp * nxp + (((long long)(c - 4 * G) * nz + z) * nyp + Y) * nxp + X;
+// A padded mirror holds its first 4G components interleaved by fours
+// ([group][z][Y][X][4]) and the others as plain arrays ([z][Y][X]) after
+// them.  The copies below walk it by units (a group of four components, or
+// one plain component) and rows: one CTA per (unit, plane, row), threads
+// along the row, so no thread divides a 64-bit index and a group moves as one
+// 16-byte vector (FP32) per site.
+__device__ __forceinline__ int wrap_mod(int v, int n) {
+  v %= n;
+  return v < 0 ? v + n : v;
 }
 
-// every padded position of component c: flat[c][z][wrap(Y - hy)][wrap(X - hx)]
+template <typename real>
+__device__ __forceinline__ void put4(real* p, real a, real b, real c, real d) {
+  if constexpr (sizeof(real) == 4) {
+    *reinterpret_cast<float4*>(p) = make_float4(a, b, c, d);
+  } else {
+    *reinterpret_cast<double2*>(p) = make_double2(a, b);
+    *reinterpret_cast<double2*>(p + 2) = make_double2(c, d);
+  }
+}
+template <typename real>
+__device__ __forceinline__ void get4(const real* p, real v[4]) {
+  if constexpr (sizeof(real) == 4) {
+    const float4 a = *reinterpret_cast<const float4*>(p);
+    v[0] = a.x, v[1] = a.y, v[2] = a.z, v[3] = a.w;
+  } else {
+    const double2 a = *reinterpret_cast<const double2*>(p), b = *reinterpret_cast<const double2*>(p + 2);
+    v[0] = a.x, v[1] = a.y, v[2] = b.x, v[3] = b.y;
+  }
+}
+
+// every padded position of every component: flat[c][z][wrap(Y - hy)][wrap(X - hx)]
 template <typename real>
 __global__ void k_pack(const real* __restrict__ flat, real* __restrict__ padded, int C, int G, int nx, int ny, int nz,
                        int hx, int hy, int nxp, int nyp) {
-  const long long total = (long long)C * nz * nyp * nxp;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
-       i += (long long)gridDim.x * blockDim.x) {
-    const int X = (int)(i % nxp);
-    const long long r = i / nxp;
+  const long long rows = (long long)(G + C - 4 * G) * nz * nyp;
+  const long long plane = (long long)ny * nx, cstride = plane * nz;    // flat component stride
+  const long long pplane = (long long)nyp * nxp, pstride = pplane * nz;  // padded plain-component stride
+  for (long long r = blockIdx.x; r < rows; r += gridDim.x) {
     const int Y = (int)(r % nyp);
-    const long long cz = r / nyp;  // c * nz + z
-    const int z = (int)(cz % nz), c = (int)(cz / nz);
-    int x = (X - hx) % nx, y = (Y - hy) % ny;
-    x += x < 0 ? nx : 0;
-    y += y < 0 ? ny : 0;
-    padded[mirror_at(c, z, Y, X, G, nz, nxp, nyp)] = flat[(cz * ny + y) * nx + x];
+    const long long uz = r / nyp;
+    const int z = (int)(uz % nz), u = (int)(uz / nz);
+    const int y = wrap_mod(Y - hy, ny);
+    const real* src = flat + (long long)z * plane + (long long)y * nx;
+    if (u < G) {
+      src += (long long)(4 * u) * cstride;
+      real* dst = padded + (((long long)u * nz + z) * nyp + Y) * nxp * 4;
+      for (int X = threadIdx.x; X < nxp; X += blockDim.x) {
+        const int x = wrap_mod(X - hx, nx);
+        put4(dst + (long long)X * 4, src[x], src[cstride + x], src[2 * cstride + x], src[3 * cstride + x]);
+      }
+    } else {
+      src += (long long)(4 * G + (u - G)) * cstride;
+      real* dst = padded + 4 * (long long)G * pstride + (long long)(u - G) * pstride + (long long)z * pplane +
+                  (long long)Y * nxp;
+      for (int X = threadIdx.x; X < nxp; X += blockDim.x) dst[X] = src[wrap_mod(X - hx, nx)];
+    }
   }
 }
 
@@ -132,31 +165,51 @@ __global__ void k_pack(const real* __restrict__ flat, real* __restrict__ padded,
 template <typename real>
 __global__ void k_unpack(const real* __restrict__ padded, real* __restrict__ flat, int C, int G, int nx, int ny,
                          int nz, int hx, int hy, int nxp, int nyp) {
-  const long long total = (long long)C * nz * ny * nx;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
-       i += (long long)gridDim.x * blockDim.x) {
-    const int x = (int)(i % nx);
-    const long long r = i / nx;
+  const long long rows = (long long)(G + C - 4 * G) * nz * ny;
+  const long long plane = (long long)ny * nx, cstride = plane * nz;
+  const long long pplane = (long long)nyp * nxp, pstride = pplane * nz;
+  for (long long r = blockIdx.x; r < rows; r += gridDim.x) {
     const int y = (int)(r % ny);
-    const long long cz = r / ny;
-    const int z = (int)(cz % nz), c = (int)(cz / nz);
-    flat[i] = padded[mirror_at(c, z, y + hy, x + hx, G, nz, nxp, nyp)];
+    const long long uz = r / ny;
+    const int z = (int)(uz % nz), u = (int)(uz / nz);
+    real* dst = flat + (long long)z * plane + (long long)y * nx;
+    if (u < G) {
+      dst += (long long)(4 * u) * cstride;
+      const real* src = padded + (((long long)u * nz + z) * nyp + (y + hy)) * nxp * 4;
+      for (int x = threadIdx.x; x < nx; x += blockDim.x) {
+        real v[4];
+        get4(src + (long long)(x + hx) * 4, v);
+        dst[x] = v[0];
+        dst[cstride + x] = v[1];
+        dst[2 * cstride + x] = v[2];
+        dst[3 * cstride + x] = v[3];
+      }
+    } else {
+      dst += (long long)(4 * G + (u - G)) * cstride;
+      const real* src = padded + 4 * (long long)G * pstride + (long long)(u - G) * pstride + (long long)z * pplane +
+                        (long long)(y + hy) * nxp;
+      for (int x = threadIdx.x; x < nx; x += blockDim.x) dst[x] = src[x + hx];
+    }
   }
 }
+
+int copy_grid(long long rows) { return (int)(rows < (1ll << 30) ? (rows > 0 ? rows : 1) : (1ll << 30)); }
 
 template <typename real>
 cudaError_t launch_pack(const void* flat, void* padded, int C, int G, int nx, int ny, int nz, int hx, int hy,
                         int nxp, int nyp, cudaStream_t s) {
-  k_pack<real><<<4096, 256, 0, s>>>(static_cast<const real*>(flat), static_cast<real*>(padded), C, G, nx, ny, nz, hx,
-                                    hy, nxp, nyp);
+  const long long rows = (long long)(C - 3 * G) * nz * nyp;
+  k_pack<real><<<copy_grid(rows), 128, 0, s>>>(static_cast<const real*>(flat), static_cast<real*>(padded), C, G, nx,
+                                               ny, nz, hx, hy, nxp, nyp);
   return cudaGetLastError();
 }
 
 template <typename real>
 cudaError_t launch_unpack(const void* padded, void* flat, int C, int G, int nx, int ny, int nz, int hx, int hy,
                           int nxp, int nyp, cudaStream_t s) {
-  k_unpack<real><<<4096, 256, 0, s>>>(static_cast<const real*>(padded), static_cast<real*>(flat), C, G, nx, ny, nz,
-                                      hx, hy, nxp, nyp);
+  const long long rows = (long long)(C - 3 * G) * nz * ny;
+  k_unpack<real><<<copy_grid(rows), 128, 0, s>>>(static_cast<const real*>(padded), static_cast<real*>(flat), C, G,
+                                                 nx, ny, nz, hx, hy, nxp, nyp);
   return cudaGetLastError();
 }
 

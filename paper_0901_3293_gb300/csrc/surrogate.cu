@@ -120,9 +120,11 @@ __global__ void k_sur_loss(const float* __restrict__ y, const float* __restrict_
   const long long n = (long long)nx * ny * nz;
   const int px = nx + 2, py = ny + 2, pz = nz + 2;
   const long long np = (long long)px * py * pz;
+  const float gscale = (float)(2.0 * inv_den);
   double acc = 0.0;
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < np; p += (long long)gridDim.x * blockDim.x) {
-    const int X = (int)(p % px), Y = (int)((p / px) % py), Z = (int)(p / ((long long)px * py));
+    const int pi = (int)p, row = pi / px;  // np <= 2^31 (checked when the surrogate is made)
+    const int X = pi - row * px, Y = row % py, Z = row / py;
     const int x = (X + nx - 1) % nx, yy = (Y + ny - 1) % ny, z = (Z + nz - 1) % nz;
     const long long s = ((long long)z * ny + yy) * nx + x;
     const bool interior = X >= 1 && X <= nx && Y >= 1 && Y <= ny && Z >= 1 && Z <= nz;
@@ -130,13 +132,15 @@ __global__ void k_sur_loss(const float* __restrict__ y, const float* __restrict_
     float g[16];
 #pragma unroll
     for (int c = 0; c < 16; ++c) g[c] = 0.f;
+    float sq = 0.f;  // this site's w |d|^2 (FP32; the sum over sites is FP64)
 #pragma unroll
     for (int c = 0; c < 5; ++c) {
       const float tc = target[c * n + s] - (rate ? ksteps * rate[c * n + s] : 0.f);
       const float d = y[s * 16 + c] - tc * inv_sdq;
-      g[c] = (float)(2.0 * w * d * inv_den);
-      if (interior) acc += (double)w * d * d;
+      g[c] = gscale * w * d;
+      sq += w * d * d;
     }
+    if (interior) acc += (double)sq;
     uint4 pk[2];
 #pragma unroll
     for (int q2 = 0; q2 < 2; ++q2) {
@@ -157,12 +161,16 @@ __global__ void k_sur_loss(const float* __restrict__ y, const float* __restrict_
   if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
 }
 
+// sum of nb partials times scale, by one warp in a fixed order: lane l adds
+// partials l, l + 32, ... in turn, then the lanes' sums meet in a fixed tree
 __global__ void k_sum(const double* __restrict__ partial, int nb, double scale, double* __restrict__ out) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
-    double s = 0;
-    for (int i = 0; i < nb; ++i) s += partial[i];
-    *out = s * scale;
-  }
+  if (blockIdx.x != 0 || threadIdx.x >= 32) return;
+  double s = 0;
+#pragma unroll 4
+  for (int i = threadIdx.x; i < nb; i += 32) s += partial[i];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if (threadIdx.x == 0) *out = s * scale;
 }
 
 // Weight gradient of one layer, FP32 on CUDA cores:
@@ -367,6 +375,7 @@ struct lcbp_surrogate {
   int ksteps;  // solver steps one call stands for
   int sms;
   int conv_kernel;  // LCBP_CONV_*
+  bool dw_cuda_cores;  // weight gradients on the CUDA-core kernel even where the tensor-core one fits
   // parameters: FP32 master (padded) per layer, BF16 forward / backward copies
   float* master;  // all layers, padded
   size_t off_w[kLayers], off_b[kLayers];
@@ -472,7 +481,7 @@ cudaError_t forward(lcbp_surrogate* s, float* qupdate, const float* rate = nullp
 // plane windows fit shared memory, else on CUDA cores (FP32 atomics)
 template <int CX, int CY>
 cudaError_t launch_dw(lcbp_surrogate* s, const __nv_bfloat16* X, const __nv_bfloat16* dY, int l) {
-  if (dw_fits(CX, CY, s->nx, s->ny, s->nz))
+  if (!s->dw_cuda_cores && dw_fits(CX, CY, s->nx, s->ny, s->nz))
     return dw_launch(CX, CY, X, dY, s->nx, s->ny, s->nz, s->dw_partial, s->grad + s->off_w[l], s->grad + s->off_b[l],
                      s->d_err, s->sms, s->stream);
   const int chunk = 4096;
@@ -679,10 +688,13 @@ int lcbp_surrogate_get_steps(lcbp_surrogate* s, int* k) {
 int lcbp_surrogate_set_conv_kernel(lcbp_surrogate* s, int kind) {
   int rc = check_s(s);
   if (rc) return rc;
+  const bool dw_cc = (kind & LCBP_CONV_DW_CUDA_CORES) != 0;
+  kind &= ~LCBP_CONV_DW_CUDA_CORES;
   if (kind < LCBP_CONV_AUTO || kind > LCBP_CONV_WINDOW) return fail(LCBP_EINVAL, "unknown conv kernel %d", kind);
   if (kind == LCBP_CONV_WINDOW && !s->tmX.use_win)
     return fail(LCBP_EINVAL, "a %d x %d plane does not fit the window kernel", s->nx, s->ny);
   s->conv_kernel = kind;
+  s->dw_cuda_cores = dw_cc;
   return LCBP_OK;
 }
 

@@ -27,6 +27,7 @@ BPII, CHOL_X, CHOL_Y, CHOL_Z, ISO_NOISE, SLAB_BPII_IN_CHOL, SLAB_BPII_IN_ISO, SL
 JACOBI, GAUSS_SEIDEL = 0, 1
 PATH_AUTO, PATH_GENERIC, PATH_FAST1, PATH_FAST2 = 0, 1, 2, 3
 CONV_AUTO, CONV_TAPS, CONV_WINDOW = 0, 1, 2
+CONV_DW_CUDA_CORES = 4  # OR-ed into a kind: weight gradients on the CUDA-core kernel
 
 _lib = None
 
@@ -625,7 +626,8 @@ class Surrogate:
         return self
 
     def set_conv_kernel(self, kind: int) -> "Surrogate":
-        """CONV_AUTO, CONV_TAPS (one shifted tile per tap) or CONV_WINDOW (one staged plane for all taps)."""
+        """CONV_AUTO, CONV_TAPS (one shifted tile per tap) or CONV_WINDOW (one staged plane for all taps),
+        optionally OR-ed with CONV_DW_CUDA_CORES (weight gradients on the CUDA-core kernel)."""
         check(lib().lcbp_surrogate_set_conv_kernel(self._h, kind))
         return self
 

@@ -74,10 +74,11 @@ def test_forward_matches_oracle(lcbp, dims, kernel):
 
 
 # (conv kernel, dims): the weight gradients run on the tensor cores (plane
-# windows staged in shared memory) for the first two, and on the CUDA-core
-# kernel for the 144-wide plane, whose windows do not fit
+# windows staged in shared memory; three stages for the 32-wide planes, two
+# for the 144-wide ones), and on the CUDA-core kernel for the 200-wide plane,
+# whose windows do not fit
 @pytest.mark.parametrize("kernel,dims", [("CONV_TAPS", (32, 8, 6)), ("CONV_WINDOW", (32, 8, 6)),
-                                         ("CONV_TAPS", (144, 4, 2))])
+                                         ("CONV_TAPS", (144, 4, 2)), ("CONV_TAPS", (200, 4, 2))])
 def test_training_gradients_match_oracle(lcbp, kernel, dims):
     nx, ny, nz = dims
     shape = (nz, ny, nx)
@@ -124,6 +125,40 @@ def test_training_gradients_match_oracle(lcbp, kernel, dims):
     # Adam moved the parameters by about lr
     step = sur.get_params().astype(np.float64) - S.flatten(P, BLOCKS)
     assert 0 < np.abs(step).max() < 1.5e-6
+
+
+def test_tensor_core_weight_gradients_match_cuda_cores_over_many_items(lcbp):
+    """32 x 32 x 72: 648 items of 128 plane positions, so each of the (up to
+    152) CTAs of the tensor-core kernel takes four or five and its ring of
+    three stages wraps.  The same training step with the weight gradients on
+    the CUDA-core kernel (FP32 atomics) gives the same loss bitwise (the
+    forward pass is the same) and the same gradients up to the FP32
+    accumulation order: 1e-3 of each layer's largest gradient bounds every
+    element, while a dropped item, a wrong stage or a stale tile is off by
+    O(1)."""
+    nx, ny, nz = 32, 32, 72
+    shape = (nz, ny, nx)
+    P = random_params(30)
+    q5 = synth.smooth_q5(shape, 0.3, 31)
+    u3 = synth.random_velocity(shape, 2e-4, 32)
+    r5 = synth.random_q5(shape, 1e-3, 33)
+    dq = 10.0 * r5 + synth.random_q5(shape, 5e-4, 34)
+    mask = np.ones(shape)
+    out = {}
+    for name, kind in (("tc", lcbp.CONV_WINDOW), ("cc", lcbp.CONV_WINDOW | lcbp.CONV_DW_CUDA_CORES)):
+        sur = lcbp.Surrogate(nx, ny, nz, training=True)
+        sur.set_conv_kernel(kind)
+        sur.set_params(S.flatten(P, BLOCKS))
+        loss = sur.train_step(q5, u3, r5, 0.9, 0.2, dq, mask, lr=1e-6)
+        out[name] = (loss, S.unflatten(sur.get_grads().astype(np.float64), P, BLOCKS))
+        sur.close()
+    assert out["tc"][0] == out["cc"][0]
+    for layer in S.layer_names(BLOCKS):
+        for k in (0, 1):
+            a, b = out["tc"][1][layer][k], out["cc"][1][layer][k]
+            err = np.abs(a - b).max() / np.abs(b).max()
+            print(layer, "W" if k == 0 else "b", f"max |tc - cc| / max|g| {err:.2e}")
+            assert err < 1e-3, (layer, k, err)
 
 
 def test_surrogate_step_applies_prediction(lcbp):
