@@ -108,9 +108,11 @@ bool use_fast(const lcbp_batch* b) {
 // (replica stride 5 cq), the rho u mirrors (stride 4 cu) and the padded
 // scratch (stride 16 (nx+4)(ny+2)nz)
 bool build_maps(lcbp_batch* b) {
-  const int ty = b->dtype == LCBP_F64 ? zm_tile_rows<double>() : zm_tile_rows<float>();
   for (int k = 0; k < b->zb.nclass; ++k) {
     const ZmClass& c = b->zb.c[k];
+    // boxes of the class's tiles (tx x ty sites): Q tx + 8 wide from x0 - 4, ty + 4 rows; rho u and the
+    // scratch tx + 2 wide from x0 - 1, ty + 2 rows
+    const int tx = c.G.tx, ty = c.G.ty;
     const cuuint64_t es = b->es;
     const cuuint64_t nx = c.G.nx, ny = c.G.ny, nz = c.G.nz;
     const cuuint64_t nxm = zm_mirror_nx(c.G.nx), nyq = ny + 4, nyu = ny + 2, cq = nxm * nyq * nz, cu = nxm * nyu * nz;
@@ -127,11 +129,11 @@ bool build_maps(lcbp_batch* b) {
     const cuuint64_t pdims[5] = {4 * nxp, nyp, (cuuint64_t)kZmPQG, nz, (cuuint64_t)c.count};
     const cuuint64_t pstr[4] = {4 * nxp * es, 4 * nxp * nyp * es, (cuuint64_t)kZmPQ * nxp * nyp * es,
                                 (cuuint64_t)kZmPQ * cp * es};
-    const cuuint32_t pbox[5] = {(cuuint32_t)(4 * kZmBoxXP), (cuuint32_t)(ty + 2), (cuuint32_t)kZmPQG, 1, 1};
-    bool ok = mirror(&b->maps[0].q[k], b->qm, c.qm0, 4 * nxm, nyq, 5 * cq, 4 * kZmBoxX, ty + 4) &&
-              mirror(&b->maps[0].q1[k], b->qm, c.qm0 + 4 * (long long)cq, nxm, nyq, 5 * cq, kZmBoxX, ty + 4) &&
-              mirror(&b->maps[0].u[k], b->um[0], c.um0, 4 * nxm, nyu, 4 * cu, 4 * kZmBoxXU, ty + 2) &&
-              mirror(&b->maps[1].u[k], b->um[1], c.um0, 4 * nxm, nyu, 4 * cu, 4 * kZmBoxXU, ty + 2) &&
+    const cuuint32_t pbox[5] = {(cuuint32_t)(4 * (tx + 2)), (cuuint32_t)(ty + 2), (cuuint32_t)kZmPQG, 1, 1};
+    bool ok = mirror(&b->maps[0].q[k], b->qm, c.qm0, 4 * nxm, nyq, 5 * cq, 4 * (tx + 8), ty + 4) &&
+              mirror(&b->maps[0].q1[k], b->qm, c.qm0 + 4 * (long long)cq, nxm, nyq, 5 * cq, tx + 8, ty + 4) &&
+              mirror(&b->maps[0].u[k], b->um[0], c.um0, 4 * nxm, nyu, 4 * cu, 4 * (tx + 2), ty + 2) &&
+              mirror(&b->maps[1].u[k], b->um[1], c.um0, 4 * nxm, nyu, 4 * cu, 4 * (tx + 2), ty + 2) &&
               encode_tiled(&b->maps[0].pq[k], static_cast<char*>(b->pq) + (size_t)c.pq0 * b->es, 5, pdims, pstr,
                            pbox, b->dtype);
     if (!ok) return false;
@@ -146,13 +148,12 @@ bool build_maps(lcbp_batch* b) {
 
 // geometry and CTA ranges of the classes for zc[k] planes per CTA in class k
 void set_zc(lcbp_batch* b, const int* zc) {
-  const int ty = b->dtype == LCBP_F64 ? zm_tile_rows<double>() : zm_tile_rows<float>();
   int cta = 0;
   for (int k = 0; k < b->zb.nclass; ++k) {
     ZmClass& c = b->zb.c[k];
     c.G.zc = std::min(zc[k], c.G.nz);
-    c.G.tiles_x = (c.G.nx + 31) / 32;
-    c.G.tiles_y = (c.G.ny + ty - 1) / ty;
+    c.G.tiles_x = (c.G.nx + c.G.tx - 1) / c.G.tx;
+    c.G.tiles_y = (c.G.ny + c.G.ty - 1) / c.G.ty;
     c.G.tiles_z = (c.G.nz + c.G.zc - 1) / c.G.zc;
     c.ctas_per_rep = c.G.tiles_x * c.G.tiles_y * c.G.tiles_z;
     c.G.nxp = c.G.nx + kZmPadX;
@@ -572,6 +573,10 @@ int lcbp_batch_create(int R, const int* dims, const lcbp_params* params, int dty
       c.G.ny = b->ny[q];
       c.G.nz = b->nz[q];
       c.G.n = b->n[q];
+      // tile shape of the fast kernels: 32 x TY, or narrow 16 x 2 TY
+      const int ty = dtype == LCBP_F64 ? zm_tile_rows<double>() : zm_tile_rows<float>();
+      c.G.tx = zm_batch_tile_x(c.G.nx, dtype != LCBP_F64);
+      c.G.ty = c.G.tx == kZmNarrowX ? 2 * ty : ty;
       c.rep0 = (int)b->order.size();
       c.count = (int)members[k].size();
     }

@@ -151,6 +151,7 @@ constexpr int kZmPQG = 4;    // groups
 struct ZmGeom {
   int nx, ny, nz, zc;
   long long n;
+  int tx, ty;  // tile width and rows: 32 x 8 (FP32) or 32 x 4 (FP64); narrow batch tiles 16 x 16
   int tiles_x, tiles_y, tiles_z;
   int nxp, nyp;    // padded scratch and rho u mirror extents: nx + 4, ny + 2
   long long cp;    // their component stride: nxp * nyp * nz
@@ -170,6 +171,11 @@ struct ZmGeom {
 // the plain array [z][Y][X] of yz.  k_lbq writes Q^{n+1} and rho u^{n+1} there,
 // images included, so the next step stages them with no patching.
 constexpr int kZmMirX = 32;  // columns before x = 0 in a mirror row
+// Batch classes of FP32 replicas whose width leaves a last 32-column tile at
+// most half full (nx % 32 in 1..16, e.g. 48) take tiles of 16 columns by 16
+// rows instead: the same 256 sites and threads, no idle lanes.
+constexpr int kZmNarrowX = 16;
+inline int zm_batch_tile_x(int nx, bool fp32) { return fp32 && nx % 32 != 0 && nx % 32 <= 16 ? kZmNarrowX : 32; }
 inline int zm_mirror_nx(int nx) { return (nx + 31) / 32 * 32 + 2 * kZmMirX; }  // mirror row length
 inline long long zm_qmirror_elems(int nx, int ny, int nz) { return 5LL * zm_mirror_nx(nx) * (ny + 4) * nz; }
 inline long long zm_umirror_elems(int nx, int ny, int nz) { return 4LL * zm_mirror_nx(nx) * (ny + 2) * nz; }

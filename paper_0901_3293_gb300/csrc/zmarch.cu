@@ -37,15 +37,18 @@ constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s bound on any barrier wa
 
 // Staged boxes of the state fields Q (halo 2) and rho u (halo 1) from their
 // padded mirrors (site x at mirror column x + 32, y at row y + 2 (Q) or y + 1
-// (rho u)), whose ghosts hold the periodic images.  QW, UW: box widths in
-// sites; QX, UX: the box column of x0.  The Q box (for its plain yz array) is
-// 40 wide from x0 - 4, a 16-byte aligned start; the rho u mirror, 16 bytes
-// per site, stages just x0 - 1 .. x0 + 32.  QPX, QPY, UPX, UPY: the mirror
-// offsets of a site.
-struct StateBox {
-  static constexpr int QW = ZM_BX, QX = ZM_XOFF, QPX = kZmMirX, QPY = 2;
-  static constexpr int UW = kZmBoxXU, UX = 1, UPX = kZmMirX, UPY = 1;
+// (rho u)), whose ghosts hold the periodic images, for tiles TX sites wide.
+// QW, UW: box widths in sites; QX, UX: the box column of x0.  The Q box (for
+// its plain yz array) is TX + 8 wide from x0 - 4, a 16-byte aligned start; the
+// rho u mirror, 16 bytes per site, stages just x0 - 1 .. x0 + TX.  QPX, QPY,
+// UPX, UPY: the mirror offsets of a site.
+template <int TX>
+struct StateBoxT {
+  static constexpr int QW = TX + 2 * ZM_XOFF, QX = ZM_XOFF, QPX = kZmMirX, QPY = 2;
+  static constexpr int UW = TX + 2, UX = 1, UPX = kZmMirX, UPY = 1;
 };
+using StateBox = StateBoxT<ZM_TX>;
+static_assert(StateBox::QW == ZM_BX && StateBox::UW == kZmBoxXU && ZM_TX + 2 == kZmBoxXP, "box widths");
 
 __host__ __device__ constexpr int align_elems(int elems, int esize) {
   // round an element count up so that it spans a multiple of 128 bytes
@@ -157,15 +160,15 @@ __device__ __forceinline__ Model<V> widen(const Model<real>& m) {
 // ---------------------------------------------------------------------------
 // Kernel A: H, sigma, tau, b and the Heun predictor
 // ---------------------------------------------------------------------------
-template <typename real, int TY>
+template <typename real, int TY, int TX = ZM_TX>
 struct QsideSmem {
-  using B = StateBox;
-  static constexpr int QROWS = TY + 4, UROWS = TY + 2, TROWS = TY + 2, TCOLS = ZM_TX + 2;
+  using B = StateBoxT<TX>;
+  static constexpr int QROWS = TY + 4, UROWS = TY + 2, TROWS = TY + 2, TCOLS = TX + 2;
   static constexpr int QSLOTS = 5, USLOTS = 4;
   static constexpr int QCS = QROWS * B::QW, UCS = UROWS * B::UW;  // per-component strides
   static constexpr int QSLOT = align_elems(5 * QCS, sizeof(real)), USLOT = align_elems(4 * UCS, sizeof(real));
   // own cells of a plane: H (5 components) then sigma_LC (5)
-  static constexpr int TSLOT = 3 * TROWS * TCOLS, HSLOT = 10 * TY * ZM_TX;
+  static constexpr int TSLOT = 3 * TROWS * TCOLS, HSLOT = 10 * TY * TX;
   static constexpr int OFF_U = QSLOTS * QSLOT, OFF_T = OFF_U + USLOTS * USLOT;
   static constexpr int OFF_H = OFF_T + 3 * TSLOT, OFF_BAR = align_elems(OFF_H + 2 * HSLOT, sizeof(real));
   // barriers, then the abort flag
@@ -175,24 +178,25 @@ struct QsideSmem {
 // Threads of a k_qside CTA: enough to cover the H / tau ring of a plane
 // ((TY + 2) x (TX + 2) cells, a pair per thread with SPT = 2) in one pass, and
 // at least the TY / SPT rows of the output pass.
-template <int TY, int SPT>
+template <int TY, int SPT, int TX = ZM_TX>
 constexpr int qside_threads() {
-  constexpr int ring = (TY + 2) / SPT * (ZM_TX + 2), out = ZM_TX * TY / SPT;
+  constexpr int ring = (TY + 2) / SPT * (TX + 2), out = TX * TY / SPT;
   return ((ring > out ? ring : out) + 31) / 32 * 32;
 }
 
-// Tile bt of one lattice (or of replica rc of a batch class, whose fields are
-// 5-D tensors with the replica outermost: BATCH) of the k_qside step.
+// Tile bt (TX x TY sites) of one lattice (or of replica rc of a batch class,
+// whose fields are 5-D tensors with the replica outermost: BATCH) of the
+// k_qside step.
 // WALLS: walls half a spacing below z = 0 and above z = nz-1.  The ghost
 // planes z = -1 and z = nz hold the anchored qw in every Q stencil, carry no
 // molecular field (tau = 0 there) and the velocity -u of the adjacent plane.
-template <typename real, int TY, int SPT, bool BATCH, bool WALLS>
+template <typename real, int TY, int SPT, bool BATCH, bool WALLS, int TX = ZM_TX>
 __device__ __forceinline__ void qside_body(const CUtensorMap* tmQ, const CUtensorMap* tmQ1, const CUtensorMap* tmU,
                                            const ZmGeom G,
                                            const Model<real> m, int bt, int rc, const real* __restrict__ bext,
                                            real* __restrict__ pq, int* __restrict__ err, const Sym5<real> qw) {
-  using L = QsideSmem<real, TY>;
-  using B = StateBox;
+  using L = QsideSmem<real, TY, TX>;
+  using B = StateBoxT<TX>;
   using V = typename LaneT<real, SPT>::V;
   constexpr int TYH = TY / SPT;  // rows handled by one pass of the CTA
   static_assert(TY % SPT == 0 && (TY + 2) % SPT == 0, "tile rows must split evenly between the lanes");
@@ -209,11 +213,11 @@ __device__ __forceinline__ void qside_body(const CUtensorMap* tmQ, const CUtenso
   // takes this path only where 15 components of every field do
   const int nx = G.nx, ny = G.ny, nz = G.nz;
   const int n = (int)G.n;
-  const int x0 = (bt % G.tiles_x) * ZM_TX;
+  const int x0 = (bt % G.tiles_x) * TX;
   const int y0 = ((bt / G.tiles_x) % G.tiles_y) * TY;
   const int z0 = (bt / (G.tiles_x * G.tiles_y)) * G.zc;
   const int z1 = min(z0 + G.zc, nz);
-  const int tx = threadIdx.x % ZM_TX, ty = threadIdx.x / ZM_TX;  // rows ty + k * TYH, k < SPT
+  const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;  // rows ty + k * TYH, k < SPT
   const int gx = x0 + tx;
   constexpr uint32_t qbytes = 5 * L::QCS * sizeof(real), ubytes = 4 * L::UCS * sizeof(real);
 
@@ -317,12 +321,12 @@ __device__ __forceinline__ void qside_body(const CUtensorMap* tmQ, const CUtenso
     real* tp = tslot(p);
     real* hp = hslot(p);
     if constexpr (SPT == 1) {
-      constexpr int NIN = TY * ZM_TX, TC = L::TCOLS;
+      constexpr int NIN = TY * TX, TC = L::TCOLS;
       const int t = threadIdx.x;
       int r = -1, c = 0;
       if (t < NIN) {
-        r = t / ZM_TX + 1;
-        c = t % ZM_TX + 1;
+        r = t / TX + 1;
+        c = t % TX + 1;
       } else {
         const int u = t - NIN;
         if (u < TC) {
@@ -405,18 +409,18 @@ __device__ __forceinline__ void qside_body(const CUtensorMap* tmQ, const CUtenso
         tp[ti] = lane<SPT, real>(tu[0], k);
         tp[L::TROWS * L::TCOLS + ti] = lane<SPT, real>(tu[1], k);
         tp[2 * L::TROWS * L::TCOLS + ti] = lane<SPT, real>(tu[2], k);
-        if (r >= 1 && r <= TY && c >= 1 && c <= ZM_TX) {
-          const int i = (r - 1) * ZM_TX + (c - 1);
-          hp[0 * TY * ZM_TX + i] = lane<SPT, real>(h.xx, k);
-          hp[1 * TY * ZM_TX + i] = lane<SPT, real>(h.xy, k);
-          hp[2 * TY * ZM_TX + i] = lane<SPT, real>(h.xz, k);
-          hp[3 * TY * ZM_TX + i] = lane<SPT, real>(h.yy, k);
-          hp[4 * TY * ZM_TX + i] = lane<SPT, real>(h.yz, k);
-          hp[5 * TY * ZM_TX + i] = lane<SPT, real>(sg.xx, k);
-          hp[6 * TY * ZM_TX + i] = lane<SPT, real>(sg.xy, k);
-          hp[7 * TY * ZM_TX + i] = lane<SPT, real>(sg.xz, k);
-          hp[8 * TY * ZM_TX + i] = lane<SPT, real>(sg.yy, k);
-          hp[9 * TY * ZM_TX + i] = lane<SPT, real>(sg.yz, k);
+        if (r >= 1 && r <= TY && c >= 1 && c <= TX) {
+          const int i = (r - 1) * TX + (c - 1);
+          hp[0 * TY * TX + i] = lane<SPT, real>(h.xx, k);
+          hp[1 * TY * TX + i] = lane<SPT, real>(h.xy, k);
+          hp[2 * TY * TX + i] = lane<SPT, real>(h.xz, k);
+          hp[3 * TY * TX + i] = lane<SPT, real>(h.yy, k);
+          hp[4 * TY * TX + i] = lane<SPT, real>(h.yz, k);
+          hp[5 * TY * TX + i] = lane<SPT, real>(sg.xx, k);
+          hp[6 * TY * TX + i] = lane<SPT, real>(sg.xy, k);
+          hp[7 * TY * TX + i] = lane<SPT, real>(sg.xz, k);
+          hp[8 * TY * TX + i] = lane<SPT, real>(sg.yy, k);
+          hp[9 * TY * TX + i] = lane<SPT, real>(sg.yz, k);
         }
       }
     }
@@ -485,14 +489,14 @@ __device__ __forceinline__ void qside_body(const CUtensorMap* tmQ, const CUtenso
         dq[0] = dq_cur[0];
         dq[1] = dq_cur[1];
         dq[2] = dq_cur[2];
-        const int hi0 = ty * ZM_TX + tx;
-        h = ld5v<SPT>(hslot(z), TY * ZM_TX, hi0, hi0);
+        const int hi0 = ty * TX + tx;
+        h = ld5v<SPT>(hslot(z), TY * TX, hi0, hi0);
       } else {
         dq[0] = diff5(ldq(qc, qi0 + 1, qi1 + 1), ldq(qc, qi0 - 1, qi1 - 1));
         dq[1] = diff5(ldq(qc, qi0 + B::QW, qi1 + B::QW), ldq(qc, qi0 - B::QW, qi1 - B::QW));
         dq[2] = diff5(ldq(qp, qi0, qi1), ldq(qm, qi0, qi1));
-        const int hi0 = ty * ZM_TX + tx;
-        h = ld5v<SPT>(hslot(z), TY * ZM_TX, hi0, hi0 + TYH * ZM_TX);
+        const int hi0 = ty * TX + tx;
+        h = ld5v<SPT>(hslot(z), TY * TX, hi0, hi0 + TYH * TX);
       }
       // body force; tau = [xy, xz, yz] with tau_yx = -tau_xy etc.
       const real* tm = tslot(z - 1);
@@ -601,8 +605,8 @@ __device__ __forceinline__ void qside_body(const CUtensorMap* tmQ, const CUtenso
 #pragma unroll
         for (int a = 0; a < 3; ++a) bt[a] += vld<SPT>(bext, a * n + sb[0], a * n + sb[SPT - 1]);
       }
-      const int hs0 = ty * ZM_TX + tx;
-      const Sym5<V> sg = ld5v<SPT>(hslot(z) + 5 * TY * ZM_TX, TY * ZM_TX, hs0, hs0 + TYH * ZM_TX);
+      const int hs0 = ty * TX + tx;
+      const Sym5<V> sg = ld5v<SPT>(hslot(z) + 5 * TY * TX, TY * TX, hs0, hs0 + TYH * TX);
       const V it = mv.inv_tau;
       const V rho = V(1) + drho;
       const V jx = rho * u[0], jy = rho * u[1], jz = rho * u[2];
@@ -702,8 +706,16 @@ __global__ void __launch_bounds__(qside_threads<TY, 1>(), sizeof(real) == 4 ? 2 
       mq1 = &maps.q1[i];
       mu = &maps.u[i];
     }
-  qside_body<real, TY, 1, true, false>(mq, mq1, mu, G, m, it.bt, it.j, nullptr,
-                                       pq + pq0 + (long long)it.j * kZmPQ * G.cp, err, Sym5<real>{});
+  real* const pqr = pq + pq0 + (long long)it.j * kZmPQ * G.cp;
+  // a class of narrow tiles (kZmNarrowX wide, twice the rows: FP32 only)
+  if constexpr (sizeof(real) == 4) {
+    if (G.tx == kZmNarrowX) {
+      qside_body<real, 2 * TY, 1, true, false, kZmNarrowX>(mq, mq1, mu, G, m, it.bt, it.j, nullptr, pqr, err,
+                                                           Sym5<real>{});
+      return;
+    }
+  }
+  qside_body<real, TY, 1, true, false>(mq, mq1, mu, G, m, it.bt, it.j, nullptr, pqr, err, Sym5<real>{});
 }
 
 // The positions of a padded mirror (site x at column x + px, y at row y + h)
@@ -735,11 +747,11 @@ __device__ __forceinline__ void mirror_positions(int px, int h, int nx, int ny, 
 // ---------------------------------------------------------------------------
 // Kernel B: LB predictor-corrector and the Heun corrector
 // ---------------------------------------------------------------------------
-template <typename real, int TY>
+template <typename real, int TY, int TX = ZM_TX>
 struct LbqSmem {
   static constexpr int ROWS = TY + 2, SLOTS = 4;
-  static constexpr int GS = ROWS * kZmBoxXP * 4;   // one group of the P / Q* box: [row][34][4]
-  static constexpr int CSU = ROWS * StateBox::UW;  // sites of the u box
+  static constexpr int GS = ROWS * (TX + 2) * 4;          // one group of the P / Q* box: [row][TX + 2][4]
+  static constexpr int CSU = ROWS * StateBoxT<TX>::UW;  // sites of the u box
   // one slot: the four groups of the padded scratch, then the u box of the
   // rho u mirror's [rho-1 u_x u_y u_z] vectors
   static constexpr int OFF_U = align_elems(kZmPQG * GS, sizeof(real));
@@ -756,18 +768,18 @@ struct LbqSmem {
 // tmF, tmQ, tmQ1 (single lattices; null for batches): maps of f^n and of the
 // Q^n mirror, whose planes are prefetched into L2 one plane before the loads
 // read them
-template <typename real, int TY, int SPT, bool BATCH, bool WALLS>
+template <typename real, int TY, int SPT, bool BATCH, bool WALLS, int TX = ZM_TX>
 __device__ __forceinline__ void lbq_body(const CUtensorMap* tmPQ, const CUtensorMap* tmU3, const CUtensorMap* tmF,
                                          const CUtensorMap* tmQ, const CUtensorMap* tmQ1, const ZmGeom& G,
                                          const Model<real>& m, int bt, int rc, const real* __restrict__ f,
                                          const real* __restrict__ Qin, real* __restrict__ fnew,
                                          real* __restrict__ rhou_new, real* __restrict__ Qout,
                                          int* __restrict__ err, const Sym5<real> qw) {
-  using L = LbqSmem<real, TY>;
-  using B = StateBox;
+  using L = LbqSmem<real, TY, TX>;
+  using B = StateBoxT<TX>;
   using V = typename LaneT<real, SPT>::V;
   constexpr int TYH = TY / SPT;  // a thread takes rows ty + k * TYH, k < SPT
-  constexpr int AW = kZmBoxXP;
+  constexpr int AW = TX + 2;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   real* ring = reinterpret_cast<real*>(smem_raw);
   uint64_t* bars = reinterpret_cast<uint64_t*>(ring + L::SLOTS * L::SLOT);
@@ -775,11 +787,11 @@ __device__ __forceinline__ void lbq_body(const CUtensorMap* tmPQ, const CUtensor
 
   const int nx = G.nx, ny = G.ny, nz = G.nz;
   const int n = (int)G.n;  // (32-bit element offsets, as in k_qside)
-  const int x0 = (bt % G.tiles_x) * ZM_TX;
+  const int x0 = (bt % G.tiles_x) * TX;
   const int y0 = ((bt / G.tiles_x) % G.tiles_y) * TY;
   const int z0 = (bt / (G.tiles_x * G.tiles_y)) * G.zc;
   const int z1 = min(z0 + G.zc, nz);
-  const int tx = threadIdx.x % ZM_TX, ty = threadIdx.x / ZM_TX;
+  const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
   const int gx = x0 + tx;
   int gy[SPT];
   bool lane_ok[SPT];
@@ -807,7 +819,7 @@ __device__ __forceinline__ void lbq_body(const CUtensorMap* tmPQ, const CUtensor
 
   auto slot = [&](int p) { return ring + ((unsigned)(p - (z0 - 1)) % L::SLOTS) * L::SLOT; };
   // plane p: the padded P / Q* box (site (x, y) at padded (x + 1, y + 1), so the
-  // box starting at padded (x0, y0) covers x0-1 .. x0+32) and the u box of rho u
+  // box starting at padded (x0, y0) covers x0-1 .. x0+TX) and the u box of rho u
   auto issue = [&](int p) {
     const unsigned k = p - (z0 - 1);
     uint64_t* bar = &bars[k % L::SLOTS];
@@ -1170,6 +1182,14 @@ __global__ void __launch_bounds__(ZM_TX* TY, 2)
       mpq = &maps.pq[i];
       mu3 = &maps.u3[i];
     }
+  if constexpr (sizeof(real) == 4) {
+    if (G.tx == kZmNarrowX) {
+      lbq_body<real, 2 * TY, 1, true, false, kZmNarrowX>(mpq, mu3, nullptr, nullptr, nullptr, G, m, it.bt, it.j,
+                                                         f + NV * o, Qin + qo, fnew + NV * o, rhou_new + uo,
+                                                         Qout + qo, err, Sym5<real>{});
+      return;
+    }
+  }
   lbq_body<real, TY, 1, true, false>(mpq, mu3, nullptr, nullptr, nullptr, G, m, it.bt, it.j, f + NV * o, Qin + qo,
                                      fnew + NV * o, rhou_new + uo, Qout + qo, err, Sym5<real>{});
 }
@@ -1186,6 +1206,14 @@ template <typename real>
 int zm_tile_rows() {
   return zm_ty<real>();
 }
+
+// A narrow batch tile has the sites, threads and at most the shared memory of a full one
+static_assert(kZmNarrowX * 2 * zm_ty<float>() == ZM_TX * zm_ty<float>(), "narrow tile sites");
+static_assert(qside_threads<2 * zm_ty<float>(), 1, kZmNarrowX>() == qside_threads<zm_ty<float>(), 1>(),
+              "narrow k_qside threads");
+static_assert(QsideSmem<float, 2 * zm_ty<float>(), kZmNarrowX>::bytes <= QsideSmem<float, zm_ty<float>()>::bytes &&
+                  LbqSmem<float, 2 * zm_ty<float>(), kZmNarrowX>::bytes <= LbqSmem<float, zm_ty<float>()>::bytes,
+              "narrow tiles fit the full tiles' shared memory");
 
 // sites per thread the kernels are built for: FP32 one or two, FP64 one
 template <typename real>
@@ -1244,6 +1272,8 @@ ZmGeom zm_geom(int nx, int ny, int nz, int zc, int ty) {
   G.nz = nz;
   G.zc = zc;
   G.n = (long long)nx * ny * nz;
+  G.tx = ZM_TX;
+  G.ty = ty;
   G.tiles_x = (nx + ZM_TX - 1) / ZM_TX;
   G.tiles_y = (ny + ty - 1) / ty;
   G.tiles_z = (nz + zc - 1) / zc;

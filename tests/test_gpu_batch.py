@@ -184,11 +184,14 @@ def test_batch_path_rules(lcbp):
         b.close()
 
 
-@pytest.mark.parametrize("dims_list", [[(8, 8, 8)], [(8, 4, 3), (12, 4, 5), (4, 8, 9), (16, 12, 2)]])
+@pytest.mark.parametrize("dims_list", [[(8, 8, 8)], [(8, 4, 3), (12, 4, 5), (4, 8, 9), (16, 12, 2)],
+                                       [(48, 20, 5), (16, 36, 3), (40, 12, 4)]])
 def test_fast_batch_edge_counts_bitwise_f32(lcbp, dims_list):
-    """One replica, and exactly four classes (one replica each, with nz of 2,
-    3, 5 and 9): the fast batch equals the lattices stepped alone on the fast
-    kernels, bit for bit."""
+    """One replica, exactly four classes (one replica each, with nz of 2, 3, 5
+    and 9), and classes of narrow tiles (16 x 16 sites, taken where a 32-wide
+    tile would be at most half full) with ragged rows and columns: the fast
+    batch equals the lattices stepped alone on the fast kernels (32 x 8
+    tiles), bit for bit."""
     params = [replica_params(0.5 + 0.4 * r, -0.3 + 0.2 * r) for r in range(len(dims_list))]
     b = lcbp.Batch(dims_list, params, dtype="f32").set_path(lcbp.PATH_FAST1)
     for r in range(len(dims_list)):
