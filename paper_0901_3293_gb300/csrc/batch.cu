@@ -62,7 +62,8 @@ struct lcbp_batch {
   long long step;
   // fast path
   std::vector<int> order;  // replica indices class by class, in storage order
-  ZmBatch zb;              // classes (zc and CTA ranges filled when tuned)
+  ZmBatch zb;              // classes (zc and CTA ranges filled when tuned) for k_lbq_batch
+  ZmBatch zbq;             // the same classes with k_qside_batch's planes per CTA
   ZmBatchMaps maps[2];     // tensor maps with rho u buffer 0 / 1
   bool fast_ok;            // every class fits the fast kernels
   bool fast_pick;          // AUTO: the fast kernels timed faster than the generic ones
@@ -146,11 +147,11 @@ bool build_maps(lcbp_batch* b) {
   return true;
 }
 
-// geometry and CTA ranges of the classes for zc[k] planes per CTA in class k
-void set_zc(lcbp_batch* b, const int* zc) {
+// geometry and CTA ranges of the classes of zb for zc[k] planes per CTA in class k
+void fill_zc(ZmBatch& zb, const int* zc) {
   int cta = 0;
-  for (int k = 0; k < b->zb.nclass; ++k) {
-    ZmClass& c = b->zb.c[k];
+  for (int k = 0; k < zb.nclass; ++k) {
+    ZmClass& c = zb.c[k];
     c.G.zc = std::min(zc[k], c.G.nz);
     c.G.tiles_x = (c.G.nx + c.G.tx - 1) / c.G.tx;
     c.G.tiles_y = (c.G.ny + c.G.ty - 1) / c.G.ty;
@@ -167,13 +168,21 @@ void set_zc(lcbp_batch* b, const int* zc) {
     c.cta0 = cta;
     cta += c.ctas_per_rep * c.count;
   }
-  b->zb.total_ctas = cta;
+  zb.total_ctas = cta;
+}
+
+// planes per CTA of each class for k_lbq_batch (zc) and k_qside_batch (zc_q)
+void set_zc(lcbp_batch* b, const int* zc, const int* zc_q) {
+  fill_zc(b->zb, zc);
+  b->zbq = b->zb;
+  fill_zc(b->zbq, zc_q);
   b->zc = zc[0];
 }
 
 ZmBatchArgs zm_args(lcbp_batch* b) {
   ZmBatchArgs a{};
   a.B = b->zb;
+  a.Bq = b->zbq;
   a.maps = &b->maps[b->cur];
   a.reps = b->d_rep;
   a.order = b->d_order;
@@ -342,62 +351,79 @@ int resident_ctas(lcbp_batch* b) {
   return std::max(1, sms * per_sm);
 }
 
-// planes per CTA of the fast path, per class: one value for every class first,
-// then each class's own value with the others held (one pass); every
-// candidate is timed as one step of the whole batch (best of 3)
+// planes per CTA of the fast path, per class and per kernel: one value for
+// every class first, then each class's own value with the others held (one
+// pass); every candidate is one step of the whole batch (best of 3) with an
+// event between the kernels, and each kernel keeps its own best values (the
+// kernels run one after the other, so their times add)
 int tune_fast(lcbp_batch* b, float* best_ms) {
-  cudaEvent_t e0, e1;
-  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return fail(LCBP_ECUDA, "events");
+  cudaEvent_t ev[3];
+  for (auto& e : ev)
+    if (cudaEventCreate(&e) != cudaSuccess) return fail(LCBP_ECUDA, "events");
   const int nc = b->zb.nclass;
   const int cand[] = {4, 6, 8, 10, 12, 16, 24, 32, 48, 64};
   cudaError_t err = cudaSuccess;
-  auto time_zc = [&](const int* zc) {
-    set_zc(b, zc);
+  // time of k_qside_batch with zc_q and of k_lbq_batch with zc (best of 3 each)
+  auto time_zc = [&](const int* zc, const int* zc_q, float* tq, float* tl) {
+    set_zc(b, zc, zc_q);
     ZmBatchArgs a = zm_args(b);
     a.qout = b->qm_tune;  // a mirror the state does not use: the state is left untouched
-    float t = 1e30f;
+    a.events = ev;
+    *tq = *tl = 1e30f;
     for (int rep = 0; rep < 3 && err == cudaSuccess; ++rep) {
-      cudaEventRecord(e0, b->stream);
       err = launch_zm(b, a);
-      cudaEventRecord(e1, b->stream);
-      if (err == cudaSuccess) err = cudaEventSynchronize(e1);
-      float ms = 0;
-      if (err == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
-      t = std::min(t, ms);
+      if (err == cudaSuccess) err = cudaEventSynchronize(ev[2]);
+      float m0 = 0, m1 = 0;
+      if (err == cudaSuccess) {
+        cudaEventElapsedTime(&m0, ev[0], ev[1]);
+        cudaEventElapsedTime(&m1, ev[1], ev[2]);
+      }
+      *tq = std::min(*tq, m0);
+      *tl = std::min(*tl, m1);
     }
-    return t;
   };
-  int zc[kZmMaxClasses], best_zc[kZmMaxClasses];
-  float best = 1e30f;
+  int zl[kZmMaxClasses], zq[kZmMaxClasses], best_l[kZmMaxClasses], best_q[kZmMaxClasses];
+  float bl = 1e30f, bq = 1e30f;
   int max_nz = 1;
   for (int k = 0; k < nc; ++k) max_nz = std::max(max_nz, b->zb.c[k].G.nz);
   for (int v : cand) {
     if (v > max_nz && v != 4) break;
-    for (int k = 0; k < nc; ++k) zc[k] = v;
-    const float t = time_zc(zc);
-    if (t < best) {
-      best = t;
-      std::copy(zc, zc + nc, best_zc);
+    for (int k = 0; k < nc; ++k) zl[k] = zq[k] = v;
+    float tq, tl;
+    time_zc(zl, zq, &tq, &tl);
+    if (tl < bl) {
+      bl = tl;
+      std::copy(zl, zl + nc, best_l);
+    }
+    if (tq < bq) {
+      bq = tq;
+      std::copy(zq, zq + nc, best_q);
     }
   }
   for (int k = 0; k < nc && nc > 1 && err == cudaSuccess; ++k) {
-    std::copy(best_zc, best_zc + nc, zc);
+    std::copy(best_l, best_l + nc, zl);
+    std::copy(best_q, best_q + nc, zq);
+    const int hold_l = best_l[k], hold_q = best_q[k];
     for (int v : cand) {
       if (v > b->zb.c[k].G.nz && v != 4) break;
-      if (v == best_zc[k]) continue;
-      zc[k] = v;
-      const float t = time_zc(zc);
-      if (t < best) {
-        best = t;
-        best_zc[k] = v;
+      if (v == hold_l && v == hold_q) continue;
+      zl[k] = zq[k] = v;
+      float tq, tl;
+      time_zc(zl, zq, &tq, &tl);
+      if (tl < bl) {
+        bl = tl;
+        best_l[k] = v;
+      }
+      if (tq < bq) {
+        bq = tq;
+        best_q[k] = v;
       }
     }
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
+  for (auto& e : ev) cudaEventDestroy(e);
   if (err != cudaSuccess) return cuda_fail(err, "batch planes-per-CTA tuning");
-  set_zc(b, best_zc);
-  *best_ms = best;
+  set_zc(b, best_l, best_q);
+  *best_ms = bl + bq;
   return check_error_flag(b);
 }
 

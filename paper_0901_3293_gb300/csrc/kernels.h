@@ -214,6 +214,7 @@ inline long long zm_pq_elems(int nx, int ny, int nz) {
   return (long long)kZmPQ * (nx + kZmPadX) * (ny + 2) * nz;
 }
 
+// box widths of 32-wide tiles (single lattices; batch classes derive theirs from the tile width)
 constexpr int kZmBoxX = 40;   // sites per TMA box row of the flat fields and of the Q mirror (x0 - 4 ..)
 constexpr int kZmBoxXP = 34;  // sites per TMA box row of the padded scratch (x0 - 1 .. x0 + 32)
 constexpr int kZmBoxXU = 34;  // sites per TMA box row of the rho u mirror (x0 - 1 .. x0 + 32)
@@ -238,16 +239,17 @@ struct ZmBatch {
   int total_ctas;
   ZmClass c[kZmMaxClasses];
 };
-// per class: Q (box rows TY + 4), rho u (4 components), the padded scratch
-// (15), u (rho u components 1..3); box rows TY + 2 but for Q; 5-D
 // Per class, with the replica as the outermost coordinate: the Q mirrors'
 // [xx xy xz yy] vectors (q) and yz arrays (q1), the rho u mirrors (u; u3 the
-// same for k_lbq) and the padded scratch (pq)
+// same for k_lbq) and the padded scratch (pq, 5-D).  Boxes fit the class's
+// tile of tx x ty sites: Q tx + 8 sites wide and ty + 4 rows, the others
+// tx + 2 wide and ty + 2 rows.
 struct ZmBatchMaps {
   CUtensorMap q[kZmMaxClasses], q1[kZmMaxClasses], u[kZmMaxClasses], pq[kZmMaxClasses], u3[kZmMaxClasses];
 };
 struct ZmBatchArgs {
-  ZmBatch B;
+  ZmBatch B;   // classes and CTA ranges of k_lbq_batch
+  ZmBatch Bq;  // the same for k_qside_batch (its own planes per CTA)
   const ZmBatchMaps* maps;  // host copy (rho u maps of the current buffer)
   const void* reps;         // device Replica<real>[R]: base offsets and models
   const int* order;         // device: replica indices, class by class in storage order
@@ -255,6 +257,7 @@ struct ZmBatchArgs {
   void *f, *fnew;           // the flat populations
   void *rhou, *rhou_new;    // rho u mirrors of all classes (current, next)
   int* err;
+  cudaEvent_t* events;      // optional: recorded before, between and after the two kernels
 };
 template <typename real>
 cudaError_t zm_batch_prepare();

@@ -1336,13 +1336,15 @@ cudaError_t zm_batch_prepare() {
 template <typename real>
 cudaError_t launch_step_zm_batch(const ZmBatchArgs& a, cudaStream_t s) {
   constexpr int TY = zm_ty<real>();
-  const int grid = a.B.total_ctas;
   const auto* reps = static_cast<const Replica<real>*>(a.reps);
-  k_qside_batch<real, TY><<<grid, qside_threads<TY, 1>(), QsideSmem<real, TY>::bytes, s>>>(
-      *a.maps, a.B, reps, a.order, static_cast<real*>(a.pq), a.err);
-  k_lbq_batch<real, TY><<<grid, ZM_TX * TY, LbqSmem<real, TY>::bytes, s>>>(
+  if (a.events) cudaEventRecord(a.events[0], s);
+  k_qside_batch<real, TY><<<a.Bq.total_ctas, qside_threads<TY, 1>(), QsideSmem<real, TY>::bytes, s>>>(
+      *a.maps, a.Bq, reps, a.order, static_cast<real*>(a.pq), a.err);
+  if (a.events) cudaEventRecord(a.events[1], s);
+  k_lbq_batch<real, TY><<<a.B.total_ctas, ZM_TX * TY, LbqSmem<real, TY>::bytes, s>>>(
       *a.maps, a.B, reps, a.order, static_cast<const real*>(a.f), static_cast<const real*>(a.q),
       static_cast<real*>(a.fnew), static_cast<real*>(a.rhou_new), static_cast<real*>(a.qout ? a.qout : a.q), a.err);
+  if (a.events) cudaEventRecord(a.events[2], s);
   return cudaGetLastError();
 }
 
