@@ -137,6 +137,16 @@ bool build_maps(lcbp_batch* b) {
               mirror(&b->maps[1].u[k], b->um[1], c.um0, 4 * nxm, nyu, 4 * cu, 4 * (tx + 2), ty + 2) &&
               encode_tiled(&b->maps[0].pq[k], static_cast<char*>(b->pq) + (size_t)c.pq0 * b->es, 5, pdims, pstr,
                            pbox, b->dtype);
+    // the flat populations of the class's replicas (blocks of NV * round64(n) elements) for L2 prefetches
+    const cuuint64_t rstride = (cuuint64_t)NV * ((c.G.n + 63) / 64 * 64);
+    const cuuint64_t fdims[5] = {nx, ny, nz, (cuuint64_t)NV, (cuuint64_t)c.count};
+    const cuuint64_t fstr[4] = {nx * es, nx * ny * es, nx * ny * nz * es, rstride * es};
+    const cuuint32_t fbox[5] = {(cuuint32_t)(tx + 8), (cuuint32_t)(ty + 2), 1, (cuuint32_t)NV, 1};
+    for (int j = 0; j < 2 && ok; ++j) {
+      const long long o = b->base[b->order[c.rep0]];  // the class's first replica
+      ok = encode_tiled(&b->maps[j].f[k], static_cast<char*>(b->f[j]) + (size_t)NV * o * es, 5, fdims, fstr, fbox,
+                        b->dtype);
+    }
     if (!ok) return false;
     b->maps[0].u3[k] = b->maps[0].u[k];
     b->maps[1].u3[k] = b->maps[1].u[k];

@@ -241,11 +241,13 @@ struct ZmBatch {
 };
 // Per class, with the replica as the outermost coordinate: the Q mirrors'
 // [xx xy xz yy] vectors (q) and yz arrays (q1), the rho u mirrors (u; u3 the
-// same for k_lbq) and the padded scratch (pq, 5-D).  Boxes fit the class's
-// tile of tx x ty sites: Q tx + 8 sites wide and ty + 4 rows, the others
-// tx + 2 wide and ty + 2 rows.
+// same for k_lbq), the padded scratch (pq, 5-D) and the flat populations
+// (f, 5-D (x, y, z, i, replica); L2 prefetches only).  Boxes fit the class's
+// tile of tx x ty sites: Q and f tx + 8 sites wide (from x0 - 4), Q ty + 4
+// rows, the others tx + 2 wide and ty + 2 rows.
 struct ZmBatchMaps {
-  CUtensorMap q[kZmMaxClasses], q1[kZmMaxClasses], u[kZmMaxClasses], pq[kZmMaxClasses], u3[kZmMaxClasses];
+  CUtensorMap q[kZmMaxClasses], q1[kZmMaxClasses], u[kZmMaxClasses], pq[kZmMaxClasses], u3[kZmMaxClasses],
+      f[kZmMaxClasses];
 };
 struct ZmBatchArgs {
   ZmBatch B;   // classes and CTA ranges of k_lbq_batch

@@ -765,9 +765,9 @@ struct LbqSmem {
 // that would arrive from beyond a wall is the reflected one of the same site
 // (half-way bounce-back); the staged Q* of a ghost plane is the anchored qw and
 // its velocity is -u of the adjacent plane.
-// tmF, tmQ, tmQ1 (single lattices; null for batches): maps of f^n and of the
-// Q^n mirror, whose planes are prefetched into L2 one plane before the loads
-// read them
+// tmF, tmQ, tmQ1: maps of f^n and of the Q^n mirror (for a batch, the
+// class's, with the replica outermost), whose planes are prefetched into L2
+// one plane before the loads read them
 template <typename real, int TY, int SPT, bool BATCH, bool WALLS, int TX = ZM_TX>
 __device__ __forceinline__ void lbq_body(const CUtensorMap* tmPQ, const CUtensorMap* tmU3, const CUtensorMap* tmF,
                                          const CUtensorMap* tmQ, const CUtensorMap* tmQ1, const ZmGeom& G,
@@ -809,11 +809,9 @@ __device__ __forceinline__ void lbq_body(const CUtensorMap* tmPQ, const CUtensor
     mbar_init_fence();
     tma_prefetch_desc(tmPQ);
     tma_prefetch_desc(tmU3);
-    if constexpr (!BATCH) {
-      tma_prefetch_desc(tmF);
-      tma_prefetch_desc(tmQ);
-      tma_prefetch_desc(tmQ1);
-    }
+    tma_prefetch_desc(tmF);
+    tma_prefetch_desc(tmQ);
+    tma_prefetch_desc(tmQ1);
   }
   __syncthreads();
 
@@ -829,14 +827,17 @@ __device__ __forceinline__ void lbq_body(const CUtensorMap* tmPQ, const CUtensor
     // the scratch as (4 X, Y, group, z): x coordinate in elements of 4 per site
     if constexpr (BATCH) tma_load_5d(sl, tmPQ, 4 * x0, y0, 0, zz, rc, bar);
     else tma_load_4d(sl, tmPQ, 4 * x0, y0, 0, zz, bar);
+    // the populations of plane p (pulled from plane p-1 on) and Q^n of plane
+    // p-1, into L2 a plane ahead of their plain loads
+    const int X = x0 - B::QX + B::QPX, Y = y0 - 2 + B::QPY;
     if constexpr (BATCH) {
       tma_load_4d(sl + L::OFF_U, tmU3, 4 * (x0 - B::UX + B::UPX), y0 - 1 + B::UPY, zz, rc, bar);
+      tma_prefetch_l2_5d(tmF, x0 - ZM_XOFF, y0 - 1, zz, 0, rc);
+      tma_prefetch_l2_4d(tmQ, 4 * X, Y, wrap(p - 1, nz), rc);
+      tma_prefetch_l2_4d(tmQ1, X, Y, wrap(p - 1, nz), rc);
     } else {
       tma_load_3d(sl + L::OFF_U, tmU3, 4 * (x0 - B::UX + B::UPX), y0 - 1 + B::UPY, zz, bar);
-      // the populations of plane p (pulled from plane p-1 on) and Q^n of plane
-      // p-1, into L2 a plane ahead of their plain loads
       tma_prefetch_l2_4d(tmF, x0 - ZM_XOFF, y0 - 1, zz, 0);
-      const int X = x0 - B::QX + B::QPX, Y = y0 - 2 + B::QPY;
       tma_prefetch_l2_3d(tmQ, 4 * X, Y, wrap(p - 1, nz));
       tma_prefetch_l2_3d(tmQ1, X, Y, wrap(p - 1, nz));
     }
@@ -1175,22 +1176,25 @@ __global__ void __launch_bounds__(ZM_TX* TY, 2)
   const long long o = reps[r].base;  // the flat populations of the replica
   const long long qo = qm0 + (long long)it.j * 5 * G.cq, uo = um0 + (long long)it.j * 4 * G.cu;  // its mirrors
   const Model<real> m = reps[r].m;
-  const CUtensorMap *mpq = &maps.pq[0], *mu3 = &maps.u3[0];
+  const CUtensorMap *mpq = &maps.pq[0], *mu3 = &maps.u3[0], *mf = &maps.f[0], *mq = &maps.q[0], *mq1 = &maps.q1[0];
 #pragma unroll
   for (int i = 1; i < kZmMaxClasses; ++i)
     if (i == it.k) {
       mpq = &maps.pq[i];
       mu3 = &maps.u3[i];
+      mf = &maps.f[i];
+      mq = &maps.q[i];
+      mq1 = &maps.q1[i];
     }
   if constexpr (sizeof(real) == 4) {
     if (G.tx == kZmNarrowX) {
-      lbq_body<real, 2 * TY, 1, true, false, kZmNarrowX>(mpq, mu3, nullptr, nullptr, nullptr, G, m, it.bt, it.j,
+      lbq_body<real, 2 * TY, 1, true, false, kZmNarrowX>(mpq, mu3, mf, mq, mq1, G, m, it.bt, it.j,
                                                          f + NV * o, Qin + qo, fnew + NV * o, rhou_new + uo,
                                                          Qout + qo, err, Sym5<real>{});
       return;
     }
   }
-  lbq_body<real, TY, 1, true, false>(mpq, mu3, nullptr, nullptr, nullptr, G, m, it.bt, it.j, f + NV * o, Qin + qo,
+  lbq_body<real, TY, 1, true, false>(mpq, mu3, mf, mq, mq1, G, m, it.bt, it.j, f + NV * o, Qin + qo,
                                      fnew + NV * o, rhou_new + uo, Qout + qo, err, Sym5<real>{});
 }
 
