@@ -292,12 +292,13 @@ __device__ __forceinline__ bool top_eigenvalue_below(double xx, double xy, doubl
 // FP32 decide unless one lies within 1e-4 m^k of zero (m: the largest entry of
 // t I - Q in size, k: the minor's order), far above their rounding error (a
 // few ulp of m^k); such sites are decided in FP64 as above.
+// tf: t rounded to FP32 (by the caller, once)
 template <typename C>
-__device__ __forceinline__ bool top_eigenvalue_below(const Sym5<C>& q, double t) {
+__device__ __forceinline__ bool top_eigenvalue_below(const Sym5<C>& q, double t, float tf) {
   if constexpr (sizeof(C) == 8) {
     return top_eigenvalue_below(q.xx, q.xy, q.xz, q.yy, q.yz, t);
   } else {
-    const float tf = (float)t, zz = -q.xx - q.yy;
+    const float zz = -q.xx - q.yy;
     const float b00 = tf - q.xx, b11 = tf - q.yy, b22 = tf - zz;
     const float m = fmaxf(fmaxf(fmaxf(fabsf(b00), fabsf(b11)), fmaxf(fabsf(b22), fabsf(q.xy))),
                           fmaxf(fabsf(q.xz), fabsf(q.yz)));
@@ -347,10 +348,29 @@ __device__ __forceinline__ C bond_energy(const Sym5<C>& a, const Sym5<C>& b, int
   return C(0.5) * K * dist2(a, b) + K * q0 * (eps_contract(A, B, g) - eps_contract(B, A, g));
 }
 
-// sums per block: [F_h, mass, Px, Py, Pz, defects, nonfinite, 0]
-template <typename real>
-__global__ void __launch_bounds__(256) k_diag(DiagGeom g, const real* __restrict__ Q, const real* __restrict__ f,
-                                              int with_f, double threshold, double* __restrict__ partials) {
+// Q:C with C_ab = eps_agd d_g Q_db for the raw differences d_g = Q(r + e_g) -
+// Q(r - e_g) (twice the central derivatives), contracted in closed form on the
+// five stored components:
+//   C_xb = d_y Q_zb - d_z Q_yb,  C_yb = d_z Q_xb - d_x Q_zb,  C_zb = d_x Q_yb - d_y Q_xb
+template <typename C>
+__device__ __forceinline__ C chiral_contraction(const Sym5<C>& q, const Sym5<C>& dx, const Sym5<C>& dy,
+                                                const Sym5<C>& dz) {
+  const C qzz = q.zz();
+  const C c_xx = dy.xz - dz.xy, c_xy = dy.yz - dz.yy, c_xz = dy.zz() - dz.yz;
+  const C c_yx = dz.xx - dx.xz, c_yy = dz.xy - dx.yz, c_yz = dz.xz - dx.zz();
+  const C c_zx = dx.xy - dy.xx, c_zy = dx.yy - dy.xy, c_zz = dx.yz - dy.xz;
+  return q.xx * c_xx + q.xy * (c_xy + c_yx) + q.xz * (c_xz + c_zx) + q.yy * c_yy + q.yz * (c_yz + c_zy) +
+         qzz * c_zz;
+}
+
+// sums per block: [F_h, mass, Px, Py, Pz, defects, nonfinite, 0].  WALLS: F_h
+// in bond form with the anchored ghost planes (a build of its own, so that the
+// periodic build keeps few registers and many warps per SM).
+template <typename real, bool WALLS>
+// (FP32: four CTAs per SM, 64 registers)
+__global__ void __launch_bounds__(256, sizeof(real) == 4 ? 4 : 2)
+    k_diag(DiagGeom g, const real* __restrict__ Q, const real* __restrict__ f, int with_f, double threshold,
+           double* __restrict__ partials) {
   using C = real;
   // F_h, then sum(rho - 1), P: FP64; the sites, defects and non-finite sites counted
   double aF = 0.0, aR = 0.0, aJx = 0.0, aJy = 0.0, aJz = 0.0;
@@ -358,11 +378,13 @@ __global__ void __launch_bounds__(256) k_diag(DiagGeom g, const real* __restrict
   const real* qp = Q + 5 * g.base;
   const real* fp = f ? f + 15 * g.base : nullptr;
   const long long n = g.n;
-  const C A0 = (C)g.A0, gam = (C)g.gamma, K = (C)g.K, q0 = (C)g.q0, c_div = (C)g.c_div;
+  const C A0 = (C)g.A0, gam = (C)g.gamma, K = (C)g.K, q0 = (C)g.q0;
   const C a2 = C(0.5) * A0 * (C(1) - gam / C(3)), a3 = A0 * gam, a4 = C(0.25) * A0 * gam;
-  const C kq0 = C(2) * K * q0, kq0sq = C(2) * K * q0 * q0;
-  const Sym5<C> qw = {(C)g.qw[0], (C)g.qw[1], (C)g.qw[2], (C)g.qw[3], (C)g.qw[4]};
-  const bool small = n < (1ll << 31);
+  // the chiral and divergence terms take raw differences: factors 1/2 and 1/4 folded in
+  const C kq0h = K * q0, kq0sq = C(2) * K * q0 * q0, cdiv4 = C(0.25) * (C)g.c_div;
+  // decided once: FP64 arithmetic is scarce, so the loop keeps only its FP64 sums
+  const bool has_div = g.c_div != 0.0, small = g.n < (1ll << 31);
+  const float tf = (float)threshold;
   for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < n; s += (long long)gridDim.x * blockDim.x) {
     int x, y, z;
     if (small) {  // 32-bit index arithmetic
@@ -381,8 +403,7 @@ __global__ void __launch_bounds__(256) k_diag(DiagGeom g, const real* __restrict
     const int zp = z + 1 == g.nz ? 0 : z + 1, zm = z == 0 ? g.nz - 1 : z - 1;
     auto at = [&](int xx, int yy, int zz) { return ((long long)zz * g.ny + yy) * g.nx + xx; };
     const Sym5<C> qc = load5(qp, n, s);
-    const Sym5<C> qn[3] = {load5(qp, n, at(xp, y, z)), load5(qp, n, at(x, yp, z)), load5(qp, n, at(x, y, zp))};
-    const Sym5<C> qs[3] = {load5(qp, n, at(xm, y, z)), load5(qp, n, at(x, ym, z)), load5(qp, n, at(x, y, zm))};
+    const Sym5<C> qxp = load5(qp, n, at(xp, y, z)), qyp = load5(qp, n, at(x, yp, z)), qzp = load5(qp, n, at(x, y, zp));
     const bool finite = isfinite(qc.xx) && isfinite(qc.xy) && isfinite(qc.xz) && isfinite(qc.yy) && isfinite(qc.yz);
     const C qzz = -qc.xx - qc.yy;
     const C tr2 = qc.xx * qc.xx + qc.yy * qc.yy + qzz * qzz + C(2) * (qc.xy * qc.xy + qc.xz * qc.xz + qc.yz * qc.yz);
@@ -391,44 +412,30 @@ __global__ void __launch_bounds__(256) k_diag(DiagGeom g, const real* __restrict
                   qc.xz * (qc.xy * qc.yz - qc.yy * qc.xz);
     const C bulk = a2 * tr2 - a3 * det + a4 * tr2 * tr2;
     C Fs;
-    if (!g.walls) {
-      const C grad2 = dist2(qc, qn[0]) + dist2(qc, qn[1]) + dist2(qc, qn[2]);
-      // Q_ab C_ab with C_ab = eps_agd D0_g Q_db
-      C Qc[3][3], P[3][3][3], M[3][3][3];
-      full3(qc, Qc);
-      for (int d = 0; d < 3; ++d) {
-        full3(qn[d], P[d]);
-        full3(qs[d], M[d]);
-      }
-      C chiral = C(0);
-      for (int b = 0; b < 3; ++b) {
-        const C Cx = C(0.5) * (P[1][2][b] - M[1][2][b]) - C(0.5) * (P[2][1][b] - M[2][1][b]);
-        const C Cy = C(0.5) * (P[2][0][b] - M[2][0][b]) - C(0.5) * (P[0][2][b] - M[0][2][b]);
-        const C Cz = C(0.5) * (P[0][1][b] - M[0][1][b]) - C(0.5) * (P[1][0][b] - M[1][0][b]);
-        chiral += Qc[0][b] * Cx + Qc[1][b] * Cy + Qc[2][b] * Cz;
-      }
-      Fs = bulk + C(0.5) * K * grad2 + kq0 * chiral + kq0sq * tr2;
-      if (g.c_div != 0.0) {
-        // div_a = sum_b D0_b Q_ab from the face neighbours
-        C d2 = C(0);
-        for (int a = 0; a < 3; ++a) {
-          C dv = C(0);
-          for (int b = 0; b < 3; ++b) dv += C(0.5) * (P[b][a][b] - M[b][a][b]);
-          d2 += dv * dv;
-        }
-        Fs -= c_div * d2;
+    if constexpr (!WALLS) {
+      const C grad2 = dist2(qc, qxp) + dist2(qc, qyp) + dist2(qc, qzp);
+      const Sym5<C> dx = diff5(qxp, load5(qp, n, at(xm, y, z)));
+      const Sym5<C> dy = diff5(qyp, load5(qp, n, at(x, ym, z)));
+      const Sym5<C> dz = diff5(qzp, load5(qp, n, at(x, y, zm)));
+      // 2 K q0 Q:C with C from central derivatives = K q0 (Q:C of the raw differences)
+      Fs = bulk + C(0.5) * K * grad2 + kq0h * chiral_contraction(qc, dx, dy, dz) + kq0sq * tr2;
+      if (has_div) {
+        // div_a = sum_b D0_b Q_ab; raw differences carry twice it
+        const C vx = dx.xx + dy.xy + dz.xz, vy = dx.xy + dy.yy + dz.yz, vz = dx.xz + dy.yz + dz.zz();
+        Fs -= cdiv4 * (vx * vx + vy * vy + vz * vz);
       }
     } else {
       // bond form: this site's three forward bonds (the z bond of the top plane
       // ends on the anchored ghost) and, on the bottom plane, the bond from the
       // ghost below; every bond touching the lattice is counted once
-      C Fb = bond_energy(qc, qn[0], 0, K, q0) + bond_energy(qc, qn[1], 1, K, q0);
-      Fb += bond_energy(qc, z == g.nz - 1 ? qw : qn[2], 2, K, q0);
+      const Sym5<C> qw = {(C)g.qw[0], (C)g.qw[1], (C)g.qw[2], (C)g.qw[3], (C)g.qw[4]};
+      C Fb = bond_energy(qc, qxp, 0, K, q0) + bond_energy(qc, qyp, 1, K, q0);
+      Fb += bond_energy(qc, z == g.nz - 1 ? qw : qzp, 2, K, q0);
       if (z == 0) Fb += bond_energy(qw, qc, 2, K, q0);
       Fs = bulk + Fb + kq0sq * tr2;
     }
     aF += (double)Fs;
-    defects += finite && top_eigenvalue_below(qc, threshold) ? 1 : 0;
+    defects += finite && top_eigenvalue_below(qc, threshold, tf) ? 1 : 0;
     ++sites;
     bool ffin = true;
     if (with_f) {
@@ -451,19 +458,25 @@ __global__ void __launch_bounds__(256) k_diag(DiagGeom g, const real* __restrict
     }
     bad += finite && ffin ? 0 : 1;
   }
-  // mass = sites + sum(rho - 1); block reduction in a fixed order
-  const double acc[7] = {aF, with_f ? aR + (double)sites : 0.0, aJx, aJy, aJz, (double)defects, (double)bad};
-  __shared__ double red[8][256];
-  for (int k = 0; k < 7; ++k) red[k][threadIdx.x] = acc[k];
+  // mass = sites + sum(rho - 1).  Block reduction in a fixed order: a shuffle
+  // tree within each warp, then warp 0 adds the eight warps' sums in order.
+  double acc[7] = {aF, with_f ? aR + (double)sites : 0.0, aJx, aJy, aJz, (double)defects, (double)bad};
+#pragma unroll
+  for (int k = 0; k < 7; ++k)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_down_sync(0xffffffffu, acc[k], o);
+  __shared__ double red[8][8];
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < 7; ++k) red[warp][k] = acc[k];
   __syncthreads();
-  for (int stride = blockDim.x / 2; stride > 0; stride >>= 1) {
-    if ((int)threadIdx.x < stride)
-      for (int k = 0; k < 7; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + stride];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    for (int k = 0; k < 7; ++k) partials[blockIdx.x * 8 + k] = red[k][0];
-    partials[blockIdx.x * 8 + 7] = 0.0;
+  if (threadIdx.x < 8) {
+    const int k = threadIdx.x;
+    double t = 0.0;
+    if (k < 7)
+      for (int w = 0; w < (int)blockDim.x / 32; ++w) t += red[w][k];
+    partials[blockIdx.x * 8 + k] = t;
   }
 }
 
@@ -503,8 +516,13 @@ constexpr int kDiagBlocks = 512;
 template <typename real>
 cudaError_t launch_diag_one(const DiagGeom& g, const void* q, const void* f, int with_f, double threshold,
                             double* partials, double* out, cudaStream_t s) {
-  k_diag<real><<<kDiagBlocks, 256, 0, s>>>(g, static_cast<const real*>(q), static_cast<const real*>(f), with_f,
-                                           threshold, partials);
+  static_assert(kDiagBlocks * 8 == kDiagPartials, "the partials buffer holds 8 values per block");
+  if (g.walls)
+    k_diag<real, true><<<kDiagBlocks, 256, 0, s>>>(g, static_cast<const real*>(q), static_cast<const real*>(f),
+                                                    with_f, threshold, partials);
+  else
+    k_diag<real, false><<<kDiagBlocks, 256, 0, s>>>(g, static_cast<const real*>(q), static_cast<const real*>(f),
+                                                     with_f, threshold, partials);
   k_diag_final<<<1, 256, 0, s>>>(partials, kDiagBlocks, out);
   return cudaGetLastError();
 }
