@@ -416,7 +416,9 @@ LCBP_API int lcbp_restore(lcbp_lattice *h, const void *src);
  *   fast (open when flow is on, coupling is Jacobi, every class has
  *     nx % 4 == 0 and there are at most 4 classes): the two z-marching TMA
  *     kernels of the single-lattice fast path, each field of a class read as
- *     one 5-D tensor; the planes per CTA are picked by timing candidates;
+ *     one 5-D tensor; each kernel's planes per CTA are picked per class by
+ *     timing candidates; FP32 classes whose last 32-column tile would be at
+ *     most half full (nx % 32 in 1..16) run tiles of 16 x 16 sites;
  *   generic: persistent CTAs walking one tile work-list that spans all
  *     replicas; the tile shape is picked by timing candidate shapes.
  * LCBP_PATH_AUTO (default) tunes both where the fast set is open and runs
@@ -473,9 +475,10 @@ LCBP_API int lcbp_batch_defect_fraction(lcbp_batch *b, int r, double threshold, 
  * graph; the next lcbp_batch_step retunes.  Errors: LCBP_EINVAL (other paths).
  */
 LCBP_API int lcbp_batch_set_path(lcbp_batch *b, int path);
-/* *fast = 1 if steps run the fast kernels; *planes_per_cta = their tuned
- * z-chunk (tuned per class; the first class's value), 0 before the first step
- * or on the generic path.  Either may be NULL. */
+/* *fast = 1 if steps run the fast kernels; *planes_per_cta = the LB /
+ * Heun-corrector kernel's tuned z-chunk (tuned per class and per kernel; the
+ * first class's value), 0 before the first step or on the generic path.
+ * Either may be NULL. */
 LCBP_API int lcbp_batch_get_path(lcbp_batch *b, int *fast, int *planes_per_cta);
 /* R, total sites, tuned tile shape (tx, ty, tz) and persistent CTAs per launch
  * of the generic path, steps done. */
