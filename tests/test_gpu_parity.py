@@ -468,3 +468,43 @@ def test_full_size_sampled_parity_256_walls(lcbp):
         dq = np.abs(q1[:, z, y, x] - lbq.q9_to_q5(Qo)[:, cz, r, r]).max()
         du = np.abs(u1[:, z, y, x] - np.moveaxis(lbq.moments(fo)[1], -1, 0)[:, cz, r, r]).max()
         assert dq < 1e-6 and du < 1e-6, ((z, y, x), dq, du)
+
+
+# ---------------------------------------------------------------------------
+# Largest lattice of the fast path: its kernels index every field of a lattice
+# with 32-bit offsets and the host takes the path only where those fit
+# (15 population planes, the 16-value scratch and the Q mirror within 2^31 - 1
+# elements).  512 x 512 x 506 is the last nz that fits at 512 x 512; one step
+# there, compared site by site with the oracle as above (the far corner, where
+# the offsets are largest, among the sites), and nz = 507 leaves the path.
+# ---------------------------------------------------------------------------
+def test_largest_fast_path_lattice_sampled(lcbp):
+    p = lbq.Params(q0=2 * np.pi / 32)
+    nx, ny, nz = 512, 512, 506
+    lat = make(lcbp, (nz, ny, nx), "f32", p)
+    lat.init_q(lcbp.BPII, 0.3, noise=1e-4, seed=SEED)
+    lat.init_f_equilibrium(1.0)
+    lat.step(1)
+    assert lat.path()[0]
+    q0 = lat.read_q(dtype=np.float32)
+    f0 = lat.read_f(dtype=np.float32)
+    lat.step(1)
+    q1 = lat.read_q(dtype=np.float32)
+    u1 = lat.read_u(dtype=np.float32)
+    lat.close()
+    rng = np.random.default_rng(13)
+    sites = [(int(rng.integers(0, nz)), int(rng.integers(0, ny)), int(rng.integers(0, nx))) for _ in range(6)]
+    sites += [(0, 0, 0), (nz - 1, ny - 1, nx - 1), (nz - 1, 0, nx - 1), (nz // 2, ny - 1, 0)]
+    r = 4
+    for (z, y, x) in sites:
+        idx = [np.arange(c - r, c + r + 1) % m for c, m in ((z, nz), (y, ny), (x, nx))]
+        cube = np.ix_(idx[0], idx[1], idx[2])
+        Qc = lbq.q5_to_q9(q0[(slice(None),) + cube].astype(np.float64))
+        fc = lbq.f_from_soa(f0[(slice(None),) + cube].astype(np.float64))
+        fo, Qo = lbq.step(fc, Qc, p)
+        dq = np.abs(q1[:, z, y, x] - lbq.q9_to_q5(Qo)[:, r, r, r]).max()
+        du = np.abs(u1[:, z, y, x] - oracle_u(fo)[:, r, r, r]).max()
+        assert dq < 1e-6 and du < 1e-6, ((z, y, x), dq, du)
+    big = make(lcbp, (nz + 1, ny, nx), "f32", p)
+    assert not big.path()[0]
+    big.close()
