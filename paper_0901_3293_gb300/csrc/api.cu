@@ -412,7 +412,11 @@ bool use_fast(lcbp_lattice* h) {
     const long long cq = (long long)nxm * nyq * h->nz;
     bool ok = make_mirror_tmap(&h->tm[0], h->qm, 4 * nxm, nyq, h->nz, 4 * kZmBoxX, ty + 4, h->dtype) &&
               make_mirror_tmap(&h->tm[8], static_cast<char*>(h->qm) + 4 * cq * h->es, nxm, nyq, h->nz, kZmBoxX,
-                               ty + 4, h->dtype);
+                               ty + 4, h->dtype) &&
+              // the same in tile-sized boxes (k_lbq's prefetches of Q^n at its own sites)
+              make_mirror_tmap(&h->tm[4], h->qm, 4 * nxm, nyq, h->nz, 4 * 32, ty, h->dtype) &&
+              make_mirror_tmap(&h->tm[5], static_cast<char*>(h->qm) + 4 * cq * h->es, nxm, nyq, h->nz, 32, ty,
+                               h->dtype);
     for (int k = 0; k < 2; ++k)
       ok = ok && make_mirror_tmap(&h->tm[1 + k], h->um[k], 4 * nxm, nyu, h->nz, 4 * kZmBoxXU, ty + 2, h->dtype);
     const int nxp = h->nx + kZmPadX;
@@ -444,6 +448,8 @@ ZmArgs zm_args(lcbp_lattice* h, const void* model) {
   a.tm_pq = &h->tm[3];
   a.tm_u3 = &h->tm[1 + h->cur];
   a.tm_f = &h->tm[6 + h->cur];
+  a.tm_qpf = &h->tm[4];
+  a.tm_q1pf = &h->tm[5];
   a.q = h->qm;
   a.qout = nullptr;
   a.pq = h->pq;

@@ -201,6 +201,9 @@ struct ZmArgs {
   // padded scratch (16 values per site)
   const CUtensorMap *tm_q, *tm_q1, *tm_u, *tm_pq, *tm_u3;
   const CUtensorMap* tm_f;  // f^n (15 components), for L2 prefetches of the pulled populations
+  // the Q mirror in boxes of one tile (32 x TY sites, no halo), for k_lbq's L2
+  // prefetches of Q^n: it reads Q^n at its own sites only
+  const CUtensorMap *tm_qpf, *tm_q1pf;
   void *q, *qout, *pq;  // qout: nullptr = update Q in place; pq: padded scratch
   const void* bext;
   void *f, *fnew, *rhou, *rhou_new;

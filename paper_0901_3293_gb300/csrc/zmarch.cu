@@ -765,9 +765,9 @@ struct LbqSmem {
 // that would arrive from beyond a wall is the reflected one of the same site
 // (half-way bounce-back); the staged Q* of a ghost plane is the anchored qw and
 // its velocity is -u of the adjacent plane.
-// tmF, tmQ, tmQ1: maps of f^n and of the Q^n mirror (for a batch, the
-// class's, with the replica outermost), whose planes are prefetched into L2
-// one plane before the loads read them
+// tmF, tmQ, tmQ1: maps of f^n and of the Q^n mirror (for a single lattice in
+// tile-sized boxes; for a batch the class's, with the replica outermost),
+// whose planes are prefetched into L2 one plane before the loads read them
 template <typename real, int TY, int SPT, bool BATCH, bool WALLS, int TX = ZM_TX>
 __device__ __forceinline__ void lbq_body(const CUtensorMap* tmPQ, const CUtensorMap* tmU3, const CUtensorMap* tmF,
                                          const CUtensorMap* tmQ, const CUtensorMap* tmQ1, const ZmGeom& G,
@@ -829,13 +829,16 @@ __device__ __forceinline__ void lbq_body(const CUtensorMap* tmPQ, const CUtensor
     else tma_load_4d(sl, tmPQ, 4 * x0, y0, 0, zz, bar);
     // the populations of plane p (pulled from plane p-1 on) and Q^n of plane
     // p-1, into L2 a plane ahead of their plain loads
-    const int X = x0 - B::QX + B::QPX, Y = y0 - 2 + B::QPY;
     if constexpr (BATCH) {
+      // the class's Q maps have k_qside's boxes (a two-site halo)
+      const int X = x0 - B::QX + B::QPX, Y = y0 - 2 + B::QPY;
       tma_load_4d(sl + L::OFF_U, tmU3, 4 * (x0 - B::UX + B::UPX), y0 - 1 + B::UPY, zz, rc, bar);
       tma_prefetch_l2_5d(tmF, x0 - ZM_XOFF, y0 - 1, zz, 0, rc);
       tma_prefetch_l2_4d(tmQ, 4 * X, Y, wrap(p - 1, nz), rc);
       tma_prefetch_l2_4d(tmQ1, X, Y, wrap(p - 1, nz), rc);
     } else {
+      // a single lattice's Q maps here are tile-sized: the tile's own sites
+      const int X = x0 + B::QPX, Y = y0 + B::QPY;
       tma_load_3d(sl + L::OFF_U, tmU3, 4 * (x0 - B::UX + B::UPX), y0 - 1 + B::UPY, zz, bar);
       tma_prefetch_l2_4d(tmF, x0 - ZM_XOFF, y0 - 1, zz, 0);
       tma_prefetch_l2_3d(tmQ, 4 * X, Y, wrap(p - 1, nz));
@@ -1306,7 +1309,7 @@ cudaError_t launch_step_zm_spt(const ZmArgs& a, cudaStream_t s) {
       *a.tm_q, *a.tm_q1, *a.tm_u, Gq, m, static_cast<const real*>(a.bext), static_cast<real*>(a.pq), a.err, qw);
   if (a.events) cudaEventRecord(a.events[1], s);
   k_lbq<real, TY, SPT, WALLS><<<grid, ZM_TX * TY / SPT, LbqSmem<real, TY>::bytes, s>>>(
-      *a.tm_pq, *a.tm_u3, *a.tm_f, *a.tm_q, *a.tm_q1, G, m, static_cast<const real*>(a.f),
+      *a.tm_pq, *a.tm_u3, *a.tm_f, *a.tm_qpf, *a.tm_q1pf, G, m, static_cast<const real*>(a.f),
       static_cast<const real*>(a.q), static_cast<real*>(a.fnew), static_cast<real*>(a.rhou_new),
       static_cast<real*>(a.qout ? a.qout : a.q), a.err, qw);
   if (a.events) cudaEventRecord(a.events[2], s);
