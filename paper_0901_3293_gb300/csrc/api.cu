@@ -210,7 +210,7 @@ struct lcbp_lattice {
   int spt;        // sites per thread of k_lbq, set by the tuner
   int spt_q;      // sites per thread of k_qside, set by the tuner
   // Q mirror vectors, rho u mirror [0], [1], padded scratch, (unused), (unused), f [0], f [1], Q mirror yz
-  CUtensorMap tm[9];
+  CUtensorMap tm[13];
   int* d_err;
 };
 
@@ -365,12 +365,13 @@ lcbp_lattice* new_handle(int nx, int ny, int nz, int dtype) {
 }
 
 // ---- fast path: tensor maps, eligibility, autotuned z-chunk -------------------
-// field [comps][nz][ny][nx] as a 4-D tensor, box = 40 x rows x 1 x comps
-bool make_field_tmap(CUtensorMap* tm, void* base, int comps, int nx, int ny, int nz, int rows, int dtype) {
+// field [comps][nz][ny][nx] as a 4-D tensor, box = 40 x rows x 1 x box_comps
+bool make_field_tmap(CUtensorMap* tm, void* base, int comps, int nx, int ny, int nz, int rows, int box_comps,
+                     int dtype) {
   const cuuint64_t es = dtype_size(dtype);
   const cuuint64_t dims[4] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz, (cuuint64_t)comps};
   const cuuint64_t strides[3] = {nx * es, (cuuint64_t)nx * ny * es, (cuuint64_t)nx * ny * nz * es};
-  const cuuint32_t box[4] = {(cuuint32_t)kZmBoxX, (cuuint32_t)rows, 1, (cuuint32_t)comps};
+  const cuuint32_t box[4] = {(cuuint32_t)kZmBoxX, (cuuint32_t)rows, 1, (cuuint32_t)box_comps};
   return encode_tiled(tm, base, 4, dims, strides, box, dtype);
 }
 
@@ -421,8 +422,11 @@ bool use_fast(lcbp_lattice* h) {
       ok = ok && make_mirror_tmap(&h->tm[1 + k], h->um[k], 4 * nxm, nyu, h->nz, 4 * kZmBoxXU, ty + 2, h->dtype);
     const int nxp = h->nx + kZmPadX;
     ok = ok && make_scratch_tmap(&h->tm[3], h->pq, nxp, nyu, h->nz, ty + 2, h->dtype);
-    for (int k = 0; k < 2; ++k)  // the populations (L2 prefetches only)
-      ok = ok && make_field_tmap(&h->tm[6 + k], h->f[k], NV, h->nx, h->ny, h->nz, ty + 2, h->dtype);
+    for (int k = 0; k < 2; ++k) {  // the populations (L2 prefetches only): the tile's rows, then halo-row boxes
+      ok = ok && make_field_tmap(&h->tm[6 + k], h->f[k], NV, h->nx, h->ny, h->nz, ty, NV, h->dtype);
+      ok = ok && make_field_tmap(&h->tm[9 + k], h->f[k], NV, h->nx, h->ny, h->nz, 1, 1, h->dtype);
+      ok = ok && make_field_tmap(&h->tm[11 + k], h->f[k], NV, h->nx, h->ny, h->nz, 1, 2, h->dtype);
+    }
     if (!ok) {
       h->path_req = LCBP_PATH_GENERIC;  // tensor maps unavailable: stay on the generic kernels
       return false;
@@ -448,6 +452,8 @@ ZmArgs zm_args(lcbp_lattice* h, const void* model) {
   a.tm_pq = &h->tm[3];
   a.tm_u3 = &h->tm[1 + h->cur];
   a.tm_f = &h->tm[6 + h->cur];
+  a.tm_f1 = &h->tm[9 + h->cur];
+  a.tm_f2 = &h->tm[11 + h->cur];
   a.tm_qpf = &h->tm[4];
   a.tm_q1pf = &h->tm[5];
   a.q = h->qm;

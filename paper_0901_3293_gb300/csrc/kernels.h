@@ -200,7 +200,10 @@ struct ZmArgs {
   // TY + 4; the rho u mirror (tm_u, 4-vectors; tm_u3 the same for k_lbq); the
   // padded scratch (16 values per site)
   const CUtensorMap *tm_q, *tm_q1, *tm_u, *tm_pq, *tm_u3;
-  const CUtensorMap* tm_f;  // f^n (15 components), for L2 prefetches of the pulled populations
+  // f^n for L2 prefetches of the pulled populations: the tile's rows with all
+  // 15 components (tm_f), and the halo rows' inward-moving populations in
+  // boxes of one (tm_f1) or two (tm_f2) components
+  const CUtensorMap *tm_f, *tm_f1, *tm_f2;
   // the Q mirror in boxes of one tile (32 x TY sites, no halo), for k_lbq's L2
   // prefetches of Q^n: it reads Q^n at its own sites only
   const CUtensorMap *tm_qpf, *tm_q1pf;

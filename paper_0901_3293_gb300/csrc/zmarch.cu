@@ -770,6 +770,7 @@ struct LbqSmem {
 // whose planes are prefetched into L2 one plane before the loads read them
 template <typename real, int TY, int SPT, bool BATCH, bool WALLS, int TX = ZM_TX>
 __device__ __forceinline__ void lbq_body(const CUtensorMap* tmPQ, const CUtensorMap* tmU3, const CUtensorMap* tmF,
+                                         const CUtensorMap* tmF1, const CUtensorMap* tmF2,
                                          const CUtensorMap* tmQ, const CUtensorMap* tmQ1, const ZmGeom& G,
                                          const Model<real>& m, int bt, int rc, const real* __restrict__ f,
                                          const real* __restrict__ Qin, real* __restrict__ fnew,
@@ -812,6 +813,10 @@ __device__ __forceinline__ void lbq_body(const CUtensorMap* tmPQ, const CUtensor
     tma_prefetch_desc(tmF);
     tma_prefetch_desc(tmQ);
     tma_prefetch_desc(tmQ1);
+    if constexpr (!BATCH) {
+      tma_prefetch_desc(tmF1);
+      tma_prefetch_desc(tmF2);
+    }
   }
   __syncthreads();
 
@@ -840,7 +845,17 @@ __device__ __forceinline__ void lbq_body(const CUtensorMap* tmPQ, const CUtensor
       // a single lattice's Q maps here are tile-sized: the tile's own sites
       const int X = x0 + B::QPX, Y = y0 + B::QPY;
       tma_load_3d(sl + L::OFF_U, tmU3, 4 * (x0 - B::UX + B::UPX), y0 - 1 + B::UPY, zz, bar);
-      tma_prefetch_l2_4d(tmF, x0 - ZM_XOFF, y0 - 1, zz, 0);
+      // f: the tile's rows with all 15 populations; of the halo rows only the
+      // populations that move into the tile: +y (3; 7, 8; 11, 12) from row
+      // y0 - 1, -y (4; 9, 10; 13, 14) from the row after the tile
+      const int ya = wrap(y0 - 1, ny), yb = wrap(min(y0 + TY, ny), ny), xf = x0 - ZM_XOFF;
+      tma_prefetch_l2_4d(tmF, xf, y0, zz, 0);
+      tma_prefetch_l2_4d(tmF1, xf, ya, zz, 3);
+      tma_prefetch_l2_4d(tmF2, xf, ya, zz, 7);
+      tma_prefetch_l2_4d(tmF2, xf, ya, zz, 11);
+      tma_prefetch_l2_4d(tmF1, xf, yb, zz, 4);
+      tma_prefetch_l2_4d(tmF2, xf, yb, zz, 9);
+      tma_prefetch_l2_4d(tmF2, xf, yb, zz, 13);
       tma_prefetch_l2_3d(tmQ, 4 * X, Y, wrap(p - 1, nz));
       tma_prefetch_l2_3d(tmQ1, X, Y, wrap(p - 1, nz));
     }
@@ -1150,12 +1165,13 @@ __device__ __forceinline__ void lbq_body(const CUtensorMap* tmPQ, const CUtensor
 template <typename real, int TY, int SPT, bool WALLS>
 __global__ void __launch_bounds__(ZM_TX* TY / SPT, 2)
     k_lbq(const __grid_constant__ CUtensorMap tmPQ, const __grid_constant__ CUtensorMap tmU3,
-          const __grid_constant__ CUtensorMap tmF, const __grid_constant__ CUtensorMap tmQ,
+          const __grid_constant__ CUtensorMap tmF, const __grid_constant__ CUtensorMap tmF1,
+          const __grid_constant__ CUtensorMap tmF2, const __grid_constant__ CUtensorMap tmQ,
           const __grid_constant__ CUtensorMap tmQ1, ZmGeom G, Model<real> m, const real* __restrict__ f,
           const real* __restrict__ Qin, real* __restrict__ fnew, real* __restrict__ rhou_new, real* __restrict__ Qout,
           int* __restrict__ err, Sym5<real> qw) {
-  lbq_body<real, TY, SPT, false, WALLS>(&tmPQ, &tmU3, &tmF, &tmQ, &tmQ1, G, m, blockIdx.x, 0, f, Qin, fnew, rhou_new,
-                                        Qout, err, qw);
+  lbq_body<real, TY, SPT, false, WALLS>(&tmPQ, &tmU3, &tmF, &tmF1, &tmF2, &tmQ, &tmQ1, G, m, blockIdx.x, 0, f, Qin,
+                                        fnew, rhou_new, Qout, err, qw);
 }
 
 template <typename real, int TY>
@@ -1191,13 +1207,13 @@ __global__ void __launch_bounds__(ZM_TX* TY, 2)
     }
   if constexpr (sizeof(real) == 4) {
     if (G.tx == kZmNarrowX) {
-      lbq_body<real, 2 * TY, 1, true, false, kZmNarrowX>(mpq, mu3, mf, mq, mq1, G, m, it.bt, it.j,
+      lbq_body<real, 2 * TY, 1, true, false, kZmNarrowX>(mpq, mu3, mf, nullptr, nullptr, mq, mq1, G, m, it.bt, it.j,
                                                          f + NV * o, Qin + qo, fnew + NV * o, rhou_new + uo,
                                                          Qout + qo, err, Sym5<real>{});
       return;
     }
   }
-  lbq_body<real, TY, 1, true, false>(mpq, mu3, mf, mq, mq1, G, m, it.bt, it.j, f + NV * o, Qin + qo,
+  lbq_body<real, TY, 1, true, false>(mpq, mu3, mf, nullptr, nullptr, mq, mq1, G, m, it.bt, it.j, f + NV * o, Qin + qo,
                                      fnew + NV * o, rhou_new + uo, Qout + qo, err, Sym5<real>{});
 }
 
@@ -1309,7 +1325,7 @@ cudaError_t launch_step_zm_spt(const ZmArgs& a, cudaStream_t s) {
       *a.tm_q, *a.tm_q1, *a.tm_u, Gq, m, static_cast<const real*>(a.bext), static_cast<real*>(a.pq), a.err, qw);
   if (a.events) cudaEventRecord(a.events[1], s);
   k_lbq<real, TY, SPT, WALLS><<<grid, ZM_TX * TY / SPT, LbqSmem<real, TY>::bytes, s>>>(
-      *a.tm_pq, *a.tm_u3, *a.tm_f, *a.tm_qpf, *a.tm_q1pf, G, m, static_cast<const real*>(a.f),
+      *a.tm_pq, *a.tm_u3, *a.tm_f, *a.tm_f1, *a.tm_f2, *a.tm_qpf, *a.tm_q1pf, G, m, static_cast<const real*>(a.f),
       static_cast<const real*>(a.q), static_cast<real*>(a.fnew), static_cast<real*>(a.rhou_new),
       static_cast<real*>(a.qout ? a.qout : a.q), a.err, qw);
   if (a.events) cudaEventRecord(a.events[2], s);
