@@ -137,17 +137,26 @@ bool build_maps(lcbp_batch* b) {
               mirror(&b->maps[1].u[k], b->um[1], c.um0, 4 * nxm, nyu, 4 * cu, 4 * (tx + 2), ty + 2) &&
               encode_tiled(&b->maps[0].pq[k], static_cast<char*>(b->pq) + (size_t)c.pq0 * b->es, 5, pdims, pstr,
                            pbox, b->dtype);
-    // the flat populations of the class's replicas (blocks of NV * round64(n) elements) for L2 prefetches
+    // k_lbq's L2 prefetches: the Q mirrors in tile-sized boxes, and the flat
+    // populations of the class's replicas (blocks of NV * round64(n) elements)
+    // in boxes of the tile's rows (all populations) or of one halo row (one or
+    // two populations)
+    ok = ok && mirror(&b->maps[0].qpf[k], b->qm, c.qm0, 4 * nxm, nyq, 5 * cq, 4 * tx, ty) &&
+         mirror(&b->maps[0].q1pf[k], b->qm, c.qm0 + 4 * (long long)cq, nxm, nyq, 5 * cq, tx, ty);
     const cuuint64_t rstride = (cuuint64_t)NV * ((c.G.n + 63) / 64 * 64);
     const cuuint64_t fdims[5] = {nx, ny, nz, (cuuint64_t)NV, (cuuint64_t)c.count};
     const cuuint64_t fstr[4] = {nx * es, nx * ny * es, nx * ny * nz * es, rstride * es};
-    const cuuint32_t fbox[5] = {(cuuint32_t)(tx + 8), (cuuint32_t)(ty + 2), 1, (cuuint32_t)NV, 1};
+    const cuuint32_t fbox[5] = {(cuuint32_t)(tx + 8), (cuuint32_t)ty, 1, (cuuint32_t)NV, 1};
+    const cuuint32_t fbox1[5] = {(cuuint32_t)(tx + 8), 1, 1, 1, 1}, fbox2[5] = {(cuuint32_t)(tx + 8), 1, 1, 2, 1};
     for (int j = 0; j < 2 && ok; ++j) {
-      const long long o = b->base[b->order[c.rep0]];  // the class's first replica
-      ok = encode_tiled(&b->maps[j].f[k], static_cast<char*>(b->f[j]) + (size_t)NV * o * es, 5, fdims, fstr, fbox,
-                        b->dtype);
+      char* fb = static_cast<char*>(b->f[j]) + (size_t)NV * b->base[b->order[c.rep0]] * es;  // first replica
+      ok = encode_tiled(&b->maps[j].f[k], fb, 5, fdims, fstr, fbox, b->dtype) &&
+           encode_tiled(&b->maps[j].f1[k], fb, 5, fdims, fstr, fbox1, b->dtype) &&
+           encode_tiled(&b->maps[j].f2[k], fb, 5, fdims, fstr, fbox2, b->dtype);
     }
     if (!ok) return false;
+    b->maps[1].qpf[k] = b->maps[0].qpf[k];
+    b->maps[1].q1pf[k] = b->maps[0].q1pf[k];
     b->maps[0].u3[k] = b->maps[0].u[k];
     b->maps[1].u3[k] = b->maps[1].u[k];
     b->maps[1].q[k] = b->maps[0].q[k];

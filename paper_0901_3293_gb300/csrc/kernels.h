@@ -247,13 +247,15 @@ struct ZmBatch {
 };
 // Per class, with the replica as the outermost coordinate: the Q mirrors'
 // [xx xy xz yy] vectors (q) and yz arrays (q1), the rho u mirrors (u; u3 the
-// same for k_lbq), the padded scratch (pq, 5-D) and the flat populations
-// (f, 5-D (x, y, z, i, replica); L2 prefetches only).  Boxes fit the class's
-// tile of tx x ty sites: Q and f tx + 8 sites wide (from x0 - 4), Q ty + 4
-// rows, the others tx + 2 wide and ty + 2 rows.
+// same for k_lbq) and the padded scratch (pq, 5-D).  Boxes fit the class's
+// tile of tx x ty sites: Q tx + 8 sites wide (from x0 - 4) and ty + 4 rows,
+// the others tx + 2 wide and ty + 2 rows.  For k_lbq's L2 prefetches only:
+// the Q mirrors in tile-sized boxes (qpf, q1pf) and the flat populations as
+// 5-D tensors (x, y, z, i, replica), tx + 8 wide, in boxes of the tile's rows
+// with all 15 populations (f) or of one halo row with one (f1) or two (f2).
 struct ZmBatchMaps {
   CUtensorMap q[kZmMaxClasses], q1[kZmMaxClasses], u[kZmMaxClasses], pq[kZmMaxClasses], u3[kZmMaxClasses],
-      f[kZmMaxClasses];
+      f[kZmMaxClasses], qpf[kZmMaxClasses], q1pf[kZmMaxClasses], f1[kZmMaxClasses], f2[kZmMaxClasses];
 };
 struct ZmBatchArgs {
   ZmBatch B;   // classes and CTA ranges of k_lbq_batch

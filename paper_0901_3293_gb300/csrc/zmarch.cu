@@ -765,9 +765,11 @@ struct LbqSmem {
 // that would arrive from beyond a wall is the reflected one of the same site
 // (half-way bounce-back); the staged Q* of a ghost plane is the anchored qw and
 // its velocity is -u of the adjacent plane.
-// tmF, tmQ, tmQ1: maps of f^n and of the Q^n mirror (for a single lattice in
-// tile-sized boxes; for a batch the class's, with the replica outermost),
-// whose planes are prefetched into L2 one plane before the loads read them
+// tmF, tmF1, tmF2, tmQ, tmQ1: maps of f^n (boxes of the tile's rows with
+// every population, and of one halo row with one or two populations) and of
+// the Q^n mirror in tile-sized boxes (for a batch the class's, with the
+// replica outermost), whose planes are prefetched into L2 one plane before
+// the loads read them
 template <typename real, int TY, int SPT, bool BATCH, bool WALLS, int TX = ZM_TX>
 __device__ __forceinline__ void lbq_body(const CUtensorMap* tmPQ, const CUtensorMap* tmU3, const CUtensorMap* tmF,
                                          const CUtensorMap* tmF1, const CUtensorMap* tmF2,
@@ -811,12 +813,10 @@ __device__ __forceinline__ void lbq_body(const CUtensorMap* tmPQ, const CUtensor
     tma_prefetch_desc(tmPQ);
     tma_prefetch_desc(tmU3);
     tma_prefetch_desc(tmF);
+    tma_prefetch_desc(tmF1);
+    tma_prefetch_desc(tmF2);
     tma_prefetch_desc(tmQ);
     tma_prefetch_desc(tmQ1);
-    if constexpr (!BATCH) {
-      tma_prefetch_desc(tmF1);
-      tma_prefetch_desc(tmF2);
-    }
   }
   __syncthreads();
 
@@ -833,22 +833,26 @@ __device__ __forceinline__ void lbq_body(const CUtensorMap* tmPQ, const CUtensor
     if constexpr (BATCH) tma_load_5d(sl, tmPQ, 4 * x0, y0, 0, zz, rc, bar);
     else tma_load_4d(sl, tmPQ, 4 * x0, y0, 0, zz, bar);
     // the populations of plane p (pulled from plane p-1 on) and Q^n of plane
-    // p-1, into L2 a plane ahead of their plain loads
+    // p-1, into L2 a plane ahead of their plain loads.  Q^n in tile-sized
+    // boxes (the tile's own sites); f for the tile's rows with all 15
+    // populations and, of the halo rows, only the populations that move into
+    // the tile: +y (3; 7, 8; 11, 12) from row y0 - 1, -y (4; 9, 10; 13, 14)
+    // from the row after the tile
+    const int X = x0 + B::QPX, Y = y0 + B::QPY;
+    const int ya = wrap(y0 - 1, ny), yb = wrap(min(y0 + TY, ny), ny), xf = x0 - ZM_XOFF;
     if constexpr (BATCH) {
-      // the class's Q maps have k_qside's boxes (a two-site halo)
-      const int X = x0 - B::QX + B::QPX, Y = y0 - 2 + B::QPY;
       tma_load_4d(sl + L::OFF_U, tmU3, 4 * (x0 - B::UX + B::UPX), y0 - 1 + B::UPY, zz, rc, bar);
-      tma_prefetch_l2_5d(tmF, x0 - ZM_XOFF, y0 - 1, zz, 0, rc);
+      tma_prefetch_l2_5d(tmF, xf, y0, zz, 0, rc);
+      tma_prefetch_l2_5d(tmF1, xf, ya, zz, 3, rc);
+      tma_prefetch_l2_5d(tmF2, xf, ya, zz, 7, rc);
+      tma_prefetch_l2_5d(tmF2, xf, ya, zz, 11, rc);
+      tma_prefetch_l2_5d(tmF1, xf, yb, zz, 4, rc);
+      tma_prefetch_l2_5d(tmF2, xf, yb, zz, 9, rc);
+      tma_prefetch_l2_5d(tmF2, xf, yb, zz, 13, rc);
       tma_prefetch_l2_4d(tmQ, 4 * X, Y, wrap(p - 1, nz), rc);
       tma_prefetch_l2_4d(tmQ1, X, Y, wrap(p - 1, nz), rc);
     } else {
-      // a single lattice's Q maps here are tile-sized: the tile's own sites
-      const int X = x0 + B::QPX, Y = y0 + B::QPY;
       tma_load_3d(sl + L::OFF_U, tmU3, 4 * (x0 - B::UX + B::UPX), y0 - 1 + B::UPY, zz, bar);
-      // f: the tile's rows with all 15 populations; of the halo rows only the
-      // populations that move into the tile: +y (3; 7, 8; 11, 12) from row
-      // y0 - 1, -y (4; 9, 10; 13, 14) from the row after the tile
-      const int ya = wrap(y0 - 1, ny), yb = wrap(min(y0 + TY, ny), ny), xf = x0 - ZM_XOFF;
       tma_prefetch_l2_4d(tmF, xf, y0, zz, 0);
       tma_prefetch_l2_4d(tmF1, xf, ya, zz, 3);
       tma_prefetch_l2_4d(tmF2, xf, ya, zz, 7);
@@ -1195,25 +1199,28 @@ __global__ void __launch_bounds__(ZM_TX* TY, 2)
   const long long o = reps[r].base;  // the flat populations of the replica
   const long long qo = qm0 + (long long)it.j * 5 * G.cq, uo = um0 + (long long)it.j * 4 * G.cu;  // its mirrors
   const Model<real> m = reps[r].m;
-  const CUtensorMap *mpq = &maps.pq[0], *mu3 = &maps.u3[0], *mf = &maps.f[0], *mq = &maps.q[0], *mq1 = &maps.q1[0];
+  const CUtensorMap *mpq = &maps.pq[0], *mu3 = &maps.u3[0], *mf = &maps.f[0], *mf1 = &maps.f1[0],
+                    *mf2 = &maps.f2[0], *mq = &maps.qpf[0], *mq1 = &maps.q1pf[0];
 #pragma unroll
   for (int i = 1; i < kZmMaxClasses; ++i)
     if (i == it.k) {
       mpq = &maps.pq[i];
       mu3 = &maps.u3[i];
       mf = &maps.f[i];
-      mq = &maps.q[i];
-      mq1 = &maps.q1[i];
+      mf1 = &maps.f1[i];
+      mf2 = &maps.f2[i];
+      mq = &maps.qpf[i];
+      mq1 = &maps.q1pf[i];
     }
   if constexpr (sizeof(real) == 4) {
     if (G.tx == kZmNarrowX) {
-      lbq_body<real, 2 * TY, 1, true, false, kZmNarrowX>(mpq, mu3, mf, nullptr, nullptr, mq, mq1, G, m, it.bt, it.j,
+      lbq_body<real, 2 * TY, 1, true, false, kZmNarrowX>(mpq, mu3, mf, mf1, mf2, mq, mq1, G, m, it.bt, it.j,
                                                          f + NV * o, Qin + qo, fnew + NV * o, rhou_new + uo,
                                                          Qout + qo, err, Sym5<real>{});
       return;
     }
   }
-  lbq_body<real, TY, 1, true, false>(mpq, mu3, mf, nullptr, nullptr, mq, mq1, G, m, it.bt, it.j, f + NV * o, Qin + qo,
+  lbq_body<real, TY, 1, true, false>(mpq, mu3, mf, mf1, mf2, mq, mq1, G, m, it.bt, it.j, f + NV * o, Qin + qo,
                                      fnew + NV * o, rhou_new + uo, Qout + qo, err, Sym5<real>{});
 }
 
