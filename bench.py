@@ -48,19 +48,19 @@ STATE_BYTES = (15 + 5) * 2 * 4  # read + write of f and Q once per site-step (FP
 HBM_NOMINAL_GBS = 7900.0  # GB300 HBM3e data-sheet bandwidth (the measured copy peak is the roofline)
 # DRAM bytes per site of one launch of each fast kernel (dram__bytes_read.sum +
 # dram__bytes_write.sum), from an ncu capture of 160^3 FP32 with its own
-# tuning (planes per CTA: k_lbq 11, k_qside 54; one site per thread);
+# tuning (planes per CTA: k_lbq 9, k_qside 54; one site per thread);
 # summary and command in profiles/step_256cube_fast_path.md.  Traffic per
 # launch scales with the sites.  Valid only for the kernel sources it was
 # taken on (hash below); otherwise null.
 MEASURED_TRAFFIC = {
     "sources": ["paper_0901_3293_gb300/csrc/zmarch.cu", "paper_0901_3293_gb300/csrc/common.cuh",
                 "paper_0901_3293_gb300/csrc/tma.cuh", "paper_0901_3293_gb300/csrc/kernels.h"],
-    "sha256_16": "43a4e60a08ef83bb",
+    "sha256_16": "83a89e0b63237421",
     # one launch of each kernel in the capture (ncu --set full)
-    "bytes_per_site": {"qside": (181613312 + 212362240) / 160 ** 3,
-                       "lbq": (780454912 + 364930304) / 160 ** 3},
+    "bytes_per_site": {"qside": (181522432 + 211604224) / 160 ** 3,
+                       "lbq": (772152320 + 364112384) / 160 ** 3},
     # smsp__inst_executed.sum (warp instructions) x 32 of the same launches
-    "thread_instr_per_site": {"qside": 101004852 * 32 / 160 ** 3, "lbq": 118034616 * 32 / 160 ** 3},
+    "thread_instr_per_site": {"qside": 101004852 * 32 / 160 ** 3, "lbq": 118693712 * 32 / 160 ** 3},
 }
 ORACLE_SAMPLE = 32  # side of the periodic cube the oracle steps (two BPII unit cells)
 WALL_Q = (0.2, 0.0, 0.0, -0.1, 0.0)  # planar anchoring S (x x - I/3), S = 0.3, on the ghost planes
